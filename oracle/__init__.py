@@ -1,0 +1,24 @@
+"""Plain, slow, float64 CPU oracle of the constrained DTT/FFT elasticity solver
+(Gelebart & Amouzou-Adoun, "Constrained minimization problems and FFT-based solvers").
+
+THIS PACKAGE IS TEST INFRASTRUCTURE.  Only the tests, the smoke check of
+__graft_entry__ and the cpu_baseline / reference legs of bench.py may import it.  The
+CUDA product path never calls it and shares no code with it.
+
+Modules:
+  transforms   -- DCT1/DCT3/DST1/DST3/DFT as naive O(n^2) trigonometric sums
+                  (Section 3.2.2, Tables 2-3, Eq. 7)
+  discrete     -- grid, BCs, HEX1/TETRA2 operators, stress, divergence, Paux R0 and its
+                  symbol, Green step, Eq. 5 residual (Sections 3.1-3.2)
+  constraints  -- strong / weak / smooth / tie rows, proj_U and proj_P, reactions,
+                  sphere-contact geometry (Sections 4.1-4.2, 5.1)
+  solver       -- Anderson acceleration, Algorithm 1, Algorithm 2
+  kkt          -- element-by-element stiffness and dense multiplier solve (Section 4.3)
+  hertz        -- Eq. 30
+
+Parity status: every function is pinned by a "not gpu" test except the Anderson
+combination rule (parity unpinned -- the paper cites the method without printing
+an accelerated iterate; it is checked only for self-consistency: the accelerated
+solve must reach the same solution as the dense multiplier system).
+"""
+from . import transforms, discrete, constraints, solver, kkt, hertz  # noqa: F401

@@ -1,0 +1,250 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module only draws and lays out inputs (grid sizes, boundary-condition codes,
+phase maps, material constants, constraint *intents*, indenter positions).  It holds
+none of the solver's arithmetic: the constraint rows (their weights) are built from the
+intents separately by the oracle and by the CUDA package's own host helpers.
+
+Boundary-condition codes: 0 periodic, 1 Dirichlet, 2 Neumann; bc[axis][face][component].
+Schemes: 0 TETRA2, 1 HEX1.
+
+The paper measures on synthetic geometries of its own (a half compact-tension-like
+specimen, Section 4.1.2; a spherical indentation of a cube, Section 5.4) and uses no
+public dataset; the workloads below are seeded stand-ins with those structures.
+"""
+import numpy as np
+
+P, D, N = 0, 1, 2
+TETRA2, HEX1 = 0, 1
+
+
+def lame(E, nu):
+    return E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), E / (2.0 * (1.0 + nu))
+
+
+class Workload(dict):
+    """nvox, h, bc, scheme, phase (nz,ny,nx) uint8, lam, mu, eps_star (3x3),
+    intents (list of dicts), lam0, mu0, tol, acv_mod, optional indenter."""
+    __getattr__ = dict.__getitem__
+
+
+def node_counts(nvox, bc):
+    return tuple(nvox[d] if bc[d][0][0] == P else nvox[d] + 1 for d in range(3))
+
+
+def on_dirichlet(nvox, bc, ijk, c):
+    """True if node ijk of component c lies on a Dirichlet face (no unknown there)."""
+    for d in range(3):
+        if bc[d][0][c] == P:
+            continue
+        if ijk[d] == 0 and bc[d][0][c] == D:
+            return True
+        if ijk[d] == nvox[d] and bc[d][1][c] == D:
+            return True
+    return False
+
+
+# ---------------------------------------------------------------------------
+# Cube 16^3 with a half-clamped bottom and 5 pinned interior nodes
+# ---------------------------------------------------------------------------
+def cube16(seed=1, n=16, scheme=TETRA2):
+    """16x16x16 voxels, E=1, nu=0.3.  Bottom face z=0: u=0 on nodes with x<n/2 (strong
+    rows), free elsewhere; top face: u_z = -0.01 (Dirichlet through the lift
+    u*_z = -0.01 z / n); lateral faces: normal component Dirichlet (symmetry),
+    tangential components Neumann; 5 seeded interior nodes pinned at u = 0."""
+    rng = np.random.default_rng(seed)
+    bc = np.full((3, 2, 3), N, dtype=np.int64)
+    bc[0, :, 0] = D
+    bc[1, :, 1] = D
+    bc[2, 1, 2] = D
+    lam, mu = lame(1.0, 0.3)
+    eps = np.zeros((3, 3))
+    eps[2, 2] = -0.01 / n
+    nvox = (n, n, n)
+    intents = []
+    for i in range(n // 2):
+        for j in range(n + 1):
+            for c in range(3):
+                if not on_dirichlet(nvox, bc, (i, j, 0), c):
+                    intents.append(dict(kind="strong", ijk=(i, j, 0), comp=c, value=0.0))
+    pins = set()
+    while len(pins) < 5:
+        pins.add(tuple(int(v) for v in rng.integers(1, n, size=3)))
+    for ijk in sorted(pins):
+        for c in range(3):
+            intents.append(dict(kind="strong", ijk=ijk, comp=c, value=0.0))
+    return Workload(name="cube16 + 5 pinned nodes", nvox=nvox, h=1.0, bc=bc, scheme=scheme,
+                    phase=np.zeros((n, n, n), np.uint8), lam=np.array([lam]), mu=np.array([mu]),
+                    eps_star=eps, intents=intents, lam0=lam, mu0=mu, tol=1e-8, acv_mod=3)
+
+
+# ---------------------------------------------------------------------------
+# Compact-tension-like plate
+# ---------------------------------------------------------------------------
+def ct_plate(nx=128, ny=128, nz=32, scheme=TETRA2, notch_scale=0.0):
+    """128x128x32 voxels, E=210 (GPa, h=1), nu=0.3; notch of void voxels
+    (stiffness notch_scale * E) x in [0, 40*nx/128), y in [ny/2-2, ny/2+2), all z.
+    notch_scale defaults to 0, the paper's void of null properties (Section 4.1.2): with
+    1e-6 E the notch interior converges at a rate of about 1 - 1e-6 per iteration and
+    the Eq. 5 residual stalls near 1e-6.  Two pins
+    of radius 6*nx/128 through the thickness centred at x = 20*nx/128,
+    y = ny/2 +- 24*ny/128: nodes inside carry u_x = 0 and u_y = +-0.05.
+    The plate is traction-free.  As in the paper's CT-like set-up (Section 4.1.2), the
+    in-plane components get their Dirichlet faces through a one-voxel buffer frame of
+    null stiffness (voxels x = 0, nx-1 and y = 0, ny-1): u_x and u_y are Dirichlet on
+    the four lateral faces of the box, which transmit no force through the buffer; u_z is
+    Dirichlet on z = 0 (mid-thickness symmetry plane); all other faces Neumann."""
+    s = nx / 128.0
+    bc = np.full((3, 2, 3), N, dtype=np.int64)
+    bc[0, :, 0:2] = D
+    bc[1, :, 0:2] = D
+    bc[2, 0, 2] = D
+    E = 210.0
+    lam, mu = lame(E, 0.3)
+    lv, mv = lame(notch_scale * E, 0.3)
+    phase = np.zeros((nz, ny, nx), np.uint8)
+    phase[:, ny // 2 - 2: ny // 2 + 2, : int(round(40 * s))] = 1
+    phase[:, :, 0] = 2
+    phase[:, :, nx - 1] = 2
+    phase[:, 0, :] = 2
+    phase[:, ny - 1, :] = 2
+    r = 6.0 * s
+    cx = 20.0 * s
+    intents = []
+    for sign, cy in ((+1.0, ny / 2 + 24.0 * ny / 128.0), (-1.0, ny / 2 - 24.0 * ny / 128.0)):
+        for k in range(nz + 1):
+            for j in range(ny + 1):
+                for i in range(nx + 1):
+                    if (i - cx) ** 2 + (j - cy) ** 2 <= r * r:
+                        intents.append(dict(kind="strong", ijk=(i, j, k), comp=0, value=0.0))
+                        intents.append(dict(kind="strong", ijk=(i, j, k), comp=1, value=0.05 * sign))
+    return Workload(name="CT-like plate %dx%dx%d" % (nx, ny, nz), nvox=(nx, ny, nz), h=1.0, bc=bc,
+                    scheme=scheme, phase=phase, lam=np.array([lam, lv, 0.0]),
+                    mu=np.array([mu, mv, 0.0]), eps_star=np.zeros((3, 3)), intents=intents,
+                    lam0=lam / 2, mu0=mu / 2, tol=1e-6, acv_mod=2)
+
+
+# ---------------------------------------------------------------------------
+# Rigid-sphere indentation
+# ---------------------------------------------------------------------------
+def indentation(nx=256, ny=256, nz=128, R=64.0, steps=10, dmin=0.001, dmax=0.05,
+                scheme=TETRA2):
+    """Elastic block (E=1, nu=0.3), bottom z=0 clamped (Dirichlet, all components),
+    lateral faces traction-free, top face z=nz the potential contact surface.  Sphere of
+    radius R centred above the middle of the top face; the indentation depths d/R are
+    geometrically spaced from dmin to dmax over `steps` increments."""
+    bc = np.full((3, 2, 3), N, dtype=np.int64)
+    bc[2, 0, :] = D
+    lam, mu = lame(1.0, 0.3)
+    ratios = np.geomspace(dmin, dmax, steps)
+    centers = [np.array([nx / 2.0, ny / 2.0, nz + R - r * R]) for r in ratios]
+    return Workload(name="sphere indentation %dx%dx%d R=%g" % (nx, ny, nz, R), nvox=(nx, ny, nz),
+                    h=1.0, bc=bc, scheme=scheme, phase=np.zeros((nz, ny, nx), np.uint8),
+                    lam=np.array([lam]), mu=np.array([mu]), eps_star=np.zeros((3, 3)), intents=[],
+                    lam0=5 * lam, mu0=5 * mu, tol=1e-6, acv_mod=3,
+                    indenter=dict(axis=2, face=1, radius=R, centers=centers, ratios=ratios,
+                                  E=1.0, nu=0.3))
+
+
+# ---------------------------------------------------------------------------
+# Random small problems for parity tests
+# ---------------------------------------------------------------------------
+def random_bc(rng, periodic_prob=0.25):
+    bc = np.zeros((3, 2, 3), dtype=np.int64)
+    for d in range(3):
+        if rng.random() < periodic_prob:
+            bc[d] = P
+        else:
+            bc[d] = rng.choice([D, N], size=(2, 3))
+    return bc
+
+
+def random_problem(seed, nvox=None, nphase=2, n_strong=3, n_weak=2, n_smooth=1, n_tie=1,
+                   scheme=TETRA2, periodic_prob=0.25, eps_scale=1e-3, anchored=True):
+    """Random cell with random per-face BCs, a random two-phase map, a random eps* and
+    a few random constraints of every kind (disjoint supports, none on a Dirichlet-face
+    unknown).  anchored=True redraws until every component has a Dirichlet face on
+    two axes (no rigid or hourglass null modes)."""
+    rng = np.random.default_rng(seed)
+    if nvox is None:
+        nvox = tuple(int(v) for v in rng.integers(4, 9, size=3))
+    while True:
+        bc = random_bc(rng, periodic_prob)
+        if not anchored:
+            break
+        ok = all(sum(1 for d in range(3) if D in bc[d, :, c]) >= 2 for c in range(3))
+        if ok:
+            break
+    nn = node_counts(nvox, bc)
+    phase = rng.integers(0, nphase, size=(nvox[2], nvox[1], nvox[0])).astype(np.uint8)
+    Es = np.array([1.0, 3.0, 0.5][:nphase])
+    lam, mu = lame(Es, 0.3)
+    e = rng.uniform(-eps_scale, eps_scale, size=(3, 3))
+    eps = 0.5 * (e + e.T)
+    used = set()
+    intents = []
+
+    def free(nodes_comps):
+        for ijk, c in nodes_comps:
+            if (tuple(ijk), c) in used or on_dirichlet(nvox, bc, ijk, c):
+                return False
+        return True
+
+    def take(nodes_comps):
+        for ijk, c in nodes_comps:
+            used.add((tuple(ijk), c))
+
+    def rand_node(lo=0, hi_pad=0):
+        return tuple(int(rng.integers(lo, nn[d] - hi_pad)) for d in range(3))
+
+    tries = 0
+    while n_strong > 0 and tries < 1000:
+        tries += 1
+        ijk, c = rand_node(), int(rng.integers(3))
+        if free([(ijk, c)]):
+            take([(ijk, c)])
+            intents.append(dict(kind="strong", ijk=ijk, comp=c, value=float(rng.uniform(-0.02, 0.02))))
+            n_strong -= 1
+    while n_weak > 0 and tries < 2000:
+        tries += 1
+        vox = tuple(int(rng.integers(0, nvox[d])) for d in range(3))
+        c = int(rng.integers(3))
+        sup = [(((vox[0] + a) % nn[0], (vox[1] + b) % nn[1], (vox[2] + g) % nn[2]), c)
+               for g in (0, 1) for b in (0, 1) for a in (0, 1)]
+        if free(sup):
+            take(sup)
+            intents.append(dict(kind="weak_voxel", vox=vox, comp=c, value=float(rng.uniform(-0.02, 0.02))))
+            n_weak -= 1
+    while n_smooth > 0 and tries < 3000:
+        tries += 1
+        ijk = tuple(int(rng.integers(1, nn[d] - 1)) for d in range(3))
+        c = int(rng.integers(3))
+        sup = []
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    q = [ijk[0] + dx, ijk[1] + dy, ijk[2] + dz]
+                    q = [q[d] % nn[d] if bc[d][0][0] == P else q[d] for d in range(3)]
+                    sup.append((tuple(q), c))
+        if all(0 <= s[0][d] < nn[d] for s in sup for d in range(3)) and free(sup):
+            take(sup)
+            intents.append(dict(kind="smooth", ijk=ijk, comp=c, value=float(rng.uniform(-0.02, 0.02))))
+            n_smooth -= 1
+    while n_tie > 0 and tries < 4000:
+        tries += 1
+        c = int(rng.integers(3))
+        base = rand_node(0, 1)
+        nodes = [base, (base[0] + 1, base[1], base[2]), (base[0], base[1] + 1, base[2])]
+        sup = [(n_, c) for n_ in nodes]
+        if free(sup):
+            take(sup)
+            intents.append(dict(kind="tie", nodes=nodes, comp=c, value=float(rng.uniform(-0.02, 0.02))))
+            n_tie -= 1
+    return Workload(name="random cell seed %d" % seed, nvox=nvox, h=1.0, bc=bc, scheme=scheme,
+                    phase=phase, lam=lam, mu=mu, eps_star=eps, intents=intents,
+                    lam0=float(np.max(lam)), mu0=float(np.max(mu)), tol=1e-10, acv_mod=3)
+
+
+def random_field(seed, shape, scale=1.0):
+    """A seeded float64 field of the given shape."""
+    return scale * np.random.default_rng(seed).standard_normal(shape)
