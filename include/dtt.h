@@ -1,0 +1,200 @@
+/* libdtt -- constrained DTT/FFT-based elasticity solver on one B300 GPU (sm_103a).
+ *
+ * The method is the displacement-based accelerated fixed point of Gelebart &
+ * Amouzou-Adoun, "Constrained minimization problems and FFT-based solvers: application
+ * to local Dirichlet boundary conditions and contact mechanics": per iteration, the
+ * stress and its discrete divergence (Eq. 3), the projections proj_P / proj_U of local
+ * kinematic constraints (Eq. 9, 11, 14, 17) or of frictionless sphere contact (Eq. 28),
+ * depth-4 Anderson acceleration (Section 4.1.1), and the Green-operator step
+ * DT -> Green -> iDT with per-face, per-component discrete trigonometric transforms
+ * (Section 3.2, Tables 1-3, Eq. 7) -- Algorithm 1 and Algorithm 2.
+ *
+ * Conventions (every entry point):
+ *   - Grid: nvox = {nx, ny, nz} voxels of size h.  Nodes at h*(i, j, k); nn_d = n_d + 1
+ *     nodes along a non-periodic axis, n_d along a periodic one.  Flat node index
+ *     n = i + nn_x * (j + nn_y * k) (x fastest).  Voxel index v = i + nx * (j + ny * k).
+ *   - Nodal vector fields are component-major: f[c * n_nodes + n], c = 0, 1, 2.
+ *   - Boundary conditions bc[18] = bc[axis][face][component] (axis 0..2 = x, y, z;
+ *     face 0 at x_axis = 0, face 1 at x_axis = n_axis), codes DTT_BC_*.  Periodic must be
+ *     set on both faces of an axis for all three components (Section 3.2.1).
+ *   - u* = eps* . x is an affine lift; the unknown is the fluctuation u~, u = u* + u~.
+ *   - Every call returns a dtt_status; on error, dtt_last_error() returns a message
+ *     (thread-local).  No C++ exception crosses this interface.
+ *   - Host pointers are read or written synchronously; the library copies what it keeps
+ *     (the caller keeps ownership of its arrays).  Where a flag ptr_is_device is given,
+ *     1 means the pointer is a CUDA device pointer on the grid's device.
+ *   - Work is issued on the stream given at creation; with NULL the grid creates its own
+ *     stream (the iteration is captured into a CUDA graph, which the legacy default
+ *     stream does not allow).  Calls that return host data synchronise that stream.
+ */
+#ifndef DTT_H
+#define DTT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dtt_grid dtt_grid;
+
+typedef enum {
+  DTT_OK = 0,
+  DTT_ERR_ARG = 1,            /* invalid argument (size, pointer, index, value) */
+  DTT_ERR_BC = 2,             /* inconsistent boundary conditions */
+  DTT_ERR_OVERLAP = 3,        /* constraint rows with overlapping supports */
+  DTT_ERR_CUDA = 4,           /* a CUDA call failed (message has the CUDA error) */
+  DTT_ERR_OOM = 5,            /* device allocation failed */
+  DTT_ERR_NOT_CONVERGED = 6,  /* iteration cap reached; the last iterate stays readable */
+  DTT_ERR_DIVERGED = 7,       /* residual non-finite or grown by 1e6 */
+  DTT_ERR_STATE = 8,          /* call out of order (e.g. solve before set_material) */
+  DTT_ERR_NULLMODE = 9        /* constraint on a component whose Green symbol has null modes */
+} dtt_status;
+
+enum { DTT_BC_PERIODIC = 0, DTT_BC_DIRICHLET = 1, DTT_BC_NEUMANN = 2 };
+enum { DTT_SCHEME_TETRA2 = 0, DTT_SCHEME_HEX1 = 1 };
+enum { DTT_PREC_FP64 = 0, DTT_PREC_MIXED = 1 };
+enum { DTT_INIT_ZERO = 0, DTT_INIT_PREVIOUS = 1 };
+enum { DTT_ACV_U = 0, DTT_ACV_P = 1 };
+
+/* Create a grid (Section 3.2.1 problem statement: cell, per-face per-component BCs, FD
+ * scheme of Section 3.1.1).  precision: DTT_PREC_FP64 = every nodal field and every
+ * transform in float64; DTT_PREC_MIXED = transforms, Green multiply, stress and the
+ * Anderson ring in float32, u~ kept as a float-float pair, and float64 for norms, Gram
+ * matrix, multipliers, reactions and the contact gap test.  stream: a cudaStream_t (or
+ * NULL).  Allocates all device buffers of the grid (about 13 nodal vector fields).
+ * Errors: DTT_ERR_ARG (sizes < 2, h <= 0, bad codes), DTT_ERR_BC, DTT_ERR_OOM, DTT_ERR_CUDA. */
+dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, const int32_t bc[18],
+                           int32_t scheme, int32_t precision, void* stream);
+void dtt_grid_destroy(dtt_grid* grid);
+
+/* Number of nodes and voxels of the grid (for sizing caller buffers). */
+dtt_status dtt_grid_sizes(const dtt_grid* grid, int64_t* n_nodes, int64_t* n_voxels, int32_t nn[3]);
+
+/* Material (Eq. 1: sigma = C : eps, isotropic per phase, Section 5.4 convention
+ * sigma = lambda tr(eps) 1 + 2 mu eps).  phase: n_voxels uint8 ids (< nphase <= 256).
+ * lambda, mu: host arrays of nphase values (>= 0).  Errors: DTT_ERR_ARG. */
+dtt_status dtt_set_material(dtt_grid* grid, const uint8_t* phase, int32_t nphase,
+                            const double* lambda, const double* mu, int32_t phase_is_device);
+
+/* Reference medium of the Green operator, Paux form (Section 3.2.3):
+ * R0 : grad u = lambda0 (grad u (.) I) + 2 mu0 grad u.  Requires mu0 > 0, lambda0 >= 0. */
+dtt_status dtt_set_reference(dtt_grid* grid, double lambda0, double mu0);
+
+/* Prescribed strain eps* (3x3 row-major, symmetric part used), Eq. 1. */
+dtt_status dtt_set_load(dtt_grid* grid, const double eps_star[9]);
+
+/* Local kinematic constraints as rows of the matrices A and B (Section 4.3, Eq. 20-23).
+ * Row r has entries e in [row_ptr[r], row_ptr[r+1]): DOF (node[e], comp[e]) with
+ * kinematic weight a[e] and reaction weight b[e] (b == NULL: b = a), and prescribes
+ *     sum_e a[e] * u_{comp[e]}(node[e]) = value[r]       (u = total displacement).
+ * Strong conditions (Eq. 21): one entry, a = b = 1.  Weak conditions (Eq. 10, 22): 8 (or
+ * 4 on a face) entries a = b = 1/8 (1/4).  Smooth conditions (Eq. 15-17): a = 1 on the
+ * node, b = neighbour weights.  Ties (Section 4.2.3): a = b = 1/|V*|.
+ * Supports must be pairwise disjoint (DTT_ERR_OVERLAP), must not contain DOFs eliminated
+ * by a Dirichlet face (DTT_ERR_ARG), and must not use a component whose Green symbol has
+ * null modes, i.e. whose transforms keep q = 0 (or the TETRA2 checkerboard / a HEX1
+ * hourglass) on every axis -- such a component needs a Dirichlet face, e.g. behind a void
+ * buffer layer as in Section 4.1.2 (DTT_ERR_NULLMODE).  n_rows = 0 clears the rows. */
+dtt_status dtt_set_constraints(dtt_grid* grid, int32_t n_rows, const int32_t* row_ptr,
+                               const int32_t* node, const int8_t* comp, const double* a,
+                               const double* b, const double* value);
+
+/* Rigid frictionless sphere (Section 5, Eq. 24): potential contact surface = all nodes of
+ * face `face` (0/1) of axis `axis`; centre and radius in length units.  Components of the
+ * face nodes must not have Green null modes (DTT_ERR_NULLMODE). */
+dtt_status dtt_set_indenter(dtt_grid* grid, int32_t axis, int32_t face, const double center[3],
+                            double radius);
+/* Move the sphere centre for the next load increment (Algorithm 2). */
+dtt_status dtt_move_indenter(dtt_grid* grid, const double center[3]);
+dtt_status dtt_clear_indenter(dtt_grid* grid);
+
+/* Initial fluctuation u~ (3 x n_nodes float64).  Values on Dirichlet-face DOFs are
+ * ignored.  A component's null-mode content (if it has null modes) is kept unchanged by
+ * the solver. */
+dtt_status dtt_set_initial(dtt_grid* grid, const double* u, int32_t ptr_is_device);
+
+typedef struct {
+  double tol;          /* Eq. 5 tolerance (RMS norms): h ||p|| / ||sigma|| < tol */
+  int32_t max_iter;    /* cap on Green steps (the paper declares failure at 2000) */
+  int32_t acv_mod;     /* accelerate every acv_mod iterations after the first four (2 or 3);
+                          0 disables acceleration */
+  int32_t acv_on;      /* DTT_ACV_P (accelerate p~, default) or DTT_ACV_U (FP64 only) */
+  int32_t init;        /* DTT_INIT_ZERO or DTT_INIT_PREVIOUS (current u~: previous step or
+                          dtt_set_initial) */
+  double update_tol;   /* contact-zone update threshold on the residual (paper: 1e-2) */
+  int32_t graph_iters; /* iterations per captured CUDA-graph launch (0: default 8) */
+} dtt_solve_opts;
+
+typedef struct {
+  int32_t iterations;          /* Green steps performed */
+  int32_t accelerations;       /* Anderson combinations applied */
+  int32_t active_set_updates;  /* contact-zone changes (Algorithm 2) */
+  int32_t status;              /* dtt_status of the solve */
+  double residual;             /* Eq. 5 residual of the returned iterate */
+  double seconds;              /* wall time of the solve (host clock, synchronised) */
+} dtt_report;
+
+/* One solve (Algorithm 1), or one load increment (Algorithm 2) when an indenter is set:
+ * the active set starts as the surface nodes with negative gap for the current sphere
+ * position.  Returns DTT_OK on convergence, DTT_ERR_NOT_CONVERGED / DTT_ERR_DIVERGED
+ * otherwise (report filled in every case). */
+dtt_status dtt_solve_step(dtt_grid* grid, const dtt_solve_opts* opts, dtt_report* report);
+
+/* Residual history of the last solve (Eq. 5 per iteration); *n in: capacity, out: count. */
+dtt_status dtt_get_history(const dtt_grid* grid, double* hist, int32_t* n);
+
+/* u~ (3 x n_nodes, float64) and optionally the stress at the integration points
+ * (sigma: n_voxels x n_ip x 6, order xx yy zz yz xz xy; n_ip = 2 TETRA2, 1 HEX1). */
+dtt_status dtt_get_fields(dtt_grid* grid, double* u, double* sigma, int32_t ptr_is_device);
+
+/* Reactions of the constraint rows after the last solve: per_row[r] = h^3 f_r
+ * sum_e W_e b_e (face DOFs halved, edge DOFs quartered, Section 4.1.3), f_r the
+ * multiplier; total = vector sum.  per_row may be NULL. */
+dtt_status dtt_get_reactions(dtt_grid* grid, double* per_row, double total[3]);
+
+/* Contact state after the last solve: active[q], gap[q], normal reaction fn[q] for the
+ * n_face surface nodes (order: flat node index), and the total contact force vector.
+ * Any pointer may be NULL; *n_face returns the count. */
+dtt_status dtt_get_contact(dtt_grid* grid, int32_t* n_face, uint8_t* active, double* gap,
+                           double* fn, double force[3]);
+
+/* ---- single-pass operators (one step of the hot path on caller data) ---- */
+
+/* Eq. 3, Algorithm 1 stress/divergence step: for u~ (3 x n_nodes float64) returns
+ * p = div_D sigma and p~ = p - div_D(R0 : grad_D u~) (both 3 x n_nodes, float64, either
+ * may be NULL) and norms[0] = sum w sigma:sigma, norms[1] = sum p^2 over all DOFs.  No
+ * constraint projection is applied.  Computed in the grid's precision. */
+dtt_status dtt_apply_residual(dtt_grid* grid, const double* u, double* p, double* ptilde,
+                              double norms[2], int32_t ptr_is_device);
+
+/* Green step (Algorithm 1, DT -> G -> iDT): u = G_D(ptilde), null modes set to zero. */
+dtt_status dtt_apply_green(dtt_grid* grid, const double* ptilde, double* u, int32_t ptr_is_device);
+
+/* Forward (inverse = 0) or inverse (inverse = 1) transform of one nodal component array
+ * (n_nodes float64) with that component's per-axis DTT types; the spectrum is stored on
+ * the node grid, spectral index k of an axis at position k (unused positions zero). */
+dtt_status dtt_transform(dtt_grid* grid, int32_t component, int32_t inverse, const double* in,
+                         double* out, int32_t ptr_is_device);
+
+/* Kernel-group timing of the iteration (tracing aid): runs `iters` iterations of the
+ * current problem launch by launch (no graph), with CUDA events on the grid's stream
+ * around each group, from the state left by the last solve, and returns the mean
+ * milliseconds per iteration of each group in ms[DTT_NPROF]:
+ *   0 stress/divergence/reference (a1), 1 projections + contact + control, 2 Anderson,
+ *   3 forward transforms (3 axis passes), 4 Green multiply, 5 inverse transforms,
+ *   6 increment update of u~.
+ * Solver state (u~, rings) is modified; call it after the timed solves. */
+#define DTT_NPROF 7
+dtt_status dtt_profile_iteration(dtt_grid* grid, const dtt_solve_opts* opts, int32_t iters, double* ms);
+
+const char* dtt_last_error(void);
+
+/* Library version string. */
+const char* dtt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DTT_H */

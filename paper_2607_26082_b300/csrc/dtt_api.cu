@@ -1,0 +1,1244 @@
+// Host side of libdtt: the C ABI of include/dtt.h.
+//
+// A dtt_grid owns every device buffer of one cell.  dtt_solve_step runs Algorithm 1 (or
+// one increment of Algorithm 2) as a fixed sequence of kernel launches per iteration,
+// captured once into a CUDA graph of `graph_iters` iterations and replayed until the
+// device-side control block reports convergence, the iteration cap or divergence; the
+// host only reads a few bytes of that block between graph launches.
+#include "dtt.h"
+#include "dtt_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace dtt;
+
+namespace {
+
+thread_local std::string g_err;
+
+dtt_status fail(dtt_status s, const std::string& m) {
+  g_err = m;
+  return s;
+}
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(DTT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKL(rc)                                                                             \
+  do {                                                                                      \
+    int r_ = (rc);                                                                          \
+    if (r_ != 0) return fail(DTT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)r_)); \
+  } while (0)
+
+template <typename P>
+dtt_status dalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return DTT_OK;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? DTT_ERR_OOM : DTT_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return DTT_OK;
+}
+
+template <typename P>
+void dfree(P*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+}  // namespace
+
+struct dtt_grid {
+  GridDev g{};
+  int prec = DTT_PREC_FP64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;   // created here when the caller passes NULL (graph capture
+                             // needs a stream other than the legacy default stream)
+  int types[3][3]{};      // [comp][axis]
+  bool has_null[3]{};
+  long long NN = 0, NV = 0;
+  size_t esz = 8;
+
+  // nodal fields
+  double* u64 = nullptr;
+  float* uhi = nullptr;
+  float* ulo = nullptr;
+  void* S[5]{};
+  void* R[4]{};
+  void* gbuf = nullptr;
+  void* spec = nullptr;
+  void** d_Sring = nullptr;
+  void** d_Rring = nullptr;
+
+  // material
+  uint8_t* phase = nullptr;
+  double* d_lam = nullptr;
+  double* d_mu = nullptr;
+  int nphase = 0;
+  bool mat_set = false;
+  double lam0 = 0, mu0 = 0;
+  bool ref_set = false;
+  double eps[3][3]{};
+
+  // transforms
+  void* fwd[3][3]{};
+  void* inv[3][3]{};
+  double* cosq[3][3]{};
+
+  // constraints (host copy + device CSR)
+  int nrows = 0;
+  std::vector<int> h_ptr;
+  std::vector<long long> h_dof;
+  std::vector<double> h_a, h_b, h_val, h_ab, h_aa;
+  int* d_ptr = nullptr;
+  long long* d_dof = nullptr;
+  double *d_a = nullptr, *d_b = nullptr, *d_target = nullptr, *d_mult = nullptr, *d_ab = nullptr,
+         *d_aa = nullptr;
+  uint8_t* cmask = nullptr;
+
+  // contact
+  bool contact = false;
+  int c_axis = 2, c_face = 1;
+  double center[3]{}, radius = 0;
+  int nface = 0;
+  long long* d_face = nullptr;
+  uint8_t *d_active = nullptr, *d_vgap = nullptr, *d_vreact = nullptr, *d_vgap_prev = nullptr,
+          *d_vreact_prev = nullptr;
+  double *d_gap = nullptr, *d_fn = nullptr, *d_nvec = nullptr;
+
+  // control
+  Ctrl* d_ctrl = nullptr;
+  Ctrl* h_ctrl = nullptr;   // pinned
+  double* d_part = nullptr;
+  size_t part_cap = 0;
+
+  // scratch for operator entry points
+  double* op_d = nullptr;   // 3 NN doubles
+  void* op_t1 = nullptr;    // 3 NN of T
+  void* op_t2 = nullptr;
+
+  // graph
+  cudaGraphExec_t gexec = nullptr;
+  int g_key = -1;
+
+  Ctrl last{};
+  bool solved = false;
+};
+
+namespace {
+
+const int kIP[2] = {2, 1};
+
+void invalidate_graph(dtt_grid* G) {
+  if (G->gexec) cudaGraphExecDestroy(G->gexec);
+  G->gexec = nullptr;
+  G->g_key = -1;
+}
+
+int ttype(int b0, int b1) {
+  if (b0 == BC_P || b1 == BC_P) return (b0 == BC_P && b1 == BC_P) ? T_DHT : -1;
+  if (b0 == BC_N && b1 == BC_N) return T_DCT1;
+  if (b0 == BC_N && b1 == BC_D) return T_DCT3;
+  if (b0 == BC_D && b1 == BC_D) return T_DST1;
+  return T_DST3;  // D, N
+}
+
+// Transform matrices of one axis: F (spectral k, node j) and B (node j, spectral k), both
+// nn x nn with zero rows/columns outside the selection (Section 3.2.2, Table 3), plus
+// cos(q_k) at every spectral position (1 where unused).
+void build_axis(int type, int n, int nn, std::vector<double>& F, std::vector<double>& B, std::vector<double>& cq) {
+  F.assign((size_t)nn * nn, 0.0);
+  B.assign((size_t)nn * nn, 0.0);
+  cq.assign(nn, 1.0);
+  const double pi = 3.14159265358979323846;
+  switch (type) {
+    case T_DCT1:
+      for (int k = 0; k <= n; ++k) {
+        cq[k] = std::cos(pi * k / n);
+        for (int j = 0; j <= n; ++j) {
+          double c = std::cos(pi * (double)j * k / n);
+          double wj = (j == 0 || j == n) ? 0.5 : 1.0;
+          double wk = (k == 0 || k == n) ? 0.5 : 1.0;
+          F[(size_t)k * nn + j] = wj * c;
+          B[(size_t)j * nn + k] = 2.0 / n * wk * c;
+        }
+      }
+      break;
+    case T_DCT3:
+      for (int k = 0; k < n; ++k) {
+        cq[k] = std::cos(pi * (2.0 * k + 1.0) / (2.0 * n));
+        for (int j = 0; j < n; ++j) {
+          double c = std::cos(pi * j * (2.0 * k + 1.0) / (2.0 * n));
+          F[(size_t)k * nn + j] = (j == 0 ? 0.5 : 1.0) * c;
+          B[(size_t)j * nn + k] = 2.0 / n * c;
+        }
+      }
+      break;
+    case T_DST1:
+      for (int k = 1; k < n; ++k) {
+        cq[k] = std::cos(pi * k / n);
+        for (int j = 1; j < n; ++j) {
+          double sv = std::sin(pi * (double)j * k / n);
+          F[(size_t)k * nn + j] = sv;
+          B[(size_t)j * nn + k] = 2.0 / n * sv;
+        }
+      }
+      break;
+    case T_DST3:
+      for (int k = 0; k < n; ++k) {
+        cq[k] = std::cos(pi * (2.0 * k + 1.0) / (2.0 * n));
+        for (int j = 1; j <= n; ++j) {
+          double sv = std::sin(pi * j * (2.0 * k + 1.0) / (2.0 * n));
+          F[(size_t)k * nn + j] = (j == n ? 0.5 : 1.0) * sv;
+          B[(size_t)j * nn + k] = 2.0 / n * sv;
+        }
+      }
+      break;
+    case T_DHT:
+      for (int k = 0; k < n; ++k) {
+        cq[k] = std::cos(2.0 * pi * k / n);
+        for (int j = 0; j < n; ++j) {
+          double th = 2.0 * pi * (double)((long long)j * k % n) / n;
+          double cas = std::cos(th) + std::sin(th);
+          F[(size_t)k * nn + j] = cas;
+          B[(size_t)j * nn + k] = cas / n;
+        }
+      }
+      break;
+  }
+}
+
+bool comp_has_null(const dtt_grid* G, int c) {
+  bool all0 = true;
+  int npi = 0;
+  for (int d = 0; d < 3; ++d) {
+    int t = G->types[c][d];
+    bool q0 = (t == T_DCT1 || t == T_DHT);
+    bool qpi = (t == T_DCT1) || (t == T_DHT && G->g.nvox[d] % 2 == 0);
+    all0 = all0 && q0;
+    npi += qpi ? 1 : 0;
+  }
+  if (all0) return true;
+  if (G->g.scheme == SCHEME_TETRA2) return npi == 3;
+  return npi >= 2;
+}
+
+// W_c and DOF flag of node n (host).
+void host_node_W(const dtt_grid* G, int c, long long n, bool& dof, double& W) {
+  int idx[3];
+  idx[0] = (int)(n % G->g.nn[0]);
+  long long r = n / G->g.nn[0];
+  idx[1] = (int)(r % G->g.nn[1]);
+  idx[2] = (int)(r / G->g.nn[1]);
+  dof = true;
+  W = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    if (G->g.periodic[d]) continue;
+    int f = -1;
+    if (idx[d] == 0) f = 0;
+    else if (idx[d] == G->g.nn[d] - 1) f = 1;
+    if (f < 0) continue;
+    int t = G->g.bc[d][f][c];
+    if (t == BC_D) dof = false;
+    else if (t == BC_N) W *= 0.5;
+  }
+}
+
+double host_ustar(const dtt_grid* G, int c, long long n) {
+  double X[3];
+  X[0] = G->g.h * (double)(n % G->g.nn[0]);
+  long long r = n / G->g.nn[0];
+  X[1] = G->g.h * (double)(r % G->g.nn[1]);
+  X[2] = G->g.h * (double)(r / G->g.nn[1]);
+  return G->eps[c][0] * X[0] + G->eps[c][1] * X[1] + G->eps[c][2] * X[2];
+}
+
+dtt_status rebuild_cmask(dtt_grid* G) {
+  std::vector<uint8_t> m((size_t)G->NN, 0);
+  for (size_t e = 0; e < G->h_dof.size(); ++e) {
+    long long d = G->h_dof[e];
+    int c = (int)(d / G->NN);
+    m[(size_t)(d - c * G->NN)] |= (uint8_t)(1u << c);
+  }
+  if (G->contact) {
+    std::vector<long long> nodes(G->nface);
+    CK(cudaMemcpy(nodes.data(), G->d_face, sizeof(long long) * G->nface, cudaMemcpyDeviceToHost));
+    for (long long n : nodes) m[(size_t)n] |= 7u;
+  }
+  CK(cudaMemcpy(G->cmask, m.data(), (size_t)G->NN, cudaMemcpyHostToDevice));
+  return DTT_OK;
+}
+
+dtt_status ensure_partials(dtt_grid* G) {
+  size_t need = 2 * (size_t)residual_blocks(G->g) + (size_t)(G->nrows + 255) / 256 + 1 +
+                4 * (size_t)contact_blocks(G->nface) + 4 + 4 * (size_t)acv_blocks(G->g) + 64;
+  if (need <= G->part_cap) return DTT_OK;
+  dfree(G->d_part);
+  dtt_status s = dalloc(&G->d_part, need * sizeof(double));
+  if (s != DTT_OK) return s;
+  G->part_cap = need;
+  return DTT_OK;
+}
+
+struct PartRegions {
+  double *res, *proj, *cont, *acv;
+  int nres, nproj, ncont, nacv;
+};
+
+PartRegions regions(dtt_grid* G) {
+  PartRegions r;
+  r.nres = residual_blocks(G->g);
+  r.nproj = (G->nrows + 255) / 256;
+  r.ncont = G->contact ? contact_blocks(G->nface) : 0;
+  r.nacv = acv_blocks(G->g);
+  r.res = G->d_part;
+  r.proj = r.res + 2 * r.nres;
+  r.cont = r.proj + r.nproj + 1;
+  r.acv = r.cont + 4 * r.ncont + 4;
+  return r;
+}
+
+RowsDev rows_dev(dtt_grid* G) {
+  RowsDev r;
+  r.nrows = G->nrows;
+  r.ptr = G->d_ptr;
+  r.dof = G->d_dof;
+  r.a = G->d_a;
+  r.b = G->d_b;
+  r.target = G->d_target;
+  r.mult = G->d_mult;
+  r.ab = G->d_ab;
+  r.aa = G->d_aa;
+  return r;
+}
+
+ContactArgs contact_args(dtt_grid* G, double* cont_part) {
+  ContactArgs a;
+  a.g = G->g;
+  a.c.nnodes_face = G->nface;
+  a.c.node = G->d_face;
+  a.c.active = G->d_active;
+  a.c.vgap = G->d_vgap;
+  a.c.vreact = G->d_vreact;
+  a.c.vgap_prev = G->d_vgap_prev;
+  a.c.vreact_prev = G->d_vreact_prev;
+  a.c.gap = G->d_gap;
+  a.c.fn = G->d_fn;
+  a.c.nvec = G->d_nvec;
+  for (int c = 0; c < 3; ++c) a.c.center[c] = G->center[c];
+  a.c.radius = G->radius;
+  a.u64 = G->u64;
+  a.uhi = G->uhi;
+  a.ulo = G->ulo;
+  std::memcpy(a.eps, G->eps, sizeof(a.eps));
+  a.ctrl = G->d_ctrl;
+  a.partials = cont_part;
+  return a;
+}
+
+TransformTables tables(dtt_grid* G) {
+  TransformTables t;
+  for (int c = 0; c < 3; ++c)
+    for (int d = 0; d < 3; ++d) {
+      t.fwd[c][d] = G->fwd[c][d];
+      t.inv[c][d] = G->inv[c][d];
+      t.cosq[c][d] = G->cosq[c][d];
+    }
+  t.lam0 = G->lam0;
+  t.mu0 = G->mu0;
+  // Null modes: a_c vanishes exactly (up to rounding) there; every other spectral point
+  // has a_c >= ~mu0 (pi / 2n)^2 / h^2.  Threshold: 1e-12 x an upper bound of a_c
+  // ((lambda0 + 6 mu0) * 4 / h^2, since every S_j <= 4 / h^2).
+  double bound = (G->lam0 + 6.0 * G->mu0) * 4.0 / (G->g.h * G->g.h);
+  for (int c = 0; c < 3; ++c) t.null_thr[c] = 1e-12 * bound;
+  return t;
+}
+
+// Optional per-group event marks (dtt_profile_iteration); null when not profiling.
+cudaEvent_t* g_prof_ev = nullptr;
+inline void prof_mark(int k, cudaStream_t s) {
+  if (g_prof_ev) cudaEventRecord(g_prof_ev[k], s);
+}
+
+template <typename T>
+dtt_status enqueue_green(dtt_grid* G, T* in_out, T* tmp, bool increment, const Ctrl* ctrl, int comp0, int ncomp) {
+  TransformTables tt = tables(G);
+  cudaStream_t s = G->stream;
+  // forward x, y, z ; Green ; inverse z, y, x  (ping-pong in_out <-> tmp)
+  CKL(launch_transform_axis<T>(G->g, in_out, tmp, tt, 0, 0, comp0, ncomp, ctrl, s));
+  CKL(launch_transform_axis<T>(G->g, tmp, in_out, tt, 1, 0, comp0, ncomp, ctrl, s));
+  CKL(launch_transform_axis<T>(G->g, in_out, tmp, tt, 2, 0, comp0, ncomp, ctrl, s));
+  prof_mark(4, s);
+  CKL(launch_green_multiply<T>(G->g, tmp, tt, G->g.scheme, ctrl, s));
+  prof_mark(5, s);
+  CKL(launch_transform_axis<T>(G->g, tmp, in_out, tt, 2, 1, comp0, ncomp, ctrl, s));
+  CKL(launch_transform_axis<T>(G->g, in_out, tmp, tt, 1, 1, comp0, ncomp, ctrl, s));
+  CKL(launch_transform_axis<T>(G->g, tmp, in_out, tt, 0, 1, comp0, ncomp, ctrl, s));
+  prof_mark(6, s);
+  if (increment) CKL(launch_add_increment<T>(G->g, in_out, G->u64, G->uhi, G->ulo, ctrl, s));
+  return DTT_OK;
+}
+
+template <typename T>
+dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
+  cudaStream_t s = G->stream;
+  PartRegions pr = regions(G);
+  Ctrl* ctrl = G->d_ctrl;
+  prof_mark(0, s);
+  if (acv && acv_on == DTT_ACV_U) {
+    CKL(launch_acv_store<T>(G->g, 0, G->d_Sring, G->d_Rring, G->u64, pr.acv, ctrl, s));
+    CKL(launch_ctrl_acv(ctrl, pr.acv, pr.nacv, s));
+    CKL(launch_acv_accel<T>(G->g, 0, G->d_Sring, G->d_Rring, (T*)G->gbuf, G->u64, ctrl, s));
+  }
+  ResidualArgs ra{};
+  ra.g = G->g;
+  ra.u64 = G->u64;
+  ra.uhi = G->uhi;
+  ra.ulo = G->ulo;
+  ra.phase = G->phase;
+  ra.lam = G->d_lam;
+  ra.mu = G->d_mu;
+  ra.nphase = G->nphase;
+  ra.cmask = G->cmask;
+  std::memcpy(ra.eps, G->eps, sizeof(ra.eps));
+  ra.lam0 = G->lam0;
+  ra.mu0 = G->mu0;
+  ra.xout = nullptr;
+  ra.pout = G->gbuf;
+  ra.partials = pr.res;
+  ra.ctrl = ctrl;
+  for (int k = 0; k < 5; ++k) ra.ring[k] = G->S[k];
+  ra.write_x_ring = (acv && acv_on == DTT_ACV_P) ? 1 : 0;
+  CKL(launch_residual<T>(ra, s));
+  prof_mark(1, s);
+  const int xr = ra.write_x_ring;
+  if (G->nrows > 0) CKL(launch_proj_P_rows<T>(G->g, rows_dev(G), (T*)G->gbuf, nullptr, xr, G->d_Sring, pr.proj, ctrl, s));
+  ContactArgs ca = contact_args(G, pr.cont);
+  if (G->contact) CKL(launch_contact_eval<T>(ca, (T*)G->gbuf, G->d_Sring, xr, s));
+  CKL(launch_ctrl_residual(ctrl, pr.res, pr.nres, pr.proj, G->nrows > 0 ? pr.nproj : 0, pr.cont, pr.ncont, G->g.h,
+                           G->NN, G->NV, s));
+  if (G->contact) {
+    CKL(launch_contact_update(ca, s));
+    CKL(launch_ctrl_contact(ctrl, s));
+  }
+  prof_mark(2, s);
+  if (acv && acv_on == DTT_ACV_P) {
+    CKL(launch_acv_store<T>(G->g, 1, G->d_Sring, G->d_Rring, G->u64, pr.acv, ctrl, s));
+    CKL(launch_ctrl_acv(ctrl, pr.acv, pr.nacv, s));
+    CKL(launch_acv_accel<T>(G->g, 1, G->d_Sring, G->d_Rring, (T*)G->gbuf, G->u64, ctrl, s));
+  }
+  prof_mark(3, s);
+  dtt_status st = enqueue_green<T>(G, (T*)G->gbuf, (T*)G->spec, true, ctrl, 0, 3);
+  if (st != DTT_OK) return st;
+  prof_mark(7, s);
+  if (G->nrows > 0) CKL(launch_proj_U_rows(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, ctrl, s));
+  if (G->contact) CKL(launch_contact_proj_U(ca, G->u64, G->uhi, G->ulo, s));
+  CKL(launch_ctrl_end(ctrl, s));
+  prof_mark(8, s);
+  return DTT_OK;
+}
+
+dtt_status enqueue_iter_any(dtt_grid* G, int acv_on, bool acv) {
+  return G->prec == DTT_PREC_FP64 ? enqueue_iteration<double>(G, acv_on, acv)
+                                  : enqueue_iteration<float>(G, acv_on, acv);
+}
+
+dtt_status build_graph(dtt_grid* G, int acv_on, bool acv, int iters) {
+  invalidate_graph(G);
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(G->stream, cudaStreamCaptureModeThreadLocal));
+  dtt_status st = DTT_OK;
+  for (int k = 0; k < iters && st == DTT_OK; ++k) st = enqueue_iter_any(G, acv_on, acv);
+  cudaError_t e = cudaStreamEndCapture(G->stream, &graph);
+  if (st != DTT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(DTT_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&G->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    G->gexec = nullptr;
+    return fail(DTT_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  G->g_key = acv_on * 1000000 + (acv ? 100000 : 0) + iters;
+  return DTT_OK;
+}
+
+dtt_status to_grid_u(dtt_grid* G, const double* u, int is_dev) {
+  // copy a float64 field into the grid's u~ storage
+  const size_t n3 = (size_t)(3 * G->NN);
+  const double* src = u;
+  if (!is_dev) {
+    CK(cudaMemcpyAsync(G->op_d, u, n3 * sizeof(double), cudaMemcpyHostToDevice, G->stream));
+    src = G->op_d;
+  }
+  if (G->prec == DTT_PREC_FP64) {
+    if (src != G->u64) CK(cudaMemcpyAsync(G->u64, src, n3 * sizeof(double), cudaMemcpyDeviceToDevice, G->stream));
+  } else {
+    CKL(launch_split((long long)n3, src, G->uhi, G->ulo, G->stream));
+  }
+  return DTT_OK;
+}
+
+dtt_status zero_dirichlet(dtt_grid* G) {
+  // enforce u~ = 0 on Dirichlet-face DOFs via a host mask pass (set-up only)
+  const size_t n3 = (size_t)(3 * G->NN);
+  std::vector<double> hu(n3);
+  if (G->prec == DTT_PREC_FP64) {
+    CK(cudaMemcpy(hu.data(), G->u64, n3 * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    CKL(launch_join((long long)n3, G->uhi, G->ulo, G->op_d, G->stream));
+    CK(cudaStreamSynchronize(G->stream));
+    CK(cudaMemcpy(hu.data(), G->op_d, n3 * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  bool changed = false;
+  for (int c = 0; c < 3; ++c)
+    for (long long n = 0; n < G->NN; ++n) {
+      bool dof;
+      double W;
+      host_node_W(G, c, n, dof, W);
+      if (!dof && hu[(size_t)(c * G->NN + n)] != 0.0) {
+        hu[(size_t)(c * G->NN + n)] = 0.0;
+        changed = true;
+      }
+    }
+  if (changed) {
+    CK(cudaMemcpy(G->op_d, hu.data(), n3 * sizeof(double), cudaMemcpyHostToDevice));
+    return to_grid_u(G, G->op_d, 1);
+  }
+  return DTT_OK;
+}
+
+dtt_status ensure_ops(dtt_grid* G) {
+  if (G->op_t1) return DTT_OK;
+  size_t n3 = (size_t)(3 * G->NN);
+  dtt_status s = dalloc(&G->op_t1, n3 * G->esz);
+  if (s == DTT_OK) s = dalloc(&G->op_t2, n3 * G->esz);
+  return s;
+}
+
+void free_rows(dtt_grid* G) {
+  dfree(G->d_ptr);
+  dfree(G->d_dof);
+  dfree(G->d_a);
+  dfree(G->d_b);
+  dfree(G->d_target);
+  dfree(G->d_mult);
+  dfree(G->d_ab);
+  dfree(G->d_aa);
+}
+
+void free_contact(dtt_grid* G) {
+  dfree(G->d_face);
+  dfree(G->d_active);
+  dfree(G->d_vgap);
+  dfree(G->d_vreact);
+  dfree(G->d_vgap_prev);
+  dfree(G->d_vreact_prev);
+  dfree(G->d_gap);
+  dfree(G->d_fn);
+  dfree(G->d_nvec);
+  G->nface = 0;
+  G->contact = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dtt_last_error(void) { return g_err.c_str(); }
+const char* dtt_version(void) { return "libdtt 0.1 (sm_103a)"; }
+
+dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, const int32_t bc[18], int32_t scheme,
+                           int32_t precision, void* stream) {
+  if (!out || !nvox || !bc) return fail(DTT_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (!(h > 0.0)) return fail(DTT_ERR_ARG, "h must be > 0");
+  if (scheme != DTT_SCHEME_TETRA2 && scheme != DTT_SCHEME_HEX1) return fail(DTT_ERR_ARG, "unknown scheme");
+  if (precision != DTT_PREC_FP64 && precision != DTT_PREC_MIXED) return fail(DTT_ERR_ARG, "unknown precision");
+  for (int d = 0; d < 3; ++d)
+    if (nvox[d] < 2 || nvox[d] > 4096) return fail(DTT_ERR_ARG, "nvox must be in [2, 4096]");
+  for (int q = 0; q < 18; ++q)
+    if (bc[q] < 0 || bc[q] > 2) return fail(DTT_ERR_ARG, "bc code must be 0, 1 or 2");
+  dtt_grid* G = new dtt_grid();
+  G->prec = precision;
+  G->esz = precision == DTT_PREC_FP64 ? 8 : 4;
+  G->stream = (cudaStream_t)stream;
+  G->g.h = h;
+  G->g.scheme = scheme;
+  for (int d = 0; d < 3; ++d) {
+    G->g.nvox[d] = nvox[d];
+    for (int f = 0; f < 2; ++f)
+      for (int c = 0; c < 3; ++c) G->g.bc[d][f][c] = bc[d * 6 + f * 3 + c];
+    int nper = 0;
+    for (int c = 0; c < 3; ++c) {
+      int t = ttype(G->g.bc[d][0][c], G->g.bc[d][1][c]);
+      if (t < 0) { delete G; return fail(DTT_ERR_BC, "periodic must be set on both faces of an axis"); }
+      G->types[c][d] = t;
+      nper += (t == T_DHT);
+    }
+    if (nper != 0 && nper != 3) { delete G; return fail(DTT_ERR_BC, "an axis is periodic for all components or none"); }
+    G->g.periodic[d] = nper == 3;
+    G->g.nn[d] = G->g.periodic[d] ? nvox[d] : nvox[d] + 1;
+  }
+  if (!G->stream) {
+    if (cudaStreamCreate(&G->stream) != cudaSuccess) {
+      delete G;
+      return fail(DTT_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    G->own_stream = true;
+  }
+  G->NN = (long long)G->g.nn[0] * G->g.nn[1] * G->g.nn[2];
+  G->NV = (long long)nvox[0] * nvox[1] * nvox[2];
+  G->g.nnodes = G->NN;
+  for (int c = 0; c < 3; ++c) G->has_null[c] = comp_has_null(G, c);
+
+  const size_t n3 = (size_t)(3 * G->NN);
+  dtt_status s = DTT_OK;
+  if (precision == DTT_PREC_FP64) s = dalloc(&G->u64, n3 * sizeof(double));
+  else {
+    s = dalloc(&G->uhi, n3 * sizeof(float));
+    if (s == DTT_OK) s = dalloc(&G->ulo, n3 * sizeof(float));
+  }
+  for (int k = 0; k < 5 && s == DTT_OK; ++k) s = dalloc(&G->S[k], n3 * G->esz);
+  for (int k = 0; k < 4 && s == DTT_OK; ++k) s = dalloc(&G->R[k], n3 * G->esz);
+  if (s == DTT_OK) s = dalloc(&G->gbuf, n3 * G->esz);
+  if (s == DTT_OK) s = dalloc(&G->spec, n3 * G->esz);
+  if (s == DTT_OK) s = dalloc(&G->d_Sring, 5 * sizeof(void*));
+  if (s == DTT_OK) s = dalloc(&G->d_Rring, 4 * sizeof(void*));
+  if (s == DTT_OK) s = dalloc(&G->phase, (size_t)G->NV);
+  if (s == DTT_OK) s = dalloc(&G->d_lam, MAX_PHASE * sizeof(double));
+  if (s == DTT_OK) s = dalloc(&G->d_mu, MAX_PHASE * sizeof(double));
+  if (s == DTT_OK) s = dalloc(&G->cmask, (size_t)G->NN);
+  if (s == DTT_OK) s = dalloc(&G->d_ctrl, sizeof(Ctrl));
+  if (s == DTT_OK) s = dalloc(&G->op_d, n3 * sizeof(double));
+  if (s == DTT_OK) {
+    cudaError_t e = cudaMallocHost((void**)&G->h_ctrl, sizeof(Ctrl));
+    if (e != cudaSuccess) s = fail(DTT_ERR_OOM, "cudaMallocHost");
+  }
+  if (s == DTT_OK) s = ensure_partials(G);
+  if (s != DTT_OK) { dtt_grid_destroy(G); return s; }
+  // transform tables
+  for (int c = 0; c < 3 && s == DTT_OK; ++c)
+    for (int d = 0; d < 3 && s == DTT_OK; ++d) {
+      std::vector<double> F, B, cq;
+      int nn = G->g.nn[d];
+      build_axis(G->types[c][d], nvox[d], nn, F, B, cq);
+      s = dalloc(&G->fwd[c][d], (size_t)nn * nn * G->esz);
+      if (s == DTT_OK) s = dalloc(&G->inv[c][d], (size_t)nn * nn * G->esz);
+      if (s == DTT_OK) s = dalloc(&G->cosq[c][d], (size_t)nn * sizeof(double));
+      if (s != DTT_OK) break;
+      if (G->esz == 8) {
+        cudaMemcpy(G->fwd[c][d], F.data(), F.size() * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(G->inv[c][d], B.data(), B.size() * 8, cudaMemcpyHostToDevice);
+      } else {
+        std::vector<float> Ff(F.begin(), F.end()), Bf(B.begin(), B.end());
+        cudaMemcpy(G->fwd[c][d], Ff.data(), Ff.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(G->inv[c][d], Bf.data(), Bf.size() * 4, cudaMemcpyHostToDevice);
+      }
+      cudaMemcpy(G->cosq[c][d], cq.data(), cq.size() * 8, cudaMemcpyHostToDevice);
+    }
+  if (s == DTT_OK) {
+    cudaError_t e = cudaMemcpy(G->d_Sring, G->S, 5 * sizeof(void*), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(G->d_Rring, G->R, 4 * sizeof(void*), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(G->cmask, 0, (size_t)G->NN);
+    if (e == cudaSuccess) e = G->u64 ? cudaMemset(G->u64, 0, n3 * 8) : cudaMemset(G->uhi, 0, n3 * 4);
+    if (e == cudaSuccess && G->ulo) e = cudaMemset(G->ulo, 0, n3 * 4);
+    if (e != cudaSuccess) s = fail(DTT_ERR_CUDA, std::string("set-up copy: ") + cudaGetErrorString(e));
+  }
+  if (s != DTT_OK) { dtt_grid_destroy(G); return s; }
+  *out = G;
+  return DTT_OK;
+}
+
+void dtt_grid_destroy(dtt_grid* G) {
+  if (!G) return;
+  if (G->stream) cudaStreamSynchronize(G->stream);
+  else cudaDeviceSynchronize();
+  invalidate_graph(G);
+  dfree(G->u64);
+  dfree(G->uhi);
+  dfree(G->ulo);
+  for (auto& p : G->S) dfree(p);
+  for (auto& p : G->R) dfree(p);
+  dfree(G->gbuf);
+  dfree(G->spec);
+  dfree(G->d_Sring);
+  dfree(G->d_Rring);
+  dfree(G->phase);
+  dfree(G->d_lam);
+  dfree(G->d_mu);
+  dfree(G->cmask);
+  dfree(G->d_ctrl);
+  dfree(G->d_part);
+  dfree(G->op_d);
+  dfree(G->op_t1);
+  dfree(G->op_t2);
+  for (int c = 0; c < 3; ++c)
+    for (int d = 0; d < 3; ++d) {
+      dfree(G->fwd[c][d]);
+      dfree(G->inv[c][d]);
+      dfree(G->cosq[c][d]);
+    }
+  free_rows(G);
+  free_contact(G);
+  if (G->h_ctrl) cudaFreeHost(G->h_ctrl);
+  if (G->own_stream) cudaStreamDestroy(G->stream);
+  delete G;
+}
+
+dtt_status dtt_grid_sizes(const dtt_grid* G, int64_t* n_nodes, int64_t* n_voxels, int32_t nn[3]) {
+  if (!G) return fail(DTT_ERR_ARG, "null grid");
+  if (n_nodes) *n_nodes = G->NN;
+  if (n_voxels) *n_voxels = G->NV;
+  if (nn)
+    for (int d = 0; d < 3; ++d) nn[d] = G->g.nn[d];
+  return DTT_OK;
+}
+
+dtt_status dtt_set_material(dtt_grid* G, const uint8_t* phase, int32_t nphase, const double* lambda, const double* mu,
+                            int32_t phase_is_device) {
+  if (!G || !phase || !lambda || !mu) return fail(DTT_ERR_ARG, "null argument");
+  if (nphase < 1 || nphase > MAX_PHASE) return fail(DTT_ERR_ARG, "nphase must be in [1, 256]");
+  for (int q = 0; q < nphase; ++q)
+    if (!(lambda[q] >= 0.0) || !(mu[q] >= 0.0) || !std::isfinite(lambda[q]) || !std::isfinite(mu[q]))
+      return fail(DTT_ERR_ARG, "Lame coefficients must be finite and >= 0");
+  if (!phase_is_device) {
+    for (long long v = 0; v < G->NV; ++v)
+      if (phase[v] >= nphase) return fail(DTT_ERR_ARG, "phase id >= nphase");
+    CK(cudaMemcpy(G->phase, phase, (size_t)G->NV, cudaMemcpyHostToDevice));
+  } else {
+    CK(cudaMemcpy(G->phase, phase, (size_t)G->NV, cudaMemcpyDeviceToDevice));
+    std::vector<uint8_t> h((size_t)G->NV);
+    CK(cudaMemcpy(h.data(), G->phase, (size_t)G->NV, cudaMemcpyDeviceToHost));
+    for (uint8_t v : h)
+      if (v >= nphase) return fail(DTT_ERR_ARG, "phase id >= nphase");
+  }
+  CK(cudaMemcpy(G->d_lam, lambda, nphase * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(G->d_mu, mu, nphase * sizeof(double), cudaMemcpyHostToDevice));
+  G->nphase = nphase;
+  G->mat_set = true;
+  invalidate_graph(G);
+  return DTT_OK;
+}
+
+dtt_status dtt_set_reference(dtt_grid* G, double lambda0, double mu0) {
+  if (!G) return fail(DTT_ERR_ARG, "null grid");
+  if (!(mu0 > 0.0) || !(lambda0 >= 0.0) || !std::isfinite(lambda0) || !std::isfinite(mu0))
+    return fail(DTT_ERR_ARG, "reference medium needs mu0 > 0, lambda0 >= 0");
+  G->lam0 = lambda0;
+  G->mu0 = mu0;
+  G->ref_set = true;
+  invalidate_graph(G);
+  return DTT_OK;
+}
+
+dtt_status dtt_set_load(dtt_grid* G, const double eps_star[9]) {
+  if (!G || !eps_star) return fail(DTT_ERR_ARG, "null argument");
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) {
+      double v = 0.5 * (eps_star[3 * p + q] + eps_star[3 * q + p]);
+      if (!std::isfinite(v)) return fail(DTT_ERR_ARG, "eps* must be finite");
+      G->eps[p][q] = v;
+    }
+  invalidate_graph(G);
+  return DTT_OK;
+}
+
+dtt_status dtt_set_constraints(dtt_grid* G, int32_t n_rows, const int32_t* row_ptr, const int32_t* node,
+                               const int8_t* comp, const double* a, const double* b, const double* value) {
+  if (!G) return fail(DTT_ERR_ARG, "null grid");
+  if (n_rows < 0) return fail(DTT_ERR_ARG, "n_rows < 0");
+  std::vector<int> ptr;
+  std::vector<long long> dof;
+  std::vector<double> va, vb, vv, vab, vaa;
+  if (n_rows > 0) {
+    if (!row_ptr || !node || !comp || !a || !value) return fail(DTT_ERR_ARG, "null constraint array");
+    if (row_ptr[0] != 0) return fail(DTT_ERR_ARG, "row_ptr[0] must be 0");
+    std::vector<uint8_t> seen((size_t)(3 * G->NN), 0);
+    ptr.assign(row_ptr, row_ptr + n_rows + 1);
+    for (int r = 0; r < n_rows; ++r) {
+      if (row_ptr[r + 1] <= row_ptr[r]) return fail(DTT_ERR_ARG, "empty or decreasing row");
+      double sab = 0.0, saa = 0.0;
+      for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+        if (node[e] < 0 || node[e] >= G->NN) return fail(DTT_ERR_ARG, "node index out of range");
+        if (comp[e] < 0 || comp[e] > 2) return fail(DTT_ERR_ARG, "component must be 0, 1 or 2");
+        if (!std::isfinite(a[e]) || (b && !std::isfinite(b[e]))) return fail(DTT_ERR_ARG, "non-finite weight");
+        int c = comp[e];
+        if (G->has_null[c])
+          return fail(DTT_ERR_NULLMODE, "constraint on component " + std::to_string(c) +
+                                             " whose Green symbol has null modes (give it a Dirichlet face)");
+        bool dofok;
+        double W;
+        host_node_W(G, c, node[e], dofok, W);
+        if (!dofok) return fail(DTT_ERR_ARG, "constraint entry on a Dirichlet-face DOF");
+        long long d = (long long)c * G->NN + node[e];
+        if (seen[(size_t)d]) return fail(DTT_ERR_OVERLAP, "constraint rows overlap");
+        seen[(size_t)d] = 1;
+        double bb = b ? b[e] : a[e];
+        dof.push_back(d);
+        va.push_back(a[e]);
+        vb.push_back(bb);
+        sab += a[e] * bb;
+        saa += a[e] * a[e];
+      }
+      if (!(saa > 0.0) || sab == 0.0) return fail(DTT_ERR_ARG, "row with sum a^2 = 0 or sum a b = 0");
+      if (!std::isfinite(value[r])) return fail(DTT_ERR_ARG, "non-finite constraint value");
+      vv.push_back(value[r]);
+      vab.push_back(sab);
+      vaa.push_back(saa);
+    }
+  }
+  free_rows(G);
+  G->nrows = n_rows;
+  G->h_ptr = ptr;
+  G->h_dof = dof;
+  G->h_a = va;
+  G->h_b = vb;
+  G->h_val = vv;
+  G->h_ab = vab;
+  G->h_aa = vaa;
+  if (n_rows > 0) {
+    size_t ne = dof.size();
+    dtt_status s = dalloc(&G->d_ptr, (n_rows + 1) * sizeof(int));
+    if (s == DTT_OK) s = dalloc(&G->d_dof, ne * sizeof(long long));
+    if (s == DTT_OK) s = dalloc(&G->d_a, ne * sizeof(double));
+    if (s == DTT_OK) s = dalloc(&G->d_b, ne * sizeof(double));
+    if (s == DTT_OK) s = dalloc(&G->d_target, n_rows * sizeof(double));
+    if (s == DTT_OK) s = dalloc(&G->d_mult, n_rows * sizeof(double));
+    if (s == DTT_OK) s = dalloc(&G->d_ab, n_rows * sizeof(double));
+    if (s == DTT_OK) s = dalloc(&G->d_aa, n_rows * sizeof(double));
+    if (s != DTT_OK) { G->nrows = 0; return s; }
+    CK(cudaMemcpy(G->d_ptr, ptr.data(), (n_rows + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->d_dof, dof.data(), ne * sizeof(long long), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->d_a, va.data(), ne * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->d_b, vb.data(), ne * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->d_ab, vab.data(), n_rows * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->d_aa, vaa.data(), n_rows * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemset(G->d_mult, 0, n_rows * sizeof(double)));
+  }
+  dtt_status s = ensure_partials(G);
+  if (s != DTT_OK) return s;
+  invalidate_graph(G);
+  return rebuild_cmask(G);
+}
+
+dtt_status dtt_set_indenter(dtt_grid* G, int32_t axis, int32_t face, const double center[3], double radius) {
+  if (!G || !center) return fail(DTT_ERR_ARG, "null argument");
+  if (axis < 0 || axis > 2 || face < 0 || face > 1) return fail(DTT_ERR_ARG, "axis in 0..2, face in 0..1");
+  if (G->g.periodic[axis]) return fail(DTT_ERR_BC, "contact face on a periodic axis");
+  if (!(radius > 0.0)) return fail(DTT_ERR_ARG, "radius must be > 0");
+  for (int c = 0; c < 3; ++c)
+    if (G->has_null[c]) return fail(DTT_ERR_NULLMODE, "contact needs components without Green null modes");
+  free_contact(G);
+  std::vector<long long> nodes;
+  const int fi = face == 0 ? 0 : G->g.nn[axis] - 1;
+  for (int k = 0; k < G->g.nn[2]; ++k)
+    for (int j = 0; j < G->g.nn[1]; ++j)
+      for (int i = 0; i < G->g.nn[0]; ++i) {
+        int idx[3] = {i, j, k};
+        if (idx[axis] != fi) continue;
+        nodes.push_back(i + (long long)G->g.nn[0] * (j + (long long)G->g.nn[1] * k));
+      }
+  G->nface = (int)nodes.size();
+  size_t nf = nodes.size();
+  dtt_status s = dalloc(&G->d_face, nf * sizeof(long long));
+  if (s == DTT_OK) s = dalloc(&G->d_active, nf);
+  if (s == DTT_OK) s = dalloc(&G->d_vgap, nf);
+  if (s == DTT_OK) s = dalloc(&G->d_vreact, nf);
+  if (s == DTT_OK) s = dalloc(&G->d_vgap_prev, nf);
+  if (s == DTT_OK) s = dalloc(&G->d_vreact_prev, nf);
+  if (s == DTT_OK) s = dalloc(&G->d_gap, nf * sizeof(double));
+  if (s == DTT_OK) s = dalloc(&G->d_fn, nf * sizeof(double));
+  if (s == DTT_OK) s = dalloc(&G->d_nvec, 3 * nf * sizeof(double));
+  if (s != DTT_OK) { free_contact(G); return s; }
+  CK(cudaMemcpy(G->d_face, nodes.data(), nf * sizeof(long long), cudaMemcpyHostToDevice));
+  CK(cudaMemset(G->d_active, 0, nf));
+  CK(cudaMemset(G->d_fn, 0, nf * sizeof(double)));
+  CK(cudaMemset(G->d_gap, 0, nf * sizeof(double)));
+  CK(cudaMemset(G->d_nvec, 0, 3 * nf * sizeof(double)));
+  G->contact = true;
+  G->c_axis = axis;
+  G->c_face = face;
+  for (int c = 0; c < 3; ++c) G->center[c] = center[c];
+  G->radius = radius;
+  s = ensure_partials(G);
+  if (s != DTT_OK) return s;
+  invalidate_graph(G);
+  return rebuild_cmask(G);
+}
+
+dtt_status dtt_move_indenter(dtt_grid* G, const double center[3]) {
+  if (!G || !center) return fail(DTT_ERR_ARG, "null argument");
+  if (!G->contact) return fail(DTT_ERR_STATE, "no indenter set");
+  for (int c = 0; c < 3; ++c) {
+    if (!std::isfinite(center[c])) return fail(DTT_ERR_ARG, "non-finite centre");
+    G->center[c] = center[c];
+  }
+  invalidate_graph(G);
+  return DTT_OK;
+}
+
+dtt_status dtt_clear_indenter(dtt_grid* G) {
+  if (!G) return fail(DTT_ERR_ARG, "null grid");
+  free_contact(G);
+  invalidate_graph(G);
+  return rebuild_cmask(G);
+}
+
+dtt_status dtt_set_initial(dtt_grid* G, const double* u, int32_t ptr_is_device) {
+  if (!G || !u) return fail(DTT_ERR_ARG, "null argument");
+  dtt_status s = to_grid_u(G, u, ptr_is_device);
+  if (s != DTT_OK) return s;
+  CK(cudaStreamSynchronize(G->stream));
+  return zero_dirichlet(G);
+}
+
+dtt_status dtt_solve_step(dtt_grid* G, const dtt_solve_opts* opts, dtt_report* rep) {
+  if (!G || !opts) return fail(DTT_ERR_ARG, "null argument");
+  if (!G->mat_set) return fail(DTT_ERR_STATE, "dtt_set_material not called");
+  if (!G->ref_set) return fail(DTT_ERR_STATE, "dtt_set_reference not called");
+  if (!(opts->tol >= 0.0) || opts->max_iter < 0) return fail(DTT_ERR_ARG, "tol >= 0 and max_iter >= 0 required");
+  if (opts->acv_mod < 0) return fail(DTT_ERR_ARG, "acv_mod >= 0");
+  if (opts->acv_on != DTT_ACV_U && opts->acv_on != DTT_ACV_P) return fail(DTT_ERR_ARG, "acv_on must be 0 or 1");
+  if (opts->acv_on == DTT_ACV_U && G->prec != DTT_PREC_FP64 && opts->acv_mod > 0)
+    return fail(DTT_ERR_ARG, "ACV on u~ is available in the FP64 path only");
+  if (opts->init != DTT_INIT_ZERO && opts->init != DTT_INIT_PREVIOUS) return fail(DTT_ERR_ARG, "init must be 0 or 1");
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = G->stream;
+  const size_t n3 = (size_t)(3 * G->NN);
+  if (opts->init == DTT_INIT_ZERO) {
+    if (G->u64) CK(cudaMemsetAsync(G->u64, 0, n3 * 8, s));
+    else {
+      CK(cudaMemsetAsync(G->uhi, 0, n3 * 4, s));
+      CK(cudaMemsetAsync(G->ulo, 0, n3 * 4, s));
+    }
+  }
+  // targets on u~ (U - A u*)
+  if (G->nrows > 0) {
+    std::vector<double> tg(G->nrows);
+    for (int r = 0; r < G->nrows; ++r) {
+      double su = 0.0;
+      for (int e = G->h_ptr[r]; e < G->h_ptr[r + 1]; ++e) {
+        long long d = G->h_dof[e];
+        int c = (int)(d / G->NN);
+        su += G->h_a[e] * host_ustar(G, c, d - c * G->NN);
+      }
+      tg[r] = G->h_val[r] - su;
+    }
+    CK(cudaMemcpyAsync(G->d_target, tg.data(), G->nrows * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  // control block
+  Ctrl& c = *G->h_ctrl;
+  std::memset(&c, 0, sizeof(Ctrl));
+  c.max_iter = opts->max_iter;
+  c.acv_mod = opts->acv_mod > 0 ? opts->acv_mod : 1;
+  c.acv_on = opts->acv_on;
+  c.contact_on = G->contact ? 1 : 0;
+  c.tol = opts->tol;
+  c.update_tol = opts->update_tol > 0.0 ? opts->update_tol : 1e-2;
+  CK(cudaMemcpyAsync(G->d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+  for (int k = 0; k < 5; ++k) CK(cudaMemsetAsync(G->S[k], 0, n3 * G->esz, s));
+  for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(G->R[k], 0, n3 * G->esz, s));
+  PartRegions pr = regions(G);
+  ContactArgs ca = contact_args(G, pr.cont);
+  if (G->contact) {
+    CKL(launch_contact_init(ca, s));
+    CKL(launch_contact_proj_U(ca, G->u64, G->uhi, G->ulo, s));
+  }
+  if (G->nrows > 0) CKL(launch_proj_U_rows(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, G->d_ctrl, s));
+  const bool acv = opts->acv_mod > 0;
+  const int iters = opts->graph_iters > 0 ? opts->graph_iters : 8;
+  const int key = opts->acv_on * 1000000 + (acv ? 100000 : 0) + iters;
+  if (!G->gexec || G->g_key != key) {
+    dtt_status st = build_graph(G, opts->acv_on, acv, iters);
+    if (st != DTT_OK) return st;
+  }
+  long long launched = 0;
+  const long long cap = (long long)opts->max_iter + 2LL * iters + 8;
+  while (true) {
+    CK(cudaGraphLaunch(G->gexec, s));
+    launched += iters;
+    CK(cudaMemcpyAsync(G->h_ctrl, G->d_ctrl, 64, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (G->h_ctrl->done) break;
+    if (launched > cap) break;   // cannot happen: the device stops at max_iter
+  }
+  CK(cudaMemcpyAsync(G->h_ctrl, G->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  G->last = *G->h_ctrl;
+  G->solved = true;
+  double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  dtt_status st = DTT_OK;
+  if (G->last.done == 2 || G->last.done == 0) st = DTT_ERR_NOT_CONVERGED;
+  if (G->last.done == 3) st = DTT_ERR_DIVERGED;
+  if (rep) {
+    rep->iterations = G->last.iter;
+    rep->accelerations = G->last.n_accel;
+    rep->active_set_updates = G->last.n_updates;
+    rep->status = st;
+    rep->residual = G->last.r;
+    rep->seconds = secs;
+  }
+  if (st == DTT_ERR_NOT_CONVERGED) g_err = "iteration cap reached";
+  if (st == DTT_ERR_DIVERGED) g_err = "residual diverged";
+  return st;
+}
+
+dtt_status dtt_get_history(const dtt_grid* G, double* hist, int32_t* n) {
+  if (!G || !n) return fail(DTT_ERR_ARG, "null argument");
+  int m = std::min(G->last.hist_len, *n);
+  if (hist)
+    for (int k = 0; k < m; ++k) hist[k] = G->last.hist[k];
+  *n = G->last.hist_len;
+  return DTT_OK;
+}
+
+dtt_status dtt_get_fields(dtt_grid* G, double* u, double* sigma, int32_t ptr_is_device) {
+  if (!G) return fail(DTT_ERR_ARG, "null grid");
+  const size_t n3 = (size_t)(3 * G->NN);
+  cudaStream_t s = G->stream;
+  const double* src = G->u64;
+  if (!src) {
+    CKL(launch_join((long long)n3, G->uhi, G->ulo, G->op_d, s));
+    src = G->op_d;
+  }
+  if (u) CK(cudaMemcpyAsync(u, src, n3 * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (sigma) {
+    if (!G->mat_set) return fail(DTT_ERR_STATE, "material not set");
+    size_t ns = (size_t)G->NV * kIP[G->g.scheme] * 6;
+    double* buf = nullptr;
+    dtt_status st = dalloc(&buf, ns * sizeof(double));
+    if (st != DTT_OK) return st;
+    int rc = launch_stress_out(G->g, src, G->phase, G->d_lam, G->d_mu, G->eps, buf, s);
+    if (rc) { dfree(buf); return fail(DTT_ERR_CUDA, "stress kernel launch"); }
+    cudaError_t e = cudaMemcpyAsync(sigma, buf, ns * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    dfree(buf);
+    if (e != cudaSuccess) return fail(DTT_ERR_CUDA, cudaGetErrorString(e));
+  }
+  CK(cudaStreamSynchronize(s));
+  return DTT_OK;
+}
+
+dtt_status dtt_get_reactions(dtt_grid* G, double* per_row, double total[3]) {
+  if (!G) return fail(DTT_ERR_ARG, "null grid");
+  std::vector<double> f(G->nrows);
+  if (G->nrows > 0) CK(cudaMemcpy(f.data(), G->d_mult, G->nrows * sizeof(double), cudaMemcpyDeviceToHost));
+  double tot[3] = {0, 0, 0};
+  const double h3 = G->g.h * G->g.h * G->g.h;
+  for (int r = 0; r < G->nrows; ++r) {
+    double pr = 0.0;
+    for (int e = G->h_ptr[r]; e < G->h_ptr[r + 1]; ++e) {
+      long long d = G->h_dof[e];
+      int c = (int)(d / G->NN);
+      bool dof;
+      double W;
+      host_node_W(G, c, d - c * G->NN, dof, W);
+      double v = h3 * W * G->h_b[e] * f[r];
+      pr += v;
+      tot[c] += v;
+    }
+    if (per_row) per_row[r] = pr;
+  }
+  if (total)
+    for (int c = 0; c < 3; ++c) total[c] = tot[c];
+  return DTT_OK;
+}
+
+dtt_status dtt_get_contact(dtt_grid* G, int32_t* n_face, uint8_t* active, double* gap, double* fn, double force[3]) {
+  if (!G) return fail(DTT_ERR_ARG, "null grid");
+  if (n_face) *n_face = G->nface;
+  if (!G->contact) {
+    if (force) force[0] = force[1] = force[2] = 0.0;
+    return DTT_OK;
+  }
+  size_t nf = G->nface;
+  std::vector<uint8_t> act(nf);
+  std::vector<double> f(nf), nv(3 * nf);
+  CK(cudaMemcpy(act.data(), G->d_active, nf, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(f.data(), G->d_fn, nf * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(nv.data(), G->d_nvec, 3 * nf * 8, cudaMemcpyDeviceToHost));
+  if (active) std::memcpy(active, act.data(), nf);
+  if (fn) std::memcpy(fn, f.data(), nf * 8);
+  if (gap) CK(cudaMemcpy(gap, G->d_gap, nf * 8, cudaMemcpyDeviceToHost));
+  if (force) {
+    double F[3] = {0, 0, 0};
+    for (size_t q = 0; q < nf; ++q)
+      if (act[q])
+        for (int c = 0; c < 3; ++c) F[c] += f[q] * nv[3 * q + c];
+    for (int c = 0; c < 3; ++c) force[c] = F[c];
+  }
+  return DTT_OK;
+}
+
+dtt_status dtt_apply_residual(dtt_grid* G, const double* u, double* p, double* ptilde, double norms[2],
+                              int32_t ptr_is_device) {
+  if (!G || !u) return fail(DTT_ERR_ARG, "null argument");
+  if (!G->mat_set || !G->ref_set) return fail(DTT_ERR_STATE, "material and reference must be set");
+  dtt_status st = ensure_ops(G);
+  if (st != DTT_OK) return st;
+  cudaStream_t s = G->stream;
+  const size_t n3 = (size_t)(3 * G->NN);
+  // u into op storage (does not touch the solver state)
+  double* ud = G->op_d;
+  CK(cudaMemcpyAsync(ud, u, n3 * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  float *hi = nullptr, *lo = nullptr;
+  if (G->prec == DTT_PREC_MIXED) {
+    hi = (float*)G->op_t1;   // reuse: 3NN floats each
+    lo = (float*)G->spec;
+    CKL(launch_split((long long)n3, ud, hi, lo, s));
+  }
+  ResidualArgs ra{};
+  ra.g = G->g;
+  ra.u64 = G->prec == DTT_PREC_FP64 ? ud : nullptr;
+  ra.uhi = hi;
+  ra.ulo = lo;
+  ra.phase = G->phase;
+  ra.lam = G->d_lam;
+  ra.mu = G->d_mu;
+  ra.nphase = G->nphase;
+  ra.cmask = nullptr;
+  std::memcpy(ra.eps, G->eps, sizeof(ra.eps));
+  ra.lam0 = G->lam0;
+  ra.mu0 = G->mu0;
+  ra.pout = G->gbuf;
+  ra.xout = G->op_t2;
+  ra.partials = G->d_part;
+  ra.ctrl = nullptr;
+  ra.write_x_ring = 0;
+  if (G->prec == DTT_PREC_FP64) CKL(launch_residual<double>(ra, s));
+  else CKL(launch_residual<float>(ra, s));
+  const int isf = G->prec == DTT_PREC_MIXED;
+  auto out = [&](const void* src, double* dst) -> dtt_status {
+    CKL(launch_to_double((long long)n3, src, isf, G->op_d, s));
+    CK(cudaMemcpyAsync(dst, G->op_d, n3 * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return DTT_OK;
+  };
+  if (p) { st = out(G->gbuf, p); if (st != DTT_OK) return st; }
+  if (ptilde) { st = out(G->op_t2, ptilde); if (st != DTT_OK) return st; }
+  if (norms) {
+    int nb = residual_blocks(G->g);
+    std::vector<double> part(2 * (size_t)nb);
+    CK(cudaMemcpyAsync(part.data(), G->d_part, part.size() * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double a0 = 0.0, a1 = 0.0;
+    for (int b = 0; b < nb; ++b) { a0 += part[2 * b]; a1 += part[2 * b + 1]; }
+    norms[0] = a0;
+    norms[1] = a1;
+  }
+  CK(cudaStreamSynchronize(s));
+  return DTT_OK;
+}
+
+dtt_status dtt_apply_green(dtt_grid* G, const double* ptilde, double* u, int32_t ptr_is_device) {
+  if (!G || !ptilde || !u) return fail(DTT_ERR_ARG, "null argument");
+  if (!G->ref_set) return fail(DTT_ERR_STATE, "reference not set");
+  dtt_status st = ensure_ops(G);
+  if (st != DTT_OK) return st;
+  cudaStream_t s = G->stream;
+  const size_t n3 = (size_t)(3 * G->NN);
+  const int isf = G->prec == DTT_PREC_MIXED;
+  CK(cudaMemcpyAsync(G->op_d, ptilde, n3 * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  CKL(launch_from_double((long long)n3, G->op_d, G->op_t1, isf, s));
+  if (isf) st = enqueue_green<float>(G, (float*)G->op_t1, (float*)G->op_t2, false, nullptr, 0, 3);
+  else st = enqueue_green<double>(G, (double*)G->op_t1, (double*)G->op_t2, false, nullptr, 0, 3);
+  if (st != DTT_OK) return st;
+  CKL(launch_to_double((long long)n3, G->op_t1, isf, G->op_d, s));
+  CK(cudaMemcpyAsync(u, G->op_d, n3 * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return DTT_OK;
+}
+
+dtt_status dtt_transform(dtt_grid* G, int32_t component, int32_t inverse, const double* in, double* out,
+                         int32_t ptr_is_device) {
+  if (!G || !in || !out) return fail(DTT_ERR_ARG, "null argument");
+  if (component < 0 || component > 2) return fail(DTT_ERR_ARG, "component in 0..2");
+  dtt_status st = ensure_ops(G);
+  if (st != DTT_OK) return st;
+  cudaStream_t s = G->stream;
+  const size_t n3 = (size_t)(3 * G->NN);
+  const size_t off = (size_t)component * G->NN;
+  const int isf = G->prec == DTT_PREC_MIXED;
+  CK(cudaMemsetAsync(G->op_d, 0, n3 * 8, s));
+  CK(cudaMemcpyAsync(G->op_d + off, in, (size_t)G->NN * 8,
+                     ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  CKL(launch_from_double((long long)n3, G->op_d, G->op_t1, isf, s));
+  TransformTables tt = tables(G);
+  const int axes_f[3] = {0, 1, 2}, axes_i[3] = {2, 1, 0};
+  void* a = G->op_t1;
+  void* b = G->op_t2;
+  for (int q = 0; q < 3; ++q) {
+    int ax = inverse ? axes_i[q] : axes_f[q];
+    if (isf) CKL(launch_transform_axis<float>(G->g, (const float*)a, (float*)b, tt, ax, inverse, component, 1, nullptr, s));
+    else CKL(launch_transform_axis<double>(G->g, (const double*)a, (double*)b, tt, ax, inverse, component, 1, nullptr, s));
+    std::swap(a, b);
+  }
+  CKL(launch_to_double((long long)n3, a, isf, G->op_d, s));
+  CK(cudaMemcpyAsync(out, G->op_d + off, (size_t)G->NN * 8,
+                     ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return DTT_OK;
+}
+
+dtt_status dtt_profile_iteration(dtt_grid* G, const dtt_solve_opts* opts, int32_t iters, double* ms) {
+  if (!G || !opts || !ms || iters < 1) return fail(DTT_ERR_ARG, "bad argument");
+  if (!G->mat_set || !G->ref_set) return fail(DTT_ERR_STATE, "material and reference must be set");
+  cudaStream_t s = G->stream;
+  // fresh control block that never stops within `iters`
+  Ctrl& c = *G->h_ctrl;
+  std::memset(&c, 0, sizeof(Ctrl));
+  c.max_iter = 1 << 30;
+  c.acv_mod = opts->acv_mod > 0 ? opts->acv_mod : 1;
+  c.acv_on = opts->acv_on;
+  c.contact_on = G->contact ? 1 : 0;
+  c.tol = 0.0;
+  c.update_tol = 1e-2;
+  c.no_stop = 1;
+  CK(cudaMemcpyAsync(G->d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+  cudaEvent_t ev[9];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  double acc[9] = {0};
+  const bool acv = opts->acv_mod > 0;
+  dtt_status st = DTT_OK;
+  for (int it = 0; it < iters && st == DTT_OK; ++it) {
+    g_prof_ev = ev;
+    st = enqueue_iter_any(G, opts->acv_on, acv);
+    g_prof_ev = nullptr;
+    CK(cudaEventSynchronize(ev[8]));
+    for (int k = 0; k < 8; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st != DTT_OK) return st;
+  // groups: 0 residual [0,1), 1 proj+contact+ctrl [1,2) + [7,8), 2 Anderson [2,3),
+  // 3 forward transforms [3,4), 4 Green [4,5), 5 inverse transforms [5,6), 6 increment [6,7)
+  ms[0] = acc[0] / iters;
+  ms[1] = (acc[1] + acc[7]) / iters;
+  ms[2] = acc[2] / iters;
+  ms[3] = acc[3] / iters;
+  ms[4] = acc[4] / iters;
+  ms[5] = acc[5] / iters;
+  ms[6] = acc[6] / iters;
+  return DTT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,200 @@
+// Internal declarations shared by the CUDA translation units of libdtt.
+//
+// Data layout in device memory (one grid):
+//   * node arrays: component-major, x fastest: field[c * nnodes + i + nnx*(j + nny*k)],
+//     nn_d = n_d + 1 on a non-periodic axis, n_d on a periodic one;
+//   * u~ (the fluctuation displacement, Eq. 3): float64 in the FP64 path; in the mixed
+//     path a float-float pair (hi, lo) so that differences of neighbouring values, and
+//     thus strains, keep ~48 bits while every arithmetic operation stays in FP32;
+//   * the other nodal fields (p, p~ ring, Anderson ring, spectra) are T = double (FP64
+//     path) or float (mixed path);
+//   * voxel phase ids: uint8, x fastest.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dtt {
+
+constexpr int BC_P = 0, BC_D = 1, BC_N = 2;
+constexpr int T_DCT1 = 0, T_DCT3 = 1, T_DST1 = 2, T_DST3 = 3, T_DHT = 4;
+constexpr int SCHEME_TETRA2 = 0, SCHEME_HEX1 = 1;
+constexpr int MAX_PHASE = 256;
+constexpr int HIST = 4096;
+
+// Geometry passed by value to every kernel.
+struct GridDev {
+  int nvox[3];
+  int nn[3];
+  long long nnodes;
+  double h;
+  int scheme;
+  int bc[3][2][3];  // [axis][face][component]
+  int periodic[3];
+};
+
+// Solver state kept on the device so that a whole iteration is a fixed sequence of
+// launches (capturable in a CUDA graph) with no host decision in it.
+struct Ctrl {
+  int i_local;        // Anderson counter (reset to 0 when the contact zone changes)
+  int iter;           // Green steps performed
+  int done;           // 0 running, 1 converged, 2 iteration cap, 3 diverged
+  int accel;          // accelerate at this iteration
+  int max_iter;
+  int acv_mod;
+  int acv_on;         // 0 = u~, 1 = p~
+  int contact_on;
+  int update;         // contact-zone update at this iteration
+  int changed;        // contact zone changed by the last update
+  int n_updates;
+  int n_accel;
+  int n_vgap, n_vreact, n_mismatch, prev_valid;
+  int hist_len;
+  int no_stop;        // profiling: never stop on tolerance, cap or divergence
+  double tol, update_tol;
+  double r, r0;
+  double p2, s2;
+  double alpha[4];
+  double gram[4][4];
+  double hist[HIST];
+};
+
+// Sparse constraint rows (CSR over entries), disjoint supports.
+struct RowsDev {
+  int nrows;
+  const int* ptr;        // nrows + 1
+  const long long* dof;  // c * nnodes + node
+  const double* a;
+  const double* b;
+  const double* target;  // value on u~ (U - A u*)
+  double* mult;          // f_r = -lambda_r
+  const double* ab;      // sum a b
+  const double* aa;      // sum a a
+};
+
+struct ContactDev {
+  int nnodes_face;
+  const long long* node;   // flat node index of each surface node
+  uint8_t* active;
+  uint8_t* vgap;
+  uint8_t* vreact;
+  uint8_t* vgap_prev;
+  uint8_t* vreact_prev;
+  double* gap;
+  double* fn;
+  double* nvec;            // 3 x nnodes_face normals at the last evaluation
+  double center[3];
+  double radius;
+};
+
+// ---------------------------------------------------------------------------------
+// Float-float helpers (mixed path).  TwoSum (Knuth) and Fast2Sum (Dekker): error-free
+// transformations of a floating-point sum, written from their published definitions.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float d) {
+  float s = __fadd_rn(hi, d);
+  float bb = __fsub_rn(s, hi);
+  float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+  e = __fadd_rn(e, lo);
+  float h2 = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(h2, s));
+  hi = h2;
+}
+__device__ __forceinline__ void ff_set(float& hi, float& lo, double v) {
+  hi = __double2float_rn(v);
+  lo = __double2float_rn(v - (double)hi);
+}
+
+// ---------------------------------------------------------------------------------
+// Launch wrappers (kernels.cu).  T = double (FP64 path) or float (mixed path).
+// ---------------------------------------------------------------------------------
+struct ResidualArgs {
+  GridDev g;
+  const double* u64;
+  const float* uhi;
+  const float* ulo;
+  const uint8_t* phase;
+  const double* lam;
+  const double* mu;
+  int nphase;
+  const uint8_t* cmask;   // bit c set: DOF (node, c) belongs to a row support / contact face
+  double eps[3][3];
+  double lam0, mu0;
+  void* xout;             // p~ = p + A0 u~ (may be null)
+  void* pout;             // p (may be null)
+  double* partials;       // 2 per block: sum w sigma:sigma, sum p^2 (unmasked DOFs)
+  const Ctrl* ctrl;       // if non-null: skip when done; xout = ring slot from i_local
+  void* ring[5];          // ring slots for p~ (ACV_P) when ctrl is set
+  int write_x_ring;
+  int zchunk;             // z planes per CTA (set by the launcher)
+};
+template <typename T> int launch_residual(const ResidualArgs& a, cudaStream_t s);
+int residual_blocks(const GridDev& g);
+int residual_zchunk(const GridDev& g);
+
+struct TransformTables {
+  const void* fwd[3][3];   // [comp][axis] nn x nn row-major (spectral k, node j)
+  const void* inv[3][3];   // [comp][axis] nn x nn row-major (node j, spectral k)
+  const double* cosq[3][3];
+  double lam0, mu0;
+  double null_thr[3];
+};
+template <typename T>
+int launch_transform_axis(const GridDev& g, const T* in, T* out, const TransformTables& tt,
+                          int axis, int inverse, int ncomp_first, int ncomp, const Ctrl* ctrl,
+                          cudaStream_t s);
+template <typename T>
+int launch_green_multiply(const GridDev& g, T* spec, const TransformTables& tt, int scheme,
+                          const Ctrl* ctrl, cudaStream_t s);
+template <typename T>
+int launch_add_increment(const GridDev& g, const T* delta, double* u64, float* uhi, float* ulo,
+                         const Ctrl* ctrl, cudaStream_t s);
+
+template <typename T>
+int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p, T* x_or_null, int x_from_ring,
+                       void* const* ring, double* partials, const Ctrl* ctrl, cudaStream_t s);
+int launch_proj_U_rows(const GridDev& g, const RowsDev& r, double* u64, float* uhi, float* ulo,
+                       const Ctrl* ctrl, cudaStream_t s);
+
+struct ContactArgs {
+  GridDev g;
+  ContactDev c;
+  const double* u64;
+  const float* uhi;
+  const float* ulo;
+  double eps[3][3];
+  const Ctrl* ctrl;
+  double* partials;   // 3 per block: p^2, n_vgap, n_vreact (+ mismatches in [3])
+};
+template <typename T>
+int launch_contact_eval(const ContactArgs& a, T* p, void* const* ring, int x_from_ring,
+                        cudaStream_t s);
+int launch_contact_update(const ContactArgs& a, cudaStream_t s);
+int launch_contact_proj_U(const ContactArgs& a, double* u64, float* uhi, float* ulo,
+                          cudaStream_t s);
+int launch_contact_init(const ContactArgs& a, cudaStream_t s);
+int contact_blocks(int nface);
+
+template <typename T>
+int launch_acv_store(const GridDev& g, int acv_on, void* const* Sring, void* const* Rring,
+                     const double* u64, double* partials, const Ctrl* ctrl, cudaStream_t s);
+template <typename T>
+int launch_acv_accel(const GridDev& g, int acv_on, void* const* Sring, void* const* Rring,
+                     T* gbuf, double* u64, const Ctrl* ctrl, cudaStream_t s);
+int acv_blocks(const GridDev& g);
+
+// control kernels
+int launch_ctrl_residual(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, const double* cp,
+                         int ncont, double h, long long nnodes, long long nvox, cudaStream_t s);
+int launch_ctrl_contact(Ctrl* c, cudaStream_t s);
+int launch_ctrl_acv(Ctrl* c, const double* partials, int nblk, cudaStream_t s);
+int launch_ctrl_end(Ctrl* c, cudaStream_t s);
+
+// utilities (k_util.cu)
+int launch_to_double(long long n, const void* in, int in_is_float, double* out, cudaStream_t s);
+int launch_from_double(long long n, const double* in, void* out, int out_is_float, cudaStream_t s);
+int launch_split(long long n, const double* in, float* hi, float* lo, cudaStream_t s);
+int launch_join(long long n, const float* hi, const float* lo, double* out, cudaStream_t s);
+int launch_stress_out(const GridDev& g, const double* u, const uint8_t* phase, const double* lam,
+                      const double* mu, const double eps[3][3], double* out, cudaStream_t s);
+
+}  // namespace dtt

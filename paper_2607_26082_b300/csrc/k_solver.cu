@@ -1,0 +1,530 @@
+// Constraint projections, contact evaluation, Anderson acceleration and the device-side
+// control of the fixed-point iteration.
+//
+//  * proj_P (Eq. 9, 14, 17): lambda_r = (sum_e a_e p_e) / (sum_e a_e b_e), p_e -= b_e lambda_r,
+//    multiplier f_r = -lambda_r kept in FP64.  The same shift is applied to p~ (= p + A0 u~).
+//  * proj_U (Eq. 9, 11, 15): u~_e += a_e (t_r - sum a u~) / (sum a a), in FP64.
+//  * Contact (Section 5.1, Eq. 24-28, Algorithm 2): gap g = |O - M'| - R, normal
+//    n_c = (O - M')/|O - M'| with M' = M + u* + u~ (FP64); on the active set C,
+//    p <- p - (p.n_c) n_c; normal reaction f = -h^3 sum_c W_c p_c n_c (one-sided divergence,
+//    evaluated before the projection); violation sets V_gap = {M not in C: g < 0},
+//    V_react = {M in C: f > 0}; proj_U places an active node radially on the sphere,
+//    u(M) = O - R n_c - M.
+//  * Anderson depth 4 (Section 4.1.1): R_{i-1} = x_i - S_{i-1}; every mod_ACV iterations
+//    after the first four, alpha = argmin ||sum alpha_k R_k|| with sum alpha_k = 1 (FP64
+//    Gram, Gaussian elimination with partial pivoting, skipped on a pivot <= 1e-14 max G_kk),
+//    x_i <- sum alpha_k (S_k + R_k).
+// All scalar decisions run in single-thread control kernels so that an iteration is a fixed
+// sequence of launches; every kernel returns at once when the solve is finished.
+#include "dtt_internal.cuh"
+
+namespace dtt {
+
+constexpr int SB = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  #pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+  return t;   // valid in thread 0
+}
+
+__device__ __forceinline__ double read_u(long long e, const double* u64, const float* uhi, const float* ulo) {
+  return u64 ? u64[e] : (double)uhi[e] + (double)ulo[e];
+}
+__device__ __forceinline__ void write_u(long long e, double v, double* u64, float* uhi, float* ulo) {
+  if (u64) u64[e] = v;
+  else { float h, l; ff_set(h, l, v); uhi[e] = h; ulo[e] = l; }
+}
+
+__device__ __forceinline__ void node_ijk(const GridDev& g, long long n, int& i, int& j, int& k) {
+  i = (int)(n % g.nn[0]);
+  long long r = n / g.nn[0];
+  j = (int)(r % g.nn[1]);
+  k = (int)(r / g.nn[1]);
+}
+
+__device__ __forceinline__ void node_W(const GridDev& g, int c, int i, int j, int k, bool& dof, double& W) {
+  W = 1.0;
+  dof = true;
+  const int idx[3] = {i, j, k};
+  for (int d = 0; d < 3; ++d) {
+    if (g.periodic[d]) continue;
+    int f = -1;
+    if (idx[d] == 0) f = 0;
+    else if (idx[d] == g.nn[d] - 1) f = 1;
+    if (f < 0) continue;
+    int t = g.bc[d][f][c];
+    if (t == BC_D) dof = false;
+    else if (t == BC_N) W *= 0.5;
+  }
+}
+
+// ------------------------------------------------------------------ proj_P (rows)
+template <typename T>
+__global__ void k_proj_P(const RowsDev r, T* __restrict__ p, void* const* ring, int x_from_ring,
+                         T* xdirect, double* partials, const Ctrl* ctrl) {
+  __shared__ double sh[SB / 32];
+  if (ctrl && ctrl->done) return;
+  T* x = xdirect;
+  if (x_from_ring && ctrl) x = (T*)ring[ctrl->i_local % 5];
+  double acc = 0.0;
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row < r.nrows) {
+    double sap = 0.0;
+    for (int e = r.ptr[row]; e < r.ptr[row + 1]; ++e) sap += r.a[e] * (double)p[r.dof[e]];
+    double lam = sap / r.ab[row];
+    for (int e = r.ptr[row]; e < r.ptr[row + 1]; ++e) {
+      long long d = r.dof[e];
+      double sh_ = r.b[e] * lam;
+      double pn = (double)p[d] - sh_;
+      p[d] = (T)pn;
+      if (x) x[d] = (T)((double)x[d] - sh_);
+      acc += (double)(T)pn * (double)(T)pn;
+    }
+    r.mult[row] = -lam;
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+template <typename T>
+int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p, T* x_or_null, int x_from_ring,
+                       void* const* ring, double* partials, const Ctrl* ctrl, cudaStream_t s) {
+  (void)g;
+  int blocks = (r.nrows + SB - 1) / SB;
+  if (blocks == 0) return 0;
+  k_proj_P<T><<<blocks, SB, 0, s>>>(r, p, ring, x_from_ring, x_or_null, partials, ctrl);
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ proj_U (rows)
+__global__ void k_proj_U(const RowsDev r, double* u64, float* uhi, float* ulo, const Ctrl* ctrl) {
+  if (ctrl && ctrl->done) return;
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= r.nrows) return;
+  double sau = 0.0;
+  for (int e = r.ptr[row]; e < r.ptr[row + 1]; ++e) sau += r.a[e] * read_u(r.dof[e], u64, uhi, ulo);
+  double corr = (r.target[row] - sau) / r.aa[row];
+  for (int e = r.ptr[row]; e < r.ptr[row + 1]; ++e) {
+    if (r.a[e] == 0.0) continue;
+    long long d = r.dof[e];
+    write_u(d, read_u(d, u64, uhi, ulo) + r.a[e] * corr, u64, uhi, ulo);
+  }
+}
+
+int launch_proj_U_rows(const GridDev& g, const RowsDev& r, double* u64, float* uhi, float* ulo,
+                       const Ctrl* ctrl, cudaStream_t s) {
+  (void)g;
+  int blocks = (r.nrows + SB - 1) / SB;
+  if (blocks == 0) return 0;
+  k_proj_U<<<blocks, SB, 0, s>>>(r, u64, uhi, ulo, ctrl);
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ contact
+int contact_blocks(int nface) { return (nface + SB - 1) / SB; }
+
+__device__ void contact_geom(const ContactArgs& a, long long n, double Mp[3], double nv[3], double& gap,
+                             double X[3]) {
+  int i, j, k;
+  node_ijk(a.g, n, i, j, k);
+  X[0] = a.g.h * i; X[1] = a.g.h * j; X[2] = a.g.h * k;
+  double v[3], dist2 = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    double us = a.eps[c][0] * X[0] + a.eps[c][1] * X[1] + a.eps[c][2] * X[2];
+    Mp[c] = X[c] + us + read_u((long long)c * a.g.nnodes + n, a.u64, a.uhi, a.ulo);
+    v[c] = a.c.center[c] - Mp[c];
+    dist2 += v[c] * v[c];
+  }
+  double dist = sqrt(dist2);
+  for (int c = 0; c < 3; ++c) nv[c] = v[c] / dist;
+  gap = dist - a.c.radius;
+}
+
+template <typename T>
+__global__ void k_contact_eval(const ContactArgs a, T* __restrict__ p, void* const* ring, int x_from_ring) {
+  __shared__ double sh[SB / 32];
+  if (a.ctrl && a.ctrl->done) return;
+  T* x = nullptr;
+  if (x_from_ring && a.ctrl) x = (T*)ring[a.ctrl->i_local % 5];
+  double p2 = 0.0, ng = 0.0, nr = 0.0, mm = 0.0;
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < a.c.nnodes_face) {
+    long long n = a.c.node[q];
+    double Mp[3], nv[3], X[3], gap;
+    contact_geom(a, n, Mp, nv, gap, X);
+    int i, j, k;
+    node_ijk(a.g, n, i, j, k);
+    double pv[3], W[3];
+    bool dof[3];
+    double f = 0.0, pn = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      node_W(a.g, c, i, j, k, dof[c], W[c]);
+      pv[c] = dof[c] ? (double)p[(long long)c * a.g.nnodes + n] : 0.0;
+      f += W[c] * pv[c] * nv[c];
+      pn += pv[c] * nv[c];
+    }
+    f *= -(a.g.h * a.g.h * a.g.h);
+    const bool act = a.c.active[q] != 0;
+    if (act) {
+      for (int c = 0; c < 3; ++c) {
+        if (!dof[c]) continue;
+        long long e = (long long)c * a.g.nnodes + n;
+        double sh_ = pn * nv[c];
+        double np_ = pv[c] - sh_;
+        p[e] = (T)np_;
+        if (x) x[e] = (T)((double)x[e] - sh_);
+        pv[c] = (double)(T)np_;
+      }
+    }
+    for (int c = 0; c < 3; ++c) p2 += pv[c] * pv[c];
+    uint8_t vg = (!act && gap < 0.0) ? 1 : 0;
+    uint8_t vr = (act && f > 0.0) ? 1 : 0;
+    if (vg != a.c.vgap_prev[q] || vr != a.c.vreact_prev[q]) mm = 1.0;
+    a.c.vgap[q] = vg;
+    a.c.vreact[q] = vr;
+    ng = vg;
+    nr = vr;
+    a.c.gap[q] = gap;
+    a.c.fn[q] = f;
+    for (int c = 0; c < 3; ++c) a.c.nvec[3 * q + c] = nv[c];
+  }
+  double t0 = block_sum(p2, sh);
+  double t1 = block_sum(ng, sh);
+  double t2 = block_sum(nr, sh);
+  double t3 = block_sum(mm, sh);
+  if (threadIdx.x == 0) {
+    a.partials[4 * blockIdx.x] = t0;
+    a.partials[4 * blockIdx.x + 1] = t1;
+    a.partials[4 * blockIdx.x + 2] = t2;
+    a.partials[4 * blockIdx.x + 3] = t3;
+  }
+}
+
+template <typename T>
+int launch_contact_eval(const ContactArgs& a, T* p, void* const* ring, int x_from_ring, cudaStream_t s) {
+  int blocks = contact_blocks(a.c.nnodes_face);
+  if (blocks == 0) return 0;
+  k_contact_eval<T><<<blocks, SB, 0, s>>>(a, p, ring, x_from_ring);
+  return (int)cudaGetLastError();
+}
+
+__global__ void k_contact_update(const ContactArgs a) {
+  Ctrl* ctrl = const_cast<Ctrl*>(a.ctrl);
+  if (ctrl->done) return;
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.c.nnodes_face) return;
+  uint8_t vg = a.c.vgap[q], vr = a.c.vreact[q];
+  if (ctrl->update) {
+    uint8_t old = a.c.active[q];
+    uint8_t nw = (uint8_t)((old | vg) & (vr ? 0 : 1));
+    if (nw != old) { a.c.active[q] = nw; atomicAdd(&ctrl->changed, 1); }
+  }
+  a.c.vgap_prev[q] = vg;
+  a.c.vreact_prev[q] = vr;
+}
+
+int launch_contact_update(const ContactArgs& a, cudaStream_t s) {
+  int blocks = contact_blocks(a.c.nnodes_face);
+  if (blocks == 0) return 0;
+  k_contact_update<<<blocks, SB, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+__global__ void k_contact_proj_U(const ContactArgs a, double* u64, float* uhi, float* ulo) {
+  if (a.ctrl && a.ctrl->done) return;
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.c.nnodes_face || !a.c.active[q]) return;
+  long long n = a.c.node[q];
+  double Mp[3], nv[3], X[3], gap;
+  contact_geom(a, n, Mp, nv, gap, X);
+  int i, j, k;
+  node_ijk(a.g, n, i, j, k);
+  for (int c = 0; c < 3; ++c) {
+    bool dof;
+    double W;
+    node_W(a.g, c, i, j, k, dof, W);
+    if (!dof) continue;
+    double us = a.eps[c][0] * X[0] + a.eps[c][1] * X[1] + a.eps[c][2] * X[2];
+    double target = a.c.center[c] - a.c.radius * nv[c] - X[c] - us;
+    write_u((long long)c * a.g.nnodes + n, target, u64, uhi, ulo);
+  }
+}
+
+int launch_contact_proj_U(const ContactArgs& a, double* u64, float* uhi, float* ulo, cudaStream_t s) {
+  int blocks = contact_blocks(a.c.nnodes_face);
+  if (blocks == 0) return 0;
+  k_contact_proj_U<<<blocks, SB, 0, s>>>(a, u64, uhi, ulo);
+  return (int)cudaGetLastError();
+}
+
+__global__ void k_contact_init(const ContactArgs a) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.c.nnodes_face) return;
+  long long n = a.c.node[q];
+  double Mp[3], nv[3], X[3], gap;
+  contact_geom(a, n, Mp, nv, gap, X);
+  a.c.active[q] = gap < 0.0 ? 1 : 0;
+  a.c.vgap_prev[q] = 0;
+  a.c.vreact_prev[q] = 0;
+  a.c.gap[q] = gap;
+}
+
+int launch_contact_init(const ContactArgs& a, cudaStream_t s) {
+  int blocks = contact_blocks(a.c.nnodes_face);
+  if (blocks == 0) return 0;
+  k_contact_init<<<blocks, SB, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Anderson
+int acv_blocks(const GridDev& g) {
+  long long total = 3 * g.nnodes;
+  return (int)std::min<long long>((total + SB - 1) / SB, 148LL * 8);
+}
+
+// storeR: R_{i-1} = x_i - S_{i-1}, and its dot products with the four ring slots.
+template <typename T>
+__global__ void k_acv_store(long long total, int acv_on, void* const* S, void* const* R, const double* u64,
+                            double* partials, const Ctrl* ctrl) {
+  __shared__ double sh[SB / 32];
+  if (ctrl->done) return;
+  const int i = ctrl->i_local;
+  if (i <= 0) return;
+  const T* x = (acv_on == 1) ? (const T*)S[i % 5] : nullptr;
+  const T* sp = (const T*)S[(i - 1) % 5];
+  const int rs = (i - 1) % 4;
+  T* Rn = (T*)R[rs];
+  const T* R0 = (const T*)R[0];
+  const T* R1 = (const T*)R[1];
+  const T* R2 = (const T*)R[2];
+  const T* R3 = (const T*)R[3];
+  double d[4] = {0, 0, 0, 0};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    T xv = (acv_on == 1) ? x[e] : (T)u64[e];
+    T rv = xv - sp[e];
+    Rn[e] = rv;
+    double r = (double)rv;
+    d[0] += r * (double)(rs == 0 ? rv : R0[e]);
+    d[1] += r * (double)(rs == 1 ? rv : R1[e]);
+    d[2] += r * (double)(rs == 2 ? rv : R2[e]);
+    d[3] += r * (double)(rs == 3 ? rv : R3[e]);
+  }
+  for (int k = 0; k < 4; ++k) {
+    double t = block_sum(d[k], sh);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + k] = t;
+  }
+}
+
+template <typename T>
+int launch_acv_store(const GridDev& g, int acv_on, void* const* Sring, void* const* Rring,
+                     const double* u64, double* partials, const Ctrl* ctrl, cudaStream_t s) {
+  long long total = 3 * g.nnodes;
+  k_acv_store<T><<<acv_blocks(g), SB, 0, s>>>(total, acv_on, Sring, Rring, u64, partials, ctrl);
+  return (int)cudaGetLastError();
+}
+
+// accelerate: x_i <- sum_m alpha_m (S_{j_m} + R_{j_m}), j_m = i-4+m.  ACV_P: the Green input
+// becomes p + (x^ - x_i) (increment form); ACV_U: u~ is replaced and S_i = u~ stored.
+template <typename T>
+__global__ void k_acv_accel(long long total, int acv_on, void* const* S, void* const* R, T* gbuf,
+                            double* u64, const Ctrl* ctrl) {
+  if (ctrl->done) return;
+  const int i = ctrl->i_local;
+  const bool acc = ctrl->accel != 0;
+  if (acv_on == 1 && !acc) return;
+  const T *s0 = nullptr, *s1 = nullptr, *s2 = nullptr, *s3 = nullptr;
+  const T *r0 = nullptr, *r1 = nullptr, *r2 = nullptr, *r3 = nullptr;
+  double al[4] = {0, 0, 0, 0};
+  if (acc) {
+    s0 = (const T*)S[(i - 4) % 5]; r0 = (const T*)R[(i - 4) % 4];
+    s1 = (const T*)S[(i - 3) % 5]; r1 = (const T*)R[(i - 3) % 4];
+    s2 = (const T*)S[(i - 2) % 5]; r2 = (const T*)R[(i - 2) % 4];
+    s3 = (const T*)S[(i - 1) % 5]; r3 = (const T*)R[(i - 1) % 4];
+    for (int m = 0; m < 4; ++m) al[m] = ctrl->alpha[m];
+  }
+  T* si = (T*)S[i % 5];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (acv_on == 1) {
+      double xh = al[0] * ((double)s0[e] + (double)r0[e]) + al[1] * ((double)s1[e] + (double)r1[e]) +
+                  al[2] * ((double)s2[e] + (double)r2[e]) + al[3] * ((double)s3[e] + (double)r3[e]);
+      T xo = si[e];
+      T xn = (T)xh;
+      gbuf[e] = (T)((double)gbuf[e] + ((double)xn - (double)xo));
+      si[e] = xn;
+    } else {
+      if (acc) {
+        double v = al[0] * ((double)s0[e] + (double)r0[e]) + al[1] * ((double)s1[e] + (double)r1[e]) +
+                   al[2] * ((double)s2[e] + (double)r2[e]) + al[3] * ((double)s3[e] + (double)r3[e]);
+        u64[e] = v;
+      }
+      si[e] = (T)u64[e];
+    }
+  }
+}
+
+template <typename T>
+int launch_acv_accel(const GridDev& g, int acv_on, void* const* Sring, void* const* Rring, T* gbuf,
+                     double* u64, const Ctrl* ctrl, cudaStream_t s) {
+  long long total = 3 * g.nnodes;
+  k_acv_accel<T><<<acv_blocks(g), SB, 0, s>>>(total, acv_on, Sring, Rring, gbuf, u64, ctrl);
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ control
+// Deterministic reduction of partial sums: fixed strided order + fixed tree.
+__device__ double reduce_fixed(const double* v, int n, int stride, int off, double* sh) {
+  double t = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) t += v[(long long)k * stride + off];
+  double s = block_sum(t, sh);
+  return s;
+}
+
+__global__ void k_ctrl_residual(Ctrl* c, const double* rp, int nres, const double* pp, int nproj,
+                                const double* cp, int ncont, double h, long long nnodes, long long nvox) {
+  __shared__ double sh[SB / 32];
+  if (c->done) return;
+  double s2 = reduce_fixed(rp, nres, 2, 0, sh);
+  double p2 = reduce_fixed(rp, nres, 2, 1, sh);
+  double q2 = (nproj > 0) ? reduce_fixed(pp, nproj, 1, 0, sh) : 0.0;
+  double c2 = 0.0, ng = 0.0, nr = 0.0, mm = 0.0;
+  if (ncont > 0) {
+    c2 = reduce_fixed(cp, ncont, 4, 0, sh);
+    ng = reduce_fixed(cp, ncont, 4, 1, sh);
+    nr = reduce_fixed(cp, ncont, 4, 2, sh);
+    mm = reduce_fixed(cp, ncont, 4, 3, sh);
+  }
+  if (threadIdx.x != 0) return;
+  double pt = p2 + q2 + c2;
+  c->p2 = pt;
+  c->s2 = s2;
+  double pn = sqrt(pt / (double)nnodes), sn = sqrt(s2 / (double)nvox);
+  double r = (sn == 0.0) ? (pn == 0.0 ? 0.0 : INFINITY) : h * pn / sn;
+  c->r = r;
+  if (c->iter == 0) c->r0 = r;
+  if (c->hist_len < HIST) c->hist[c->hist_len++] = r;
+  c->n_vgap = (int)ng;
+  c->n_vreact = (int)nr;
+  c->n_mismatch = (int)mm;
+  c->update = 0;
+  c->changed = 0;
+  const bool sets_empty = (c->n_vgap == 0 && c->n_vreact == 0);
+  if (c->no_stop) return;
+  if (r < c->tol && (!c->contact_on || sets_empty)) { c->done = 1; return; }
+  if (c->iter >= c->max_iter) { c->done = 2; return; }
+  if (!isfinite(r) || (c->r0 > 0.0 && r > 1e6 * c->r0)) { c->done = 3; return; }
+  if (c->contact_on) {
+    if (c->prev_valid && c->n_mismatch == 0 && r < c->update_tol) c->update = 1;
+    c->prev_valid = 1;
+  }
+}
+
+__global__ void k_ctrl_contact(Ctrl* c) {
+  if (c->done) return;
+  if (c->changed > 0) {
+    c->i_local = 0;
+    c->n_updates += 1;
+  }
+}
+
+int launch_ctrl_contact(Ctrl* c, cudaStream_t s) {
+  k_ctrl_contact<<<1, 1, 0, s>>>(c);
+  return (int)cudaGetLastError();
+}
+
+__global__ void k_ctrl_acv(Ctrl* c, const double* partials, int nblk) {
+  __shared__ double sh[SB / 32];
+  if (c->done) return;
+  const int i = c->i_local;
+  double d[4] = {0, 0, 0, 0};
+  if (i > 0)
+    for (int k = 0; k < 4; ++k) d[k] = reduce_fixed(partials, nblk, 4, k, sh);
+  if (threadIdx.x != 0) return;
+  c->accel = 0;
+  if (i > 0) {
+    int s = (i - 1) % 4;
+    for (int k = 0; k < 4; ++k) { c->gram[s][k] = d[k]; c->gram[k][s] = d[k]; }
+  }
+  if (i >= 4 && (i % c->acv_mod) == 0) {
+    double A[4][4], b[4] = {1, 1, 1, 1};
+    double scale = 0.0;
+    for (int r = 0; r < 4; ++r) {
+      for (int q = 0; q < 4; ++q) A[r][q] = c->gram[r][q];
+      scale = fmax(scale, fabs(A[r][r]));
+    }
+    bool ok = scale > 0.0;
+    for (int col = 0; col < 4 && ok; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < 4; ++r)
+        if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+      if (fabs(A[piv][col]) <= 1e-14 * scale) { ok = false; break; }
+      if (piv != col) {
+        for (int q = 0; q < 4; ++q) { double t = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = t; }
+        double t = b[col]; b[col] = b[piv]; b[piv] = t;
+      }
+      for (int r = col + 1; r < 4; ++r) {
+        double m = A[r][col] / A[col][col];
+        for (int q = col; q < 4; ++q) A[r][q] -= m * A[col][q];
+        b[r] -= m * b[col];
+      }
+    }
+    if (ok) {
+      double y[4];
+      for (int r = 3; r >= 0; --r) {
+        double t = b[r];
+        for (int q = r + 1; q < 4; ++q) t -= A[r][q] * y[q];
+        y[r] = t / A[r][r];
+      }
+      double sy = y[0] + y[1] + y[2] + y[3];
+      if (sy != 0.0 && isfinite(sy)) {
+        for (int m = 0; m < 4; ++m) c->alpha[m] = y[(i - 4 + m) % 4] / sy;
+        c->accel = 1;
+        c->n_accel += 1;
+      }
+    }
+  }
+}
+
+int launch_ctrl_acv(Ctrl* c, const double* partials, int nblk, cudaStream_t s) {
+  k_ctrl_acv<<<1, SB, 0, s>>>(c, partials, nblk);
+  return (int)cudaGetLastError();
+}
+
+__global__ void k_ctrl_end(Ctrl* c) {
+  if (c->done) return;
+  c->iter += 1;
+  c->i_local += 1;
+}
+
+int launch_ctrl_end(Ctrl* c, cudaStream_t s) {
+  k_ctrl_end<<<1, 1, 0, s>>>(c);
+  return (int)cudaGetLastError();
+}
+
+// residual control: partial regions of the residual (2 per block), row projection (1 per
+// block) and contact (4 per block) kernels
+int launch_ctrl_residual(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, const double* cp,
+                          int ncont, double h, long long nnodes, long long nvox, cudaStream_t s) {
+  k_ctrl_residual<<<1, SB, 0, s>>>(c, rp, nres, pp, nproj, cp, ncont, h, nnodes, nvox);
+  return (int)cudaGetLastError();
+}
+
+template int launch_proj_P_rows<double>(const GridDev&, const RowsDev&, double*, double*, int, void* const*, double*, const Ctrl*, cudaStream_t);
+template int launch_proj_P_rows<float>(const GridDev&, const RowsDev&, float*, float*, int, void* const*, double*, const Ctrl*, cudaStream_t);
+template int launch_contact_eval<double>(const ContactArgs&, double*, void* const*, int, cudaStream_t);
+template int launch_contact_eval<float>(const ContactArgs&, float*, void* const*, int, cudaStream_t);
+template int launch_acv_store<double>(const GridDev&, int, void* const*, void* const*, const double*, double*, const Ctrl*, cudaStream_t);
+template int launch_acv_store<float>(const GridDev&, int, void* const*, void* const*, const double*, double*, const Ctrl*, cudaStream_t);
+template int launch_acv_accel<double>(const GridDev&, int, void* const*, void* const*, double*, double*, const Ctrl*, cudaStream_t);
+template int launch_acv_accel<float>(const GridDev&, int, void* const*, void* const*, float*, double*, const Ctrl*, cudaStream_t);
+
+}  // namespace dtt

@@ -1,0 +1,109 @@
+// Small utility kernels: precision conversion, float-float split/join, and the stress
+// output at the integration points (Section 3.1.1 gradients, sigma = lambda tr(eps) 1 +
+// 2 mu eps) used by dtt_get_fields.  Not on the iteration path.
+#include "dtt_internal.cuh"
+
+namespace dtt {
+
+template <typename A, typename B>
+__global__ void k_convert(long long n, const A* __restrict__ in, B* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = (B)in[e];
+}
+
+__global__ void k_split(long long n, const double* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    float h, l;
+    ff_set(h, l, in[e]);
+    hi[e] = h;
+    lo[e] = l;
+  }
+}
+
+__global__ void k_join(long long n, const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = (double)hi[e] + (double)lo[e];
+}
+
+static int nblk(long long n) { return (int)std::min<long long>((n + 255) / 256, 148LL * 16); }
+
+int launch_to_double(long long n, const void* in, int in_is_float, double* out, cudaStream_t s) {
+  if (in_is_float) k_convert<float, double><<<nblk(n), 256, 0, s>>>(n, (const float*)in, out);
+  else k_convert<double, double><<<nblk(n), 256, 0, s>>>(n, (const double*)in, out);
+  return (int)cudaGetLastError();
+}
+int launch_from_double(long long n, const double* in, void* out, int out_is_float, cudaStream_t s) {
+  if (out_is_float) k_convert<double, float><<<nblk(n), 256, 0, s>>>(n, in, (float*)out);
+  else k_convert<double, double><<<nblk(n), 256, 0, s>>>(n, in, (double*)out);
+  return (int)cudaGetLastError();
+}
+int launch_split(long long n, const double* in, float* hi, float* lo, cudaStream_t s) {
+  k_split<<<nblk(n), 256, 0, s>>>(n, in, hi, lo);
+  return (int)cudaGetLastError();
+}
+int launch_join(long long n, const float* hi, const float* lo, double* out, cudaStream_t s) {
+  k_join<<<nblk(n), 256, 0, s>>>(n, hi, lo, out);
+  return (int)cudaGetLastError();
+}
+
+// sigma at every integration point from a float64 u~ (3 x nnodes).
+__global__ void k_stress_out(const GridDev g, const double* __restrict__ u, const uint8_t* __restrict__ phase,
+                             const double* __restrict__ lam, const double* __restrict__ mu, const double eps00,
+                             const double eps11, const double eps22, const double eps12, const double eps02,
+                             const double eps01, double* __restrict__ out) {
+  const long long NV = (long long)g.nvox[0] * g.nvox[1] * g.nvox[2];
+  const int nip = g.scheme == SCHEME_TETRA2 ? 2 : 1;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < NV; v += (long long)gridDim.x * blockDim.x) {
+    int vx = (int)(v % g.nvox[0]);
+    long long r = v / g.nvox[0];
+    int vy = (int)(r % g.nvox[1]);
+    int vz = (int)(r / g.nvox[1]);
+    double U[3][8];
+    for (int q = 0; q < 8; ++q) {
+      int dx = q & 1, dy = (q >> 1) & 1, dz = (q >> 2) & 1;
+      int i = (vx + dx) % g.nn[0], j = (vy + dy) % g.nn[1], k = (vz + dz) % g.nn[2];
+      long long n = i + (long long)g.nn[0] * (j + (long long)g.nn[1] * k);
+      for (int c = 0; c < 3; ++c) U[c][q] = u[(long long)c * g.nnodes + n];
+    }
+    double L = lam[phase[v]], M = mu[phase[v]];
+    for (int t = 0; t < nip; ++t) {
+      double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      for (int q = 0; q < 8; ++q) {
+        int dx = q & 1, dy = (q >> 1) & 1, dz = (q >> 2) & 1;
+        double coef;
+        if (nip == 2) {
+          if (((dx + dy + dz) & 1) != t) continue;
+          coef = 1.0 / (2.0 * g.h);
+        } else {
+          coef = 1.0 / (4.0 * g.h);
+        }
+        double s[3] = {dx ? 1.0 : -1.0, dy ? 1.0 : -1.0, dz ? 1.0 : -1.0};
+        for (int c = 0; c < 3; ++c)
+          for (int d = 0; d < 3; ++d) G[c][d] += coef * s[d] * U[c][q];
+      }
+      double exx = eps00 + G[0][0], eyy = eps11 + G[1][1], ezz = eps22 + G[2][2];
+      double eyz = eps12 + 0.5 * (G[1][2] + G[2][1]);
+      double exz = eps02 + 0.5 * (G[0][2] + G[2][0]);
+      double exy = eps01 + 0.5 * (G[0][1] + G[1][0]);
+      double tr = exx + eyy + ezz;
+      double* o = out + (v * nip + t) * 6;
+      o[0] = L * tr + 2 * M * exx;
+      o[1] = L * tr + 2 * M * eyy;
+      o[2] = L * tr + 2 * M * ezz;
+      o[3] = 2 * M * eyz;
+      o[4] = 2 * M * exz;
+      o[5] = 2 * M * exy;
+    }
+  }
+}
+
+int launch_stress_out(const GridDev& g, const double* u, const uint8_t* phase, const double* lam,
+                      const double* mu, const double eps[3][3], double* out, cudaStream_t s) {
+  long long NV = (long long)g.nvox[0] * g.nvox[1] * g.nvox[2];
+  k_stress_out<<<nblk(NV), 256, 0, s>>>(g, u, phase, lam, mu, eps[0][0], eps[1][1], eps[2][2],
+                                        0.5 * (eps[1][2] + eps[2][1]), 0.5 * (eps[0][2] + eps[2][0]),
+                                        0.5 * (eps[0][1] + eps[1][0]), out);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace dtt

@@ -1,0 +1,298 @@
+"""GPU parity: the CUDA path (through the C ABI) against the float64 oracle on the same
+seeded inputs.
+
+Tolerances: FP64 path <= 1e-11 relative (transforms, Green step, residual operator,
+plain fixed-iteration solves); Anderson-accelerated fixed-iteration runs 1e-9 (the Gram
+solve amplifies summation-order differences); mixed path: operators at float32 rounding
+(2e-6 relative to the field scale), converged solutions (residual 2e-7, near the float32
+stress floor) within 2e-6 relative L2 of the oracle converged to 1e-12.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import constraints as ocs, discrete as odz, solver as osv, transforms as otr
+from tests.helpers import gpu_grid, oracle_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2607_26082_b300 import dtt  # noqa: E402
+
+FP64, MIXED = dtt.PREC_FP64, dtt.PREC_MIXED
+
+
+def _spec(seed, nvox=None, scheme=wl.TETRA2, periodic_prob=0.25, **kw):
+    if kw.get("anchored", True) is False:
+        # operator tests: any BC mix, no constraint rows
+        kw.update(n_strong=0, n_weak=0, n_smooth=0, n_tie=0)
+    return wl.random_problem(seed, nvox=nvox, scheme=scheme, periodic_prob=periodic_prob, **kw)
+
+
+def _oracle_forward_real(pb, c, x):
+    """Forward transform of component c with the oracle's per-type matrices, axis by
+    axis; a periodic axis is turned from the oracle's complex DFT into the real Hartley
+    spectrum by H = Re(X) - Im(X) (exact along one axis for real data)."""
+    y = np.asarray(x, dtype=np.float64)
+    for d, ax in ((0, 2), (1, 1), (2, 0)):
+        t = pb.types[c][d]
+        Y = otr.apply_along(otr.forward_matrix(t, pb.nvox[d]), y, ax)
+        if t == otr.DFT:
+            Y = Y.real - Y.imag
+        # place spectral index k at position k of the node axis
+        sel, kidx, _ = otr.selection(t, pb.nvox[d])
+        full_shape = list(Y.shape)
+        full_shape[ax] = pb.nn[d]
+        Z = np.zeros(full_shape)
+        idx = [slice(None)] * 3
+        idx[ax] = kidx
+        Z[tuple(idx)] = Y
+        y = Z
+    return y
+
+
+# ----------------------------------------------------------------------------- transforms
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("nvox", [(5, 4, 6), (33, 7, 18), (70, 9, 35)])
+def test_transform_forward_fp64(seed, nvox):
+    spec = _spec(seed, nvox=nvox, periodic_prob=0.3, anchored=False)
+    pb, _ = oracle_problem(spec)
+    g = gpu_grid(spec, FP64)
+    rng = np.random.default_rng(seed)
+    for c in range(3):
+        x = rng.standard_normal(pb.node_shape) * pb.dof_mask(c)
+        got = g.dtt_transform(c, 0, x)
+        ref = _oracle_forward_real(pb, c, x)
+        assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+        back = g.dtt_transform(c, 1, got)
+        assert np.abs(back - x).max() <= 1e-12 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_transform_mixed(seed):
+    spec = _spec(seed, nvox=(33, 7, 18), periodic_prob=0.3, anchored=False)
+    pb, _ = oracle_problem(spec)
+    g = gpu_grid(spec, MIXED)
+    x = np.random.default_rng(seed).standard_normal(pb.node_shape) * pb.dof_mask(1)
+    got = g.dtt_transform(1, 0, x)
+    ref = _oracle_forward_real(pb, 1, x)
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+# ----------------------------------------------------------------------------- Green step
+@pytest.mark.parametrize("scheme", [wl.TETRA2, wl.HEX1])
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-11), (MIXED, 2e-6)])
+def test_green_step(scheme, seed, prec, tol):
+    spec = _spec(seed, nvox=(37, 10, 19), scheme=scheme, periodic_prob=0.3, anchored=False)
+    pb, _ = oracle_problem(spec)
+    g = gpu_grid(spec, prec)
+    rng = np.random.default_rng(10 + seed)
+    pt = rng.standard_normal((3,) + pb.node_shape)
+    for c in range(3):
+        pt[c][~pb.dof_mask(c)] = 0.0
+    ref = odz.green_apply(pb, pt, spec["lam0"], spec["mu0"])
+    got = g.dtt_apply_green(pt)
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+
+
+# ----------------------------------------------------------------------------- residual
+@pytest.mark.parametrize("scheme", [wl.TETRA2, wl.HEX1])
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("nvox", [(2, 2, 2), (31, 5, 17), (67, 9, 40)])
+def test_residual_operator_fp64(scheme, seed, nvox):
+    spec = _spec(seed, nvox=nvox, scheme=scheme, periodic_prob=0.3, anchored=False)
+    pb, _ = oracle_problem(spec)
+    g = gpu_grid(spec, FP64)
+    u = 1e-2 * np.random.default_rng(seed).standard_normal((3,) + pb.node_shape)
+    for c in range(3):
+        u[c][~pb.dof_mask(c)] = 0.0
+    p_ref, sig = odz.residual(pb, u)
+    a0 = odz.apply_A0(pb, u, spec["lam0"], spec["mu0"])
+    p, pt, norms = g.dtt_apply_residual(u)
+    scale = max(np.abs(p_ref).max(), np.abs(a0).max())
+    assert np.abs(p - p_ref).max() <= 1e-11 * scale
+    assert np.abs(pt - (p_ref + a0)).max() <= 1e-11 * scale
+    w = np.array([ip[0] for ip in pb.ip_sets()])
+    s2 = np.sum(w[:, None, None, None, None, None] * sig * sig)
+    assert abs(norms[0] - s2) <= 1e-11 * s2
+    assert abs(norms[1] - np.sum(p_ref ** 2)) <= 1e-10 * np.sum(p_ref ** 2)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_residual_operator_mixed(seed):
+    spec = _spec(seed, nvox=(40, 6, 21))
+    pb, _ = oracle_problem(spec)
+    g = gpu_grid(spec, MIXED)
+    u = 1e-2 * np.random.default_rng(seed).standard_normal((3,) + pb.node_shape)
+    for c in range(3):
+        u[c][~pb.dof_mask(c)] = 0.0
+    p_ref, sig = odz.residual(pb, u)
+    p, pt, norms = g.dtt_apply_residual(u)
+    scale = np.abs(sig).max() / pb.h
+    assert np.abs(p - p_ref).max() <= 2e-6 * scale
+
+
+def test_residual_mixed_keeps_small_differences():
+    """A large smooth u~ plus a tiny perturbation: the float-float u~ keeps the strain of
+    the perturbation (a plain float32 u~ would lose it)."""
+    spec = _spec(3, nvox=(24, 8, 12), eps_scale=0.0)
+    pb, _ = oracle_problem(spec)
+    g = gpu_grid(spec, MIXED)
+    X = pb.node_positions()
+    u = np.stack([1e3 + 0.0 * X[0], -2e3 + 0.0 * X[1], 5e2 + 0.0 * X[2]])
+    u = u + 1e-6 * np.random.default_rng(0).standard_normal(u.shape)
+    for c in range(3):
+        u[c][~pb.dof_mask(c)] = 0.0
+    p_ref, sig = odz.residual(pb, u)
+    p, _, _ = g.dtt_apply_residual(u)
+    inner = np.ones(pb.node_shape, bool)
+    # compare away from the Dirichlet jump of the constant field
+    for c in range(3):
+        m = pb.dof_mask(c)
+        inner &= m
+    d = np.abs(p - p_ref)[:, inner].max()
+    assert d <= 1e-3 * np.abs(p_ref[:, inner]).max()
+
+
+# ----------------------------------------------------------------------------- solver
+@pytest.mark.parametrize("seed", range(6))
+def test_fixed_iterations_plain_fp64(seed):
+    """Plain fixed point (no acceleration), same number of Green steps on both sides:
+    iterate-for-iterate parity at the FP64 bound."""
+    spec = _spec(seed, nvox=(9, 6, 7), scheme=wl.TETRA2 if seed % 2 == 0 else wl.HEX1,
+                 n_smooth=1 if seed % 2 == 0 else 0)
+    pb, rows = oracle_problem(spec)
+    K = 25
+    ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 0.0, K, acv=False)
+    g = gpu_grid(spec, FP64)
+    rep = g.dtt_solve_step(0.0, K, acv_mod=0)
+    assert rep.iterations == K and rep.accelerations == 0
+    assert rel_l2(g.dtt_get_fields(), ref.u) <= 1e-11
+    hist = g.dtt_get_history()
+    assert np.allclose(hist, ref.history, rtol=1e-11, atol=1e-13 * ref.history[0])
+    per, tot = g.dtt_get_reactions(len(rows))
+    assert np.abs(per - ref.reactions).max() <= 1e-11 * max(np.abs(ref.reactions).max(), 1e-30)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("acv_on", [dtt.ACV_P, dtt.ACV_U])
+def test_fixed_iterations_accelerated_fp64(seed, acv_on):
+    """Anderson-accelerated runs, same number of Green steps.  The 4x4 Gram solve
+    amplifies last-bit differences of summation order (its condition number reaches
+    ~1e7 late in a run), so iterate-for-iterate agreement is held at 1e-9."""
+    spec = _spec(seed, nvox=(9, 6, 7), scheme=wl.TETRA2 if seed % 2 == 0 else wl.HEX1,
+                 n_smooth=1 if seed % 2 == 0 else 0)
+    pb, rows = oracle_problem(spec)
+    K = 25
+    ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 0.0, K, acv_on="P" if acv_on else "U", acv_mod=2)
+    g = gpu_grid(spec, FP64)
+    rep = g.dtt_solve_step(0.0, K, acv_mod=2, acv_on=acv_on)
+    assert rep.iterations == K
+    assert rep.accelerations == ref.accelerations
+    assert rel_l2(g.dtt_get_fields(), ref.u) <= 1e-9
+    hist = g.dtt_get_history()
+    assert np.allclose(hist, ref.history, rtol=1e-7, atol=1e-9 * ref.history[0])
+
+
+@pytest.mark.parametrize("prec,tol_u", [(FP64, 1e-10), (MIXED, 2e-6)])
+def test_cube16_converged(prec, tol_u):
+    """16^3 cube, half-clamped bottom, 5 pinned interior nodes, top u_z = -0.01."""
+    spec = wl.cube16()
+    pb, rows = oracle_problem(spec)
+    ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 1e-12, 3000, acv_mod=3)
+    g = gpu_grid(spec, prec)
+    rep = g.dtt_solve_step(1e-12 if prec == FP64 else 2e-7, 3000, acv_mod=3)
+    assert rep.status == dtt.OK
+    u, sig = g.dtt_get_fields(sigma=True)
+    assert rel_l2(u, ref.u) <= tol_u
+    sref = np.moveaxis(ref.sigma, (0, 1, 2), (3, 4, 5))   # (vox..., ip, 3, 3)
+    s6 = np.stack([sref[..., 0, 0], sref[..., 1, 1], sref[..., 2, 2], sref[..., 1, 2], sref[..., 0, 2],
+                   sref[..., 0, 1]], axis=-1)
+    assert rel_l2(sig, s6) <= 10 * tol_u
+    per, tot = g.dtt_get_reactions(len(rows))
+    assert rel_l2(per, ref.reactions) <= 10 * tol_u
+    assert np.abs(tot - ref.total_reaction).max() <= 10 * tol_u * np.abs(ref.total_reaction).max()
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_random_problems_converged(prec):
+    for seed in range(4):
+        spec = _spec(seed, nvox=(11, 8, 9))
+        pb, rows = oracle_problem(spec)
+        ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 1e-12, 3000)
+        g = gpu_grid(spec, prec)
+        rep = g.dtt_solve_step(1e-12 if prec == FP64 else 2e-7, 3000)
+        assert rep.status == dtt.OK, (seed, rep.as_dict())
+        assert rel_l2(g.dtt_get_fields(), ref.u) <= (1e-10 if prec == FP64 else 2e-6)
+
+
+# ----------------------------------------------------------------------------- contact
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_contact_increments(prec):
+    w = wl.indentation(16, 16, 8, R=6.0, steps=2, dmin=0.01, dmax=0.05)
+    pb, _ = oracle_problem(w)
+    I = w.indenter
+    g = gpu_grid(w, prec)
+    u_ref = np.zeros((3,) + pb.node_shape)
+    g.dtt_set_indenter(I["axis"], I["face"], I["centers"][0], I["radius"])
+    for step, O in enumerate(I["centers"]):
+        ind = ocs.Indenter(pb, I["axis"], I["face"], O, I["radius"])
+        ref = osv.solve_alg2_increment(pb, ind, [], w.lam0, w.mu0, 1e-10, 2000, u_ref)
+        u_ref = ref.u
+        g.dtt_move_indenter(O)
+        rep = g.dtt_solve_step(1e-10 if prec == FP64 else 1e-7, 2000, acv_mod=3,
+                               init=dtt.INIT_PREVIOUS if step else dtt.INIT_ZERO)
+        assert rep.status == dtt.OK, rep.as_dict()
+        act, gap, fn, force = g.dtt_get_contact()
+        if prec == FP64:
+            assert np.array_equal(act, ref.active)
+            assert rel_l2(g.dtt_get_fields(), ref.u) <= 1e-9
+            assert np.abs(force - ref.force).max() <= 1e-8 * np.abs(ref.force).max()
+        else:
+            tie = np.abs(ref.gap) < 1e-8 * I["radius"]
+            assert np.array_equal(act[~tie], ref.active[~tie])
+            assert rel_l2(g.dtt_get_fields(), ref.u) <= 1e-5
+            assert np.abs(force - ref.force).max() <= 1e-5 * np.abs(ref.force).max()
+
+
+# ----------------------------------------------------------------------------- errors
+def test_error_statuses():
+    bc = np.full((3, 2, 3), wl.N)
+    bc[0, 0, :] = wl.P    # periodic on one face only
+    with pytest.raises(dtt.DttError) as e:
+        dtt.Grid((4, 4, 4), 1.0, bc)
+    assert e.value.status == dtt.ERR_BC
+    bc = np.full((3, 2, 3), wl.N)
+    g = dtt.Grid((4, 4, 4), 1.0, bc)
+    with pytest.raises(dtt.DttError) as e:
+        g.dtt_solve_step(1e-6, 10)
+    assert e.value.status == dtt.ERR_STATE
+    # all-Neumann component with a constraint: null modes
+    with pytest.raises(dtt.DttError) as e:
+        g.dtt_set_constraints([0, 1], [7], [0], [1.0], None, [0.0])
+    assert e.value.status == dtt.ERR_NULLMODE
+    bc[0, 0, :] = wl.D
+    bc[1, 0, :] = wl.D
+    g = dtt.Grid((4, 4, 4), 1.0, bc)
+    with pytest.raises(dtt.DttError) as e:       # overlapping rows
+        g.dtt_set_constraints([0, 1, 2], [31, 31], [0, 0], [1.0, 1.0], None, [0.0, 0.0])
+    assert e.value.status == dtt.ERR_OVERLAP
+    with pytest.raises(dtt.DttError) as e:       # Dirichlet-face DOF (node 0 is on x = 0)
+        g.dtt_set_constraints([0, 1], [0], [0], [1.0], None, [0.0])
+    assert e.value.status == dtt.ERR_ARG
+    with pytest.raises(dtt.DttError) as e:
+        g.dtt_set_material(np.zeros(64, np.uint8) + 3, [1.0], [1.0])
+    assert e.value.status == dtt.ERR_ARG
+
+
+def test_not_converged_keeps_iterate():
+    spec = _spec(1, nvox=(8, 8, 8))
+    g = gpu_grid(spec, FP64)
+    rep = g.dtt_solve_step(1e-30, 5)
+    assert rep.status == dtt.ERR_NOT_CONVERGED and rep.iterations == 5
+    u = g.dtt_get_fields()
+    assert np.isfinite(u).all() and np.abs(u).max() > 0
