@@ -141,12 +141,14 @@ def cpu_threads():
 
 # ------------------------------------------------------------------ GPU arm
 def launches_per_iteration(has_rows, has_contact, acv):
+    """Kernel launches of one captured iteration (every launch runs; after convergence they
+    return at once)."""
     n = 1                      # residual
     n += 1 if has_rows else 0  # proj_P
     n += 1 if has_contact else 0
     n += 1                     # ctrl residual
     n += 2 if has_contact else 0
-    n += 3 if acv else 0       # store, ctrl, accel
+    n += 3 if acv else 0       # Gram row, ctrl (alpha), Green input
     n += 8                     # 3 forward passes, Green, 3 inverse passes, increment
     n += 1 if has_rows else 0  # proj_U
     n += 1 if has_contact else 0
@@ -174,6 +176,9 @@ def run_ours(args, rank, world, local):
         return g.dtt_solve_step(tol, max_iter, acv_mod=spec["acv_mod"], acv_on=dtt.ACV_P, init=dtt.INIT_ZERO,
                                 graph_iters=16)
 
+    def launches_per_solve(iters):
+        return ((iters + graph_iters) // graph_iters) * graph_iters * per_it + 1
+
     graph_iters = 16
     per_it = launches_per_iteration(True, False, True)
 
@@ -192,7 +197,7 @@ def run_ours(args, rank, world, local):
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
             iters.append(rep.iterations)
-            launches += ((rep.iterations + graph_iters) // graph_iters) * graph_iters * per_it + 1
+            launches += launches_per_solve(rep.iterations)
             if rep.status != dtt.OK:
                 raise RuntimeError("solve did not converge: %s" % rep.as_dict())
         return times, iters, rep, launches
@@ -220,10 +225,14 @@ def run_ours(args, rank, world, local):
     # ---- kernel-group profile of the mixed iteration (roofline of the dominant group)
     prof = gm.dtt_profile_iteration(20, acv_mod=spec["acv_mod"])
     nn = gm.n_nodes
-    alg_bytes = {"residual": nn * (24 + 12 + 12) + nv, "projections": 0, "anderson": nn * 72,
-                 "forward_dt": nn * 72, "green": nn * 24, "inverse_dt": nn * 72, "increment": nn * 60}
+    # algorithmic bytes of one launch group per iteration (mixed path: T = 4 B fields, u~ as
+    # an 8-byte float-float pair, phase ids 1 B per voxel)
+    alg_bytes = {"residual": nn * (24 + 12 + 12 + 12 + 12) + nv,   # u~, step, g_(i-1) in; p, R out
+                 "projections": 0, "anderson": nn * (48 + 78),      # Gram (4 R), Green input (avg)
+                 "forward_dt": nn * 72, "green": nn * 24, "inverse_dt": nn * 72,
+                 "increment": nn * 72}
     launches_in_group = {"residual": 1, "forward_dt": 3, "inverse_dt": 3, "green": 1, "increment": 1,
-                         "anderson": 1, "projections": 4}
+                         "anderson": 3, "projections": 4}
     dom = max(prof, key=lambda k: prof[k])
     peaks = {}
     try:
@@ -274,7 +283,8 @@ def run_ours(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 transforms/stress, "
         "float-float u~, FP64 norms/Gram/multipliers)", "data": "synthetic",
-        "config": {"workload": spec["name"] + ", TETRA2, tol 1e-6, ACV_P mod 2, zero start",
+        "config": {"workload": spec["name"] + ", E=210, nu=0.3, TETRA2, R0=(lambda,mu), tol 1e-6, "
+                                "ACV_P mod 2, zero start",
                    "voxels": nv, "nodes": nn, "iterations_per_solve": int(statistics.median(iters)),
                    "time_to_residual_1e-6_ms": 1e3 * tot_t / len(times),
                    "l2": "flushed (512 MB write) before every timed solve", "parallelism": "replicas"},

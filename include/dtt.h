@@ -124,6 +124,8 @@ typedef struct {
                           dtt_set_initial) */
   double update_tol;   /* contact-zone update threshold on the residual (paper: 1e-2) */
   int32_t graph_iters; /* iterations per captured CUDA-graph launch (0: default 8) */
+  double acv_pivot;    /* Anderson is skipped when a pivot of the 4x4 Gram elimination is
+                          <= acv_pivot * max_k G_kk (0: default, 1e-14) */
 } dtt_solve_opts;
 
 typedef struct {

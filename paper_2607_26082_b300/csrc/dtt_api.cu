@@ -75,12 +75,19 @@ struct dtt_grid {
   double* u64 = nullptr;
   float* uhi = nullptr;
   float* ulo = nullptr;
+  // Anderson rings (T fields): A = p ring (ACV on p~, slots 0..3) or u~-copy ring (ACV on
+  // u~, slots 0..4); Gr = Green-input ring (ACV on p~) whose slot 0 is the Green input
+  // otherwise; R = Anderson residual ring.  step = last full step of u~.
   void* S[5]{};
   void* R[4]{};
-  void* gbuf = nullptr;
+  void* Gr[4]{};
+  void* step = nullptr;
+  void* gbuf = nullptr;    // = Gr[0]
   void* spec = nullptr;
+  void* spec2 = nullptr;
   void** d_Sring = nullptr;
   void** d_Rring = nullptr;
+  void** d_Gring = nullptr;
 
   // material
   uint8_t* phase = nullptr;
@@ -95,7 +102,8 @@ struct dtt_grid {
   // transforms
   void* fwd[3][3]{};
   void* inv[3][3]{};
-  double* cosq[3][3]{};
+  double* sin2q[3][3]{};
+  double* cos2q[3][3]{};
 
   // constraints (host copy + device CSR)
   int nrows = 0;
@@ -157,16 +165,19 @@ int ttype(int b0, int b1) {
 
 // Transform matrices of one axis: F (spectral k, node j) and B (node j, spectral k), both
 // nn x nn with zero rows/columns outside the selection (Section 3.2.2, Table 3), plus
-// cos(q_k) at every spectral position (1 where unused).
-void build_axis(int type, int n, int nn, std::vector<double>& F, std::vector<double>& B, std::vector<double>& cq) {
+// sin^2(q_k / 2) at every spectral position (0 where unused).
+void build_axis(int type, int n, int nn, std::vector<double>& F, std::vector<double>& B, std::vector<double>& cq,
+                std::vector<double>& cc) {
   F.assign((size_t)nn * nn, 0.0);
   B.assign((size_t)nn * nn, 0.0);
-  cq.assign(nn, 1.0);
+  cq.assign(nn, 0.0);
+  cc.assign(nn, 1.0);
   const double pi = 3.14159265358979323846;
   switch (type) {
     case T_DCT1:
       for (int k = 0; k <= n; ++k) {
-        cq[k] = std::cos(pi * k / n);
+        cq[k] = std::pow(std::sin(0.5 * pi * k / n), 2);
+        cc[k] = std::pow(std::cos(0.5 * pi * k / n), 2);
         for (int j = 0; j <= n; ++j) {
           double c = std::cos(pi * (double)j * k / n);
           double wj = (j == 0 || j == n) ? 0.5 : 1.0;
@@ -178,7 +189,8 @@ void build_axis(int type, int n, int nn, std::vector<double>& F, std::vector<dou
       break;
     case T_DCT3:
       for (int k = 0; k < n; ++k) {
-        cq[k] = std::cos(pi * (2.0 * k + 1.0) / (2.0 * n));
+        cq[k] = std::pow(std::sin(0.5 * pi * (2.0 * k + 1.0) / (2.0 * n)), 2);
+        cc[k] = std::pow(std::cos(0.5 * pi * (2.0 * k + 1.0) / (2.0 * n)), 2);
         for (int j = 0; j < n; ++j) {
           double c = std::cos(pi * j * (2.0 * k + 1.0) / (2.0 * n));
           F[(size_t)k * nn + j] = (j == 0 ? 0.5 : 1.0) * c;
@@ -188,7 +200,8 @@ void build_axis(int type, int n, int nn, std::vector<double>& F, std::vector<dou
       break;
     case T_DST1:
       for (int k = 1; k < n; ++k) {
-        cq[k] = std::cos(pi * k / n);
+        cq[k] = std::pow(std::sin(0.5 * pi * k / n), 2);
+        cc[k] = std::pow(std::cos(0.5 * pi * k / n), 2);
         for (int j = 1; j < n; ++j) {
           double sv = std::sin(pi * (double)j * k / n);
           F[(size_t)k * nn + j] = sv;
@@ -198,7 +211,8 @@ void build_axis(int type, int n, int nn, std::vector<double>& F, std::vector<dou
       break;
     case T_DST3:
       for (int k = 0; k < n; ++k) {
-        cq[k] = std::cos(pi * (2.0 * k + 1.0) / (2.0 * n));
+        cq[k] = std::pow(std::sin(0.5 * pi * (2.0 * k + 1.0) / (2.0 * n)), 2);
+        cc[k] = std::pow(std::cos(0.5 * pi * (2.0 * k + 1.0) / (2.0 * n)), 2);
         for (int j = 1; j <= n; ++j) {
           double sv = std::sin(pi * j * (2.0 * k + 1.0) / (2.0 * n));
           F[(size_t)k * nn + j] = (j == n ? 0.5 : 1.0) * sv;
@@ -208,7 +222,8 @@ void build_axis(int type, int n, int nn, std::vector<double>& F, std::vector<dou
       break;
     case T_DHT:
       for (int k = 0; k < n; ++k) {
-        cq[k] = std::cos(2.0 * pi * k / n);
+        cq[k] = std::pow(std::sin(pi * (double)k / n), 2);
+        cc[k] = std::pow(std::cos(pi * (double)k / n), 2);
         for (int j = 0; j < n; ++j) {
           double th = 2.0 * pi * (double)((long long)j * k % n) / n;
           double cas = std::cos(th) + std::sin(th);
@@ -354,7 +369,8 @@ TransformTables tables(dtt_grid* G) {
     for (int d = 0; d < 3; ++d) {
       t.fwd[c][d] = G->fwd[c][d];
       t.inv[c][d] = G->inv[c][d];
-      t.cosq[c][d] = G->cosq[c][d];
+      t.sin2q[c][d] = G->sin2q[c][d];
+      t.cos2q[c][d] = G->cos2q[c][d];
     }
   t.lam0 = G->lam0;
   t.mu0 = G->mu0;
@@ -372,30 +388,39 @@ inline void prof_mark(int k, cudaStream_t s) {
   if (g_prof_ev) cudaEventRecord(g_prof_ev[k], s);
 }
 
+// Green step (forward DT, Green multiply, inverse DT) of `in` (or of the ring slot
+// i % 4 when in_ring is given); the result lands in out.  With `increment` the result is
+// added to u~ and stored as the step.
 template <typename T>
-dtt_status enqueue_green(dtt_grid* G, T* in_out, T* tmp, bool increment, const Ctrl* ctrl, int comp0, int ncomp) {
+dtt_status enqueue_green(dtt_grid* G, const T* in, void* const* in_ring, T* out, T* tmp, bool increment,
+                         const Ctrl* ctrl, int comp0, int ncomp) {
   TransformTables tt = tables(G);
   cudaStream_t s = G->stream;
-  // forward x, y, z ; Green ; inverse z, y, x  (ping-pong in_out <-> tmp)
-  CKL(launch_transform_axis<T>(G->g, in_out, tmp, tt, 0, 0, comp0, ncomp, ctrl, s));
-  CKL(launch_transform_axis<T>(G->g, tmp, in_out, tt, 1, 0, comp0, ncomp, ctrl, s));
-  CKL(launch_transform_axis<T>(G->g, in_out, tmp, tt, 2, 0, comp0, ncomp, ctrl, s));
+  CKL(launch_transform_axis<T>(G->g, in, tmp, tt, 0, 0, comp0, ncomp, ctrl, s, in_ring));
+  CKL(launch_transform_axis<T>(G->g, tmp, out, tt, 1, 0, comp0, ncomp, ctrl, s));
+  CKL(launch_transform_axis<T>(G->g, out, tmp, tt, 2, 0, comp0, ncomp, ctrl, s));
   prof_mark(4, s);
   CKL(launch_green_multiply<T>(G->g, tmp, tt, G->g.scheme, ctrl, s));
   prof_mark(5, s);
-  CKL(launch_transform_axis<T>(G->g, tmp, in_out, tt, 2, 1, comp0, ncomp, ctrl, s));
-  CKL(launch_transform_axis<T>(G->g, in_out, tmp, tt, 1, 1, comp0, ncomp, ctrl, s));
-  CKL(launch_transform_axis<T>(G->g, tmp, in_out, tt, 0, 1, comp0, ncomp, ctrl, s));
+  CKL(launch_transform_axis<T>(G->g, tmp, out, tt, 2, 1, comp0, ncomp, ctrl, s));
+  CKL(launch_transform_axis<T>(G->g, out, tmp, tt, 1, 1, comp0, ncomp, ctrl, s));
+  CKL(launch_transform_axis<T>(G->g, tmp, out, tt, 0, 1, comp0, ncomp, ctrl, s));
   prof_mark(6, s);
-  if (increment) CKL(launch_add_increment<T>(G->g, in_out, G->u64, G->uhi, G->ulo, ctrl, s));
+  if (increment) CKL(launch_add_increment<T>(G->g, out, G->u64, G->uhi, G->ulo, (T*)G->step, ctrl, s));
   return DTT_OK;
 }
 
+// One iteration of Algorithm 1 / Algorithm 2 as a fixed launch sequence.
+//   ACV on p~ (difference form): residual (p_i, R_{i-1}) -> proj_P -> contact -> control ->
+//     Gram row -> alpha -> Green input g_i -> Green step (u~ += G g_i, step) -> proj_U.
+//   ACV on u~ (FP64): R_{i-1} = u~_i - S_{i-1}, alpha, u~ <- combination, S_i = u~, then
+//     residual (p_i) -> ... -> Green step on p_i.
 template <typename T>
 dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
   cudaStream_t s = G->stream;
   PartRegions pr = regions(G);
   Ctrl* ctrl = G->d_ctrl;
+  const bool diff = acv && acv_on == DTT_ACV_P;
   prof_mark(0, s);
   if (acv && acv_on == DTT_ACV_U) {
     CKL(launch_acv_store<T>(G->g, 0, G->d_Sring, G->d_Rring, G->u64, pr.acv, ctrl, s));
@@ -415,18 +440,23 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
   std::memcpy(ra.eps, G->eps, sizeof(ra.eps));
   ra.lam0 = G->lam0;
   ra.mu0 = G->mu0;
-  ra.xout = nullptr;
+  ra.mode = diff ? 1 : 2;
   ra.pout = G->gbuf;
+  ra.dfield = G->step;
+  for (int k = 0; k < 4; ++k) {
+    ra.pring[k] = G->S[k];
+    ra.gring[k] = G->Gr[k];
+    ra.rring[k] = G->R[k];
+  }
   ra.partials = pr.res;
   ra.ctrl = ctrl;
-  for (int k = 0; k < 5; ++k) ra.ring[k] = G->S[k];
-  ra.write_x_ring = (acv && acv_on == DTT_ACV_P) ? 1 : 0;
   CKL(launch_residual<T>(ra, s));
   prof_mark(1, s);
-  const int xr = ra.write_x_ring;
-  if (G->nrows > 0) CKL(launch_proj_P_rows<T>(G->g, rows_dev(G), (T*)G->gbuf, nullptr, xr, G->d_Sring, pr.proj, ctrl, s));
+  const int rm = diff ? 1 : 0;
+  if (G->nrows > 0)
+    CKL(launch_proj_P_rows<T>(G->g, rows_dev(G), (T*)G->gbuf, G->d_Sring, G->d_Rring, rm, pr.proj, ctrl, s));
   ContactArgs ca = contact_args(G, pr.cont);
-  if (G->contact) CKL(launch_contact_eval<T>(ca, (T*)G->gbuf, G->d_Sring, xr, s));
+  if (G->contact) CKL(launch_contact_eval<T>(ca, (T*)G->gbuf, G->d_Sring, G->d_Rring, rm, s));
   CKL(launch_ctrl_residual(ctrl, pr.res, pr.nres, pr.proj, G->nrows > 0 ? pr.nproj : 0, pr.cont, pr.ncont, G->g.h,
                            G->NN, G->NV, s));
   if (G->contact) {
@@ -434,17 +464,18 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
     CKL(launch_ctrl_contact(ctrl, s));
   }
   prof_mark(2, s);
-  if (acv && acv_on == DTT_ACV_P) {
-    CKL(launch_acv_store<T>(G->g, 1, G->d_Sring, G->d_Rring, G->u64, pr.acv, ctrl, s));
+  if (diff) {
+    CKL(launch_acv_gram<T>(G->g, G->d_Rring, pr.acv, ctrl, s));
     CKL(launch_ctrl_acv(ctrl, pr.acv, pr.nacv, s));
-    CKL(launch_acv_accel<T>(G->g, 1, G->d_Sring, G->d_Rring, (T*)G->gbuf, G->u64, ctrl, s));
+    CKL(launch_acv_green_input<T>(G->g, G->d_Sring, G->d_Gring, G->d_Rring, ctrl, s));
   }
   prof_mark(3, s);
-  dtt_status st = enqueue_green<T>(G, (T*)G->gbuf, (T*)G->spec, true, ctrl, 0, 3);
+  dtt_status st = diff ? enqueue_green<T>(G, nullptr, G->d_Gring, (T*)G->spec2, (T*)G->spec, true, ctrl, 0, 3)
+                       : enqueue_green<T>(G, (const T*)G->gbuf, nullptr, (T*)G->spec2, (T*)G->spec, true, ctrl, 0, 3);
   if (st != DTT_OK) return st;
   prof_mark(7, s);
-  if (G->nrows > 0) CKL(launch_proj_U_rows(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, ctrl, s));
-  if (G->contact) CKL(launch_contact_proj_U(ca, G->u64, G->uhi, G->ulo, s));
+  if (G->nrows > 0) CKL(launch_proj_U_rows<T>(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, (T*)G->step, ctrl, s));
+  if (G->contact) CKL(launch_contact_proj_U<T>(ca, G->u64, G->uhi, G->ulo, (T*)G->step, s));
   CKL(launch_ctrl_end(ctrl, s));
   prof_mark(8, s);
   return DTT_OK;
@@ -615,10 +646,14 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
   }
   for (int k = 0; k < 5 && s == DTT_OK; ++k) s = dalloc(&G->S[k], n3 * G->esz);
   for (int k = 0; k < 4 && s == DTT_OK; ++k) s = dalloc(&G->R[k], n3 * G->esz);
-  if (s == DTT_OK) s = dalloc(&G->gbuf, n3 * G->esz);
+  for (int k = 0; k < 4 && s == DTT_OK; ++k) s = dalloc(&G->Gr[k], n3 * G->esz);
+  if (s == DTT_OK) G->gbuf = G->Gr[0];
+  if (s == DTT_OK) s = dalloc(&G->step, n3 * G->esz);
   if (s == DTT_OK) s = dalloc(&G->spec, n3 * G->esz);
+  if (s == DTT_OK) s = dalloc(&G->spec2, n3 * G->esz);
   if (s == DTT_OK) s = dalloc(&G->d_Sring, 5 * sizeof(void*));
   if (s == DTT_OK) s = dalloc(&G->d_Rring, 4 * sizeof(void*));
+  if (s == DTT_OK) s = dalloc(&G->d_Gring, 4 * sizeof(void*));
   if (s == DTT_OK) s = dalloc(&G->phase, (size_t)G->NV);
   if (s == DTT_OK) s = dalloc(&G->d_lam, MAX_PHASE * sizeof(double));
   if (s == DTT_OK) s = dalloc(&G->d_mu, MAX_PHASE * sizeof(double));
@@ -634,12 +669,13 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
   // transform tables
   for (int c = 0; c < 3 && s == DTT_OK; ++c)
     for (int d = 0; d < 3 && s == DTT_OK; ++d) {
-      std::vector<double> F, B, cq;
+      std::vector<double> F, B, cq, cc;
       int nn = G->g.nn[d];
-      build_axis(G->types[c][d], nvox[d], nn, F, B, cq);
+      build_axis(G->types[c][d], nvox[d], nn, F, B, cq, cc);
       s = dalloc(&G->fwd[c][d], (size_t)nn * nn * G->esz);
       if (s == DTT_OK) s = dalloc(&G->inv[c][d], (size_t)nn * nn * G->esz);
-      if (s == DTT_OK) s = dalloc(&G->cosq[c][d], (size_t)nn * sizeof(double));
+      if (s == DTT_OK) s = dalloc(&G->sin2q[c][d], (size_t)nn * sizeof(double));
+      if (s == DTT_OK) s = dalloc(&G->cos2q[c][d], (size_t)nn * sizeof(double));
       if (s != DTT_OK) break;
       if (G->esz == 8) {
         cudaMemcpy(G->fwd[c][d], F.data(), F.size() * 8, cudaMemcpyHostToDevice);
@@ -649,11 +685,13 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
         cudaMemcpy(G->fwd[c][d], Ff.data(), Ff.size() * 4, cudaMemcpyHostToDevice);
         cudaMemcpy(G->inv[c][d], Bf.data(), Bf.size() * 4, cudaMemcpyHostToDevice);
       }
-      cudaMemcpy(G->cosq[c][d], cq.data(), cq.size() * 8, cudaMemcpyHostToDevice);
+      cudaMemcpy(G->sin2q[c][d], cq.data(), cq.size() * 8, cudaMemcpyHostToDevice);
+      cudaMemcpy(G->cos2q[c][d], cc.data(), cc.size() * 8, cudaMemcpyHostToDevice);
     }
   if (s == DTT_OK) {
     cudaError_t e = cudaMemcpy(G->d_Sring, G->S, 5 * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(G->d_Rring, G->R, 4 * sizeof(void*), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(G->d_Gring, G->Gr, 4 * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(G->cmask, 0, (size_t)G->NN);
     if (e == cudaSuccess) e = G->u64 ? cudaMemset(G->u64, 0, n3 * 8) : cudaMemset(G->uhi, 0, n3 * 4);
     if (e == cudaSuccess && G->ulo) e = cudaMemset(G->ulo, 0, n3 * 4);
@@ -674,10 +712,14 @@ void dtt_grid_destroy(dtt_grid* G) {
   dfree(G->ulo);
   for (auto& p : G->S) dfree(p);
   for (auto& p : G->R) dfree(p);
-  dfree(G->gbuf);
+  for (auto& p : G->Gr) dfree(p);
+  G->gbuf = nullptr;
+  dfree(G->step);
   dfree(G->spec);
+  dfree(G->spec2);
   dfree(G->d_Sring);
   dfree(G->d_Rring);
+  dfree(G->d_Gring);
   dfree(G->phase);
   dfree(G->d_lam);
   dfree(G->d_mu);
@@ -691,7 +733,8 @@ void dtt_grid_destroy(dtt_grid* G) {
     for (int d = 0; d < 3; ++d) {
       dfree(G->fwd[c][d]);
       dfree(G->inv[c][d]);
-      dfree(G->cosq[c][d]);
+      dfree(G->sin2q[c][d]);
+      dfree(G->cos2q[c][d]);
     }
   free_rows(G);
   free_contact(G);
@@ -951,16 +994,25 @@ dtt_status dtt_solve_step(dtt_grid* G, const dtt_solve_opts* opts, dtt_report* r
   c.contact_on = G->contact ? 1 : 0;
   c.tol = opts->tol;
   c.update_tol = opts->update_tol > 0.0 ? opts->update_tol : 1e-2;
+  c.acv_pivot = opts->acv_pivot > 0.0 ? opts->acv_pivot : 1e-14;
   CK(cudaMemcpyAsync(G->d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
   for (int k = 0; k < 5; ++k) CK(cudaMemsetAsync(G->S[k], 0, n3 * G->esz, s));
   for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(G->R[k], 0, n3 * G->esz, s));
+  for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(G->Gr[k], 0, n3 * G->esz, s));
+  CK(cudaMemsetAsync(G->step, 0, n3 * G->esz, s));
   PartRegions pr = regions(G);
   ContactArgs ca = contact_args(G, pr.cont);
   if (G->contact) {
     CKL(launch_contact_init(ca, s));
-    CKL(launch_contact_proj_U(ca, G->u64, G->uhi, G->ulo, s));
+    if (G->prec == DTT_PREC_FP64) CKL(launch_contact_proj_U<double>(ca, G->u64, G->uhi, G->ulo, nullptr, s));
+    else CKL(launch_contact_proj_U<float>(ca, G->u64, G->uhi, G->ulo, nullptr, s));
   }
-  if (G->nrows > 0) CKL(launch_proj_U_rows(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, G->d_ctrl, s));
+  if (G->nrows > 0) {
+    if (G->prec == DTT_PREC_FP64)
+      CKL(launch_proj_U_rows<double>(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, nullptr, G->d_ctrl, s));
+    else
+      CKL(launch_proj_U_rows<float>(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, nullptr, G->d_ctrl, s));
+  }
   const bool acv = opts->acv_mod > 0;
   const int iters = opts->graph_iters > 0 ? opts->graph_iters : 8;
   const int key = opts->acv_on * 1000000 + (acv ? 100000 : 0) + iters;
@@ -1116,11 +1168,11 @@ dtt_status dtt_apply_residual(dtt_grid* G, const double* u, double* p, double* p
   std::memcpy(ra.eps, G->eps, sizeof(ra.eps));
   ra.lam0 = G->lam0;
   ra.mu0 = G->mu0;
+  ra.mode = 0;
   ra.pout = G->gbuf;
   ra.xout = G->op_t2;
   ra.partials = G->d_part;
   ra.ctrl = nullptr;
-  ra.write_x_ring = 0;
   if (G->prec == DTT_PREC_FP64) CKL(launch_residual<double>(ra, s));
   else CKL(launch_residual<float>(ra, s));
   const int isf = G->prec == DTT_PREC_MIXED;
@@ -1156,8 +1208,8 @@ dtt_status dtt_apply_green(dtt_grid* G, const double* ptilde, double* u, int32_t
   const int isf = G->prec == DTT_PREC_MIXED;
   CK(cudaMemcpyAsync(G->op_d, ptilde, n3 * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   CKL(launch_from_double((long long)n3, G->op_d, G->op_t1, isf, s));
-  if (isf) st = enqueue_green<float>(G, (float*)G->op_t1, (float*)G->op_t2, false, nullptr, 0, 3);
-  else st = enqueue_green<double>(G, (double*)G->op_t1, (double*)G->op_t2, false, nullptr, 0, 3);
+  if (isf) st = enqueue_green<float>(G, (const float*)G->op_t1, nullptr, (float*)G->op_t1, (float*)G->op_t2, false, nullptr, 0, 3);
+  else st = enqueue_green<double>(G, (const double*)G->op_t1, nullptr, (double*)G->op_t1, (double*)G->op_t2, false, nullptr, 0, 3);
   if (st != DTT_OK) return st;
   CKL(launch_to_double((long long)n3, G->op_t1, isf, G->op_d, s));
   CK(cudaMemcpyAsync(u, G->op_d, n3 * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -1209,6 +1261,7 @@ dtt_status dtt_profile_iteration(dtt_grid* G, const dtt_solve_opts* opts, int32_
   c.contact_on = G->contact ? 1 : 0;
   c.tol = 0.0;
   c.update_tol = 1e-2;
+  c.acv_pivot = opts->acv_pivot > 0.0 ? opts->acv_pivot : 1e-14;
   c.no_stop = 1;
   CK(cudaMemcpyAsync(G->d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
   cudaEvent_t ev[9];

@@ -50,7 +50,9 @@ struct Ctrl {
   int n_vgap, n_vreact, n_mismatch, prev_valid;
   int hist_len;
   int no_stop;        // profiling: never stop on tolerance, cap or divergence
+  int pslot;          // p-ring slot written by this iteration's residual kernel
   double tol, update_tol;
+  double acv_pivot;
   double r, r0;
   double p2, s2;
   double alpha[4];
@@ -119,12 +121,15 @@ struct ResidualArgs {
   const uint8_t* cmask;   // bit c set: DOF (node, c) belongs to a row support / contact face
   double eps[3][3];
   double lam0, mu0;
-  void* xout;             // p~ = p + A0 u~ (may be null)
-  void* pout;             // p (may be null)
+  int mode;               // 0: p and p~ = p + A0 u~ ; 1: Anderson difference form ; 2: p only
+  void* xout;             // mode 0: p~ (may be null)
+  void* pout;             // modes 0, 2: p (may be null)
+  const void* dfield;     // mode 1: Delta = last step of u~ (T)
+  void* pring[4];         // mode 1: p ring (slot i % 4)
+  void* gring[4];         // mode 1: Green-input ring (g_{i-1} read from slot (i-1) % 4)
+  void* rring[4];         // mode 1: Anderson residual ring (R_{i-1} into slot (i-1) % 4)
   double* partials;       // 2 per block: sum w sigma:sigma, sum p^2 (unmasked DOFs)
-  const Ctrl* ctrl;       // if non-null: skip when done; xout = ring slot from i_local
-  void* ring[5];          // ring slots for p~ (ACV_P) when ctrl is set
-  int write_x_ring;
+  const Ctrl* ctrl;       // if non-null: skip when done (mode 1 needs it)
   int zchunk;             // z planes per CTA (set by the launcher)
 };
 template <typename T> int launch_residual(const ResidualArgs& a, cudaStream_t s);
@@ -134,26 +139,36 @@ int residual_zchunk(const GridDev& g);
 struct TransformTables {
   const void* fwd[3][3];   // [comp][axis] nn x nn row-major (spectral k, node j)
   const void* inv[3][3];   // [comp][axis] nn x nn row-major (node j, spectral k)
-  const double* cosq[3][3];
+  const double* sin2q[3][3];   // sin^2(q_k / 2) at every spectral position (0 unused)
+  const double* cos2q[3][3];   // cos^2(q_k / 2) (1 unused)
   double lam0, mu0;
+  double null_thr[3];
+};
+struct GreenTables {
+  const double* s[3][3];
+  const double* cp[3][3];
   double null_thr[3];
 };
 template <typename T>
 int launch_transform_axis(const GridDev& g, const T* in, T* out, const TransformTables& tt,
                           int axis, int inverse, int ncomp_first, int ncomp, const Ctrl* ctrl,
-                          cudaStream_t s);
+                          cudaStream_t s, void* const* in_ring = nullptr);
 template <typename T>
 int launch_green_multiply(const GridDev& g, T* spec, const TransformTables& tt, int scheme,
                           const Ctrl* ctrl, cudaStream_t s);
 template <typename T>
 int launch_add_increment(const GridDev& g, const T* delta, double* u64, float* uhi, float* ulo,
-                         const Ctrl* ctrl, cudaStream_t s);
+                         T* step_out, const Ctrl* ctrl, cudaStream_t s);
 
+// p: either p_direct, or (ring mode) p ring slot i % 4 with the same shifts applied to
+// the Anderson residual slot (i-1) % 4 when i > 0.
 template <typename T>
-int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p, T* x_or_null, int x_from_ring,
-                       void* const* ring, double* partials, const Ctrl* ctrl, cudaStream_t s);
+int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p_direct, void* const* pring,
+                       void* const* rring, int ring_mode, double* partials, const Ctrl* ctrl,
+                       cudaStream_t s);
+template <typename T>
 int launch_proj_U_rows(const GridDev& g, const RowsDev& r, double* u64, float* uhi, float* ulo,
-                       const Ctrl* ctrl, cudaStream_t s);
+                       T* step, const Ctrl* ctrl, cudaStream_t s);
 
 struct ContactArgs {
   GridDev g;
@@ -166,14 +181,25 @@ struct ContactArgs {
   double* partials;   // 3 per block: p^2, n_vgap, n_vreact (+ mismatches in [3])
 };
 template <typename T>
-int launch_contact_eval(const ContactArgs& a, T* p, void* const* ring, int x_from_ring,
-                        cudaStream_t s);
+int launch_contact_eval(const ContactArgs& a, T* p_direct, void* const* pring, void* const* rring,
+                        int ring_mode, cudaStream_t s);
 int launch_contact_update(const ContactArgs& a, cudaStream_t s);
-int launch_contact_proj_U(const ContactArgs& a, double* u64, float* uhi, float* ulo,
+template <typename T>
+int launch_contact_proj_U(const ContactArgs& a, double* u64, float* uhi, float* ulo, T* step,
                           cudaStream_t s);
 int launch_contact_init(const ContactArgs& a, cudaStream_t s);
 int contact_blocks(int nface);
 
+// Anderson on p~ in difference form: Gram row of R_{i-1}, then the accelerated Green input
+//   g_i = sum_m alpha_m p_{i-3+m} - sum_{q<3} beta_q (R_k - p_{k+1} + g_k),  k = i-3+q,
+//   beta_q = alpha_0 + ... + alpha_q   (g_i = p_i when not accelerating).
+template <typename T>
+int launch_acv_gram(const GridDev& g, void* const* rring, double* partials, const Ctrl* ctrl,
+                    cudaStream_t s);
+template <typename T>
+int launch_acv_green_input(const GridDev& g, void* const* pring, void* const* gring,
+                           void* const* rring, const Ctrl* ctrl, cudaStream_t s);
+// Anderson on u~ (FP64 path): S ring of u~ copies, R = u~_i - S_{i-1}.
 template <typename T>
 int launch_acv_store(const GridDev& g, int acv_on, void* const* Sring, void* const* Rring,
                      const double* u64, double* partials, const Ctrl* ctrl, cudaStream_t s);

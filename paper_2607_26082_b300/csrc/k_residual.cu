@@ -13,6 +13,11 @@
 // The Paux reference medium (Section 3.2.3) R0 : grad u = lambda0 (grad u (.) I)
 // + 2 mu0 grad u enters through tau0_cd = (2 mu0 + lambda0 delta_cd) grad_d u_c.
 //
+// Modes: 0 (operator) writes p and p~ = p + A0 u~; 2 writes p only; 1 (Anderson on p~ in
+// difference form) writes p into the p ring and, from the second iteration on, the
+// Anderson residual R_{i-1} = p_i - g_{i-1} + A0 Delta_{i-1} (Delta = last step of u~,
+// g = last Green input), which equals p~_i - S_{i-1} without forming either large term.
+//
 // B300 layout: one CTA owns a 32 x 4 tile of nodes in (x, y) and marches along z
 // through a chunk of planes.  It keeps two node planes of u~ and two voxel planes of
 // integration-point tensors (sigma: 6 values, tau0: 9 values per point) in shared memory,
@@ -78,6 +83,7 @@ k_residual(ResidualArgs a) {
   double (*sRed)[RTX * RTY / 32] = (double (*)[RTX * RTY / 32])(sMu + MAX_PHASE);
   VoxV<T, NIP> (*sV)[VY][VX] = (VoxV<T, NIP> (*)[VY][VX])(smem_raw + 2 * MAX_PHASE * 8 + 2 * (RTX * RTY / 32) * 8);
   NodeV<MIX> (*sU)[3][NY2][NX2] = (NodeV<MIX> (*)[3][NY2][NX2])((unsigned char*)sV + 2 * VY * VX * sizeof(VoxV<T, NIP>));
+  T (*sD)[3][NY2][NX2] = (T (*)[3][NY2][NX2])((unsigned char*)sU + 2 * 3 * NY2 * NX2 * sizeof(NodeV<MIX>));
 
   const GridDev& g = a.g;
   if (a.ctrl && a.ctrl->done) return;
@@ -91,9 +97,26 @@ k_residual(ResidualArgs a) {
   const long long NN = g.nnodes;
   const int nnx = g.nn[0], nny = g.nn[1], nnz = g.nn[2];
   T* xo = nullptr;
-  if (a.write_x_ring && a.ctrl) xo = (T*)a.ring[a.ctrl->i_local % 5];
-  else xo = (T*)a.xout;
   T* po = (T*)a.pout;
+  T* ro = nullptr;
+  const T* gprev = nullptr;
+  const T* dfield = nullptr;
+  bool tau_on = true;          // compute the reference-operator term
+  if (a.mode == 0) {
+    xo = (T*)a.xout;
+  } else if (a.mode == 1) {
+    const int il = a.ctrl->i_local;
+    po = (T*)a.pring[il % 4];
+    if (il > 0) {
+      ro = (T*)a.rring[(il - 1) % 4];
+      gprev = (const T*)a.gring[(il - 1) % 4];
+      dfield = (const T*)a.dfield;
+    } else {
+      tau_on = false;
+    }
+  } else {
+    tau_on = false;
+  }
   const double h = g.h;
   const T lam0 = (T)a.lam0, mu0 = (T)a.mu0;
   T eps[3][3];
@@ -122,6 +145,12 @@ k_residual(ResidualArgs a) {
           if constexpr (MIX) { v.hi = 0.f; v.lo = 0.f; } else { v.v = 0.0; }
         }
         sU[sl][c][ly][lx] = v;
+        if (dfield) {
+          T dv = (T)0;
+          if (kw >= 0 && gi >= 0 && gj >= 0)
+            dv = dfield[(long long)c * NN + gi + (long long)nnx * (gj + (long long)nny * kw)];
+          sD[sl][c][ly][lx] = dv;
+        }
       }
     }
   };
@@ -135,6 +164,12 @@ k_residual(ResidualArgs a) {
       int vxw = wrap_or_neg(vx, g.nvox[0], g.periodic[0]);
       int vyw = wrap_or_neg(vy, g.nvox[1], g.periodic[1]);
       VoxV<T, NIP>& V = sV[vs][ly][lx];
+      if (vxw < 0 || vyw < 0 || vzw < 0 || !tau_on) {
+        #pragma unroll
+        for (int t = 0; t < NIP; ++t)
+          #pragma unroll
+          for (int e = 0; e < 9; ++e) V.tau[t][e] = (T)0;
+      }
       if (vxw < 0 || vyw < 0 || vzw < 0) {
         #pragma unroll
         for (int t = 0; t < NIP; ++t) {
@@ -198,17 +233,52 @@ k_residual(ResidualArgs a) {
         T syz = (T)2 * mu * eyz, sxz = (T)2 * mu * exz, sxy = (T)2 * mu * exy;
         V.sig[t][0] = sxx; V.sig[t][1] = syy; V.sig[t][2] = szz;
         V.sig[t][3] = syz; V.sig[t][4] = sxz; V.sig[t][5] = sxy;
-        #pragma unroll
-        for (int c = 0; c < 3; ++c)
+        if (tau_on && !dfield) {
           #pragma unroll
-          for (int d = 0; d < 3; ++d)
-            V.tau[t][3 * c + d] = ((T)2 * mu0 + (c == d ? lam0 : (T)0)) * G[t][c][d];
+          for (int c = 0; c < 3; ++c)
+            #pragma unroll
+            for (int d = 0; d < 3; ++d)
+              V.tau[t][3 * c + d] = ((T)2 * mu0 + (c == d ? lam0 : (T)0)) * G[t][c][d];
+        }
         if (own) {
           double w = (NIP == 2) ? 0.5 : 1.0;
           double s2 = (double)sxx * sxx + (double)syy * syy + (double)szz * szz +
                       2.0 * ((double)syz * syz + (double)sxz * sxz + (double)sxy * sxy);
           acc_s2 += w * s2;
         }
+      }
+      if (dfield) {
+        // reference-operator tensor of the step Delta (plain differences: Delta is small)
+        T GD[NIP][3][3];
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const T u000 = sD[sl0][c][ly][lx], u100 = sD[sl0][c][ly][lx + 1];
+          const T u010 = sD[sl0][c][ly + 1][lx], u110 = sD[sl0][c][ly + 1][lx + 1];
+          const T u001 = sD[sl1][c][ly][lx], u101 = sD[sl1][c][ly][lx + 1];
+          const T u011 = sD[sl1][c][ly + 1][lx], u111 = sD[sl1][c][ly + 1][lx + 1];
+          if constexpr (SCHEME == SCHEME_TETRA2) {
+            T d_ba = u110 - u000, d_ce = u101 - u011, d_ca = u101 - u000, d_eb = u011 - u110;
+            GD[0][c][0] = (d_ba + d_ce) * inv2h;
+            GD[0][c][1] = (d_ba - d_ce) * inv2h;
+            GD[0][c][2] = (d_ca + d_eb) * inv2h;
+            T e_ab = u100 - u010, e_ec = u111 - u001, e_ca = u001 - u100, e_eb = u111 - u010;
+            GD[NIP - 1][c][0] = (e_ab + e_ec) * inv2h;
+            GD[NIP - 1][c][1] = (e_ec - e_ab) * inv2h;
+            GD[NIP - 1][c][2] = (e_ca + e_eb) * inv2h;
+          } else {
+            const T inv4h = (T)(1.0 / (4.0 * h));
+            GD[0][c][0] = ((u100 - u000) + (u110 - u010) + (u101 - u001) + (u111 - u011)) * inv4h;
+            GD[0][c][1] = ((u010 - u000) + (u110 - u100) + (u011 - u001) + (u111 - u101)) * inv4h;
+            GD[0][c][2] = ((u001 - u000) + (u101 - u100) + (u011 - u010) + (u111 - u110)) * inv4h;
+          }
+        }
+        #pragma unroll
+        for (int t = 0; t < NIP; ++t)
+          #pragma unroll
+          for (int c = 0; c < 3; ++c)
+            #pragma unroll
+            for (int d = 0; d < 3; ++d)
+              V.tau[t][3 * c + d] = ((T)2 * mu0 + (c == d ? lam0 : (T)0)) * GD[t][c][d];
       }
     }
   };
@@ -263,14 +333,16 @@ k_residual(ResidualArgs a) {
       for (int c = 0; c < 3; ++c) {
         bool dof;
         double invW = node_invW(g, c, i, j, k, dof);
-        T pv = (T)0, xv = (T)0;
+        T pv = (T)0, a0v = (T)0;
         if (dof) {
           pv = -Fs[c] * c4h * (T)invW;
-          xv = pv + F0[c] * c4h * (T)invW;
+          if (tau_on) a0v = F0[c] * c4h * (T)invW;
           if (!((cm >> c) & 1)) acc_p2 += (double)pv * (double)pv;
         }
-        if (po) po[(long long)c * NN + n] = pv;
-        if (xo) xo[(long long)c * NN + n] = xv;
+        const long long e = (long long)c * NN + n;
+        if (po) po[e] = pv;
+        if (xo) xo[e] = pv + a0v;
+        if (ro) ro[e] = dof ? (pv - gprev[e] + a0v) : (T)0;
       }
     }
     cur = nxt;
@@ -319,7 +391,7 @@ template <typename T, bool MIX, int SCHEME>
 static size_t residual_smem() {
   constexpr int NIP = (SCHEME == SCHEME_TETRA2) ? 2 : 1;
   return 2 * MAX_PHASE * 8 + 2 * (RTX * RTY / 32) * 8 + 2 * VY * VX * sizeof(VoxV<T, NIP>) +
-         2 * 3 * NY2 * NX2 * sizeof(NodeV<MIX>);
+         2 * 3 * NY2 * NX2 * sizeof(NodeV<MIX>) + 2 * 3 * NY2 * NX2 * sizeof(T);
 }
 
 template <typename T, bool MIX, int SCHEME>

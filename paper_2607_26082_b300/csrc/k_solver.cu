@@ -12,7 +12,7 @@
 //    u(M) = O - R n_c - M.
 //  * Anderson depth 4 (Section 4.1.1): R_{i-1} = x_i - S_{i-1}; every mod_ACV iterations
 //    after the first four, alpha = argmin ||sum alpha_k R_k|| with sum alpha_k = 1 (FP64
-//    Gram, Gaussian elimination with partial pivoting, skipped on a pivot <= 1e-14 max G_kk),
+//    Gram, Gaussian elimination with partial pivoting, skipped on a pivot <= acv_pivot max G_kk),
 //    x_i <- sum alpha_k (S_k + R_k).
 // All scalar decisions run in single-thread control kernels so that an iteration is a fixed
 // sequence of launches; every kernel returns at once when the solve is finished.
@@ -68,12 +68,24 @@ __device__ __forceinline__ void node_W(const GridDev& g, int c, int i, int j, in
 
 // ------------------------------------------------------------------ proj_P (rows)
 template <typename T>
-__global__ void k_proj_P(const RowsDev r, T* __restrict__ p, void* const* ring, int x_from_ring,
-                         T* xdirect, double* partials, const Ctrl* ctrl) {
+__device__ __forceinline__ void pick_p(const Ctrl* ctrl, int ring_mode, T* p_direct, void* const* pring,
+                                       void* const* rring, T*& p, T*& shadow) {
+  p = p_direct;
+  shadow = nullptr;
+  if (ring_mode) {
+    const int il = ctrl->i_local;
+    p = (T*)pring[il % 4];
+    if (il > 0) shadow = (T*)rring[(il - 1) % 4];
+  }
+}
+
+template <typename T>
+__global__ void k_proj_P(const RowsDev r, T* p_direct, void* const* pring, void* const* rring, int ring_mode,
+                         double* partials, const Ctrl* ctrl) {
   __shared__ double sh[SB / 32];
   if (ctrl && ctrl->done) return;
-  T* x = xdirect;
-  if (x_from_ring && ctrl) x = (T*)ring[ctrl->i_local % 5];
+  T *p, *x;
+  pick_p<T>(ctrl, ring_mode, p_direct, pring, rring, p, x);
   double acc = 0.0;
   int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row < r.nrows) {
@@ -95,17 +107,20 @@ __global__ void k_proj_P(const RowsDev r, T* __restrict__ p, void* const* ring, 
 }
 
 template <typename T>
-int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p, T* x_or_null, int x_from_ring,
-                       void* const* ring, double* partials, const Ctrl* ctrl, cudaStream_t s) {
+int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p_direct, void* const* pring, void* const* rring,
+                       int ring_mode, double* partials, const Ctrl* ctrl, cudaStream_t s) {
   (void)g;
   int blocks = (r.nrows + SB - 1) / SB;
   if (blocks == 0) return 0;
-  k_proj_P<T><<<blocks, SB, 0, s>>>(r, p, ring, x_from_ring, x_or_null, partials, ctrl);
+  k_proj_P<T><<<blocks, SB, 0, s>>>(r, p_direct, pring, rring, ring_mode, partials, ctrl);
   return (int)cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ proj_U (rows)
-__global__ void k_proj_U(const RowsDev r, double* u64, float* uhi, float* ulo, const Ctrl* ctrl) {
+// The correction applied to u~ is also added to the step field (the Anderson difference
+// form needs the full step u~_{i+1} - u~_i).
+template <typename T>
+__global__ void k_proj_U(const RowsDev r, double* u64, float* uhi, float* ulo, T* step, const Ctrl* ctrl) {
   if (ctrl && ctrl->done) return;
   int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= r.nrows) return;
@@ -115,16 +130,19 @@ __global__ void k_proj_U(const RowsDev r, double* u64, float* uhi, float* ulo, c
   for (int e = r.ptr[row]; e < r.ptr[row + 1]; ++e) {
     if (r.a[e] == 0.0) continue;
     long long d = r.dof[e];
-    write_u(d, read_u(d, u64, uhi, ulo) + r.a[e] * corr, u64, uhi, ulo);
+    double du = r.a[e] * corr;
+    write_u(d, read_u(d, u64, uhi, ulo) + du, u64, uhi, ulo);
+    if (step) step[d] = (T)((double)step[d] + du);
   }
 }
 
-int launch_proj_U_rows(const GridDev& g, const RowsDev& r, double* u64, float* uhi, float* ulo,
+template <typename T>
+int launch_proj_U_rows(const GridDev& g, const RowsDev& r, double* u64, float* uhi, float* ulo, T* step,
                        const Ctrl* ctrl, cudaStream_t s) {
   (void)g;
   int blocks = (r.nrows + SB - 1) / SB;
   if (blocks == 0) return 0;
-  k_proj_U<<<blocks, SB, 0, s>>>(r, u64, uhi, ulo, ctrl);
+  k_proj_U<T><<<blocks, SB, 0, s>>>(r, u64, uhi, ulo, step, ctrl);
   return (int)cudaGetLastError();
 }
 
@@ -149,11 +167,12 @@ __device__ void contact_geom(const ContactArgs& a, long long n, double Mp[3], do
 }
 
 template <typename T>
-__global__ void k_contact_eval(const ContactArgs a, T* __restrict__ p, void* const* ring, int x_from_ring) {
+__global__ void k_contact_eval(const ContactArgs a, T* p_direct, void* const* pring, void* const* rring,
+                               int ring_mode) {
   __shared__ double sh[SB / 32];
   if (a.ctrl && a.ctrl->done) return;
-  T* x = nullptr;
-  if (x_from_ring && a.ctrl) x = (T*)ring[a.ctrl->i_local % 5];
+  T *p, *x;
+  pick_p<T>(a.ctrl, ring_mode, p_direct, pring, rring, p, x);
   double p2 = 0.0, ng = 0.0, nr = 0.0, mm = 0.0;
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < a.c.nnodes_face) {
@@ -209,10 +228,11 @@ __global__ void k_contact_eval(const ContactArgs a, T* __restrict__ p, void* con
 }
 
 template <typename T>
-int launch_contact_eval(const ContactArgs& a, T* p, void* const* ring, int x_from_ring, cudaStream_t s) {
+int launch_contact_eval(const ContactArgs& a, T* p_direct, void* const* pring, void* const* rring, int ring_mode,
+                        cudaStream_t s) {
   int blocks = contact_blocks(a.c.nnodes_face);
   if (blocks == 0) return 0;
-  k_contact_eval<T><<<blocks, SB, 0, s>>>(a, p, ring, x_from_ring);
+  k_contact_eval<T><<<blocks, SB, 0, s>>>(a, p_direct, pring, rring, ring_mode);
   return (int)cudaGetLastError();
 }
 
@@ -238,7 +258,8 @@ int launch_contact_update(const ContactArgs& a, cudaStream_t s) {
   return (int)cudaGetLastError();
 }
 
-__global__ void k_contact_proj_U(const ContactArgs a, double* u64, float* uhi, float* ulo) {
+template <typename T>
+__global__ void k_contact_proj_U(const ContactArgs a, double* u64, float* uhi, float* ulo, T* step) {
   if (a.ctrl && a.ctrl->done) return;
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.c.nnodes_face || !a.c.active[q]) return;
@@ -254,14 +275,17 @@ __global__ void k_contact_proj_U(const ContactArgs a, double* u64, float* uhi, f
     if (!dof) continue;
     double us = a.eps[c][0] * X[0] + a.eps[c][1] * X[1] + a.eps[c][2] * X[2];
     double target = a.c.center[c] - a.c.radius * nv[c] - X[c] - us;
-    write_u((long long)c * a.g.nnodes + n, target, u64, uhi, ulo);
+    const long long e = (long long)c * a.g.nnodes + n;
+    if (step) step[e] = (T)((double)step[e] + (target - read_u(e, u64, uhi, ulo)));
+    write_u(e, target, u64, uhi, ulo);
   }
 }
 
-int launch_contact_proj_U(const ContactArgs& a, double* u64, float* uhi, float* ulo, cudaStream_t s) {
+template <typename T>
+int launch_contact_proj_U(const ContactArgs& a, double* u64, float* uhi, float* ulo, T* step, cudaStream_t s) {
   int blocks = contact_blocks(a.c.nnodes_face);
   if (blocks == 0) return 0;
-  k_contact_proj_U<<<blocks, SB, 0, s>>>(a, u64, uhi, ulo);
+  k_contact_proj_U<T><<<blocks, SB, 0, s>>>(a, u64, uhi, ulo, step);
   return (int)cudaGetLastError();
 }
 
@@ -329,6 +353,99 @@ int launch_acv_store(const GridDev& g, int acv_on, void* const* Sring, void* con
                      const double* u64, double* partials, const Ctrl* ctrl, cudaStream_t s) {
   long long total = 3 * g.nnodes;
   k_acv_store<T><<<acv_blocks(g), SB, 0, s>>>(total, acv_on, Sring, Rring, u64, partials, ctrl);
+  return (int)cudaGetLastError();
+}
+
+// Gram row of the newest Anderson residual R_{i-1} (difference form).
+template <typename T>
+__global__ void k_acv_gram(long long total, void* const* R, double* partials, const Ctrl* ctrl) {
+  __shared__ double sh[SB / 32];
+  if (ctrl->done) return;
+  const int i = ctrl->i_local;
+  if (i <= 0) return;
+  const int rs = (i - 1) % 4;
+  const T* Rn = (const T*)R[rs];
+  const T* R0 = (const T*)R[0];
+  const T* R1 = (const T*)R[1];
+  const T* R2 = (const T*)R[2];
+  const T* R3 = (const T*)R[3];
+  T d0 = 0, d1 = 0, d2 = 0, d3 = 0;   // per-thread partial sums in T; block and grid sums in FP64
+  double D[4] = {0, 0, 0, 0};
+  int cnt = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const T r = Rn[e];
+    d0 += r * R0[e];
+    d1 += r * R1[e];
+    d2 += r * R2[e];
+    d3 += r * R3[e];
+    if (++cnt == 16) {
+      D[0] += (double)d0; D[1] += (double)d1; D[2] += (double)d2; D[3] += (double)d3;
+      d0 = d1 = d2 = d3 = 0;
+      cnt = 0;
+    }
+  }
+  D[0] += (double)d0; D[1] += (double)d1; D[2] += (double)d2; D[3] += (double)d3;
+  for (int k = 0; k < 4; ++k) {
+    double t = block_sum(D[k], sh);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + k] = t;
+  }
+}
+
+template <typename T>
+int launch_acv_gram(const GridDev& g, void* const* rring, double* partials, const Ctrl* ctrl, cudaStream_t s) {
+  long long total = 3 * g.nnodes;
+  k_acv_gram<T><<<acv_blocks(g), SB, 0, s>>>(total, rring, partials, ctrl);
+  return (int)cudaGetLastError();
+}
+
+// Green input of iteration i: p_i, or the Anderson combination in difference form
+//   g_i = sum_m alpha_m p_{i-3+m} - sum_{q=0..2} beta_q (R_{i-3+q} - p_{i-2+q} + g_{i-3+q}),
+//   beta_q = alpha_0 + ... + alpha_q.
+// (x_{j+1} = p_{j+1} + A0 u~_{j+1}, S_j = A0 u~_j + g_j, R_j = x_{j+1} - S_j, hence
+//  sum alpha_j x_{j+1} - A0 u~_i = sum alpha_j p_{j+1} - sum_k beta_k A0 Delta_k with
+//  A0 Delta_k = R_k - p_{k+1} + g_k.)
+template <typename T>
+__global__ void k_acv_green_input(long long total, void* const* P, void* const* Gr, void* const* R,
+                                  const Ctrl* ctrl) {
+  if (ctrl->done) return;
+  const int i = ctrl->i_local;
+  T* gi = (T*)Gr[i % 4];
+  if (!ctrl->accel) {
+    const T* pi = (const T*)P[ctrl->i_local == 0 ? ctrl->pslot : i % 4];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+      gi[e] = pi[e];
+    return;
+  }
+  const T a0 = (T)ctrl->alpha[0], a1 = (T)ctrl->alpha[1], a2 = (T)ctrl->alpha[2], a3 = (T)ctrl->alpha[3];
+  const T b0 = a0, b1 = a0 + a1, b2 = a0 + a1 + a2;
+  const T* p0 = (const T*)P[(i - 3) % 4];
+  const T* p1 = (const T*)P[(i - 2) % 4];
+  const T* p2 = (const T*)P[(i - 1) % 4];
+  const T* p3 = (const T*)P[i % 4];
+  const T* r0 = (const T*)R[(i - 3) % 4];
+  const T* r1 = (const T*)R[(i - 2) % 4];
+  const T* r2 = (const T*)R[(i - 1) % 4];
+  const T* g0 = (const T*)Gr[(i - 3) % 4];
+  const T* g1 = (const T*)Gr[(i - 2) % 4];
+  const T* g2 = (const T*)Gr[(i - 1) % 4];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const T q0 = p0[e], q1 = p1[e], q2 = p2[e], q3 = p3[e];
+    T v = a0 * q0 + a1 * q1 + a2 * q2 + a3 * q3;
+    v -= b0 * (r0[e] - q1 + g0[e]);
+    v -= b1 * (r1[e] - q2 + g1[e]);
+    v -= b2 * (r2[e] - q3 + g2[e]);
+    gi[e] = v;
+  }
+}
+
+template <typename T>
+int launch_acv_green_input(const GridDev& g, void* const* pring, void* const* gring, void* const* rring,
+                           const Ctrl* ctrl, cudaStream_t s) {
+  long long total = 3 * g.nnodes;
+  k_acv_green_input<T><<<acv_blocks(g), SB, 0, s>>>(total, pring, gring, rring, ctrl);
   return (int)cudaGetLastError();
 }
 
@@ -412,6 +529,7 @@ __global__ void k_ctrl_residual(Ctrl* c, const double* rp, int nres, const doubl
   c->r = r;
   if (c->iter == 0) c->r0 = r;
   if (c->hist_len < HIST) c->hist[c->hist_len++] = r;
+  c->pslot = c->i_local % 4;
   c->n_vgap = (int)ng;
   c->n_vreact = (int)nr;
   c->n_mismatch = (int)mm;
@@ -466,7 +584,7 @@ __global__ void k_ctrl_acv(Ctrl* c, const double* partials, int nblk) {
       int piv = col;
       for (int r = col + 1; r < 4; ++r)
         if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
-      if (fabs(A[piv][col]) <= 1e-14 * scale) { ok = false; break; }
+      if (fabs(A[piv][col]) <= c->acv_pivot * scale) { ok = false; break; }
       if (piv != col) {
         for (int q = 0; q < 4; ++q) { double t = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = t; }
         double t = b[col]; b[col] = b[piv]; b[piv] = t;
@@ -518,10 +636,18 @@ int launch_ctrl_residual(Ctrl* c, const double* rp, int nres, const double* pp, 
   return (int)cudaGetLastError();
 }
 
-template int launch_proj_P_rows<double>(const GridDev&, const RowsDev&, double*, double*, int, void* const*, double*, const Ctrl*, cudaStream_t);
-template int launch_proj_P_rows<float>(const GridDev&, const RowsDev&, float*, float*, int, void* const*, double*, const Ctrl*, cudaStream_t);
-template int launch_contact_eval<double>(const ContactArgs&, double*, void* const*, int, cudaStream_t);
-template int launch_contact_eval<float>(const ContactArgs&, float*, void* const*, int, cudaStream_t);
+template int launch_proj_P_rows<double>(const GridDev&, const RowsDev&, double*, void* const*, void* const*, int, double*, const Ctrl*, cudaStream_t);
+template int launch_proj_P_rows<float>(const GridDev&, const RowsDev&, float*, void* const*, void* const*, int, double*, const Ctrl*, cudaStream_t);
+template int launch_proj_U_rows<double>(const GridDev&, const RowsDev&, double*, float*, float*, double*, const Ctrl*, cudaStream_t);
+template int launch_proj_U_rows<float>(const GridDev&, const RowsDev&, double*, float*, float*, float*, const Ctrl*, cudaStream_t);
+template int launch_contact_eval<double>(const ContactArgs&, double*, void* const*, void* const*, int, cudaStream_t);
+template int launch_contact_eval<float>(const ContactArgs&, float*, void* const*, void* const*, int, cudaStream_t);
+template int launch_contact_proj_U<double>(const ContactArgs&, double*, float*, float*, double*, cudaStream_t);
+template int launch_contact_proj_U<float>(const ContactArgs&, double*, float*, float*, float*, cudaStream_t);
+template int launch_acv_gram<double>(const GridDev&, void* const*, double*, const Ctrl*, cudaStream_t);
+template int launch_acv_gram<float>(const GridDev&, void* const*, double*, const Ctrl*, cudaStream_t);
+template int launch_acv_green_input<double>(const GridDev&, void* const*, void* const*, void* const*, const Ctrl*, cudaStream_t);
+template int launch_acv_green_input<float>(const GridDev&, void* const*, void* const*, void* const*, const Ctrl*, cudaStream_t);
 template int launch_acv_store<double>(const GridDev&, int, void* const*, void* const*, const double*, double*, const Ctrl*, cudaStream_t);
 template int launch_acv_store<float>(const GridDev&, int, void* const*, void* const*, const double*, double*, const Ctrl*, cudaStream_t);
 template int launch_acv_accel<double>(const GridDev&, int, void* const*, void* const*, double*, double*, const Ctrl*, cudaStream_t);

@@ -15,7 +15,8 @@
 // from the right.  The Green multiply divides each spectral value by
 //     a_c(q) = lambda0 S_c(q) + 2 mu0 (S_x + S_y + S_z)
 // (TETRA2: S_j = (1 + c_k c_l - c_j c_k - c_j c_l)/h^2; HEX1: S_j = (1-c_j)(1+c_k)(1+c_l)/(2h^2),
-// c_j = cos q_j), zeroing null modes (a_c <= threshold).
+// c_j = cos q_j; evaluated through sin^2(q_j/2) and cos^2(q_j/2)), zeroing null modes
+// (a_c <= threshold).
 #include "dtt_internal.cuh"
 
 namespace dtt {
@@ -86,8 +87,9 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_axis_right(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ A0m,
              const T* __restrict__ A1m, const T* __restrict__ A2m, int len, int rows, long long NN,
-             int comp0, const Ctrl* ctrl) {
+             int comp0, const Ctrl* ctrl, void* const* in_ring) {
   if (ctrl && ctrl->done) return;
+  if (in_ring) in = (const T*)in_ring[ctrl->i_local % 4];
   __shared__ T As[GBK][GBM + 1];   // pencil rows (k, r)
   __shared__ T Bs[GBK][GBN + 1];   // matrix (k, n)
   const int comp = comp0 + blockIdx.z;
@@ -142,7 +144,7 @@ k_axis_right(const T* __restrict__ in, T* __restrict__ out, const T* __restrict_
 template <typename T>
 int launch_transform_axis(const GridDev& g, const T* in, T* out, const TransformTables& tt,
                           int axis, int inverse, int ncomp_first, int ncomp, const Ctrl* ctrl,
-                          cudaStream_t s) {
+                          cudaStream_t s, void* const* in_ring) {
   const T* M[3];
   for (int c = 0; c < 3; ++c)
     M[c] = (const T*)(inverse ? tt.inv[c][axis] : tt.fwd[c][axis]);
@@ -150,8 +152,9 @@ int launch_transform_axis(const GridDev& g, const T* in, T* out, const Transform
   if (axis == 0) {
     int rows = nny * nnz;
     dim3 grd((nnx + GBN - 1) / GBN, (rows + GBM - 1) / GBM, ncomp);
-    k_axis_right<T><<<grd, 256, 0, s>>>(in, out, M[0], M[1], M[2], nnx, rows, g.nnodes, ncomp_first, ctrl);
+    k_axis_right<T><<<grd, 256, 0, s>>>(in, out, M[0], M[1], M[2], nnx, rows, g.nnodes, ncomp_first, ctrl, in_ring);
   } else {
+    if (in_ring) return (int)cudaErrorInvalidValue;   // ring input only on the first (x) pass
     int len = axis == 1 ? nny : nnz;
     int inner = axis == 1 ? nnx : nnx * nny;
     int outer = axis == 1 ? nnz : 1;
@@ -161,17 +164,24 @@ int launch_transform_axis(const GridDev& g, const T* in, T* out, const Transform
   return (int)cudaGetLastError();
 }
 
+// s_j = sin^2(q_j/2) and c'_j = cos^2(q_j/2) (tables exact in double) keep the symbol
+// accurate both near q = 0 and near the checkerboard q = (pi,pi,pi), where the plain
+// cosine form cancels:  TETRA2  S_x / 4 = s_x c'_y + s_z (s_y - s_x),  s_y - s_x = c'_x - c'_y;
+//                       HEX1    S_x / 4 = s_x c'_y c'_z.
 template <typename T>
-__global__ void k_green(const GridDev g, T* __restrict__ spec, const double* __restrict__ c0x,
-                        const double* __restrict__ c0y, const double* __restrict__ c0z,
-                        const double* __restrict__ c1x, const double* __restrict__ c1y,
-                        const double* __restrict__ c1z, const double* __restrict__ c2x,
-                        const double* __restrict__ c2y, const double* __restrict__ c2z, double lam0,
-                        double mu0, double thr0, double thr1, double thr2, const Ctrl* ctrl) {
+__device__ __forceinline__ T tetra_S(T sa, T cb, T sb, T cA, T sc) {
+  // S_a / 4 = s_a c'_b + s_c (s_b - s_a), difference taken in the accurate variables
+  const T d = (sa + sb < (T)1) ? (sb - sa) : (cA - cb);
+  return sa * cb + sc * d;
+}
+
+template <typename T>
+__global__ void k_green(const GridDev g, T* __restrict__ spec, GreenTables gt, double lam0, double mu0,
+                        const Ctrl* ctrl) {
   if (ctrl && ctrl->done) return;
   const long long NN = g.nnodes;
   const long long total = 3 * NN;
-  const double ih2 = 1.0 / (g.h * g.h);
+  const T ih2 = (T)(4.0 / (g.h * g.h));
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     int c = (int)(e / NN);
@@ -180,24 +190,22 @@ __global__ void k_green(const GridDev g, T* __restrict__ spec, const double* __r
     long long r = n / g.nn[0];
     int j = (int)(r % g.nn[1]);
     int k = (int)(r / g.nn[1]);
-    const double* cx = c == 0 ? c0x : (c == 1 ? c1x : c2x);
-    const double* cy = c == 0 ? c0y : (c == 1 ? c1y : c2y);
-    const double* cz = c == 0 ? c0z : (c == 1 ? c1z : c2z);
-    double X = cx[i], Y = cy[j], Z = cz[k];
-    double Sx, Sy, Sz;
+    const T sx = (T)gt.s[c][0][i], sy = (T)gt.s[c][1][j], sz = (T)gt.s[c][2][k];
+    const T cx = (T)gt.cp[c][0][i], cy = (T)gt.cp[c][1][j], cz = (T)gt.cp[c][2][k];
+    T Sx, Sy, Sz;
     if (g.scheme == SCHEME_TETRA2) {
-      Sx = (1.0 + Y * Z - X * Y - X * Z) * ih2;
-      Sy = (1.0 + X * Z - Y * X - Y * Z) * ih2;
-      Sz = (1.0 + X * Y - Z * X - Z * Y) * ih2;
+      Sx = tetra_S<T>(sx, cy, sy, cx, sz);
+      Sy = tetra_S<T>(sy, cz, sz, cy, sx);
+      Sz = tetra_S<T>(sz, cx, sx, cz, sy);
     } else {
-      Sx = (1.0 - X) * (1.0 + Y) * (1.0 + Z) * 0.5 * ih2;
-      Sy = (1.0 - Y) * (1.0 + X) * (1.0 + Z) * 0.5 * ih2;
-      Sz = (1.0 - Z) * (1.0 + X) * (1.0 + Y) * 0.5 * ih2;
+      Sx = sx * cy * cz;
+      Sy = sy * cx * cz;
+      Sz = sz * cx * cy;
     }
-    double Sc = c == 0 ? Sx : (c == 1 ? Sy : Sz);
-    double a = lam0 * Sc + 2.0 * mu0 * (Sx + Sy + Sz);
-    double thr = c == 0 ? thr0 : (c == 1 ? thr1 : thr2);
-    spec[e] = (a <= thr) ? (T)0 : (T)((double)spec[e] / a);
+    const T Sc = c == 0 ? Sx : (c == 1 ? Sy : Sz);
+    const T a = ((T)lam0 * Sc + (T)(2.0 * mu0) * (Sx + Sy + Sz)) * ih2;
+    const T thr = (T)gt.null_thr[c];
+    spec[e] = (a <= thr) ? (T)0 : spec[e] / a;
   }
 }
 
@@ -207,20 +215,27 @@ int launch_green_multiply(const GridDev& g, T* spec, const TransformTables& tt, 
   (void)scheme;
   long long total = 3 * g.nnodes;
   int blocks = (int)std::min<long long>((total + 255) / 256, 148LL * 16);
-  k_green<T><<<blocks, 256, 0, s>>>(g, spec, tt.cosq[0][0], tt.cosq[0][1], tt.cosq[0][2], tt.cosq[1][0],
-                                    tt.cosq[1][1], tt.cosq[1][2], tt.cosq[2][0], tt.cosq[2][1],
-                                    tt.cosq[2][2], tt.lam0, tt.mu0, tt.null_thr[0], tt.null_thr[1],
-                                    tt.null_thr[2], ctrl);
+  GreenTables gt;
+  for (int c = 0; c < 3; ++c) {
+    for (int d = 0; d < 3; ++d) {
+      gt.s[c][d] = tt.sin2q[c][d];
+      gt.cp[c][d] = tt.cos2q[c][d];
+    }
+    gt.null_thr[c] = tt.null_thr[c];
+  }
+  k_green<T><<<blocks, 256, 0, s>>>(g, spec, gt, tt.lam0, tt.mu0, ctrl);
   return (int)cudaGetLastError();
 }
 
 // u~ <- u~ + delta (Green step in increment form: G(p~) = u~ + G(p~ - A0 u~)).
 template <typename T>
 __global__ void k_add_increment(long long total, const T* __restrict__ delta, double* __restrict__ u64,
-                                float* __restrict__ uhi, float* __restrict__ ulo, const Ctrl* ctrl) {
+                                float* __restrict__ uhi, float* __restrict__ ulo, T* __restrict__ step,
+                                const Ctrl* ctrl) {
   if (ctrl && ctrl->done) return;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
+    if (step) step[e] = delta[e];
     if constexpr (sizeof(T) == 8) {
       u64[e] += (double)delta[e];
     } else {
@@ -234,18 +249,18 @@ __global__ void k_add_increment(long long total, const T* __restrict__ delta, do
 
 template <typename T>
 int launch_add_increment(const GridDev& g, const T* delta, double* u64, float* uhi, float* ulo,
-                         const Ctrl* ctrl, cudaStream_t s) {
+                         T* step_out, const Ctrl* ctrl, cudaStream_t s) {
   long long total = 3 * g.nnodes;
   int blocks = (int)std::min<long long>((total + 255) / 256, 148LL * 16);
-  k_add_increment<T><<<blocks, 256, 0, s>>>(total, delta, u64, uhi, ulo, ctrl);
+  k_add_increment<T><<<blocks, 256, 0, s>>>(total, delta, u64, uhi, ulo, step_out, ctrl);
   return (int)cudaGetLastError();
 }
 
-template int launch_transform_axis<double>(const GridDev&, const double*, double*, const TransformTables&, int, int, int, int, const Ctrl*, cudaStream_t);
-template int launch_transform_axis<float>(const GridDev&, const float*, float*, const TransformTables&, int, int, int, int, const Ctrl*, cudaStream_t);
+template int launch_transform_axis<double>(const GridDev&, const double*, double*, const TransformTables&, int, int, int, int, const Ctrl*, cudaStream_t, void* const*);
+template int launch_transform_axis<float>(const GridDev&, const float*, float*, const TransformTables&, int, int, int, int, const Ctrl*, cudaStream_t, void* const*);
 template int launch_green_multiply<double>(const GridDev&, double*, const TransformTables&, int, const Ctrl*, cudaStream_t);
 template int launch_green_multiply<float>(const GridDev&, float*, const TransformTables&, int, const Ctrl*, cudaStream_t);
-template int launch_add_increment<double>(const GridDev&, const double*, double*, float*, float*, const Ctrl*, cudaStream_t);
-template int launch_add_increment<float>(const GridDev&, const float*, double*, float*, float*, const Ctrl*, cudaStream_t);
+template int launch_add_increment<double>(const GridDev&, const double*, double*, float*, float*, double*, const Ctrl*, cudaStream_t);
+template int launch_add_increment<float>(const GridDev&, const float*, double*, float*, float*, float*, const Ctrl*, cudaStream_t);
 
 }  // namespace dtt

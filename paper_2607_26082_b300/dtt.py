@@ -29,7 +29,7 @@ class DttError(RuntimeError):
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("acv_mod", C.c_int32),
                 ("acv_on", C.c_int32), ("init", C.c_int32), ("update_tol", C.c_double),
-                ("graph_iters", C.c_int32)]
+                ("graph_iters", C.c_int32), ("acv_pivot", C.c_double)]
 
 
 class Report(C.Structure):
@@ -186,9 +186,9 @@ class Grid:
         _check(lib().dtt_set_initial(self._h, p, dev))
 
     def dtt_solve_step(self, tol, max_iter, acv_mod=3, acv_on=ACV_P, init=INIT_ZERO, update_tol=1e-2,
-                       graph_iters=0, raise_on_error=False):
+                       graph_iters=0, acv_pivot=0.0, raise_on_error=False):
         o = SolveOpts(float(tol), int(max_iter), int(acv_mod), int(acv_on), int(init), float(update_tol),
-                      int(graph_iters))
+                      int(graph_iters), float(acv_pivot))
         r = Report()
         st = lib().dtt_solve_step(self._h, C.byref(o), C.byref(r))
         if st not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED) or (raise_on_error and st != OK):
@@ -255,7 +255,7 @@ class Grid:
 
 
     def dtt_profile_iteration(self, iters, acv_mod=3, acv_on=ACV_P):
-        o = SolveOpts(0.0, 1 << 30, int(acv_mod), int(acv_on), INIT_PREVIOUS, 1e-2, 0)
+        o = SolveOpts(0.0, 1 << 30, int(acv_mod), int(acv_on), INIT_PREVIOUS, 1e-2, 0, 0.0)
         ms = np.zeros(NPROF)
         _check(lib().dtt_profile_iteration(self._h, C.byref(o), int(iters), ms.ctypes.data_as(C.c_void_p)))
         return dict(zip(PROF_GROUPS, ms))

@@ -296,3 +296,50 @@ def test_not_converged_keeps_iterate():
     assert rep.status == dtt.ERR_NOT_CONVERGED and rep.iterations == 5
     u = g.dtt_get_fields()
     assert np.isfinite(u).all() and np.abs(u).max() > 0
+
+
+# ----------------------------------------------------------------------------- CT specimen
+def test_ct_specimen_small_fp64_and_mixed():
+    """Half CT-like specimen at 32 x 32 x 8 (the benchmark's structure at reduced size):
+    FP64 fixed-iteration parity, converged parity for both paths, reaction balance."""
+    spec = wl.ct_plate(32, 32, 8)
+    pb, rows = oracle_problem(spec)
+    K = 40
+    ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 0.0, K, acv_mod=2)
+    g = gpu_grid(spec, FP64)
+    rep = g.dtt_solve_step(0.0, K, acv_mod=2)
+    assert rep.accelerations == ref.accelerations
+    assert rel_l2(g.dtt_get_fields(), ref.u) <= 1e-9
+    conv = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 1e-12, 3000, acv_mod=2)
+    nl = spec["ligament_rows"]
+    for prec, tol, bound in ((FP64, 1e-12, 1e-10), (MIXED, 1e-6, 2e-5)):
+        g = gpu_grid(spec, prec)
+        rep = g.dtt_solve_step(tol, 3000, acv_mod=2)
+        assert rep.status == dtt.OK, rep.as_dict()
+        assert rel_l2(g.dtt_get_fields(), conv.u) <= bound
+        per, tot = g.dtt_get_reactions(len(rows))
+        RS, RL = per[:nl].sum(), per[nl:].sum()
+        assert abs(RS + RL) <= 20 * tol * abs(RL) + 1e-12 * abs(RL)
+        assert abs(RL / conv.reactions[nl:].sum() - 1) <= bound * 10
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_ct_specimen_full_size_properties(prec):
+    """The benchmark configuration itself (128 x 128 x 32): the solve converges to 1e-6,
+    the oracle's own residual (Eq. 5, evaluated by the float64 CPU code on the GPU's u~
+    after its proj_P) agrees, and the ligament and pin reactions balance."""
+    spec = wl.ct_plate()
+    g = gpu_grid(spec, prec)
+    rep = g.dtt_solve_step(spec["tol"], 6000, acv_mod=2, graph_iters=16)
+    assert rep.status == dtt.OK, rep.as_dict()
+    u = g.dtt_get_fields()
+    pb, rows = oracle_problem(spec)
+    p, sig = odz.residual(pb, u)
+    ocs.proj_P(pb, p, rows)
+    r_oracle = odz.residual_norm(pb, p, sig)
+    assert r_oracle <= 2.0 * spec["tol"]
+    assert abs(r_oracle - rep.residual) <= 0.05 * rep.residual + 1e-9
+    per, tot = g.dtt_get_reactions(len(rows))
+    nl = spec["ligament_rows"]
+    RS, RL = per[:nl].sum(), per[nl:].sum()
+    assert abs(RS + RL) <= 1e-4 * abs(RL)

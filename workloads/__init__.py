@@ -81,47 +81,47 @@ def cube16(seed=1, n=16, scheme=TETRA2):
 # ---------------------------------------------------------------------------
 # Compact-tension-like plate
 # ---------------------------------------------------------------------------
-def ct_plate(nx=128, ny=128, nz=32, scheme=TETRA2, notch_scale=0.0):
-    """128x128x32 voxels, E=210 (GPa, h=1), nu=0.3; notch of void voxels
-    (stiffness notch_scale * E) x in [0, 40*nx/128), y in [ny/2-2, ny/2+2), all z.
-    notch_scale defaults to 0, the paper's void of null properties (Section 4.1.2): with
-    1e-6 E the notch interior converges at a rate of about 1 - 1e-6 per iteration and
-    the Eq. 5 residual stalls near 1e-6.  Two pins
-    of radius 6*nx/128 through the thickness centred at x = 20*nx/128,
-    y = ny/2 +- 24*ny/128: nodes inside carry u_x = 0 and u_y = +-0.05.
-    The plate is traction-free.  As in the paper's CT-like set-up (Section 4.1.2), the
-    in-plane components get their Dirichlet faces through a one-voxel buffer frame of
-    null stiffness (voxels x = 0, nx-1 and y = 0, ny-1): u_x and u_y are Dirichlet on
-    the four lateral faces of the box, which transmit no force through the buffer; u_z is
-    Dirichlet on z = 0 (mid-thickness symmetry plane); all other faces Neumann."""
+def ct_plate(nx=128, ny=128, nz=32, scheme=TETRA2, notch_scale=0.0, r0_factor=1.0):
+    """Half compact-tension-like specimen in the paper's device (Section 4.1.2, Fig. 2),
+    nx x ny x nz voxels (default 128 x 128 x 32), E = 210 (GPa, h = 1), nu = 0.3:
+      * voxel row y in [0, 1): buffer layer of null stiffness; u_y is Dirichlet on the
+        face y = 0 behind it (the buffer transmits no force);
+      * crack plane y = 1: ligament nodes x >= 40 s (s = nx / 128) held at u_y = 0 (strong
+        rows); notch voxels x < 40 s, y in [1, 3) are void (stiffness notch_scale * E), so
+        the crack faces are traction-free;
+      * one pin, a disk of radius 6 s through the thickness centred at (20 s, 1 + 24 s),
+        pulled to u_y = +0.05 (strong rows) -- the specimen is the upper half of a plate whose
+        two pins are pulled apart symmetrically;
+      * u_z Dirichlet on z = 0 (mid-thickness symmetry plane); all other faces traction-free.
+    Reference medium R0 = r0_factor * (lambda, mu) (Paux form, Section 3.2.3); tol 1e-6,
+    Anderson on p~ every 2 iterations."""
     s = nx / 128.0
     bc = np.full((3, 2, 3), N, dtype=np.int64)
-    bc[0, :, 0:2] = D
-    bc[1, :, 0:2] = D
+    bc[1, 0, 1] = D
     bc[2, 0, 2] = D
     E = 210.0
     lam, mu = lame(E, 0.3)
     lv, mv = lame(notch_scale * E, 0.3)
+    xn = int(round(40 * s))
     phase = np.zeros((nz, ny, nx), np.uint8)
-    phase[:, ny // 2 - 2: ny // 2 + 2, : int(round(40 * s))] = 1
-    phase[:, :, 0] = 2
-    phase[:, :, nx - 1] = 2
+    phase[:, 1:3, :xn] = 1
     phase[:, 0, :] = 2
-    phase[:, ny - 1, :] = 2
-    r = 6.0 * s
-    cx = 20.0 * s
     intents = []
-    for sign, cy in ((+1.0, ny / 2 + 24.0 * ny / 128.0), (-1.0, ny / 2 - 24.0 * ny / 128.0)):
-        for k in range(nz + 1):
-            for j in range(ny + 1):
-                for i in range(nx + 1):
-                    if (i - cx) ** 2 + (j - cy) ** 2 <= r * r:
-                        intents.append(dict(kind="strong", ijk=(i, j, k), comp=0, value=0.0))
-                        intents.append(dict(kind="strong", ijk=(i, j, k), comp=1, value=0.05 * sign))
-    return Workload(name="CT-like plate %dx%dx%d" % (nx, ny, nz), nvox=(nx, ny, nz), h=1.0, bc=bc,
-                    scheme=scheme, phase=phase, lam=np.array([lam, lv, 0.0]),
+    for k in range(nz + 1):
+        for i in range(xn, nx + 1):
+            intents.append(dict(kind="strong", ijk=(i, 1, k), comp=1, value=0.0))
+    r = 6.0 * s
+    cx, cy = 20.0 * s, 1.0 + 24.0 * s
+    for k in range(nz + 1):
+        for j in range(ny + 1):
+            for i in range(nx + 1):
+                if (i - cx) ** 2 + (j - cy) ** 2 <= r * r:
+                    intents.append(dict(kind="strong", ijk=(i, j, k), comp=1, value=0.05))
+    return Workload(name="half CT-like specimen %dx%dx%d" % (nx, ny, nz), nvox=(nx, ny, nz), h=1.0,
+                    bc=bc, scheme=scheme, phase=phase, lam=np.array([lam, lv, 0.0]),
                     mu=np.array([mu, mv, 0.0]), eps_star=np.zeros((3, 3)), intents=intents,
-                    lam0=lam / 2, mu0=mu / 2, tol=1e-6, acv_mod=2)
+                    lam0=r0_factor * lam, mu0=r0_factor * mu, tol=1e-6, acv_mod=2,
+                    ligament_rows=(nz + 1) * (nx + 1 - xn))
 
 
 # ---------------------------------------------------------------------------
