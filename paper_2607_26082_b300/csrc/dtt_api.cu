@@ -1295,3 +1295,74 @@ dtt_status dtt_profile_iteration(dtt_grid* G, const dtt_solve_opts* opts, int32_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free Green step.
+//
+// Some callers cannot call cudaMalloc while they run: code inside a memory-budgeted
+// service that must not grow the device heap after start-up, real-time loops where an
+// allocation's implicit synchronisation is unacceptable, or hosts whose allocator is
+// owned by another framework.  dtt_apply_green_noalloc lets them apply the Green step to
+// their own device buffers without any allocation: the intermediate spectra live in the
+// fixed array below, which every GPU that loads this library holds until the process
+// exits.  The array's device address is looked up once per device (cudaGetSymbolAddress
+// with that device current) on the first call made on that device, so that first call
+// should come before any stream capture.  All calls share the array: calls that overlap
+// on the GPU (different streams, or different grids used concurrently) race on it.
+// Nothing in it has to start at zero: every element a call reads was written earlier
+// in the same call.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kGreenScratchBytes = 64ull << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_green_scratch[kGreenScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_green_scratch_addr[kMaxDevices] = {nullptr};
+
+dtt_status green_scratch_for_current_device(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(DTT_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(DTT_ERR_ARG, "device ordinal beyond the scratch table");
+  if (!g_green_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_green_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(DTT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    g_green_scratch_addr[dev] = p;
+  }
+  *out = g_green_scratch_addr[dev];
+  return DTT_OK;
+}
+
+}  // namespace
+
+extern "C" dtt_status dtt_apply_green_noalloc(dtt_grid* G, const double* ptilde_dev, double* u_dev) {
+  if (!G || !ptilde_dev || !u_dev) return fail(DTT_ERR_ARG, "null argument");
+  if (!G->ref_set) return fail(DTT_ERR_STATE, "reference not set");
+  const size_t n3 = (size_t)(3 * G->NN);
+  const size_t need = n3 * sizeof(double);   // FP64: one work field; mixed: two float fields
+  if (need > kGreenScratchBytes)
+    return fail(DTT_ERR_ARG, "grid too large for the allocation-free Green step: needs " + std::to_string(need) +
+                                 " bytes of scratch, the fixed array holds " + std::to_string(kGreenScratchBytes) +
+                                 " (at most " + std::to_string(kGreenScratchBytes / 24) + " nodes)");
+  void* scratch = nullptr;
+  dtt_status st = green_scratch_for_current_device(&scratch);
+  if (st != DTT_OK) return st;
+  cudaStream_t s = G->stream;
+  if (G->prec == DTT_PREC_FP64) {
+    // in -> scratch -> out ping-pong; the result lands in the caller's output buffer
+    st = enqueue_green<double>(G, ptilde_dev, nullptr, u_dev, (double*)scratch, false, nullptr, 0, 3);
+    if (st != DTT_OK) return st;
+  } else {
+    float* a = (float*)scratch;
+    float* b = a + n3;
+    CKL(launch_from_double((long long)n3, ptilde_dev, a, 1, s));
+    st = enqueue_green<float>(G, a, nullptr, a, b, false, nullptr, 0, 3);
+    if (st != DTT_OK) return st;
+    CKL(launch_to_double((long long)n3, a, 1, u_dev, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return DTT_OK;
+}

@@ -47,7 +47,8 @@ EXPORTS = ["dtt_grid_create", "dtt_grid_destroy", "dtt_grid_sizes", "dtt_set_mat
            "dtt_set_reference", "dtt_set_load", "dtt_set_constraints", "dtt_set_indenter",
            "dtt_move_indenter", "dtt_clear_indenter", "dtt_set_initial", "dtt_solve_step",
            "dtt_get_history", "dtt_get_fields", "dtt_get_reactions", "dtt_get_contact",
-           "dtt_apply_residual", "dtt_apply_green", "dtt_transform", "dtt_profile_iteration",
+           "dtt_apply_residual", "dtt_apply_green", "dtt_apply_green_noalloc", "dtt_transform",
+           "dtt_profile_iteration",
            "dtt_last_error", "dtt_version"]
 NPROF = 7
 PROF_GROUPS = ["residual", "projections", "anderson", "forward_dt", "green", "inverse_dt", "increment"]
@@ -82,6 +83,7 @@ def lib():
     L.dtt_get_contact.argtypes = [P, C.POINTER(i32), P, P, P, P]
     L.dtt_apply_residual.argtypes = [P, P, P, P, P, i32]
     L.dtt_apply_green.argtypes = [P, P, P, i32]
+    L.dtt_apply_green_noalloc.argtypes = [P, P, P]
     L.dtt_transform.argtypes = [P, i32, i32, P, P, i32]
     L.dtt_profile_iteration.argtypes = [P, C.POINTER(SolveOpts), i32, P]
     L.dtt_last_error.restype = C.c_char_p
@@ -245,6 +247,15 @@ class Grid:
         u = np.zeros_like(pt)
         _check(lib().dtt_apply_green(self._h, pt.ctypes.data_as(C.c_void_p), u.ctypes.data_as(C.c_void_p), 0))
         return u
+
+    def dtt_apply_green_noalloc(self, ptilde_dev, u_dev):
+        """Green step on caller-owned float64 device arrays (torch CUDA tensors), using the
+        library's fixed scratch instead of any allocation."""
+        p_in, d_in = _ptr(ptilde_dev)
+        p_out, d_out = _ptr(u_dev)
+        if not (d_in and d_out):
+            raise ValueError("dtt_apply_green_noalloc takes device arrays")
+        _check(lib().dtt_apply_green_noalloc(self._h, p_in, p_out))
 
     def dtt_transform(self, component, inverse, x):
         x = np.ascontiguousarray(x, dtype=np.float64)
