@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -100,6 +101,9 @@ struct dtt_grid {
   double eps[3][3]{};
 
   // transforms
+  FftAxisInfo fft[3]{};
+  void* fft_tw[3]{};
+  void* fft_ph[3]{};
   void* fwd[3][3]{};
   void* inv[3][3]{};
   double* sin2q[3][3]{};
@@ -235,6 +239,51 @@ void build_axis(int type, int n, int nn, std::vector<double>& F, std::vector<dou
   }
 }
 
+// FFT plan of one axis: length L = 2n (n on a periodic axis) factored into radices 4, 2
+// and 3; axes whose length has another prime factor, or n < 4, keep the dense contraction.
+dtt_status build_fft_axis(dtt_grid* G, int d) {
+  FftAxisInfo& f = G->fft[d];
+  f = FftAxisInfo{};
+  const int n = G->g.nvox[d];
+  const int L = G->g.periodic[d] ? n : 2 * n;
+  if (n < 4 || std::getenv("DTT_DENSE_TRANSFORMS")) return DTT_OK;
+  int m = L, ns = 0;
+  int rad[12];
+  while (m % 4 == 0 && ns < 12) { rad[ns++] = 4; m /= 4; }
+  while (m % 2 == 0 && ns < 12) { rad[ns++] = 2; m /= 2; }
+  while (m % 3 == 0 && ns < 12) { rad[ns++] = 3; m /= 3; }
+  if (m != 1) return DTT_OK;
+  const double pi = 3.14159265358979323846;
+  const size_t csz = 2 * G->esz;
+  std::vector<double> tw(2 * (size_t)L), ph(2 * (size_t)(2 * n));
+  for (int q = 0; q < L; ++q) {
+    tw[2 * q] = std::cos(2.0 * pi * q / L);
+    tw[2 * q + 1] = -std::sin(2.0 * pi * q / L);
+  }
+  for (int j = 0; j < 2 * n; ++j) {
+    ph[2 * j] = std::cos(pi * j / (2.0 * n));
+    ph[2 * j + 1] = -std::sin(pi * j / (2.0 * n));
+  }
+  dtt_status s = dalloc(&G->fft_tw[d], (size_t)L * csz);
+  if (s == DTT_OK) s = dalloc(&G->fft_ph[d], (size_t)(2 * n) * csz);
+  if (s != DTT_OK) return s;
+  if (G->esz == 8) {
+    CK(cudaMemcpy(G->fft_tw[d], tw.data(), tw.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->fft_ph[d], ph.data(), ph.size() * 8, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> twf(tw.begin(), tw.end()), phf(ph.begin(), ph.end());
+    CK(cudaMemcpy(G->fft_tw[d], twf.data(), twf.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->fft_ph[d], phf.data(), phf.size() * 4, cudaMemcpyHostToDevice));
+  }
+  f.use = 1;
+  f.L = L;
+  f.nst = ns;
+  for (int q = 0; q < ns; ++q) f.radix[q] = rad[q];
+  f.tw = G->fft_tw[d];
+  f.ph = G->fft_ph[d];
+  return DTT_OK;
+}
+
 bool comp_has_null(const dtt_grid* G, int c) {
   bool all0 = true;
   int npi = 0;
@@ -296,9 +345,14 @@ dtt_status rebuild_cmask(dtt_grid* G) {
   return DTT_OK;
 }
 
+int res_blocks(const dtt_grid* G) {
+  return G->prec == DTT_PREC_FP64 ? residual_nblocks<double>(G->g) : residual_nblocks<float>(G->g);
+}
+
 dtt_status ensure_partials(dtt_grid* G) {
-  size_t need = 2 * (size_t)residual_blocks(G->g) + (size_t)(G->nrows + 255) / 256 + 1 +
-                4 * (size_t)contact_blocks(G->nface) + 4 + 4 * (size_t)acv_blocks(G->g) + 64;
+  size_t need = RES_STRIDE * (size_t)std::max(residual_blocks(G->g), residual_f32_blocks(G->g)) +
+                PROJ_STRIDE * ((size_t)(G->nrows + 255) / 256 + 1) + CONT_STRIDE * ((size_t)contact_blocks(G->nface) + 1) +
+                4 * (size_t)acv_blocks(G->g) + 64;
   if (need <= G->part_cap) return DTT_OK;
   dfree(G->d_part);
   dtt_status s = dalloc(&G->d_part, need * sizeof(double));
@@ -314,14 +368,14 @@ struct PartRegions {
 
 PartRegions regions(dtt_grid* G) {
   PartRegions r;
-  r.nres = residual_blocks(G->g);
+  r.nres = res_blocks(G);
   r.nproj = (G->nrows + 255) / 256;
   r.ncont = G->contact ? contact_blocks(G->nface) : 0;
   r.nacv = acv_blocks(G->g);
   r.res = G->d_part;
-  r.proj = r.res + 2 * r.nres;
-  r.cont = r.proj + r.nproj + 1;
-  r.acv = r.cont + 4 * r.ncont + 4;
+  r.proj = r.res + RES_STRIDE * r.nres;
+  r.cont = r.proj + PROJ_STRIDE * (r.nproj + 1);
+  r.acv = r.cont + CONT_STRIDE * (r.ncont + 1);
   return r;
 }
 
@@ -365,6 +419,9 @@ ContactArgs contact_args(dtt_grid* G, double* cont_part) {
 
 TransformTables tables(dtt_grid* G) {
   TransformTables t;
+  for (int d = 0; d < 3; ++d) t.fft[d] = G->fft[d];
+  for (int c = 0; c < 3; ++c)
+    for (int d = 0; d < 3; ++d) t.types[c][d] = G->types[c][d];
   for (int c = 0; c < 3; ++c)
     for (int d = 0; d < 3; ++d) {
       t.fwd[c][d] = G->fwd[c][d];
@@ -389,13 +446,40 @@ inline void prof_mark(int k, cudaStream_t s) {
 }
 
 // Green step (forward DT, Green multiply, inverse DT) of `in` (or of the ring slot
-// i % 4 when in_ring is given); the result lands in out.  With `increment` the result is
-// added to u~ and stored as the step.
+// i % 4 when in_ring is given); the result lands in out, or, with `increment`, is added to
+// u~ and stored as the step.  When the z axis takes the FFT route, the forward z transform,
+// the Green multiply and the inverse z transform run as one fused pass; when the x axis
+// takes it too, the increment is fused into the inverse x pass.
 template <typename T>
 dtt_status enqueue_green(dtt_grid* G, const T* in, void* const* in_ring, T* out, T* tmp, bool increment,
                          const Ctrl* ctrl, int comp0, int ncomp) {
   TransformTables tt = tables(G);
   cudaStream_t s = G->stream;
+  if (tt.fft[2].use) {
+    const bool alias = (in_ring == nullptr && (const void*)in == (const void*)out);
+    T* b1 = alias ? tmp : out;
+    T* b2 = alias ? out : tmp;
+    CKL(launch_transform_axis<T>(G->g, in, b1, tt, 0, 0, comp0, ncomp, ctrl, s, in_ring));
+    CKL(launch_transform_axis<T>(G->g, b1, b2, tt, 1, 0, comp0, ncomp, ctrl, s));
+    prof_mark(4, s);
+    CKL(launch_z_green<T>(G->g, b2, b1, tt, comp0, ncomp, ctrl, s));
+    prof_mark(5, s);
+    CKL(launch_transform_axis<T>(G->g, b1, b2, tt, 1, 1, comp0, ncomp, ctrl, s));
+    if (increment && tt.fft[0].use) {
+      IncrTarget it{G->u64, G->uhi, G->ulo, G->step};
+      CKL(launch_transform_axis<T>(G->g, b2, b1, tt, 0, 1, comp0, ncomp, ctrl, s, nullptr, &it));
+      prof_mark(6, s);
+      return DTT_OK;
+    }
+    CKL(launch_transform_axis<T>(G->g, b2, b1, tt, 0, 1, comp0, ncomp, ctrl, s));
+    prof_mark(6, s);
+    if (increment) {
+      CKL(launch_add_increment<T>(G->g, b1, G->u64, G->uhi, G->ulo, (T*)G->step, ctrl, s));
+    } else if (b1 != out) {
+      CK(cudaMemcpyAsync(out, b1, (size_t)3 * G->NN * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    }
+    return DTT_OK;
+  }
   CKL(launch_transform_axis<T>(G->g, in, tmp, tt, 0, 0, comp0, ncomp, ctrl, s, in_ring));
   CKL(launch_transform_axis<T>(G->g, tmp, out, tt, 1, 0, comp0, ncomp, ctrl, s));
   CKL(launch_transform_axis<T>(G->g, out, tmp, tt, 2, 0, comp0, ncomp, ctrl, s));
@@ -453,10 +537,11 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
   CKL(launch_residual<T>(ra, s));
   prof_mark(1, s);
   const int rm = diff ? 1 : 0;
+  const int fused = (diff && sizeof(T) == 4) ? 1 : 0;   // the FP32 residual kernel fuses the Gram row
   if (G->nrows > 0)
-    CKL(launch_proj_P_rows<T>(G->g, rows_dev(G), (T*)G->gbuf, G->d_Sring, G->d_Rring, rm, pr.proj, ctrl, s));
+    CKL(launch_proj_P_rows<T>(G->g, rows_dev(G), (T*)G->gbuf, G->d_Sring, G->d_Rring, rm, fused, pr.proj, ctrl, s));
   ContactArgs ca = contact_args(G, pr.cont);
-  if (G->contact) CKL(launch_contact_eval<T>(ca, (T*)G->gbuf, G->d_Sring, G->d_Rring, rm, s));
+  if (G->contact) CKL(launch_contact_eval<T>(ca, (T*)G->gbuf, G->d_Sring, G->d_Rring, rm, fused, s));
   CKL(launch_ctrl_residual(ctrl, pr.res, pr.nres, pr.proj, G->nrows > 0 ? pr.nproj : 0, pr.cont, pr.ncont, G->g.h,
                            G->NN, G->NV, s));
   if (G->contact) {
@@ -465,8 +550,12 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
   }
   prof_mark(2, s);
   if (diff) {
-    CKL(launch_acv_gram<T>(G->g, G->d_Rring, pr.acv, ctrl, s));
-    CKL(launch_ctrl_acv(ctrl, pr.acv, pr.nacv, s));
+    if (fused) {
+      CKL(launch_ctrl_acv_fused(ctrl, pr.res, pr.nres, pr.proj, G->nrows > 0 ? pr.nproj : 0, pr.cont, pr.ncont, s));
+    } else {
+      CKL(launch_acv_gram<T>(G->g, G->d_Rring, pr.acv, ctrl, s));
+      CKL(launch_ctrl_acv(ctrl, pr.acv, pr.nacv, s));
+    }
     CKL(launch_acv_green_input<T>(G->g, G->d_Sring, G->d_Gring, G->d_Rring, ctrl, s));
   }
   prof_mark(3, s);
@@ -688,6 +777,7 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
       cudaMemcpy(G->sin2q[c][d], cq.data(), cq.size() * 8, cudaMemcpyHostToDevice);
       cudaMemcpy(G->cos2q[c][d], cc.data(), cc.size() * 8, cudaMemcpyHostToDevice);
     }
+  for (int d = 0; d < 3 && s == DTT_OK; ++d) s = build_fft_axis(G, d);
   if (s == DTT_OK) {
     cudaError_t e = cudaMemcpy(G->d_Sring, G->S, 5 * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(G->d_Rring, G->R, 4 * sizeof(void*), cudaMemcpyHostToDevice);
@@ -736,6 +826,10 @@ void dtt_grid_destroy(dtt_grid* G) {
       dfree(G->sin2q[c][d]);
       dfree(G->cos2q[c][d]);
     }
+  for (int d = 0; d < 3; ++d) {
+    dfree(G->fft_tw[d]);
+    dfree(G->fft_ph[d]);
+  }
   free_rows(G);
   free_contact(G);
   if (G->h_ctrl) cudaFreeHost(G->h_ctrl);
@@ -1185,12 +1279,12 @@ dtt_status dtt_apply_residual(dtt_grid* G, const double* u, double* p, double* p
   if (p) { st = out(G->gbuf, p); if (st != DTT_OK) return st; }
   if (ptilde) { st = out(G->op_t2, ptilde); if (st != DTT_OK) return st; }
   if (norms) {
-    int nb = residual_blocks(G->g);
-    std::vector<double> part(2 * (size_t)nb);
+    int nb = res_blocks(G);
+    std::vector<double> part(RES_STRIDE * (size_t)nb);
     CK(cudaMemcpyAsync(part.data(), G->d_part, part.size() * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     double a0 = 0.0, a1 = 0.0;
-    for (int b = 0; b < nb; ++b) { a0 += part[2 * b]; a1 += part[2 * b + 1]; }
+    for (int b = 0; b < nb; ++b) { a0 += part[RES_STRIDE * b]; a1 += part[RES_STRIDE * b + 1]; }
     norms[0] = a0;
     norms[1] = a1;
   }

@@ -132,11 +132,55 @@ struct ResidualArgs {
   const Ctrl* ctrl;       // if non-null: skip when done (mode 1 needs it)
   int zchunk;             // z planes per CTA (set by the launcher)
 };
+// Residual partial sums: 6 doubles per CTA [w sigma:sigma, p^2, Gram 0..3] (the FP64
+// kernel leaves the Gram entries 0; the FP32 kernel fills them in the Anderson mode).
+constexpr int RES_STRIDE = 6;
 template <typename T> int launch_residual(const ResidualArgs& a, cudaStream_t s);
 int residual_blocks(const GridDev& g);
 int residual_zchunk(const GridDev& g);
+int launch_residual_f32(const ResidualArgs& a, cudaStream_t s);
+int residual_f32_blocks(const GridDev& g);
+template <typename T> int residual_nblocks(const GridDev& g) {
+  return sizeof(T) == 4 ? residual_f32_blocks(g) : residual_blocks(g);
+}
+
+// FFT route of one axis (shared by the three components: same length, per-component type).
+struct FftAxisInfo {
+  int use;                 // 1: FFT route; 0: dense contraction
+  int L;                   // FFT length (2n, or n on a periodic axis)
+  int nst;                 // number of Stockham stages
+  int radix[12];
+  const void* tw;          // L complex twiddles e^{-2 pi i m / L} (field precision)
+  const void* ph;          // 2n complex e^{-i pi j / 2n} (quarter-wave types)
+};
+struct FftParams {
+  int axis, n, nn, L, nst;
+  int radix[12];
+  const void* tw;
+  const void* ph;
+  int type[3];
+  int inverse;
+  double scale;
+  int comp0;
+  int nnx, nny;
+  long long npencil, NN;
+  int incr;                // inverse x pass: add the result to u~ and store it as the step
+  double* u64;
+  float* uhi;
+  float* ulo;
+  void* step;
+};
+template <typename T>
+int launch_fft_axis(const T* in, T* out, const FftParams& p, int ncomp, const Ctrl* ctrl, void* const* in_ring,
+                    cudaStream_t s);
+struct GreenTables;
+template <typename T>
+int launch_fft_z_green(const T* in, T* out, const FftParams& p, const GreenTables& gt, double lam0, double mu0,
+                       int scheme, double h, int ncomp, const Ctrl* ctrl, cudaStream_t s);
 
 struct TransformTables {
+  FftAxisInfo fft[3];
+  int types[3][3];         // [comp][axis]
   const void* fwd[3][3];   // [comp][axis] nn x nn row-major (spectral k, node j)
   const void* inv[3][3];   // [comp][axis] nn x nn row-major (node j, spectral k)
   const double* sin2q[3][3];   // sin^2(q_k / 2) at every spectral position (0 unused)
@@ -149,10 +193,20 @@ struct GreenTables {
   const double* cp[3][3];
   double null_thr[3];
 };
+struct IncrTarget {
+  double* u64;
+  float* uhi;
+  float* ulo;
+  void* step;
+};
 template <typename T>
 int launch_transform_axis(const GridDev& g, const T* in, T* out, const TransformTables& tt,
                           int axis, int inverse, int ncomp_first, int ncomp, const Ctrl* ctrl,
-                          cudaStream_t s, void* const* in_ring = nullptr);
+                          cudaStream_t s, void* const* in_ring = nullptr, const IncrTarget* incr = nullptr);
+// fused forward z DTT + Green multiply + inverse z DTT (FFT route on z only)
+template <typename T>
+int launch_z_green(const GridDev& g, const T* in, T* out, const TransformTables& tt, int ncomp_first, int ncomp,
+                   const Ctrl* ctrl, cudaStream_t s);
 template <typename T>
 int launch_green_multiply(const GridDev& g, T* spec, const TransformTables& tt, int scheme,
                           const Ctrl* ctrl, cudaStream_t s);
@@ -161,10 +215,13 @@ int launch_add_increment(const GridDev& g, const T* delta, double* u64, float* u
                          T* step_out, const Ctrl* ctrl, cudaStream_t s);
 
 // p: either p_direct, or (ring mode) p ring slot i % 4 with the same shifts applied to
-// the Anderson residual slot (i-1) % 4 when i > 0.
+// the Anderson residual slot (i-1) % 4 when i > 0.  With gram = 1 the kernel also adds the
+// Gram-row contributions of its DOFs (partials: 5 per block [p^2, Gram 0..3]).
+constexpr int PROJ_STRIDE = 5;
+constexpr int CONT_STRIDE = 8;   // [p^2, n_vgap, n_vreact, mismatches, Gram 0..3]
 template <typename T>
 int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p_direct, void* const* pring,
-                       void* const* rring, int ring_mode, double* partials, const Ctrl* ctrl,
+                       void* const* rring, int ring_mode, int gram, double* partials, const Ctrl* ctrl,
                        cudaStream_t s);
 template <typename T>
 int launch_proj_U_rows(const GridDev& g, const RowsDev& r, double* u64, float* uhi, float* ulo,
@@ -182,7 +239,7 @@ struct ContactArgs {
 };
 template <typename T>
 int launch_contact_eval(const ContactArgs& a, T* p_direct, void* const* pring, void* const* rring,
-                        int ring_mode, cudaStream_t s);
+                        int ring_mode, int gram, cudaStream_t s);
 int launch_contact_update(const ContactArgs& a, cudaStream_t s);
 template <typename T>
 int launch_contact_proj_U(const ContactArgs& a, double* u64, float* uhi, float* ulo, T* step,
@@ -213,6 +270,10 @@ int launch_ctrl_residual(Ctrl* c, const double* rp, int nres, const double* pp, 
                          int ncont, double h, long long nnodes, long long nvox, cudaStream_t s);
 int launch_ctrl_contact(Ctrl* c, cudaStream_t s);
 int launch_ctrl_acv(Ctrl* c, const double* partials, int nblk, cudaStream_t s);
+// Gram row from the fused sources: residual (RES_STRIDE, offset 2), projections
+// (PROJ_STRIDE, offset 1), contact (CONT_STRIDE, offset 4)
+int launch_ctrl_acv_fused(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, const double* cp,
+                          int ncont, cudaStream_t s);
 int launch_ctrl_end(Ctrl* c, cudaStream_t s);
 
 // utilities (k_util.cu)

@@ -1,0 +1,419 @@
+// Fast per-axis DTTs: two real pencils of the same component and axis packed into one
+// complex sequence, one shared-memory Stockham FFT (radices 4, 2, 3), and type-specific
+// pre/post-processing.  O(n log n) per pencil instead of the O(n^2) dense contraction.
+//
+// With z = a + i b (a, b two real pencils, node values x_j) and L the FFT length:
+//   DCT1 (L = 2n): even extension y_j = z_j, y_{2n-j} = z_j;  X_a = Re Y / 2, X_b = Im Y / 2.
+//   DST1 (L = 2n): odd extension, y_0 = y_n = 0;             X_a = -Im Y / 2, X_b = Re Y / 2.
+//   DCT3 (L = 2n): odd extension about n, y_n = 0, times e^{-i pi j / 2n}; Re / Im as DCT1.
+//   DST3 (L = 2n): even extension about n, y_0 = 0, times e^{-i pi j / 2n}; as DST1.
+//   Hartley (L = n, periodic axis): H_a = (u + u' - v + v') / 2, H_b = (u - u' + v + v') / 2
+//     with Y_k = u + i v, Y_{(n-k) mod n} = u' + i v'.
+// (Y = DFT of the extended sequence; e.g. the DFT of the even extension is 2 X for DCT1, and
+// the modulated quarter-wave extensions give 2 X exactly, so the pair separates without
+// further work.)  The inverses of DCT1, DST1 and the Hartley transform are the forward
+// formulas times 2/n (1/n); the inverses of DCT3 / DST3 take the length-2n unnormalised
+// inverse DFT of X extended as X_{2n-1-k} = +-X_k and read x_j from e^{+i pi j / 2n} Z_j / n.
+// These follow from the trigonometric sums of the transforms (Section 3.2.2, Tables 2-3);
+// the 4n-extended DFT of Eq. 7 is the same idea with the redundant half removed.
+#include "dtt_internal.cuh"
+
+namespace dtt {
+
+template <typename T> struct Cx { T x, y; };
+
+template <typename T>
+__device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+// R-point DFT in registers, sign s = -1 (forward) or +1 (inverse, unnormalised).
+template <typename T>
+__device__ __forceinline__ void dft2(Cx<T>* v) {
+  Cx<T> a = v[0], b = v[1];
+  v[0] = {a.x + b.x, a.y + b.y};
+  v[1] = {a.x - b.x, a.y - b.y};
+}
+template <typename T>
+__device__ __forceinline__ void dft4(Cx<T>* v, int s) {
+  Cx<T> a = {v[0].x + v[2].x, v[0].y + v[2].y}, b = {v[0].x - v[2].x, v[0].y - v[2].y};
+  Cx<T> c = {v[1].x + v[3].x, v[1].y + v[3].y}, d = {v[1].x - v[3].x, v[1].y - v[3].y};
+  // w d with w = s i:  s (-d.y + i d.x)
+  Cx<T> wd = {(T)(-s) * d.y, (T)s * d.x};
+  v[0] = {a.x + c.x, a.y + c.y};
+  v[2] = {a.x - c.x, a.y - c.y};
+  v[1] = {b.x + wd.x, b.y + wd.y};
+  v[3] = {b.x - wd.x, b.y - wd.y};
+}
+template <typename T>
+__device__ __forceinline__ void dft3(Cx<T>* v, int s) {
+  const T c = (T)-0.5, sn = (T)s * (T)0.86602540378443864676;
+  Cx<T> t1 = {v[1].x + v[2].x, v[1].y + v[2].y}, t2 = {v[1].x - v[2].x, v[1].y - v[2].y};
+  Cx<T> m = {v[0].x + c * t1.x, v[0].y + c * t1.y};
+  // i sn t2 = (-sn t2.y, sn t2.x)
+  v[0] = {v[0].x + t1.x, v[0].y + t1.y};
+  v[1] = {m.x - sn * t2.y, m.y + sn * t2.x};
+  v[2] = {m.x + sn * t2.y, m.y - sn * t2.x};
+}
+
+// One Stockham stage of radix R for all PB sequences of the CTA (registers only).
+template <typename T, int R>
+__device__ __forceinline__ void stockham_stage(const Cx<T>* __restrict__ S, Cx<T>* __restrict__ D, int L, int Ns,
+                                               int PBL, const Cx<T>* __restrict__ tw, int sgn, int tid, int nthr) {
+  const int LR = L / R;
+  const int twstep = L / (Ns * R);
+  for (int idx = tid; idx < PBL / R; idx += nthr) {
+    const int q = idx / LR, jb = idx - q * LR;
+    const int k = jb % Ns;
+    const Cx<T>* Sq = S + q * L;
+    Cx<T>* Dq = D + q * L;
+    Cx<T> v[R];
+    #pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = Sq[jb + r * LR];
+    #pragma unroll
+    for (int r = 1; r < R; ++r) {
+      Cx<T> w = tw[k * r * twstep];   // k r twstep < L
+      if (sgn > 0) w.y = -w.y;
+      v[r] = cmul(v[r], w);
+    }
+    if constexpr (R == 4) dft4(v, sgn);
+    else if constexpr (R == 2) dft2(v);
+    else dft3(v, sgn);
+    const int o = (jb - k) * R + k;
+    #pragma unroll
+    for (int r = 0; r < R; ++r) Dq[o + r * Ns] = v[r];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T tetra_S(T sa, T cb, T sb, T cA, T sc) {
+  const T d = (sa + sb < (T)1) ? (sb - sa) : (cA - cb);
+  return sa * cb + sc * d;
+}
+
+// ---- building blocks of one CTA's work on PB pencil pairs --------------------------------
+
+// Extended (and, for quarter-wave forward types, modulated) complex sequences of the CTA
+// in A, from values get(pb, j) of pencil pb (0..2PB-1) at axis position j (0..nn-1).
+template <typename T, int PB, typename Get>
+__device__ __forceinline__ void fill_sequences(Cx<T>* A, int L, int n, int nn, int type, int inverse, int npen,
+                                               const Cx<T>* ph, Get get, int tid, int nthr) {
+  const bool quarter = (type == T_DCT3 || type == T_DST3);
+  for (int q = tid; q < PB; q += nthr) {
+    Cx<T>* S = A + q * L;
+    if (!inverse || !quarter) {
+      if (type == T_DST1) { S[0] = {(T)0, (T)0}; S[n] = {(T)0, (T)0}; }
+      else if (type == T_DCT3) S[n] = {(T)0, (T)0};
+      else if (type == T_DST3) S[0] = {(T)0, (T)0};
+    }
+  }
+  if (npen < 2 * PB)
+    for (int q = tid; q < PB * L; q += nthr) A[q] = {(T)0, (T)0};
+  __syncthreads();
+  for (int idx = tid; idx < 2 * PB * nn; idx += nthr) {
+    const int pb = idx % (2 * PB), j = idx / (2 * PB);
+    if (pb >= npen) continue;
+    const T v = get(pb, j);
+    Cx<T>* S = A + (pb >> 1) * L;
+    const bool im = pb & 1;
+    auto put = [&](int pos, T val) {
+      if (im) S[pos].y = val; else S[pos].x = val;
+    };
+    if (!inverse || !quarter) {
+      switch (type) {
+        case T_DCT1:
+          put(j, v);
+          if (j >= 1 && j <= n - 1) put(2 * n - j, v);
+          break;
+        case T_DST1:
+          if (j >= 1 && j <= n - 1) { put(j, v); put(2 * n - j, -v); }
+          break;
+        case T_DCT3:
+          if (j <= n - 1) { put(j, v); if (j >= 1) put(2 * n - j, -v); }
+          break;
+        case T_DST3:
+          if (j >= 1) { put(j, v); if (j <= n - 1) put(2 * n - j, v); }
+          break;
+        default:
+          put(j, v);
+          break;
+      }
+    } else if (j < n) {
+      put(j, v);
+      put(2 * n - 1 - j, type == T_DCT3 ? v : -v);
+    }
+  }
+  __syncthreads();
+  if (quarter && !inverse) {
+    for (int q = tid; q < PB * L; q += nthr) A[q] = cmul(A[q], ph[q % L]);
+    __syncthreads();
+  }
+}
+
+// Stockham FFT of the PB sequences; returns the buffer holding the result.
+template <typename T, int PB>
+__device__ __forceinline__ Cx<T>* fft_sequences(Cx<T>* s0, Cx<T>* s1, const FftParams& p, const Cx<T>* tw, int sgn,
+                                                int tid, int nthr) {
+  int Ns = 1;
+  for (int st = 0; st < p.nst; ++st) {
+    const int R = p.radix[st];
+    if (R == 4) stockham_stage<T, 4>(s0, s1, p.L, Ns, PB * p.L, tw, sgn, tid, nthr);
+    else if (R == 2) stockham_stage<T, 2>(s0, s1, p.L, Ns, PB * p.L, tw, sgn, tid, nthr);
+    else stockham_stage<T, 3>(s0, s1, p.L, Ns, PB * p.L, tw, sgn, tid, nthr);
+    __syncthreads();
+    Cx<T>* t = s0;
+    s0 = s1;
+    s1 = t;
+    Ns *= R;
+  }
+  return s0;
+}
+
+// Transform value of pencil pb at spectral / node position k from the FFT result Y.
+template <typename T>
+__device__ __forceinline__ T post_value(const Cx<T>* Yall, int L, int n, int type, int inverse, T sc, const Cx<T>* ph,
+                                        int pb, int k) {
+  const Cx<T>* Y = Yall + (pb >> 1) * L;
+  const bool im = pb & 1;
+  const T half = (T)0.5;
+  const bool quarter = (type == T_DCT3 || type == T_DST3);
+  if (!inverse || !quarter) {
+    T val = (T)0;
+    switch (type) {
+      case T_DCT1:
+        val = im ? half * Y[k].y : half * Y[k].x;
+        break;
+      case T_DST1:
+        if (k >= 1 && k <= n - 1) val = im ? half * Y[k].x : -half * Y[k].y;
+        break;
+      case T_DCT3:
+        if (k <= n - 1) val = im ? half * Y[k].y : half * Y[k].x;
+        break;
+      case T_DST3:
+        if (k <= n - 1) val = im ? half * Y[k].x : -half * Y[k].y;
+        break;
+      default: {
+        const Cx<T> a = Y[k], b = Y[k == 0 ? 0 : n - k];
+        val = im ? half * (a.x - b.x + a.y + b.y) : half * (a.x + b.x - a.y + b.y);
+        break;
+      }
+    }
+    return val * sc;
+  }
+  const Cx<T> w = {ph[k].x, -ph[k].y};
+  const Cx<T> e = cmul(Y[k], w);
+  const T inv_n = (T)1 / (T)n;
+  if (type == T_DCT3) return (k <= n - 1) ? (im ? e.y : e.x) * inv_n : (T)0;
+  return (k >= 1) ? (im ? -e.x : e.y) * inv_n : (T)0;
+}
+
+template <typename T, int PB>
+__device__ __forceinline__ void pencil_bases(long long* sbase, const FftParams& p, long long pen0, int tid) {
+  if (tid < 2 * PB) {
+    const long long pen = pen0 + tid;
+    long long b = 0;
+    if (pen < p.npencil) {
+      if (p.axis == 0) b = pen * p.nnx;
+      else if (p.axis == 1) b = (pen / p.nnx) * (long long)p.nnx * p.nny + (pen % p.nnx);
+      else b = pen;
+    }
+    sbase[tid] = b;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void add_to_u(long long e, T val, const FftParams& p) {
+  if constexpr (sizeof(T) == 8) {
+    p.u64[e] += (double)val;
+  } else {
+    float h = p.uhi[e], l = p.ulo[e];
+    ff_add(h, l, (float)val);
+    p.uhi[e] = h;
+    p.ulo[e] = l;
+  }
+  ((T*)p.step)[e] = val;
+}
+
+// One axis pass: forward or inverse DTT of every pencil along p.axis.  With p.incr (inverse
+// x pass), the result is added to u~ and written as the step instead of to `out`.
+template <typename T, int PB>
+__global__ void __launch_bounds__(256)
+k_fft_axis(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctrl* ctrl, void* const* in_ring) {
+  if (ctrl && ctrl->done) return;
+  if (in_ring) in = (const T*)in_ring[ctrl->i_local % 4];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long sbase[2 * PB];
+  Cx<T>* bufA = (Cx<T>*)smem_raw;
+  Cx<T>* bufB = bufA + PB * p.L;
+  const Cx<T>* tw = (const Cx<T>*)p.tw;
+  const Cx<T>* ph = (const Cx<T>*)p.ph;
+  const int comp = p.comp0 + blockIdx.y;
+  const int type = p.type[comp];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const long long pen0 = (long long)blockIdx.x * (2 * PB);
+  const T* src = in + (long long)comp * p.NN;
+  const long long coff = (long long)comp * p.NN;
+  const long long stride = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)p.nnx : (long long)p.nnx * p.nny);
+  const int npen = (int)min((long long)(2 * PB), p.npencil - pen0);
+  pencil_bases<T, PB>(sbase, p, pen0, tid);
+  __syncthreads();
+  fill_sequences<T, PB>(bufA, p.L, p.n, p.nn, type, p.inverse, npen, ph,
+                        [&](int pb, int j) { return src[sbase[pb] + j * stride]; }, tid, nthr);
+  const bool quarter = (type == T_DCT3 || type == T_DST3);
+  const int sgn = (p.inverse && quarter) ? 1 : -1;
+  Cx<T>* Y = fft_sequences<T, PB>(bufA, bufB, p, tw, sgn, tid, nthr);
+  const T sc = (T)p.scale;
+  for (int idx = tid; idx < 2 * PB * p.nn; idx += nthr) {
+    const int pb = idx % (2 * PB), k = idx / (2 * PB);
+    if (pb >= npen) continue;
+    const T v = post_value<T>(Y, p.L, p.n, type, p.inverse, sc, ph, pb, k);
+    const long long e = coff + sbase[pb] + k * stride;
+    if (p.incr) add_to_u<T>(e, v, p);
+    else out[e] = v;
+  }
+}
+
+// Fused z pass: forward DTT along z, Green multiply (Eq. 4 adapted to the Paux reference,
+// Section 3.2.3), inverse DTT along z, for pencils whose x and y spectra are already taken.
+template <typename T, int PB>
+__global__ void __launch_bounds__(256)
+k_fft_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenTables gt, double lam0, double mu0,
+              int scheme, double h, const Ctrl* ctrl) {
+  if (ctrl && ctrl->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long sbase[2 * PB];
+  Cx<T>* bufA = (Cx<T>*)smem_raw;
+  Cx<T>* bufB = bufA + PB * p.L;
+  const Cx<T>* tw = (const Cx<T>*)p.tw;
+  const Cx<T>* ph = (const Cx<T>*)p.ph;
+  const int comp = p.comp0 + blockIdx.y;
+  const int type = p.type[comp];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const long long pen0 = (long long)blockIdx.x * (2 * PB);
+  const long long coff = (long long)comp * p.NN;
+  const long long stride = (long long)p.nnx * p.nny;
+  const int npen = (int)min((long long)(2 * PB), p.npencil - pen0);
+  const int nn = p.nn;
+  pencil_bases<T, PB>(sbase, p, pen0, tid);
+  __syncthreads();
+  const bool quarter = (type == T_DCT3 || type == T_DST3);
+  // forward along z
+  fill_sequences<T, PB>(bufA, p.L, p.n, nn, type, 0, npen, ph,
+                        [&](int pb, int j) { return in[coff + sbase[pb] + j * stride]; }, tid, nthr);
+  Cx<T>* Y = fft_sequences<T, PB>(bufA, bufB, p, tw, -1, tid, nthr);
+  Cx<T>* I = (Y == bufA) ? bufB : bufA;
+  T* spec = (T*)I;   // 2 PB x nn real spectra (fits in one complex buffer)
+  const T ih2 = (T)(4.0 / (h * h));
+  const T l0 = (T)lam0, m2 = (T)(2.0 * mu0), thr = (T)gt.null_thr[comp];
+  for (int idx = tid; idx < 2 * PB * nn; idx += nthr) {
+    const int pb = idx % (2 * PB), k = idx / (2 * PB);
+    T v = (T)0;
+    if (pb < npen) {
+      v = post_value<T>(Y, p.L, p.n, type, 0, (T)1, ph, pb, k);
+      const long long b = sbase[pb];
+      const int ix = (int)(b % p.nnx), iy = (int)(b / p.nnx);
+      const T sx = (T)gt.s[comp][0][ix], sy = (T)gt.s[comp][1][iy], sz = (T)gt.s[comp][2][k];
+      const T cx = (T)gt.cp[comp][0][ix], cy = (T)gt.cp[comp][1][iy], cz = (T)gt.cp[comp][2][k];
+      T Sx, Sy, Sz;
+      if (scheme == SCHEME_TETRA2) {
+        Sx = tetra_S<T>(sx, cy, sy, cx, sz);
+        Sy = tetra_S<T>(sy, cz, sz, cy, sx);
+        Sz = tetra_S<T>(sz, cx, sx, cz, sy);
+      } else {
+        Sx = sx * cy * cz;
+        Sy = sy * cx * cz;
+        Sz = sz * cx * cy;
+      }
+      const T Sc = comp == 0 ? Sx : (comp == 1 ? Sy : Sz);
+      const T a = (l0 * Sc + m2 * (Sx + Sy + Sz)) * ih2;
+      v = (a <= thr) ? (T)0 : v / a;
+    }
+    spec[pb * nn + k] = v;
+  }
+  __syncthreads();
+  // inverse along z
+  Cx<T>* X = Y;
+  fill_sequences<T, PB>(X, p.L, p.n, nn, type, 1, npen, ph, [&](int pb, int j) { return spec[pb * nn + j]; }, tid,
+                        nthr);
+  Y = fft_sequences<T, PB>(X, I, p, tw, quarter ? 1 : -1, tid, nthr);
+  const T sc = (T)((p.L == p.n) ? 1.0 / p.n : 2.0 / p.n);   // Hartley 1/n, DCT1 / DST1 2/n
+  for (int idx = tid; idx < 2 * PB * nn; idx += nthr) {
+    const int pb = idx % (2 * PB), k = idx / (2 * PB);
+    if (pb >= npen) continue;
+    out[coff + sbase[pb] + k * stride] = post_value<T>(Y, p.L, p.n, type, 1, sc, ph, pb, k);
+  }
+}
+
+template <typename T>
+int fft_pb(int L) {
+  // pairs per CTA: two buffers of PB * L complex values within ~100 KB of shared memory
+  const int bytes = 2 * L * (int)sizeof(Cx<T>);
+  int pb = 102400 / bytes;
+  if (pb >= 8) return 8;
+  if (pb >= 4) return 4;
+  if (pb >= 2) return 2;
+  return pb >= 1 ? 1 : 0;
+}
+
+template <typename T, int PB>
+static int launch_fft_pb(const T* in, T* out, const FftParams& p, int ncomp, const Ctrl* ctrl, void* const* in_ring,
+                         cudaStream_t s) {
+  dim3 grd((unsigned)((p.npencil + 2 * PB - 1) / (2 * PB)), ncomp);
+  size_t sm = (size_t)2 * PB * p.L * sizeof(Cx<T>);
+  static int attr_done = 0;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_axis<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
+    if (e != cudaSuccess) return (int)e;
+    attr_done = 1;
+  }
+  k_fft_axis<T, PB><<<grd, 256, sm, s>>>(in, out, p, ctrl, in_ring);
+  return (int)cudaGetLastError();
+}
+
+template <typename T, int PB>
+static int launch_zg_pb(const T* in, T* out, const FftParams& p, const GreenTables& gt, double lam0, double mu0,
+                        int scheme, double h, int ncomp, const Ctrl* ctrl, cudaStream_t s) {
+  dim3 grd((unsigned)((p.npencil + 2 * PB - 1) / (2 * PB)), ncomp);
+  size_t sm = (size_t)2 * PB * p.L * sizeof(Cx<T>);
+  static int attr_done = 0;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_z_green<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
+    if (e != cudaSuccess) return (int)e;
+    attr_done = 1;
+  }
+  k_fft_z_green<T, PB><<<grd, 256, sm, s>>>(in, out, p, gt, lam0, mu0, scheme, h, ctrl);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_fft_z_green(const T* in, T* out, const FftParams& p, const GreenTables& gt, double lam0, double mu0,
+                       int scheme, double h, int ncomp, const Ctrl* ctrl, cudaStream_t s) {
+  switch (fft_pb<T>(p.L)) {
+    case 8: return launch_zg_pb<T, 8>(in, out, p, gt, lam0, mu0, scheme, h, ncomp, ctrl, s);
+    case 4: return launch_zg_pb<T, 4>(in, out, p, gt, lam0, mu0, scheme, h, ncomp, ctrl, s);
+    case 2: return launch_zg_pb<T, 2>(in, out, p, gt, lam0, mu0, scheme, h, ncomp, ctrl, s);
+    case 1: return launch_zg_pb<T, 1>(in, out, p, gt, lam0, mu0, scheme, h, ncomp, ctrl, s);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+int launch_fft_axis(const T* in, T* out, const FftParams& p, int ncomp, const Ctrl* ctrl, void* const* in_ring,
+                    cudaStream_t s) {
+  switch (fft_pb<T>(p.L)) {
+    case 8: return launch_fft_pb<T, 8>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 4: return launch_fft_pb<T, 4>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 2: return launch_fft_pb<T, 2>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 1: return launch_fft_pb<T, 1>(in, out, p, ncomp, ctrl, in_ring, s);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+template int launch_fft_axis<double>(const double*, double*, const FftParams&, int, const Ctrl*, void* const*, cudaStream_t);
+template int launch_fft_axis<float>(const float*, float*, const FftParams&, int, const Ctrl*, void* const*, cudaStream_t);
+template int launch_fft_z_green<double>(const double*, double*, const FftParams&, const GreenTables&, double, double, int, double, int, const Ctrl*, cudaStream_t);
+template int launch_fft_z_green<float>(const float*, float*, const FftParams&, const GreenTables&, double, double, int, double, int, const Ctrl*, cudaStream_t);
+template int fft_pb<double>(int);
+template int fft_pb<float>(int);
+
+}  // namespace dtt

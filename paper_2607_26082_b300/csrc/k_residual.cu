@@ -365,8 +365,10 @@ k_residual(ResidualArgs a) {
     double s = 0.0, p = 0.0;
     for (int w = 0; w < RTX * RTY / 32; ++w) { s += sRed[0][w]; p += sRed[1][w]; }
     long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-    a.partials[2 * b] = s;
-    a.partials[2 * b + 1] = p;
+    double* o = a.partials + RES_STRIDE * b;
+    o[0] = s;
+    o[1] = p;
+    for (int q = 2; q < RES_STRIDE; ++q) o[q] = 0.0;
   }
 }
 
@@ -415,9 +417,12 @@ static int launch_res_impl(const ResidualArgs& a, cudaStream_t s) {
 
 template <typename T>
 int launch_residual(const ResidualArgs& a, cudaStream_t s) {
-  constexpr bool MIX = sizeof(T) == 4;
-  if (a.g.scheme == SCHEME_TETRA2) return launch_res_impl<T, MIX, SCHEME_TETRA2>(a, s);
-  return launch_res_impl<T, MIX, SCHEME_HEX1>(a, s);
+  if constexpr (sizeof(T) == 4) {
+    return launch_residual_f32(a, s);   // thread-per-node FP32 kernel (k_residual_f32.cu)
+  } else {
+    if (a.g.scheme == SCHEME_TETRA2) return launch_res_impl<T, false, SCHEME_TETRA2>(a, s);
+    return launch_res_impl<T, false, SCHEME_HEX1>(a, s);
+  }
 }
 
 template int launch_residual<double>(const ResidualArgs&, cudaStream_t);

@@ -79,14 +79,24 @@ __device__ __forceinline__ void pick_p(const Ctrl* ctrl, int ring_mode, T* p_dir
   }
 }
 
+// Gram-row contributions <R_new, R_k> of one DOF (fused Gram mode).
+template <typename T>
+__device__ __forceinline__ void gram_add(double* G, void* const* rring, int rslot, long long d) {
+  const double rn = (double)((const T*)rring[rslot])[d];
+  #pragma unroll
+  for (int q = 0; q < 4; ++q) G[q] += rn * (q == rslot ? rn : (double)((const T*)rring[q])[d]);
+}
+
 template <typename T>
 __global__ void k_proj_P(const RowsDev r, T* p_direct, void* const* pring, void* const* rring, int ring_mode,
-                         double* partials, const Ctrl* ctrl) {
+                         int gram, double* partials, const Ctrl* ctrl) {
   __shared__ double sh[SB / 32];
   if (ctrl && ctrl->done) return;
   T *p, *x;
   pick_p<T>(ctrl, ring_mode, p_direct, pring, rring, p, x);
+  const int rslot = (ring_mode && ctrl->i_local > 0) ? (ctrl->i_local - 1) % 4 : -1;
   double acc = 0.0;
+  double G[4] = {0, 0, 0, 0};
   int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row < r.nrows) {
     double sap = 0.0;
@@ -99,20 +109,25 @@ __global__ void k_proj_P(const RowsDev r, T* p_direct, void* const* pring, void*
       p[d] = (T)pn;
       if (x) x[d] = (T)((double)x[d] - sh_);
       acc += (double)(T)pn * (double)(T)pn;
+      if (gram && rslot >= 0) gram_add<T>(G, rring, rslot, d);
     }
     r.mult[row] = -lam;
   }
   double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  if (threadIdx.x == 0) partials[PROJ_STRIDE * blockIdx.x] = t;
+  for (int q = 0; q < 4; ++q) {
+    double tq = block_sum(G[q], sh);
+    if (threadIdx.x == 0) partials[PROJ_STRIDE * blockIdx.x + 1 + q] = tq;
+  }
 }
 
 template <typename T>
 int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p_direct, void* const* pring, void* const* rring,
-                       int ring_mode, double* partials, const Ctrl* ctrl, cudaStream_t s) {
+                       int ring_mode, int gram, double* partials, const Ctrl* ctrl, cudaStream_t s) {
   (void)g;
   int blocks = (r.nrows + SB - 1) / SB;
   if (blocks == 0) return 0;
-  k_proj_P<T><<<blocks, SB, 0, s>>>(r, p_direct, pring, rring, ring_mode, partials, ctrl);
+  k_proj_P<T><<<blocks, SB, 0, s>>>(r, p_direct, pring, rring, ring_mode, gram, partials, ctrl);
   return (int)cudaGetLastError();
 }
 
@@ -168,11 +183,13 @@ __device__ void contact_geom(const ContactArgs& a, long long n, double Mp[3], do
 
 template <typename T>
 __global__ void k_contact_eval(const ContactArgs a, T* p_direct, void* const* pring, void* const* rring,
-                               int ring_mode) {
+                               int ring_mode, int gram) {
   __shared__ double sh[SB / 32];
   if (a.ctrl && a.ctrl->done) return;
   T *p, *x;
   pick_p<T>(a.ctrl, ring_mode, p_direct, pring, rring, p, x);
+  const int rslot = (ring_mode && a.ctrl->i_local > 0) ? (a.ctrl->i_local - 1) % 4 : -1;
+  double G[4] = {0, 0, 0, 0};
   double p2 = 0.0, ng = 0.0, nr = 0.0, mm = 0.0;
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < a.c.nnodes_face) {
@@ -204,6 +221,9 @@ __global__ void k_contact_eval(const ContactArgs a, T* p_direct, void* const* pr
       }
     }
     for (int c = 0; c < 3; ++c) p2 += pv[c] * pv[c];
+    if (gram && rslot >= 0)
+      for (int c = 0; c < 3; ++c)
+        if (dof[c]) gram_add<T>(G, rring, rslot, (long long)c * a.g.nnodes + n);
     uint8_t vg = (!act && gap < 0.0) ? 1 : 0;
     uint8_t vr = (act && f > 0.0) ? 1 : 0;
     if (vg != a.c.vgap_prev[q] || vr != a.c.vreact_prev[q]) mm = 1.0;
@@ -220,19 +240,23 @@ __global__ void k_contact_eval(const ContactArgs a, T* p_direct, void* const* pr
   double t2 = block_sum(nr, sh);
   double t3 = block_sum(mm, sh);
   if (threadIdx.x == 0) {
-    a.partials[4 * blockIdx.x] = t0;
-    a.partials[4 * blockIdx.x + 1] = t1;
-    a.partials[4 * blockIdx.x + 2] = t2;
-    a.partials[4 * blockIdx.x + 3] = t3;
+    a.partials[CONT_STRIDE * blockIdx.x] = t0;
+    a.partials[CONT_STRIDE * blockIdx.x + 1] = t1;
+    a.partials[CONT_STRIDE * blockIdx.x + 2] = t2;
+    a.partials[CONT_STRIDE * blockIdx.x + 3] = t3;
+  }
+  for (int q = 0; q < 4; ++q) {
+    double tq = block_sum(G[q], sh);
+    if (threadIdx.x == 0) a.partials[CONT_STRIDE * blockIdx.x + 4 + q] = tq;
   }
 }
 
 template <typename T>
 int launch_contact_eval(const ContactArgs& a, T* p_direct, void* const* pring, void* const* rring, int ring_mode,
-                        cudaStream_t s) {
+                        int gram, cudaStream_t s) {
   int blocks = contact_blocks(a.c.nnodes_face);
   if (blocks == 0) return 0;
-  k_contact_eval<T><<<blocks, SB, 0, s>>>(a, p_direct, pring, rring, ring_mode);
+  k_contact_eval<T><<<blocks, SB, 0, s>>>(a, p_direct, pring, rring, ring_mode, gram);
   return (int)cudaGetLastError();
 }
 
@@ -499,7 +523,7 @@ int launch_acv_accel(const GridDev& g, int acv_on, void* const* Sring, void* con
 
 // ------------------------------------------------------------------ control
 // Deterministic reduction of partial sums: fixed strided order + fixed tree.
-__device__ double reduce_fixed(const double* v, int n, int stride, int off, double* sh) {
+__device__ __forceinline__ double reduce_fixed(const double* v, int n, int stride, int off, double* sh) {
   double t = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) t += v[(long long)k * stride + off];
   double s = block_sum(t, sh);
@@ -510,15 +534,15 @@ __global__ void k_ctrl_residual(Ctrl* c, const double* rp, int nres, const doubl
                                 const double* cp, int ncont, double h, long long nnodes, long long nvox) {
   __shared__ double sh[SB / 32];
   if (c->done) return;
-  double s2 = reduce_fixed(rp, nres, 2, 0, sh);
-  double p2 = reduce_fixed(rp, nres, 2, 1, sh);
-  double q2 = (nproj > 0) ? reduce_fixed(pp, nproj, 1, 0, sh) : 0.0;
+  double s2 = reduce_fixed(rp, nres, RES_STRIDE, 0, sh);
+  double p2 = reduce_fixed(rp, nres, RES_STRIDE, 1, sh);
+  double q2 = (nproj > 0) ? reduce_fixed(pp, nproj, PROJ_STRIDE, 0, sh) : 0.0;
   double c2 = 0.0, ng = 0.0, nr = 0.0, mm = 0.0;
   if (ncont > 0) {
-    c2 = reduce_fixed(cp, ncont, 4, 0, sh);
-    ng = reduce_fixed(cp, ncont, 4, 1, sh);
-    nr = reduce_fixed(cp, ncont, 4, 2, sh);
-    mm = reduce_fixed(cp, ncont, 4, 3, sh);
+    c2 = reduce_fixed(cp, ncont, CONT_STRIDE, 0, sh);
+    ng = reduce_fixed(cp, ncont, CONT_STRIDE, 1, sh);
+    nr = reduce_fixed(cp, ncont, CONT_STRIDE, 2, sh);
+    mm = reduce_fixed(cp, ncont, CONT_STRIDE, 3, sh);
   }
   if (threadIdx.x != 0) return;
   double pt = p2 + q2 + c2;
@@ -559,14 +583,10 @@ int launch_ctrl_contact(Ctrl* c, cudaStream_t s) {
   return (int)cudaGetLastError();
 }
 
-__global__ void k_ctrl_acv(Ctrl* c, const double* partials, int nblk) {
-  __shared__ double sh[SB / 32];
-  if (c->done) return;
+// Gram update of slot (i-1) % 4 and, every acv_mod iterations after the first four, the
+// constrained least squares for alpha (thread 0).
+__device__ __forceinline__ void ctrl_acv_core(Ctrl* c, const double* d) {
   const int i = c->i_local;
-  double d[4] = {0, 0, 0, 0};
-  if (i > 0)
-    for (int k = 0; k < 4; ++k) d[k] = reduce_fixed(partials, nblk, 4, k, sh);
-  if (threadIdx.x != 0) return;
   c->accel = 0;
   if (i > 0) {
     int s = (i - 1) % 4;
@@ -612,6 +632,46 @@ __global__ void k_ctrl_acv(Ctrl* c, const double* partials, int nblk) {
   }
 }
 
+__global__ void k_ctrl_acv(Ctrl* c, const double* partials, int nblk) {
+  __shared__ double sh[SB / 32];
+  if (c->done) return;
+  __shared__ double d[4];   // Gram row, written and read by thread 0
+  const int i = c->i_local;
+  #pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double t = (i > 0) ? reduce_fixed(partials, nblk, 4, k, sh) : 0.0;
+    if (threadIdx.x == 0) d[k] = t;
+  }
+  if (threadIdx.x != 0) return;
+  ctrl_acv_core(c, d);
+}
+
+__global__ void k_ctrl_acv_fused(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, const double* cp,
+                                 int ncont) {
+  __shared__ double sh[SB / 32];
+  if (c->done) return;
+  __shared__ double d[4];   // Gram row, written and read by thread 0
+  const int i = c->i_local;
+  #pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double t = 0.0;
+    if (i > 0) {
+      t = reduce_fixed(rp, nres, RES_STRIDE, 2 + k, sh);
+      if (nproj > 0) t += reduce_fixed(pp, nproj, PROJ_STRIDE, 1 + k, sh);
+      if (ncont > 0) t += reduce_fixed(cp, ncont, CONT_STRIDE, 4 + k, sh);
+    }
+    if (threadIdx.x == 0) d[k] = t;
+  }
+  if (threadIdx.x != 0) return;
+  ctrl_acv_core(c, d);
+}
+
+int launch_ctrl_acv_fused(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, const double* cp,
+                          int ncont, cudaStream_t s) {
+  k_ctrl_acv_fused<<<1, SB, 0, s>>>(c, rp, nres, pp, nproj, cp, ncont);
+  return (int)cudaGetLastError();
+}
+
 int launch_ctrl_acv(Ctrl* c, const double* partials, int nblk, cudaStream_t s) {
   k_ctrl_acv<<<1, SB, 0, s>>>(c, partials, nblk);
   return (int)cudaGetLastError();
@@ -636,12 +696,12 @@ int launch_ctrl_residual(Ctrl* c, const double* rp, int nres, const double* pp, 
   return (int)cudaGetLastError();
 }
 
-template int launch_proj_P_rows<double>(const GridDev&, const RowsDev&, double*, void* const*, void* const*, int, double*, const Ctrl*, cudaStream_t);
-template int launch_proj_P_rows<float>(const GridDev&, const RowsDev&, float*, void* const*, void* const*, int, double*, const Ctrl*, cudaStream_t);
+template int launch_proj_P_rows<double>(const GridDev&, const RowsDev&, double*, void* const*, void* const*, int, int, double*, const Ctrl*, cudaStream_t);
+template int launch_proj_P_rows<float>(const GridDev&, const RowsDev&, float*, void* const*, void* const*, int, int, double*, const Ctrl*, cudaStream_t);
 template int launch_proj_U_rows<double>(const GridDev&, const RowsDev&, double*, float*, float*, double*, const Ctrl*, cudaStream_t);
 template int launch_proj_U_rows<float>(const GridDev&, const RowsDev&, double*, float*, float*, float*, const Ctrl*, cudaStream_t);
-template int launch_contact_eval<double>(const ContactArgs&, double*, void* const*, void* const*, int, cudaStream_t);
-template int launch_contact_eval<float>(const ContactArgs&, float*, void* const*, void* const*, int, cudaStream_t);
+template int launch_contact_eval<double>(const ContactArgs&, double*, void* const*, void* const*, int, int, cudaStream_t);
+template int launch_contact_eval<float>(const ContactArgs&, float*, void* const*, void* const*, int, int, cudaStream_t);
 template int launch_contact_proj_U<double>(const ContactArgs&, double*, float*, float*, double*, cudaStream_t);
 template int launch_contact_proj_U<float>(const ContactArgs&, double*, float*, float*, float*, cudaStream_t);
 template int launch_acv_gram<double>(const GridDev&, void* const*, double*, const Ctrl*, cudaStream_t);

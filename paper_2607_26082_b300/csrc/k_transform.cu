@@ -141,14 +141,70 @@ k_axis_right(const T* __restrict__ in, T* __restrict__ out, const T* __restrict_
   }
 }
 
+static FftParams fft_params(const GridDev& g, const TransformTables& tt, int axis, int inverse, int ncomp_first) {
+  const FftAxisInfo& fa = tt.fft[axis];
+  FftParams p{};
+  p.axis = axis;
+  p.n = g.nvox[axis];
+  p.nn = g.nn[axis];
+  p.L = fa.L;
+  p.nst = fa.nst;
+  for (int q = 0; q < 12; ++q) p.radix[q] = fa.radix[q];
+  p.tw = fa.tw;
+  p.ph = fa.ph;
+  for (int c = 0; c < 3; ++c) p.type[c] = tt.types[c][axis];
+  p.inverse = inverse;
+  p.comp0 = ncomp_first;
+  p.nnx = g.nn[0];
+  p.nny = g.nn[1];
+  p.NN = g.nnodes;
+  p.npencil = g.nnodes / g.nn[axis];
+  p.scale = 1.0;
+  if (inverse) p.scale = g.periodic[axis] ? 1.0 / g.nvox[axis] : 2.0 / g.nvox[axis];
+  return p;
+}
+
+template <typename T>
+int launch_z_green(const GridDev& g, const T* in, T* out, const TransformTables& tt, int ncomp_first, int ncomp,
+                   const Ctrl* ctrl, cudaStream_t s) {
+  if (!tt.fft[2].use) return (int)cudaErrorInvalidValue;
+  FftParams p = fft_params(g, tt, 2, 0, ncomp_first);
+  GreenTables gt;
+  for (int c = 0; c < 3; ++c) {
+    for (int d = 0; d < 3; ++d) {
+      gt.s[c][d] = tt.sin2q[c][d];
+      gt.cp[c][d] = tt.cos2q[c][d];
+    }
+    gt.null_thr[c] = tt.null_thr[c];
+  }
+  return launch_fft_z_green<T>(in, out, p, gt, tt.lam0, tt.mu0, g.scheme, g.h, ncomp, ctrl, s);
+}
+
 template <typename T>
 int launch_transform_axis(const GridDev& g, const T* in, T* out, const TransformTables& tt,
                           int axis, int inverse, int ncomp_first, int ncomp, const Ctrl* ctrl,
-                          cudaStream_t s, void* const* in_ring) {
+                          cudaStream_t s, void* const* in_ring, const IncrTarget* incr) {
+  const int nnx = g.nn[0], nny = g.nn[1], nnz = g.nn[2];
+  if (tt.fft[axis].use) {
+    FftParams p = fft_params(g, tt, axis, inverse, ncomp_first);
+    if (incr) {
+      if (axis != 0 || !inverse) return (int)cudaErrorInvalidValue;
+      p.incr = 1;
+      p.u64 = incr->u64;
+      p.uhi = incr->uhi;
+      p.ulo = incr->ulo;
+      p.step = incr->step;
+    }
+    return launch_fft_axis<T>(in, out, p, ncomp, ctrl, in_ring, s);
+  }
+  if (incr) return (int)cudaErrorInvalidValue;
+  {
+    FftParams p;
+    (void)p;
+  }
   const T* M[3];
   for (int c = 0; c < 3; ++c)
     M[c] = (const T*)(inverse ? tt.inv[c][axis] : tt.fwd[c][axis]);
-  const int nnx = g.nn[0], nny = g.nn[1], nnz = g.nn[2];
   if (axis == 0) {
     int rows = nny * nnz;
     dim3 grd((nnx + GBN - 1) / GBN, (rows + GBM - 1) / GBM, ncomp);
@@ -179,19 +235,17 @@ template <typename T>
 __global__ void k_green(const GridDev g, T* __restrict__ spec, GreenTables gt, double lam0, double mu0,
                         const Ctrl* ctrl) {
   if (ctrl && ctrl->done) return;
-  const long long NN = g.nnodes;
-  const long long total = 3 * NN;
+  // grid: x = x-index blocks, y = y index, z = component * nn_z + z index
+  const int c = blockIdx.z / g.nn[2];
+  const int k = blockIdx.z - c * g.nn[2];
+  const int j = blockIdx.y;
   const T ih2 = (T)(4.0 / (g.h * g.h));
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    int c = (int)(e / NN);
-    long long n = e - c * NN;
-    int i = (int)(n % g.nn[0]);
-    long long r = n / g.nn[0];
-    int j = (int)(r % g.nn[1]);
-    int k = (int)(r / g.nn[1]);
-    const T sx = (T)gt.s[c][0][i], sy = (T)gt.s[c][1][j], sz = (T)gt.s[c][2][k];
-    const T cx = (T)gt.cp[c][0][i], cy = (T)gt.cp[c][1][j], cz = (T)gt.cp[c][2][k];
+  const T sy = (T)gt.s[c][1][j], sz = (T)gt.s[c][2][k];
+  const T cy = (T)gt.cp[c][1][j], cz = (T)gt.cp[c][2][k];
+  const T l0 = (T)lam0, m2 = (T)(2.0 * mu0), thr = (T)gt.null_thr[c];
+  T* row = spec + (long long)c * g.nnodes + ((long long)k * g.nn[1] + j) * g.nn[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nn[0]; i += gridDim.x * blockDim.x) {
+    const T sx = (T)gt.s[c][0][i], cx = (T)gt.cp[c][0][i];
     T Sx, Sy, Sz;
     if (g.scheme == SCHEME_TETRA2) {
       Sx = tetra_S<T>(sx, cy, sy, cx, sz);
@@ -203,9 +257,8 @@ __global__ void k_green(const GridDev g, T* __restrict__ spec, GreenTables gt, d
       Sz = sz * cx * cy;
     }
     const T Sc = c == 0 ? Sx : (c == 1 ? Sy : Sz);
-    const T a = ((T)lam0 * Sc + (T)(2.0 * mu0) * (Sx + Sy + Sz)) * ih2;
-    const T thr = (T)gt.null_thr[c];
-    spec[e] = (a <= thr) ? (T)0 : spec[e] / a;
+    const T a = (l0 * Sc + m2 * (Sx + Sy + Sz)) * ih2;
+    row[i] = (a <= thr) ? (T)0 : row[i] / a;
   }
 }
 
@@ -213,8 +266,6 @@ template <typename T>
 int launch_green_multiply(const GridDev& g, T* spec, const TransformTables& tt, int scheme,
                           const Ctrl* ctrl, cudaStream_t s) {
   (void)scheme;
-  long long total = 3 * g.nnodes;
-  int blocks = (int)std::min<long long>((total + 255) / 256, 148LL * 16);
   GreenTables gt;
   for (int c = 0; c < 3; ++c) {
     for (int d = 0; d < 3; ++d) {
@@ -223,7 +274,8 @@ int launch_green_multiply(const GridDev& g, T* spec, const TransformTables& tt, 
     }
     gt.null_thr[c] = tt.null_thr[c];
   }
-  k_green<T><<<blocks, 256, 0, s>>>(g, spec, gt, tt.lam0, tt.mu0, ctrl);
+  dim3 grd((g.nn[0] + 127) / 128, g.nn[1], 3 * g.nn[2]);
+  k_green<T><<<grd, 128, 0, s>>>(g, spec, gt, tt.lam0, tt.mu0, ctrl);
   return (int)cudaGetLastError();
 }
 
@@ -256,8 +308,10 @@ int launch_add_increment(const GridDev& g, const T* delta, double* u64, float* u
   return (int)cudaGetLastError();
 }
 
-template int launch_transform_axis<double>(const GridDev&, const double*, double*, const TransformTables&, int, int, int, int, const Ctrl*, cudaStream_t, void* const*);
-template int launch_transform_axis<float>(const GridDev&, const float*, float*, const TransformTables&, int, int, int, int, const Ctrl*, cudaStream_t, void* const*);
+template int launch_transform_axis<double>(const GridDev&, const double*, double*, const TransformTables&, int, int, int, int, const Ctrl*, cudaStream_t, void* const*, const IncrTarget*);
+template int launch_transform_axis<float>(const GridDev&, const float*, float*, const TransformTables&, int, int, int, int, const Ctrl*, cudaStream_t, void* const*, const IncrTarget*);
+template int launch_z_green<double>(const GridDev&, const double*, double*, const TransformTables&, int, int, const Ctrl*, cudaStream_t);
+template int launch_z_green<float>(const GridDev&, const float*, float*, const TransformTables&, int, int, const Ctrl*, cudaStream_t);
 template int launch_green_multiply<double>(const GridDev&, double*, const TransformTables&, int, const Ctrl*, cudaStream_t);
 template int launch_green_multiply<float>(const GridDev&, float*, const TransformTables&, int, const Ctrl*, cudaStream_t);
 template int launch_add_increment<double>(const GridDev&, const double*, double*, float*, float*, double*, const Ctrl*, cudaStream_t);

@@ -55,8 +55,12 @@ def _oracle_forward_real(pb, c, x):
 
 
 # ----------------------------------------------------------------------------- transforms
+TRANSFORM_SIZES = [(5, 4, 6), (33, 7, 18), (70, 9, 35),          # dense route (prime factors)
+                   (16, 12, 24), (48, 9, 32), (27, 6, 40)]        # FFT route (radix 4/2/3)
+
+
 @pytest.mark.parametrize("seed", range(6))
-@pytest.mark.parametrize("nvox", [(5, 4, 6), (33, 7, 18), (70, 9, 35)])
+@pytest.mark.parametrize("nvox", TRANSFORM_SIZES)
 def test_transform_forward_fp64(seed, nvox):
     spec = _spec(seed, nvox=nvox, periodic_prob=0.3, anchored=False)
     pb, _ = oracle_problem(spec)
@@ -72,8 +76,9 @@ def test_transform_forward_fp64(seed, nvox):
 
 
 @pytest.mark.parametrize("seed", range(4))
-def test_transform_mixed(seed):
-    spec = _spec(seed, nvox=(33, 7, 18), periodic_prob=0.3, anchored=False)
+@pytest.mark.parametrize("nvox", [(33, 7, 18), (48, 12, 16)])
+def test_transform_mixed(seed, nvox):
+    spec = _spec(seed, nvox=nvox, periodic_prob=0.3, anchored=False)
     pb, _ = oracle_problem(spec)
     g = gpu_grid(spec, MIXED)
     x = np.random.default_rng(seed).standard_normal(pb.node_shape) * pb.dof_mask(1)
@@ -82,12 +87,31 @@ def test_transform_mixed(seed):
     assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
 
 
+def test_fft_and_dense_routes_agree(monkeypatch):
+    """The FFT route and the dense contraction give the same spectra (all five types)."""
+    for seed in range(6):
+        spec = _spec(seed, nvox=(24, 12, 16), periodic_prob=0.4, anchored=False)
+        pb, _ = oracle_problem(spec)
+        g_fft = gpu_grid(spec, FP64)
+        monkeypatch.setenv("DTT_DENSE_TRANSFORMS", "1")
+        g_den = gpu_grid(spec, FP64)
+        monkeypatch.delenv("DTT_DENSE_TRANSFORMS")
+        rng = np.random.default_rng(seed)
+        for c in range(3):
+            x = rng.standard_normal(pb.node_shape) * pb.dof_mask(c)
+            for inv in (0, 1):
+                a = g_fft.dtt_transform(c, inv, x)
+                b = g_den.dtt_transform(c, inv, x)
+                assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
 # ----------------------------------------------------------------------------- Green step
 @pytest.mark.parametrize("scheme", [wl.TETRA2, wl.HEX1])
 @pytest.mark.parametrize("seed", range(5))
 @pytest.mark.parametrize("prec,tol", [(FP64, 1e-11), (MIXED, 2e-6)])
-def test_green_step(scheme, seed, prec, tol):
-    spec = _spec(seed, nvox=(37, 10, 19), scheme=scheme, periodic_prob=0.3, anchored=False)
+@pytest.mark.parametrize("nvox", [(37, 10, 19), (32, 12, 18)])
+def test_green_step(scheme, seed, prec, tol, nvox):
+    spec = _spec(seed, nvox=nvox, scheme=scheme, periodic_prob=0.3, anchored=False)
     pb, _ = oracle_problem(spec)
     g = gpu_grid(spec, prec)
     rng = np.random.default_rng(10 + seed)
@@ -196,6 +220,23 @@ def test_fixed_iterations_accelerated_fp64(seed, acv_on):
     assert rel_l2(g.dtt_get_fields(), ref.u) <= 1e-9
     hist = g.dtt_get_history()
     assert np.allclose(hist, ref.history, rtol=1e-7, atol=1e-9 * ref.history[0])
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_fixed_iterations_accelerated_mixed(seed):
+    """Mixed precision with Anderson on p~ (difference form, Gram row fused into the
+    residual and projection kernels): the residual history of the first 14 iterations,
+    across the first accelerations, follows the FP64 oracle's."""
+    spec = wl.random_problem(seed, nvox=(20, 12, 9))
+    pb, rows = oracle_problem(spec)
+    K = 14
+    ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 0.0, K, acv_on="P", acv_mod=spec["acv_mod"])
+    g = gpu_grid(spec, MIXED)
+    rep = g.dtt_solve_step(0.0, K, acv_mod=spec["acv_mod"], graph_iters=1)
+    assert rep.iterations == K
+    assert rep.accelerations == ref.accelerations
+    hist = g.dtt_get_history()
+    assert np.allclose(hist, ref.history, rtol=2e-3, atol=1e-6 * ref.history[0])
 
 
 @pytest.mark.parametrize("prec,tol_u", [(FP64, 1e-10), (MIXED, 2e-6)])
