@@ -1,14 +1,16 @@
 #!/usr/bin/env python3
 """Benchmark: voxel-iterations/s and time to residual 1e-6 of the constrained DTT
-solver on one B300, mixed precision against plain FP64.
+solver on one B300, mixed precision against the plain FP64 GPU solver.
 
-Workload (default): compact-tension-like plate, 128 x 128 x 32 voxels, E = 210, nu = 0.3,
-void notch, two pinned disks pulled apart (local Dirichlet rows), zero-stiffness buffer
-frame carrying the in-plane Dirichlet faces, TETRA2, Paux reference (lambda/2, mu/2),
-ACV_P every 2 iterations, tolerance 1e-6 (Eq. 5).  One step = one complete solve from
-u~ = 0 to the tolerance; every step runs all of the iteration's kernels.
+Workload (default): the upper half of a compact-tension-like plate in the paper's buffer
+device (Section 4.1.2), 128 x 128 x 32 voxels, E = 210, nu = 0.3, TETRA2: a null-stiffness
+buffer row behind a u_y-Dirichlet face, ligament nodes held at u_y = 0 (strong rows), a
+void notch, one pin disk pulled to u_y = +0.05 (strong rows), u_z Dirichlet on z = 0;
+Paux reference (lambda, mu); Anderson on p~ every 2 iterations; tolerance 1e-6 (Eq. 5).
+One step = one complete solve from u~ = 0 to the tolerance; every step runs all of the
+iteration's kernels.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload ct|indent]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line.  N > 1 (under torchrun): every rank solves its own replica of the
 workload (the solve does not shard); value = all ranks' voxel-iterations / max time.
@@ -148,8 +150,8 @@ def launches_per_iteration(has_rows, has_contact, acv):
     n += 1 if has_contact else 0
     n += 1                     # ctrl residual
     n += 2 if has_contact else 0
-    n += 3 if acv else 0       # Gram row, ctrl (alpha), Green input
-    n += 8                     # 3 forward passes, Green, 3 inverse passes, increment
+    n += 2 if acv else 0       # ctrl (Gram row, alpha), Green input
+    n += 5                     # x, y forward; z forward + Green + z inverse; y, x inverse + increment
     n += 1 if has_rows else 0  # proj_U
     n += 1 if has_contact else 0
     n += 1                     # ctrl end
@@ -165,7 +167,8 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.Stream(device=dev)
     spec = workload(args.workload)
     if args.workload != "ct":
-        raise SystemExit("the contact workload bench is run through tests / _work probes")
+        raise SystemExit("bench.py times the ct workload; run the indentation block with "
+                         "python -m paper_2607_26082_b300.run --workload indent")
     nv = nvox_of(spec)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -227,12 +230,16 @@ def run_ours(args, rank, world, local):
     nn = gm.n_nodes
     # algorithmic bytes of one launch group per iteration (mixed path: T = 4 B fields, u~ as
     # an 8-byte float-float pair, phase ids 1 B per voxel)
-    alg_bytes = {"residual": nn * (24 + 12 + 12 + 12 + 12) + nv,   # u~, step, g_(i-1) in; p, R out
-                 "projections": 0, "anderson": nn * (48 + 78),      # Gram (4 R), Green input (avg)
-                 "forward_dt": nn * 72, "green": nn * 24, "inverse_dt": nn * 72,
-                 "increment": nn * 72}
-    launches_in_group = {"residual": 1, "forward_dt": 3, "inverse_dt": 3, "green": 1, "increment": 1,
-                         "anderson": 3, "projections": 4}
+    # residual: u~ hi/lo 24, step 12, g_(i-1) 12, three older R slots for the Gram row 36 in;
+    # p 12, R 12 out.  Anderson input: p copy (24) or the accelerated combination (132),
+    # one in acv_mod.  FFT route: x, y forward passes 24 each; z forward + Green + z
+    # inverse 24; y inverse 24, x inverse + increment (u~ hi/lo in and out, step out) 72.
+    mod = spec["acv_mod"]
+    alg_bytes = {"residual": nn * 108 + nv, "projections": 0,
+                 "anderson": nn * (24 * (mod - 1) + 132) / mod,
+                 "forward_dt": nn * 48, "green": nn * 24, "inverse_dt": nn * 96, "increment": 0}
+    launches_in_group = {"residual": 1, "forward_dt": 2, "inverse_dt": 2, "green": 1, "increment": 1,
+                         "anderson": 2, "projections": 4}
     dom = max(prof, key=lambda k: prof[k])
     peaks = {}
     try:
