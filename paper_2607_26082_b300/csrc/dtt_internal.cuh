@@ -131,6 +131,9 @@ struct ResidualArgs {
   double* partials;       // 2 per block: sum w sigma:sigma, sum p^2 (unmasked DOFs)
   const Ctrl* ctrl;       // if non-null: skip when done (mode 1 needs it)
   int zchunk;             // z planes per CTA (set by the launcher)
+  // FP32 constants of the mixed kernel (set by its launcher from the fields above)
+  float f_eps[3][3];
+  float f_lam0, f_mu0, f_inv2h, f_inv4h;
 };
 // Residual partial sums: 6 doubles per CTA [w sigma:sigma, p^2, Gram 0..3] (the FP64
 // kernel leaves the Gram entries 0; the FP32 kernel fills them in the Anderson mode).
@@ -164,6 +167,8 @@ struct FftParams {
   int comp0;
   int nnx, nny;
   long long npencil, NN;
+  float fscale;            // scale in FP32 (mixed path)
+  double inv_n;            // 1 / n (quarter-wave inverses)
   int incr;                // inverse x pass: add the result to u~ and store it as the step
   double* u64;
   float* uhi;

@@ -56,15 +56,25 @@ __device__ __forceinline__ void dft3(Cx<T>* v, int s) {
   v[2] = {m.x + sn * t2.y, m.y - sn * t2.x};
 }
 
-// One Stockham stage of radix R for all PB sequences of the CTA (registers only).
+// One Stockham stage of radix R for all PB sequences of the CTA (registers only).  lgLR /
+// lgNs are log2 of L/R and Ns when L is a power of two (shift and mask index math), else -1.
 template <typename T, int R>
 __device__ __forceinline__ void stockham_stage(const Cx<T>* __restrict__ S, Cx<T>* __restrict__ D, int L, int Ns,
-                                               int PBL, const Cx<T>* __restrict__ tw, int sgn, int tid, int nthr) {
+                                               int PBL, const Cx<T>* __restrict__ tw, int sgn, int tid, int nthr,
+                                               int lgLR, int lgNs) {
   const int LR = L / R;
   const int twstep = L / (Ns * R);
   for (int idx = tid; idx < PBL / R; idx += nthr) {
-    const int q = idx / LR, jb = idx - q * LR;
-    const int k = jb % Ns;
+    int q, jb, k;
+    if (lgLR >= 0) {
+      q = idx >> lgLR;
+      jb = idx & (LR - 1);
+      k = jb & (Ns - 1);
+    } else {
+      q = idx / LR;
+      jb = idx - q * LR;
+      k = jb % Ns;
+    }
     const Cx<T>* Sq = S + q * L;
     Cx<T>* Dq = D + q * L;
     Cx<T> v[R];
@@ -95,9 +105,12 @@ __device__ __forceinline__ T tetra_S(T sa, T cb, T sb, T cA, T sc) {
 
 // Extended (and, for quarter-wave forward types, modulated) complex sequences of the CTA
 // in A, from values get(pb, j) of pencil pb (0..2PB-1) at axis position j (0..nn-1).
+// rowwise: a warp reads one pencil at consecutive j (pencils contiguous in memory, x axis);
+// otherwise consecutive threads take consecutive pencils at the same j (y and z axes, whose
+// neighbouring pencils are neighbours in memory).
 template <typename T, int PB, typename Get>
 __device__ __forceinline__ void fill_sequences(Cx<T>* A, int L, int n, int nn, int type, int inverse, int npen,
-                                               const Cx<T>* ph, Get get, int tid, int nthr) {
+                                               const Cx<T>* ph, Get get, int tid, int nthr, bool rowwise) {
   const bool quarter = (type == T_DCT3 || type == T_DST3);
   for (int q = tid; q < PB; q += nthr) {
     Cx<T>* S = A + q * L;
@@ -110,10 +123,7 @@ __device__ __forceinline__ void fill_sequences(Cx<T>* A, int L, int n, int nn, i
   if (npen < 2 * PB)
     for (int q = tid; q < PB * L; q += nthr) A[q] = {(T)0, (T)0};
   __syncthreads();
-  for (int idx = tid; idx < 2 * PB * nn; idx += nthr) {
-    const int pb = idx % (2 * PB), j = idx / (2 * PB);
-    if (pb >= npen) continue;
-    const T v = get(pb, j);
+  auto place = [&](int pb, int j, T v) {
     Cx<T>* S = A + (pb >> 1) * L;
     const bool im = pb & 1;
     auto put = [&](int pos, T val) {
@@ -142,10 +152,25 @@ __device__ __forceinline__ void fill_sequences(Cx<T>* A, int L, int n, int nn, i
       put(j, v);
       put(2 * n - 1 - j, type == T_DCT3 ? v : -v);
     }
+  };
+  if (rowwise) {
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    for (int pb = warp; pb < npen; pb += nw)
+      for (int j = lane; j < nn; j += 32) place(pb, j, get(pb, j));
+  } else {
+    for (int idx = tid; idx < 2 * PB * nn; idx += nthr) {
+      const int pb = idx % (2 * PB), j = idx / (2 * PB);
+      if (pb >= npen) continue;
+      place(pb, j, get(pb, j));
+    }
   }
   __syncthreads();
   if (quarter && !inverse) {
-    for (int q = tid; q < PB * L; q += nthr) A[q] = cmul(A[q], ph[q % L]);
+    for (int j = tid; j < L; j += nthr) {
+      const Cx<T> w = ph[j];
+      #pragma unroll
+      for (int q = 0; q < PB; ++q) A[q * L + j] = cmul(A[q * L + j], w);
+    }
     __syncthreads();
   }
 }
@@ -154,17 +179,23 @@ __device__ __forceinline__ void fill_sequences(Cx<T>* A, int L, int n, int nn, i
 template <typename T, int PB>
 __device__ __forceinline__ Cx<T>* fft_sequences(Cx<T>* s0, Cx<T>* s1, const FftParams& p, const Cx<T>* tw, int sgn,
                                                 int tid, int nthr) {
-  int Ns = 1;
+  const bool pow2 = (p.L & (p.L - 1)) == 0;
+  const int lgL = pow2 ? __ffs(p.L) - 1 : -1;
+  int Ns = 1, lgNs = 0;
   for (int st = 0; st < p.nst; ++st) {
     const int R = p.radix[st];
-    if (R == 4) stockham_stage<T, 4>(s0, s1, p.L, Ns, PB * p.L, tw, sgn, tid, nthr);
-    else if (R == 2) stockham_stage<T, 2>(s0, s1, p.L, Ns, PB * p.L, tw, sgn, tid, nthr);
-    else stockham_stage<T, 3>(s0, s1, p.L, Ns, PB * p.L, tw, sgn, tid, nthr);
+    const int lgR = R == 4 ? 2 : (R == 2 ? 1 : -1);
+    const int lgLR = pow2 ? lgL - lgR : -1;
+    const int lns = pow2 ? lgNs : -1;
+    if (R == 4) stockham_stage<T, 4>(s0, s1, p.L, Ns, PB * p.L, tw, sgn, tid, nthr, lgLR, lns);
+    else if (R == 2) stockham_stage<T, 2>(s0, s1, p.L, Ns, PB * p.L, tw, sgn, tid, nthr, lgLR, lns);
+    else stockham_stage<T, 3>(s0, s1, p.L, Ns, PB * p.L, tw, sgn, tid, nthr, -1, -1);
     __syncthreads();
     Cx<T>* t = s0;
     s0 = s1;
     s1 = t;
     Ns *= R;
+    if (lgR > 0) lgNs += lgR;
   }
   return s0;
 }
@@ -172,7 +203,7 @@ __device__ __forceinline__ Cx<T>* fft_sequences(Cx<T>* s0, Cx<T>* s1, const FftP
 // Transform value of pencil pb at spectral / node position k from the FFT result Y.
 template <typename T>
 __device__ __forceinline__ T post_value(const Cx<T>* Yall, int L, int n, int type, int inverse, T sc, const Cx<T>* ph,
-                                        int pb, int k) {
+                                        int pb, int k, T inv_n) {
   const Cx<T>* Y = Yall + (pb >> 1) * L;
   const bool im = pb & 1;
   const T half = (T)0.5;
@@ -202,7 +233,6 @@ __device__ __forceinline__ T post_value(const Cx<T>* Yall, int L, int n, int typ
   }
   const Cx<T> w = {ph[k].x, -ph[k].y};
   const Cx<T> e = cmul(Y[k], w);
-  const T inv_n = (T)1 / (T)n;
   if (type == T_DCT3) return (k <= n - 1) ? (im ? e.y : e.x) * inv_n : (T)0;
   return (k >= 1) ? (im ? -e.x : e.y) * inv_n : (T)0;
 }
@@ -234,6 +264,13 @@ __device__ __forceinline__ void add_to_u(long long e, T val, const FftParams& p)
   ((T*)p.step)[e] = val;
 }
 
+// Shared-memory layout of one CTA: two buffers of PB sequences of length L, then the L
+// twiddles, then (z pass) per-position symbol tables.
+template <typename T, int PB>
+__host__ __device__ constexpr size_t fft_smem_base(int L) {
+  return (size_t)(2 * PB + 1) * (size_t)L * sizeof(Cx<T>);
+}
+
 // One axis pass: forward or inverse DTT of every pencil along p.axis.  With p.incr (inverse
 // x pass), the result is added to u~ and written as the step instead of to `out`.
 template <typename T, int PB>
@@ -245,6 +282,7 @@ k_fft_axis(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   __shared__ long long sbase[2 * PB];
   Cx<T>* bufA = (Cx<T>*)smem_raw;
   Cx<T>* bufB = bufA + PB * p.L;
+  Cx<T>* tws = bufB + PB * p.L;
   const Cx<T>* tw = (const Cx<T>*)p.tw;
   const Cx<T>* ph = (const Cx<T>*)p.ph;
   const int comp = p.comp0 + blockIdx.y;
@@ -255,35 +293,53 @@ k_fft_axis(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   const long long coff = (long long)comp * p.NN;
   const long long stride = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)p.nnx : (long long)p.nnx * p.nny);
   const int npen = (int)min((long long)(2 * PB), p.npencil - pen0);
+  const bool rowwise = p.axis == 0;
   pencil_bases<T, PB>(sbase, p, pen0, tid);
+  for (int q = tid; q < p.L; q += nthr) tws[q] = tw[q];
   __syncthreads();
   fill_sequences<T, PB>(bufA, p.L, p.n, p.nn, type, p.inverse, npen, ph,
-                        [&](int pb, int j) { return src[sbase[pb] + j * stride]; }, tid, nthr);
+                        [&](int pb, int j) { return src[sbase[pb] + j * stride]; }, tid, nthr, rowwise);
   const bool quarter = (type == T_DCT3 || type == T_DST3);
   const int sgn = (p.inverse && quarter) ? 1 : -1;
-  Cx<T>* Y = fft_sequences<T, PB>(bufA, bufB, p, tw, sgn, tid, nthr);
-  const T sc = (T)p.scale;
-  for (int idx = tid; idx < 2 * PB * p.nn; idx += nthr) {
-    const int pb = idx % (2 * PB), k = idx / (2 * PB);
-    if (pb >= npen) continue;
-    const T v = post_value<T>(Y, p.L, p.n, type, p.inverse, sc, ph, pb, k);
+  Cx<T>* Y = fft_sequences<T, PB>(bufA, bufB, p, tws, sgn, tid, nthr);
+  const T sc = sizeof(T) == 4 ? (T)p.fscale : (T)p.scale;
+  const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
+  auto emit = [&](int pb, int k) {
+    const T v = post_value<T>(Y, p.L, p.n, type, p.inverse, sc, ph, pb, k, inv_n);
     const long long e = coff + sbase[pb] + k * stride;
     if (p.incr) add_to_u<T>(e, v, p);
     else out[e] = v;
+  };
+  if (rowwise) {
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    for (int pb = warp; pb < npen; pb += nw)
+      for (int k = lane; k < p.nn; k += 32) emit(pb, k);
+  } else {
+    for (int idx = tid; idx < 2 * PB * p.nn; idx += nthr) {
+      const int pb = idx % (2 * PB), k = idx / (2 * PB);
+      if (pb >= npen) continue;
+      emit(pb, k);
+    }
   }
 }
 
 // Fused z pass: forward DTT along z, Green multiply (Eq. 4 adapted to the Paux reference,
 // Section 3.2.3), inverse DTT along z, for pencils whose x and y spectra are already taken.
+// The symbol factors sin^2(q/2), cos^2(q/2) of the z positions are staged in shared memory
+// once per CTA, those of the CTA's pencils (x and y positions) once per pencil.
 template <typename T, int PB>
 __global__ void __launch_bounds__(256)
-k_fft_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenTables gt, double lam0, double mu0,
-              int scheme, double h, const Ctrl* ctrl) {
+k_fft_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenTables gt, T l0, T m2, T ih2,
+              int scheme, T zscale, const Ctrl* ctrl) {
   if (ctrl && ctrl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long sbase[2 * PB];
+  __shared__ T pxy[2 * PB][4];   // per pencil: s_x, c'_x, s_y, c'_y
   Cx<T>* bufA = (Cx<T>*)smem_raw;
   Cx<T>* bufB = bufA + PB * p.L;
+  Cx<T>* tws = bufB + PB * p.L;
+  T* zs = (T*)(tws + p.L);        // s_z[k], k < nn
+  T* zc = zs + p.nn;              // c'_z[k]
   const Cx<T>* tw = (const Cx<T>*)p.tw;
   const Cx<T>* ph = (const Cx<T>*)p.ph;
   const int comp = p.comp0 + blockIdx.y;
@@ -295,25 +351,36 @@ k_fft_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenT
   const int npen = (int)min((long long)(2 * PB), p.npencil - pen0);
   const int nn = p.nn;
   pencil_bases<T, PB>(sbase, p, pen0, tid);
+  if (tid < 2 * PB) {
+    const long long pen = pen0 + tid;
+    const int ix = pen < p.npencil ? (int)(pen % p.nnx) : 0, iy = pen < p.npencil ? (int)(pen / p.nnx) : 0;
+    pxy[tid][0] = (T)gt.s[comp][0][ix];
+    pxy[tid][1] = (T)gt.cp[comp][0][ix];
+    pxy[tid][2] = (T)gt.s[comp][1][iy];
+    pxy[tid][3] = (T)gt.cp[comp][1][iy];
+  }
+  for (int q = tid; q < p.L; q += nthr) tws[q] = tw[q];
+  for (int q = tid; q < nn; q += nthr) {
+    zs[q] = (T)gt.s[comp][2][q];
+    zc[q] = (T)gt.cp[comp][2][q];
+  }
   __syncthreads();
   const bool quarter = (type == T_DCT3 || type == T_DST3);
+  const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
   // forward along z
   fill_sequences<T, PB>(bufA, p.L, p.n, nn, type, 0, npen, ph,
-                        [&](int pb, int j) { return in[coff + sbase[pb] + j * stride]; }, tid, nthr);
-  Cx<T>* Y = fft_sequences<T, PB>(bufA, bufB, p, tw, -1, tid, nthr);
+                        [&](int pb, int j) { return in[coff + sbase[pb] + j * stride]; }, tid, nthr, false);
+  Cx<T>* Y = fft_sequences<T, PB>(bufA, bufB, p, tws, -1, tid, nthr);
   Cx<T>* I = (Y == bufA) ? bufB : bufA;
   T* spec = (T*)I;   // 2 PB x nn real spectra (fits in one complex buffer)
-  const T ih2 = (T)(4.0 / (h * h));
-  const T l0 = (T)lam0, m2 = (T)(2.0 * mu0), thr = (T)gt.null_thr[comp];
+  const T thr = (T)gt.null_thr[comp];
   for (int idx = tid; idx < 2 * PB * nn; idx += nthr) {
     const int pb = idx % (2 * PB), k = idx / (2 * PB);
     T v = (T)0;
     if (pb < npen) {
-      v = post_value<T>(Y, p.L, p.n, type, 0, (T)1, ph, pb, k);
-      const long long b = sbase[pb];
-      const int ix = (int)(b % p.nnx), iy = (int)(b / p.nnx);
-      const T sx = (T)gt.s[comp][0][ix], sy = (T)gt.s[comp][1][iy], sz = (T)gt.s[comp][2][k];
-      const T cx = (T)gt.cp[comp][0][ix], cy = (T)gt.cp[comp][1][iy], cz = (T)gt.cp[comp][2][k];
+      v = post_value<T>(Y, p.L, p.n, type, 0, (T)1, ph, pb, k, inv_n);
+      const T sx = pxy[pb][0], cx = pxy[pb][1], sy = pxy[pb][2], cy = pxy[pb][3];
+      const T sz = zs[k], cz = zc[k];
       T Sx, Sy, Sz;
       if (scheme == SCHEME_TETRA2) {
         Sx = tetra_S<T>(sx, cy, sy, cx, sz);
@@ -334,13 +401,12 @@ k_fft_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenT
   // inverse along z
   Cx<T>* X = Y;
   fill_sequences<T, PB>(X, p.L, p.n, nn, type, 1, npen, ph, [&](int pb, int j) { return spec[pb * nn + j]; }, tid,
-                        nthr);
-  Y = fft_sequences<T, PB>(X, I, p, tw, quarter ? 1 : -1, tid, nthr);
-  const T sc = (T)((p.L == p.n) ? 1.0 / p.n : 2.0 / p.n);   // Hartley 1/n, DCT1 / DST1 2/n
+                        nthr, false);
+  Y = fft_sequences<T, PB>(X, I, p, tws, quarter ? 1 : -1, tid, nthr);
   for (int idx = tid; idx < 2 * PB * nn; idx += nthr) {
     const int pb = idx % (2 * PB), k = idx / (2 * PB);
     if (pb >= npen) continue;
-    out[coff + sbase[pb] + k * stride] = post_value<T>(Y, p.L, p.n, type, 1, sc, ph, pb, k);
+    out[coff + sbase[pb] + k * stride] = post_value<T>(Y, p.L, p.n, type, 1, zscale, ph, pb, k, inv_n);
   }
 }
 
@@ -355,17 +421,22 @@ int fft_pb(int L) {
   return pb >= 1 ? 1 : 0;
 }
 
+template <typename K>
+static int ensure_smem(K kernel, size_t sm, size_t& done) {
+  if (sm <= done) return 0;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return (int)e;
+  done = sm;
+  return 0;
+}
+
 template <typename T, int PB>
 static int launch_fft_pb(const T* in, T* out, const FftParams& p, int ncomp, const Ctrl* ctrl, void* const* in_ring,
                          cudaStream_t s) {
   dim3 grd((unsigned)((p.npencil + 2 * PB - 1) / (2 * PB)), ncomp);
-  size_t sm = (size_t)2 * PB * p.L * sizeof(Cx<T>);
-  static int attr_done = 0;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_fft_axis<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
-    if (e != cudaSuccess) return (int)e;
-    attr_done = 1;
-  }
+  const size_t sm = fft_smem_base<T, PB>(p.L);
+  static size_t attr = 48 * 1024;
+  if (int e = ensure_smem(k_fft_axis<T, PB>, sm, attr)) return e;
   k_fft_axis<T, PB><<<grd, 256, sm, s>>>(in, out, p, ctrl, in_ring);
   return (int)cudaGetLastError();
 }
@@ -374,14 +445,12 @@ template <typename T, int PB>
 static int launch_zg_pb(const T* in, T* out, const FftParams& p, const GreenTables& gt, double lam0, double mu0,
                         int scheme, double h, int ncomp, const Ctrl* ctrl, cudaStream_t s) {
   dim3 grd((unsigned)((p.npencil + 2 * PB - 1) / (2 * PB)), ncomp);
-  size_t sm = (size_t)2 * PB * p.L * sizeof(Cx<T>);
-  static int attr_done = 0;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_fft_z_green<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
-    if (e != cudaSuccess) return (int)e;
-    attr_done = 1;
-  }
-  k_fft_z_green<T, PB><<<grd, 256, sm, s>>>(in, out, p, gt, lam0, mu0, scheme, h, ctrl);
+  const size_t sm = fft_smem_base<T, PB>(p.L) + (size_t)2 * p.nn * sizeof(T);
+  static size_t attr = 48 * 1024;
+  if (int e = ensure_smem(k_fft_z_green<T, PB>, sm, attr)) return e;
+  const T l0 = (T)lam0, m2 = (T)(2.0 * mu0), ih2 = (T)(4.0 / (h * h));
+  const T zscale = (T)((p.L == p.n) ? 1.0 / p.n : 2.0 / p.n);   // Hartley 1/n, DCT1 / DST1 2/n
+  k_fft_z_green<T, PB><<<grd, 256, sm, s>>>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ctrl);
   return (int)cudaGetLastError();
 }
 

@@ -3,24 +3,37 @@
 // reference medium of Section 3.2.3 and the symmetry weights W of Table 1), organised for
 // FP32 throughput on B300:
 //
-//  * one thread per node, a 32 x 8 node tile per CTA marching along z;
-//  * every node evaluates, for each of its 8 voxels, only the integration point whose
-//    tetrahedron contains it (TETRA2) or the voxel's single point (HEX1) -- FP32 work is
-//    cheap, and this removes the per-voxel shared-memory stage and two of its barriers;
-//  * u~ (float-float hi / lo), the step Delta and the voxel phases of the planes k-1..k+2
-//    sit in a 4-slot shared-memory ring filled with cp.async one plane ahead, so the
-//    global loads of plane k+2 overlap the arithmetic of plane k (one barrier per plane);
-//  * in the Anderson difference form the kernel also accumulates the Gram row
-//    <R_{i-1}, R_k> (k = 0..3) over the unconstrained DOFs; the projection kernels add the
-//    constrained ones after they have shifted R_{i-1}.
-// Partial sums per CTA (FP64 across threads): [sum w sigma:sigma, sum p^2, Gram 0..3].
+//  * a CTA owns a 32 x 8 tile of node columns and marches along z one voxel layer at a
+//    time; the layer between node planes L and L+1 is processed in two phases:
+//      A. one thread per voxel of the 33 x 9 halo layer forms, once, the gradients of both
+//         tetrahedra (TETRA2) or of the single point (HEX1), the stress sigma = C:(eps* +
+//         sym grad u~) and the reference-medium flux tau_cd = (2 mu0 + lambda0 delta_cd)
+//         d(.)_c/dx_d, and stores them in shared memory (structure of arrays);
+//      B. one thread per node gathers, from the 4 voxels of the layer around its column,
+//         the divergence contributions to node L (as their lower corner) and to node L+1
+//         (as their upper corner); node L is then complete and its outputs are written;
+//  * u~ (float-float hi / lo), the step Delta and the voxel phases of node planes L..L+2
+//    sit in a 3-slot shared-memory ring filled with cp.async one plane ahead;
+//  * in the Anderson difference form the kernel also forms the Gram row <R_{i-1}, R_k>
+//    (k = 0..3) over the unconstrained DOFs; the projection kernels add the constrained
+//    ones after they have shifted R_{i-1};
+//  * no FP64 arithmetic inside the march: per-thread sums are compensated FP32 pairs
+//    (TwoSum), converted to FP64 once per thread before the block reduction.
+// Partial sums per CTA (FP64): [sum w sigma:sigma, sum p^2, Gram 0..3].
 #include "dtt_internal.cuh"
 
 namespace dtt {
 
-constexpr int FTX = 32, FTY = 8, FNP = 4;
-constexpr int FHX = FTX + 2, FHY = FTY + 2;
-constexpr int FPLANE = 3 * FHY * FHX;   // floats per plane (3 components)
+namespace {
+
+constexpr int FTX = 32, FTY = 8;                 // node tile
+constexpr int FVX = FTX + 1, FVY = FTY + 1;      // voxel layer with its low-side halo
+constexpr int NVL = FVX * FVY;                   // 297 voxels per layer
+constexpr int FTHREADS = 320;                    // >= NVL, multiple of 32
+constexpr int FNP = 3;                           // node-plane ring slots
+constexpr int FHX = FTX + 2, FHY = FTY + 2;      // node plane with halo (x0-1 .. x0+32)
+constexpr int FPLANE = 3 * FHY * FHX;            // floats per plane (3 components)
+constexpr int QV = 15;                           // per point: sigma 6 + tau 9
 
 __device__ __forceinline__ void cp_async4(void* smem_ptr, const void* gptr) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_ptr);
@@ -33,31 +46,47 @@ __device__ __forceinline__ int wrapi(int i, int n, int per) {
   if (per) { i %= n; if (i < 0) i += n; return i; }
   return (i < 0 || i >= n) ? -1 : i;
 }
+__device__ __forceinline__ int slot_of(int plane) { return ((plane % FNP) + FNP) % FNP; }
 
-struct F32Tile {
-  const float* H;   // hi, base of the 4-plane ring
-  const float* Lo;  // lo
-  const float* D;   // Delta
+// compensated FP32 accumulator (TwoSum: s + c carries the sum to about FP32^2)
+struct Acc2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
-// value accessors: plane slot, component, local y, local x
 __device__ __forceinline__ int sidx(int slot, int c, int ly, int lx) { return ((slot * 3 + c) * FHY + ly) * FHX + lx; }
 
+// (ph + pl) - (qh + ql) from the pairs' differences, so that increments far below the
+// FP32 resolution of u~ survive
+__device__ __forceinline__ float fdiff(float ph, float pl, float qh, float ql) {
+  return __fadd_rn(__fsub_rn(ph, qh), __fsub_rn(pl, ql));
+}
+
+}  // namespace
+
 template <int SCHEME>
-__global__ void __launch_bounds__(FTX * FTY)
+__global__ void __launch_bounds__(FTHREADS, 2)
 k_residual_f32(ResidualArgs a) {
+  constexpr int NPT = (SCHEME == SCHEME_TETRA2) ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sH = (float*)smem_raw;
-  float* sL = sH + FNP * FPLANE;
-  float* sD = sL + FNP * FPLANE;
-  uint8_t* sP = (uint8_t*)(sD + FNP * FPLANE);   // [FNP][FHY][FHX] voxel phases
+  float* sH = (float*)smem_raw;                 // [FNP][3][FHY][FHX] u~ hi
+  float* sL = sH + FNP * FPLANE;                // u~ lo
+  float* sD = sL + FNP * FPLANE;                // Delta
+  float* sV = sD + FNP * FPLANE;                // [NPT * QV][NVL] point data of the current layer
+  uint8_t* sP = (uint8_t*)(sV + NPT * QV * NVL);   // [FNP][FHY][FHX] voxel phases (layer of plane)
   __shared__ float sLam[MAX_PHASE], sMu[MAX_PHASE];
-  __shared__ double sRed[6][FTX * FTY / 32];
+  __shared__ double sRed[6][FTHREADS / 32];
 
   if (a.ctrl && a.ctrl->done) return;
   const GridDev& g = a.g;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
-  for (int q = tid; q < a.nphase; q += FTX * FTY) {
+  const int tid = threadIdx.x;
+  for (int q = tid; q < a.nphase; q += FTHREADS) {
     sLam[q] = (float)a.lam[q];
     sMu[q] = (float)a.mu[q];
   }
@@ -88,6 +117,7 @@ k_residual_f32(ResidualArgs a) {
       gprev = (const float*)a.gring[rslot];
       dfield = (const float*)a.dfield;
       tau_from_delta = true;
+      #pragma unroll
       for (int q = 0; q < 4; ++q) Rk[q] = (const float*)a.rring[q];
     } else {
       tau_on = false;
@@ -95,21 +125,17 @@ k_residual_f32(ResidualArgs a) {
   } else {
     tau_on = false;
   }
-  const float lam0 = (float)a.lam0, mu0 = (float)a.mu0;
-  float eps[3][3];
-  #pragma unroll
-  for (int p = 0; p < 3; ++p)
-    #pragma unroll
-    for (int q = 0; q < 3; ++q) eps[p][q] = (float)a.eps[p][q];
-  const float c4h = (float)(1.0 / (4.0 * g.h));
-  const float inv2h = (float)(1.0 / (2.0 * g.h));
-  const float inv4h = (float)(1.0 / (4.0 * g.h));
+  const float lam0 = a.f_lam0, mu0 = a.f_mu0;
+  const float inv2h = a.f_inv2h, inv4h = a.f_inv4h;
+  const float c4h = inv4h;
+  const float (&eps)[3][3] = a.f_eps;
 
-  // ---- plane loader: node plane kk into ring slot, voxel phase plane kk into ring slot
+  // ---- plane loader: node plane kk and the voxel phases of layer kk into ring slot
   auto load_plane = [&](int kk) {
-    const int slot = (kk + 8) & (FNP - 1);
+    const int slot = slot_of(kk);
     const int kw = wrapi(kk, nnz, g.periodic[2]);
-    for (int q = tid; q < FHX * FHY; q += FTX * FTY) {
+    const int vz = wrapi(kk, g.nvox[2], g.periodic[2]);
+    for (int q = tid; q < FHX * FHY; q += FTHREADS) {
       const int lx = q % FHX, ly = q / FHX;
       const int gi = wrapi(x0 - 1 + lx, nnx, g.periodic[0]);
       const int gj = wrapi(y0 - 1 + ly, nny, g.periodic[1]);
@@ -122,211 +148,292 @@ k_residual_f32(ResidualArgs a) {
           cp_async4(&sH[si], a.uhi + c * NN + n);
           cp_async4(&sL[si], a.ulo + c * NN + n);
           if (dfield) cp_async4(&sD[si], dfield + c * NN + n);
+          else sD[si] = 0.f;
         } else {
           sH[si] = 0.f;
           sL[si] = 0.f;
           sD[si] = 0.f;
         }
       }
-      // voxel (x0-1+lx, y0-1+ly, kk)
       const int vx = wrapi(x0 - 1 + lx, g.nvox[0], g.periodic[0]);
       const int vy = wrapi(y0 - 1 + ly, g.nvox[1], g.periodic[1]);
-      const int vz = wrapi(kk, g.nvox[2], g.periodic[2]);
       uint8_t ph = 255;   // 255 = no voxel
       if (vx >= 0 && vy >= 0 && vz >= 0) ph = a.phase[vx + (long long)g.nvox[0] * (vy + (long long)g.nvox[1] * vz)];
       sP[(slot * FHY + ly) * FHX + lx] = ph;
     }
   };
 
-  double acc_s2 = 0.0, acc_p2 = 0.0;
-  double acc_g[4] = {0.0, 0.0, 0.0, 0.0};
+  Acc2 acc_s2, acc_p2, acc_g[4];
+
+  // node thread (i, j)
+  const bool node_thread = tid < FTX * FTY;
+  const int tx = tid % FTX, ty = tid / FTX;
+  const int i = x0 + tx, j = y0 + ty;
+  const bool active = node_thread && (i < nnx && j < nny);
+  // voxel thread: local voxel (vlx, vly) = global voxel (x0 - 1 + vlx, y0 - 1 + vly); warps
+  // 0..8 take the voxel rows' first 32 columns (one row per warp: bank-conflict free), the
+  // first 9 lanes of warp 9 take column 32
+  const bool vox_thread = tid < NVL;
+  const int vlx = tid < FTX * FVY ? (tid % FTX) : FTX;
+  const int vly = tid < FTX * FVY ? (tid / FTX) : (tid - FTX * FVY);
+  const int vslot = vly * FVX + vlx;
+
+  float Fc[3] = {0.f, 0.f, 0.f}, F0c[3] = {0.f, 0.f, 0.f};   // node plane L (complete after layer L)
+  float Fn[3] = {0.f, 0.f, 0.f}, F0n[3] = {0.f, 0.f, 0.f};   // node plane L+1 (partial)
 
   load_plane(z0 - 1);
   load_plane(z0);
-  load_plane(z0 + 1);
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
 
-  const int i = x0 + tx, j = y0 + ty;
-  const bool active = (i < nnx && j < nny);
-  for (int k = z0; k < z1; ++k) {
-    load_plane(k + 2);
+  for (int L = z0 - 1; L < z1; ++L) {
+    if (L + 2 <= z1) load_plane(L + 2);
     cp_async_commit();
-    if (active) {
-      float Fs[3] = {0.f, 0.f, 0.f}, F0[3] = {0.f, 0.f, 0.f};
-      float s2loc = 0.f;
-      #pragma unroll
-      for (int ez = 0; ez < 2; ++ez) {
-        const int sl0 = (k - 1 + ez + 8) & (FNP - 1);   // lower node plane of the voxel
-        const int sl1 = (k + ez + 8) & (FNP - 1);
+    const int s0 = slot_of(L), s1 = slot_of(L + 1);
+    // operands of node L's outputs, loaded now so that their latency overlaps phase A
+    uint8_t cm = 0;
+    float pg[3] = {0.f, 0.f, 0.f}, pr[4][3];
+    const bool fin = active && L >= z0;
+    const long long nL = (long long)i + (long long)nnx * (j + (long long)nny * L);
+    if (fin) {
+      cm = a.cmask ? a.cmask[nL] : 0;
+      if (ro) {
         #pragma unroll
-        for (int ey = 0; ey < 2; ++ey) {
+        for (int c = 0; c < 3; ++c) {
+          pg[c] = gprev[c * NN + nL];
           #pragma unroll
-          for (int ex = 0; ex < 2; ++ex) {
-            const int lx = tx + ex, ly = ty + ey;   // voxel lower corner in tile coordinates
-            const uint8_t ph = sP[(sl0 * FHY + ly) * FHX + lx];
-            if (ph == 255) continue;
-            const float lam = sLam[ph], mu = sMu[ph];
-            // node is corner delta = (1-ex, 1-ey, 1-ez) of this voxel
-            const int dx = 1 - ex, dy = 1 - ey, dz = 1 - ez;
-            const float sx = dx ? 1.f : -1.f, sy = dy ? 1.f : -1.f, sz = dz ? 1.f : -1.f;
-            float G[3][3], GD[3][3];
-            #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              auto u = [&](int cx, int cy, int cz) -> float2 {
-                const int si = sidx(cz ? sl1 : sl0, c, ly + cy, lx + cx);
-                return make_float2(sH[si], sL[si]);
-              };
-              auto dd = [&](int cx, int cy, int cz) -> float {
-                return sD[sidx(cz ? sl1 : sl0, c, ly + cy, lx + cx)];
-              };
-              auto df = [](float2 p, float2 q) -> float {
-                return __fadd_rn(__fsub_rn(p.x, q.x), __fsub_rn(p.y, q.y));
-              };
-              if constexpr (SCHEME == SCHEME_TETRA2) {
-                if (((dx + dy + dz) & 1) == 0) {
-                  // T1 = {000, 110, 101, 011}
-                  const float2 a0 = u(0, 0, 0), b0 = u(1, 1, 0), c0 = u(1, 0, 1), e0 = u(0, 1, 1);
-                  const float d_ba = df(b0, a0), d_ce = df(c0, e0), d_ca = df(c0, a0), d_eb = df(e0, b0);
-                  G[c][0] = (d_ba + d_ce) * inv2h;
-                  G[c][1] = (d_ba - d_ce) * inv2h;
-                  G[c][2] = (d_ca + d_eb) * inv2h;
-                  if (tau_from_delta) {
-                    const float A = dd(0, 0, 0), B = dd(1, 1, 0), Cc = dd(1, 0, 1), E = dd(0, 1, 1);
-                    GD[c][0] = ((B - A) + (Cc - E)) * inv2h;
-                    GD[c][1] = ((B - A) - (Cc - E)) * inv2h;
-                    GD[c][2] = ((Cc - A) + (E - B)) * inv2h;
-                  }
-                } else {
-                  // T2 = {100, 010, 001, 111}
-                  const float2 a1 = u(1, 0, 0), b1 = u(0, 1, 0), c1 = u(0, 0, 1), e1 = u(1, 1, 1);
-                  const float e_ab = df(a1, b1), e_ec = df(e1, c1), e_ca = df(c1, a1), e_eb = df(e1, b1);
-                  G[c][0] = (e_ab + e_ec) * inv2h;
-                  G[c][1] = (e_ec - e_ab) * inv2h;
-                  G[c][2] = (e_ca + e_eb) * inv2h;
-                  if (tau_from_delta) {
-                    const float A = dd(1, 0, 0), B = dd(0, 1, 0), Cc = dd(0, 0, 1), E = dd(1, 1, 1);
-                    GD[c][0] = ((A - B) + (E - Cc)) * inv2h;
-                    GD[c][1] = ((E - Cc) - (A - B)) * inv2h;
-                    GD[c][2] = ((Cc - A) + (E - B)) * inv2h;
-                  }
-                }
-              } else {
-                const float2 u000 = u(0, 0, 0), u100 = u(1, 0, 0), u010 = u(0, 1, 0), u110 = u(1, 1, 0);
-                const float2 u001 = u(0, 0, 1), u101 = u(1, 0, 1), u011 = u(0, 1, 1), u111 = u(1, 1, 1);
-                G[c][0] = (df(u100, u000) + df(u110, u010) + df(u101, u001) + df(u111, u011)) * inv4h;
-                G[c][1] = (df(u010, u000) + df(u110, u100) + df(u011, u001) + df(u111, u101)) * inv4h;
-                G[c][2] = (df(u001, u000) + df(u101, u100) + df(u011, u010) + df(u111, u110)) * inv4h;
-                if (tau_from_delta) {
-                  const float v000 = dd(0, 0, 0), v100 = dd(1, 0, 0), v010 = dd(0, 1, 0), v110 = dd(1, 1, 0);
-                  const float v001 = dd(0, 0, 1), v101 = dd(1, 0, 1), v011 = dd(0, 1, 1), v111 = dd(1, 1, 1);
-                  GD[c][0] = ((v100 - v000) + (v110 - v010) + (v101 - v001) + (v111 - v011)) * inv4h;
-                  GD[c][1] = ((v010 - v000) + (v110 - v100) + (v011 - v001) + (v111 - v101)) * inv4h;
-                  GD[c][2] = ((v001 - v000) + (v101 - v100) + (v011 - v010) + (v111 - v110)) * inv4h;
-                }
-              }
-            }
-            const float exx = eps[0][0] + G[0][0], eyy = eps[1][1] + G[1][1], ezz = eps[2][2] + G[2][2];
-            const float eyz = eps[1][2] + 0.5f * (G[1][2] + G[2][1]);
-            const float exz = eps[0][2] + 0.5f * (G[0][2] + G[2][0]);
-            const float exy = eps[0][1] + 0.5f * (G[0][1] + G[1][0]);
-            const float tr = exx + eyy + ezz;
-            const float sxx = lam * tr + 2.f * mu * exx, syy = lam * tr + 2.f * mu * eyy;
-            const float szz = lam * tr + 2.f * mu * ezz;
-            const float syz = 2.f * mu * eyz, sxz = 2.f * mu * exz, sxy = 2.f * mu * exy;
-            Fs[0] += sxx * sx + sxy * sy + sxz * sz;
-            Fs[1] += sxy * sx + syy * sy + syz * sz;
-            Fs[2] += sxz * sx + syz * sy + szz * sz;
-            if (tau_on) {
-              const float (*GT)[3] = tau_from_delta ? GD : G;
-              #pragma unroll
-              for (int c = 0; c < 3; ++c)
-                F0[c] += (2.f * mu0 + (c == 0 ? lam0 : 0.f)) * GT[c][0] * sx +
-                         (2.f * mu0 + (c == 1 ? lam0 : 0.f)) * GT[c][1] * sy +
-                         (2.f * mu0 + (c == 2 ? lam0 : 0.f)) * GT[c][2] * sz;
-            }
-            // each (voxel, integration point) counted once: TETRA2 T1 by corner 000, T2 by
-            // corner 100; HEX1 by corner 000
-            bool own;
-            if constexpr (SCHEME == SCHEME_TETRA2) own = (dx == 0 && dy == 0 && dz == 0) || (dx == 1 && dy == 0 && dz == 0);
-            else own = (dx == 0 && dy == 0 && dz == 0);
-            if (own) {
-              const float w = (SCHEME == SCHEME_TETRA2) ? 0.5f : 1.f;
-              s2loc += w * (sxx * sxx + syy * syy + szz * szz + 2.f * (syz * syz + sxz * sxz + sxy * sxy));
-            }
-          }
+          for (int q = 0; q < 4; ++q) pr[q][c] = (q == rslot) ? 0.f : Rk[q][c * NN + nL];
         }
       }
-      acc_s2 += (double)s2loc;
-      // node boundary data
-      const long long n = i + (long long)nnx * (j + (long long)nny * k);
-      const uint8_t cm = a.cmask ? a.cmask[n] : 0;
-      const int idx[3] = {i, j, k};
-      #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float invW = 1.f;
-        bool dof = true;
+    }
+
+    // ---------------- phase A: point data of voxel layer L
+    if (vox_thread) {
+      const uint8_t ph = sP[(s0 * FHY + vly) * FHX + vlx];
+      float* out = sV + vslot;
+      if (ph == 255) {
         #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          if (g.periodic[d]) continue;
-          int f = -1;
-          if (idx[d] == 0) f = 0;
-          else if (idx[d] == g.nn[d] - 1) f = 1;
-          if (f < 0) continue;
-          const int t = g.bc[d][f][c];
-          if (t == BC_D) dof = false;
-          else if (t == BC_N) invW *= 2.f;
-        }
-        float pv = 0.f, a0v = 0.f;
-        if (dof) {
-          pv = -Fs[c] * c4h * invW;
-          if (tau_on) a0v = F0[c] * c4h * invW;
-        }
-        const long long e = c * NN + n;
-        const bool free_dof = dof && !((cm >> c) & 1);
-        if (free_dof) acc_p2 += (double)(pv * pv);
-        if (po) po[e] = pv;
-        if (xo) xo[e] = pv + a0v;
-        if (ro) {
-          const float rv = dof ? (pv - gprev[e] + a0v) : 0.f;
-          ro[e] = rv;
-          if (free_dof) {
+        for (int q = 0; q < NPT * QV; ++q) out[q * NVL] = 0.f;
+      } else {
+        const float lam = sLam[ph], mu = sMu[ph];
+        // each voxel's sigma:sigma counted by the tile that holds its lower corner node
+        const bool own = vlx >= 1 && vly >= 1 && L >= z0 && (x0 - 1 + vlx) < g.nvox[0] &&
+                         (y0 - 1 + vly) < g.nvox[1] && L < g.nvox[2];
+        const float w = (SCHEME == SCHEME_TETRA2) ? 0.5f : 1.f;
+        // corner b = cx + 2 cy + 4 cz of the voxel, component c
+        auto corner = [&](int b, int c) { return sidx((b >> 2) ? s1 : s0, c, vly + ((b >> 1) & 1), vlx + (b & 1)); };
+        #pragma unroll
+        for (int t = 0; t < NPT; ++t) {
+          float G[3][3], GD[3][3];
+          #pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            if constexpr (SCHEME == SCHEME_TETRA2) {
+              // T1 = {000, 110, 101, 011} = corners {0, 3, 5, 6}; T2 = {100, 010, 001, 111} =
+              // corners {1, 2, 4, 7}; with (a, b, c, e) in that order the two gradients are
+              //   T1: ((b-a) + (c-e), (b-a) - (c-e), (c-a) + (e-b)) / 2h
+              //   T2: ((a-b) + (e-c), (e-c) - (a-b), (c-a) + (e-b)) / 2h
+              const int ia = corner(t ? 1 : 0, c), ib = corner(t ? 2 : 3, c);
+              const int ic = corner(t ? 4 : 5, c), ie = corner(t ? 7 : 6, c);
+              const float ah = sH[ia], al = sL[ia], bh = sH[ib], bl = sL[ib];
+              const float ch = sH[ic], cl = sL[ic], eh = sH[ie], el = sL[ie];
+              const float A = sD[ia], B = sD[ib], Cc = sD[ic], E = sD[ie];
+              const float d_ca = fdiff(ch, cl, ah, al), d_eb = fdiff(eh, el, bh, bl);
+              G[c][2] = (d_ca + d_eb) * inv2h;
+              GD[c][2] = ((Cc - A) + (E - B)) * inv2h;
+              if (t == 0) {
+                const float d_ba = fdiff(bh, bl, ah, al), d_ce = fdiff(ch, cl, eh, el);
+                G[c][0] = (d_ba + d_ce) * inv2h;
+                G[c][1] = (d_ba - d_ce) * inv2h;
+                GD[c][0] = ((B - A) + (Cc - E)) * inv2h;
+                GD[c][1] = ((B - A) - (Cc - E)) * inv2h;
+              } else {
+                const float e_ab = fdiff(ah, al, bh, bl), e_ec = fdiff(eh, el, ch, cl);
+                G[c][0] = (e_ab + e_ec) * inv2h;
+                G[c][1] = (e_ec - e_ab) * inv2h;
+                GD[c][0] = ((A - B) + (E - Cc)) * inv2h;
+                GD[c][1] = ((E - Cc) - (A - B)) * inv2h;
+              }
+            } else {
+              float uh[8], ul[8], ud[8];
+              #pragma unroll
+              for (int b = 0; b < 8; ++b) {
+                const int si = corner(b, c);
+                uh[b] = sH[si];
+                ul[b] = sL[si];
+                ud[b] = sD[si];
+              }
+              auto d = [&](int p, int q) { return fdiff(uh[p], ul[p], uh[q], ul[q]); };
+              G[c][0] = (d(1, 0) + d(3, 2) + d(5, 4) + d(7, 6)) * inv4h;
+              G[c][1] = (d(2, 0) + d(3, 1) + d(6, 4) + d(7, 5)) * inv4h;
+              G[c][2] = (d(4, 0) + d(5, 1) + d(6, 2) + d(7, 3)) * inv4h;
+              GD[c][0] = ((ud[1] - ud[0]) + (ud[3] - ud[2]) + (ud[5] - ud[4]) + (ud[7] - ud[6])) * inv4h;
+              GD[c][1] = ((ud[2] - ud[0]) + (ud[3] - ud[1]) + (ud[6] - ud[4]) + (ud[7] - ud[5])) * inv4h;
+              GD[c][2] = ((ud[4] - ud[0]) + (ud[5] - ud[1]) + (ud[6] - ud[2]) + (ud[7] - ud[3])) * inv4h;
+            }
+          }
+          const float exx = eps[0][0] + G[0][0], eyy = eps[1][1] + G[1][1];
+          const float ezz = eps[2][2] + G[2][2];
+          const float eyz = eps[1][2] + 0.5f * (G[1][2] + G[2][1]);
+          const float exz = eps[0][2] + 0.5f * (G[0][2] + G[2][0]);
+          const float exy = eps[0][1] + 0.5f * (G[0][1] + G[1][0]);
+          const float tr = exx + eyy + ezz;
+          const float sxx = lam * tr + 2.f * mu * exx, syy = lam * tr + 2.f * mu * eyy;
+          const float szz = lam * tr + 2.f * mu * ezz;
+          const float syz = 2.f * mu * eyz, sxz = 2.f * mu * exz, sxy = 2.f * mu * exy;
+          float* o = out + t * QV * NVL;
+          o[0 * NVL] = sxx;
+          o[1 * NVL] = syy;
+          o[2 * NVL] = szz;
+          o[3 * NVL] = syz;
+          o[4 * NVL] = sxz;
+          o[5 * NVL] = sxy;
+          if (tau_on) {
             #pragma unroll
-            for (int q = 0; q < 4; ++q) acc_g[q] += (double)(rv * (q == rslot ? rv : Rk[q][e]));
+            for (int c = 0; c < 3; ++c)
+              #pragma unroll
+              for (int dd = 0; dd < 3; ++dd)
+                o[(6 + 3 * c + dd) * NVL] =
+                    (2.f * mu0 + (c == dd ? lam0 : 0.f)) * (tau_from_delta ? GD[c][dd] : G[c][dd]);
+          }
+          if (own) acc_s2.add(w * (sxx * sxx + syy * syy + szz * szz + 2.f * (syz * syz + sxz * sxz + sxy * sxy)));
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---------------- phase B: gather into node L (lower corner) and node L+1 (upper corner)
+    if (active) {
+      #pragma unroll
+      for (int ey = 0; ey < 2; ++ey) {
+        #pragma unroll
+        for (int ex = 0; ex < 2; ++ex) {
+          const int v = (ty + ey) * FVX + (tx + ex);
+          const int dx = 1 - ex, dy = 1 - ey;
+          const float sx = dx ? 1.f : -1.f, sy = dy ? 1.f : -1.f;
+          // node L is corner (dx, dy, 0) of the voxel, node L+1 its corner (dx, dy, 1);
+          // TETRA2: the point whose tetrahedron holds the corner (T1 = even parity)
+          const int tlo = (SCHEME == SCHEME_TETRA2) ? ((dx + dy) & 1) : 0;
+          const int thi = (SCHEME == SCHEME_TETRA2) ? (1 - tlo) : 0;
+          auto gather = [&](float (&F)[3], float (&F0)[3], int t, float sz) {
+            const float* q = sV + t * QV * NVL + v;
+            const float sxx = q[0], syy = q[NVL], szz = q[2 * NVL];
+            const float syz = q[3 * NVL], sxz = q[4 * NVL], sxy = q[5 * NVL];
+            F[0] += sxx * sx + sxy * sy + sxz * sz;
+            F[1] += sxy * sx + syy * sy + syz * sz;
+            F[2] += sxz * sx + syz * sy + szz * sz;
+            if (tau_on) {
+              #pragma unroll
+              for (int c = 0; c < 3; ++c)
+                F0[c] += q[(6 + 3 * c) * NVL] * sx + q[(7 + 3 * c) * NVL] * sy + q[(8 + 3 * c) * NVL] * sz;
+            }
+          };
+          gather(Fc, F0c, tlo, -1.f);
+          gather(Fn, F0n, thi, 1.f);
+        }
+      }
+      // node plane L is complete
+      if (fin) {
+        const int k = L;
+        const long long n = nL;
+        const int idx[3] = {i, j, k};
+        float p2loc = 0.f, gloc[4] = {0.f, 0.f, 0.f, 0.f};
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float invW = 1.f;
+          bool dof = true;
+          #pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            if (g.periodic[d]) continue;
+            int f = -1;
+            if (idx[d] == 0) f = 0;
+            else if (idx[d] == g.nn[d] - 1) f = 1;
+            if (f < 0) continue;
+            const int t = g.bc[d][f][c];
+            if (t == BC_D) dof = false;
+            else if (t == BC_N) invW *= 2.f;
+          }
+          float pv = 0.f, a0v = 0.f;
+          if (dof) {
+            pv = -Fc[c] * c4h * invW;
+            if (tau_on) a0v = F0c[c] * c4h * invW;
+          }
+          const long long e = c * NN + n;
+          const bool free_dof = dof && !((cm >> c) & 1);
+          if (free_dof) p2loc = fmaf(pv, pv, p2loc);
+          if (po) po[e] = pv;
+          if (xo) xo[e] = pv + a0v;
+          if (ro) {
+            const float rv = dof ? (pv - pg[c] + a0v) : 0.f;
+            ro[e] = rv;
+            if (free_dof) {
+              #pragma unroll
+              for (int q = 0; q < 4; ++q) gloc[q] = fmaf(rv, (q == rslot ? rv : pr[q][c]), gloc[q]);
+            }
           }
         }
+        acc_p2.add(p2loc);
+        if (ro) {
+          #pragma unroll
+          for (int q = 0; q < 4; ++q) acc_g[q].add(gloc[q]);
+        }
+      }
+      #pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Fc[c] = Fn[c];
+        F0c[c] = F0n[c];
+        Fn[c] = 0.f;
+        F0n[c] = 0.f;
       }
     }
     cp_async_wait_all();
     __syncthreads();
   }
 
-  // block reduction (FP64)
-  double v[6] = {acc_s2, acc_p2, acc_g[0], acc_g[1], acc_g[2], acc_g[3]};
+  // block reduction: compensated FP32 pairs across the warp, FP64 across warps
+  Acc2 v[6] = {acc_s2, acc_p2, acc_g[0], acc_g[1], acc_g[2], acc_g[3]};
   const int warp = tid >> 5, lane = tid & 31;
   #pragma unroll
   for (int q = 0; q < 6; ++q) {
-    double t = v[q];
+    Acc2 t = v[q];
     #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-    if (lane == 0) sRed[q][warp] = t;
+    for (int off = 16; off > 0; off >>= 1) {
+      const float os = __shfl_down_sync(0xffffffffu, t.s, off);
+      const float oc = __shfl_down_sync(0xffffffffu, t.c, off);
+      t.add(os);
+      t.c += oc;
+    }
+    if (lane == 0) sRed[q][warp] = t.value();
   }
   __syncthreads();
   if (tid < 6) {
     double t = 0.0;
-    for (int w = 0; w < FTX * FTY / 32; ++w) t += sRed[tid][w];
+    for (int w = 0; w < FTHREADS / 32; ++w) t += sRed[tid][w];
     const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     a.partials[6 * b + tid] = t;
   }
 }
 
+namespace {
+int resident_ctas() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cached = 2 * sms;
+  }
+  return cached;
+}
+}  // namespace
+
+// z planes per CTA: about two waves of resident CTAs, at least 4 planes per CTA (each CTA
+// also processes the voxel layer below its first plane).
 int residual_f32_zchunk(const GridDev& g) {
   long long bxy = (long long)((g.nn[0] + FTX - 1) / FTX) * ((g.nn[1] + FTY - 1) / FTY);
-  long long want = 148LL * 4;
+  long long want = 2LL * resident_ctas();
   long long zc = (g.nn[2] * bxy + want - 1) / want;
-  if (zc < 2) zc = 2;
-  if (zc > 32) zc = 32;
+  if (zc < 4) zc = 4;
+  if (zc > 64) zc = 64;
   return (int)zc;
 }
 
@@ -338,18 +445,25 @@ int residual_f32_blocks(const GridDev& g) {
 template <int SCHEME>
 static int launch_f32_impl(const ResidualArgs& a, cudaStream_t s) {
   const int zc = residual_f32_zchunk(a.g);
-  dim3 blk(FTX, FTY);
   dim3 grd((a.g.nn[0] + FTX - 1) / FTX, (a.g.nn[1] + FTY - 1) / FTY, (a.g.nn[2] + zc - 1) / zc);
   ResidualArgs aa = a;
   aa.zchunk = zc;
-  const size_t sm = (size_t)3 * FNP * FPLANE * sizeof(float) + (size_t)FNP * FHY * FHX;
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) aa.f_eps[p][q] = (float)a.eps[p][q];
+  aa.f_lam0 = (float)a.lam0;
+  aa.f_mu0 = (float)a.mu0;
+  aa.f_inv2h = (float)(1.0 / (2.0 * a.g.h));
+  aa.f_inv4h = (float)(1.0 / (4.0 * a.g.h));
+  constexpr int NPT = (SCHEME == SCHEME_TETRA2) ? 2 : 1;
+  const size_t sm = (size_t)3 * FNP * FPLANE * sizeof(float) + (size_t)NPT * QV * NVL * sizeof(float) +
+                    (size_t)FNP * FHY * FHX;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_residual_f32<SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     attr = true;
   }
-  k_residual_f32<SCHEME><<<grd, blk, sm, s>>>(aa);
+  k_residual_f32<SCHEME><<<grd, FTHREADS, sm, s>>>(aa);
   return (int)cudaGetLastError();
 }
 
