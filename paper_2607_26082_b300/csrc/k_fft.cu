@@ -16,6 +16,8 @@
 // inverse DFT of X extended as X_{2n-1-k} = +-X_k and read x_j from e^{+i pi j / 2n} Z_j / n.
 // These follow from the trigonometric sums of the transforms (Section 3.2.2, Tables 2-3);
 // the 4n-extended DFT of Eq. 7 is the same idea with the redundant half removed.
+#include <cstdlib>
+
 #include "dtt_internal.cuh"
 
 namespace dtt {
@@ -410,6 +412,424 @@ k_fft_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenT
   }
 }
 
+// ==== register-radix route for power-of-two lengths 16..2048 (compile-time L) ==============
+//
+// L / 8 threads own one complex sequence; each radix-8 pass (radix 4 or 2 for the last
+// factor) loads 8 values per thread from shared memory, applies the Stockham twiddles and a
+// DFT in registers, and writes back in place between two barriers.  The sequence lives in
+// shared memory as separate real and imaginary arrays with one padding word per 32, so the
+// strided writes of the first passes hit distinct banks.  256 threads: 2048 / L sequences
+// (twice as many real pencils) per CTA.
+
+__device__ __forceinline__ int padi(int i) { return i + (i >> 5); }
+
+template <int L>
+struct FastPlan {
+  static constexpr int NT = L / 8;        // threads per sequence
+  static constexpr int SEQ = 2048 / L;    // sequences per CTA
+  static constexpr int PADL = L + L / 32; // padded words per component of one sequence
+};
+
+// 8-point DFT with kernel e^{s 2 pi i j k / 8}, natural-order output (decimation in
+// frequency; the bit-reversed result is reordered in registers).
+template <typename T>
+__device__ __forceinline__ void dft8(Cx<T>* v, int s) {
+  const T h = (T)0.70710678118654752440;
+  const T sf = (T)s;
+  Cx<T> a[8];
+  #pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    a[j] = {v[j].x + v[j + 4].x, v[j].y + v[j + 4].y};
+    a[j + 4] = {v[j].x - v[j + 4].x, v[j].y - v[j + 4].y};
+  }
+  // a[4 + j] *= w^j, w = e^{s 2 pi i / 8}
+  {
+    const Cx<T> b = a[5];
+    a[5] = {h * (b.x - sf * b.y), h * (sf * b.x + b.y)};
+    const Cx<T> c = a[6];
+    a[6] = {-sf * c.y, sf * c.x};
+    const Cx<T> d = a[7];
+    a[7] = {h * (-d.x - sf * d.y), h * (sf * d.x - d.y)};
+  }
+  #pragma unroll
+  for (int hb = 0; hb < 8; hb += 4) {
+    #pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const Cx<T> x = a[hb + j], y = a[hb + j + 2];
+      a[hb + j] = {x.x + y.x, x.y + y.y};
+      const Cx<T> d = {x.x - y.x, x.y - y.y};
+      a[hb + j + 2] = j ? Cx<T>{-sf * d.y, sf * d.x} : d;
+    }
+  }
+  #pragma unroll
+  for (int p = 0; p < 8; p += 2) {
+    const Cx<T> x = a[p], y = a[p + 1];
+    a[p] = {x.x + y.x, x.y + y.y};
+    a[p + 1] = {x.x - y.x, x.y - y.y};
+  }
+  v[0] = a[0]; v[4] = a[1]; v[2] = a[2]; v[6] = a[3];
+  v[1] = a[4]; v[5] = a[5]; v[3] = a[6]; v[7] = a[7];
+}
+
+// One in-place Stockham pass of radix R (stride NS) over the CTA's sequences; thread t of
+// sequence `seq` takes butterflies t, t + NT, ... (8 / R of them).  With `mod`, the inputs
+// are first multiplied by mod[index] (quarter-wave modulation of the forward transforms).
+template <typename T, int L, int R, int NS>
+__device__ __forceinline__ void fast_pass(T* re, T* im, const Cx<T>* __restrict__ tw, int sgn, int seq, int t,
+                                          const Cx<T>* __restrict__ mod) {
+  constexpr int NT = FastPlan<L>::NT, PADL = FastPlan<L>::PADL;
+  constexpr int LR = L / R, PER = 8 / R, TWS = L / (NS * R);
+  T* sr = re + seq * PADL;
+  T* si = im + seq * PADL;
+  Cx<T> v[PER][R];
+  #pragma unroll
+  for (int m = 0; m < PER; ++m) {
+    const int jb = t + m * NT;
+    const int k = jb & (NS - 1);
+    #pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int idx = jb + r * LR;
+      v[m][r] = {sr[padi(idx)], si[padi(idx)]};
+      if (mod) v[m][r] = cmul(v[m][r], mod[idx]);
+    }
+    if (NS > 1) {
+      #pragma unroll
+      for (int r = 1; r < R; ++r) {
+        Cx<T> w = tw[k * r * TWS];
+        if (sgn > 0) w.y = -w.y;
+        v[m][r] = cmul(v[m][r], w);
+      }
+    }
+    if constexpr (R == 8) dft8(v[m], sgn);
+    else if constexpr (R == 4) dft4(v[m], sgn);
+    else dft2(v[m]);
+  }
+  __syncthreads();
+  #pragma unroll
+  for (int m = 0; m < PER; ++m) {
+    const int jb = t + m * NT;
+    const int k = jb & (NS - 1);
+    const int o = (jb - k) * R + k;
+    #pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int idx = o + r * NS;
+      sr[padi(idx)] = v[m][r].x;
+      si[padi(idx)] = v[m][r].y;
+    }
+  }
+  __syncthreads();
+}
+
+// Whole FFT of length L: radix-8 passes, then one radix-4 or radix-2 pass for the rest.
+template <typename T, int L, int NS = 1>
+__device__ __forceinline__ void fast_fft(T* re, T* im, const Cx<T>* tw, int sgn, int seq, int t,
+                                         const Cx<T>* mod) {
+  if constexpr (NS * 8 <= L) {
+    fast_pass<T, L, 8, NS>(re, im, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
+    fast_fft<T, L, NS * 8>(re, im, tw, sgn, seq, t, nullptr);
+  } else if constexpr (NS * 4 == L) {
+    fast_pass<T, L, 4, NS>(re, im, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
+  } else if constexpr (NS * 2 == L) {
+    fast_pass<T, L, 2, NS>(re, im, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
+  }
+}
+
+// Value v of real pencil pb at axis position j into the extended sequence of its pair (the
+// same extensions as fill_sequences), in the padded real / imaginary arrays.
+template <typename T, int L>
+__device__ __forceinline__ void fast_place(T* re, T* im, int pb, int j, T v, int n, int type, int inverse) {
+  constexpr int PADL = FastPlan<L>::PADL;
+  T* S = ((pb & 1) ? im : re) + (pb >> 1) * PADL;
+  const bool quarter = (type == T_DCT3 || type == T_DST3);
+  if (!inverse || !quarter) {
+    switch (type) {
+      case T_DCT1:
+        S[padi(j)] = v;
+        if (j >= 1 && j <= n - 1) S[padi(2 * n - j)] = v;
+        break;
+      case T_DST1:
+        if (j >= 1 && j <= n - 1) { S[padi(j)] = v; S[padi(2 * n - j)] = -v; }
+        break;
+      case T_DCT3:
+        if (j <= n - 1) { S[padi(j)] = v; if (j >= 1) S[padi(2 * n - j)] = -v; }
+        break;
+      case T_DST3:
+        if (j >= 1) { S[padi(j)] = v; if (j <= n - 1) S[padi(2 * n - j)] = v; }
+        break;
+      default:
+        S[padi(j)] = v;
+        break;
+    }
+  } else if (j < n) {
+    S[padi(j)] = v;
+    S[padi(2 * n - 1 - j)] = type == T_DCT3 ? v : -v;
+  }
+}
+
+// Transform value of pencil pb at position k from the FFT result of its pair (post_value on
+// the padded arrays).
+template <typename T, int L>
+__device__ __forceinline__ T fast_post(const T* re, const T* im, int pb, int k, int n, int type, int inverse, T sc,
+                                       const Cx<T>* ph, T inv_n) {
+  constexpr int PADL = FastPlan<L>::PADL;
+  const T* yr = re + (pb >> 1) * PADL;
+  const T* yi = im + (pb >> 1) * PADL;
+  const bool imf = pb & 1;
+  const T half = (T)0.5;
+  const bool quarter = (type == T_DCT3 || type == T_DST3);
+  if (!inverse || !quarter) {
+    T val = (T)0;
+    switch (type) {
+      case T_DCT1:
+        val = half * (imf ? yi[padi(k)] : yr[padi(k)]);
+        break;
+      case T_DST1:
+        if (k >= 1 && k <= n - 1) val = imf ? half * yr[padi(k)] : -half * yi[padi(k)];
+        break;
+      case T_DCT3:
+        if (k <= n - 1) val = half * (imf ? yi[padi(k)] : yr[padi(k)]);
+        break;
+      case T_DST3:
+        if (k <= n - 1) val = imf ? half * yr[padi(k)] : -half * yi[padi(k)];
+        break;
+      default: {
+        const int kk = k == 0 ? 0 : n - k;
+        const T ax = yr[padi(k)], ay = yi[padi(k)], bx = yr[padi(kk)], by = yi[padi(kk)];
+        val = imf ? half * (ax - bx + ay + by) : half * (ax + bx - ay + by);
+        break;
+      }
+    }
+    return val * sc;
+  }
+  const Cx<T> w = {ph[k].x, -ph[k].y};
+  const Cx<T> e = cmul(Cx<T>{yr[padi(k)], yi[padi(k)]}, w);
+  if (type == T_DCT3) return (k <= n - 1) ? (imf ? e.y : e.x) * inv_n : (T)0;
+  return (k >= 1) ? (imf ? -e.x : e.y) * inv_n : (T)0;
+}
+
+template <typename T, int L>
+__host__ __device__ constexpr size_t fast_smem(int extra_bytes) {
+  return (size_t)2 * FastPlan<L>::SEQ * FastPlan<L>::PADL * sizeof(T) + (size_t)L * sizeof(Cx<T>) +
+         (size_t)extra_bytes;
+}
+
+// Axis pass on the register-radix route (same contract as k_fft_axis).
+template <typename T, int L>
+__global__ void __launch_bounds__(256)
+k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctrl* ctrl, void* const* in_ring) {
+  constexpr int SEQ = FastPlan<L>::SEQ, NT = FastPlan<L>::NT, PADL = FastPlan<L>::PADL, NPEN = 2 * SEQ;
+  if (ctrl && ctrl->done) return;
+  if (in_ring) in = (const T*)in_ring[ctrl->i_local % 4];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long sbase[NPEN];
+  T* re = (T*)smem_raw;
+  T* im = re + SEQ * PADL;
+  Cx<T>* tws = (Cx<T>*)(im + SEQ * PADL);
+  const int comp = p.comp0 + blockIdx.y;
+  const int type = p.type[comp];
+  const int tid = threadIdx.x;
+  const long long pen0 = (long long)blockIdx.x * NPEN;
+  const T* src = in + (long long)comp * p.NN;
+  const long long coff = (long long)comp * p.NN;
+  const long long stride = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)p.nnx : (long long)p.nnx * p.nny);
+  const int npen = (int)min((long long)NPEN, p.npencil - pen0);
+  const int n = p.n, nn = p.nn;
+  pencil_bases<T, SEQ>(sbase, p, pen0, tid);
+  for (int q = tid; q < L; q += 256) tws[q] = ((const Cx<T>*)p.tw)[q];
+  for (int q = tid; q < 2 * SEQ * PADL; q += 256) re[q] = (T)0;
+  __syncthreads();
+  if (p.axis == 0) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int pb = warp; pb < npen; pb += 8)
+      for (int j = lane; j < nn; j += 32) fast_place<T, L>(re, im, pb, j, src[sbase[pb] + j], n, type, p.inverse);
+  } else {
+    for (int idx = tid; idx < NPEN * nn; idx += 256) {
+      const int pb = idx % NPEN, j = idx / NPEN;
+      if (pb < npen) fast_place<T, L>(re, im, pb, j, src[sbase[pb] + j * stride], n, type, p.inverse);
+    }
+  }
+  __syncthreads();
+  const bool quarter = (type == T_DCT3 || type == T_DST3);
+  const int sgn = (p.inverse && quarter) ? 1 : -1;
+  const Cx<T>* ph = (const Cx<T>*)p.ph;
+  fast_fft<T, L>(re, im, tws, sgn, tid / NT, tid % NT, (quarter && !p.inverse) ? ph : nullptr);
+  const T sc = sizeof(T) == 4 ? (T)p.fscale : (T)p.scale;
+  const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
+  auto emit = [&](int pb, int k) {
+    const T v = fast_post<T, L>(re, im, pb, k, n, type, p.inverse, sc, ph, inv_n);
+    const long long e = coff + sbase[pb] + k * stride;
+    if (p.incr) add_to_u<T>(e, v, p);
+    else out[e] = v;
+  };
+  if (p.axis == 0) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int pb = warp; pb < npen; pb += 8)
+      for (int k = lane; k < nn; k += 32) emit(pb, k);
+  } else {
+    for (int idx = tid; idx < NPEN * nn; idx += 256) {
+      const int pb = idx % NPEN, k = idx / NPEN;
+      if (pb < npen) emit(pb, k);
+    }
+  }
+}
+
+// Fused z pass on the register-radix route (same contract as k_fft_z_green).
+template <typename T, int L>
+__global__ void __launch_bounds__(256)
+k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenTables gt, T l0, T m2, T ih2,
+                   int scheme, T zscale, const Ctrl* ctrl) {
+  constexpr int SEQ = FastPlan<L>::SEQ, NT = FastPlan<L>::NT, PADL = FastPlan<L>::PADL, NPEN = 2 * SEQ;
+  if (ctrl && ctrl->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long sbase[NPEN];
+  __shared__ T pxy[NPEN][4];   // per pencil: s_x, c'_x, s_y, c'_y
+  T* re = (T*)smem_raw;
+  T* im = re + SEQ * PADL;
+  Cx<T>* tws = (Cx<T>*)(im + SEQ * PADL);
+  T* zs = (T*)(tws + L);   // s_z[k], k < nn
+  T* zc = zs + p.nn;       // c'_z[k]
+  T* spec = zc + p.nn;     // NPEN x nn spectra
+  const int comp = p.comp0 + blockIdx.y;
+  const int type = p.type[comp];
+  const int tid = threadIdx.x;
+  const long long pen0 = (long long)blockIdx.x * NPEN;
+  const long long coff = (long long)comp * p.NN;
+  const long long stride = (long long)p.nnx * p.nny;
+  const int npen = (int)min((long long)NPEN, p.npencil - pen0);
+  const int n = p.n, nn = p.nn;
+  const Cx<T>* ph = (const Cx<T>*)p.ph;
+  pencil_bases<T, SEQ>(sbase, p, pen0, tid);
+  for (int q = tid; q < NPEN; q += 256) {
+    const long long pen = pen0 + q;
+    const int ix = pen < p.npencil ? (int)(pen % p.nnx) : 0, iy = pen < p.npencil ? (int)(pen / p.nnx) : 0;
+    pxy[q][0] = (T)gt.s[comp][0][ix];
+    pxy[q][1] = (T)gt.cp[comp][0][ix];
+    pxy[q][2] = (T)gt.s[comp][1][iy];
+    pxy[q][3] = (T)gt.cp[comp][1][iy];
+  }
+  for (int q = tid; q < L; q += 256) tws[q] = ((const Cx<T>*)p.tw)[q];
+  for (int q = tid; q < nn; q += 256) {
+    zs[q] = (T)gt.s[comp][2][q];
+    zc[q] = (T)gt.cp[comp][2][q];
+  }
+  for (int q = tid; q < 2 * SEQ * PADL; q += 256) re[q] = (T)0;
+  __syncthreads();
+  const bool quarter = (type == T_DCT3 || type == T_DST3);
+  const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
+  // forward along z
+  for (int idx = tid; idx < NPEN * nn; idx += 256) {
+    const int pb = idx % NPEN, j = idx / NPEN;
+    if (pb < npen) fast_place<T, L>(re, im, pb, j, in[coff + sbase[pb] + j * stride], n, type, 0);
+  }
+  __syncthreads();
+  fast_fft<T, L>(re, im, tws, -1, tid / NT, tid % NT, quarter ? ph : nullptr);
+  // Green multiply into spec
+  const T thr = (T)gt.null_thr[comp];
+  for (int idx = tid; idx < NPEN * nn; idx += 256) {
+    const int pb = idx % NPEN, k = idx / NPEN;
+    T v = (T)0;
+    if (pb < npen) {
+      v = fast_post<T, L>(re, im, pb, k, n, type, 0, (T)1, ph, inv_n);
+      const T sx = pxy[pb][0], cx = pxy[pb][1], sy = pxy[pb][2], cy = pxy[pb][3];
+      const T sz = zs[k], cz = zc[k];
+      T Sx, Sy, Sz;
+      if (scheme == SCHEME_TETRA2) {
+        Sx = tetra_S<T>(sx, cy, sy, cx, sz);
+        Sy = tetra_S<T>(sy, cz, sz, cy, sx);
+        Sz = tetra_S<T>(sz, cx, sx, cz, sy);
+      } else {
+        Sx = sx * cy * cz;
+        Sy = sy * cx * cz;
+        Sz = sz * cx * cy;
+      }
+      const T Sc = comp == 0 ? Sx : (comp == 1 ? Sy : Sz);
+      const T a = (l0 * Sc + m2 * (Sx + Sy + Sz)) * ih2;
+      v = (a <= thr) ? (T)0 : v / a;
+    }
+    spec[pb * nn + k] = v;
+  }
+  __syncthreads();
+  // inverse along z
+  for (int q = tid; q < 2 * SEQ * PADL; q += 256) re[q] = (T)0;
+  __syncthreads();
+  for (int idx = tid; idx < NPEN * nn; idx += 256) {
+    const int pb = idx % NPEN, j = idx / NPEN;
+    if (pb < npen) fast_place<T, L>(re, im, pb, j, spec[pb * nn + j], n, type, 1);
+  }
+  __syncthreads();
+  fast_fft<T, L>(re, im, tws, quarter ? 1 : -1, tid / NT, tid % NT, nullptr);
+  for (int idx = tid; idx < NPEN * nn; idx += 256) {
+    const int pb = idx % NPEN, k = idx / NPEN;
+    if (pb < npen) out[coff + sbase[pb] + k * stride] = fast_post<T, L>(re, im, pb, k, n, type, 1, zscale, ph, inv_n);
+  }
+}
+
+template <typename K>
+static int ensure_smem(K kernel, size_t sm, size_t& done);
+
+// DTT_FFT_GENERIC=1 keeps every length on the generic Stockham kernels (route-agreement
+// tests); read at every launch, so it applies to graphs captured after it is set.
+static bool generic_only() {
+  const char* e = std::getenv("DTT_FFT_GENERIC");
+  return e && e[0] == '1';
+}
+
+// Register-radix dispatch; returns -1 when L is not a power of two in 16..2048.
+template <typename T, int L>
+static int launch_fast_L(const T* in, T* out, const FftParams& p, int ncomp, const Ctrl* ctrl, void* const* in_ring,
+                         cudaStream_t s) {
+  constexpr int NPEN = 2 * FastPlan<L>::SEQ;
+  dim3 grd((unsigned)((p.npencil + NPEN - 1) / NPEN), ncomp);
+  const size_t sm = fast_smem<T, L>(0);
+  static size_t attr = 48 * 1024;
+  if (int e = ensure_smem(k_fft_fast<T, L>, sm, attr)) return e;
+  k_fft_fast<T, L><<<grd, 256, sm, s>>>(in, out, p, ctrl, in_ring);
+  return (int)cudaGetLastError();
+}
+
+template <typename T, int L>
+static int launch_fast_zg_L(const T* in, T* out, const FftParams& p, const GreenTables& gt, T l0, T m2, T ih2,
+                            int scheme, T zscale, int ncomp, const Ctrl* ctrl, cudaStream_t s) {
+  constexpr int NPEN = 2 * FastPlan<L>::SEQ;
+  dim3 grd((unsigned)((p.npencil + NPEN - 1) / NPEN), ncomp);
+  const size_t sm = fast_smem<T, L>((int)((2 + NPEN) * p.nn * sizeof(T)));
+  static size_t attr = 48 * 1024;
+  if (int e = ensure_smem(k_fft_fast_z_green<T, L>, sm, attr)) return e;
+  k_fft_fast_z_green<T, L><<<grd, 256, sm, s>>>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ctrl);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+static int launch_fast(const T* in, T* out, const FftParams& p, int ncomp, const Ctrl* ctrl, void* const* in_ring,
+                       cudaStream_t s) {
+  switch (p.L) {
+    case 16: return launch_fast_L<T, 16>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 32: return launch_fast_L<T, 32>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 64: return launch_fast_L<T, 64>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 128: return launch_fast_L<T, 128>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 256: return launch_fast_L<T, 256>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 512: return launch_fast_L<T, 512>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 1024: return launch_fast_L<T, 1024>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 2048: return launch_fast_L<T, 2048>(in, out, p, ncomp, ctrl, in_ring, s);
+    default: return -1;
+  }
+}
+
+template <typename T>
+static int launch_fast_zg(const T* in, T* out, const FftParams& p, const GreenTables& gt, T l0, T m2, T ih2,
+                          int scheme, T zscale, int ncomp, const Ctrl* ctrl, cudaStream_t s) {
+  switch (p.L) {
+    case 16: return launch_fast_zg_L<T, 16>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    case 32: return launch_fast_zg_L<T, 32>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    case 64: return launch_fast_zg_L<T, 64>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    case 128: return launch_fast_zg_L<T, 128>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    case 256: return launch_fast_zg_L<T, 256>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    case 512: return launch_fast_zg_L<T, 512>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    case 1024: return launch_fast_zg_L<T, 1024>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    default: return -1;
+  }
+}
+
 template <typename T>
 int fft_pb(int L) {
   // pairs per CTA: two buffers of PB * L complex values within ~100 KB of shared memory
@@ -457,6 +877,12 @@ static int launch_zg_pb(const T* in, T* out, const FftParams& p, const GreenTabl
 template <typename T>
 int launch_fft_z_green(const T* in, T* out, const FftParams& p, const GreenTables& gt, double lam0, double mu0,
                        int scheme, double h, int ncomp, const Ctrl* ctrl, cudaStream_t s) {
+  if (!generic_only()) {
+    const T l0 = (T)lam0, m2 = (T)(2.0 * mu0), ih2 = (T)(4.0 / (h * h));
+    const T zscale = (T)((p.L == p.n) ? 1.0 / p.n : 2.0 / p.n);
+    const int r = launch_fast_zg<T>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    if (r >= 0) return r;
+  }
   switch (fft_pb<T>(p.L)) {
     case 8: return launch_zg_pb<T, 8>(in, out, p, gt, lam0, mu0, scheme, h, ncomp, ctrl, s);
     case 4: return launch_zg_pb<T, 4>(in, out, p, gt, lam0, mu0, scheme, h, ncomp, ctrl, s);
@@ -469,6 +895,10 @@ int launch_fft_z_green(const T* in, T* out, const FftParams& p, const GreenTable
 template <typename T>
 int launch_fft_axis(const T* in, T* out, const FftParams& p, int ncomp, const Ctrl* ctrl, void* const* in_ring,
                     cudaStream_t s) {
+  if (!generic_only()) {
+    const int r = launch_fast<T>(in, out, p, ncomp, ctrl, in_ring, s);
+    if (r >= 0) return r;
+  }
   switch (fft_pb<T>(p.L)) {
     case 8: return launch_fft_pb<T, 8>(in, out, p, ncomp, ctrl, in_ring, s);
     case 4: return launch_fft_pb<T, 4>(in, out, p, ncomp, ctrl, in_ring, s);

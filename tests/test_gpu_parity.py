@@ -56,7 +56,8 @@ def _oracle_forward_real(pb, c, x):
 
 # ----------------------------------------------------------------------------- transforms
 TRANSFORM_SIZES = [(5, 4, 6), (33, 7, 18), (70, 9, 35),          # dense route (prime factors)
-                   (16, 12, 24), (48, 9, 32), (27, 6, 40)]        # FFT route (radix 4/2/3)
+                   (16, 12, 24), (48, 9, 32), (27, 6, 40),        # FFT route (radix 4/2/3)
+                   (32, 8, 64), (128, 4, 16), (1024, 2, 3)]       # register-radix route (2^k)
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -103,6 +104,31 @@ def test_fft_and_dense_routes_agree(monkeypatch):
                 a = g_fft.dtt_transform(c, inv, x)
                 b = g_den.dtt_transform(c, inv, x)
                 assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (MIXED, 3e-6)])
+def test_fft_register_and_generic_routes_agree(monkeypatch, prec, tol):
+    """Power-of-two lengths take the register-radix kernels; the generic Stockham kernels
+    (DTT_FFT_GENERIC=1) give the same transforms and the same Green step."""
+    for seed, nvox in enumerate([(8, 16, 32), (64, 8, 16), (127, 4, 8), (256, 3, 4)]):
+        spec = _spec(seed, nvox=nvox, periodic_prob=0.4, anchored=False)
+        pb, _ = oracle_problem(spec)
+        g = gpu_grid(spec, prec)
+        rng = np.random.default_rng(seed)
+        for c in range(3):
+            x = rng.standard_normal(pb.node_shape) * pb.dof_mask(c)
+            for inv in (0, 1):
+                a = g.dtt_transform(c, inv, x)
+                monkeypatch.setenv("DTT_FFT_GENERIC", "1")
+                b = g.dtt_transform(c, inv, x)
+                monkeypatch.delenv("DTT_FFT_GENERIC")
+                assert np.abs(a - b).max() <= tol * np.abs(b).max()
+        pt = rng.standard_normal((3,) + pb.node_shape)
+        a = g.dtt_apply_green(pt)
+        monkeypatch.setenv("DTT_FFT_GENERIC", "1")
+        b = g.dtt_apply_green(pt)
+        monkeypatch.delenv("DTT_FFT_GENERIC")
+        assert np.abs(a - b).max() <= tol * np.abs(b).max()
 
 
 # ----------------------------------------------------------------------------- Green step
