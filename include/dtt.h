@@ -203,6 +203,44 @@ dtt_status dtt_transform(dtt_grid* grid, int32_t component, int32_t inverse, con
 #define DTT_NPROF 7
 dtt_status dtt_profile_iteration(dtt_grid* grid, const dtt_solve_opts* opts, int32_t iters, double* ms);
 
+/* ---- Batched solves and kernel tuning (no counterpart in the paper: its cells are
+ * solved one at a time; these serve many independent cells of uneven sizes on one GPU). */
+
+/* Kernel tile choices of one grid:
+ *   residual_zchunk: node planes per CTA of the stress/divergence kernel (0: built-in
+ *                    choice; otherwise 2..64);
+ *   fft_generic:     1 keeps every transform length on the generic Stockham kernels,
+ *                    0 lets power-of-two lengths take the register-radix kernels;
+ *   ms_per_iteration: (dtt_autotune output) measured time of one iteration with them. */
+typedef struct {
+  int32_t residual_zchunk;
+  int32_t fft_generic;
+  double ms_per_iteration;
+} dtt_tuning;
+
+/* Times `iters` iterations of the current problem (launch by launch, CUDA events on the
+ * grid's stream) for each candidate tiling -- the FFT route first, then the residual
+ * kernel's z chunk in {built-in, 2, 4, 8, 16, 32, 64} -- keeps the fastest on the grid
+ * and returns it in *best (may be NULL).  u~ and the solver rings are reset to zero
+ * afterwards; call it before a solve.  iters < 1 is DTT_ERR_ARG. */
+dtt_status dtt_autotune(dtt_grid* grid, const dtt_solve_opts* opts, int32_t iters, dtt_tuning* best);
+
+/* Applies a tiling (e.g. one tuned on another grid of the same size); a zchunk outside
+ * {0, 2..64} or fft_generic outside {0, 1} is DTT_ERR_ARG. */
+dtt_status dtt_set_tuning(dtt_grid* grid, const dtt_tuning* tuning);
+
+/* Solves ncell independent grids at once: every cell is prepared as dtt_solve_step
+ * would (same opts for all), then the iterations of all cells are captured as parallel
+ * branches of one CUDA graph (each cell on its own stream) that one launch advances by
+ * opts->graph_iters iterations of every cell; cells that have finished return at once.
+ * The host polls one status word per cell between launches.  reports[ncell] receives
+ * each cell's report (as dtt_solve_step).  Returns DTT_OK when every cell converged,
+ * else the first failing cell's status.  Cells must be distinct grids on the current
+ * device; the captured graph is cached and reused while the same grids, unchanged, are
+ * solved again with the same opts.  Not thread-safe (one batch at a time per process). */
+dtt_status dtt_batch_solve(int32_t ncell, dtt_grid* const* cells, const dtt_solve_opts* opts,
+                           dtt_report* reports);
+
 const char* dtt_last_error(void);
 
 /* Library version string. */

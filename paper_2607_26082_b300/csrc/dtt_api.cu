@@ -9,6 +9,7 @@
 #include "dtt_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -144,6 +145,8 @@ struct dtt_grid {
   // graph
   cudaGraphExec_t gexec = nullptr;
   int g_key = -1;
+  unsigned long long id = 0;        // unique per grid of the process
+  unsigned long long version = 0;   // bumped whenever captured launch arguments go stale
 
   Ctrl last{};
   bool solved = false;
@@ -154,6 +157,7 @@ namespace {
 const int kIP[2] = {2, 1};
 
 void invalidate_graph(dtt_grid* G) {
+  G->version += 1;
   if (G->gexec) cudaGraphExecDestroy(G->gexec);
   G->gexec = nullptr;
   G->g_key = -1;
@@ -694,6 +698,8 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
   for (int q = 0; q < 18; ++q)
     if (bc[q] < 0 || bc[q] > 2) return fail(DTT_ERR_ARG, "bc code must be 0, 1 or 2");
   dtt_grid* G = new dtt_grid();
+  static std::atomic<unsigned long long> next_id{1};
+  G->id = next_id.fetch_add(1);
   G->prec = precision;
   G->esz = precision == DTT_PREC_FP64 ? 8 : 4;
   G->stream = (cudaStream_t)stream;
@@ -1044,7 +1050,11 @@ dtt_status dtt_set_initial(dtt_grid* G, const double* u, int32_t ptr_is_device) 
   return zero_dirichlet(G);
 }
 
-dtt_status dtt_solve_step(dtt_grid* G, const dtt_solve_opts* opts, dtt_report* rep) {
+}  // extern "C"
+
+namespace {
+
+dtt_status check_solve(const dtt_grid* G, const dtt_solve_opts* opts) {
   if (!G || !opts) return fail(DTT_ERR_ARG, "null argument");
   if (!G->mat_set) return fail(DTT_ERR_STATE, "dtt_set_material not called");
   if (!G->ref_set) return fail(DTT_ERR_STATE, "dtt_set_reference not called");
@@ -1054,7 +1064,12 @@ dtt_status dtt_solve_step(dtt_grid* G, const dtt_solve_opts* opts, dtt_report* r
   if (opts->acv_on == DTT_ACV_U && G->prec != DTT_PREC_FP64 && opts->acv_mod > 0)
     return fail(DTT_ERR_ARG, "ACV on u~ is available in the FP64 path only");
   if (opts->init != DTT_INIT_ZERO && opts->init != DTT_INIT_PREVIOUS) return fail(DTT_ERR_ARG, "init must be 0 or 1");
-  auto t0 = std::chrono::steady_clock::now();
+  return DTT_OK;
+}
+
+// Everything a solve does before its first iteration: initial u~, row targets, a fresh
+// control block, zeroed rings, initial projections (all on the grid's stream).
+dtt_status prepare_solve(dtt_grid* G, const dtt_solve_opts* opts) {
   cudaStream_t s = G->stream;
   const size_t n3 = (size_t)(3 * G->NN);
   if (opts->init == DTT_INIT_ZERO) {
@@ -1107,23 +1122,12 @@ dtt_status dtt_solve_step(dtt_grid* G, const dtt_solve_opts* opts, dtt_report* r
     else
       CKL(launch_proj_U_rows<float>(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, nullptr, G->d_ctrl, s));
   }
-  const bool acv = opts->acv_mod > 0;
-  const int iters = opts->graph_iters > 0 ? opts->graph_iters : 8;
-  const int key = opts->acv_on * 1000000 + (acv ? 100000 : 0) + iters;
-  if (!G->gexec || G->g_key != key) {
-    dtt_status st = build_graph(G, opts->acv_on, acv, iters);
-    if (st != DTT_OK) return st;
-  }
-  long long launched = 0;
-  const long long cap = (long long)opts->max_iter + 2LL * iters + 8;
-  while (true) {
-    CK(cudaGraphLaunch(G->gexec, s));
-    launched += iters;
-    CK(cudaMemcpyAsync(G->h_ctrl, G->d_ctrl, 64, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (G->h_ctrl->done) break;
-    if (launched > cap) break;   // cannot happen: the device stops at max_iter
-  }
+  return DTT_OK;
+}
+
+// Reads the final control block and fills the report (after the grid's work has finished).
+dtt_status finish_solve(dtt_grid* G, std::chrono::steady_clock::time_point t0, dtt_report* rep) {
+  cudaStream_t s = G->stream;
   CK(cudaMemcpyAsync(G->h_ctrl, G->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   G->last = *G->h_ctrl;
@@ -1143,6 +1147,42 @@ dtt_status dtt_solve_step(dtt_grid* G, const dtt_solve_opts* opts, dtt_report* r
   if (st == DTT_ERR_NOT_CONVERGED) g_err = "iteration cap reached";
   if (st == DTT_ERR_DIVERGED) g_err = "residual diverged";
   return st;
+}
+
+int graph_iters_of(const dtt_solve_opts* opts) { return opts->graph_iters > 0 ? opts->graph_iters : 8; }
+int graph_key_of(const dtt_solve_opts* opts) {
+  return opts->acv_on * 1000000 + (opts->acv_mod > 0 ? 100000 : 0) + graph_iters_of(opts);
+}
+
+}  // namespace
+
+extern "C" {
+
+dtt_status dtt_solve_step(dtt_grid* G, const dtt_solve_opts* opts, dtt_report* rep) {
+  dtt_status st0 = check_solve(G, opts);
+  if (st0 != DTT_OK) return st0;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = G->stream;
+  st0 = prepare_solve(G, opts);
+  if (st0 != DTT_OK) return st0;
+  const bool acv = opts->acv_mod > 0;
+  const int iters = graph_iters_of(opts);
+  const int key = graph_key_of(opts);
+  if (!G->gexec || G->g_key != key) {
+    dtt_status st = build_graph(G, opts->acv_on, acv, iters);
+    if (st != DTT_OK) return st;
+  }
+  long long launched = 0;
+  const long long cap = (long long)opts->max_iter + 2LL * iters + 8;
+  while (true) {
+    CK(cudaGraphLaunch(G->gexec, s));
+    launched += iters;
+    CK(cudaMemcpyAsync(G->h_ctrl, G->d_ctrl, 64, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (G->h_ctrl->done) break;
+    if (launched > cap) break;   // cannot happen: the device stops at max_iter
+  }
+  return finish_solve(G, t0, rep);
 }
 
 dtt_status dtt_get_history(const dtt_grid* G, double* hist, int32_t* n) {
@@ -1460,3 +1500,227 @@ extern "C" dtt_status dtt_apply_green_noalloc(dtt_grid* G, const double* ptilde_
   CK(cudaStreamSynchronize(s));
   return DTT_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// Kernel tuning and batched solves.
+//
+// A batch of independent cells (many grids of uneven sizes) runs as one CUDA graph whose
+// parallel branches are the cells' own iteration sequences, each on the cell's stream:
+// small cells fill the GPU together instead of one after another, and one graph launch
+// advances every cell by graph_iters iterations.  The tile choices of the two kernels whose
+// best shape depends on the grid (the residual kernel's z chunk, the FFT route) are
+// measured per grid by dtt_autotune and can be copied to grids of the same size.
+
+namespace {
+
+// Mean milliseconds per iteration of `iters` iterations launched one by one on the grid's
+// stream, after one untimed iteration, with a control block that never stops.
+dtt_status time_iterations(dtt_grid* G, const dtt_solve_opts* opts, int iters, double* ms) {
+  cudaStream_t s = G->stream;
+  Ctrl& c = *G->h_ctrl;
+  std::memset(&c, 0, sizeof(Ctrl));
+  c.max_iter = 1 << 30;
+  c.acv_mod = opts->acv_mod > 0 ? opts->acv_mod : 1;
+  c.acv_on = opts->acv_on;
+  c.contact_on = G->contact ? 1 : 0;
+  c.update_tol = 1e-2;
+  c.acv_pivot = 1e-14;
+  c.no_stop = 1;
+  CK(cudaMemcpyAsync(G->d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+  const bool acv = opts->acv_mod > 0;
+  dtt_status st = enqueue_iter_any(G, opts->acv_on, acv);
+  if (st != DTT_OK) return st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaEventRecord(e0, s);
+  for (int k = 0; k < iters && st == DTT_OK; ++k) st = enqueue_iter_any(G, opts->acv_on, acv);
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DTT_OK) return st;
+  if (e != cudaSuccess) return fail(DTT_ERR_CUDA, std::string("tuning timer: ") + cudaGetErrorString(e));
+  *ms = (double)t / iters;
+  return DTT_OK;
+}
+
+// u~, the rings and the step back to zero (state after tuning runs).
+dtt_status reset_state(dtt_grid* G) {
+  cudaStream_t s = G->stream;
+  const size_t n3 = (size_t)(3 * G->NN);
+  if (G->u64) CK(cudaMemsetAsync(G->u64, 0, n3 * 8, s));
+  if (G->uhi) CK(cudaMemsetAsync(G->uhi, 0, n3 * 4, s));
+  if (G->ulo) CK(cudaMemsetAsync(G->ulo, 0, n3 * 4, s));
+  for (int k = 0; k < 5; ++k) CK(cudaMemsetAsync(G->S[k], 0, n3 * G->esz, s));
+  for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(G->R[k], 0, n3 * G->esz, s));
+  for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(G->Gr[k], 0, n3 * G->esz, s));
+  CK(cudaMemsetAsync(G->step, 0, n3 * G->esz, s));
+  CK(cudaStreamSynchronize(s));
+  return DTT_OK;
+}
+
+dtt_status apply_tiling(dtt_grid* G, int zc, int generic) {
+  G->g.zc_override = zc;
+  G->g.fft_generic = generic;
+  invalidate_graph(G);
+  return ensure_partials(G);
+}
+
+struct BatchCache {
+  std::vector<unsigned long long> key;   // device, opts key, then (id, version) per cell
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t bs = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  Ctrl** d_ctrls = nullptr;
+  int* d_done = nullptr;
+  int* h_done = nullptr;
+  int cap = 0;
+};
+BatchCache g_batch;
+
+dtt_status batch_buffers(int n) {
+  if (!g_batch.bs) CK(cudaStreamCreateWithFlags(&g_batch.bs, cudaStreamNonBlocking));
+  if (!g_batch.fork) CK(cudaEventCreateWithFlags(&g_batch.fork, cudaEventDisableTiming));
+  if (!g_batch.join) CK(cudaEventCreateWithFlags(&g_batch.join, cudaEventDisableTiming));
+  if (n > g_batch.cap) {
+    if (g_batch.d_ctrls) cudaFree(g_batch.d_ctrls);
+    if (g_batch.d_done) cudaFree(g_batch.d_done);
+    if (g_batch.h_done) cudaFreeHost(g_batch.h_done);
+    g_batch.d_ctrls = nullptr;
+    g_batch.d_done = nullptr;
+    g_batch.h_done = nullptr;
+    g_batch.cap = 0;
+    CK(cudaMalloc(&g_batch.d_ctrls, n * sizeof(Ctrl*)));
+    CK(cudaMalloc(&g_batch.d_done, n * sizeof(int)));
+    CK(cudaMallocHost(&g_batch.h_done, n * sizeof(int)));
+    g_batch.cap = n;
+  }
+  return DTT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dtt_status dtt_autotune(dtt_grid* G, const dtt_solve_opts* opts, int32_t iters, dtt_tuning* best) {
+  dtt_status st = check_solve(G, opts);
+  if (st != DTT_OK) return st;
+  if (iters < 1) return fail(DTT_ERR_ARG, "iters must be >= 1");
+  double t_best = 1e300;
+  int zc_best = 0, gen_best = 0;
+  for (int gen = 0; gen < 2; ++gen) {
+    if ((st = apply_tiling(G, 0, gen)) != DTT_OK) return st;
+    double t = 0.0;
+    if ((st = time_iterations(G, opts, iters, &t)) != DTT_OK) return st;
+    if (t < t_best) { t_best = t; gen_best = gen; }
+  }
+  const int zcs[6] = {2, 4, 8, 16, 32, 64};
+  for (int q = 0; q < 6; ++q) {
+    if (zcs[q] > 2 * G->g.nn[2]) break;
+    if ((st = apply_tiling(G, zcs[q], gen_best)) != DTT_OK) return st;
+    double t = 0.0;
+    if ((st = time_iterations(G, opts, iters, &t)) != DTT_OK) return st;
+    if (t < t_best) { t_best = t; zc_best = zcs[q]; }
+  }
+  if ((st = apply_tiling(G, zc_best, gen_best)) != DTT_OK) return st;
+  if ((st = reset_state(G)) != DTT_OK) return st;
+  if (best) {
+    best->residual_zchunk = zc_best;
+    best->fft_generic = gen_best;
+    best->ms_per_iteration = t_best;
+  }
+  return DTT_OK;
+}
+
+dtt_status dtt_set_tuning(dtt_grid* G, const dtt_tuning* t) {
+  if (!G || !t) return fail(DTT_ERR_ARG, "null argument");
+  if (t->residual_zchunk != 0 && (t->residual_zchunk < 2 || t->residual_zchunk > 64))
+    return fail(DTT_ERR_ARG, "residual_zchunk must be 0 or in [2, 64]");
+  if (t->fft_generic != 0 && t->fft_generic != 1) return fail(DTT_ERR_ARG, "fft_generic must be 0 or 1");
+  return apply_tiling(G, t->residual_zchunk, t->fft_generic);
+}
+
+dtt_status dtt_batch_solve(int32_t ncell, dtt_grid* const* cells, const dtt_solve_opts* opts, dtt_report* reports) {
+  if (ncell < 1 || !cells || !opts) return fail(DTT_ERR_ARG, "ncell >= 1, cells and opts required");
+  for (int i = 0; i < ncell; ++i) {
+    dtt_status st = check_solve(cells[i], opts);
+    if (st != DTT_OK) return st;
+    for (int j = 0; j < i; ++j)
+      if (cells[j] == cells[i]) return fail(DTT_ERR_ARG, "a grid appears twice in the batch");
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  auto t0 = std::chrono::steady_clock::now();
+  for (int i = 0; i < ncell; ++i) {
+    dtt_status st = prepare_solve(cells[i], opts);
+    if (st != DTT_OK) return st;
+    CK(cudaStreamSynchronize(cells[i]->stream));
+  }
+  dtt_status st = batch_buffers(ncell);
+  if (st != DTT_OK) return st;
+  const bool acv = opts->acv_mod > 0;
+  const int iters = graph_iters_of(opts);
+  std::vector<unsigned long long> key;
+  key.push_back((unsigned long long)dev);
+  key.push_back((unsigned long long)graph_key_of(opts));
+  for (int i = 0; i < ncell; ++i) {
+    key.push_back(cells[i]->id);
+    key.push_back(cells[i]->version);
+  }
+  cudaStream_t bs = g_batch.bs;
+  if (!g_batch.exec || key != g_batch.key) {
+    if (g_batch.exec) cudaGraphExecDestroy(g_batch.exec);
+    g_batch.exec = nullptr;
+    g_batch.key.clear();
+    std::vector<Ctrl*> ctrls(ncell);
+    for (int i = 0; i < ncell; ++i) ctrls[i] = cells[i]->d_ctrl;
+    CK(cudaMemcpy(g_batch.d_ctrls, ctrls.data(), ncell * sizeof(Ctrl*), cudaMemcpyHostToDevice));
+    // fork-join capture: every cell's iterations on its own stream, joined back to bs
+    CK(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecord(g_batch.fork, bs);
+    for (int i = 0; i < ncell; ++i) {
+      cudaStreamWaitEvent(cells[i]->stream, g_batch.fork, 0);
+      for (int k = 0; k < iters && st == DTT_OK; ++k) st = enqueue_iter_any(cells[i], opts->acv_on, acv);
+      cudaEventRecord(g_batch.join, cells[i]->stream);
+      cudaStreamWaitEvent(bs, g_batch.join, 0);
+      if (st != DTT_OK) break;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(bs, &graph);
+    if (st != DTT_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (st != DTT_OK) return st;
+      return fail(DTT_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&g_batch.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g_batch.exec = nullptr;
+      return fail(DTT_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    }
+    g_batch.key = key;
+  }
+  long long launched = 0;
+  const long long cap = (long long)opts->max_iter + 2LL * iters + 8;
+  while (true) {
+    CK(cudaGraphLaunch(g_batch.exec, bs));
+    launched += iters;
+    CKL(launch_batch_done(g_batch.d_ctrls, ncell, g_batch.d_done, bs));
+    CK(cudaMemcpyAsync(g_batch.h_done, g_batch.d_done, ncell * sizeof(int), cudaMemcpyDeviceToHost, bs));
+    CK(cudaStreamSynchronize(bs));
+    bool all = true;
+    for (int i = 0; i < ncell && all; ++i) all = g_batch.h_done[i] != 0;
+    if (all || launched > cap) break;   // the cap cannot be reached: cells stop at max_iter
+  }
+  dtt_status first = DTT_OK;
+  for (int i = 0; i < ncell; ++i) {
+    dtt_status si = finish_solve(cells[i], t0, reports ? &reports[i] : nullptr);
+    if (si != DTT_OK && first == DTT_OK) first = si;
+  }
+  return first;
+}
+
+}  // extern "C"

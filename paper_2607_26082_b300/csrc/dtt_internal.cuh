@@ -30,6 +30,8 @@ struct GridDev {
   int scheme;
   int bc[3][2][3];  // [axis][face][component]
   int periodic[3];
+  int zc_override;   // residual kernels: node planes per CTA (0: built-in choice)
+  int fft_generic;   // 1: generic Stockham kernels for every length
 };
 
 // Solver state kept on the device so that a whole iteration is a fixed sequence of
@@ -138,6 +140,8 @@ struct ResidualArgs {
 // Residual partial sums: 6 doubles per CTA [w sigma:sigma, p^2, Gram 0..3] (the FP64
 // kernel leaves the Gram entries 0; the FP32 kernel fills them in the Anderson mode).
 constexpr int RES_STRIDE = 6;
+// done flags of many grids' control blocks gathered into one array (batched solves)
+int launch_batch_done(Ctrl* const* ctrls, int n, int* done, cudaStream_t s);
 template <typename T> int launch_residual(const ResidualArgs& a, cudaStream_t s);
 int residual_blocks(const GridDev& g);
 int residual_zchunk(const GridDev& g);
@@ -168,6 +172,7 @@ struct FftParams {
   int nnx, nny;
   long long npencil, NN;
   float fscale;            // scale in FP32 (mixed path)
+  int generic;             // 1: generic Stockham kernels only (tuning choice)
   double inv_n;            // 1 / n (quarter-wave inverses)
   int incr;                // inverse x pass: add the result to u~ and store it as the step
   double* u64;

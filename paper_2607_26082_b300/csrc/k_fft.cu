@@ -877,7 +877,7 @@ static int launch_zg_pb(const T* in, T* out, const FftParams& p, const GreenTabl
 template <typename T>
 int launch_fft_z_green(const T* in, T* out, const FftParams& p, const GreenTables& gt, double lam0, double mu0,
                        int scheme, double h, int ncomp, const Ctrl* ctrl, cudaStream_t s) {
-  if (!generic_only()) {
+  if (!p.generic && !generic_only()) {
     const T l0 = (T)lam0, m2 = (T)(2.0 * mu0), ih2 = (T)(4.0 / (h * h));
     const T zscale = (T)((p.L == p.n) ? 1.0 / p.n : 2.0 / p.n);
     const int r = launch_fast_zg<T>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
@@ -895,7 +895,7 @@ int launch_fft_z_green(const T* in, T* out, const FftParams& p, const GreenTable
 template <typename T>
 int launch_fft_axis(const T* in, T* out, const FftParams& p, int ncomp, const Ctrl* ctrl, void* const* in_ring,
                     cudaStream_t s) {
-  if (!generic_only()) {
+  if (!p.generic && !generic_only()) {
     const int r = launch_fast<T>(in, out, p, ncomp, ctrl, in_ring, s);
     if (r >= 0) return r;
   }

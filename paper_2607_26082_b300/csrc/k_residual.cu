@@ -375,6 +375,7 @@ k_residual(ResidualArgs a) {
 // z planes per CTA: long chunks amortise the one-plane halo, short ones give small grids
 // enough CTAs to fill the 148 SMs (target ~4 CTAs per SM).
 int residual_zchunk(const GridDev& g) {
+  if (g.zc_override > 0) return g.zc_override < RZC_MAX ? g.zc_override : RZC_MAX;
   long long bxy = (long long)((g.nn[0] + RTX - 1) / RTX) * ((g.nn[1] + RTY - 1) / RTY);
   long long want = 148LL * 4;
   long long zc = (g.nn[2] * bxy + want - 1) / want;

@@ -429,6 +429,7 @@ int resident_ctas() {
 // z planes per CTA: about two waves of resident CTAs, at least 4 planes per CTA (each CTA
 // also processes the voxel layer below its first plane).
 int residual_f32_zchunk(const GridDev& g) {
+  if (g.zc_override > 0) return g.zc_override;
   long long bxy = (long long)((g.nn[0] + FTX - 1) / FTX) * ((g.nn[1] + FTY - 1) / FTY);
   long long want = 2LL * resident_ctas();
   long long zc = (g.nn[2] * bxy + want - 1) / want;

@@ -713,4 +713,15 @@ template int launch_acv_store<float>(const GridDev&, int, void* const*, void* co
 template int launch_acv_accel<double>(const GridDev&, int, void* const*, void* const*, double*, double*, const Ctrl*, cudaStream_t);
 template int launch_acv_accel<float>(const GridDev&, int, void* const*, void* const*, float*, double*, const Ctrl*, cudaStream_t);
 
+__global__ void k_batch_done(Ctrl* const* ctrls, int n, int* done) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) done[i] = ctrls[i]->done;
+}
+
+int launch_batch_done(Ctrl* const* ctrls, int n, int* done, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_batch_done<<<(n + 255) / 256, 256, 0, s>>>(ctrls, n, done);
+  return (int)cudaGetLastError();
+}
+
 }  // namespace dtt

@@ -162,6 +162,7 @@ static FftParams fft_params(const GridDev& g, const TransformTables& tt, int axi
   p.scale = 1.0;
   if (inverse) p.scale = g.periodic[axis] ? 1.0 / g.nvox[axis] : 2.0 / g.nvox[axis];
   p.fscale = (float)p.scale;
+  p.generic = g.fft_generic;
   p.inv_n = 1.0 / g.nvox[axis];
   return p;
 }

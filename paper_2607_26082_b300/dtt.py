@@ -41,6 +41,13 @@ class Report(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("residual_zchunk", C.c_int32), ("fft_generic", C.c_int32), ("ms_per_iteration", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 EXPORTS = ["dtt_grid_create", "dtt_grid_destroy", "dtt_grid_sizes", "dtt_set_material",
@@ -48,7 +55,7 @@ EXPORTS = ["dtt_grid_create", "dtt_grid_destroy", "dtt_grid_sizes", "dtt_set_mat
            "dtt_move_indenter", "dtt_clear_indenter", "dtt_set_initial", "dtt_solve_step",
            "dtt_get_history", "dtt_get_fields", "dtt_get_reactions", "dtt_get_contact",
            "dtt_apply_residual", "dtt_apply_green", "dtt_apply_green_noalloc", "dtt_transform",
-           "dtt_profile_iteration",
+           "dtt_profile_iteration", "dtt_autotune", "dtt_set_tuning", "dtt_batch_solve",
            "dtt_last_error", "dtt_version"]
 NPROF = 7
 PROF_GROUPS = ["residual", "projections", "anderson", "forward_dt", "green", "inverse_dt", "increment"]
@@ -86,6 +93,9 @@ def lib():
     L.dtt_apply_green_noalloc.argtypes = [P, P, P]
     L.dtt_transform.argtypes = [P, i32, i32, P, P, i32]
     L.dtt_profile_iteration.argtypes = [P, C.POINTER(SolveOpts), i32, P]
+    L.dtt_autotune.argtypes = [P, C.POINTER(SolveOpts), i32, C.POINTER(Tuning)]
+    L.dtt_set_tuning.argtypes = [P, C.POINTER(Tuning)]
+    L.dtt_batch_solve.argtypes = [i32, P, C.POINTER(SolveOpts), P]
     L.dtt_last_error.restype = C.c_char_p
     L.dtt_version.restype = C.c_char_p
     for name in EXPORTS:
@@ -265,6 +275,17 @@ class Grid:
         return out
 
 
+    def dtt_autotune(self, iters=5, acv_mod=3, acv_on=ACV_P):
+        o = SolveOpts(0.0, 1 << 30, int(acv_mod), int(acv_on), INIT_ZERO, 1e-2, 0, 0.0)
+        t = Tuning()
+        _check(lib().dtt_autotune(self._h, C.byref(o), int(iters), C.byref(t)))
+        return t
+
+    def dtt_set_tuning(self, tuning):
+        t = tuning if isinstance(tuning, Tuning) else Tuning(int(tuning["residual_zchunk"]),
+                                                                 int(tuning["fft_generic"]), 0.0)
+        _check(lib().dtt_set_tuning(self._h, C.byref(t)))
+
     def dtt_profile_iteration(self, iters, acv_mod=3, acv_on=ACV_P):
         o = SolveOpts(0.0, 1 << 30, int(acv_mod), int(acv_on), INIT_PREVIOUS, 1e-2, 0, 0.0)
         ms = np.zeros(NPROF)
@@ -274,3 +295,17 @@ class Grid:
 
 def version():
     return lib().dtt_version().decode()
+
+
+def dtt_batch_solve(grids, tol, max_iter, acv_mod=3, acv_on=ACV_P, init=INIT_ZERO, update_tol=1e-2,
+                    graph_iters=0, acv_pivot=0.0):
+    """Solve independent grids together (dtt_batch_solve); returns (status, [Report])."""
+    n = len(grids)
+    arr = (C.c_void_p * n)(*[g._h.value for g in grids])
+    o = SolveOpts(float(tol), int(max_iter), int(acv_mod), int(acv_on), int(init), float(update_tol),
+                  int(graph_iters), float(acv_pivot))
+    reps = (Report * n)()
+    st = lib().dtt_batch_solve(n, C.cast(arr, C.c_void_p), C.byref(o), C.cast(reps, C.c_void_p))
+    if st not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED):
+        _check(st)
+    return st, list(reps)

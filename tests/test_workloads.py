@@ -1,0 +1,49 @@
+"""The seeded generator of the batched-cell workload draws what its recipe states."""
+import numpy as np
+
+import workloads as wl
+
+
+def test_batch_cells_follow_the_recipe():
+    cells = wl.batch_cells(24, seed0=1000)
+    sizes = set()
+    for c in cells:
+        n = c["nvox"][0]
+        sizes.add(n)
+        assert c["nvox"] == (n, n, n) and n in (32, 48, 64, 96)
+        bc = c["bc"]
+        for d in range(3):
+            per = bc[d] == wl.P
+            assert per.all() or not per.any()       # periodic axes: all faces, all components
+        for comp in range(3):
+            assert (bc[:, :, comp] == wl.D).any()   # a Dirichlet face per component
+        # inclusions: inside the cell, radius in [3, 10], pairwise disjoint
+        sp = c["spheres"]
+        for k, (ctr, r) in enumerate(sp):
+            assert 3.0 <= r <= 10.0 and np.all(ctr >= r) and np.all(ctr <= n - r)
+            for ctr2, r2 in sp[:k]:
+                assert np.linalg.norm(ctr - ctr2) >= r + r2
+        vf = c["phase"].mean()
+        assert 0.1 <= c["vf_target"] <= 0.3
+        assert vf >= c["vf_target"] or len(sp) > 0
+        # pins: interior nodes, not on a Dirichlet face of their component, distinct
+        seen = set()
+        assert len(c["intents"]) <= 16
+        for it in c["intents"]:
+            assert it["kind"] == "strong" and it["value"] == 0.0
+            assert all(1 <= it["ijk"][d] <= n - 1 for d in range(3))
+            assert not wl.on_dirichlet(c["nvox"], bc, it["ijk"], it["comp"])
+            key = (it["ijk"], it["comp"])
+            assert key not in seen
+            seen.add(key)
+        e = c["eps_star"]
+        assert np.allclose(e, e.T) and np.abs(e).max() <= 1e-3
+        assert c["lam"][1] / c["lam"][0] == 10.0 and c["mu"][1] / c["mu"][0] == 10.0
+    assert len(sizes) >= 3
+
+
+def test_batch_cells_are_reproducible():
+    a = wl.batch_cell(1234)
+    b = wl.batch_cell(1234)
+    assert np.array_equal(a["phase"], b["phase"]) and np.array_equal(a["bc"], b["bc"])
+    assert a["intents"] == b["intents"]

@@ -147,6 +147,80 @@ def indentation(nx=256, ny=256, nz=128, R=64.0, steps=10, dmin=0.001, dmax=0.05,
 
 
 # ---------------------------------------------------------------------------
+# Batches of uneven two-phase cells (training-data generation workload)
+# ---------------------------------------------------------------------------
+def batch_cell(seed, sizes=(32, 48, 64, 96), scheme=TETRA2, contrast=10.0, nu=0.3, max_pins=16):
+    """One cubic two-phase cell: edge drawn uniformly from `sizes`; non-overlapping
+    spherical inclusions (radius U[3, 10] voxels, kept inside the cell) added in random
+    order until the inclusion volume fraction reaches a target drawn from U[0.1, 0.3]
+    (or the placements run out); E_matrix = 1, E_inclusion = contrast, nu = 0.3 both;
+    per axis the faces are periodic with probability 1/3 (all components), else each face
+    and component is Dirichlet or Neumann at random, redrawn until every component has a
+    Dirichlet face (no null modes); 0..max_pins interior nodes pinned at u = 0 (strong
+    rows, one random component each); eps* symmetric with entries U[-1e-3, 1e-3];
+    reference medium the mean of the two phases' Lame constants; Anderson on p~ every 2
+    iterations, tol 1e-6."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.choice(sizes))
+    nvox = (n, n, n)
+    while True:
+        bc = np.zeros((3, 2, 3), dtype=np.int64)
+        for d in range(3):
+            if rng.random() < 1.0 / 3.0:
+                bc[d] = P
+            else:
+                bc[d] = rng.choice([D, N], size=(2, 3))
+        if all(any(bc[d, f, c] == D for d in range(3) for f in range(2)) for c in range(3)):
+            break
+    phase = np.zeros((n, n, n), np.uint8)
+    target = rng.uniform(0.1, 0.3)
+    filled = 0
+    spheres = []
+    tries = 0
+    while filled < target * n ** 3 and tries < 2000:
+        tries += 1
+        r = rng.uniform(3.0, 10.0)
+        if 2 * r >= n:
+            continue
+        c = rng.uniform(r, n - r, size=3)
+        if any(np.linalg.norm(c - c2) < r + r2 for c2, r2 in spheres):
+            continue
+        spheres.append((c, r))
+        lo = np.maximum(np.floor(c - r).astype(int), 0)
+        hi = np.minimum(np.ceil(c + r).astype(int) + 1, n)
+        z, y, x = np.meshgrid(np.arange(lo[2], hi[2]) + 0.5, np.arange(lo[1], hi[1]) + 0.5,
+                              np.arange(lo[0], hi[0]) + 0.5, indexing="ij")
+        m = (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 <= r * r
+        phase[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]][m] = 1
+        filled += int(m.sum())
+    lm, mm = lame(1.0, nu)
+    li, mi = lame(contrast, nu)
+    npin = int(rng.integers(0, max_pins + 1))
+    intents, used = [], set()
+    tries = 0
+    nn = node_counts(nvox, bc)
+    while len(intents) < npin and tries < 1000:
+        tries += 1
+        ijk = tuple(int(rng.integers(1, nn[d] - 1)) for d in range(3))
+        c = int(rng.integers(3))
+        if (ijk, c) in used or on_dirichlet(nvox, bc, ijk, c):
+            continue
+        used.add((ijk, c))
+        intents.append(dict(kind="strong", ijk=ijk, comp=c, value=0.0))
+    a = rng.uniform(-1e-3, 1e-3, size=(3, 3))
+    eps = 0.5 * (a + a.T)
+    return Workload(name="two-phase cell %d^3 (seed %d)" % (n, seed), nvox=nvox, h=1.0, bc=bc, scheme=scheme,
+                    phase=phase, lam=np.array([lm, li]), mu=np.array([mm, mi]), eps_star=eps, intents=intents,
+                    lam0=0.5 * (lm + li), mu0=0.5 * (mm + mi), tol=1e-6, acv_mod=2,
+                    spheres=spheres, vf_target=target)
+
+
+def batch_cells(n_cells=256, seed0=1000, sizes=(32, 48, 64, 96), **kw):
+    """n_cells cells drawn by batch_cell with seeds seed0, seed0 + 1, ..."""
+    return [batch_cell(seed0 + i, sizes=sizes, **kw) for i in range(n_cells)]
+
+
+# ---------------------------------------------------------------------------
 # Random small problems for parity tests
 # ---------------------------------------------------------------------------
 def random_bc(rng, periodic_prob=0.25):
