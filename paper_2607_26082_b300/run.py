@@ -2,6 +2,13 @@
 
   python -m paper_2607_26082_b300.run --workload ct|cube16|indent [--precision mixed|fp64]
          [--iters K | --tol T] [--steps S] [--graph-iters G] [--nvox nx,ny,nz]
+  python -m paper_2607_26082_b300.run --workload batch [--cells N] [--seed0 S] [--no-tune]
+         [--sequential]
+
+The batch workload draws N uneven two-phase cells (edges 32, 48, 64, 96), tunes the kernel
+tiling once per cell size (dtt_autotune on one cell, dtt_set_tuning on the others) and
+solves all cells with one dtt_batch_solve; --sequential also solves them one after the
+other with dtt_solve_step for comparison.
 
 --iters K runs exactly K iterations (tolerance 0) of the first load step, which is the
 short, fixed launch sequence a profiler wants; --tol runs to convergence.  For the
@@ -16,6 +23,8 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
 
 import workloads as wl  # noqa: E402
 
@@ -36,9 +45,51 @@ def make_workload(name, nvox=None):
     raise SystemExit("unknown workload %r" % name)
 
 
+def run_batch(a, prec):
+    import time
+    cells = wl.batch_cells(a.cells, seed0=a.seed0)
+    grids = [rows.setup_grid(c, prec) for c in cells]
+    nvox = sum(int(np.prod(c["nvox"])) for c in cells)
+    tuned = {}
+    t0 = time.perf_counter()
+    if not a.no_tune:
+        for c, g in zip(cells, grids):
+            n = c["nvox"][0]
+            if n not in tuned:
+                tuned[n] = g.dtt_autotune(iters=4, acv_mod=2)
+            else:
+                g.dtt_set_tuning(tuned[n])
+    t_tune = time.perf_counter() - t0
+    out = {"workload": "batch of %d two-phase cells" % len(cells), "precision": a.precision,
+           "voxels": nvox, "tuning_s": t_tune,
+           "tuning": {str(k): v.as_dict() for k, v in tuned.items()}}
+    for rep_i in range(2):   # the first call captures the batch graph
+        t0 = time.perf_counter()
+        st, reps = dtt.dtt_batch_solve(grids, 1e-6, 20000, acv_mod=2, graph_iters=16)
+        dt = time.perf_counter() - t0
+    vi = sum(int(np.prod(c["nvox"])) * r.iterations for c, r in zip(cells, reps))
+    out.update({"status": st, "batch_s": dt, "voxel_iters": vi, "voxel_iters_per_s": vi / dt,
+                "iterations": {"min": min(r.iterations for r in reps), "max": max(r.iterations for r in reps),
+                               "mean": float(np.mean([r.iterations for r in reps]))},
+                "failed": [i for i, r in enumerate(reps) if r.status != dtt.OK]})
+    if a.sequential:
+        t0 = time.perf_counter()
+        for g in grids:
+            g.dtt_solve_step(1e-6, 20000, acv_mod=2, graph_iters=16)
+        out["sequential_s"] = time.perf_counter() - t0
+    print(json.dumps(out), flush=True)
+    for g in grids:
+        g.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="ct", choices=["ct", "cube16", "indent"])
+    ap.add_argument("--workload", default="ct", choices=["ct", "cube16", "indent", "batch"])
+    ap.add_argument("--cells", type=int, default=256)
+    ap.add_argument("--seed0", type=int, default=1000)
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--sequential", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--iters", type=int, default=0, help="fixed iteration count (tolerance 0)")
     ap.add_argument("--tol", type=float, default=None)
@@ -46,6 +97,8 @@ def main(argv=None):
     ap.add_argument("--graph-iters", type=int, default=0)
     ap.add_argument("--nvox", default=None, help="voxels nx,ny,nz (ct and indent)")
     a = ap.parse_args(argv)
+    if a.workload == "batch":
+        return run_batch(a, dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64)
     spec = make_workload(a.workload, tuple(int(v) for v in a.nvox.split(",")) if a.nvox else None)
     prec = dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64
     g = rows.setup_grid(spec, prec)
