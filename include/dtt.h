@@ -54,7 +54,7 @@ typedef enum {
 enum { DTT_BC_PERIODIC = 0, DTT_BC_DIRICHLET = 1, DTT_BC_NEUMANN = 2 };
 enum { DTT_SCHEME_TETRA2 = 0, DTT_SCHEME_HEX1 = 1 };
 enum { DTT_PREC_FP64 = 0, DTT_PREC_MIXED = 1 };
-enum { DTT_INIT_ZERO = 0, DTT_INIT_PREVIOUS = 1 };
+enum { DTT_INIT_ZERO = 0, DTT_INIT_PREVIOUS = 1, DTT_INIT_GUESS = 2 };
 enum { DTT_ACV_U = 0, DTT_ACV_P = 1 };
 
 /* Create a grid (Section 3.2.1 problem statement: cell, per-face per-component BCs, FD
@@ -120,8 +120,11 @@ typedef struct {
   int32_t acv_mod;     /* accelerate every acv_mod iterations after the first four (2 or 3);
                           0 disables acceleration */
   int32_t acv_on;      /* DTT_ACV_P (accelerate p~, default) or DTT_ACV_U (FP64 only) */
-  int32_t init;        /* DTT_INIT_ZERO or DTT_INIT_PREVIOUS (current u~: previous step or
-                          dtt_set_initial) */
+  int32_t init;        /* DTT_INIT_ZERO, DTT_INIT_PREVIOUS (current u~: previous step or
+                          dtt_set_initial) or DTT_INIT_GUESS: the current u~ is a guess (e.g.
+                          dtt_net_predict); the solve evaluates the Eq. 5 residual at it and at
+                          u~ = 0 (both after the initial projections) and starts from the
+                          lower one, so a guess never starts worse than the plain start */
   double update_tol;   /* contact-zone update threshold on the residual (paper: 1e-2) */
   int32_t graph_iters; /* iterations per captured CUDA-graph launch (0: default 8) */
   double acv_pivot;    /* Anderson is skipped when a pivot of the 4x4 Gram elimination is
@@ -135,6 +138,8 @@ typedef struct {
   int32_t status;              /* dtt_status of the solve */
   double residual;             /* Eq. 5 residual of the returned iterate */
   double seconds;              /* wall time of the solve (host clock, synchronised) */
+  int32_t start_from_guess;    /* DTT_INIT_GUESS: 1 if the guess was kept, 0 if u~ = 0 won */
+  double start_residual;       /* Eq. 5 residual of the starting iterate (DTT_INIT_GUESS) */
 } dtt_report;
 
 /* One solve (Algorithm 1), or one load increment (Algorithm 2) when an indenter is set:

@@ -1,0 +1,83 @@
+/* Learned warm start for the constrained DTT solver: a small 3-D convolutional
+ * encoder-decoder that maps a cell's phase map, boundary/constraint masks and load to a
+ * first guess of u~, trained on fields the solver produces.
+ *
+ * The paper only names this as a prospect (reducing iteration counts through better
+ * initialisation, Section 5.4 and the conclusion); the network is this library's own.
+ * Its forward and backward passes run in hand-written BF16 implicit-GEMM convolution
+ * kernels with FP32 accumulation; master weights and the Adam optimiser are FP32.
+ *
+ * Network (node grid of the cell, channels last, 3x3x3 convolutions with zero padding,
+ * bias; c1/c2/c3 channels at full, 1/2 and 1/4 resolution; "pool" = mean over 2x2x2 blocks,
+ * partial at odd edges; "up" = nearest-neighbour back to the finer size):
+ *   e1 = relu(conv(relu(conv(x))))             16 -> c1 -> c1
+ *   e2 = relu(conv(relu(conv(pool(e1)))))      c1 -> c2 -> c2
+ *   e3 = relu(conv(relu(conv(pool(e2)))))      c2 -> c3 -> c3
+ *   d2 = relu(conv(relu(conv(up(e3))) + e2))   c3 -> c2, c2 -> c2
+ *   d1 = relu(conv(relu(conv(up(d2))) + e1))   c2 -> c1, c1 -> c1
+ *   y  = conv(d1)                               c1 -> 16, channels 0..2 used
+ * Input features per node (16 channels, 13 used): mean normalised stiffness E/E_max of the
+ * adjacent voxels; for each component, 1 where the DOF is fixed (Dirichlet face or a
+ * constraint row); eps* (6 entries) times 1000; the node coordinates divided by the cell
+ * edge.  Output: u~ / (n_max * 1e-3), n_max the largest voxel count of the cell's axes.
+ * Parameters are packed layer by layer as W[27][cout][cin] (tap = 9 (dz+1) + 3 (dy+1) +
+ * (dx+1)) followed by b[cout], in the layer order above; c1, c2, c3 are multiples of 16
+ * in [16, 64].
+ *
+ * All calls return dtt_status (dtt.h); messages via dtt_last_error().  A dtt_net is used
+ * on its own stream; calls on one net are not thread-safe. */
+#ifndef DTT_NET_H
+#define DTT_NET_H
+
+#include <stdint.h>
+
+#include "dtt.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dtt_net dtt_net;
+
+/* Creates a network with He-normal weights drawn from `seed` and zero biases. */
+dtt_status dtt_net_create(dtt_net** out, int32_t c1, int32_t c2, int32_t c3, uint64_t seed, void* cuda_stream);
+void dtt_net_destroy(dtt_net* net);
+int64_t dtt_net_num_params(const dtt_net* net);
+/* FP32 master parameters in the packed order (host arrays of dtt_net_num_params floats). */
+dtt_status dtt_net_get_params(const dtt_net* net, float* params);
+dtt_status dtt_net_set_params(dtt_net* net, const float* params);
+
+/* Loss and gradients of one input (tracing and parity aid).  x: host float array
+ * [nz][ny][nx][16]; target: host [nz][ny][nx][3]; with d = y - target on the three output
+ * channels and s the largest of nx, ny, nz,
+ *   loss = mean over nodes and channels of  d^2 + w s^2 sum_axis (d(next node) - d)^2
+ * (forward differences between neighbouring nodes inside the grid: the scaled difference
+ * is a strain-like error, which is what the solver's first residual sees; w is set by
+ * dtt_net_set_loss, default 0); grad (host, num_params floats) receives dloss/dparam. */
+dtt_status dtt_net_loss_grad(dtt_net* net, int32_t nx, int32_t ny, int32_t nz, const float* x, const float* target,
+                             double* loss, float* grad);
+
+/* Weight w of the difference term of the training loss (>= 0; 0 = plain mean squares). */
+dtt_status dtt_net_set_loss(dtt_net* net, float grad_weight);
+
+/* Network output y[:, :, :, 0:3] for a host input x (as above) into host out [nz][ny][nx][3]. */
+dtt_status dtt_net_forward(dtt_net* net, int32_t nx, int32_t ny, int32_t nz, const float* x, float* out);
+
+/* Input features of a configured grid (material, constraints and load set), host float
+ * [nz][ny][nx][16] in node order (feature layout above). */
+dtt_status dtt_net_features(dtt_net* net, dtt_grid* grid, float* x);
+
+/* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) on one grid: features, forward,
+ * loss against u_target (host, 3 x n_nodes float64 in the grid's node order, the solver's
+ * converged u~), backward, update.  *loss receives the loss before the update. */
+dtt_status dtt_net_train_step(dtt_net* net, dtt_grid* grid, const double* u_target, float lr, double* loss);
+
+/* Writes the network's guess of u~ into the grid (as dtt_set_initial), for a solve with
+ * init = DTT_INIT_GUESS. */
+dtt_status dtt_net_predict(dtt_net* net, dtt_grid* grid);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DTT_NET_H */

@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdtt.so")
-SOURCES = ["dtt_api.cu", "k_residual.cu", "k_residual_f32.cu", "k_transform.cu", "k_fft.cu", "k_solver.cu", "k_util.cu"]
+SOURCES = ["dtt_api.cu", "k_residual.cu", "k_residual_f32.cu", "k_transform.cu", "k_fft.cu", "k_solver.cu", "k_util.cu",
+           "dtt_net.cu", "k_net.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
@@ -31,7 +32,7 @@ def build(verbose=False, force=False):
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     objs = []
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "dtt.h")]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     newest_dep = max(os.path.getmtime(d) for d in deps)
     for src in SOURCES:
         s = os.path.join(CSRC, src)

@@ -62,95 +62,9 @@ void dfree(P*& p) {
 
 }  // namespace
 
-struct dtt_grid {
-  GridDev g{};
-  int prec = DTT_PREC_FP64;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;   // created here when the caller passes NULL (graph capture
-                             // needs a stream other than the legacy default stream)
-  int types[3][3]{};      // [comp][axis]
-  bool has_null[3]{};
-  long long NN = 0, NV = 0;
-  size_t esz = 8;
+#include "grid_internal.cuh"
 
-  // nodal fields
-  double* u64 = nullptr;
-  float* uhi = nullptr;
-  float* ulo = nullptr;
-  // Anderson rings (T fields): A = p ring (ACV on p~, slots 0..3) or u~-copy ring (ACV on
-  // u~, slots 0..4); Gr = Green-input ring (ACV on p~) whose slot 0 is the Green input
-  // otherwise; R = Anderson residual ring.  step = last full step of u~.
-  void* S[5]{};
-  void* R[4]{};
-  void* Gr[4]{};
-  void* step = nullptr;
-  void* gbuf = nullptr;    // = Gr[0]
-  void* spec = nullptr;
-  void* spec2 = nullptr;
-  void** d_Sring = nullptr;
-  void** d_Rring = nullptr;
-  void** d_Gring = nullptr;
-
-  // material
-  uint8_t* phase = nullptr;
-  double* d_lam = nullptr;
-  double* d_mu = nullptr;
-  int nphase = 0;
-  bool mat_set = false;
-  double lam0 = 0, mu0 = 0;
-  bool ref_set = false;
-  double eps[3][3]{};
-
-  // transforms
-  FftAxisInfo fft[3]{};
-  void* fft_tw[3]{};
-  void* fft_ph[3]{};
-  void* fwd[3][3]{};
-  void* inv[3][3]{};
-  double* sin2q[3][3]{};
-  double* cos2q[3][3]{};
-
-  // constraints (host copy + device CSR)
-  int nrows = 0;
-  std::vector<int> h_ptr;
-  std::vector<long long> h_dof;
-  std::vector<double> h_a, h_b, h_val, h_ab, h_aa;
-  int* d_ptr = nullptr;
-  long long* d_dof = nullptr;
-  double *d_a = nullptr, *d_b = nullptr, *d_target = nullptr, *d_mult = nullptr, *d_ab = nullptr,
-         *d_aa = nullptr;
-  uint8_t* cmask = nullptr;
-
-  // contact
-  bool contact = false;
-  int c_axis = 2, c_face = 1;
-  double center[3]{}, radius = 0;
-  int nface = 0;
-  long long* d_face = nullptr;
-  uint8_t *d_active = nullptr, *d_vgap = nullptr, *d_vreact = nullptr, *d_vgap_prev = nullptr,
-          *d_vreact_prev = nullptr;
-  double *d_gap = nullptr, *d_fn = nullptr, *d_nvec = nullptr;
-
-  // control
-  Ctrl* d_ctrl = nullptr;
-  Ctrl* h_ctrl = nullptr;   // pinned
-  double* d_part = nullptr;
-  size_t part_cap = 0;
-
-  // scratch for operator entry points
-  double* op_d = nullptr;   // 3 NN doubles
-  void* op_t1 = nullptr;    // 3 NN of T
-  void* op_t2 = nullptr;
-
-  // graph
-  cudaGraphExec_t gexec = nullptr;
-  int g_key = -1;
-  unsigned long long id = 0;        // unique per grid of the process
-  unsigned long long version = 0;   // bumped whenever captured launch arguments go stale
-
-  Ctrl last{};
-  bool solved = false;
-};
+dtt_status dtt::set_error(dtt_status s, const std::string& msg) { return fail(s, msg); }
 
 namespace {
 
@@ -1054,6 +968,93 @@ dtt_status dtt_set_initial(dtt_grid* G, const double* u, int32_t ptr_is_device) 
 
 namespace {
 
+// Eq. 5 residual of the current u~ after the initial projections (rows, contact), as the
+// first iteration of a solve would measure it (u~ is projected in place).
+template <typename T>
+dtt_status eval_start_residual(dtt_grid* G, double* r) {
+  cudaStream_t s = G->stream;
+  PartRegions pr = regions(G);
+  Ctrl& c = *G->h_ctrl;
+  std::memset(&c, 0, sizeof(Ctrl));
+  c.max_iter = 1 << 30;
+  c.acv_mod = 1;
+  c.contact_on = G->contact ? 1 : 0;
+  c.update_tol = 1e-2;
+  c.no_stop = 1;
+  Ctrl* ctrl = G->d_ctrl;
+  CK(cudaMemcpyAsync(ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+  ContactArgs ca = contact_args(G, pr.cont);
+  if (G->contact) {
+    CKL(launch_contact_init(ca, s));
+    CKL(launch_contact_proj_U<T>(ca, G->u64, G->uhi, G->ulo, nullptr, s));
+  }
+  if (G->nrows > 0) CKL(launch_proj_U_rows<T>(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, nullptr, ctrl, s));
+  ResidualArgs ra{};
+  ra.g = G->g;
+  ra.u64 = G->u64;
+  ra.uhi = G->uhi;
+  ra.ulo = G->ulo;
+  ra.phase = G->phase;
+  ra.lam = G->d_lam;
+  ra.mu = G->d_mu;
+  ra.nphase = G->nphase;
+  ra.cmask = G->cmask;
+  std::memcpy(ra.eps, G->eps, sizeof(ra.eps));
+  ra.lam0 = G->lam0;
+  ra.mu0 = G->mu0;
+  ra.mode = 2;
+  ra.pout = G->gbuf;
+  ra.partials = pr.res;
+  ra.ctrl = ctrl;
+  CKL(launch_residual<T>(ra, s));
+  if (G->nrows > 0)
+    CKL(launch_proj_P_rows<T>(G->g, rows_dev(G), (T*)G->gbuf, G->d_Sring, G->d_Rring, 0, 0, pr.proj, ctrl, s));
+  if (G->contact) CKL(launch_contact_eval<T>(ca, (T*)G->gbuf, G->d_Sring, G->d_Rring, 0, 0, s));
+  CKL(launch_ctrl_residual(ctrl, pr.res, pr.nres, pr.proj, G->nrows > 0 ? pr.nproj : 0, pr.cont, pr.ncont, G->g.h,
+                           G->NN, G->NV, s));
+  CK(cudaMemcpyAsync(G->h_ctrl, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *r = G->h_ctrl->r;
+  return DTT_OK;
+}
+
+// DTT_INIT_GUESS: keep the supplied u~ only if its starting residual is below u~ = 0's.
+dtt_status choose_start(dtt_grid* G) {
+  cudaStream_t s = G->stream;
+  const size_t n3 = (size_t)(3 * G->NN);
+  const bool f64 = G->prec == DTT_PREC_FP64;
+  double rg = 0.0, r0 = 0.0;
+  dtt_status st = f64 ? eval_start_residual<double>(G, &rg) : eval_start_residual<float>(G, &rg);
+  if (st != DTT_OK) return st;
+  if (f64) {
+    CK(cudaMemcpyAsync(G->S[4], G->u64, n3 * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(G->u64, 0, n3 * 8, s));
+  } else {
+    CK(cudaMemcpyAsync(G->S[3], G->uhi, n3 * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(G->S[4], G->ulo, n3 * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(G->uhi, 0, n3 * 4, s));
+    CK(cudaMemsetAsync(G->ulo, 0, n3 * 4, s));
+  }
+  st = f64 ? eval_start_residual<double>(G, &r0) : eval_start_residual<float>(G, &r0);
+  if (st != DTT_OK) return st;
+  G->start_guess = (std::isfinite(rg) && rg < r0) ? 1 : 0;
+  G->start_r = G->start_guess ? rg : r0;
+  if (G->start_guess) {
+    if (f64) {
+      CK(cudaMemcpyAsync(G->u64, G->S[4], n3 * 8, cudaMemcpyDeviceToDevice, s));
+    } else {
+      CK(cudaMemcpyAsync(G->uhi, G->S[3], n3 * 4, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(G->ulo, G->S[4], n3 * 4, cudaMemcpyDeviceToDevice, s));
+    }
+  } else if (G->contact) {
+    // the contact zone was initialised for the guess; zero u~ takes the plain start's
+    dtt_status st2 = f64 ? eval_start_residual<double>(G, &r0) : eval_start_residual<float>(G, &r0);
+    if (st2 != DTT_OK) return st2;
+  }
+  CK(cudaStreamSynchronize(s));
+  return DTT_OK;
+}
+
 dtt_status check_solve(const dtt_grid* G, const dtt_solve_opts* opts) {
   if (!G || !opts) return fail(DTT_ERR_ARG, "null argument");
   if (!G->mat_set) return fail(DTT_ERR_STATE, "dtt_set_material not called");
@@ -1063,7 +1064,8 @@ dtt_status check_solve(const dtt_grid* G, const dtt_solve_opts* opts) {
   if (opts->acv_on != DTT_ACV_U && opts->acv_on != DTT_ACV_P) return fail(DTT_ERR_ARG, "acv_on must be 0 or 1");
   if (opts->acv_on == DTT_ACV_U && G->prec != DTT_PREC_FP64 && opts->acv_mod > 0)
     return fail(DTT_ERR_ARG, "ACV on u~ is available in the FP64 path only");
-  if (opts->init != DTT_INIT_ZERO && opts->init != DTT_INIT_PREVIOUS) return fail(DTT_ERR_ARG, "init must be 0 or 1");
+  if (opts->init != DTT_INIT_ZERO && opts->init != DTT_INIT_PREVIOUS && opts->init != DTT_INIT_GUESS)
+    return fail(DTT_ERR_ARG, "init must be 0, 1 or 2");
   return DTT_OK;
 }
 
@@ -1093,6 +1095,12 @@ dtt_status prepare_solve(dtt_grid* G, const dtt_solve_opts* opts) {
     }
     CK(cudaMemcpyAsync(G->d_target, tg.data(), G->nrows * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
+  }
+  G->start_guess = 0;
+  G->start_r = 0.0;
+  if (opts->init == DTT_INIT_GUESS) {
+    dtt_status st = choose_start(G);
+    if (st != DTT_OK) return st;
   }
   // control block
   Ctrl& c = *G->h_ctrl;
@@ -1143,6 +1151,8 @@ dtt_status finish_solve(dtt_grid* G, std::chrono::steady_clock::time_point t0, d
     rep->status = st;
     rep->residual = G->last.r;
     rep->seconds = secs;
+    rep->start_from_guess = G->start_guess;
+    rep->start_residual = G->start_r;
   }
   if (st == DTT_ERR_NOT_CONVERGED) g_err = "iteration cap reached";
   if (st == DTT_ERR_DIVERGED) g_err = "residual diverged";

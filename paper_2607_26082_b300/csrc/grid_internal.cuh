@@ -1,0 +1,109 @@
+// Host-side state of one cell (dtt_grid of include/dtt.h), shared by the source files of
+// the library that need a grid's buffers (the solver API and the warm-start network).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "dtt.h"
+#include "dtt_internal.cuh"
+
+using dtt::Ctrl;
+using dtt::FftAxisInfo;
+using dtt::GridDev;
+
+struct dtt_grid {
+  GridDev g{};
+  int prec = DTT_PREC_FP64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;   // created here when the caller passes NULL (graph capture
+                             // needs a stream other than the legacy default stream)
+  int types[3][3]{};      // [comp][axis]
+  bool has_null[3]{};
+  long long NN = 0, NV = 0;
+  size_t esz = 8;
+
+  // nodal fields
+  double* u64 = nullptr;
+  float* uhi = nullptr;
+  float* ulo = nullptr;
+  // Anderson rings (T fields): A = p ring (ACV on p~, slots 0..3) or u~-copy ring (ACV on
+  // u~, slots 0..4); Gr = Green-input ring (ACV on p~) whose slot 0 is the Green input
+  // otherwise; R = Anderson residual ring.  step = last full step of u~.
+  void* S[5]{};
+  void* R[4]{};
+  void* Gr[4]{};
+  void* step = nullptr;
+  void* gbuf = nullptr;    // = Gr[0]
+  void* spec = nullptr;
+  void* spec2 = nullptr;
+  void** d_Sring = nullptr;
+  void** d_Rring = nullptr;
+  void** d_Gring = nullptr;
+
+  // material
+  uint8_t* phase = nullptr;
+  double* d_lam = nullptr;
+  double* d_mu = nullptr;
+  int nphase = 0;
+  bool mat_set = false;
+  double lam0 = 0, mu0 = 0;
+  bool ref_set = false;
+  double eps[3][3]{};
+
+  // transforms
+  FftAxisInfo fft[3]{};
+  void* fft_tw[3]{};
+  void* fft_ph[3]{};
+  void* fwd[3][3]{};
+  void* inv[3][3]{};
+  double* sin2q[3][3]{};
+  double* cos2q[3][3]{};
+
+  // constraints (host copy + device CSR)
+  int nrows = 0;
+  std::vector<int> h_ptr;
+  std::vector<long long> h_dof;
+  std::vector<double> h_a, h_b, h_val, h_ab, h_aa;
+  int* d_ptr = nullptr;
+  long long* d_dof = nullptr;
+  double *d_a = nullptr, *d_b = nullptr, *d_target = nullptr, *d_mult = nullptr, *d_ab = nullptr,
+         *d_aa = nullptr;
+  uint8_t* cmask = nullptr;
+
+  // contact
+  bool contact = false;
+  int c_axis = 2, c_face = 1;
+  double center[3]{}, radius = 0;
+  int nface = 0;
+  long long* d_face = nullptr;
+  uint8_t *d_active = nullptr, *d_vgap = nullptr, *d_vreact = nullptr, *d_vgap_prev = nullptr,
+          *d_vreact_prev = nullptr;
+  double *d_gap = nullptr, *d_fn = nullptr, *d_nvec = nullptr;
+
+  // control
+  Ctrl* d_ctrl = nullptr;
+  Ctrl* h_ctrl = nullptr;   // pinned
+  double* d_part = nullptr;
+  size_t part_cap = 0;
+
+  // scratch for operator entry points
+  double* op_d = nullptr;   // 3 NN doubles
+  void* op_t1 = nullptr;    // 3 NN of T
+  void* op_t2 = nullptr;
+
+  // graph
+  cudaGraphExec_t gexec = nullptr;
+  int g_key = -1;
+  unsigned long long id = 0;        // unique per grid of the process
+  unsigned long long version = 0;   // bumped whenever captured launch arguments go stale
+
+  Ctrl last{};
+  int start_guess = 0;      // last solve started from the supplied guess (DTT_INIT_GUESS)
+  double start_r = 0.0;     // Eq. 5 residual of that solve's starting iterate
+  bool solved = false;
+};
+
+namespace dtt {
+// sets the thread's last-error message and returns s (dtt_last_error reads it)
+dtt_status set_error(dtt_status s, const std::string& msg);
+}  // namespace dtt

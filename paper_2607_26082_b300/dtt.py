@@ -16,7 +16,7 @@ OK, ERR_ARG, ERR_BC, ERR_OVERLAP, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_DIVE
 BC_PERIODIC, BC_DIRICHLET, BC_NEUMANN = 0, 1, 2
 SCHEME_TETRA2, SCHEME_HEX1 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
-INIT_ZERO, INIT_PREVIOUS = 0, 1
+INIT_ZERO, INIT_PREVIOUS, INIT_GUESS = 0, 1, 2
 ACV_U, ACV_P = 0, 1
 
 
@@ -35,7 +35,8 @@ class SolveOpts(C.Structure):
 class Report(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("accelerations", C.c_int32),
                 ("active_set_updates", C.c_int32), ("status", C.c_int32),
-                ("residual", C.c_double), ("seconds", C.c_double)]
+                ("residual", C.c_double), ("seconds", C.c_double), ("start_from_guess", C.c_int32),
+                ("start_residual", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

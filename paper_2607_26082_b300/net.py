@@ -1,0 +1,122 @@
+"""ctypes binding of the warm-start network (include/dtt_net.h): argument marshalling only.
+
+Every method maps to one C entry point of the same name in libdtt; the forward, backward
+and optimiser steps run in the library's CUDA kernels.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import dtt
+
+NET_CIN = 16
+EXPORTS = ["dtt_net_create", "dtt_net_destroy", "dtt_net_num_params", "dtt_net_get_params", "dtt_net_set_params",
+           "dtt_net_loss_grad", "dtt_net_forward", "dtt_net_features", "dtt_net_train_step", "dtt_net_predict",
+           "dtt_net_set_loss"]
+_bound = False
+
+
+def _lib():
+    global _bound
+    L = dtt.lib()
+    if not _bound:
+        P, i32, i64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_float
+        L.dtt_net_create.argtypes = [C.POINTER(P), i32, i32, i32, C.c_uint64, P]
+        L.dtt_net_destroy.argtypes = [P]
+        L.dtt_net_destroy.restype = None
+        L.dtt_net_num_params.argtypes = [P]
+        L.dtt_net_num_params.restype = i64
+        L.dtt_net_get_params.argtypes = [P, P]
+        L.dtt_net_set_params.argtypes = [P, P]
+        L.dtt_net_loss_grad.argtypes = [P, i32, i32, i32, P, P, C.POINTER(C.c_double), P]
+        L.dtt_net_forward.argtypes = [P, i32, i32, i32, P, P]
+        L.dtt_net_features.argtypes = [P, P, P]
+        L.dtt_net_train_step.argtypes = [P, P, P, f32, C.POINTER(C.c_double)]
+        L.dtt_net_predict.argtypes = [P, P]
+        L.dtt_net_set_loss.argtypes = [P, f32]
+        for name in ("dtt_net_create", "dtt_net_get_params", "dtt_net_set_params", "dtt_net_loss_grad",
+                     "dtt_net_forward", "dtt_net_features", "dtt_net_train_step", "dtt_net_predict",
+                     "dtt_net_set_loss"):
+            getattr(L, name).restype = i32
+        _bound = True
+    return L
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Net:
+    """dtt_net: channels (c1, c2, c3) at full, 1/2 and 1/4 resolution."""
+
+    def __init__(self, c1=16, c2=32, c3=64, seed=0, stream=None):
+        L = _lib()
+        self._h = C.c_void_p()
+        dtt._check(L.dtt_net_create(C.byref(self._h), int(c1), int(c2), int(c3), int(seed),
+                                    C.c_void_p(stream) if stream else None))
+        self.channels = (c1, c2, c3)
+
+    def close(self):
+        if self._h:
+            _lib().dtt_net_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self):
+        return int(_lib().dtt_net_num_params(self._h))
+
+    def get_params(self):
+        p = np.zeros(self.num_params, np.float32)
+        dtt._check(_lib().dtt_net_get_params(self._h, p.ctypes.data_as(C.c_void_p)))
+        return p
+
+    def set_params(self, p):
+        p = _f32(p)
+        assert p.size == self.num_params
+        dtt._check(_lib().dtt_net_set_params(self._h, p.ctypes.data_as(C.c_void_p)))
+
+    def set_loss(self, grad_weight):
+        dtt._check(_lib().dtt_net_set_loss(self._h, float(grad_weight)))
+
+    def loss_grad(self, x, target):
+        """x: [nz, ny, nx, 16], target: [nz, ny, nx, 3] -> (loss, grad[num_params])."""
+        x, t = _f32(x), _f32(target)
+        nz, ny, nx = x.shape[:3]
+        loss = C.c_double()
+        g = np.zeros(self.num_params, np.float32)
+        dtt._check(_lib().dtt_net_loss_grad(self._h, nx, ny, nz, x.ctypes.data_as(C.c_void_p),
+                                            t.ctypes.data_as(C.c_void_p), C.byref(loss),
+                                            g.ctypes.data_as(C.c_void_p)))
+        return loss.value, g
+
+    def forward(self, x):
+        x = _f32(x)
+        nz, ny, nx = x.shape[:3]
+        out = np.zeros((nz, ny, nx, 3), np.float32)
+        dtt._check(_lib().dtt_net_forward(self._h, nx, ny, nz, x.ctypes.data_as(C.c_void_p),
+                                          out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def features(self, grid):
+        nn = grid.node_shape   # (nz, ny, nx)
+        x = np.zeros(tuple(nn) + (NET_CIN,), np.float32)
+        dtt._check(_lib().dtt_net_features(self._h, grid._h, x.ctypes.data_as(C.c_void_p)))
+        return x
+
+    def train_step(self, grid, u_target, lr):
+        """u_target: (3,) + node_shape float64 (the solver's converged u~)."""
+        u = np.ascontiguousarray(u_target, dtype=np.float64)
+        loss = C.c_double()
+        dtt._check(_lib().dtt_net_train_step(self._h, grid._h, u.ctypes.data_as(C.c_void_p), float(lr),
+                                             C.byref(loss)))
+        return loss.value
+
+    def predict(self, grid):
+        """Writes the network's guess of u~ into the grid (solve with init=INIT_GUESS)."""
+        dtt._check(_lib().dtt_net_predict(self._h, grid._h))

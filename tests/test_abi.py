@@ -9,10 +9,15 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "dtt.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(dtt_[a-z_]+)\s*\(", src)))
+def _declared(header=None):
+    """Entry points declared by one header of include/ (all headers when None)."""
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)) if header is None else [header]:
+        src = open(os.path.join(inc, h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(dtt_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
@@ -36,8 +41,9 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_binding_names_match_header():
-    from paper_2607_26082_b300 import dtt
-    assert sorted(dtt.EXPORTS) == _declared()
+    from paper_2607_26082_b300 import dtt, net
+    assert sorted(dtt.EXPORTS) == _declared("dtt.h")
+    assert sorted(net.EXPORTS) == _declared("dtt_net.h")
 
 
 def test_package_import_is_lazy():
