@@ -346,6 +346,8 @@ TransformTables tables(dtt_grid* G) {
       t.inv[c][d] = G->inv[c][d];
       t.sin2q[c][d] = G->sin2q[c][d];
       t.cos2q[c][d] = G->cos2q[c][d];
+      t.sin2q_f[c][d] = G->sin2q_f[c][d];
+      t.cos2q_f[c][d] = G->cos2q_f[c][d];
     }
   t.lam0 = G->lam0;
   t.mu0 = G->mu0;
@@ -460,8 +462,16 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
     CKL(launch_proj_P_rows<T>(G->g, rows_dev(G), (T*)G->gbuf, G->d_Sring, G->d_Rring, rm, fused, pr.proj, ctrl, s));
   ContactArgs ca = contact_args(G, pr.cont);
   if (G->contact) CKL(launch_contact_eval<T>(ca, (T*)G->gbuf, G->d_Sring, G->d_Rring, rm, fused, s));
-  CKL(launch_ctrl_residual(ctrl, pr.res, pr.nres, pr.proj, G->nrows > 0 ? pr.nproj : 0, pr.cont, pr.ncont, G->g.h,
-                           G->NN, G->NV, s));
+  // residual control and (no contact, Gram row fused into the residual and projection
+  // kernels) the Anderson solve in one launch
+  const bool merged = diff && fused && !G->contact;
+  if (merged) {
+    CKL(launch_ctrl_residual_acv(ctrl, pr.res, pr.nres, pr.proj, G->nrows > 0 ? pr.nproj : 0, G->g.h, G->NN, G->NV,
+                                 s));
+  } else {
+    CKL(launch_ctrl_residual(ctrl, pr.res, pr.nres, pr.proj, G->nrows > 0 ? pr.nproj : 0, pr.cont, pr.ncont, G->g.h,
+                             G->NN, G->NV, s));
+  }
   if (G->contact) {
     CKL(launch_contact_update(ca, s));
     CKL(launch_ctrl_contact(ctrl, s));
@@ -469,7 +479,8 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
   prof_mark(2, s);
   if (diff) {
     if (fused) {
-      CKL(launch_ctrl_acv_fused(ctrl, pr.res, pr.nres, pr.proj, G->nrows > 0 ? pr.nproj : 0, pr.cont, pr.ncont, s));
+      if (!merged)
+        CKL(launch_ctrl_acv_fused(ctrl, pr.res, pr.nres, pr.proj, G->nrows > 0 ? pr.nproj : 0, pr.cont, pr.ncont, s));
     } else {
       CKL(launch_acv_gram<T>(G->g, G->d_Rring, pr.acv, ctrl, s));
       CKL(launch_ctrl_acv(ctrl, pr.acv, pr.nacv, s));
@@ -685,6 +696,8 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
       if (s == DTT_OK) s = dalloc(&G->inv[c][d], (size_t)nn * nn * G->esz);
       if (s == DTT_OK) s = dalloc(&G->sin2q[c][d], (size_t)nn * sizeof(double));
       if (s == DTT_OK) s = dalloc(&G->cos2q[c][d], (size_t)nn * sizeof(double));
+      if (s == DTT_OK) s = dalloc(&G->sin2q_f[c][d], (size_t)nn * sizeof(float));
+      if (s == DTT_OK) s = dalloc(&G->cos2q_f[c][d], (size_t)nn * sizeof(float));
       if (s != DTT_OK) break;
       if (G->esz == 8) {
         cudaMemcpy(G->fwd[c][d], F.data(), F.size() * 8, cudaMemcpyHostToDevice);
@@ -696,6 +709,11 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
       }
       cudaMemcpy(G->sin2q[c][d], cq.data(), cq.size() * 8, cudaMemcpyHostToDevice);
       cudaMemcpy(G->cos2q[c][d], cc.data(), cc.size() * 8, cudaMemcpyHostToDevice);
+      {
+        std::vector<float> cqf(cq.begin(), cq.end()), ccf(cc.begin(), cc.end());
+        cudaMemcpy(G->sin2q_f[c][d], cqf.data(), cqf.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(G->cos2q_f[c][d], ccf.data(), ccf.size() * 4, cudaMemcpyHostToDevice);
+      }
     }
   for (int d = 0; d < 3 && s == DTT_OK; ++d) s = build_fft_axis(G, d);
   if (s == DTT_OK) {
@@ -745,6 +763,8 @@ void dtt_grid_destroy(dtt_grid* G) {
       dfree(G->inv[c][d]);
       dfree(G->sin2q[c][d]);
       dfree(G->cos2q[c][d]);
+      dfree(G->sin2q_f[c][d]);
+      dfree(G->cos2q_f[c][d]);
     }
   for (int d = 0; d < 3; ++d) {
     dfree(G->fft_tw[d]);

@@ -195,14 +195,30 @@ struct TransformTables {
   const void* inv[3][3];   // [comp][axis] nn x nn row-major (node j, spectral k)
   const double* sin2q[3][3];   // sin^2(q_k / 2) at every spectral position (0 unused)
   const double* cos2q[3][3];   // cos^2(q_k / 2) (1 unused)
+  const float* sin2q_f[3][3];  // the same tables in FP32
+  const float* cos2q_f[3][3];
   double lam0, mu0;
   double null_thr[3];
 };
 struct GreenTables {
   const double* s[3][3];
   const double* cp[3][3];
+  const float* sf[3][3];    // FP32 copies
+  const float* cpf[3][3];
   double null_thr[3];
+  float null_thr_f[3];
 };
+// symbol factor tables in the field precision (no conversions in the mixed path)
+template <typename T>
+__device__ __forceinline__ T gt_s(const GreenTables& gt, int c, int d, int k) {
+  if constexpr (sizeof(T) == 4) return gt.sf[c][d][k];
+  else return (T)gt.s[c][d][k];
+}
+template <typename T>
+__device__ __forceinline__ T gt_c(const GreenTables& gt, int c, int d, int k) {
+  if constexpr (sizeof(T) == 4) return gt.cpf[c][d][k];
+  else return (T)gt.cp[c][d][k];
+}
 struct IncrTarget {
   double* u64;
   float* uhi;
@@ -282,6 +298,8 @@ int launch_ctrl_contact(Ctrl* c, cudaStream_t s);
 int launch_ctrl_acv(Ctrl* c, const double* partials, int nblk, cudaStream_t s);
 // Gram row from the fused sources: residual (RES_STRIDE, offset 2), projections
 // (PROJ_STRIDE, offset 1), contact (CONT_STRIDE, offset 4)
+int launch_ctrl_residual_acv(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, double h,
+                             long long nnodes, long long nvox, cudaStream_t s);
 int launch_ctrl_acv_fused(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, const double* cp,
                           int ncont, cudaStream_t s);
 int launch_ctrl_end(Ctrl* c, cudaStream_t s);

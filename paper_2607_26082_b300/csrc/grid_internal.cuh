@@ -58,6 +58,8 @@ struct dtt_grid {
   void* inv[3][3]{};
   double* sin2q[3][3]{};
   double* cos2q[3][3]{};
+  float* sin2q_f[3][3]{};   // FP32 copies (mixed-precision Green multiply)
+  float* cos2q_f[3][3]{};
 
   // constraints (host copy + device CSR)
   int nrows = 0;

@@ -356,15 +356,15 @@ k_fft_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenT
   if (tid < 2 * PB) {
     const long long pen = pen0 + tid;
     const int ix = pen < p.npencil ? (int)(pen % p.nnx) : 0, iy = pen < p.npencil ? (int)(pen / p.nnx) : 0;
-    pxy[tid][0] = (T)gt.s[comp][0][ix];
-    pxy[tid][1] = (T)gt.cp[comp][0][ix];
-    pxy[tid][2] = (T)gt.s[comp][1][iy];
-    pxy[tid][3] = (T)gt.cp[comp][1][iy];
+    pxy[tid][0] = gt_s<T>(gt, comp, 0, ix);
+    pxy[tid][1] = gt_c<T>(gt, comp, 0, ix);
+    pxy[tid][2] = gt_s<T>(gt, comp, 1, iy);
+    pxy[tid][3] = gt_c<T>(gt, comp, 1, iy);
   }
   for (int q = tid; q < p.L; q += nthr) tws[q] = tw[q];
   for (int q = tid; q < nn; q += nthr) {
-    zs[q] = (T)gt.s[comp][2][q];
-    zc[q] = (T)gt.cp[comp][2][q];
+    zs[q] = gt_s<T>(gt, comp, 2, q);
+    zc[q] = gt_c<T>(gt, comp, 2, q);
   }
   __syncthreads();
   const bool quarter = (type == T_DCT3 || type == T_DST3);
@@ -375,7 +375,7 @@ k_fft_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenT
   Cx<T>* Y = fft_sequences<T, PB>(bufA, bufB, p, tws, -1, tid, nthr);
   Cx<T>* I = (Y == bufA) ? bufB : bufA;
   T* spec = (T*)I;   // 2 PB x nn real spectra (fits in one complex buffer)
-  const T thr = (T)gt.null_thr[comp];
+  const T thr = sizeof(T) == 4 ? (T)gt.null_thr_f[comp] : (T)gt.null_thr[comp];
   for (int idx = tid; idx < 2 * PB * nn; idx += nthr) {
     const int pb = idx % (2 * PB), k = idx / (2 * PB);
     T v = (T)0;
@@ -701,16 +701,17 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
   pencil_bases<T, SEQ>(sbase, p, pen0, tid);
   for (int q = tid; q < NPEN; q += 256) {
     const long long pen = pen0 + q;
-    const int ix = pen < p.npencil ? (int)(pen % p.nnx) : 0, iy = pen < p.npencil ? (int)(pen / p.nnx) : 0;
-    pxy[q][0] = (T)gt.s[comp][0][ix];
-    pxy[q][1] = (T)gt.cp[comp][0][ix];
-    pxy[q][2] = (T)gt.s[comp][1][iy];
-    pxy[q][3] = (T)gt.cp[comp][1][iy];
+    const int pen32 = pen < p.npencil ? (int)pen : 0;   // z pencils: pen = ix + nnx iy < 2^31
+    const int ix = pen32 % p.nnx, iy = pen32 / p.nnx;
+    pxy[q][0] = gt_s<T>(gt, comp, 0, ix);
+    pxy[q][1] = gt_c<T>(gt, comp, 0, ix);
+    pxy[q][2] = gt_s<T>(gt, comp, 1, iy);
+    pxy[q][3] = gt_c<T>(gt, comp, 1, iy);
   }
   for (int q = tid; q < L; q += 256) tws[q] = ((const Cx<T>*)p.tw)[q];
   for (int q = tid; q < nn; q += 256) {
-    zs[q] = (T)gt.s[comp][2][q];
-    zc[q] = (T)gt.cp[comp][2][q];
+    zs[q] = gt_s<T>(gt, comp, 2, q);
+    zc[q] = gt_c<T>(gt, comp, 2, q);
   }
   for (int q = tid; q < 2 * SEQ * PADL; q += 256) re[q] = (T)0;
   __syncthreads();
@@ -724,7 +725,7 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
   __syncthreads();
   fast_fft<T, L>(re, im, tws, -1, tid / NT, tid % NT, quarter ? ph : nullptr);
   // Green multiply into spec
-  const T thr = (T)gt.null_thr[comp];
+  const T thr = sizeof(T) == 4 ? (T)gt.null_thr_f[comp] : (T)gt.null_thr[comp];
   for (int idx = tid; idx < NPEN * nn; idx += 256) {
     const int pb = idx % NPEN, k = idx / NPEN;
     T v = (T)0;

@@ -130,20 +130,34 @@ k_residual_f32(ResidualArgs a) {
   const float c4h = inv4h;
   const float (&eps)[3][3] = a.f_eps;
 
-  // ---- plane loader: node plane kk and the voxel phases of layer kk into ring slot
+  // ---- plane loader: node plane kk and the voxel phases of layer kk into ring slot.  Each
+  // thread owns at most two positions of the 34 x 10 plane; their xy offsets are fixed for
+  // the whole march.
+  int nq = 0, q_off[2] = {0, 0};
+  long long q_node[2] = {-1, -1}, q_vox[2] = {-1, -1};
+  for (int q = tid; q < FHX * FHY; q += FTHREADS, ++nq) {
+    const int lx = q % FHX, ly = q / FHX;
+    q_off[nq] = ly * FHX + lx;
+    const int gi = wrapi(x0 - 1 + lx, nnx, g.periodic[0]);
+    const int gj = wrapi(y0 - 1 + ly, nny, g.periodic[1]);
+    q_node[nq] = (gi >= 0 && gj >= 0) ? gi + (long long)nnx * gj : -1;
+    const int vx = wrapi(x0 - 1 + lx, g.nvox[0], g.periodic[0]);
+    const int vy = wrapi(y0 - 1 + ly, g.nvox[1], g.periodic[1]);
+    q_vox[nq] = (vx >= 0 && vy >= 0) ? vx + (long long)g.nvox[0] * vy : -1;
+  }
+  const long long plane_n = (long long)nnx * nny, plane_v = (long long)g.nvox[0] * g.nvox[1];
   auto load_plane = [&](int kk) {
     const int slot = slot_of(kk);
     const int kw = wrapi(kk, nnz, g.periodic[2]);
     const int vz = wrapi(kk, g.nvox[2], g.periodic[2]);
-    for (int q = tid; q < FHX * FHY; q += FTHREADS) {
-      const int lx = q % FHX, ly = q / FHX;
-      const int gi = wrapi(x0 - 1 + lx, nnx, g.periodic[0]);
-      const int gj = wrapi(y0 - 1 + ly, nny, g.periodic[1]);
-      const bool ok = kw >= 0 && gi >= 0 && gj >= 0;
-      const long long n = ok ? gi + (long long)nnx * (gj + (long long)nny * kw) : 0;
+    #pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      if (m >= nq) break;
+      const bool ok = kw >= 0 && q_node[m] >= 0;
+      const long long n = ok ? q_node[m] + plane_n * kw : 0;
       #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const int si = sidx(slot, c, ly, lx);
+        const int si = (slot * 3 + c) * FHY * FHX + q_off[m];
         if (ok) {
           cp_async4(&sH[si], a.uhi + c * NN + n);
           cp_async4(&sL[si], a.ulo + c * NN + n);
@@ -155,11 +169,9 @@ k_residual_f32(ResidualArgs a) {
           sD[si] = 0.f;
         }
       }
-      const int vx = wrapi(x0 - 1 + lx, g.nvox[0], g.periodic[0]);
-      const int vy = wrapi(y0 - 1 + ly, g.nvox[1], g.periodic[1]);
       uint8_t ph = 255;   // 255 = no voxel
-      if (vx >= 0 && vy >= 0 && vz >= 0) ph = a.phase[vx + (long long)g.nvox[0] * (vy + (long long)g.nvox[1] * vz)];
-      sP[(slot * FHY + ly) * FHX + lx] = ph;
+      if (vz >= 0 && q_vox[m] >= 0) ph = a.phase[q_vox[m] + plane_v * vz];
+      sP[slot * FHY * FHX + q_off[m]] = ph;
     }
   };
 
@@ -337,21 +349,27 @@ k_residual_f32(ResidualArgs a) {
         const int k = L;
         const long long n = nL;
         const int idx[3] = {i, j, k};
+        // nodes on no non-periodic face (most of them) skip the per-component face checks
+        bool face = false;
+        #pragma unroll
+        for (int d = 0; d < 3; ++d) face |= !g.periodic[d] && (idx[d] == 0 || idx[d] == g.nn[d] - 1);
         float p2loc = 0.f, gloc[4] = {0.f, 0.f, 0.f, 0.f};
         #pragma unroll
         for (int c = 0; c < 3; ++c) {
           float invW = 1.f;
           bool dof = true;
-          #pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            if (g.periodic[d]) continue;
-            int f = -1;
-            if (idx[d] == 0) f = 0;
-            else if (idx[d] == g.nn[d] - 1) f = 1;
-            if (f < 0) continue;
-            const int t = g.bc[d][f][c];
-            if (t == BC_D) dof = false;
-            else if (t == BC_N) invW *= 2.f;
+          if (face) {
+            #pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              if (g.periodic[d]) continue;
+              int f = -1;
+              if (idx[d] == 0) f = 0;
+              else if (idx[d] == g.nn[d] - 1) f = 1;
+              if (f < 0) continue;
+              const int t = g.bc[d][f][c];
+              if (t == BC_D) dof = false;
+              else if (t == BC_N) invW *= 2.f;
+            }
           }
           float pv = 0.f, a0v = 0.f;
           if (dof) {

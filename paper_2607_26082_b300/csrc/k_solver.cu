@@ -523,6 +523,38 @@ int launch_acv_accel(const GridDev& g, int acv_on, void* const* Sring, void* con
 
 // ------------------------------------------------------------------ control
 // Deterministic reduction of partial sums: fixed strided order + fixed tree.
+// NV consecutive entries (off .. off + NV - 1) of n strided partial-sum records reduced in one
+// pass: per thread in index order, then the warp shuffle tree, then warp totals in warp
+// order -- the same order as NV separate reduce_fixed calls, with one barrier round.
+// Results in out[0..NV-1] (shared memory, valid in every thread after the call).
+template <int NV>
+__device__ __forceinline__ void reduce_many(const double* v, int n, int stride, int off, double* out,
+                                            double (*sh)[SB / 32]) {
+  double acc[NV];
+  #pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    #pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] += v[(long long)k * stride + off + q];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  #pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+  }
+  __syncthreads();
+  if (lane == 0)
+    #pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q][w] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[threadIdx.x][k];
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ double reduce_fixed(const double* v, int n, int stride, int off, double* sh) {
   double t = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) t += v[(long long)k * stride + off];
@@ -530,21 +562,9 @@ __device__ __forceinline__ double reduce_fixed(const double* v, int n, int strid
   return s;
 }
 
-__global__ void k_ctrl_residual(Ctrl* c, const double* rp, int nres, const double* pp, int nproj,
-                                const double* cp, int ncont, double h, long long nnodes, long long nvox) {
-  __shared__ double sh[SB / 32];
-  if (c->done) return;
-  double s2 = reduce_fixed(rp, nres, RES_STRIDE, 0, sh);
-  double p2 = reduce_fixed(rp, nres, RES_STRIDE, 1, sh);
-  double q2 = (nproj > 0) ? reduce_fixed(pp, nproj, PROJ_STRIDE, 0, sh) : 0.0;
-  double c2 = 0.0, ng = 0.0, nr = 0.0, mm = 0.0;
-  if (ncont > 0) {
-    c2 = reduce_fixed(cp, ncont, CONT_STRIDE, 0, sh);
-    ng = reduce_fixed(cp, ncont, CONT_STRIDE, 1, sh);
-    nr = reduce_fixed(cp, ncont, CONT_STRIDE, 2, sh);
-    mm = reduce_fixed(cp, ncont, CONT_STRIDE, 3, sh);
-  }
-  if (threadIdx.x != 0) return;
+// Residual norms (Eq. 5), history and exit decision of one iteration (thread 0).
+__device__ void ctrl_residual_core(Ctrl* c, double s2, double p2, double q2, double c2, double ng, double nr,
+                                   double mm, double h, long long nnodes, long long nvox) {
   double pt = p2 + q2 + c2;
   c->p2 = pt;
   c->s2 = s2;
@@ -568,6 +588,24 @@ __global__ void k_ctrl_residual(Ctrl* c, const double* rp, int nres, const doubl
     if (c->prev_valid && c->n_mismatch == 0 && r < c->update_tol) c->update = 1;
     c->prev_valid = 1;
   }
+}
+
+__global__ void k_ctrl_residual(Ctrl* c, const double* rp, int nres, const double* pp, int nproj,
+                                const double* cp, int ncont, double h, long long nnodes, long long nvox) {
+  __shared__ double sh[SB / 32];
+  if (c->done) return;
+  double s2 = reduce_fixed(rp, nres, RES_STRIDE, 0, sh);
+  double p2 = reduce_fixed(rp, nres, RES_STRIDE, 1, sh);
+  double q2 = (nproj > 0) ? reduce_fixed(pp, nproj, PROJ_STRIDE, 0, sh) : 0.0;
+  double c2 = 0.0, ng = 0.0, nr = 0.0, mm = 0.0;
+  if (ncont > 0) {
+    c2 = reduce_fixed(cp, ncont, CONT_STRIDE, 0, sh);
+    ng = reduce_fixed(cp, ncont, CONT_STRIDE, 1, sh);
+    nr = reduce_fixed(cp, ncont, CONT_STRIDE, 2, sh);
+    mm = reduce_fixed(cp, ncont, CONT_STRIDE, 3, sh);
+  }
+  if (threadIdx.x != 0) return;
+  ctrl_residual_core(c, s2, p2, q2, c2, ng, nr, mm, h, nnodes, nvox);
 }
 
 __global__ void k_ctrl_contact(Ctrl* c) {
@@ -664,6 +702,39 @@ __global__ void k_ctrl_acv_fused(Ctrl* c, const double* rp, int nres, const doub
   }
   if (threadIdx.x != 0) return;
   ctrl_acv_core(c, d);
+}
+
+// k_ctrl_residual followed by k_ctrl_acv_fused in one launch (iterations without contact,
+// where nothing runs between the two); both reductions in one pass each.
+__global__ void k_ctrl_residual_acv(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, double h,
+                                    long long nnodes, long long nvox) {
+  __shared__ double sh[RES_STRIDE][SB / 32];
+  __shared__ double rs[RES_STRIDE], ps[PROJ_STRIDE];
+  __shared__ double d[4];   // Gram row (thread 0)
+  __shared__ int sdone;
+  if (c->done) return;
+  reduce_many<RES_STRIDE>(rp, nres, RES_STRIDE, 0, rs, sh);   // [s2, p2, Gram 0..3]
+  if (nproj > 0) {
+    reduce_many<PROJ_STRIDE>(pp, nproj, PROJ_STRIDE, 0, ps, sh);   // [p2, Gram 0..3]
+  } else if (threadIdx.x < PROJ_STRIDE) {
+    ps[threadIdx.x] = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctrl_residual_core(c, rs[0], rs[1], ps[0], 0.0, 0.0, 0.0, 0.0, h, nnodes, nvox);
+    sdone = c->done;
+  }
+  __syncthreads();
+  if (sdone || threadIdx.x != 0) return;
+  const bool row = c->i_local > 0;
+  for (int k = 0; k < 4; ++k) d[k] = row ? rs[2 + k] + ps[1 + k] : 0.0;
+  ctrl_acv_core(c, d);
+}
+
+int launch_ctrl_residual_acv(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, double h,
+                             long long nnodes, long long nvox, cudaStream_t s) {
+  k_ctrl_residual_acv<<<1, SB, 0, s>>>(c, rp, nres, pp, nproj, h, nnodes, nvox);
+  return (int)cudaGetLastError();
 }
 
 int launch_ctrl_acv_fused(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, const double* cp,

@@ -177,8 +177,11 @@ int launch_z_green(const GridDev& g, const T* in, T* out, const TransformTables&
     for (int d = 0; d < 3; ++d) {
       gt.s[c][d] = tt.sin2q[c][d];
       gt.cp[c][d] = tt.cos2q[c][d];
+      gt.sf[c][d] = tt.sin2q_f[c][d];
+      gt.cpf[c][d] = tt.cos2q_f[c][d];
     }
     gt.null_thr[c] = tt.null_thr[c];
+    gt.null_thr_f[c] = (float)tt.null_thr[c];
   }
   return launch_fft_z_green<T>(in, out, p, gt, tt.lam0, tt.mu0, g.scheme, g.h, ncomp, ctrl, s);
 }
@@ -243,12 +246,12 @@ __global__ void k_green(const GridDev g, T* __restrict__ spec, GreenTables gt, d
   const int k = blockIdx.z - c * g.nn[2];
   const int j = blockIdx.y;
   const T ih2 = (T)(4.0 / (g.h * g.h));
-  const T sy = (T)gt.s[c][1][j], sz = (T)gt.s[c][2][k];
-  const T cy = (T)gt.cp[c][1][j], cz = (T)gt.cp[c][2][k];
-  const T l0 = (T)lam0, m2 = (T)(2.0 * mu0), thr = (T)gt.null_thr[c];
+  const T sy = gt_s<T>(gt, c, 1, j), sz = gt_s<T>(gt, c, 2, k);
+  const T cy = gt_c<T>(gt, c, 1, j), cz = gt_c<T>(gt, c, 2, k);
+  const T l0 = (T)lam0, m2 = (T)(2.0 * mu0), thr = sizeof(T) == 4 ? (T)gt.null_thr_f[c] : (T)gt.null_thr[c];
   T* row = spec + (long long)c * g.nnodes + ((long long)k * g.nn[1] + j) * g.nn[0];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nn[0]; i += gridDim.x * blockDim.x) {
-    const T sx = (T)gt.s[c][0][i], cx = (T)gt.cp[c][0][i];
+    const T sx = gt_s<T>(gt, c, 0, i), cx = gt_c<T>(gt, c, 0, i);
     T Sx, Sy, Sz;
     if (g.scheme == SCHEME_TETRA2) {
       Sx = tetra_S<T>(sx, cy, sy, cx, sz);
@@ -274,8 +277,11 @@ int launch_green_multiply(const GridDev& g, T* spec, const TransformTables& tt, 
     for (int d = 0; d < 3; ++d) {
       gt.s[c][d] = tt.sin2q[c][d];
       gt.cp[c][d] = tt.cos2q[c][d];
+      gt.sf[c][d] = tt.sin2q_f[c][d];
+      gt.cpf[c][d] = tt.cos2q_f[c][d];
     }
     gt.null_thr[c] = tt.null_thr[c];
+    gt.null_thr_f[c] = (float)tt.null_thr[c];
   }
   dim3 grd((g.nn[0] + 127) / 128, g.nn[1], 3 * g.nn[2]);
   k_green<T><<<grd, 128, 0, s>>>(g, spec, gt, tt.lam0, tt.mu0, ctrl);
