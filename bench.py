@@ -31,6 +31,24 @@ sys.path.insert(0, ROOT)
 import workloads as wl  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
+
+# DRAM traffic per launch of the dominant kernel on this workload, from one ncu capture
+# (profiles/k_residual_f32_ct_128x128x32.md); reported only while the kernel source is the
+# one that was profiled.
+PROFILED_TRAFFIC = {"residual": {"source": "paper_2607_26082_b300/csrc/k_residual_f32.cu",
+                                 "sha256_prefix": "8983976e78458012", "bytes": 48171264}}
+
+
+def profiled_traffic(group):
+    import hashlib
+    rec = PROFILED_TRAFFIC.get(group)
+    if not rec:
+        return None
+    try:
+        h = hashlib.sha256(open(os.path.join(ROOT, rec["source"]), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return rec["bytes"] if h.startswith(rec["sha256_prefix"]) else None
 FP32_LANES_PER_SM = 128
 
 
@@ -302,7 +320,7 @@ def run_ours(args, rank, world, local):
         "speedup_per_iteration_vs_fp64": (tot_vi / tot_t) / fp64["value"],
         "tuning": gm.tuning.as_dict(),
         "roofline": {"bound": "hbm", "kernel_group": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_source": peak_src, "traffic": None,
+                     "frac": achieved / hbm, "peak_source": peak_src, "traffic": profiled_traffic(dom),
                      "group_ms_per_iteration": prof},
         "cpu_baseline": cpu,
         "clocks": clocks,
