@@ -115,6 +115,14 @@ def main(argv=None):
                                init=dtt.INIT_PREVIOUS if s else dtt.INIT_ZERO, graph_iters=a.graph_iters)
         out = {"workload": spec["name"], "precision": a.precision, "step": s}
         out.update(rep.as_dict())
+        if ind:
+            # contact force on the sphere and the Hertz value (Eq. 30) at this depth
+            act, gap, fn, force = g.dtt_get_contact()
+            d = float(ind["ratios"][s]) * ind["radius"]
+            Es = ind["E"] / (1.0 - ind["nu"] ** 2)
+            out.update({"depth": d, "d_over_R": float(ind["ratios"][s]), "contact_nodes": int(np.sum(act)),
+                        "force": float(np.linalg.norm(force)),
+                        "hertz": 4.0 / 3.0 * Es * np.sqrt(ind["radius"]) * d ** 1.5})
         print(json.dumps(out), flush=True)
     g.close()
     return 0

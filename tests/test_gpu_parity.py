@@ -326,6 +326,28 @@ def test_contact_increments(prec):
             assert np.abs(force - ref.force).max() <= 1e-5 * np.abs(ref.force).max()
 
 
+def test_hertz_law_small_depths():
+    """Frictionless sphere on a bottom-clamped block (Section 5.4): at depths where the
+    contact patch spans several nodes and the block is still much larger than it, the
+    contact force follows Eq. 30 within 3 %."""
+    w = wl.indentation(128, 128, 64, R=32.0, steps=3, dmin=0.0016, dmax=0.004)
+    I = w.indenter
+    g = gpu_grid(w, MIXED)
+    g.dtt_set_indenter(I["axis"], I["face"], I["centers"][0], I["radius"])
+    for step, O in enumerate(I["centers"]):
+        g.dtt_move_indenter(O)
+        rep = g.dtt_solve_step(1e-7, 20000, acv_mod=3, init=dtt.INIT_PREVIOUS if step else dtt.INIT_ZERO)
+        assert rep.status == dtt.OK
+        act, gap, fn, force = g.dtt_get_contact()
+        d = I["ratios"][step] * I["radius"]
+        hertz = 4.0 / 3.0 * I["E"] / (1 - I["nu"] ** 2) * np.sqrt(I["radius"]) * d ** 1.5
+        assert abs(np.linalg.norm(force) / hertz - 1.0) <= 0.03, (step, np.linalg.norm(force), hertz)
+        # complementarity at convergence: no penetration beyond rounding, no tensile reaction
+        assert gap.min() >= -1e-6 * I["radius"]
+        assert (fn[act] <= 1e-8 * np.abs(fn).max()).all()
+    g.close()
+
+
 # ----------------------------------------------------------------------------- errors
 def test_error_statuses():
     bc = np.full((3, 2, 3), wl.N)
