@@ -638,14 +638,42 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   for (int q = tid; q < L; q += 256) tws[q] = ((const Cx<T>*)p.tw)[q];
   for (int q = tid; q < 2 * SEQ * PADL; q += 256) re[q] = (T)0;
   __syncthreads();
+  // global loads in groups of FB per thread before they are placed, so that several are in
+  // flight at once
+  constexpr int FB = 4;
   if (p.axis == 0) {
     const int warp = tid >> 5, lane = tid & 31;
-    for (int pb = warp; pb < npen; pb += 8)
-      for (int j = lane; j < nn; j += 32) fast_place<T, L>(re, im, pb, j, src[sbase[pb] + j], n, type, p.inverse);
+    for (int pb = warp; pb < npen; pb += 8) {
+      const T* row = src + sbase[pb];
+      for (int j0 = lane; j0 < nn; j0 += 32 * FB) {
+        T v[FB];
+        #pragma unroll
+        for (int u = 0; u < FB; ++u) {
+          const int j = j0 + 32 * u;
+          v[u] = j < nn ? row[j] : (T)0;
+        }
+        #pragma unroll
+        for (int u = 0; u < FB; ++u) {
+          const int j = j0 + 32 * u;
+          if (j < nn) fast_place<T, L>(re, im, pb, j, v[u], n, type, p.inverse);
+        }
+      }
+    }
   } else {
-    for (int idx = tid; idx < NPEN * nn; idx += 256) {
-      const int pb = idx % NPEN, j = idx / NPEN;
-      if (pb < npen) fast_place<T, L>(re, im, pb, j, src[sbase[pb] + j * stride], n, type, p.inverse);
+    for (int i0 = tid; i0 < NPEN * nn; i0 += 256 * FB) {
+      T v[FB];
+      #pragma unroll
+      for (int u = 0; u < FB; ++u) {
+        const int idx = i0 + 256 * u;
+        const int pb = idx % NPEN, j = idx / NPEN;
+        v[u] = (idx < NPEN * nn && pb < npen) ? src[sbase[pb] + j * stride] : (T)0;
+      }
+      #pragma unroll
+      for (int u = 0; u < FB; ++u) {
+        const int idx = i0 + 256 * u;
+        const int pb = idx % NPEN, j = idx / NPEN;
+        if (idx < NPEN * nn && pb < npen) fast_place<T, L>(re, im, pb, j, v[u], n, type, p.inverse);
+      }
     }
   }
   __syncthreads();
@@ -718,9 +746,20 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
   const bool quarter = (type == T_DCT3 || type == T_DST3);
   const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
   // forward along z
-  for (int idx = tid; idx < NPEN * nn; idx += 256) {
-    const int pb = idx % NPEN, j = idx / NPEN;
-    if (pb < npen) fast_place<T, L>(re, im, pb, j, in[coff + sbase[pb] + j * stride], n, type, 0);
+  for (int i0 = tid; i0 < NPEN * nn; i0 += 256 * 4) {
+    T v[4];
+    #pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = i0 + 256 * u;
+      const int pb = idx % NPEN, j = idx / NPEN;
+      v[u] = (idx < NPEN * nn && pb < npen) ? in[coff + sbase[pb] + j * stride] : (T)0;
+    }
+    #pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = i0 + 256 * u;
+      const int pb = idx % NPEN, j = idx / NPEN;
+      if (idx < NPEN * nn && pb < npen) fast_place<T, L>(re, im, pb, j, v[u], n, type, 0);
+    }
   }
   __syncthreads();
   fast_fft<T, L>(re, im, tws, -1, tid / NT, tid % NT, quarter ? ph : nullptr);

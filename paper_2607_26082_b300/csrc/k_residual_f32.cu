@@ -234,7 +234,11 @@ k_residual_f32(ResidualArgs a) {
                          (y0 - 1 + vly) < g.nvox[1] && L < g.nvox[2];
         const float w = (SCHEME == SCHEME_TETRA2) ? 0.5f : 1.f;
         // corner b = cx + 2 cy + 4 cz of the voxel, component c
-        auto corner = [&](int b, int c) { return sidx((b >> 2) ? s1 : s0, c, vly + ((b >> 1) & 1), vlx + (b & 1)); };
+        // corner b = cx + 2 cy + 4 cz, component c: the plane's base index plus a constant
+        const int base0 = sidx(s0, 0, vly, vlx), base1 = sidx(s1, 0, vly, vlx);
+        auto corner = [&](int b, int c) {
+          return ((b >> 2) ? base1 : base0) + c * (FHY * FHX) + ((b >> 1) & 1) * FHX + (b & 1);
+        };
         #pragma unroll
         for (int t = 0; t < NPT; ++t) {
           float G[3][3], GD[3][3];
