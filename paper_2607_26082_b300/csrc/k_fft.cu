@@ -701,9 +701,10 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   }
 }
 
-// Fused z pass on the register-radix route (same contract as k_fft_z_green).
+// Fused z pass on the register-radix route (same contract as k_fft_z_green).  Five CTAs of
+// 256 threads per SM fit its shared memory; the launch bound keeps registers to match.
 template <typename T, int L>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 5)
 k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenTables gt, T l0, T m2, T ih2,
                    int scheme, T zscale, const Ctrl* ctrl) {
   constexpr int SEQ = FastPlan<L>::SEQ, NT = FastPlan<L>::NT, PADL = FastPlan<L>::PADL, NPEN = 2 * SEQ;

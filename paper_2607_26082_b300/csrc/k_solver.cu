@@ -465,11 +465,70 @@ __global__ void k_acv_green_input(long long total, void* const* P, void* const* 
   }
 }
 
+// FP32 form of k_acv_green_input on float4 vectors (ring fields are 256-byte aligned; the
+// last total % 4 values take the scalar path), same arithmetic per value.
+__device__ __forceinline__ float acv_combine(float q0, float q1, float q2, float q3, float r0, float r1, float r2,
+                                             float g0, float g1, float g2, float a0, float a1, float a2, float a3,
+                                             float b0, float b1, float b2) {
+  float v = a0 * q0 + a1 * q1 + a2 * q2 + a3 * q3;
+  v -= b0 * (r0 - q1 + g0);
+  v -= b1 * (r1 - q2 + g1);
+  v -= b2 * (r2 - q3 + g2);
+  return v;
+}
+
+__global__ void k_acv_green_input_v4(long long total, void* const* P, void* const* Gr, void* const* R,
+                                     const Ctrl* ctrl) {
+  if (ctrl->done) return;
+  const int i = ctrl->i_local;
+  float* gi = (float*)Gr[i % 4];
+  const long long n4 = total / 4;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (!ctrl->accel) {
+    const float* pi = (const float*)P[i == 0 ? ctrl->pslot : i % 4];
+    for (long long e = t0; e < n4; e += stride) ((float4*)gi)[e] = ((const float4*)pi)[e];
+    for (long long e = 4 * n4 + t0; e < total; e += stride) gi[e] = pi[e];
+    return;
+  }
+  const float a0 = (float)ctrl->alpha[0], a1 = (float)ctrl->alpha[1], a2 = (float)ctrl->alpha[2],
+              a3 = (float)ctrl->alpha[3];
+  const float b0 = a0, b1 = a0 + a1, b2 = a0 + a1 + a2;
+  const float* p0 = (const float*)P[(i - 3) % 4];
+  const float* p1 = (const float*)P[(i - 2) % 4];
+  const float* p2 = (const float*)P[(i - 1) % 4];
+  const float* p3 = (const float*)P[i % 4];
+  const float* r0 = (const float*)R[(i - 3) % 4];
+  const float* r1 = (const float*)R[(i - 2) % 4];
+  const float* r2 = (const float*)R[(i - 1) % 4];
+  const float* g0 = (const float*)Gr[(i - 3) % 4];
+  const float* g1 = (const float*)Gr[(i - 2) % 4];
+  const float* g2 = (const float*)Gr[(i - 1) % 4];
+  for (long long e = t0; e < n4; e += stride) {
+    const float4 q0 = ((const float4*)p0)[e], q1 = ((const float4*)p1)[e], q2 = ((const float4*)p2)[e],
+                 q3 = ((const float4*)p3)[e];
+    const float4 s0 = ((const float4*)r0)[e], s1 = ((const float4*)r1)[e], s2 = ((const float4*)r2)[e];
+    const float4 h0 = ((const float4*)g0)[e], h1 = ((const float4*)g1)[e], h2 = ((const float4*)g2)[e];
+    float4 v;
+    v.x = acv_combine(q0.x, q1.x, q2.x, q3.x, s0.x, s1.x, s2.x, h0.x, h1.x, h2.x, a0, a1, a2, a3, b0, b1, b2);
+    v.y = acv_combine(q0.y, q1.y, q2.y, q3.y, s0.y, s1.y, s2.y, h0.y, h1.y, h2.y, a0, a1, a2, a3, b0, b1, b2);
+    v.z = acv_combine(q0.z, q1.z, q2.z, q3.z, s0.z, s1.z, s2.z, h0.z, h1.z, h2.z, a0, a1, a2, a3, b0, b1, b2);
+    v.w = acv_combine(q0.w, q1.w, q2.w, q3.w, s0.w, s1.w, s2.w, h0.w, h1.w, h2.w, a0, a1, a2, a3, b0, b1, b2);
+    ((float4*)gi)[e] = v;
+  }
+  for (long long e = 4 * n4 + t0; e < total; e += stride)
+    gi[e] = acv_combine(p0[e], p1[e], p2[e], p3[e], r0[e], r1[e], r2[e], g0[e], g1[e], g2[e], a0, a1, a2, a3, b0, b1,
+                        b2);
+}
+
 template <typename T>
 int launch_acv_green_input(const GridDev& g, void* const* pring, void* const* gring, void* const* rring,
                            const Ctrl* ctrl, cudaStream_t s) {
   long long total = 3 * g.nnodes;
-  k_acv_green_input<T><<<acv_blocks(g), SB, 0, s>>>(total, pring, gring, rring, ctrl);
+  if constexpr (sizeof(T) == 4)
+    k_acv_green_input_v4<<<acv_blocks(g), SB, 0, s>>>(total, pring, gring, rring, ctrl);
+  else
+    k_acv_green_input<T><<<acv_blocks(g), SB, 0, s>>>(total, pring, gring, rring, ctrl);
   return (int)cudaGetLastError();
 }
 
