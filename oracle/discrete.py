@@ -15,6 +15,8 @@ Paper passages followed:
                 grad_d u = (1/(2h)) sum_{delta in T} s_d u(delta), weight 1/2 each;
         HEX1:   grad_d u = (1/(4h)) sum_{all 8} s_d u(delta), weight 1.
   * Eq. 3: sigma = C : (eps* + sym grad_D u~), p = div_D(sigma - R0 : grad_D u~).
+    Finite strain (Section 5.2, Eq. 29): sigma is replaced by the first Piola-Kirchhoff
+    stress Pi (function piola); the reference term is unchanged.
     div_D is the discrete divergence at nodes, the negative adjoint of grad_D; it is
     computed here as  p = -F / (h^3 W)  with F = dE/du~ the finite-element nodal force of
     the real cell and W the symmetry weight below.
@@ -180,6 +182,32 @@ def stress(pb, u):
     return sig
 
 
+def piola(pb, u):
+    """First Piola-Kirchhoff stress at the integration points (finite strain, Section 5.2).
+
+    Eq. 29 replaces sigma by Pi = F(F~) with F~ = 1 + grad_D u; the behaviour used is the
+    example given right after Eq. 29 (and in Section 5.4): S = C : E with the per-phase
+    isotropic C, E = (F^T F - 1) / 2 the Green-Lagrange strain, Pi = F . S.  The prescribed
+    load eps* enters as an imposed displacement gradient (u* = eps* . x, as in small strain),
+    so F = 1 + eps* + grad u~.  Returns Pi[t, c, d] (n_ip, 3, 3, voxels); Pi[t, c, d] is
+    the derivative of the strain energy density with respect to grad_d u_c, so it pairs
+    with grad u in nodal_force exactly as sigma does.
+    """
+    g = gradients(pb, u)
+    F = g + pb.eps_star[None, :, :, None, None, None]
+    for a in range(3):
+        F[:, a, a] += 1.0
+    E = 0.5 * np.einsum("tkazyx,tkbzyx->tabzyx", F, F)
+    for a in range(3):
+        E[:, a, a] -= 0.5
+    lam, mu = pb.material()
+    tr = E[:, 0, 0] + E[:, 1, 1] + E[:, 2, 2]
+    S = 2.0 * mu * E
+    for a in range(3):
+        S[:, a, a] += lam * tr
+    return np.einsum("tckzyx,tkdzyx->tcdzyx", F, S)
+
+
 def nodal_force(pb, tau):
     """F_c(node) = sum_voxels sum_t w_t h^3 sum_d tau[t, c, d] * d(grad_d u_c)/d u_c(node).
 
@@ -208,9 +236,10 @@ def div_from_force(pb, F):
     return p
 
 
-def residual(pb, u):
-    """Eq. 3 first two lines: (p, sigma) for the current fluctuation u (3, nodes)."""
-    sig = stress(pb, u)
+def residual(pb, u, kinematics="SS"):
+    """Eq. 3 first two lines: (p, sigma) for the current fluctuation u (3, nodes).
+    kinematics "FS": Eq. 29, the stress and divergence steps of Algorithm 3: p = div_D(Pi), returned with Pi."""
+    sig = piola(pb, u) if kinematics == "FS" else stress(pb, u)
     return div_from_force(pb, nodal_force(pb, sig)), sig
 
 
@@ -270,7 +299,8 @@ def green_apply(pb, ptilde, lam0, mu0):
 
 
 def residual_norm(pb, p, sig):
-    """Eq. 5 with RMS norms: r = h ||p||_rms / ||sigma||_rms.
+    """Eq. 5 with RMS norms: r = h ||p||_rms / ||sigma||_rms (||Pi||_rms in finite strain:
+    the stress that p is the divergence of).
 
     ||p||_rms^2 = sum_nodes sum_c p_c^2 / N_nodes;
     ||sigma||_rms^2 = sum_voxels sum_t w_t sum_ab sigma_ab^2 / N_voxels.

@@ -1,6 +1,8 @@
 """Oracle: Anderson convergence acceleration and the fixed-point solvers of
 Algorithm 1 (local Dirichlet / linear constraints) and Algorithm 2 (frictionless
-sphere contact, small strain).
+sphere contact, small strain); with kinematics="FS" the same loops are Algorithm 3 (and
+its Algorithm 1 counterpart): Pi replaces sigma in the divergence, in the Eq. 5 norm and
+in the contact reaction, nothing else changes (Section 5.2).
 
 Test infrastructure only (see oracle/__init__.py).  Plain float64 numpy, the steps in
 the paper's order.
@@ -86,7 +88,7 @@ class Result:
 
 
 def solve_alg1(pb, rows, lam0, mu0, tol, max_iter, acv_on="P", acv_mod=3, u0=None,
-               acv=True):
+               acv=True, kinematics="SS"):
     """Algorithm 1 (Section 4.1.1).  Returns a Result with u, p, sigma, multipliers,
     iterations, residual history."""
     cs.check_rows(pb, rows)
@@ -102,7 +104,7 @@ def solve_alg1(pb, rows, lam0, mu0, tol, max_iter, acv_on="P", acv_mod=3, u0=Non
     while True:
         if acv and acv_on == "U":
             u = ander.step(i, u)
-        p, sig = dz.residual(pb, u)
+        p, sig = dz.residual(pb, u, kinematics)
         f = cs.proj_P(pb, p, rows)
         r = dz.residual_norm(pb, p, sig)
         hist.append(r)
@@ -125,7 +127,7 @@ def solve_alg1(pb, rows, lam0, mu0, tol, max_iter, acv_on="P", acv_mod=3, u0=Non
 
 
 def solve_alg2_increment(pb, ind, rows, lam0, mu0, tol, max_iter, u_prev, acv_on="P",
-                         acv_mod=3, update_tol=1e-2):
+                         acv_mod=3, update_tol=1e-2, kinematics="SS"):
     """One load increment of Algorithm 2 (Section 5.1.3); ind.center is the moved
     sphere centre O'_s.  u_prev is u~ at the end of the previous increment."""
     cs.check_rows(pb, rows)
@@ -144,7 +146,7 @@ def solve_alg2_increment(pb, ind, rows, lam0, mu0, tol, max_iter, u_prev, acv_on
     while True:
         if acv_on == "U":
             u = ander.step(i, u)
-        p, sig = dz.residual(pb, u)
+        p, sig = dz.residual(pb, u, kinematics)
         f_rows = cs.proj_P(pb, p, rows)
         g, _ = cs.contact_geometry(pb, ind, u)
         fn, _ = cs.contact_proj_P(pb, ind, u, p, active)
@@ -183,6 +185,7 @@ def solve_alg2_increment(pb, ind, rows, lam0, mu0, tol, max_iter, u_prev, acv_on
 
 
 def mean_stress(pb, sig):
-    """Volume average of sigma over the cell: sum_vox sum_t w_t sigma / N_vox."""
+    """Volume average of sigma (or Pi) over the cell: sum_vox sum_t w_t sigma / N_vox
+    (Section 5.4 takes the reaction force from it)."""
     w = np.array([ip[0] for ip in pb.ip_sets()])
     return np.einsum("t,tabzyx->ab", w, sig) / float(np.prod(pb.vox_shape))
