@@ -56,6 +56,7 @@ enum { DTT_SCHEME_TETRA2 = 0, DTT_SCHEME_HEX1 = 1 };
 enum { DTT_PREC_FP64 = 0, DTT_PREC_MIXED = 1 };
 enum { DTT_INIT_ZERO = 0, DTT_INIT_PREVIOUS = 1, DTT_INIT_GUESS = 2 };
 enum { DTT_ACV_U = 0, DTT_ACV_P = 1 };
+enum { DTT_SMALL_STRAIN = 0, DTT_FINITE_STRAIN = 1 };
 
 /* Create a grid (Section 3.2.1 problem statement: cell, per-face per-component BCs, FD
  * scheme of Section 3.1.1).  precision: DTT_PREC_FP64 = every nodal field and every
@@ -81,8 +82,18 @@ dtt_status dtt_set_material(dtt_grid* grid, const uint8_t* phase, int32_t nphase
  * R0 : grad u = lambda0 (grad u (.) I) + 2 mu0 grad u.  Requires mu0 > 0, lambda0 >= 0. */
 dtt_status dtt_set_reference(dtt_grid* grid, double lambda0, double mu0);
 
-/* Prescribed strain eps* (3x3 row-major, symmetric part used), Eq. 1. */
+/* Prescribed strain eps* (3x3 row-major, symmetric part used), Eq. 1.  In finite strain
+ * it is the prescribed displacement gradient: F = 1 + eps* + grad u~. */
 dtt_status dtt_set_load(dtt_grid* grid, const double eps_star[9]);
+
+/* Kinematics of the stress step (Section 5.2, Eq. 29, Algorithm 3).  DTT_SMALL_STRAIN
+ * (default): sigma = C : (eps* + sym grad u~).  DTT_FINITE_STRAIN: the divergence acts on
+ * the first Piola-Kirchhoff stress Pi = F.S of a St Venant-Kirchhoff material (the
+ * paper's example law: S = C : E, E = (F^T F - 1)/2, F = 1 + eps* + grad u~); Pi also
+ * replaces sigma in the Eq. 5 norm and in the contact reaction.  The Green operator, the
+ * projections and the contact logic are unchanged.  Other values: DTT_ERR_ARG.  A change
+ * invalidates the captured iteration graph. */
+dtt_status dtt_set_kinematics(dtt_grid* grid, int32_t kinematics);
 
 /* Local kinematic constraints as rows of the matrices A and B (Section 4.3, Eq. 20-23).
  * Row r has entries e in [row_ptr[r], row_ptr[r+1]): DOF (node[e], comp[e]) with
@@ -152,8 +163,16 @@ dtt_status dtt_solve_step(dtt_grid* grid, const dtt_solve_opts* opts, dtt_report
 dtt_status dtt_get_history(const dtt_grid* grid, double* hist, int32_t* n);
 
 /* u~ (3 x n_nodes, float64) and optionally the stress at the integration points
- * (sigma: n_voxels x n_ip x 6, order xx yy zz yz xz xy; n_ip = 2 TETRA2, 1 HEX1). */
+ * (sigma: n_voxels x n_ip x 6, order xx yy zz yz xz xy; n_ip = 2 TETRA2, 1 HEX1): the
+ * Cauchy stress in small strain, the second Piola-Kirchhoff stress S in finite strain. */
 dtt_status dtt_get_fields(dtt_grid* grid, double* u, double* sigma, int32_t ptr_is_device);
+
+/* The stress that the divergence acts on, at the integration points, all nine values
+ * (tensor: n_voxels x n_ip x 9, row c, column d, float64, caller-owned, host or device):
+ * sigma in small strain, the first Piola-Kirchhoff Pi = F.S in finite strain (Section 5.2;
+ * Section 5.4 takes the reaction force from its volume average).  DTT_ERR_STATE without
+ * a material. */
+dtt_status dtt_get_stress_tensor(dtt_grid* grid, double* tensor, int32_t ptr_is_device);
 
 /* Reactions of the constraint rows after the last solve: per_row[r] = h^3 f_r
  * sum_e W_e b_e (face DOFs halved, edge DOFs quartered, Section 4.1.3), f_r the

@@ -8,11 +8,13 @@ CUDA product path never calls it and shares no code with it.
 Modules:
   transforms   -- DCT1/DCT3/DST1/DST3/DFT as naive O(n^2) trigonometric sums
                   (Section 3.2.2, Tables 2-3, Eq. 7)
-  discrete     -- grid, BCs, HEX1/TETRA2 operators, stress, divergence, Paux R0 and its
-                  symbol, Green step, Eq. 5 residual (Sections 3.1-3.2)
+  discrete     -- grid, BCs, HEX1/TETRA2 operators, stress (small strain) and first
+                  Piola-Kirchhoff stress (finite strain, Section 5.2), divergence, Paux R0
+                  and its symbol, Green step, Eq. 5 residual (Sections 3.1-3.2)
   constraints  -- strong / weak / smooth / tie rows, proj_U and proj_P, reactions,
                   sphere-contact geometry (Sections 4.1-4.2, 5.1)
-  solver       -- Anderson acceleration, Algorithm 1, Algorithm 2
+  solver       -- Anderson acceleration, Algorithm 1, Algorithm 2 (Algorithm 3 with
+                  kinematics="FS")
   kkt          -- element-by-element stiffness and dense multiplier solve (Section 4.3)
   hertz        -- Eq. 30
 

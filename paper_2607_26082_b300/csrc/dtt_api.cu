@@ -1224,30 +1224,69 @@ dtt_status dtt_get_history(const dtt_grid* G, double* hist, int32_t* n) {
   return DTT_OK;
 }
 
+// Stress at the integration points into `out` (n_voxels x n_ip x ncomp), ncomp 6 or 9.
+static dtt_status stress_to(dtt_grid* G, const double* src, double* out, int full, int32_t ptr_is_device) {
+  cudaStream_t s = G->stream;
+  if (!G->mat_set) return fail(DTT_ERR_STATE, "material not set");
+  size_t ns = (size_t)G->NV * kIP[G->g.scheme] * (full ? 9 : 6);
+  double* buf = nullptr;
+  dtt_status st = dalloc(&buf, ns * sizeof(double));
+  if (st != DTT_OK) return st;
+  int rc = launch_stress_out(G->g, src, G->phase, G->d_lam, G->d_mu, G->eps, full, buf, s);
+  if (rc) { dfree(buf); return fail(DTT_ERR_CUDA, "stress kernel launch"); }
+  cudaError_t e = cudaMemcpyAsync(out, buf, ns * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  dfree(buf);
+  if (e != cudaSuccess) return fail(DTT_ERR_CUDA, cudaGetErrorString(e));
+  return DTT_OK;
+}
+
+// u~ as float64 on the device (the mixed path joins its float-float pair into op_d).
+static dtt_status u_f64(dtt_grid* G, const double** src) {
+  *src = G->u64;
+  if (!*src) {
+    CKL(launch_join((long long)(3 * G->NN), G->uhi, G->ulo, G->op_d, G->stream));
+    *src = G->op_d;
+  }
+  return DTT_OK;
+}
+
 dtt_status dtt_get_fields(dtt_grid* G, double* u, double* sigma, int32_t ptr_is_device) {
   if (!G) return fail(DTT_ERR_ARG, "null grid");
   const size_t n3 = (size_t)(3 * G->NN);
   cudaStream_t s = G->stream;
-  const double* src = G->u64;
-  if (!src) {
-    CKL(launch_join((long long)n3, G->uhi, G->ulo, G->op_d, s));
-    src = G->op_d;
-  }
+  const double* src = nullptr;
+  dtt_status st = u_f64(G, &src);
+  if (st != DTT_OK) return st;
   if (u) CK(cudaMemcpyAsync(u, src, n3 * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   if (sigma) {
-    if (!G->mat_set) return fail(DTT_ERR_STATE, "material not set");
-    size_t ns = (size_t)G->NV * kIP[G->g.scheme] * 6;
-    double* buf = nullptr;
-    dtt_status st = dalloc(&buf, ns * sizeof(double));
+    st = stress_to(G, src, sigma, 0, ptr_is_device);
     if (st != DTT_OK) return st;
-    int rc = launch_stress_out(G->g, src, G->phase, G->d_lam, G->d_mu, G->eps, buf, s);
-    if (rc) { dfree(buf); return fail(DTT_ERR_CUDA, "stress kernel launch"); }
-    cudaError_t e = cudaMemcpyAsync(sigma, buf, ns * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    dfree(buf);
-    if (e != cudaSuccess) return fail(DTT_ERR_CUDA, cudaGetErrorString(e));
   }
   CK(cudaStreamSynchronize(s));
+  return DTT_OK;
+}
+
+dtt_status dtt_get_stress_tensor(dtt_grid* G, double* tensor, int32_t ptr_is_device) {
+  if (!G || !tensor) return fail(DTT_ERR_ARG, "null argument");
+  const double* src = nullptr;
+  dtt_status st = u_f64(G, &src);
+  if (st != DTT_OK) return st;
+  st = stress_to(G, src, tensor, 1, ptr_is_device);
+  if (st != DTT_OK) return st;
+  CK(cudaStreamSynchronize(G->stream));
+  return DTT_OK;
+}
+
+dtt_status dtt_set_kinematics(dtt_grid* G, int32_t kinematics) {
+  if (!G) return fail(DTT_ERR_ARG, "null grid");
+  if (kinematics != DTT_SMALL_STRAIN && kinematics != DTT_FINITE_STRAIN)
+    return fail(DTT_ERR_ARG, "kinematics must be DTT_SMALL_STRAIN or DTT_FINITE_STRAIN");
+  const int fs = kinematics == DTT_FINITE_STRAIN;
+  if (G->g.finite_strain != fs) {
+    G->g.finite_strain = fs;
+    invalidate_graph(G);
+  }
   return DTT_OK;
 }
 

@@ -32,6 +32,7 @@ struct GridDev {
   int periodic[3];
   int zc_override;   // residual kernels: node planes per CTA (0: built-in choice)
   int fft_generic;   // 1: generic Stockham kernels for every length
+  int finite_strain; // 1: first Piola-Kirchhoff stress (Section 5.2), 0: small strain
 };
 
 // Solver state kept on the device so that a whole iteration is a fixed sequence of
@@ -310,6 +311,6 @@ int launch_from_double(long long n, const double* in, void* out, int out_is_floa
 int launch_split(long long n, const double* in, float* hi, float* lo, cudaStream_t s);
 int launch_join(long long n, const float* hi, const float* lo, double* out, cudaStream_t s);
 int launch_stress_out(const GridDev& g, const double* u, const uint8_t* phase, const double* lam,
-                      const double* mu, const double eps[3][3], double* out, cudaStream_t s);
+                      const double* mu, const double eps[3][3], int full, double* out, cudaStream_t s);
 
 }  // namespace dtt

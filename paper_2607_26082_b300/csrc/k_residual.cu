@@ -13,6 +13,12 @@
 // The Paux reference medium (Section 3.2.3) R0 : grad u = lambda0 (grad u (.) I)
 // + 2 mu0 grad u enters through tau0_cd = (2 mu0 + lambda0 delta_cd) grad_d u_c.
 //
+// Finite strain (FS = true; Section 5.2, Eq. 29): the divergence acts on the first
+// Piola-Kirchhoff stress Pi = F.S of a St Venant-Kirchhoff material, S = C : E with
+// E = (F^T F - 1) / 2 formed as (H + H^T + H^T H) / 2, H = eps* + grad u~, F = 1 + H (the
+// same quantity without the cancellation of F^T F - 1 at small strain).  Pi is not
+// symmetric: 9 values per point, gathered row by row; the Eq. 5 norm takes Pi : Pi.
+//
 // Modes: 0 (operator) writes p and p~ = p + A0 u~; 2 writes p only; 1 (Anderson on p~ in
 // difference form) writes p into the p ring and, from the second iteration on, the
 // Anderson residual R_{i-1} = p_i - g_{i-1} + A0 Delta_{i-1} (Delta = last step of u~,
@@ -44,8 +50,8 @@ __device__ __forceinline__ float ndiff(const NodeV<true>& a, const NodeV<true>& 
   return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
 }
 
-template <typename T, int NIP> struct VoxV {
-  T sig[NIP][6];    // xx yy zz yz xz xy
+template <typename T, int NIP, int NS> struct VoxV {
+  T sig[NIP][NS];   // NS = 6: sigma xx yy zz yz xz xy; NS = 9: Pi row c, column d
   T tau[NIP][9];    // row c, column d
 };
 
@@ -73,16 +79,18 @@ __device__ __forceinline__ double node_invW(const GridDev& g, int c, int i, int 
   return invW;
 }
 
-template <typename T, bool MIX, int SCHEME>
+template <typename T, bool MIX, int SCHEME, bool FS>
 __global__ void __launch_bounds__(RTX * RTY)
 k_residual(ResidualArgs a) {
   constexpr int NIP = (SCHEME == SCHEME_TETRA2) ? 2 : 1;
+  constexpr int NS = FS ? 9 : 6;
+  using Vox = VoxV<T, NIP, NS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sLam = (double*)smem_raw;
   double* sMu = sLam + MAX_PHASE;
   double (*sRed)[RTX * RTY / 32] = (double (*)[RTX * RTY / 32])(sMu + MAX_PHASE);
-  VoxV<T, NIP> (*sV)[VY][VX] = (VoxV<T, NIP> (*)[VY][VX])(smem_raw + 2 * MAX_PHASE * 8 + 2 * (RTX * RTY / 32) * 8);
-  NodeV<MIX> (*sU)[3][NY2][NX2] = (NodeV<MIX> (*)[3][NY2][NX2])((unsigned char*)sV + 2 * VY * VX * sizeof(VoxV<T, NIP>));
+  Vox (*sV)[VY][VX] = (Vox (*)[VY][VX])(smem_raw + 2 * MAX_PHASE * 8 + 2 * (RTX * RTY / 32) * 8);
+  NodeV<MIX> (*sU)[3][NY2][NX2] = (NodeV<MIX> (*)[3][NY2][NX2])((unsigned char*)sV + 2 * VY * VX * sizeof(Vox));
   T (*sD)[3][NY2][NX2] = (T (*)[3][NY2][NX2])((unsigned char*)sU + 2 * 3 * NY2 * NX2 * sizeof(NodeV<MIX>));
 
   const GridDev& g = a.g;
@@ -163,7 +171,7 @@ k_residual(ResidualArgs a) {
       int vx = x0 - 1 + lx, vy = y0 - 1 + ly;
       int vxw = wrap_or_neg(vx, g.nvox[0], g.periodic[0]);
       int vyw = wrap_or_neg(vy, g.nvox[1], g.periodic[1]);
-      VoxV<T, NIP>& V = sV[vs][ly][lx];
+      Vox& V = sV[vs][ly][lx];
       if (vxw < 0 || vyw < 0 || vzw < 0 || !tau_on) {
         #pragma unroll
         for (int t = 0; t < NIP; ++t)
@@ -174,7 +182,7 @@ k_residual(ResidualArgs a) {
         #pragma unroll
         for (int t = 0; t < NIP; ++t) {
           #pragma unroll
-          for (int e = 0; e < 6; ++e) V.sig[t][e] = (T)0;
+          for (int e = 0; e < NS; ++e) V.sig[t][e] = (T)0;
           #pragma unroll
           for (int e = 0; e < 9; ++e) V.tau[t][e] = (T)0;
         }
@@ -224,6 +232,47 @@ k_residual(ResidualArgs a) {
                  vx < g.nvox[0] && vy < g.nvox[1];
       #pragma unroll
       for (int t = 0; t < NIP; ++t) {
+        if constexpr (FS) {
+          T H[3][3], E[3][3], S[3][3];
+          #pragma unroll
+          for (int c = 0; c < 3; ++c)
+            #pragma unroll
+            for (int d = 0; d < 3; ++d) H[c][d] = eps[c][d] + G[t][c][d];
+          #pragma unroll
+          for (int p = 0; p < 3; ++p)
+            #pragma unroll
+            for (int q = p; q < 3; ++q) {
+              T v = H[p][q] + H[q][p];
+              #pragma unroll
+              for (int k = 0; k < 3; ++k) v += H[k][p] * H[k][q];
+              E[p][q] = E[q][p] = (T)0.5 * v;
+            }
+          const T tr = E[0][0] + E[1][1] + E[2][2];
+          #pragma unroll
+          for (int p = 0; p < 3; ++p)
+            #pragma unroll
+            for (int q = 0; q < 3; ++q) S[p][q] = (T)2 * mu * E[p][q] + (p == q ? lam * tr : (T)0);
+          double s2 = 0.0;
+          #pragma unroll
+          for (int c = 0; c < 3; ++c)
+            #pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              T v = S[c][d];
+              #pragma unroll
+              for (int k = 0; k < 3; ++k) v += H[c][k] * S[k][d];
+              V.sig[t][3 * c + d] = v;
+              s2 += (double)v * v;
+            }
+          if (tau_on && !dfield) {
+            #pragma unroll
+            for (int c = 0; c < 3; ++c)
+              #pragma unroll
+              for (int d = 0; d < 3; ++d)
+                V.tau[t][3 * c + d] = ((T)2 * mu0 + (c == d ? lam0 : (T)0)) * G[t][c][d];
+          }
+          if (own) acc_s2 += ((NIP == 2) ? 0.5 : 1.0) * s2;
+          continue;
+        }
         T exx = eps[0][0] + G[t][0][0], eyy = eps[1][1] + G[t][1][1], ezz = eps[2][2] + G[t][2][2];
         T eyz = eps[1][2] + (T)0.5 * (G[t][1][2] + G[t][2][1]);
         T exz = eps[0][2] + (T)0.5 * (G[t][0][2] + G[t][2][0]);
@@ -311,15 +360,21 @@ k_residual(ResidualArgs a) {
           #pragma unroll
           for (int ex = 0; ex < 2; ++ex) {
             // voxel with lower corner (i-1+ex, j-1+ey, k-1+ez): local (tx+ex, ty+ey)
-            const VoxV<T, NIP>& V = sV[vs][ty + ey][tx + ex];
+            const Vox& V = sV[vs][ty + ey][tx + ex];
             // node is corner delta = (1-ex, 1-ey, 1-ez) of that voxel
             const int dx = 1 - ex, dy = 1 - ey, dzc = 1 - ez;
             const T sx = dx ? (T)1 : (T)-1, sy = dy ? (T)1 : (T)-1, sz = dzc ? (T)1 : (T)-1;
             const int t = (NIP == 2) ? ((dx + dy + dzc) & 1) : 0;
-            // sigma rows: x: (xx, xy, xz), y: (xy, yy, yz), z: (xz, yz, zz)
-            Fs[0] += V.sig[t][0] * sx + V.sig[t][5] * sy + V.sig[t][4] * sz;
-            Fs[1] += V.sig[t][5] * sx + V.sig[t][1] * sy + V.sig[t][3] * sz;
-            Fs[2] += V.sig[t][4] * sx + V.sig[t][3] * sy + V.sig[t][2] * sz;
+            if constexpr (FS) {
+              #pragma unroll
+              for (int c = 0; c < 3; ++c)
+                Fs[c] += V.sig[t][3 * c] * sx + V.sig[t][3 * c + 1] * sy + V.sig[t][3 * c + 2] * sz;
+            } else {
+              // sigma rows: x: (xx, xy, xz), y: (xy, yy, yz), z: (xz, yz, zz)
+              Fs[0] += V.sig[t][0] * sx + V.sig[t][5] * sy + V.sig[t][4] * sz;
+              Fs[1] += V.sig[t][5] * sx + V.sig[t][1] * sy + V.sig[t][3] * sz;
+              Fs[2] += V.sig[t][4] * sx + V.sig[t][3] * sy + V.sig[t][2] * sz;
+            }
             #pragma unroll
             for (int c = 0; c < 3; ++c)
               F0[c] += V.tau[t][3 * c] * sx + V.tau[t][3 * c + 1] * sy + V.tau[t][3 * c + 2] * sz;
@@ -390,29 +445,29 @@ int residual_blocks(const GridDev& g) {
   return bx * by * bz;
 }
 
-template <typename T, bool MIX, int SCHEME>
+template <typename T, bool MIX, int SCHEME, bool FS>
 static size_t residual_smem() {
   constexpr int NIP = (SCHEME == SCHEME_TETRA2) ? 2 : 1;
-  return 2 * MAX_PHASE * 8 + 2 * (RTX * RTY / 32) * 8 + 2 * VY * VX * sizeof(VoxV<T, NIP>) +
+  return 2 * MAX_PHASE * 8 + 2 * (RTX * RTY / 32) * 8 + 2 * VY * VX * sizeof(VoxV<T, NIP, FS ? 9 : 6>) +
          2 * 3 * NY2 * NX2 * sizeof(NodeV<MIX>) + 2 * 3 * NY2 * NX2 * sizeof(T);
 }
 
-template <typename T, bool MIX, int SCHEME>
+template <typename T, bool MIX, int SCHEME, bool FS>
 static int launch_res_impl(const ResidualArgs& a, cudaStream_t s) {
   dim3 blk(RTX, RTY);
   const int zc = residual_zchunk(a.g);
   dim3 grd((a.g.nn[0] + RTX - 1) / RTX, (a.g.nn[1] + RTY - 1) / RTY, (a.g.nn[2] + zc - 1) / zc);
   ResidualArgs aa = a;
   aa.zchunk = zc;
-  size_t sm = residual_smem<T, MIX, SCHEME>();
+  size_t sm = residual_smem<T, MIX, SCHEME, FS>();
   static bool attr_set = false;   // per template instance; the attribute is per function
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_residual<T, MIX, SCHEME>,
+    cudaError_t e = cudaFuncSetAttribute(k_residual<T, MIX, SCHEME, FS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
-  k_residual<T, MIX, SCHEME><<<grd, blk, sm, s>>>(aa);
+  k_residual<T, MIX, SCHEME, FS><<<grd, blk, sm, s>>>(aa);
   return (int)cudaGetLastError();
 }
 
@@ -421,8 +476,10 @@ int launch_residual(const ResidualArgs& a, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
     return launch_residual_f32(a, s);   // thread-per-node FP32 kernel (k_residual_f32.cu)
   } else {
-    if (a.g.scheme == SCHEME_TETRA2) return launch_res_impl<T, false, SCHEME_TETRA2>(a, s);
-    return launch_res_impl<T, false, SCHEME_HEX1>(a, s);
+    const bool fs = a.g.finite_strain != 0;
+    if (a.g.scheme == SCHEME_TETRA2)
+      return fs ? launch_res_impl<T, false, SCHEME_TETRA2, true>(a, s) : launch_res_impl<T, false, SCHEME_TETRA2, false>(a, s);
+    return fs ? launch_res_impl<T, false, SCHEME_HEX1, true>(a, s) : launch_res_impl<T, false, SCHEME_HEX1, false>(a, s);
   }
 }
 

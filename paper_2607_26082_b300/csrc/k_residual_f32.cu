@@ -19,6 +19,10 @@
 //    ones after they have shifted R_{i-1};
 //  * no FP64 arithmetic inside the march: per-thread sums are compensated FP32 pairs
 //    (TwoSum), converted to FP64 once per thread before the block reduction.
+// Finite strain (FS = true, Section 5.2): phase A stores the 9 values of the first
+// Piola-Kirchhoff stress Pi = F.S (St Venant-Kirchhoff, E = (H + H^T + H^T H) / 2 with
+// H = eps* + grad u~, F = 1 + H, S = C : E) in place of sigma's 6, and phase B gathers
+// its rows; the norm takes Pi : Pi.
 // Partial sums per CTA (FP64): [sum w sigma:sigma, sum p^2, Gram 0..3].
 #include "dtt_internal.cuh"
 
@@ -33,7 +37,10 @@ constexpr int FTHREADS = 320;                    // >= NVL, multiple of 32
 constexpr int FNP = 3;                           // node-plane ring slots
 constexpr int FHX = FTX + 2, FHY = FTY + 2;      // node plane with halo (x0-1 .. x0+32)
 constexpr int FPLANE = 3 * FHY * FHX;            // floats per plane (3 components)
-constexpr int QV = 15;                           // per point: sigma 6 + tau 9
+template <bool FS> struct PointLayout {
+  static constexpr int NS = FS ? 9 : 6;          // stress values per point (Pi or sigma)
+  static constexpr int QV = NS + 9;              // plus tau 9
+};
 
 __device__ __forceinline__ void cp_async4(void* smem_ptr, const void* gptr) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_ptr);
@@ -70,10 +77,11 @@ __device__ __forceinline__ float fdiff(float ph, float pl, float qh, float ql) {
 
 }  // namespace
 
-template <int SCHEME>
+template <int SCHEME, bool FS>
 __global__ void __launch_bounds__(FTHREADS, 2)
 k_residual_f32(ResidualArgs a) {
   constexpr int NPT = (SCHEME == SCHEME_TETRA2) ? 2 : 1;
+  constexpr int NS = PointLayout<FS>::NS, QV = PointLayout<FS>::QV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sH = (float*)smem_raw;                 // [FNP][3][FHY][FHX] u~ hi
   float* sL = sH + FNP * FPLANE;                // u~ lo
@@ -288,6 +296,49 @@ k_residual_f32(ResidualArgs a) {
               GD[c][2] = ((ud[4] - ud[0]) + (ud[5] - ud[1]) + (ud[6] - ud[2]) + (ud[7] - ud[3])) * inv4h;
             }
           }
+          float* o = out + t * QV * NVL;
+          if constexpr (FS) {
+            float H[3][3], S[3][3];
+            #pragma unroll
+            for (int c = 0; c < 3; ++c)
+              #pragma unroll
+              for (int dd = 0; dd < 3; ++dd) H[c][dd] = eps[c][dd] + G[c][dd];
+            #pragma unroll
+            for (int p = 0; p < 3; ++p)
+              #pragma unroll
+              for (int q = p; q < 3; ++q) {
+                float v = H[p][q] + H[q][p];
+                #pragma unroll
+                for (int k = 0; k < 3; ++k) v = fmaf(H[k][p], H[k][q], v);
+                S[p][q] = S[q][p] = 0.5f * v;   // E for now
+              }
+            const float tr = S[0][0] + S[1][1] + S[2][2];
+            #pragma unroll
+            for (int p = 0; p < 3; ++p)
+              #pragma unroll
+              for (int q = p; q < 3; ++q) S[p][q] = S[q][p] = 2.f * mu * S[p][q] + (p == q ? lam * tr : 0.f);
+            float s2 = 0.f;
+            #pragma unroll
+            for (int c = 0; c < 3; ++c)
+              #pragma unroll
+              for (int dd = 0; dd < 3; ++dd) {
+                float v = S[c][dd];
+                #pragma unroll
+                for (int k = 0; k < 3; ++k) v = fmaf(H[c][k], S[k][dd], v);
+                o[(3 * c + dd) * NVL] = v;
+                s2 = fmaf(v, v, s2);
+              }
+            if (tau_on) {
+              #pragma unroll
+              for (int c = 0; c < 3; ++c)
+                #pragma unroll
+                for (int dd = 0; dd < 3; ++dd)
+                  o[(NS + 3 * c + dd) * NVL] =
+                      (2.f * mu0 + (c == dd ? lam0 : 0.f)) * (tau_from_delta ? GD[c][dd] : G[c][dd]);
+            }
+            if (own) acc_s2.add(w * s2);
+            continue;
+          }
           const float exx = eps[0][0] + G[0][0], eyy = eps[1][1] + G[1][1];
           const float ezz = eps[2][2] + G[2][2];
           const float eyz = eps[1][2] + 0.5f * (G[1][2] + G[2][1]);
@@ -297,7 +348,6 @@ k_residual_f32(ResidualArgs a) {
           const float sxx = lam * tr + 2.f * mu * exx, syy = lam * tr + 2.f * mu * eyy;
           const float szz = lam * tr + 2.f * mu * ezz;
           const float syz = 2.f * mu * eyz, sxz = 2.f * mu * exz, sxy = 2.f * mu * exy;
-          float* o = out + t * QV * NVL;
           o[0 * NVL] = sxx;
           o[1 * NVL] = syy;
           o[2 * NVL] = szz;
@@ -309,7 +359,7 @@ k_residual_f32(ResidualArgs a) {
             for (int c = 0; c < 3; ++c)
               #pragma unroll
               for (int dd = 0; dd < 3; ++dd)
-                o[(6 + 3 * c + dd) * NVL] =
+                o[(NS + 3 * c + dd) * NVL] =
                     (2.f * mu0 + (c == dd ? lam0 : 0.f)) * (tau_from_delta ? GD[c][dd] : G[c][dd]);
           }
           if (own) acc_s2.add(w * (sxx * sxx + syy * syy + szz * szz + 2.f * (syz * syz + sxz * sxz + sxy * sxy)));
@@ -333,15 +383,21 @@ k_residual_f32(ResidualArgs a) {
           const int thi = (SCHEME == SCHEME_TETRA2) ? (1 - tlo) : 0;
           auto gather = [&](float (&F)[3], float (&F0)[3], int t, float sz) {
             const float* q = sV + t * QV * NVL + v;
-            const float sxx = q[0], syy = q[NVL], szz = q[2 * NVL];
-            const float syz = q[3 * NVL], sxz = q[4 * NVL], sxy = q[5 * NVL];
-            F[0] += sxx * sx + sxy * sy + sxz * sz;
-            F[1] += sxy * sx + syy * sy + syz * sz;
-            F[2] += sxz * sx + syz * sy + szz * sz;
+            if constexpr (FS) {
+              #pragma unroll
+              for (int c = 0; c < 3; ++c)
+                F[c] += q[(3 * c) * NVL] * sx + q[(3 * c + 1) * NVL] * sy + q[(3 * c + 2) * NVL] * sz;
+            } else {
+              const float sxx = q[0], syy = q[NVL], szz = q[2 * NVL];
+              const float syz = q[3 * NVL], sxz = q[4 * NVL], sxy = q[5 * NVL];
+              F[0] += sxx * sx + sxy * sy + sxz * sz;
+              F[1] += sxy * sx + syy * sy + syz * sz;
+              F[2] += sxz * sx + syz * sy + szz * sz;
+            }
             if (tau_on) {
               #pragma unroll
               for (int c = 0; c < 3; ++c)
-                F0[c] += q[(6 + 3 * c) * NVL] * sx + q[(7 + 3 * c) * NVL] * sy + q[(8 + 3 * c) * NVL] * sz;
+                F0[c] += q[(NS + 3 * c) * NVL] * sx + q[(NS + 1 + 3 * c) * NVL] * sy + q[(NS + 2 + 3 * c) * NVL] * sz;
             }
           };
           gather(Fc, F0c, tlo, -1.f);
@@ -465,7 +521,7 @@ int residual_f32_blocks(const GridDev& g) {
   return ((g.nn[0] + FTX - 1) / FTX) * ((g.nn[1] + FTY - 1) / FTY) * ((g.nn[2] + zc - 1) / zc);
 }
 
-template <int SCHEME>
+template <int SCHEME, bool FS>
 static int launch_f32_impl(const ResidualArgs& a, cudaStream_t s) {
   const int zc = residual_f32_zchunk(a.g);
   dim3 grd((a.g.nn[0] + FTX - 1) / FTX, (a.g.nn[1] + FTY - 1) / FTY, (a.g.nn[2] + zc - 1) / zc);
@@ -478,21 +534,24 @@ static int launch_f32_impl(const ResidualArgs& a, cudaStream_t s) {
   aa.f_inv2h = (float)(1.0 / (2.0 * a.g.h));
   aa.f_inv4h = (float)(1.0 / (4.0 * a.g.h));
   constexpr int NPT = (SCHEME == SCHEME_TETRA2) ? 2 : 1;
+  constexpr int QV = PointLayout<FS>::QV;
   const size_t sm = (size_t)3 * FNP * FPLANE * sizeof(float) + (size_t)NPT * QV * NVL * sizeof(float) +
                     (size_t)FNP * FHY * FHX;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_residual_f32<SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_residual_f32<SCHEME, FS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     attr = true;
   }
-  k_residual_f32<SCHEME><<<grd, FTHREADS, sm, s>>>(aa);
+  k_residual_f32<SCHEME, FS><<<grd, FTHREADS, sm, s>>>(aa);
   return (int)cudaGetLastError();
 }
 
 int launch_residual_f32(const ResidualArgs& a, cudaStream_t s) {
-  if (a.g.scheme == SCHEME_TETRA2) return launch_f32_impl<SCHEME_TETRA2>(a, s);
-  return launch_f32_impl<SCHEME_HEX1>(a, s);
+  const bool fs = a.g.finite_strain != 0;
+  if (a.g.scheme == SCHEME_TETRA2)
+    return fs ? launch_f32_impl<SCHEME_TETRA2, true>(a, s) : launch_f32_impl<SCHEME_TETRA2, false>(a, s);
+  return fs ? launch_f32_impl<SCHEME_HEX1, true>(a, s) : launch_f32_impl<SCHEME_HEX1, false>(a, s);
 }
 
 }  // namespace dtt

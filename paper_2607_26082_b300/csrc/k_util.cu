@@ -46,13 +46,18 @@ int launch_join(long long n, const float* hi, const float* lo, double* out, cuda
   return (int)cudaGetLastError();
 }
 
-// sigma at every integration point from a float64 u~ (3 x nnodes).
+// Stress at every integration point from a float64 u~ (3 x nnodes).  full = 0: the
+// symmetric tensor, 6 values (xx yy zz yz xz xy) -- sigma in small strain, the second
+// Piola-Kirchhoff S in finite strain; full = 1: the tensor paired with grad u, 9 values
+// row c, column d -- sigma, or the first Piola-Kirchhoff Pi = F.S (Section 5.2).
+struct Eps9 { double e[3][3]; };
+
 __global__ void k_stress_out(const GridDev g, const double* __restrict__ u, const uint8_t* __restrict__ phase,
-                             const double* __restrict__ lam, const double* __restrict__ mu, const double eps00,
-                             const double eps11, const double eps22, const double eps12, const double eps02,
-                             const double eps01, double* __restrict__ out) {
+                             const double* __restrict__ lam, const double* __restrict__ mu, const Eps9 eps, int full,
+                             double* __restrict__ out) {
   const long long NV = (long long)g.nvox[0] * g.nvox[1] * g.nvox[2];
   const int nip = g.scheme == SCHEME_TETRA2 ? 2 : 1;
+  const int nout = full ? 9 : 6;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < NV; v += (long long)gridDim.x * blockDim.x) {
     int vx = (int)(v % g.nvox[0]);
     long long r = v / g.nvox[0];
@@ -81,28 +86,49 @@ __global__ void k_stress_out(const GridDev g, const double* __restrict__ u, cons
         for (int c = 0; c < 3; ++c)
           for (int d = 0; d < 3; ++d) G[c][d] += coef * s[d] * U[c][q];
       }
-      double exx = eps00 + G[0][0], eyy = eps11 + G[1][1], ezz = eps22 + G[2][2];
-      double eyz = eps12 + 0.5 * (G[1][2] + G[2][1]);
-      double exz = eps02 + 0.5 * (G[0][2] + G[2][0]);
-      double exy = eps01 + 0.5 * (G[0][1] + G[1][0]);
-      double tr = exx + eyy + ezz;
-      double* o = out + (v * nip + t) * 6;
-      o[0] = L * tr + 2 * M * exx;
-      o[1] = L * tr + 2 * M * eyy;
-      o[2] = L * tr + 2 * M * ezz;
-      o[3] = 2 * M * eyz;
-      o[4] = 2 * M * exz;
-      o[5] = 2 * M * exy;
+      double H[3][3], E[3][3], S[3][3], P[3][3];
+      for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) H[c][d] = eps.e[c][d] + G[c][d];
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+          double e = 0.5 * (H[p][q] + H[q][p]);
+          if (g.finite_strain)
+            for (int k = 0; k < 3; ++k) e += 0.5 * H[k][p] * H[k][q];
+          E[p][q] = e;
+        }
+      const double tr = E[0][0] + E[1][1] + E[2][2];
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) S[p][q] = 2 * M * E[p][q] + (p == q ? L * tr : 0.0);
+      for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) {
+          double x = S[c][d];
+          if (g.finite_strain)
+            for (int k = 0; k < 3; ++k) x += H[c][k] * S[k][d];
+          P[c][d] = x;
+        }
+      double* o = out + (v * nip + t) * nout;
+      if (full) {
+        for (int c = 0; c < 3; ++c)
+          for (int d = 0; d < 3; ++d) o[3 * c + d] = P[c][d];
+      } else {
+        o[0] = S[0][0];
+        o[1] = S[1][1];
+        o[2] = S[2][2];
+        o[3] = S[1][2];
+        o[4] = S[0][2];
+        o[5] = S[0][1];
+      }
     }
   }
 }
 
 int launch_stress_out(const GridDev& g, const double* u, const uint8_t* phase, const double* lam,
-                      const double* mu, const double eps[3][3], double* out, cudaStream_t s) {
+                      const double* mu, const double eps[3][3], int full, double* out, cudaStream_t s) {
   long long NV = (long long)g.nvox[0] * g.nvox[1] * g.nvox[2];
-  k_stress_out<<<nblk(NV), 256, 0, s>>>(g, u, phase, lam, mu, eps[0][0], eps[1][1], eps[2][2],
-                                        0.5 * (eps[1][2] + eps[2][1]), 0.5 * (eps[0][2] + eps[2][0]),
-                                        0.5 * (eps[0][1] + eps[1][0]), out);
+  Eps9 e;
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) e.e[p][q] = eps[p][q];
+  k_stress_out<<<nblk(NV), 256, 0, s>>>(g, u, phase, lam, mu, e, full, out);
   return (int)cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ SCHEME_TETRA2, SCHEME_HEX1 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 INIT_ZERO, INIT_PREVIOUS, INIT_GUESS = 0, 1, 2
 ACV_U, ACV_P = 0, 1
+SMALL_STRAIN, FINITE_STRAIN = 0, 1
 
 
 class DttError(RuntimeError):
@@ -55,6 +56,7 @@ EXPORTS = ["dtt_grid_create", "dtt_grid_destroy", "dtt_grid_sizes", "dtt_set_mat
            "dtt_set_reference", "dtt_set_load", "dtt_set_constraints", "dtt_set_indenter",
            "dtt_move_indenter", "dtt_clear_indenter", "dtt_set_initial", "dtt_solve_step",
            "dtt_get_history", "dtt_get_fields", "dtt_get_reactions", "dtt_get_contact",
+           "dtt_set_kinematics", "dtt_get_stress_tensor",
            "dtt_apply_residual", "dtt_apply_green", "dtt_apply_green_noalloc", "dtt_transform",
            "dtt_profile_iteration", "dtt_autotune", "dtt_set_tuning", "dtt_batch_solve",
            "dtt_last_error", "dtt_version"]
@@ -87,6 +89,8 @@ def lib():
     L.dtt_solve_step.argtypes = [P, C.POINTER(SolveOpts), C.POINTER(Report)]
     L.dtt_get_history.argtypes = [P, P, C.POINTER(i32)]
     L.dtt_get_fields.argtypes = [P, P, P, i32]
+    L.dtt_set_kinematics.argtypes = [P, i32]
+    L.dtt_get_stress_tensor.argtypes = [P, P, i32]
     L.dtt_get_reactions.argtypes = [P, P, P]
     L.dtt_get_contact.argtypes = [P, C.POINTER(i32), P, P, P, P]
     L.dtt_apply_residual.argtypes = [P, P, P, P, P, i32]
@@ -224,6 +228,17 @@ class Grid:
         ps, _ = _ptr(s)
         _check(lib().dtt_get_fields(self._h, pu, ps, dev))
         return (u, s) if sigma else u
+
+    def dtt_set_kinematics(self, kinematics):
+        _check(lib().dtt_set_kinematics(self._h, int(kinematics)))
+
+    def dtt_get_stress_tensor(self, out=None):
+        """(nvox_z, nvox_y, nvox_x, n_ip, 3, 3): sigma, or Pi in finite strain."""
+        nip = 2 if self.scheme == SCHEME_TETRA2 else 1
+        t = np.zeros((self.nvox[2], self.nvox[1], self.nvox[0], nip, 3, 3)) if out is None else out
+        pt, dev = _ptr(t)
+        _check(lib().dtt_get_stress_tensor(self._h, pt, dev))
+        return t
 
     def dtt_get_reactions(self, n_rows):
         per = np.zeros(max(n_rows, 1))
