@@ -118,12 +118,15 @@ def csr_from_intents(nvox, bc, intents):
 
 def setup_grid(spec, precision, stream=None):
     """Create and configure a Grid from a mapping with keys nvox, h, bc, scheme, phase,
-    lam, mu, eps_star, lam0, mu0, intents (and optionally indenter)."""
+    lam, mu, eps_star, lam0, mu0, intents (and optionally indenter, and kinematics "SS" or
+    "FS")."""
     from . import dtt
     g = dtt.Grid(spec["nvox"], spec["h"], spec["bc"], spec["scheme"], precision, stream)
     g.dtt_set_material(spec["phase"], spec["lam"], spec["mu"])
     g.dtt_set_reference(spec["lam0"], spec["mu0"])
     g.dtt_set_load(np.asarray(spec.get("eps_star", np.zeros((3, 3)))))
+    if spec.get("kinematics", "SS") == "FS":
+        g.dtt_set_kinematics(dtt.FINITE_STRAIN)
     if spec.get("intents"):
         ptr, node, comp, a, b, val = csr_from_intents(spec["nvox"], spec["bc"], spec["intents"])
         g.dtt_set_constraints(ptr, node, comp, a, b, val)

@@ -2,6 +2,7 @@
 
   python -m paper_2607_26082_b300.run --workload ct|cube16|indent [--precision mixed|fp64]
          [--iters K | --tol T] [--steps S] [--graph-iters G] [--nvox nx,ny,nz]
+         [--kinematics ss|fs] [--r0-scale K]
   python -m paper_2607_26082_b300.run --workload batch [--cells N] [--seed0 S] [--no-tune]
          [--sequential]
 
@@ -10,7 +11,9 @@ tiling once per cell size (dtt_autotune on one cell, dtt_set_tuning on the other
 solves all cells with one dtt_batch_solve; --sequential also solves them one after the
 other with dtt_solve_step for comparison.
 
---iters K runs exactly K iterations (tolerance 0) of the first load step, which is the
+--kinematics fs solves with the finite-strain stress step (Section 5.2, Algorithm 3 for
+the indentation); --r0-scale multiplies the workload's reference medium (the paper takes a
+stiffer one in finite strain).  --iters K runs exactly K iterations (tolerance 0) of the first load step, which is the
 short, fixed launch sequence a profiler wants; --tol runs to convergence.  For the
 indentation block every load step moves the sphere (Algorithm 2, one increment each),
 starting from the previous step's solution.  Prints one JSON report per step.
@@ -96,11 +99,16 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1, help="load steps (indentation only)")
     ap.add_argument("--graph-iters", type=int, default=0)
     ap.add_argument("--nvox", default=None, help="voxels nx,ny,nz (ct and indent)")
+    ap.add_argument("--kinematics", default="ss", choices=["ss", "fs"])
+    ap.add_argument("--r0-scale", type=float, default=1.0)
     a = ap.parse_args(argv)
     if a.workload == "batch":
         return run_batch(a, dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64)
     spec = make_workload(a.workload, tuple(int(v) for v in a.nvox.split(",")) if a.nvox else None)
     prec = dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64
+    spec["kinematics"] = a.kinematics.upper()
+    spec["lam0"] = a.r0_scale * spec["lam0"]
+    spec["mu0"] = a.r0_scale * spec["mu0"]
     g = rows.setup_grid(spec, prec)
     tol = 0.0 if a.iters > 0 else (spec["tol"] if a.tol is None else a.tol)
     max_iter = a.iters if a.iters > 0 else 20000
@@ -113,7 +121,7 @@ def main(argv=None):
             g.dtt_move_indenter(ind["centers"][s])
         rep = g.dtt_solve_step(tol, max_iter, acv_mod=spec["acv_mod"], acv_on=dtt.ACV_P,
                                init=dtt.INIT_PREVIOUS if s else dtt.INIT_ZERO, graph_iters=a.graph_iters)
-        out = {"workload": spec["name"], "precision": a.precision, "step": s}
+        out = {"workload": spec["name"], "precision": a.precision, "kinematics": a.kinematics, "step": s}
         out.update(rep.as_dict())
         if ind:
             # contact force on the sphere and the Hertz value (Eq. 30) at this depth
