@@ -174,6 +174,13 @@ dtt_status dtt_get_fields(dtt_grid* grid, double* u, double* sigma, int32_t ptr_
  * a material. */
 dtt_status dtt_get_stress_tensor(dtt_grid* grid, double* tensor, int32_t ptr_is_device);
 
+/* Smallest det F over the integration points, F = 1 + eps* + grad u~ of the current u~
+ * (Section 5.2's deformation gradient; meaningful in either kinematics).  A value <= 0
+ * means an inverted point: a St Venant-Kirchhoff solve (Section 5.4's law) can converge to
+ * such a branch when a load increment is too large, and it is then not a physical
+ * solution.  *det_min: host double. */
+dtt_status dtt_get_min_jacobian(dtt_grid* grid, double* det_min);
+
 /* Reactions of the constraint rows after the last solve: per_row[r] = h^3 f_r
  * sum_e W_e b_e (face DOFs halved, edge DOFs quartered, Section 4.1.3), f_r the
  * multiplier; total = vector sum.  per_row may be NULL. */

@@ -1278,6 +1278,28 @@ dtt_status dtt_get_stress_tensor(dtt_grid* G, double* tensor, int32_t ptr_is_dev
   return DTT_OK;
 }
 
+dtt_status dtt_get_min_jacobian(dtt_grid* G, double* det_min) {
+  if (!G || !det_min) return fail(DTT_ERR_ARG, "null argument");
+  const double* src = nullptr;
+  dtt_status st = u_f64(G, &src);
+  if (st != DTT_OK) return st;
+  const int nb = min_jacobian_blocks(G->g);
+  double* buf = nullptr;
+  st = dalloc(&buf, (size_t)nb * sizeof(double));
+  if (st != DTT_OK) return st;
+  std::vector<double> h(nb);
+  int rc = launch_min_jacobian(G->g, src, G->eps, buf, G->stream);
+  cudaError_t e = rc ? (cudaError_t)rc
+                     : cudaMemcpyAsync(h.data(), buf, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, G->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
+  dfree(buf);
+  if (e != cudaSuccess) return fail(DTT_ERR_CUDA, cudaGetErrorString(e));
+  double m = h[0];
+  for (int b = 1; b < nb; ++b) m = std::min(m, h[b]);
+  *det_min = m;
+  return DTT_OK;
+}
+
 dtt_status dtt_set_kinematics(dtt_grid* G, int32_t kinematics) {
   if (!G) return fail(DTT_ERR_ARG, "null grid");
   if (kinematics != DTT_SMALL_STRAIN && kinematics != DTT_FINITE_STRAIN)

@@ -310,6 +310,9 @@ int launch_to_double(long long n, const void* in, int in_is_float, double* out, 
 int launch_from_double(long long n, const double* in, void* out, int out_is_float, cudaStream_t s);
 int launch_split(long long n, const double* in, float* hi, float* lo, cudaStream_t s);
 int launch_join(long long n, const float* hi, const float* lo, double* out, cudaStream_t s);
+int min_jacobian_blocks(const GridDev& g);
+int launch_min_jacobian(const GridDev& g, const double* u, const double eps[3][3], double* block_min,
+                        cudaStream_t s);
 int launch_stress_out(const GridDev& g, const double* u, const uint8_t* phase, const double* lam,
                       const double* mu, const double eps[3][3], int full, double* out, cudaStream_t s);
 

@@ -1,6 +1,8 @@
-// Small utility kernels: precision conversion, float-float split/join, and the stress
-// output at the integration points (Section 3.1.1 gradients, sigma = lambda tr(eps) 1 +
-// 2 mu eps) used by dtt_get_fields.  Not on the iteration path.
+// Small utility kernels: precision conversion, float-float split/join, the stress output
+// at the integration points (Section 3.1.1 gradients, sigma = lambda tr(eps) 1 + 2 mu eps,
+// or the finite-strain stresses of Section 5.2) used by dtt_get_fields and
+// dtt_get_stress_tensor, and the smallest det F over the integration points.  Not on the
+// iteration path.
 #include "dtt_internal.cuh"
 
 namespace dtt {
@@ -52,6 +54,31 @@ int launch_join(long long n, const float* hi, const float* lo, double* out, cuda
 // row c, column d -- sigma, or the first Piola-Kirchhoff Pi = F.S (Section 5.2).
 struct Eps9 { double e[3][3]; };
 
+// Displacement gradients G[t][c][d] = d u_c / d x_d at the integration points of voxel v
+// (x fastest): TETRA2 two points (even / odd parity corners, 1 / 2h), HEX1 one (1 / 4h).
+__device__ void voxel_gradients(const GridDev& g, const double* __restrict__ u, long long v, double G[2][3][3]) {
+  int vx = (int)(v % g.nvox[0]);
+  long long r = v / g.nvox[0];
+  int vy = (int)(r % g.nvox[1]);
+  int vz = (int)(r / g.nvox[1]);
+  const int nip = g.scheme == SCHEME_TETRA2 ? 2 : 1;
+  for (int t = 0; t < 2; ++t)
+    for (int c = 0; c < 3; ++c)
+      for (int d = 0; d < 3; ++d) G[t][c][d] = 0.0;
+  for (int q = 0; q < 8; ++q) {
+    int dx = q & 1, dy = (q >> 1) & 1, dz = (q >> 2) & 1;
+    int i = (vx + dx) % g.nn[0], j = (vy + dy) % g.nn[1], k = (vz + dz) % g.nn[2];
+    long long n = i + (long long)g.nn[0] * (j + (long long)g.nn[1] * k);
+    const int t = nip == 2 ? ((dx + dy + dz) & 1) : 0;
+    const double coef = nip == 2 ? 1.0 / (2.0 * g.h) : 1.0 / (4.0 * g.h);
+    const double s[3] = {dx ? 1.0 : -1.0, dy ? 1.0 : -1.0, dz ? 1.0 : -1.0};
+    for (int c = 0; c < 3; ++c) {
+      const double uc = u[(long long)c * g.nnodes + n];
+      for (int d = 0; d < 3; ++d) G[t][c][d] += coef * s[d] * uc;
+    }
+  }
+}
+
 __global__ void k_stress_out(const GridDev g, const double* __restrict__ u, const uint8_t* __restrict__ phase,
                              const double* __restrict__ lam, const double* __restrict__ mu, const Eps9 eps, int full,
                              double* __restrict__ out) {
@@ -59,33 +86,11 @@ __global__ void k_stress_out(const GridDev g, const double* __restrict__ u, cons
   const int nip = g.scheme == SCHEME_TETRA2 ? 2 : 1;
   const int nout = full ? 9 : 6;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < NV; v += (long long)gridDim.x * blockDim.x) {
-    int vx = (int)(v % g.nvox[0]);
-    long long r = v / g.nvox[0];
-    int vy = (int)(r % g.nvox[1]);
-    int vz = (int)(r / g.nvox[1]);
-    double U[3][8];
-    for (int q = 0; q < 8; ++q) {
-      int dx = q & 1, dy = (q >> 1) & 1, dz = (q >> 2) & 1;
-      int i = (vx + dx) % g.nn[0], j = (vy + dy) % g.nn[1], k = (vz + dz) % g.nn[2];
-      long long n = i + (long long)g.nn[0] * (j + (long long)g.nn[1] * k);
-      for (int c = 0; c < 3; ++c) U[c][q] = u[(long long)c * g.nnodes + n];
-    }
+    double GG[2][3][3];
+    voxel_gradients(g, u, v, GG);
     double L = lam[phase[v]], M = mu[phase[v]];
     for (int t = 0; t < nip; ++t) {
-      double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-      for (int q = 0; q < 8; ++q) {
-        int dx = q & 1, dy = (q >> 1) & 1, dz = (q >> 2) & 1;
-        double coef;
-        if (nip == 2) {
-          if (((dx + dy + dz) & 1) != t) continue;
-          coef = 1.0 / (2.0 * g.h);
-        } else {
-          coef = 1.0 / (4.0 * g.h);
-        }
-        double s[3] = {dx ? 1.0 : -1.0, dy ? 1.0 : -1.0, dz ? 1.0 : -1.0};
-        for (int c = 0; c < 3; ++c)
-          for (int d = 0; d < 3; ++d) G[c][d] += coef * s[d] * U[c][q];
-      }
+      double (&G)[3][3] = GG[t];
       double H[3][3], E[3][3], S[3][3], P[3][3];
       for (int c = 0; c < 3; ++c)
         for (int d = 0; d < 3; ++d) H[c][d] = eps.e[c][d] + G[c][d];
@@ -120,6 +125,47 @@ __global__ void k_stress_out(const GridDev g, const double* __restrict__ u, cons
       }
     }
   }
+}
+
+// Smallest det F, F = 1 + eps* + grad u~, over every integration point; one value per
+// block (the host takes the minimum of the blocks).
+__global__ void k_min_jacobian(const GridDev g, const double* __restrict__ u, const Eps9 eps,
+                               double* __restrict__ block_min) {
+  __shared__ double red[256];
+  const long long NV = (long long)g.nvox[0] * g.nvox[1] * g.nvox[2];
+  const int nip = g.scheme == SCHEME_TETRA2 ? 2 : 1;
+  double m = 1.0e300;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < NV; v += (long long)gridDim.x * blockDim.x) {
+    double GG[2][3][3];
+    voxel_gradients(g, u, v, GG);
+    for (int t = 0; t < nip; ++t) {
+      double F[3][3];
+      for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) F[c][d] = (c == d ? 1.0 : 0.0) + eps.e[c][d] + GG[t][c][d];
+      const double det = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
+                         F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+                         F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+      m = fmin(m, det);
+    }
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + off]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) block_min[blockIdx.x] = red[0];
+}
+
+int min_jacobian_blocks(const GridDev& g) { return nblk((long long)g.nvox[0] * g.nvox[1] * g.nvox[2]); }
+
+int launch_min_jacobian(const GridDev& g, const double* u, const double eps[3][3], double* block_min,
+                        cudaStream_t s) {
+  Eps9 e;
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) e.e[p][q] = eps[p][q];
+  k_min_jacobian<<<min_jacobian_blocks(g), 256, 0, s>>>(g, u, e, block_min);
+  return (int)cudaGetLastError();
 }
 
 int launch_stress_out(const GridDev& g, const double* u, const uint8_t* phase, const double* lam,

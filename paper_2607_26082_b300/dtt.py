@@ -56,7 +56,7 @@ EXPORTS = ["dtt_grid_create", "dtt_grid_destroy", "dtt_grid_sizes", "dtt_set_mat
            "dtt_set_reference", "dtt_set_load", "dtt_set_constraints", "dtt_set_indenter",
            "dtt_move_indenter", "dtt_clear_indenter", "dtt_set_initial", "dtt_solve_step",
            "dtt_get_history", "dtt_get_fields", "dtt_get_reactions", "dtt_get_contact",
-           "dtt_set_kinematics", "dtt_get_stress_tensor",
+           "dtt_set_kinematics", "dtt_get_stress_tensor", "dtt_get_min_jacobian",
            "dtt_apply_residual", "dtt_apply_green", "dtt_apply_green_noalloc", "dtt_transform",
            "dtt_profile_iteration", "dtt_autotune", "dtt_set_tuning", "dtt_batch_solve",
            "dtt_last_error", "dtt_version"]
@@ -91,6 +91,7 @@ def lib():
     L.dtt_get_fields.argtypes = [P, P, P, i32]
     L.dtt_set_kinematics.argtypes = [P, i32]
     L.dtt_get_stress_tensor.argtypes = [P, P, i32]
+    L.dtt_get_min_jacobian.argtypes = [P, C.POINTER(f64)]
     L.dtt_get_reactions.argtypes = [P, P, P]
     L.dtt_get_contact.argtypes = [P, C.POINTER(i32), P, P, P, P]
     L.dtt_apply_residual.argtypes = [P, P, P, P, P, i32]
@@ -239,6 +240,11 @@ class Grid:
         pt, dev = _ptr(t)
         _check(lib().dtt_get_stress_tensor(self._h, pt, dev))
         return t
+
+    def dtt_get_min_jacobian(self):
+        v = C.c_double()
+        _check(lib().dtt_get_min_jacobian(self._h, C.byref(v)))
+        return v.value
 
     def dtt_get_reactions(self, n_rows):
         per = np.zeros(max(n_rows, 1))

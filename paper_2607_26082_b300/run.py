@@ -2,7 +2,7 @@
 
   python -m paper_2607_26082_b300.run --workload ct|cube16|indent [--precision mixed|fp64]
          [--iters K | --tol T] [--steps S] [--graph-iters G] [--nvox nx,ny,nz]
-         [--kinematics ss|fs] [--r0-scale K]
+         [--kinematics ss|fs] [--r0-scale K] [--load-steps N]
   python -m paper_2607_26082_b300.run --workload batch [--cells N] [--seed0 S] [--no-tune]
          [--sequential]
 
@@ -13,7 +13,8 @@ other with dtt_solve_step for comparison.
 
 --kinematics fs solves with the finite-strain stress step (Section 5.2, Algorithm 3 for
 the indentation); --r0-scale multiplies the workload's reference medium (the paper takes a
-stiffer one in finite strain).  --iters K runs exactly K iterations (tolerance 0) of the first load step, which is the
+stiffer one in finite strain); --load-steps N splits the indentation into N geometric
+increments (default 10).  --iters K runs exactly K iterations (tolerance 0) of the first load step, which is the
 short, fixed launch sequence a profiler wants; --tol runs to convergence.  For the
 indentation block every load step moves the sphere (Algorithm 2, one increment each),
 starting from the previous step's solution.  Prints one JSON report per step.
@@ -34,7 +35,7 @@ import workloads as wl  # noqa: E402
 from . import dtt, rows  # noqa: E402
 
 
-def make_workload(name, nvox=None):
+def make_workload(name, nvox=None, load_steps=10):
     """ct: half compact-tension-like specimen 128x128x32; cube16: 16^3 cube with pinned
     nodes; indent: sphere indentation of a 256x256x128 block, R = 64.  nvox rescales ct and
     indent (the indenter radius scales with the block)."""
@@ -44,7 +45,7 @@ def make_workload(name, nvox=None):
         return wl.cube16()
     if name == "indent":
         n = nvox or (256, 256, 128)
-        return wl.indentation(*n, R=64.0 * n[0] / 256.0, steps=10)
+        return wl.indentation(*n, R=64.0 * n[0] / 256.0, steps=load_steps)
     raise SystemExit("unknown workload %r" % name)
 
 
@@ -101,10 +102,11 @@ def main(argv=None):
     ap.add_argument("--nvox", default=None, help="voxels nx,ny,nz (ct and indent)")
     ap.add_argument("--kinematics", default="ss", choices=["ss", "fs"])
     ap.add_argument("--r0-scale", type=float, default=1.0)
+    ap.add_argument("--load-steps", type=int, default=10)
     a = ap.parse_args(argv)
     if a.workload == "batch":
         return run_batch(a, dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64)
-    spec = make_workload(a.workload, tuple(int(v) for v in a.nvox.split(",")) if a.nvox else None)
+    spec = make_workload(a.workload, tuple(int(v) for v in a.nvox.split(",")) if a.nvox else None, a.load_steps)
     prec = dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64
     spec["kinematics"] = a.kinematics.upper()
     spec["lam0"] = a.r0_scale * spec["lam0"]
@@ -130,7 +132,8 @@ def main(argv=None):
             Es = ind["E"] / (1.0 - ind["nu"] ** 2)
             out.update({"depth": d, "d_over_R": float(ind["ratios"][s]), "contact_nodes": int(np.sum(act)),
                         "force": float(np.linalg.norm(force)),
-                        "hertz": 4.0 / 3.0 * Es * np.sqrt(ind["radius"]) * d ** 1.5})
+                        "hertz": 4.0 / 3.0 * Es * np.sqrt(ind["radius"]) * d ** 1.5,
+                        "min_det_F": g.dtt_get_min_jacobian()})
         print(json.dumps(out), flush=True)
     g.close()
     return 0

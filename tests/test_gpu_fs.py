@@ -256,3 +256,36 @@ def test_kinematics_switch_recaptures_and_rejects_bad_values():
         assert e.value.status == dtt.ERR_ARG
     for q in (g, g2):
         q.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (MIXED, 1e-6)])
+def test_min_jacobian(prec, tol):
+    """dtt_get_min_jacobian against det(1 + eps* + grad u) from the oracle's gradients: a
+    random field, a field that inverts part of the cell, and a finite rotation (det F = 1
+    everywhere).  Traction-free faces, so that every nodal value is an unknown."""
+    spec = wl.random_problem(31, nvox=(9, 7, 8), eps_scale=0.03, scheme=wl.HEX1,
+                             n_strong=0, n_weak=0, n_smooth=0, n_tie=0, anchored=False)
+    spec["bc"] = np.full((3, 2, 3), N)
+    pb, _ = oracle_problem(spec)
+    g = gpu_grid(spec, prec)
+
+    def ref_min(u, eps):
+        gr = odz.gradients(pb, u) + eps[None, :, :, None, None, None]
+        F = np.moveaxis(gr, (1, 2), (-2, -1)) + np.eye(3)
+        return np.linalg.det(F).min()
+
+    u = 0.2 * np.random.default_rng(31).standard_normal((3,) + pb.node_shape)
+    g.dtt_set_initial(u)
+    assert abs(g.dtt_get_min_jacobian() - ref_min(u, pb.eps_star)) <= tol
+    X = pb.node_positions()
+    u_inv = np.zeros_like(u)
+    u_inv[0] = np.where(X[0] < 4, -2.5 * X[0], -10.0)   # F_xx about -1.5 left of x = 4
+    g.dtt_set_initial(u_inv)
+    m = g.dtt_get_min_jacobian()
+    assert m < 0 and abs(m - ref_min(u_inv, pb.eps_star)) <= 10 * tol
+    g.dtt_set_load(np.zeros((3, 3)))
+    th = 0.7
+    Q = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1.0]])
+    g.dtt_set_initial(np.einsum("ab,bzyx->azyx", Q - np.eye(3), X))
+    assert abs(g.dtt_get_min_jacobian() - 1.0) <= tol
+    g.close()
