@@ -1,8 +1,8 @@
 """Command-line runner: solve one of the synthetic workloads with the CUDA path.
 
-  python -m paper_2607_26082_b300.run --workload ct|cube16|indent [--precision mixed|fp64]
+  python -m paper_2607_26082_b300.run --workload ct|cube16|indent|indent_cube [--precision mixed|fp64]
          [--iters K | --tol T] [--steps S] [--graph-iters G] [--nvox nx,ny,nz]
-         [--kinematics ss|fs] [--r0-scale K] [--load-steps N]
+         [--kinematics ss|fs] [--r0-scale K] [--load-steps N] [--max-iter M] [--stop-on-fail]
   python -m paper_2607_26082_b300.run --workload batch [--cells N] [--seed0 S] [--no-tune]
          [--sequential]
 
@@ -14,7 +14,9 @@ other with dtt_solve_step for comparison.
 --kinematics fs solves with the finite-strain stress step (Section 5.2, Algorithm 3 for
 the indentation); --r0-scale multiplies the workload's reference medium (the paper takes a
 stiffer one in finite strain); --load-steps N splits the indentation into N geometric
-increments (default 10).  --iters K runs exactly K iterations (tolerance 0) of the first load step, which is the
+increments (default 10); --max-iter caps the iterations of each step (default 20000) and
+--stop-on-fail ends the run at the first step that does not converge.  --iters K runs
+exactly K iterations (tolerance 0) of the first load step, which is the
 short, fixed launch sequence a profiler wants; --tol runs to convergence.  For the
 indentation block every load step moves the sphere (Algorithm 2, one increment each),
 starting from the previous step's solution.  Prints one JSON report per step.
@@ -38,11 +40,14 @@ from . import dtt, rows  # noqa: E402
 def make_workload(name, nvox=None, load_steps=10):
     """ct: half compact-tension-like specimen 128x128x32; cube16: 16^3 cube with pinned
     nodes; indent: sphere indentation of a 256x256x128 block, R = 64.  nvox rescales ct and
-    indent (the indenter radius scales with the block)."""
+    indent (the indenter radius scales with the block); indent_cube: Section 5.4's 65^3 cube
+    with a sphere of the cube's diameter, `load_steps` equal steps to d/R = 0.2."""
     if name == "ct":
         return wl.ct_plate(*(nvox or (128, 128, 32)))
     if name == "cube16":
         return wl.cube16()
+    if name == "indent_cube":
+        return wl.indentation_cube(nvox[0] if nvox else 65, steps=load_steps, dmax=0.2)
     if name == "indent":
         n = nvox or (256, 256, 128)
         return wl.indentation(*n, R=64.0 * n[0] / 256.0, steps=load_steps)
@@ -89,7 +94,7 @@ def run_batch(a, prec):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="ct", choices=["ct", "cube16", "indent", "batch"])
+    ap.add_argument("--workload", default="ct", choices=["ct", "cube16", "indent", "indent_cube", "batch"])
     ap.add_argument("--cells", type=int, default=256)
     ap.add_argument("--seed0", type=int, default=1000)
     ap.add_argument("--no-tune", action="store_true")
@@ -103,6 +108,8 @@ def main(argv=None):
     ap.add_argument("--kinematics", default="ss", choices=["ss", "fs"])
     ap.add_argument("--r0-scale", type=float, default=1.0)
     ap.add_argument("--load-steps", type=int, default=10)
+    ap.add_argument("--max-iter", type=int, default=20000)
+    ap.add_argument("--stop-on-fail", action="store_true")
     a = ap.parse_args(argv)
     if a.workload == "batch":
         return run_batch(a, dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64)
@@ -113,7 +120,7 @@ def main(argv=None):
     spec["mu0"] = a.r0_scale * spec["mu0"]
     g = rows.setup_grid(spec, prec)
     tol = 0.0 if a.iters > 0 else (spec["tol"] if a.tol is None else a.tol)
-    max_iter = a.iters if a.iters > 0 else 20000
+    max_iter = a.iters if a.iters > 0 else a.max_iter
     ind = spec.get("indenter")
     nsteps = min(a.steps, len(ind["centers"])) if ind else 1
     if ind:
@@ -135,6 +142,8 @@ def main(argv=None):
                         "hertz": 4.0 / 3.0 * Es * np.sqrt(ind["radius"]) * d ** 1.5,
                         "min_det_F": g.dtt_get_min_jacobian()})
         print(json.dumps(out), flush=True)
+        if a.stop_on_fail and rep.status != dtt.OK:
+            break
     g.close()
     return 0
 

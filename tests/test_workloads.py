@@ -47,3 +47,17 @@ def test_batch_cells_are_reproducible():
     b = wl.batch_cell(1234)
     assert np.array_equal(a["phase"], b["phase"]) and np.array_equal(a["bc"], b["bc"])
     assert a["intents"] == b["intents"]
+
+
+def test_indentation_cube_follows_the_benchmark_geometry():
+    w = wl.indentation_cube(65, steps=80, dmax=0.2)
+    I = w["indenter"]
+    assert w["nvox"] == (65, 65, 65) and I["radius"] == 32.5
+    assert np.allclose(np.diff(I["ratios"]), 0.2 / 80) and np.isclose(I["ratios"][-1], 0.2)
+    # depth d = (n + R) - centre_z, measured from the undeformed top face
+    d = np.array([65 + 32.5 - c[2] for c in I["centers"]])
+    assert np.allclose(d, I["ratios"] * 32.5)
+    assert np.allclose([c[:2] for c in I["centers"]], 32.5)
+    assert (w["bc"][2, 0] == wl.D).all() and (w["bc"][2, 1] == wl.N).all()
+    assert (w["bc"][:2] == wl.N).all()
+    assert w["lam0"] == w["lam"][0] and w["mu0"] == w["mu"][0]

@@ -146,6 +146,24 @@ def indentation(nx=256, ny=256, nz=128, R=64.0, steps=10, dmin=0.001, dmax=0.05,
                                   E=1.0, nu=0.3))
 
 
+def indentation_cube(n=65, steps=80, dmax=0.2, scheme=TETRA2):
+    """Section 5.4's benchmark geometry: a cube of n^3 voxels, bottom face clamped, the
+    other faces traction-free, a rigid sphere of diameter equal to the cube edge (R = n/2
+    voxels) centred over the top face, pushed in `steps` equal increments to d/R = dmax.
+    nu = 0.3 as for the paper's steel (lambda = 120, mu = 80 GPa), with E = 1: forces scale
+    with E and iteration counts do not.  The reference medium is 1 x (lambda, mu), so that
+    a multiplier of it is the paper's R0 factor."""
+    w = indentation(n, n, n, R=n / 2.0, steps=steps, dmin=dmax / steps, dmax=dmax, scheme=scheme)
+    ratios = np.linspace(dmax / steps, dmax, steps)
+    R = n / 2.0
+    w["indenter"]["ratios"] = ratios
+    w["indenter"]["centers"] = [np.array([n / 2.0, n / 2.0, n + R - r * R]) for r in ratios]
+    w["lam0"] = float(w["lam"][0])
+    w["mu0"] = float(w["mu"][0])
+    w["name"] = "sphere indentation of a %d^3 cube, R=%g, %d equal steps to d/R=%g" % (n, R, steps, dmax)
+    return w
+
+
 # ---------------------------------------------------------------------------
 # Batches of uneven two-phase cells (training-data generation workload)
 # ---------------------------------------------------------------------------
