@@ -1,8 +1,9 @@
 """Command-line runner: solve one of the synthetic workloads with the CUDA path.
 
-  python -m paper_2607_26082_b300.run --workload ct|cube16|indent|indent_cube [--precision mixed|fp64]
+  python -m paper_2607_26082_b300.run --workload ct|ct_paper|cube16|indent|indent_cube [--precision mixed|fp64]
          [--iters K | --tol T] [--steps S] [--graph-iters G] [--nvox nx,ny,nz]
          [--kinematics ss|fs] [--r0-scale K] [--load-steps N] [--max-iter M] [--stop-on-fail]
+         [--ct-load strong_line|weak_line|strong_node|weak_node|smooth_node] [--acv-on u|p] [--acv-mod M]
   python -m paper_2607_26082_b300.run --workload batch [--cells N] [--seed0 S] [--no-tune]
          [--sequential]
 
@@ -15,7 +16,10 @@ other with dtt_solve_step for comparison.
 the indentation); --r0-scale multiplies the workload's reference medium (the paper takes a
 stiffer one in finite strain); --load-steps N splits the indentation into N geometric
 increments (default 10); --max-iter caps the iterations of each step (default 20000) and
---stop-on-fail ends the run at the first step that does not converge.  --iters K runs
+--stop-on-fail ends the run at the first step that does not converge.  ct_paper is the
+paper's 10 x 100 x (50 + 1) CT-like specimen with the loading --ct-load; it reports the
+reactions of the load rows and of the ligament rows and their balance.  --acv-on and
+--acv-mod override the workload's Anderson settings.  --iters K runs
 exactly K iterations (tolerance 0) of the first load step, which is the
 short, fixed launch sequence a profiler wants; --tol runs to convergence.  For the
 indentation block every load step moves the sphere (Algorithm 2, one increment each),
@@ -46,6 +50,8 @@ def make_workload(name, nvox=None, load_steps=10):
         return wl.ct_plate(*(nvox or (128, 128, 32)))
     if name == "cube16":
         return wl.cube16()
+    if name.startswith("ct_paper:"):
+        return wl.ct_specimen(name.split(":", 1)[1])
     if name == "indent_cube":
         return wl.indentation_cube(nvox[0] if nvox else 65, steps=load_steps, dmax=0.2)
     if name == "indent":
@@ -94,7 +100,10 @@ def run_batch(a, prec):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="ct", choices=["ct", "cube16", "indent", "indent_cube", "batch"])
+    ap.add_argument("--workload", default="ct", choices=["ct", "ct_paper", "cube16", "indent", "indent_cube", "batch"])
+    ap.add_argument("--ct-load", default="strong_line", choices=list(wl.CT_LOADS))
+    ap.add_argument("--acv-on", default="p", choices=["u", "p"])
+    ap.add_argument("--acv-mod", type=int, default=0, help="0: the workload's")
     ap.add_argument("--cells", type=int, default=256)
     ap.add_argument("--seed0", type=int, default=1000)
     ap.add_argument("--no-tune", action="store_true")
@@ -113,7 +122,8 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.workload == "batch":
         return run_batch(a, dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64)
-    spec = make_workload(a.workload, tuple(int(v) for v in a.nvox.split(",")) if a.nvox else None, a.load_steps)
+    wname = "ct_paper:" + a.ct_load if a.workload == "ct_paper" else a.workload
+    spec = make_workload(wname, tuple(int(v) for v in a.nvox.split(",")) if a.nvox else None, a.load_steps)
     prec = dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64
     spec["kinematics"] = a.kinematics.upper()
     spec["lam0"] = a.r0_scale * spec["lam0"]
@@ -128,10 +138,18 @@ def main(argv=None):
     for s in range(nsteps):
         if ind:
             g.dtt_move_indenter(ind["centers"][s])
-        rep = g.dtt_solve_step(tol, max_iter, acv_mod=spec["acv_mod"], acv_on=dtt.ACV_P,
+        rep = g.dtt_solve_step(tol, max_iter, acv_mod=a.acv_mod or spec["acv_mod"],
+                               acv_on=dtt.ACV_P if a.acv_on == "p" else dtt.ACV_U,
                                init=dtt.INIT_PREVIOUS if s else dtt.INIT_ZERO, graph_iters=a.graph_iters)
-        out = {"workload": spec["name"], "precision": a.precision, "kinematics": a.kinematics, "step": s}
+        out = {"workload": spec["name"], "precision": a.precision, "kinematics": a.kinematics, "step": s,
+               "acv_on": a.acv_on, "acv_mod": a.acv_mod or spec["acv_mod"]}
         out.update(rep.as_dict())
+        if "ligament_rows" in spec and g.n_rows:
+            per, _ = g.dtt_get_reactions(g.n_rows)
+            nl = spec["ligament_rows"]
+            r_l, r_s = float(per[:nl].sum()), float(per[nl:].sum())
+            out.update({"reaction_ligament": r_l, "reaction_load": r_s,
+                        "balance": abs(r_l + r_s) / max(abs(r_l), 1e-300)})
         if ind:
             # contact force on the sphere and the Hertz value (Eq. 30) at this depth
             act, gap, fn, force = g.dtt_get_contact()

@@ -124,6 +124,59 @@ def ct_plate(nx=128, ny=128, nz=32, scheme=TETRA2, notch_scale=0.0, r0_factor=1.
                     ligament_rows=(nz + 1) * (nx + 1 - xn))
 
 
+CT_LOADS = ("strong_line", "weak_line", "strong_node", "weak_node", "smooth_node")
+
+
+def ct_specimen(load="strong_line", scheme=TETRA2, tol=1e-4):
+    """The paper's half CT-like specimen (Section 4.1.2, Fig. 2; Section 4.2.3), axes
+    (e1, e2, e3) = (x, y, z), 10 x 100 x (50 + 1) voxels:
+      * voxel layer z in [0, 1) is the void buffer (null Lame coefficients); u_z is
+        Dirichlet on its outer face z = 0, every other face and component is traction-free;
+      * the specimen is z in [1, 51), lambda = 4.04e4, mu = 2.70e4; the paper's height
+        x3 is z - 1;
+      * the ligament, nodes (0:10, 50:100) of the plane x3 = 0, is held at u_z = 0 by
+        strong rows; the crack (0:10, 0:50) of that plane is free;
+      * the load pulls by 10 in e3 at (x2, x3) = (24, 24):
+          strong_line  strong rows on the line of nodes (0:10, 24, 24);
+          weak_line    one row over the 44 nodes of the line of elements with centres
+                       (0.5:9.5, 24.5, 24.5): their mean u_z = 10, reaction spread evenly
+                       (Eq. 10-14 with V(i0) replaced by the 44-node set);
+          strong_node  one strong row at node (2, 24, 24);
+          weak_node    one weak row at the element centre (2.5, 24.5, 24.5) (Eq. 10-14);
+          smooth_node  one smooth row at node (2, 24, 24) (Eq. 15-17).
+    Reference medium (lambda / 2, mu / 2), Anderson on p~ every 2 iterations, tol 1e-4
+    (the tolerance of the paper's acceleration table)."""
+    if load not in CT_LOADS:
+        raise ValueError(load)
+    nx, ny, nz = 10, 100, 51
+    bc = np.full((3, 2, 3), N, dtype=np.int64)
+    bc[2, 0, 2] = D
+    lam, mu = 4.04e4, 2.70e4
+    phase = np.zeros((nz, ny, nx), np.uint8)
+    phase[0] = 1
+    intents = []
+    for j in range(50, ny + 1):
+        for i in range(nx + 1):
+            intents.append(dict(kind="strong", ijk=(i, j, 1), comp=2, value=0.0))
+    jl, kl, U = 24, 24 + 1, 10.0
+    if load == "strong_line":
+        for i in range(nx + 1):
+            intents.append(dict(kind="strong", ijk=(i, jl, kl), comp=2, value=U))
+    elif load == "weak_line":
+        nodes = [(i, jl + dy, kl + dz) for dz in (0, 1) for dy in (0, 1) for i in range(nx + 1)]
+        intents.append(dict(kind="tie", nodes=nodes, comp=2, value=U))
+    elif load == "strong_node":
+        intents.append(dict(kind="strong", ijk=(2, jl, kl), comp=2, value=U))
+    elif load == "weak_node":
+        intents.append(dict(kind="weak_voxel", vox=(2, jl, kl), comp=2, value=U))
+    else:
+        intents.append(dict(kind="smooth", ijk=(2, jl, kl), comp=2, value=U))
+    return Workload(name="CT-like specimen 10x100x(50+1), %s load" % load, nvox=(nx, ny, nz), h=1.0,
+                    bc=bc, scheme=scheme, phase=phase, lam=np.array([lam, 0.0]), mu=np.array([mu, 0.0]),
+                    eps_star=np.zeros((3, 3)), intents=intents, lam0=lam / 2, mu0=mu / 2, tol=tol,
+                    acv_mod=2, ligament_rows=51 * (nx + 1))
+
+
 # ---------------------------------------------------------------------------
 # Rigid-sphere indentation
 # ---------------------------------------------------------------------------
