@@ -61,3 +61,29 @@ def test_indentation_cube_follows_the_benchmark_geometry():
     assert (w["bc"][2, 0] == wl.D).all() and (w["bc"][2, 1] == wl.N).all()
     assert (w["bc"][:2] == wl.N).all()
     assert w["lam0"] == w["lam"][0] and w["mu0"] == w["mu"][0]
+
+
+def test_ct_specimen_follows_the_paper_set_up():
+    for load in wl.CT_LOADS:
+        w = wl.ct_specimen(load)
+        assert w["nvox"] == (10, 100, 51)
+        assert (w["phase"][0] == 1).all() and (w["phase"][1:] == 0).all()
+        assert w["lam"][1] == 0.0 and w["mu"][1] == 0.0
+        assert w["bc"][2, 0, 2] == wl.D and (np.delete(w["bc"].reshape(-1), 2 * 6 + 2) == wl.N).all()
+        lig = w["intents"][:w["ligament_rows"]]
+        assert len(lig) == 561
+        assert all(it["kind"] == "strong" and it["comp"] == 2 and it["value"] == 0.0 and it["ijk"][2] == 1
+                   and 50 <= it["ijk"][1] <= 100 for it in lig)
+        load_rows = w["intents"][w["ligament_rows"]:]
+        assert all(it["comp"] == 2 and it["value"] == 10.0 for it in load_rows)
+        if load == "strong_line":
+            assert sorted(it["ijk"] for it in load_rows) == [(i, 24, 25) for i in range(11)]
+        elif load == "weak_line":
+            (row,) = load_rows
+            assert row["kind"] == "tie" and len(set(row["nodes"])) == 44
+            assert {n[1] for n in row["nodes"]} == {24, 25} and {n[2] for n in row["nodes"]} == {25, 26}
+        else:
+            (row,) = load_rows
+            kind = {"strong_node": "strong", "weak_node": "weak_voxel", "smooth_node": "smooth"}[load]
+            assert row["kind"] == kind
+            assert row.get("ijk", row.get("vox")) == (2, 24, 25)
