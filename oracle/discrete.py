@@ -258,6 +258,79 @@ def apply_A0(pb, u, lam0, mu0):
     return out
 
 
+def is_normal_mixed(pb):
+    """True when every face has "normal mixed" conditions: on each face the normal
+    component's condition differs from both tangential components' (normal Dirichlet with
+    tangential Neumann, or the reverse), and no axis is periodic.  Section 3.2.3: the
+    isotropic reference medium is usable with the per-component DTTs only for periodic and
+    normal mixed conditions; this library takes the non-periodic ones (its periodic axes
+    use a separable Hartley transform, which the medium's cross terms do not keep
+    diagonal)."""
+    for d in range(3):
+        if pb.periodic[d]:
+            return False
+        for f in range(2):
+            normal = pb.bc[d, f, d]
+            for c in range(3):
+                if c != d and pb.bc[d, f, c] == normal:
+                    return False
+    return True
+
+
+def apply_A0_iso(pb, u, lam0, mu0):
+    """A0 u = -div_D(R0 : grad_D u) for the isotropic reference medium of Section 3.2.3,
+    R0 : grad u = lambda0 tr(grad u) 1 + mu0 (grad u + grad u^T), extension form.  Unlike
+    the Paux medium it couples the components (through lambda0 div u and mu0 grad u^T)."""
+    g = gradients(pb, u)
+    tr = g[:, 0, 0] + g[:, 1, 1] + g[:, 2, 2]
+    tau = mu0 * (g + np.swapaxes(g, 1, 2))
+    for a in range(3):
+        tau[:, a, a] += lam0 * tr
+    F = nodal_force(pb, tau)
+    out = np.zeros_like(F)
+    for c in range(3):
+        m = pb.dof_mask(c)
+        out[c][m] = F[c][m] / (pb.h ** 3 * pb.weight_W(c)[m])
+    return out
+
+
+def green_apply_dense(pb, ptilde, apply_op, rcond=1e-10):
+    """The Green step by its definition, for small grids: u~ = A0^-1 p~ on the unknowns,
+    where A0 = apply_op (a linear map of nodal fields), with the part of p~ along the null
+    space of A0 discarded and u~ orthogonal to it, both in the W-weighted inner product
+    <a, b> = sum a b W.  A0 is symmetric in that inner product, and the DTT bases are
+    orthogonal in it, so this is the spectral Green step with null modes set to zero
+    (a pin compares the two for the Paux medium).  Dense matrix of the map, symmetric
+    eigen-solve in float64."""
+    masks = [pb.dof_mask(c) for c in range(3)]
+    sizes = [int(m.sum()) for m in masks]
+    n = sum(sizes)
+    off = np.cumsum([0] + sizes)
+
+    def gather(f):
+        return np.concatenate([f[c][masks[c]] for c in range(3)])
+
+    def scatter(v):
+        f = np.zeros((3,) + pb.node_shape)
+        for c in range(3):
+            f[c][masks[c]] = v[off[c]:off[c + 1]]
+        return f
+
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = gather(apply_op(scatter(e)))
+    w = gather(np.stack([pb.weight_W(c) for c in range(3)]))
+    sw = np.sqrt(w)
+    B = sw[:, None] * A / sw[None, :]
+    B = 0.5 * (B + B.T)
+    lam, V = np.linalg.eigh(B)
+    keep = lam > rcond * np.max(np.abs(lam))
+    y = V[:, keep] @ ((V[:, keep].T @ (sw * gather(ptilde))) / lam[keep])
+    return scatter(y / sw)
+
+
 def S_symbols(pb, qx, qy, qz):
     """(S_x, S_y, S_z) on the broadcast grid of wave numbers (z, y, x array order)."""
     cx = np.cos(qx)[None, None, :]

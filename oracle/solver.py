@@ -88,9 +88,17 @@ class Result:
 
 
 def solve_alg1(pb, rows, lam0, mu0, tol, max_iter, acv_on="P", acv_mod=3, u0=None,
-               acv=True, kinematics="SS"):
+               acv=True, kinematics="SS", medium="paux"):
     """Algorithm 1 (Section 4.1.1).  Returns a Result with u, p, sigma, multipliers,
-    iterations, residual history."""
+    iterations, residual history.  medium "iso": the isotropic reference medium of Section
+    3.2.3 (A0 by discrete.apply_A0_iso, the Green step by discrete.green_apply_dense; small
+    grids with normal mixed conditions)."""
+    if medium == "iso":
+        a0 = lambda u: dz.apply_A0_iso(pb, u, lam0, mu0)          # noqa: E731
+        green = lambda p: dz.green_apply_dense(pb, p, a0)         # noqa: E731
+    else:
+        a0 = lambda u: dz.apply_A0(pb, u, lam0, mu0)              # noqa: E731
+        green = lambda p: dz.green_apply(pb, p, lam0, mu0)        # noqa: E731
     cs.check_rows(pb, rows)
     tgt = cs.targets(pb, rows)
     u = np.zeros((3,) + pb.node_shape) if u0 is None else np.array(u0, dtype=np.float64)
@@ -110,10 +118,10 @@ def solve_alg1(pb, rows, lam0, mu0, tol, max_iter, acv_on="P", acv_mod=3, u0=Non
         hist.append(r)
         if r < tol or it >= max_iter:
             break
-        pt = p + dz.apply_A0(pb, u, lam0, mu0)
+        pt = p + a0(u)
         if acv and acv_on == "P":
             pt = ander.step(i, pt)
-        u = dz.green_apply(pb, pt, lam0, mu0)
+        u = green(pt)
         cs.proj_U(pb, u, rows, tgt)
         i += 1
         it += 1
