@@ -57,6 +57,7 @@ enum { DTT_PREC_FP64 = 0, DTT_PREC_MIXED = 1 };
 enum { DTT_INIT_ZERO = 0, DTT_INIT_PREVIOUS = 1, DTT_INIT_GUESS = 2 };
 enum { DTT_ACV_U = 0, DTT_ACV_P = 1 };
 enum { DTT_SMALL_STRAIN = 0, DTT_FINITE_STRAIN = 1 };
+enum { DTT_MEDIUM_PAUX = 0, DTT_MEDIUM_ISOTROPIC = 1 };
 
 /* Create a grid (Section 3.2.1 problem statement: cell, per-face per-component BCs, FD
  * scheme of Section 3.1.1).  precision: DTT_PREC_FP64 = every nodal field and every
@@ -81,6 +82,17 @@ dtt_status dtt_set_material(dtt_grid* grid, const uint8_t* phase, int32_t nphase
 /* Reference medium of the Green operator, Paux form (Section 3.2.3):
  * R0 : grad u = lambda0 (grad u (.) I) + 2 mu0 grad u.  Requires mu0 > 0, lambda0 >= 0. */
 dtt_status dtt_set_reference(dtt_grid* grid, double lambda0, double mu0);
+
+/* Kind of reference medium (Section 3.2.3).  DTT_MEDIUM_PAUX (default): the Paux medium
+ * above, which decouples the components and works with every boundary condition.
+ * DTT_MEDIUM_ISOTROPIC: R0 : grad u = lambda0 tr(grad u) 1 + mu0 (grad u + grad u^T), whose
+ * Green operator (Eq. 4 for HEX1, with the scheme's own symbols for TETRA2) couples the
+ * components through a 3 x 3 solve per wave vector; usable only with normal mixed
+ * conditions on every face -- the normal component Dirichlet and the tangential ones
+ * Neumann, or the reverse -- and no periodic axis (else DTT_ERR_BC).  The Green step then
+ * runs unfused (forward DTTs of the three components, the solve, inverse DTTs).  Other
+ * values: DTT_ERR_ARG.  A change invalidates the captured iteration graph. */
+dtt_status dtt_set_reference_medium(dtt_grid* grid, int32_t medium);
 
 /* Prescribed strain eps* (3x3 row-major, symmetric part used), Eq. 1.  In finite strain
  * it is the prescribed displacement gradient: F = 1 + eps* + grad u~. */

@@ -294,14 +294,14 @@ def apply_A0_iso(pb, u, lam0, mu0):
     return out
 
 
-def green_apply_dense(pb, ptilde, apply_op, rcond=1e-10):
-    """The Green step by its definition, for small grids: u~ = A0^-1 p~ on the unknowns,
-    where A0 = apply_op (a linear map of nodal fields), with the part of p~ along the null
-    space of A0 discarded and u~ orthogonal to it, both in the W-weighted inner product
-    <a, b> = sum a b W.  A0 is symmetric in that inner product, and the DTT bases are
-    orthogonal in it, so this is the spectral Green step with null modes set to zero
-    (a pin compares the two for the Paux medium).  Dense matrix of the map, symmetric
-    eigen-solve in float64."""
+def make_dense_green(pb, apply_op, rcond=1e-10):
+    """The Green step by its definition, for small grids: returns p~ -> u~ = A0^-1 p~ on
+    the unknowns, where A0 = apply_op (a linear map of nodal fields), with the part of p~
+    along the null space of A0 discarded and u~ orthogonal to it, both in the W-weighted
+    inner product <a, b> = sum a b W.  A0 is symmetric in that inner product, and the DTT
+    bases are orthogonal in it, so this is the spectral Green step with null modes set to
+    zero (a pin compares the two for the Paux medium).  Dense matrix of the map, symmetric
+    eigen-decomposition in float64, built once."""
     masks = [pb.dof_mask(c) for c in range(3)]
     sizes = [int(m.sum()) for m in masks]
     n = sum(sizes)
@@ -327,8 +327,17 @@ def green_apply_dense(pb, ptilde, apply_op, rcond=1e-10):
     B = 0.5 * (B + B.T)
     lam, V = np.linalg.eigh(B)
     keep = lam > rcond * np.max(np.abs(lam))
-    y = V[:, keep] @ ((V[:, keep].T @ (sw * gather(ptilde))) / lam[keep])
-    return scatter(y / sw)
+    Vk, lk = V[:, keep], lam[keep]
+
+    def green(ptilde):
+        y = Vk @ ((Vk.T @ (sw * gather(ptilde))) / lk)
+        return scatter(y / sw)
+    return green
+
+
+def green_apply_dense(pb, ptilde, apply_op, rcond=1e-10):
+    """One application of make_dense_green(pb, apply_op)."""
+    return make_dense_green(pb, apply_op, rcond)(ptilde)
 
 
 def S_symbols(pb, qx, qy, qz):

@@ -95,7 +95,7 @@ def solve_alg1(pb, rows, lam0, mu0, tol, max_iter, acv_on="P", acv_mod=3, u0=Non
     grids with normal mixed conditions)."""
     if medium == "iso":
         a0 = lambda u: dz.apply_A0_iso(pb, u, lam0, mu0)          # noqa: E731
-        green = lambda p: dz.green_apply_dense(pb, p, a0)         # noqa: E731
+        green = dz.make_dense_green(pb, a0)
     else:
         a0 = lambda u: dz.apply_A0(pb, u, lam0, mu0)              # noqa: E731
         green = lambda p: dz.green_apply(pb, p, lam0, mu0)        # noqa: E731

@@ -356,6 +356,15 @@ TransformTables tables(dtt_grid* G) {
   // ((lambda0 + 6 mu0) * 4 / h^2, since every S_j <= 4 / h^2).
   double bound = (G->lam0 + 6.0 * G->mu0) * 4.0 / (G->g.h * G->g.h);
   for (int c = 0; c < 3; ++c) t.null_thr[c] = 1e-12 * bound;
+  for (int d = 0; d < 3; ++d) {
+    t.iso.s[d] = G->iso_s[d];
+    t.iso.c[d] = G->iso_c[d];
+    t.iso.sf[d] = G->iso_sf[d];
+    t.iso.cf[d] = G->iso_cf[d];
+    t.iso.valid[d] = G->iso_valid[d];
+    t.iso.sign[d] = (G->types[d][d] == T_DST1 || G->types[d][d] == T_DST3) ? 1 : -1;
+  }
+  t.iso.null_thr = 1e-12 * bound;
   return t;
 }
 
@@ -375,7 +384,9 @@ dtt_status enqueue_green(dtt_grid* G, const T* in, void* const* in_ring, T* out,
                          const Ctrl* ctrl, int comp0, int ncomp) {
   TransformTables tt = tables(G);
   cudaStream_t s = G->stream;
-  if (tt.fft[2].use) {
+  // the isotropic medium couples the components: its Green step needs all three spectra,
+  // so it takes the unfused route
+  if (tt.fft[2].use && !G->g.ref_iso) {
     const bool alias = (in_ring == nullptr && (const void*)in == (const void*)out);
     T* b1 = alias ? tmp : out;
     T* b2 = alias ? out : tmp;
@@ -404,7 +415,8 @@ dtt_status enqueue_green(dtt_grid* G, const T* in, void* const* in_ring, T* out,
   CKL(launch_transform_axis<T>(G->g, tmp, out, tt, 1, 0, comp0, ncomp, ctrl, s));
   CKL(launch_transform_axis<T>(G->g, out, tmp, tt, 2, 0, comp0, ncomp, ctrl, s));
   prof_mark(4, s);
-  CKL(launch_green_multiply<T>(G->g, tmp, tt, G->g.scheme, ctrl, s));
+  if (G->g.ref_iso) CKL(launch_green_iso<T>(G->g, tmp, tt, ctrl, s));
+  else CKL(launch_green_multiply<T>(G->g, tmp, tt, G->g.scheme, ctrl, s));
   prof_mark(5, s);
   CKL(launch_transform_axis<T>(G->g, tmp, out, tt, 2, 1, comp0, ncomp, ctrl, s));
   CKL(launch_transform_axis<T>(G->g, out, tmp, tt, 1, 1, comp0, ncomp, ctrl, s));
@@ -765,6 +777,13 @@ void dtt_grid_destroy(dtt_grid* G) {
       dfree(G->cos2q[c][d]);
       dfree(G->sin2q_f[c][d]);
       dfree(G->cos2q_f[c][d]);
+      if (c == 0) {
+        dfree(G->iso_s[d]);
+        dfree(G->iso_c[d]);
+        dfree(G->iso_sf[d]);
+        dfree(G->iso_cf[d]);
+        dfree(G->iso_valid[d]);
+      }
     }
   for (int d = 0; d < 3; ++d) {
     dfree(G->fft_tw[d]);
@@ -820,6 +839,79 @@ dtt_status dtt_set_reference(dtt_grid* G, double lambda0, double mu0) {
   G->mu0 = mu0;
   G->ref_set = true;
   invalidate_graph(G);
+  return DTT_OK;
+}
+
+// Normal mixed conditions on every face (no periodic axis): the normal component's
+// condition differs from both tangential components'.
+static bool normal_mixed(const dtt_grid* G) {
+  for (int d = 0; d < 3; ++d) {
+    if (G->g.periodic[d]) return false;
+    for (int f = 0; f < 2; ++f) {
+      const int nrm = G->g.bc[d][f][d];
+      for (int c = 0; c < 3; ++c)
+        if (c != d && G->g.bc[d][f][c] == nrm) return false;
+    }
+  }
+  return true;
+}
+
+// Per-axis tables of the isotropic medium: sin^2(q/2), cos^2(q/2) at each position from
+// any component with a mode there (normal mixed conditions give the components the same
+// q wherever they have a mode), and the bit set of those components.
+static dtt_status build_iso_tables(dtt_grid* G) {
+  for (int d = 0; d < 3; ++d) {
+    const int nn = G->g.nn[d];
+    std::vector<double> sq(nn, 0.0), cq(nn, 1.0);
+    std::vector<uint8_t> valid(nn, 0);
+    for (int c = 0; c < 3; ++c) {
+      std::vector<double> F, B, cs, cc;
+      build_axis(G->types[c][d], G->g.nvox[d], nn, F, B, cs, cc);
+      for (int i = 0; i < nn; ++i) {
+        // a position carries a mode when the forward transform's row is not all zero
+        bool any = false;
+        for (int j = 0; j < nn && !any; ++j) any = F[(size_t)i * nn + j] != 0.0;
+        if (!any) continue;
+        valid[i] |= (uint8_t)(1 << c);
+        sq[i] = cs[i];
+        cq[i] = cc[i];
+      }
+    }
+    std::vector<float> sqf(sq.begin(), sq.end()), cqf(cq.begin(), cq.end());
+    dtt_status st = DTT_OK;
+    if (!G->iso_s[d]) {
+      st = dalloc(&G->iso_s[d], nn * sizeof(double));
+      if (st == DTT_OK) st = dalloc(&G->iso_c[d], nn * sizeof(double));
+      if (st == DTT_OK) st = dalloc(&G->iso_sf[d], nn * sizeof(float));
+      if (st == DTT_OK) st = dalloc(&G->iso_cf[d], nn * sizeof(float));
+      if (st == DTT_OK) st = dalloc(&G->iso_valid[d], nn);
+      if (st != DTT_OK) return st;
+    }
+    CK(cudaMemcpy(G->iso_s[d], sq.data(), nn * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->iso_c[d], cq.data(), nn * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->iso_sf[d], sqf.data(), nn * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->iso_cf[d], cqf.data(), nn * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->iso_valid[d], valid.data(), nn, cudaMemcpyHostToDevice));
+  }
+  return DTT_OK;
+}
+
+dtt_status dtt_set_reference_medium(dtt_grid* G, int32_t medium) {
+  if (!G) return fail(DTT_ERR_ARG, "null grid");
+  if (medium != DTT_MEDIUM_PAUX && medium != DTT_MEDIUM_ISOTROPIC)
+    return fail(DTT_ERR_ARG, "medium must be DTT_MEDIUM_PAUX or DTT_MEDIUM_ISOTROPIC");
+  const int iso = medium == DTT_MEDIUM_ISOTROPIC;
+  if (iso && !normal_mixed(G))
+    return fail(DTT_ERR_BC, "the isotropic reference medium needs normal mixed conditions on every face "
+                            "(normal component Dirichlet with tangential Neumann, or the reverse; no periodic axis)");
+  if (iso && !G->iso_s[0]) {
+    dtt_status st = build_iso_tables(G);
+    if (st != DTT_OK) return st;
+  }
+  if (G->g.ref_iso != iso) {
+    G->g.ref_iso = iso;
+    invalidate_graph(G);
+  }
   return DTT_OK;
 }
 

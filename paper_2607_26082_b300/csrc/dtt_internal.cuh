@@ -33,6 +33,7 @@ struct GridDev {
   int zc_override;   // residual kernels: node planes per CTA (0: built-in choice)
   int fft_generic;   // 1: generic Stockham kernels for every length
   int finite_strain; // 1: first Piola-Kirchhoff stress (Section 5.2), 0: small strain
+  int ref_iso;       // 1: isotropic reference medium (Section 3.2.3), 0: Paux
 };
 
 // Solver state kept on the device so that a whole iteration is a fixed sequence of
@@ -189,6 +190,19 @@ template <typename T>
 int launch_fft_z_green(const T* in, T* out, const FftParams& p, const GreenTables& gt, double lam0, double mu0,
                        int scheme, double h, int ncomp, const Ctrl* ctrl, cudaStream_t s);
 
+// Isotropic reference medium: per-axis symbol factors shared by the three components
+// (normal mixed conditions), the components present at each position, and the sign of
+// the cross terms: sign[d] = +1 when the normal component's transform along axis d is a
+// sine transform, -1 for a cosine transform; the (c, d) term carries sign[c] sign[d].
+struct IsoTables {
+  const double* s[3];
+  const double* c[3];
+  const float* sf[3];
+  const float* cf[3];
+  const uint8_t* valid[3];
+  int sign[3];
+  double null_thr;
+};
 struct TransformTables {
   FftAxisInfo fft[3];
   int types[3][3];         // [comp][axis]
@@ -200,6 +214,7 @@ struct TransformTables {
   const float* cos2q_f[3][3];
   double lam0, mu0;
   double null_thr[3];
+  IsoTables iso;           // isotropic reference medium (GridDev::ref_iso)
 };
 struct GreenTables {
   const double* s[3][3];
@@ -234,6 +249,10 @@ int launch_transform_axis(const GridDev& g, const T* in, T* out, const Transform
 template <typename T>
 int launch_z_green(const GridDev& g, const T* in, T* out, const TransformTables& tt, int ncomp_first, int ncomp,
                    const Ctrl* ctrl, cudaStream_t s);
+// Green step of the isotropic reference medium: a 3 x 3 solve per spectral position over
+// the three components' spectra (component-major, node-grid positions), in place.
+template <typename T>
+int launch_green_iso(const GridDev& g, T* spec, const TransformTables& tt, const Ctrl* ctrl, cudaStream_t s);
 template <typename T>
 int launch_green_multiply(const GridDev& g, T* spec, const TransformTables& tt, int scheme,
                           const Ctrl* ctrl, cudaStream_t s);

@@ -60,6 +60,13 @@ struct dtt_grid {
   double* cos2q[3][3]{};
   float* sin2q_f[3][3]{};   // FP32 copies (mixed-precision Green multiply)
   float* cos2q_f[3][3]{};
+  // isotropic reference medium (Section 3.2.3): per-axis tables of sin^2(q/2), cos^2(q/2)
+  // shared by the components, and per position the components with a mode there (bit c)
+  double* iso_s[3]{};
+  double* iso_c[3]{};
+  float* iso_sf[3]{};
+  float* iso_cf[3]{};
+  uint8_t* iso_valid[3]{};
 
   // constraints (host copy + device CSR)
   int nrows = 0;

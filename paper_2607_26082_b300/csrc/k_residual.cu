@@ -79,6 +79,15 @@ __device__ __forceinline__ double node_invW(const GridDev& g, int c, int i, int 
   return invW;
 }
 
+// Reference flux tau = R0 : grad u (row c, column d) of the Paux medium,
+// (2 mu0 + lambda0 delta_cd) grad_d u_c, or of the isotropic medium,
+// lambda0 delta_cd tr(grad u) + mu0 (grad_d u_c + grad_c u_d) (Section 3.2.3).
+template <typename T>
+__device__ __forceinline__ T ref_flux(const T (&Gm)[3][3], int c, int d, T lam0, T mu0, bool iso) {
+  if (iso) return (c == d ? lam0 * (Gm[0][0] + Gm[1][1] + Gm[2][2]) : (T)0) + mu0 * (Gm[c][d] + Gm[d][c]);
+  return ((T)2 * mu0 + (c == d ? lam0 : (T)0)) * Gm[c][d];
+}
+
 template <typename T, bool MIX, int SCHEME, bool FS>
 __global__ void __launch_bounds__(RTX * RTY)
 k_residual(ResidualArgs a) {
@@ -127,6 +136,7 @@ k_residual(ResidualArgs a) {
   }
   const double h = g.h;
   const T lam0 = (T)a.lam0, mu0 = (T)a.mu0;
+  const bool iso = g.ref_iso != 0;
   T eps[3][3];
   #pragma unroll
   for (int p = 0; p < 3; ++p)
@@ -268,7 +278,7 @@ k_residual(ResidualArgs a) {
             for (int c = 0; c < 3; ++c)
               #pragma unroll
               for (int d = 0; d < 3; ++d)
-                V.tau[t][3 * c + d] = ((T)2 * mu0 + (c == d ? lam0 : (T)0)) * G[t][c][d];
+                V.tau[t][3 * c + d] = ref_flux<T>(G[t], c, d, lam0, mu0, iso);
           }
           if (own) acc_s2 += ((NIP == 2) ? 0.5 : 1.0) * s2;
           continue;
@@ -287,7 +297,7 @@ k_residual(ResidualArgs a) {
           for (int c = 0; c < 3; ++c)
             #pragma unroll
             for (int d = 0; d < 3; ++d)
-              V.tau[t][3 * c + d] = ((T)2 * mu0 + (c == d ? lam0 : (T)0)) * G[t][c][d];
+              V.tau[t][3 * c + d] = ref_flux<T>(G[t], c, d, lam0, mu0, iso);
         }
         if (own) {
           double w = (NIP == 2) ? 0.5 : 1.0;
@@ -327,7 +337,7 @@ k_residual(ResidualArgs a) {
           for (int c = 0; c < 3; ++c)
             #pragma unroll
             for (int d = 0; d < 3; ++d)
-              V.tau[t][3 * c + d] = ((T)2 * mu0 + (c == d ? lam0 : (T)0)) * GD[t][c][d];
+              V.tau[t][3 * c + d] = ref_flux<T>(GD[t], c, d, lam0, mu0, iso);
       }
     }
   };

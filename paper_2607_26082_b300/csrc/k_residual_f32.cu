@@ -75,6 +75,12 @@ __device__ __forceinline__ float fdiff(float ph, float pl, float qh, float ql) {
   return __fadd_rn(__fsub_rn(ph, qh), __fsub_rn(pl, ql));
 }
 
+// Reference flux tau = R0 : grad u, Paux or isotropic medium (Section 3.2.3).
+__device__ __forceinline__ float ref_flux(const float (&Gm)[3][3], int c, int d, float lam0, float mu0, bool iso) {
+  if (iso) return (c == d ? lam0 * (Gm[0][0] + Gm[1][1] + Gm[2][2]) : 0.f) + mu0 * (Gm[c][d] + Gm[d][c]);
+  return (2.f * mu0 + (c == d ? lam0 : 0.f)) * Gm[c][d];
+}
+
 }  // namespace
 
 template <int SCHEME, bool FS>
@@ -134,6 +140,7 @@ k_residual_f32(ResidualArgs a) {
     tau_on = false;
   }
   const float lam0 = a.f_lam0, mu0 = a.f_mu0;
+  const bool iso = g.ref_iso != 0;
   const float inv2h = a.f_inv2h, inv4h = a.f_inv4h;
   const float c4h = inv4h;
   const float (&eps)[3][3] = a.f_eps;
@@ -334,7 +341,7 @@ k_residual_f32(ResidualArgs a) {
                 #pragma unroll
                 for (int dd = 0; dd < 3; ++dd)
                   o[(NS + 3 * c + dd) * NVL] =
-                      (2.f * mu0 + (c == dd ? lam0 : 0.f)) * (tau_from_delta ? GD[c][dd] : G[c][dd]);
+                      (tau_from_delta ? ref_flux(GD, c, dd, lam0, mu0, iso) : ref_flux(G, c, dd, lam0, mu0, iso));
             }
             if (own) acc_s2.add(w * s2);
             continue;
@@ -360,7 +367,7 @@ k_residual_f32(ResidualArgs a) {
               #pragma unroll
               for (int dd = 0; dd < 3; ++dd)
                 o[(NS + 3 * c + dd) * NVL] =
-                    (2.f * mu0 + (c == dd ? lam0 : 0.f)) * (tau_from_delta ? GD[c][dd] : G[c][dd]);
+                    (tau_from_delta ? ref_flux(GD, c, dd, lam0, mu0, iso) : ref_flux(G, c, dd, lam0, mu0, iso));
           }
           if (own) acc_s2.add(w * (sxx * sxx + syy * syy + szz * szz + 2.f * (syz * syz + sxz * sxz + sxy * sxy)));
         }

@@ -17,6 +17,8 @@
 // (TETRA2: S_j = (1 + c_k c_l - c_j c_k - c_j c_l)/h^2; HEX1: S_j = (1-c_j)(1+c_k)(1+c_l)/(2h^2),
 // c_j = cos q_j; evaluated through sin^2(q_j/2) and cos^2(q_j/2)), zeroing null modes
 // (a_c <= threshold).
+#include <algorithm>
+
 #include "dtt_internal.cuh"
 
 namespace dtt {
@@ -287,6 +289,104 @@ int launch_green_multiply(const GridDev& g, T* spec, const TransformTables& tt, 
   k_green<T><<<grd, 128, 0, s>>>(g, spec, gt, tt.lam0, tt.mu0, ctrl);
   return (int)cudaGetLastError();
 }
+
+// Green step of the isotropic reference medium R0 : grad u = lambda0 tr(grad u) 1 +
+// mu0 (grad u + grad u^T) (Section 3.2.3; Eq. 4 for HEX1 in the periodic case).  With
+// normal mixed conditions every component's DTT basis function of wave vector q is mapped
+// by A0 onto the same q of every component, so A0 is a symmetric 3 x 3 matrix per
+// position:
+//     M_cc = (lambda0 + mu0) S_c + mu0 (S_x + S_y + S_z),
+//     M_cd = sign_c sign_d (lambda0 + mu0) T_cd            (c != d),
+// with the scheme's S_j (as in k_green) and the cross symbols
+//     TETRA2: T_cd = sin q_c sin q_d / h^2,  HEX1: T_cd = sin q_c sin q_d cos^2(q_e / 2) / h^2
+// (e the third axis; both from the schemes' gradients, and real because both stencils are
+// centrosymmetric).  In the quarter units of the tables (4 / h^2 factored out):
+// sin q_c sin q_d / 4 = sqrt(s_c c'_c s_d c'_d).  A component without a mode at the position,
+// or whose diagonal vanishes (a null mode, where all its cross terms vanish too), keeps
+// a zero coefficient; the rest is solved by LDL^T (symmetric positive definite).
+template <typename T>
+__global__ void k_green_iso(const GridDev g, T* __restrict__ spec, IsoTables it, double lam0, double mu0,
+                            const Ctrl* ctrl) {
+  if (ctrl && ctrl->done) return;
+  const long long NN = g.nnodes;
+  const T ih2 = (T)(4.0 / (g.h * g.h));
+  const T lm = (T)(lam0 + mu0), m0 = (T)mu0;
+  const T thr = (T)it.null_thr;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(n % g.nn[0]);
+    const long long r = n / g.nn[0];
+    const int j = (int)(r % g.nn[1]);
+    const int k = (int)(r / g.nn[1]);
+    const int valid = it.valid[0][i] & it.valid[1][j] & it.valid[2][k];
+    T sv[3], cv[3];
+    const int pos[3] = {i, j, k};
+    #pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if constexpr (sizeof(T) == 4) { sv[d] = it.sf[d][pos[d]]; cv[d] = it.cf[d][pos[d]]; }
+      else { sv[d] = (T)it.s[d][pos[d]]; cv[d] = (T)it.c[d][pos[d]]; }
+    }
+    T S[3];
+    if (g.scheme == SCHEME_TETRA2) {
+      S[0] = tetra_S<T>(sv[0], cv[1], sv[1], cv[0], sv[2]);
+      S[1] = tetra_S<T>(sv[1], cv[2], sv[2], cv[1], sv[0]);
+      S[2] = tetra_S<T>(sv[2], cv[0], sv[0], cv[2], sv[1]);
+    } else {
+      S[0] = sv[0] * cv[1] * cv[2];
+      S[1] = sv[1] * cv[0] * cv[2];
+      S[2] = sv[2] * cv[0] * cv[1];
+    }
+    T rt[3];   // sqrt(s c'): sin q / 2
+    #pragma unroll
+    for (int d = 0; d < 3; ++d) rt[d] = sqrt(sv[d] * cv[d]);
+    const T Ssum = S[0] + S[1] + S[2];
+    T M[3][3], b[3];
+    bool on[3];
+    #pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      M[c][c] = lm * S[c] + m0 * Ssum;
+      on[c] = ((valid >> c) & 1) && M[c][c] * ih2 > thr;
+      b[c] = on[c] ? spec[(long long)c * NN + n] : (T)0;
+    }
+    #pragma unroll
+    for (int c = 0; c < 3; ++c)
+      #pragma unroll
+      for (int d = c + 1; d < 3; ++d) {
+        const int e = 3 - c - d;
+        T t = rt[c] * rt[d];
+        if (g.scheme != SCHEME_TETRA2) t *= cv[e];
+        t *= (T)(it.sign[c] * it.sign[d]) * lm;
+        if (!on[c] || !on[d]) t = (T)0;
+        M[c][d] = t;
+        M[d][c] = t;
+      }
+    #pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (!on[c]) M[c][c] = (T)1;
+    // LDL^T of the symmetric positive definite M, then the two triangular solves
+    const T D0 = M[0][0];
+    const T L10 = M[1][0] / D0, L20 = M[2][0] / D0;
+    const T D1 = M[1][1] - L10 * M[1][0];
+    const T L21 = (M[2][1] - L20 * M[1][0]) / D1;
+    const T D2 = M[2][2] - L20 * M[2][0] - L21 * L21 * D1;
+    const T y0 = b[0], y1 = b[1] - L10 * y0, y2 = b[2] - L20 * y0 - L21 * y1;
+    const T x2 = y2 / D2;
+    const T x1 = y1 / D1 - L21 * x2;
+    const T x0 = y0 / D0 - L10 * x1 - L20 * x2;
+    const T x[3] = {x0, x1, x2};
+    #pragma unroll
+    for (int c = 0; c < 3; ++c) spec[(long long)c * NN + n] = on[c] ? x[c] / ih2 : (T)0;
+  }
+}
+
+template <typename T>
+int launch_green_iso(const GridDev& g, T* spec, const TransformTables& tt, const Ctrl* ctrl, cudaStream_t s) {
+  const long long nb = std::min<long long>((g.nnodes + 255) / 256, 148LL * 16);
+  k_green_iso<T><<<(int)nb, 256, 0, s>>>(g, spec, tt.iso, tt.lam0, tt.mu0, ctrl);
+  return (int)cudaGetLastError();
+}
+
+template int launch_green_iso<double>(const GridDev&, double*, const TransformTables&, const Ctrl*, cudaStream_t);
+template int launch_green_iso<float>(const GridDev&, float*, const TransformTables&, const Ctrl*, cudaStream_t);
 
 // u~ <- u~ + delta (Green step in increment form: G(p~) = u~ + G(p~ - A0 u~)).
 template <typename T>

@@ -19,6 +19,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 INIT_ZERO, INIT_PREVIOUS, INIT_GUESS = 0, 1, 2
 ACV_U, ACV_P = 0, 1
 SMALL_STRAIN, FINITE_STRAIN = 0, 1
+MEDIUM_PAUX, MEDIUM_ISOTROPIC = 0, 1
 
 
 class DttError(RuntimeError):
@@ -56,7 +57,7 @@ EXPORTS = ["dtt_grid_create", "dtt_grid_destroy", "dtt_grid_sizes", "dtt_set_mat
            "dtt_set_reference", "dtt_set_load", "dtt_set_constraints", "dtt_set_indenter",
            "dtt_move_indenter", "dtt_clear_indenter", "dtt_set_initial", "dtt_solve_step",
            "dtt_get_history", "dtt_get_fields", "dtt_get_reactions", "dtt_get_contact",
-           "dtt_set_kinematics", "dtt_get_stress_tensor", "dtt_get_min_jacobian",
+           "dtt_set_kinematics", "dtt_get_stress_tensor", "dtt_get_min_jacobian", "dtt_set_reference_medium",
            "dtt_apply_residual", "dtt_apply_green", "dtt_apply_green_noalloc", "dtt_transform",
            "dtt_profile_iteration", "dtt_autotune", "dtt_set_tuning", "dtt_batch_solve",
            "dtt_last_error", "dtt_version"]
@@ -90,6 +91,7 @@ def lib():
     L.dtt_get_history.argtypes = [P, P, C.POINTER(i32)]
     L.dtt_get_fields.argtypes = [P, P, P, i32]
     L.dtt_set_kinematics.argtypes = [P, i32]
+    L.dtt_set_reference_medium.argtypes = [P, i32]
     L.dtt_get_stress_tensor.argtypes = [P, P, i32]
     L.dtt_get_min_jacobian.argtypes = [P, C.POINTER(f64)]
     L.dtt_get_reactions.argtypes = [P, P, P]
@@ -229,6 +231,9 @@ class Grid:
         ps, _ = _ptr(s)
         _check(lib().dtt_get_fields(self._h, pu, ps, dev))
         return (u, s) if sigma else u
+
+    def dtt_set_reference_medium(self, medium):
+        _check(lib().dtt_set_reference_medium(self._h, int(medium)))
 
     def dtt_set_kinematics(self, kinematics):
         _check(lib().dtt_set_kinematics(self._h, int(kinematics)))

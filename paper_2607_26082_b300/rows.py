@@ -118,8 +118,8 @@ def csr_from_intents(nvox, bc, intents):
 
 def setup_grid(spec, precision, stream=None):
     """Create and configure a Grid from a mapping with keys nvox, h, bc, scheme, phase,
-    lam, mu, eps_star, lam0, mu0, intents (and optionally indenter, and kinematics "SS" or
-    "FS")."""
+    lam, mu, eps_star, lam0, mu0, intents (and optionally indenter, kinematics "SS" or
+    "FS", and medium "paux" or "iso")."""
     from . import dtt
     g = dtt.Grid(spec["nvox"], spec["h"], spec["bc"], spec["scheme"], precision, stream)
     g.dtt_set_material(spec["phase"], spec["lam"], spec["mu"])
@@ -127,6 +127,8 @@ def setup_grid(spec, precision, stream=None):
     g.dtt_set_load(np.asarray(spec.get("eps_star", np.zeros((3, 3)))))
     if spec.get("kinematics", "SS") == "FS":
         g.dtt_set_kinematics(dtt.FINITE_STRAIN)
+    if spec.get("medium", "paux") == "iso":
+        g.dtt_set_reference_medium(dtt.MEDIUM_ISOTROPIC)
     if spec.get("intents"):
         ptr, node, comp, a, b, val = csr_from_intents(spec["nvox"], spec["bc"], spec["intents"])
         g.dtt_set_constraints(ptr, node, comp, a, b, val)

@@ -124,6 +124,42 @@ def ct_plate(nx=128, ny=128, nz=32, scheme=TETRA2, notch_scale=0.0, r0_factor=1.
                     ligament_rows=(nz + 1) * (nx + 1 - xn))
 
 
+def normal_mixed_bc(normal):
+    """bc[axis][face][component] from normal[axis][face] in (D, N): the normal component takes
+    that condition and the tangential components the other one (sliding wall or its
+    reverse, the conditions of the isotropic reference medium, Section 3.2.3)."""
+    bc = np.zeros((3, 2, 3), dtype=np.int64)
+    for d in range(3):
+        for f in range(2):
+            for c in range(3):
+                bc[d, f, c] = normal[d][f] if c == d else (N if normal[d][f] == D else D)
+    return bc
+
+
+def iso_cell(seed, nvox=(12, 10, 8), scheme=TETRA2, n_strong=3, eps_scale=1e-3, contrast=4.0):
+    """Two-phase cell for the isotropic reference medium: every face normal mixed (drawn at
+    random), a random two-phase map of stiffness ratio `contrast` (nu = 0.3), random eps*,
+    and up to n_strong interior strong rows on components that have a Dirichlet face.
+    Reference media: (lambda0, mu0) = the mean of the phases' Lame coefficients."""
+    rng = np.random.default_rng(seed)
+    normal = rng.choice([D, N], size=(3, 2))
+    bc = normal_mixed_bc(normal)
+    phase = (rng.random((nvox[2], nvox[1], nvox[0])) < 0.35).astype(np.uint8)
+    lam, mu = lame(np.array([1.0, contrast]), 0.3)
+    e = rng.uniform(-eps_scale, eps_scale, size=(3, 3))
+    intents = []
+    for _ in range(n_strong):
+        c = int(rng.integers(0, 3))
+        if not (bc[:, :, c] == D).any():
+            continue
+        ijk = tuple(int(rng.integers(1, nvox[d])) for d in range(3))
+        if all(it["ijk"] != ijk or it["comp"] != c for it in intents):
+            intents.append(dict(kind="strong", ijk=ijk, comp=c, value=float(rng.uniform(-1e-3, 1e-3))))
+    return Workload(name="normal-mixed two-phase cell %dx%dx%d" % tuple(nvox), nvox=tuple(nvox), h=1.0, bc=bc,
+                    scheme=scheme, phase=phase, lam=lam, mu=mu, eps_star=0.5 * (e + e.T), intents=intents,
+                    lam0=float(lam.mean()), mu0=float(mu.mean()), tol=1e-6, acv_mod=2, medium="iso")
+
+
 CT_LOADS = ("strong_line", "weak_line", "strong_node", "weak_node", "smooth_node")
 
 
