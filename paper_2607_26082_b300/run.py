@@ -1,9 +1,10 @@
 """Command-line runner: solve one of the synthetic workloads with the CUDA path.
 
-  python -m paper_2607_26082_b300.run --workload ct|ct_paper|cube16|indent|indent_cube [--precision mixed|fp64]
+  python -m paper_2607_26082_b300.run --workload ct|ct_paper|cube16|indent|indent_cube|iso_cell [--precision mixed|fp64]
          [--iters K | --tol T] [--steps S] [--graph-iters G] [--nvox nx,ny,nz]
          [--kinematics ss|fs] [--r0-scale K] [--load-steps N] [--max-iter M] [--stop-on-fail]
          [--ct-load strong_line|weak_line|strong_node|weak_node|smooth_node] [--acv-on u|p] [--acv-mod M]
+         [--medium paux|iso] [--scheme tetra2|hex1] [--contrast K]
   python -m paper_2607_26082_b300.run --workload batch [--cells N] [--seed0 S] [--no-tune]
          [--sequential]
 
@@ -19,7 +20,10 @@ increments (default 10); --max-iter caps the iterations of each step (default 20
 --stop-on-fail ends the run at the first step that does not converge.  ct_paper is the
 paper's 10 x 100 x (50 + 1) CT-like specimen with the loading --ct-load; it reports the
 reactions of the load rows and of the ligament rows and their balance.  --acv-on and
---acv-mod override the workload's Anderson settings.  --iters K runs
+--acv-mod override the workload's Anderson settings.  iso_cell is a two-phase cell with
+normal mixed conditions on every face (--nvox, --seed0, --contrast: stiffness ratio of
+the phases); --medium picks the reference medium
+(Section 3.2.3) and --scheme the discretisation for any workload.  --iters K runs
 exactly K iterations (tolerance 0) of the first load step, which is the
 short, fixed launch sequence a profiler wants; --tol runs to convergence.  For the
 indentation block every load step moves the sphere (Algorithm 2, one increment each),
@@ -41,7 +45,7 @@ import workloads as wl  # noqa: E402
 from . import dtt, rows  # noqa: E402
 
 
-def make_workload(name, nvox=None, load_steps=10):
+def make_workload(name, nvox=None, load_steps=10, contrast=4.0):
     """ct: half compact-tension-like specimen 128x128x32; cube16: 16^3 cube with pinned
     nodes; indent: sphere indentation of a 256x256x128 block, R = 64.  nvox rescales ct and
     indent (the indenter radius scales with the block); indent_cube: Section 5.4's 65^3 cube
@@ -52,6 +56,8 @@ def make_workload(name, nvox=None, load_steps=10):
         return wl.cube16()
     if name.startswith("ct_paper:"):
         return wl.ct_specimen(name.split(":", 1)[1])
+    if name.startswith("iso_cell:"):
+        return wl.iso_cell(int(name.split(":", 1)[1]), nvox=nvox or (128, 128, 128), n_strong=0, contrast=contrast)
     if name == "indent_cube":
         return wl.indentation_cube(nvox[0] if nvox else 65, steps=load_steps, dmax=0.2)
     if name == "indent":
@@ -100,7 +106,11 @@ def run_batch(a, prec):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="ct", choices=["ct", "ct_paper", "cube16", "indent", "indent_cube", "batch"])
+    ap.add_argument("--workload", default="ct",
+                    choices=["ct", "ct_paper", "cube16", "indent", "indent_cube", "iso_cell", "batch"])
+    ap.add_argument("--medium", default=None, choices=["paux", "iso"])
+    ap.add_argument("--scheme", default=None, choices=["tetra2", "hex1"])
+    ap.add_argument("--contrast", type=float, default=4.0)
     ap.add_argument("--ct-load", default="strong_line", choices=list(wl.CT_LOADS))
     ap.add_argument("--acv-on", default="p", choices=["u", "p"])
     ap.add_argument("--acv-mod", type=int, default=0, help="0: the workload's")
@@ -123,9 +133,16 @@ def main(argv=None):
     if a.workload == "batch":
         return run_batch(a, dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64)
     wname = "ct_paper:" + a.ct_load if a.workload == "ct_paper" else a.workload
-    spec = make_workload(wname, tuple(int(v) for v in a.nvox.split(",")) if a.nvox else None, a.load_steps)
+    if a.workload == "iso_cell":
+        wname = "iso_cell:%d" % a.seed0
+    spec = make_workload(wname, tuple(int(v) for v in a.nvox.split(",")) if a.nvox else None, a.load_steps,
+                         a.contrast)
     prec = dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64
     spec["kinematics"] = a.kinematics.upper()
+    if a.medium:
+        spec["medium"] = a.medium
+    if a.scheme:
+        spec["scheme"] = wl.TETRA2 if a.scheme == "tetra2" else wl.HEX1
     spec["lam0"] = a.r0_scale * spec["lam0"]
     spec["mu0"] = a.r0_scale * spec["mu0"]
     g = rows.setup_grid(spec, prec)
@@ -142,6 +159,7 @@ def main(argv=None):
                                acv_on=dtt.ACV_P if a.acv_on == "p" else dtt.ACV_U,
                                init=dtt.INIT_PREVIOUS if s else dtt.INIT_ZERO, graph_iters=a.graph_iters)
         out = {"workload": spec["name"], "precision": a.precision, "kinematics": a.kinematics, "step": s,
+               "medium": spec.get("medium", "paux"), "scheme": "tetra2" if spec["scheme"] == wl.TETRA2 else "hex1",
                "acv_on": a.acv_on, "acv_mod": a.acv_mod or spec["acv_mod"]}
         out.update(rep.as_dict())
         if "ligament_rows" in spec and g.n_rows:
