@@ -416,18 +416,28 @@ k_fft_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenT
 //
 // L / 8 threads own one complex sequence; each radix-8 pass (radix 4 or 2 for the last
 // factor) loads 8 values per thread from shared memory, applies the Stockham twiddles and a
-// DFT in registers, and writes back in place between two barriers.  The sequence lives in
-// shared memory as separate real and imaginary arrays with one padding word per 32, so the
-// strided writes of the first passes hit distinct banks.  256 threads: 2048 / L sequences
-// (twice as many real pencils) per CTA.
-
-__device__ __forceinline__ int padi(int i) { return i + (i >> 5); }
+// DFT in registers, and writes back in place between two barriers.  The sequences live in
+// shared memory as a real and an imaginary array; FastMap<L> places element i of sequence
+// seq so that the warps' strided accesses (the Stockham writes, the column-wise fills and
+// reads of several pencils at one position) spread over the 32 banks.  256 threads:
+// 2048 / L sequences (twice as many real pencils) per CTA.
 
 template <int L>
 struct FastPlan {
   static constexpr int NT = L / 8;        // threads per sequence
   static constexpr int SEQ = 2048 / L;    // sequences per CTA
-  static constexpr int PADL = L + L / 32; // padded words per component of one sequence
+};
+
+// Shared-memory word of element i of sequence seq in array arr (0 real, 1 imaginary).
+// Padded form: seq * PADL + i + (i >> S) * A, PADL = L + (L >> S) * A + EXTRA, the
+// imaginary array ARR = SEQ * PADL + OFF words after the real one.
+template <int L>
+struct FastMap {
+  static constexpr int S = 5, A = 1, EXTRA = 0, OFF = 0;
+  static constexpr int PADL = L + (L >> S) * A + EXTRA;
+  static constexpr int ARR = FastPlan<L>::SEQ * PADL + OFF;
+  static constexpr int WORDS = (2 * ARR + 3) & ~3;   // both arrays, 16-byte multiple
+  __device__ static __forceinline__ int at(int arr, int seq, int i) { return arr * ARR + seq * PADL + i + (i >> S) * A; }
 };
 
 // 8-point DFT with kernel e^{s 2 pi i j k / 8}, natural-order output (decimation in
@@ -475,12 +485,11 @@ __device__ __forceinline__ void dft8(Cx<T>* v, int s) {
 // sequence `seq` takes butterflies t, t + NT, ... (8 / R of them).  With `mod`, the inputs
 // are first multiplied by mod[index] (quarter-wave modulation of the forward transforms).
 template <typename T, int L, int R, int NS>
-__device__ __forceinline__ void fast_pass(T* re, T* im, const Cx<T>* __restrict__ tw, int sgn, int seq, int t,
+__device__ __forceinline__ void fast_pass(T* buf, const Cx<T>* __restrict__ tw, int sgn, int seq, int t,
                                           const Cx<T>* __restrict__ mod) {
-  constexpr int NT = FastPlan<L>::NT, PADL = FastPlan<L>::PADL;
+  using M = FastMap<L>;
+  constexpr int NT = FastPlan<L>::NT;
   constexpr int LR = L / R, PER = 8 / R, TWS = L / (NS * R);
-  T* sr = re + seq * PADL;
-  T* si = im + seq * PADL;
   Cx<T> v[PER][R];
   #pragma unroll
   for (int m = 0; m < PER; ++m) {
@@ -489,7 +498,7 @@ __device__ __forceinline__ void fast_pass(T* re, T* im, const Cx<T>* __restrict_
     #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int idx = jb + r * LR;
-      v[m][r] = {sr[padi(idx)], si[padi(idx)]};
+      v[m][r] = {buf[M::at(0, seq, idx)], buf[M::at(1, seq, idx)]};
       if (mod) v[m][r] = cmul(v[m][r], mod[idx]);
     }
     if (NS > 1) {
@@ -513,8 +522,8 @@ __device__ __forceinline__ void fast_pass(T* re, T* im, const Cx<T>* __restrict_
     #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int idx = o + r * NS;
-      sr[padi(idx)] = v[m][r].x;
-      si[padi(idx)] = v[m][r].y;
+      buf[M::at(0, seq, idx)] = v[m][r].x;
+      buf[M::at(1, seq, idx)] = v[m][r].y;
     }
   }
   __syncthreads();
@@ -522,58 +531,57 @@ __device__ __forceinline__ void fast_pass(T* re, T* im, const Cx<T>* __restrict_
 
 // Whole FFT of length L: radix-8 passes, then one radix-4 or radix-2 pass for the rest.
 template <typename T, int L, int NS = 1>
-__device__ __forceinline__ void fast_fft(T* re, T* im, const Cx<T>* tw, int sgn, int seq, int t,
-                                         const Cx<T>* mod) {
+__device__ __forceinline__ void fast_fft(T* buf, const Cx<T>* tw, int sgn, int seq, int t, const Cx<T>* mod) {
   if constexpr (NS * 8 <= L) {
-    fast_pass<T, L, 8, NS>(re, im, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
-    fast_fft<T, L, NS * 8>(re, im, tw, sgn, seq, t, nullptr);
+    fast_pass<T, L, 8, NS>(buf, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
+    fast_fft<T, L, NS * 8>(buf, tw, sgn, seq, t, nullptr);
   } else if constexpr (NS * 4 == L) {
-    fast_pass<T, L, 4, NS>(re, im, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
+    fast_pass<T, L, 4, NS>(buf, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
   } else if constexpr (NS * 2 == L) {
-    fast_pass<T, L, 2, NS>(re, im, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
+    fast_pass<T, L, 2, NS>(buf, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
   }
 }
 
 // Value v of real pencil pb at axis position j into the extended sequence of its pair (the
-// same extensions as fill_sequences), in the padded real / imaginary arrays.
+// same extensions as fill_sequences), in the real / imaginary arrays of the buffer.
 template <typename T, int L>
-__device__ __forceinline__ void fast_place(T* re, T* im, int pb, int j, T v, int n, int type, int inverse) {
-  constexpr int PADL = FastPlan<L>::PADL;
-  T* S = ((pb & 1) ? im : re) + (pb >> 1) * PADL;
+__device__ __forceinline__ void fast_place(T* buf, int pb, int j, T v, int n, int type, int inverse) {
+  const int arr = pb & 1, seq = pb >> 1;
+  auto S = [&](int i) -> T& { return buf[FastMap<L>::at(arr, seq, i)]; };
   const bool quarter = (type == T_DCT3 || type == T_DST3);
   if (!inverse || !quarter) {
     switch (type) {
       case T_DCT1:
-        S[padi(j)] = v;
-        if (j >= 1 && j <= n - 1) S[padi(2 * n - j)] = v;
+        S(j) = v;
+        if (j >= 1 && j <= n - 1) S(2 * n - j) = v;
         break;
       case T_DST1:
-        if (j >= 1 && j <= n - 1) { S[padi(j)] = v; S[padi(2 * n - j)] = -v; }
+        if (j >= 1 && j <= n - 1) { S(j) = v; S(2 * n - j) = -v; }
         break;
       case T_DCT3:
-        if (j <= n - 1) { S[padi(j)] = v; if (j >= 1) S[padi(2 * n - j)] = -v; }
+        if (j <= n - 1) { S(j) = v; if (j >= 1) S(2 * n - j) = -v; }
         break;
       case T_DST3:
-        if (j >= 1) { S[padi(j)] = v; if (j <= n - 1) S[padi(2 * n - j)] = v; }
+        if (j >= 1) { S(j) = v; if (j <= n - 1) S(2 * n - j) = v; }
         break;
       default:
-        S[padi(j)] = v;
+        S(j) = v;
         break;
     }
   } else if (j < n) {
-    S[padi(j)] = v;
-    S[padi(2 * n - 1 - j)] = type == T_DCT3 ? v : -v;
+    S(j) = v;
+    S(2 * n - 1 - j) = type == T_DCT3 ? v : -v;
   }
 }
 
 // Transform value of pencil pb at position k from the FFT result of its pair (post_value on
 // the padded arrays).
 template <typename T, int L>
-__device__ __forceinline__ T fast_post(const T* re, const T* im, int pb, int k, int n, int type, int inverse, T sc,
+__device__ __forceinline__ T fast_post(const T* buf, int pb, int k, int n, int type, int inverse, T sc,
                                        const Cx<T>* ph, T inv_n) {
-  constexpr int PADL = FastPlan<L>::PADL;
-  const T* yr = re + (pb >> 1) * PADL;
-  const T* yi = im + (pb >> 1) * PADL;
+  const int seq = pb >> 1;
+  auto yr = [&](int i) { return buf[FastMap<L>::at(0, seq, i)]; };
+  auto yi = [&](int i) { return buf[FastMap<L>::at(1, seq, i)]; };
   const bool imf = pb & 1;
   const T half = (T)0.5;
   const bool quarter = (type == T_DCT3 || type == T_DST3);
@@ -581,20 +589,20 @@ __device__ __forceinline__ T fast_post(const T* re, const T* im, int pb, int k, 
     T val = (T)0;
     switch (type) {
       case T_DCT1:
-        val = half * (imf ? yi[padi(k)] : yr[padi(k)]);
+        val = half * (imf ? yi(k) : yr(k));
         break;
       case T_DST1:
-        if (k >= 1 && k <= n - 1) val = imf ? half * yr[padi(k)] : -half * yi[padi(k)];
+        if (k >= 1 && k <= n - 1) val = imf ? half * yr(k) : -half * yi(k);
         break;
       case T_DCT3:
-        if (k <= n - 1) val = half * (imf ? yi[padi(k)] : yr[padi(k)]);
+        if (k <= n - 1) val = half * (imf ? yi(k) : yr(k));
         break;
       case T_DST3:
-        if (k <= n - 1) val = imf ? half * yr[padi(k)] : -half * yi[padi(k)];
+        if (k <= n - 1) val = imf ? half * yr(k) : -half * yi(k);
         break;
       default: {
         const int kk = k == 0 ? 0 : n - k;
-        const T ax = yr[padi(k)], ay = yi[padi(k)], bx = yr[padi(kk)], by = yi[padi(kk)];
+        const T ax = yr(k), ay = yi(k), bx = yr(kk), by = yi(kk);
         val = imf ? half * (ax - bx + ay + by) : half * (ax + bx - ay + by);
         break;
       }
@@ -602,14 +610,14 @@ __device__ __forceinline__ T fast_post(const T* re, const T* im, int pb, int k, 
     return val * sc;
   }
   const Cx<T> w = {ph[k].x, -ph[k].y};
-  const Cx<T> e = cmul(Cx<T>{yr[padi(k)], yi[padi(k)]}, w);
+  const Cx<T> e = cmul(Cx<T>{yr(k), yi(k)}, w);
   if (type == T_DCT3) return (k <= n - 1) ? (imf ? e.y : e.x) * inv_n : (T)0;
   return (k >= 1) ? (imf ? -e.x : e.y) * inv_n : (T)0;
 }
 
 template <typename T, int L>
 __host__ __device__ constexpr size_t fast_smem(int extra_bytes) {
-  return (size_t)2 * FastPlan<L>::SEQ * FastPlan<L>::PADL * sizeof(T) + (size_t)L * sizeof(Cx<T>) +
+  return (size_t)FastMap<L>::WORDS * sizeof(T) + (size_t)L * sizeof(Cx<T>) +
          (size_t)extra_bytes;
 }
 
@@ -617,14 +625,13 @@ __host__ __device__ constexpr size_t fast_smem(int extra_bytes) {
 template <typename T, int L>
 __global__ void __launch_bounds__(256)
 k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctrl* ctrl, void* const* in_ring) {
-  constexpr int SEQ = FastPlan<L>::SEQ, NT = FastPlan<L>::NT, PADL = FastPlan<L>::PADL, NPEN = 2 * SEQ;
+  constexpr int SEQ = FastPlan<L>::SEQ, NT = FastPlan<L>::NT, WORDS = FastMap<L>::WORDS, NPEN = 2 * SEQ;
   if (ctrl && ctrl->done) return;
   if (in_ring) in = (const T*)in_ring[ctrl->i_local % 4];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long sbase[NPEN];
-  T* re = (T*)smem_raw;
-  T* im = re + SEQ * PADL;
-  Cx<T>* tws = (Cx<T>*)(im + SEQ * PADL);
+  T* buf = (T*)smem_raw;
+  Cx<T>* tws = (Cx<T>*)(buf + WORDS);
   const int comp = p.comp0 + blockIdx.y;
   const int type = p.type[comp];
   const int tid = threadIdx.x;
@@ -636,7 +643,7 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   const int n = p.n, nn = p.nn;
   pencil_bases<T, SEQ>(sbase, p, pen0, tid);
   for (int q = tid; q < L; q += 256) tws[q] = ((const Cx<T>*)p.tw)[q];
-  for (int q = tid; q < 2 * SEQ * PADL; q += 256) re[q] = (T)0;
+  for (int q = tid; q < WORDS; q += 256) buf[q] = (T)0;
   __syncthreads();
   // global loads in groups of FB per thread before they are placed, so that several are in
   // flight at once
@@ -655,7 +662,7 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
         #pragma unroll
         for (int u = 0; u < FB; ++u) {
           const int j = j0 + 32 * u;
-          if (j < nn) fast_place<T, L>(re, im, pb, j, v[u], n, type, p.inverse);
+          if (j < nn) fast_place<T, L>(buf, pb, j, v[u], n, type, p.inverse);
         }
       }
     }
@@ -672,7 +679,7 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
       for (int u = 0; u < FB; ++u) {
         const int idx = i0 + 256 * u;
         const int pb = idx % NPEN, j = idx / NPEN;
-        if (idx < NPEN * nn && pb < npen) fast_place<T, L>(re, im, pb, j, v[u], n, type, p.inverse);
+        if (idx < NPEN * nn && pb < npen) fast_place<T, L>(buf, pb, j, v[u], n, type, p.inverse);
       }
     }
   }
@@ -680,11 +687,11 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   const bool quarter = (type == T_DCT3 || type == T_DST3);
   const int sgn = (p.inverse && quarter) ? 1 : -1;
   const Cx<T>* ph = (const Cx<T>*)p.ph;
-  fast_fft<T, L>(re, im, tws, sgn, tid / NT, tid % NT, (quarter && !p.inverse) ? ph : nullptr);
+  fast_fft<T, L>(buf, tws, sgn, tid / NT, tid % NT, (quarter && !p.inverse) ? ph : nullptr);
   const T sc = sizeof(T) == 4 ? (T)p.fscale : (T)p.scale;
   const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
   auto emit = [&](int pb, int k) {
-    const T v = fast_post<T, L>(re, im, pb, k, n, type, p.inverse, sc, ph, inv_n);
+    const T v = fast_post<T, L>(buf, pb, k, n, type, p.inverse, sc, ph, inv_n);
     const long long e = coff + sbase[pb] + k * stride;
     if (p.incr) add_to_u<T>(e, v, p);
     else out[e] = v;
@@ -707,14 +714,13 @@ template <typename T, int L>
 __global__ void __launch_bounds__(256, 5)
 k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenTables gt, T l0, T m2, T ih2,
                    int scheme, T zscale, const Ctrl* ctrl) {
-  constexpr int SEQ = FastPlan<L>::SEQ, NT = FastPlan<L>::NT, PADL = FastPlan<L>::PADL, NPEN = 2 * SEQ;
+  constexpr int SEQ = FastPlan<L>::SEQ, NT = FastPlan<L>::NT, WORDS = FastMap<L>::WORDS, NPEN = 2 * SEQ;
   if (ctrl && ctrl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long sbase[NPEN];
   __shared__ T pxy[NPEN][4];   // per pencil: s_x, c'_x, s_y, c'_y
-  T* re = (T*)smem_raw;
-  T* im = re + SEQ * PADL;
-  Cx<T>* tws = (Cx<T>*)(im + SEQ * PADL);
+  T* buf = (T*)smem_raw;
+  Cx<T>* tws = (Cx<T>*)(buf + WORDS);
   T* zs = (T*)(tws + L);   // s_z[k], k < nn
   T* zc = zs + p.nn;       // c'_z[k]
   T* spec = zc + p.nn;     // NPEN x nn spectra
@@ -742,7 +748,7 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
     zs[q] = gt_s<T>(gt, comp, 2, q);
     zc[q] = gt_c<T>(gt, comp, 2, q);
   }
-  for (int q = tid; q < 2 * SEQ * PADL; q += 256) re[q] = (T)0;
+  for (int q = tid; q < WORDS; q += 256) buf[q] = (T)0;
   __syncthreads();
   const bool quarter = (type == T_DCT3 || type == T_DST3);
   const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
@@ -759,18 +765,18 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
     for (int u = 0; u < 4; ++u) {
       const int idx = i0 + 256 * u;
       const int pb = idx % NPEN, j = idx / NPEN;
-      if (idx < NPEN * nn && pb < npen) fast_place<T, L>(re, im, pb, j, v[u], n, type, 0);
+      if (idx < NPEN * nn && pb < npen) fast_place<T, L>(buf, pb, j, v[u], n, type, 0);
     }
   }
   __syncthreads();
-  fast_fft<T, L>(re, im, tws, -1, tid / NT, tid % NT, quarter ? ph : nullptr);
+  fast_fft<T, L>(buf, tws, -1, tid / NT, tid % NT, quarter ? ph : nullptr);
   // Green multiply into spec
   const T thr = sizeof(T) == 4 ? (T)gt.null_thr_f[comp] : (T)gt.null_thr[comp];
   for (int idx = tid; idx < NPEN * nn; idx += 256) {
     const int pb = idx % NPEN, k = idx / NPEN;
     T v = (T)0;
     if (pb < npen) {
-      v = fast_post<T, L>(re, im, pb, k, n, type, 0, (T)1, ph, inv_n);
+      v = fast_post<T, L>(buf, pb, k, n, type, 0, (T)1, ph, inv_n);
       const T sx = pxy[pb][0], cx = pxy[pb][1], sy = pxy[pb][2], cy = pxy[pb][3];
       const T sz = zs[k], cz = zc[k];
       T Sx, Sy, Sz;
@@ -791,17 +797,17 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
   }
   __syncthreads();
   // inverse along z
-  for (int q = tid; q < 2 * SEQ * PADL; q += 256) re[q] = (T)0;
+  for (int q = tid; q < WORDS; q += 256) buf[q] = (T)0;
   __syncthreads();
   for (int idx = tid; idx < NPEN * nn; idx += 256) {
     const int pb = idx % NPEN, j = idx / NPEN;
-    if (pb < npen) fast_place<T, L>(re, im, pb, j, spec[pb * nn + j], n, type, 1);
+    if (pb < npen) fast_place<T, L>(buf, pb, j, spec[pb * nn + j], n, type, 1);
   }
   __syncthreads();
-  fast_fft<T, L>(re, im, tws, quarter ? 1 : -1, tid / NT, tid % NT, nullptr);
+  fast_fft<T, L>(buf, tws, quarter ? 1 : -1, tid / NT, tid % NT, nullptr);
   for (int idx = tid; idx < NPEN * nn; idx += 256) {
     const int pb = idx % NPEN, k = idx / NPEN;
-    if (pb < npen) out[coff + sbase[pb] + k * stride] = fast_post<T, L>(re, im, pb, k, n, type, 1, zscale, ph, inv_n);
+    if (pb < npen) out[coff + sbase[pb] + k * stride] = fast_post<T, L>(buf, pb, k, n, type, 1, zscale, ph, inv_n);
   }
 }
 
