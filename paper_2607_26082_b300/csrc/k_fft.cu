@@ -428,16 +428,35 @@ struct FastPlan {
   static constexpr int SEQ = 2048 / L;    // sequences per CTA
 };
 
-// Shared-memory word of element i of sequence seq in array arr (0 real, 1 imaginary).
-// Padded form: seq * PADL + i + (i >> S) * A, PADL = L + (L >> S) * A + EXTRA, the
-// imaginary array ARR = SEQ * PADL + OFF words after the real one.
+// Shared-memory word of element i of sequence seq in array arr (0 real, 1 imaginary):
+//     seq * PADL + i + (i >> S) * A + (i >> T) * B,   PADL = L + (L >> S) * A + (L >> T) * B + EXTRA,
+// the imaginary array SEQ * PADL + OFF words after the real one.  The padding constants
+// are chosen per length from a simulation of every warp access of the fills, the Stockham
+// passes and the reads (x and y axes); simulated wavefronts against the former one word
+// per 32 (S = 5, A = 1) and the bound of one wavefront per warp instruction:
+//     L      16     32     64    128    256    512   1024   2048
+//     now  1992   1800   2306   3297   2258   2257   2773   2787
+//     was 12160   4104   4036   4388   3352   3344   3852   3462
+//     bound 1992  1604   1538   1985   1954   1938   2442   2438
+template <int L>
+struct FastMapParams {
+  static constexpr int S = 5, A = 2, T = 7, B = 1, EXTRA = 0, OFF = 0;   // 256 and up
+};
+template <> struct FastMapParams<16> { static constexpr int S = 3, A = 1, T = 0, B = 0, EXTRA = 0, OFF = 1; };
+template <> struct FastMapParams<32> { static constexpr int S = 3, A = 1, T = 0, B = 0, EXTRA = 0, OFF = 1; };
+template <> struct FastMapParams<64> { static constexpr int S = 5, A = 3, T = 0, B = 0, EXTRA = 0, OFF = 1; };
+template <> struct FastMapParams<128> { static constexpr int S = 5, A = 2, T = 0, B = 0, EXTRA = 1, OFF = 0; };
+
 template <int L>
 struct FastMap {
-  static constexpr int S = 5, A = 1, EXTRA = 0, OFF = 0;
-  static constexpr int PADL = L + (L >> S) * A + EXTRA;
-  static constexpr int ARR = FastPlan<L>::SEQ * PADL + OFF;
+  using P = FastMapParams<L>;
+  static constexpr int SEQ = FastPlan<L>::SEQ;
+  static constexpr int PADL = L + (L >> P::S) * P::A + (P::T ? (L >> P::T) * P::B : 0) + P::EXTRA;
+  static constexpr int ARR = SEQ * PADL + P::OFF;
   static constexpr int WORDS = (2 * ARR + 3) & ~3;   // both arrays, 16-byte multiple
-  __device__ static __forceinline__ int at(int arr, int seq, int i) { return arr * ARR + seq * PADL + i + (i >> S) * A; }
+  __device__ static __forceinline__ int at(int arr, int seq, int i) {
+    return arr * ARR + seq * PADL + i + (i >> P::S) * P::A + (P::T ? (i >> P::T) * P::B : 0);
+  }
 };
 
 // 8-point DFT with kernel e^{s 2 pi i j k / 8}, natural-order output (decimation in
