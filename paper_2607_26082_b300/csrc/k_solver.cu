@@ -16,6 +16,8 @@
 //    x_i <- sum alpha_k (S_k + R_k).
 // All scalar decisions run in single-thread control kernels so that an iteration is a fixed
 // sequence of launches; every kernel returns at once when the solve is finished.
+#include <cstddef>
+
 #include "dtt_internal.cuh"
 
 namespace dtt {
@@ -623,7 +625,7 @@ __device__ __forceinline__ double reduce_fixed(const double* v, int n, int strid
 
 // Residual norms (Eq. 5), history and exit decision of one iteration (thread 0).
 __device__ void ctrl_residual_core(Ctrl* c, double s2, double p2, double q2, double c2, double ng, double nr,
-                                   double mm, double h, long long nnodes, long long nvox) {
+                                   double mm, double h, long long nnodes, long long nvox, double* hist) {
   double pt = p2 + q2 + c2;
   c->p2 = pt;
   c->s2 = s2;
@@ -631,7 +633,7 @@ __device__ void ctrl_residual_core(Ctrl* c, double s2, double p2, double q2, dou
   double r = (sn == 0.0) ? (pn == 0.0 ? 0.0 : INFINITY) : h * pn / sn;
   c->r = r;
   if (c->iter == 0) c->r0 = r;
-  if (c->hist_len < HIST) c->hist[c->hist_len++] = r;
+  if (c->hist_len < HIST) hist[c->hist_len++] = r;
   c->pslot = c->i_local % 4;
   c->n_vgap = (int)ng;
   c->n_vreact = (int)nr;
@@ -664,7 +666,7 @@ __global__ void k_ctrl_residual(Ctrl* c, const double* rp, int nres, const doubl
     mm = reduce_fixed(cp, ncont, CONT_STRIDE, 3, sh);
   }
   if (threadIdx.x != 0) return;
-  ctrl_residual_core(c, s2, p2, q2, c2, ng, nr, mm, h, nnodes, nvox);
+  ctrl_residual_core(c, s2, p2, q2, c2, ng, nr, mm, h, nnodes, nvox, c->hist);
 }
 
 __global__ void k_ctrl_contact(Ctrl* c) {
@@ -764,14 +766,24 @@ __global__ void k_ctrl_acv_fused(Ctrl* c, const double* rp, int nres, const doub
 }
 
 // k_ctrl_residual followed by k_ctrl_acv_fused in one launch (iterations without contact,
-// where nothing runs between the two); both reductions in one pass each.
+// where nothing runs between the two); both reductions in one pass each.  The control
+// state except the residual history is staged in shared memory by one parallel copy, so
+// that thread 0's sequential logic (the Eq. 5 test, the Gram update, the 4 x 4 solve) does
+// not wait on a global-memory round trip per field; it is written back the same way.
+constexpr int CTRL_HEAD_WORDS = (int)(offsetof(Ctrl, hist) / sizeof(double));
+static_assert(offsetof(Ctrl, hist) % sizeof(double) == 0, "Ctrl head must be a whole number of doubles");
+
 __global__ void k_ctrl_residual_acv(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, double h,
                                     long long nnodes, long long nvox) {
   __shared__ double sh[RES_STRIDE][SB / 32];
   __shared__ double rs[RES_STRIDE], ps[PROJ_STRIDE];
   __shared__ double d[4];   // Gram row (thread 0)
   __shared__ int sdone;
-  if (c->done) return;
+  __shared__ double head[CTRL_HEAD_WORDS];
+  for (int q = threadIdx.x; q < CTRL_HEAD_WORDS; q += blockDim.x) head[q] = ((const double*)c)[q];
+  __syncthreads();
+  Ctrl* sc = (Ctrl*)head;   // only members before the history are touched through sc
+  if (sc->done) return;
   reduce_many<RES_STRIDE>(rp, nres, RES_STRIDE, 0, rs, sh);   // [s2, p2, Gram 0..3]
   if (nproj > 0) {
     reduce_many<PROJ_STRIDE>(pp, nproj, PROJ_STRIDE, 0, ps, sh);   // [p2, Gram 0..3]
@@ -780,14 +792,16 @@ __global__ void k_ctrl_residual_acv(Ctrl* c, const double* rp, int nres, const d
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    ctrl_residual_core(c, rs[0], rs[1], ps[0], 0.0, 0.0, 0.0, 0.0, h, nnodes, nvox);
-    sdone = c->done;
+    ctrl_residual_core(sc, rs[0], rs[1], ps[0], 0.0, 0.0, 0.0, 0.0, h, nnodes, nvox, c->hist);
+    sdone = sc->done;
+    if (!sdone) {
+      const bool row = sc->i_local > 0;
+      for (int k = 0; k < 4; ++k) d[k] = row ? rs[2 + k] + ps[1 + k] : 0.0;
+      ctrl_acv_core(sc, d);
+    }
   }
   __syncthreads();
-  if (sdone || threadIdx.x != 0) return;
-  const bool row = c->i_local > 0;
-  for (int k = 0; k < 4; ++k) d[k] = row ? rs[2 + k] + ps[1 + k] : 0.0;
-  ctrl_acv_core(c, d);
+  for (int q = threadIdx.x; q < CTRL_HEAD_WORDS; q += blockDim.x) ((double*)c)[q] = head[q];
 }
 
 int launch_ctrl_residual_acv(Ctrl* c, const double* rp, int nres, const double* pp, int nproj, double h,
