@@ -176,6 +176,22 @@ def launches_per_iteration(has_rows, has_contact, acv):
     return n
 
 
+def max_over_ranks(value, world, device):
+    """The largest value over the ranks (the slowest rank's time), every rank gets it."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds_max, world):
+    """Throughput of the whole job: every rank processes the same units (weak scaling),
+    divided by the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2607_26082_b300 import dtt, rows
@@ -237,13 +253,9 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
-    tot_t = sum(times)
     tot_vi = nv * sum(iters)
-    if world > 1:
-        t = torch.tensor([tot_t], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_t = float(t.item())
-    value = world * tot_vi / tot_t
+    tot_t = max_over_ranks(sum(times), world, dev)
+    value = whole_job_rate(tot_vi, tot_t, world)
 
     # ---- kernel-group profile of the mixed iteration (roofline of the dominant group)
     prof = gm.dtt_profile_iteration(20, acv_mod=spec["acv_mod"])
@@ -288,7 +300,7 @@ def run_ours(args, rank, world, local):
         gm.dtt_get_fields(u_out=u_host)
         e2e_t += time.perf_counter() - t0
         e2e_vi += nv * rep.iterations
-    e2e_value = world * e2e_vi / e2e_t
+    e2e_value = whole_job_rate(e2e_vi, max_over_ranks(e2e_t, world, dev), world)
 
     # ---- plain FP64 GPU solver on the same input
     g64 = make(dtt.PREC_FP64)
