@@ -17,6 +17,7 @@
 // These follow from the trigonometric sums of the transforms (Section 3.2.2, Tables 2-3);
 // the 4n-extended DFT of Eq. 7 is the same idea with the redundant half removed.
 #include <cstdlib>
+#include <type_traits>
 
 #include "dtt_internal.cuh"
 
@@ -561,6 +562,19 @@ __device__ __forceinline__ void fast_fft(T* buf, const Cx<T>* tw, int sgn, int s
   }
 }
 
+// Runs f with the transform type as a compile-time constant: the CTA's type is uniform, so
+// the per-value branches of the extension and the post-processing fold away.
+template <typename F>
+__device__ __forceinline__ void by_type(int type, F&& f) {
+  switch (type) {
+    case T_DCT1: f(std::integral_constant<int, T_DCT1>()); break;
+    case T_DCT3: f(std::integral_constant<int, T_DCT3>()); break;
+    case T_DST1: f(std::integral_constant<int, T_DST1>()); break;
+    case T_DST3: f(std::integral_constant<int, T_DST3>()); break;
+    default: f(std::integral_constant<int, T_DHT>()); break;
+  }
+}
+
 // Value v of real pencil pb at axis position j into the extended sequence of its pair (the
 // same extensions as fill_sequences), in the real / imaginary arrays of the buffer.
 template <typename T, int L>
@@ -667,41 +681,44 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   // global loads in groups of FB per thread before they are placed, so that several are in
   // flight at once
   constexpr int FB = 4;
-  if (p.axis == 0) {
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int pb = warp; pb < npen; pb += 8) {
-      const T* row = src + sbase[pb];
-      for (int j0 = lane; j0 < nn; j0 += 32 * FB) {
+  by_type(type, [&](auto ty) {
+    constexpr int TY = decltype(ty)::value;
+    if (p.axis == 0) {
+      const int warp = tid >> 5, lane = tid & 31;
+      for (int pb = warp; pb < npen; pb += 8) {
+        const T* row = src + sbase[pb];
+        for (int j0 = lane; j0 < nn; j0 += 32 * FB) {
+          T v[FB];
+          #pragma unroll
+          for (int u = 0; u < FB; ++u) {
+            const int j = j0 + 32 * u;
+            v[u] = j < nn ? row[j] : (T)0;
+          }
+          #pragma unroll
+          for (int u = 0; u < FB; ++u) {
+            const int j = j0 + 32 * u;
+            if (j < nn) fast_place<T, L>(buf, pb, j, v[u], n, TY, p.inverse);
+          }
+        }
+      }
+    } else {
+      for (int i0 = tid; i0 < NPEN * nn; i0 += 256 * FB) {
         T v[FB];
         #pragma unroll
         for (int u = 0; u < FB; ++u) {
-          const int j = j0 + 32 * u;
-          v[u] = j < nn ? row[j] : (T)0;
+          const int idx = i0 + 256 * u;
+          const int pb = idx % NPEN, j = idx / NPEN;
+          v[u] = (idx < NPEN * nn && pb < npen) ? src[sbase[pb] + j * stride] : (T)0;
         }
         #pragma unroll
         for (int u = 0; u < FB; ++u) {
-          const int j = j0 + 32 * u;
-          if (j < nn) fast_place<T, L>(buf, pb, j, v[u], n, type, p.inverse);
+          const int idx = i0 + 256 * u;
+          const int pb = idx % NPEN, j = idx / NPEN;
+          if (idx < NPEN * nn && pb < npen) fast_place<T, L>(buf, pb, j, v[u], n, TY, p.inverse);
         }
       }
     }
-  } else {
-    for (int i0 = tid; i0 < NPEN * nn; i0 += 256 * FB) {
-      T v[FB];
-      #pragma unroll
-      for (int u = 0; u < FB; ++u) {
-        const int idx = i0 + 256 * u;
-        const int pb = idx % NPEN, j = idx / NPEN;
-        v[u] = (idx < NPEN * nn && pb < npen) ? src[sbase[pb] + j * stride] : (T)0;
-      }
-      #pragma unroll
-      for (int u = 0; u < FB; ++u) {
-        const int idx = i0 + 256 * u;
-        const int pb = idx % NPEN, j = idx / NPEN;
-        if (idx < NPEN * nn && pb < npen) fast_place<T, L>(buf, pb, j, v[u], n, type, p.inverse);
-      }
-    }
-  }
+  });
   __syncthreads();
   const bool quarter = (type == T_DCT3 || type == T_DST3);
   const int sgn = (p.inverse && quarter) ? 1 : -1;
@@ -709,22 +726,25 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   fast_fft<T, L>(buf, tws, sgn, tid / NT, tid % NT, (quarter && !p.inverse) ? ph : nullptr);
   const T sc = sizeof(T) == 4 ? (T)p.fscale : (T)p.scale;
   const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
-  auto emit = [&](int pb, int k) {
-    const T v = fast_post<T, L>(buf, pb, k, n, type, p.inverse, sc, ph, inv_n);
-    const long long e = coff + sbase[pb] + k * stride;
-    if (p.incr) add_to_u<T>(e, v, p);
-    else out[e] = v;
-  };
-  if (p.axis == 0) {
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int pb = warp; pb < npen; pb += 8)
-      for (int k = lane; k < nn; k += 32) emit(pb, k);
-  } else {
-    for (int idx = tid; idx < NPEN * nn; idx += 256) {
-      const int pb = idx % NPEN, k = idx / NPEN;
-      if (pb < npen) emit(pb, k);
+  by_type(type, [&](auto ty) {
+    constexpr int TY = decltype(ty)::value;
+    auto emit = [&](int pb, int k) {
+      const T v = fast_post<T, L>(buf, pb, k, n, TY, p.inverse, sc, ph, inv_n);
+      const long long e = coff + sbase[pb] + k * stride;
+      if (p.incr) add_to_u<T>(e, v, p);
+      else out[e] = v;
+    };
+    if (p.axis == 0) {
+      const int warp = tid >> 5, lane = tid & 31;
+      for (int pb = warp; pb < npen; pb += 8)
+        for (int k = lane; k < nn; k += 32) emit(pb, k);
+    } else {
+      for (int idx = tid; idx < NPEN * nn; idx += 256) {
+        const int pb = idx % NPEN, k = idx / NPEN;
+        if (pb < npen) emit(pb, k);
+      }
     }
-  }
+  });
 }
 
 // Fused z pass on the register-radix route (same contract as k_fft_z_green).  Five CTAs of
@@ -771,63 +791,66 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
   __syncthreads();
   const bool quarter = (type == T_DCT3 || type == T_DST3);
   const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
-  // forward along z
-  for (int i0 = tid; i0 < NPEN * nn; i0 += 256 * 4) {
-    T v[4];
-    #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int idx = i0 + 256 * u;
-      const int pb = idx % NPEN, j = idx / NPEN;
-      v[u] = (idx < NPEN * nn && pb < npen) ? in[coff + sbase[pb] + j * stride] : (T)0;
-    }
-    #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int idx = i0 + 256 * u;
-      const int pb = idx % NPEN, j = idx / NPEN;
-      if (idx < NPEN * nn && pb < npen) fast_place<T, L>(buf, pb, j, v[u], n, type, 0);
-    }
-  }
-  __syncthreads();
-  fast_fft<T, L>(buf, tws, -1, tid / NT, tid % NT, quarter ? ph : nullptr);
-  // Green multiply into spec
-  const T thr = sizeof(T) == 4 ? (T)gt.null_thr_f[comp] : (T)gt.null_thr[comp];
-  for (int idx = tid; idx < NPEN * nn; idx += 256) {
-    const int pb = idx % NPEN, k = idx / NPEN;
-    T v = (T)0;
-    if (pb < npen) {
-      v = fast_post<T, L>(buf, pb, k, n, type, 0, (T)1, ph, inv_n);
-      const T sx = pxy[pb][0], cx = pxy[pb][1], sy = pxy[pb][2], cy = pxy[pb][3];
-      const T sz = zs[k], cz = zc[k];
-      T Sx, Sy, Sz;
-      if (scheme == SCHEME_TETRA2) {
-        Sx = tetra_S<T>(sx, cy, sy, cx, sz);
-        Sy = tetra_S<T>(sy, cz, sz, cy, sx);
-        Sz = tetra_S<T>(sz, cx, sx, cz, sy);
-      } else {
-        Sx = sx * cy * cz;
-        Sy = sy * cx * cz;
-        Sz = sz * cx * cy;
+  by_type(type, [&](auto ty) {
+    constexpr int TY = decltype(ty)::value;
+    // forward along z
+    for (int i0 = tid; i0 < NPEN * nn; i0 += 256 * 4) {
+      T v[4];
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = i0 + 256 * u;
+        const int pb = idx % NPEN, j = idx / NPEN;
+        v[u] = (idx < NPEN * nn && pb < npen) ? in[coff + sbase[pb] + j * stride] : (T)0;
       }
-      const T Sc = comp == 0 ? Sx : (comp == 1 ? Sy : Sz);
-      const T a = (l0 * Sc + m2 * (Sx + Sy + Sz)) * ih2;
-      v = (a <= thr) ? (T)0 : v / a;
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = i0 + 256 * u;
+        const int pb = idx % NPEN, j = idx / NPEN;
+        if (idx < NPEN * nn && pb < npen) fast_place<T, L>(buf, pb, j, v[u], n, TY, 0);
+      }
     }
-    spec[pb * nn + k] = v;
-  }
-  __syncthreads();
-  // inverse along z
-  for (int q = tid; q < WORDS; q += 256) buf[q] = (T)0;
-  __syncthreads();
-  for (int idx = tid; idx < NPEN * nn; idx += 256) {
-    const int pb = idx % NPEN, j = idx / NPEN;
-    if (pb < npen) fast_place<T, L>(buf, pb, j, spec[pb * nn + j], n, type, 1);
-  }
-  __syncthreads();
-  fast_fft<T, L>(buf, tws, quarter ? 1 : -1, tid / NT, tid % NT, nullptr);
-  for (int idx = tid; idx < NPEN * nn; idx += 256) {
-    const int pb = idx % NPEN, k = idx / NPEN;
-    if (pb < npen) out[coff + sbase[pb] + k * stride] = fast_post<T, L>(buf, pb, k, n, type, 1, zscale, ph, inv_n);
-  }
+    __syncthreads();
+    fast_fft<T, L>(buf, tws, -1, tid / NT, tid % NT, quarter ? ph : nullptr);
+    // Green multiply into spec
+    const T thr = sizeof(T) == 4 ? (T)gt.null_thr_f[comp] : (T)gt.null_thr[comp];
+    for (int idx = tid; idx < NPEN * nn; idx += 256) {
+      const int pb = idx % NPEN, k = idx / NPEN;
+      T v = (T)0;
+      if (pb < npen) {
+        v = fast_post<T, L>(buf, pb, k, n, TY, 0, (T)1, ph, inv_n);
+        const T sx = pxy[pb][0], cx = pxy[pb][1], sy = pxy[pb][2], cy = pxy[pb][3];
+        const T sz = zs[k], cz = zc[k];
+        T Sx, Sy, Sz;
+        if (scheme == SCHEME_TETRA2) {
+          Sx = tetra_S<T>(sx, cy, sy, cx, sz);
+          Sy = tetra_S<T>(sy, cz, sz, cy, sx);
+          Sz = tetra_S<T>(sz, cx, sx, cz, sy);
+        } else {
+          Sx = sx * cy * cz;
+          Sy = sy * cx * cz;
+          Sz = sz * cx * cy;
+        }
+        const T Sc = comp == 0 ? Sx : (comp == 1 ? Sy : Sz);
+        const T a = (l0 * Sc + m2 * (Sx + Sy + Sz)) * ih2;
+        v = (a <= thr) ? (T)0 : v / a;
+      }
+      spec[pb * nn + k] = v;
+    }
+    __syncthreads();
+    // inverse along z
+    for (int q = tid; q < WORDS; q += 256) buf[q] = (T)0;
+    __syncthreads();
+    for (int idx = tid; idx < NPEN * nn; idx += 256) {
+      const int pb = idx % NPEN, j = idx / NPEN;
+      if (pb < npen) fast_place<T, L>(buf, pb, j, spec[pb * nn + j], n, TY, 1);
+    }
+    __syncthreads();
+    fast_fft<T, L>(buf, tws, quarter ? 1 : -1, tid / NT, tid % NT, nullptr);
+    for (int idx = tid; idx < NPEN * nn; idx += 256) {
+      const int pb = idx % NPEN, k = idx / NPEN;
+      if (pb < npen) out[coff + sbase[pb] + k * stride] = fast_post<T, L>(buf, pb, k, n, TY, 1, zscale, ph, inv_n);
+    }
+  });
 }
 
 template <typename K>
