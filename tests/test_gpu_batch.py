@@ -122,3 +122,27 @@ def test_autotune_keeps_results(prec):
         assert e.value.status == dtt.ERR_ARG
     for q in (g0, g, g2):
         q.close()
+
+
+@pytest.mark.parametrize("kind", ["finite_strain", "isotropic"])
+def test_batch_with_finite_strain_and_isotropic_cells(kind):
+    """Cells with the finite-strain stress step or the isotropic reference medium batch like
+    the others: each cell's result equals its own solve bit for bit."""
+    if kind == "finite_strain":
+        cells = [dict(c, kinematics="FS") for c in _cells(3, seed0=4600)]
+    else:
+        cells = [wl.iso_cell(4700 + k, nvox=n) for k, n in enumerate([(8, 6, 7), (12, 8, 6), (6, 6, 6)])]
+    ref = []
+    for c in cells:
+        g = gpu_grid(c, MIXED)
+        rep = g.dtt_solve_step(2e-7, 4000, acv_mod=2, graph_iters=8)
+        assert rep.status == dtt.OK, (kind, rep.as_dict())
+        ref.append((rep.iterations, g.dtt_get_fields()))
+        g.close()
+    grids = [gpu_grid(c, MIXED) for c in cells]
+    st, reps = dtt.dtt_batch_solve(grids, 2e-7, 4000, acv_mod=2, graph_iters=8)
+    assert st == dtt.OK
+    for g, rep, (it, u) in zip(grids, reps, ref):
+        assert rep.status == dtt.OK and rep.iterations == it
+        assert np.array_equal(g.dtt_get_fields(), u)
+        g.close()
