@@ -304,19 +304,28 @@ int launch_green_multiply(const GridDev& g, T* spec, const TransformTables& tt, 
 // sin q_c sin q_d / 4 = sqrt(s_c c'_c s_d c'_d).  A component without a mode at the position,
 // or whose diagonal vanishes (a null mode, where all its cross terms vanish too), keeps
 // a zero coefficient; the rest is solved by LDL^T (symmetric positive definite).
+// The scalar constants come from the host (ih2 = 4 / h^2, ih2r = its inverse, lm = lambda0 +
+// mu0, m0 = mu0, thr the null threshold): no per-thread FP64 arithmetic.
 template <typename T>
-__global__ void k_green_iso(const GridDev g, T* __restrict__ spec, IsoTables it, double lam0, double mu0,
+__global__ void k_green_iso(const GridDev g, T* __restrict__ spec, IsoTables it, T ih2, T ih2r, T lm, T m0, T thr,
                             const Ctrl* ctrl) {
   if (ctrl && ctrl->done) return;
   const long long NN = g.nnodes;
-  const T ih2 = (T)(4.0 / (g.h * g.h));
-  const T lm = (T)(lam0 + mu0), m0 = (T)mu0;
-  const T thr = (T)it.null_thr;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(n % g.nn[0]);
-    const long long r = n / g.nn[0];
-    const int j = (int)(r % g.nn[1]);
-    const int k = (int)(r / g.nn[1]);
+    // position on the node grid; 32-bit division when the grid allows it (64-bit integer
+    // division is a long software sequence)
+    int i, j, k;
+    if (NN <= 0x7fffffffLL) {
+      const int n32 = (int)n, r = n32 / g.nn[0];
+      i = n32 - r * g.nn[0];
+      j = r % g.nn[1];
+      k = r / g.nn[1];
+    } else {
+      const long long r = n / g.nn[0];
+      i = (int)(n - r * g.nn[0]);
+      j = (int)(r % g.nn[1]);
+      k = (int)(r / g.nn[1]);
+    }
     const int valid = it.valid[0][i] & it.valid[1][j] & it.valid[2][k];
     T sv[3], cv[3];
     const int pos[3] = {i, j, k};
@@ -337,7 +346,10 @@ __global__ void k_green_iso(const GridDev g, T* __restrict__ spec, IsoTables it,
     }
     T rt[3];   // sqrt(s c'): sin q / 2
     #pragma unroll
-    for (int d = 0; d < 3; ++d) rt[d] = sqrt(sv[d] * cv[d]);
+    for (int d = 0; d < 3; ++d) {
+      if constexpr (sizeof(T) == 4) rt[d] = sqrtf(sv[d] * cv[d]);
+      else rt[d] = sqrt(sv[d] * cv[d]);
+    }
     const T Ssum = S[0] + S[1] + S[2];
     T M[3][3], b[3];
     bool on[3];
@@ -363,25 +375,29 @@ __global__ void k_green_iso(const GridDev g, T* __restrict__ spec, IsoTables it,
     for (int c = 0; c < 3; ++c)
       if (!on[c]) M[c][c] = (T)1;
     // LDL^T of the symmetric positive definite M, then the two triangular solves
-    const T D0 = M[0][0];
-    const T L10 = M[1][0] / D0, L20 = M[2][0] / D0;
+    const T r0 = (T)1 / M[0][0];
+    const T L10 = M[1][0] * r0, L20 = M[2][0] * r0;
     const T D1 = M[1][1] - L10 * M[1][0];
-    const T L21 = (M[2][1] - L20 * M[1][0]) / D1;
+    const T r1 = (T)1 / D1;
+    const T L21 = (M[2][1] - L20 * M[1][0]) * r1;
     const T D2 = M[2][2] - L20 * M[2][0] - L21 * L21 * D1;
+    const T r2 = (T)1 / D2;
     const T y0 = b[0], y1 = b[1] - L10 * y0, y2 = b[2] - L20 * y0 - L21 * y1;
-    const T x2 = y2 / D2;
-    const T x1 = y1 / D1 - L21 * x2;
-    const T x0 = y0 / D0 - L10 * x1 - L20 * x2;
+    const T x2 = y2 * r2;
+    const T x1 = y1 * r1 - L21 * x2;
+    const T x0 = y0 * r0 - L10 * x1 - L20 * x2;
     const T x[3] = {x0, x1, x2};
     #pragma unroll
-    for (int c = 0; c < 3; ++c) spec[(long long)c * NN + n] = on[c] ? x[c] / ih2 : (T)0;
+    for (int c = 0; c < 3; ++c) spec[(long long)c * NN + n] = on[c] ? x[c] * ih2r : (T)0;
   }
 }
 
 template <typename T>
 int launch_green_iso(const GridDev& g, T* spec, const TransformTables& tt, const Ctrl* ctrl, cudaStream_t s) {
   const long long nb = std::min<long long>((g.nnodes + 255) / 256, 148LL * 16);
-  k_green_iso<T><<<(int)nb, 256, 0, s>>>(g, spec, tt.iso, tt.lam0, tt.mu0, ctrl);
+  const double h2 = g.h * g.h;
+  k_green_iso<T><<<(int)nb, 256, 0, s>>>(g, spec, tt.iso, (T)(4.0 / h2), (T)(h2 / 4.0), (T)(tt.lam0 + tt.mu0),
+                                         (T)tt.mu0, (T)tt.iso.null_thr, ctrl);
   return (int)cudaGetLastError();
 }
 
