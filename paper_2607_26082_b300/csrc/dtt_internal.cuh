@@ -60,6 +60,7 @@ struct Ctrl {
   double r, r0;
   double p2, s2;
   double alpha[4];
+  float alpha_f[4];   // the same coefficients in FP32 (set with alpha; read by FP32 kernels)
   double gram[4][4];
   double hist[HIST];
 };
@@ -174,6 +175,7 @@ struct FftParams {
   int nnx, nny;
   long long npencil, NN;
   float fscale;            // scale in FP32 (mixed path)
+  float finv_n;            // inv_n in FP32 (mixed path; no per-thread conversion)
   int generic;             // 1: generic Stockham kernels only (tuning choice)
   double inv_n;            // 1 / n (quarter-wave inverses)
   int incr;                // inverse x pass: add the result to u~ and store it as the step

@@ -306,7 +306,7 @@ k_fft_axis(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   const int sgn = (p.inverse && quarter) ? 1 : -1;
   Cx<T>* Y = fft_sequences<T, PB>(bufA, bufB, p, tws, sgn, tid, nthr);
   const T sc = sizeof(T) == 4 ? (T)p.fscale : (T)p.scale;
-  const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
+  const T inv_n = sizeof(T) == 4 ? (T)p.finv_n : (T)p.inv_n;
   auto emit = [&](int pb, int k) {
     const T v = post_value<T>(Y, p.L, p.n, type, p.inverse, sc, ph, pb, k, inv_n);
     const long long e = coff + sbase[pb] + k * stride;
@@ -369,7 +369,7 @@ k_fft_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenT
   }
   __syncthreads();
   const bool quarter = (type == T_DCT3 || type == T_DST3);
-  const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
+  const T inv_n = sizeof(T) == 4 ? (T)p.finv_n : (T)p.inv_n;
   // forward along z
   fill_sequences<T, PB>(bufA, p.L, p.n, nn, type, 0, npen, ph,
                         [&](int pb, int j) { return in[coff + sbase[pb] + j * stride]; }, tid, nthr, false);
@@ -725,7 +725,7 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   const Cx<T>* ph = (const Cx<T>*)p.ph;
   fast_fft<T, L>(buf, tws, sgn, tid / NT, tid % NT, (quarter && !p.inverse) ? ph : nullptr);
   const T sc = sizeof(T) == 4 ? (T)p.fscale : (T)p.scale;
-  const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
+  const T inv_n = sizeof(T) == 4 ? (T)p.finv_n : (T)p.inv_n;
   by_type(type, [&](auto ty) {
     constexpr int TY = decltype(ty)::value;
     auto emit = [&](int pb, int k) {
@@ -790,7 +790,7 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
   for (int q = tid; q < WORDS; q += 256) buf[q] = (T)0;
   __syncthreads();
   const bool quarter = (type == T_DCT3 || type == T_DST3);
-  const T inv_n = sizeof(T) == 4 ? (T)(float)p.inv_n : (T)p.inv_n;
+  const T inv_n = sizeof(T) == 4 ? (T)p.finv_n : (T)p.inv_n;
   by_type(type, [&](auto ty) {
     constexpr int TY = decltype(ty)::value;
     // forward along z

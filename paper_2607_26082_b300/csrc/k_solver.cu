@@ -493,8 +493,8 @@ __global__ void k_acv_green_input_v4(long long total, void* const* P, void* cons
     for (long long e = 4 * n4 + t0; e < total; e += stride) gi[e] = pi[e];
     return;
   }
-  const float a0 = (float)ctrl->alpha[0], a1 = (float)ctrl->alpha[1], a2 = (float)ctrl->alpha[2],
-              a3 = (float)ctrl->alpha[3];
+  // FP32 copies made by the control kernel: no per-thread FP64 conversion
+  const float a0 = ctrl->alpha_f[0], a1 = ctrl->alpha_f[1], a2 = ctrl->alpha_f[2], a3 = ctrl->alpha_f[3];
   const float b0 = a0, b1 = a0 + a1, b2 = a0 + a1 + a2;
   const float* p0 = (const float*)P[(i - 3) % 4];
   const float* p1 = (const float*)P[(i - 2) % 4];
@@ -723,7 +723,10 @@ __device__ __forceinline__ void ctrl_acv_core(Ctrl* c, const double* d) {
       }
       double sy = y[0] + y[1] + y[2] + y[3];
       if (sy != 0.0 && isfinite(sy)) {
-        for (int m = 0; m < 4; ++m) c->alpha[m] = y[(i - 4 + m) % 4] / sy;
+        for (int m = 0; m < 4; ++m) {
+          c->alpha[m] = y[(i - 4 + m) % 4] / sy;
+          c->alpha_f[m] = (float)c->alpha[m];
+        }
         c->accel = 1;
         c->n_accel += 1;
       }

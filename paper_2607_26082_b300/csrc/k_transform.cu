@@ -166,6 +166,7 @@ static FftParams fft_params(const GridDev& g, const TransformTables& tt, int axi
   p.fscale = (float)p.scale;
   p.generic = g.fft_generic;
   p.inv_n = 1.0 / g.nvox[axis];
+  p.finv_n = (float)p.inv_n;
   return p;
 }
 
