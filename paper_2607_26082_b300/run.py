@@ -16,7 +16,8 @@ other with dtt_solve_step for comparison.
 --kinematics fs solves with the finite-strain stress step (Section 5.2, Algorithm 3 for
 the indentation); --r0-scale multiplies the workload's reference medium (the paper takes a
 stiffer one in finite strain); --load-steps N splits the indentation into N geometric
-increments (default 10); --max-iter caps the iterations of each step (default 20000) and
+increments (default 20 for indent, whose 10-increment schedule leaves the physical branch
+at its last step, and the paper's 80 for indent_cube); --max-iter caps the iterations of each step (default 20000) and
 --stop-on-fail ends the run at the first step that does not converge.  ct_paper is the
 paper's 10 x 100 x (50 + 1) CT-like specimen with the loading --ct-load; it reports the
 reactions of the load rows and of the ligament rows and their balance.  --acv-on and
@@ -45,7 +46,7 @@ import workloads as wl  # noqa: E402
 from . import dtt, rows  # noqa: E402
 
 
-def make_workload(name, nvox=None, load_steps=10, contrast=4.0):
+def make_workload(name, nvox=None, load_steps=None, contrast=4.0):
     """ct: half compact-tension-like specimen 128x128x32; cube16: 16^3 cube with pinned
     nodes; indent: sphere indentation of a 256x256x128 block, R = 64.  nvox rescales ct and
     indent (the indenter radius scales with the block); indent_cube: Section 5.4's 65^3 cube
@@ -59,10 +60,10 @@ def make_workload(name, nvox=None, load_steps=10, contrast=4.0):
     if name.startswith("iso_cell:"):
         return wl.iso_cell(int(name.split(":", 1)[1]), nvox=nvox or (128, 128, 128), n_strong=0, contrast=contrast)
     if name == "indent_cube":
-        return wl.indentation_cube(nvox[0] if nvox else 65, steps=load_steps, dmax=0.2)
+        return wl.indentation_cube(nvox[0] if nvox else 65, steps=load_steps or 80, dmax=0.2)
     if name == "indent":
         n = nvox or (256, 256, 128)
-        return wl.indentation(*n, R=64.0 * n[0] / 256.0, steps=load_steps)
+        return wl.indentation(*n, R=64.0 * n[0] / 256.0, steps=load_steps or 20)
     raise SystemExit("unknown workload %r" % name)
 
 
@@ -126,7 +127,7 @@ def main(argv=None):
     ap.add_argument("--nvox", default=None, help="voxels nx,ny,nz (ct and indent)")
     ap.add_argument("--kinematics", default="ss", choices=["ss", "fs"])
     ap.add_argument("--r0-scale", type=float, default=1.0)
-    ap.add_argument("--load-steps", type=int, default=10)
+    ap.add_argument("--load-steps", type=int, default=None)
     ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--stop-on-fail", action="store_true")
     a = ap.parse_args(argv)
