@@ -1,6 +1,7 @@
 """Command-line runner: solve one of the synthetic workloads with the CUDA path.
 
-  python -m paper_2607_26082_b300.run --workload ct|ct_paper|cube16|indent|indent_cube|iso_cell [--precision mixed|fp64]
+  python -m paper_2607_26082_b300.run --workload ct|ct_paper|cube16|indent|indent_cube|indent_inclusions|iso_cell
+         [--precision mixed|fp64]
          [--iters K | --tol T] [--steps S] [--graph-iters G] [--nvox nx,ny,nz]
          [--kinematics ss|fs] [--r0-scale K] [--load-steps N] [--max-iter M] [--stop-on-fail]
          [--ct-load strong_line|weak_line|strong_node|weak_node|smooth_node] [--acv-on u|p] [--acv-mod M]
@@ -49,7 +50,9 @@ from . import dtt, rows  # noqa: E402
 def make_workload(name, nvox=None, load_steps=None, contrast=4.0):
     """ct: half compact-tension-like specimen 128x128x32; cube16: 16^3 cube with pinned
     nodes; indent: sphere indentation of a 256x256x128 block, R = 64.  nvox rescales ct and
-    indent (the indenter radius scales with the block); indent_cube: Section 5.4's 65^3 cube
+    indent (the indenter radius scales with the block); indent_inclusions: the 384x384x192
+    block with 2-8 stiff spherical inclusions and a sphere of radius 96 (--seed0 picks the
+    sample, nvox rescales it); indent_cube: Section 5.4's 65^3 cube
     with a sphere of the cube's diameter, `load_steps` equal steps to d/R = 0.2."""
     if name == "ct":
         return wl.ct_plate(*(nvox or (128, 128, 32)))
@@ -59,6 +62,9 @@ def make_workload(name, nvox=None, load_steps=None, contrast=4.0):
         return wl.ct_specimen(name.split(":", 1)[1])
     if name.startswith("iso_cell:"):
         return wl.iso_cell(int(name.split(":", 1)[1]), nvox=nvox or (128, 128, 128), n_strong=0, contrast=contrast)
+    if name.startswith("indent_inclusions:"):
+        n = nvox or (384, 384, 192)
+        return wl.indentation_inclusions(int(name.split(":", 1)[1]), *n, steps=load_steps or 20)
     if name == "indent_cube":
         return wl.indentation_cube(nvox[0] if nvox else 65, steps=load_steps or 80, dmax=0.2)
     if name == "indent":
@@ -108,7 +114,8 @@ def run_batch(a, prec):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="ct",
-                    choices=["ct", "ct_paper", "cube16", "indent", "indent_cube", "iso_cell", "batch"])
+                    choices=["ct", "ct_paper", "cube16", "indent", "indent_cube", "indent_inclusions", "iso_cell",
+                             "batch"])
     ap.add_argument("--medium", default=None, choices=["paux", "iso"])
     ap.add_argument("--scheme", default=None, choices=["tetra2", "hex1"])
     ap.add_argument("--contrast", type=float, default=4.0)
@@ -136,6 +143,8 @@ def main(argv=None):
     wname = "ct_paper:" + a.ct_load if a.workload == "ct_paper" else a.workload
     if a.workload == "iso_cell":
         wname = "iso_cell:%d" % a.seed0
+    if a.workload == "indent_inclusions":
+        wname = "indent_inclusions:%d" % a.seed0
     spec = make_workload(wname, tuple(int(v) for v in a.nvox.split(",")) if a.nvox else None, a.load_steps,
                          a.contrast)
     prec = dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64

@@ -87,3 +87,17 @@ def test_ct_specimen_follows_the_paper_set_up():
             kind = {"strong_node": "strong", "weak_node": "weak_voxel", "smooth_node": "smooth"}[load]
             assert row["kind"] == kind
             assert row.get("ijk", row.get("vox")) == (2, 24, 25)
+
+
+def test_indentation_with_inclusions_follows_the_recipe():
+    for seed in (2000, 2001):
+        w = wl.indentation_inclusions(seed, 96, 96, 48, steps=10)
+        sp = w["spheres"]
+        assert 2 <= len(sp) <= 8
+        for k, (c, r) in enumerate(sp):
+            assert 8 <= r <= 32 and np.all(c >= r) and np.all(c <= np.array([96, 96, 48]) - r)
+            for c2, r2 in sp[:k]:
+                assert np.linalg.norm(c - c2) >= r + r2
+        assert 0.005 <= w["d_over_R"] <= 0.05 and np.isclose(w["indenter"]["ratios"][-1], w["d_over_R"])
+        assert w["indenter"]["radius"] == 24.0 and w["lam"][1] / w["lam"][0] == 5.0
+        assert w["phase"].any() and (w["bc"][2, 0] == wl.D).all()

@@ -124,6 +124,42 @@ def ct_plate(nx=128, ny=128, nz=32, scheme=TETRA2, notch_scale=0.0, r0_factor=1.
                     ligament_rows=(nz + 1) * (nx + 1 - xn))
 
 
+def indentation_inclusions(seed, nx=384, ny=384, nz=192, steps=20, contrast=5.0, scheme=TETRA2):
+    """The large indentation configuration: a block of nx x ny x nz voxels (bottom clamped,
+    lateral faces free, top face the contact surface) holding 2-8 non-overlapping spherical
+    inclusions of radius U[8, 32] voxels (capped at half the smallest edge) and stiffness `contrast` times the matrix's
+    (E = 1, nu = 0.3 both), indented by a rigid sphere of radius nx / 4 to a depth ratio
+    d/R drawn from U[0.005, 0.05], reached in `steps` geometric increments from d/R = 0.001
+    (or from the final ratio if it is smaller).  Reference medium 5 (lambda, mu) of the
+    matrix, Anderson on p~ every 3 iterations, tolerance 1e-6."""
+    rng = np.random.default_rng(seed)
+    R = nx / 4.0
+    w = indentation(nx, ny, nz, R=R, steps=steps, dmin=0.001, dmax=0.05, scheme=scheme)
+    dR = float(rng.uniform(0.005, 0.05))
+    ratios = np.geomspace(min(0.001, dR), dR, steps)
+    w["indenter"]["ratios"] = ratios
+    w["indenter"]["centers"] = [np.array([nx / 2.0, ny / 2.0, nz + R - r * R]) for r in ratios]
+    ninc = int(rng.integers(2, 9))
+    spheres = []
+    tries = 0
+    while len(spheres) < ninc and tries < 10000:
+        tries += 1
+        r = float(rng.uniform(8.0, min(32.0, min(nx, ny, nz) / 2.0 - 1.0)))
+        c = np.array([rng.uniform(r, nx - r), rng.uniform(r, ny - r), rng.uniform(r, nz - r)])
+        if all(np.linalg.norm(c - c2) >= r + r2 for c2, r2 in spheres):
+            spheres.append((c, r))
+    phase = np.zeros((nz, ny, nx), np.uint8)
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    for c, r in spheres:
+        phase[(x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 <= r * r] = 1
+    lam, mu = lame(np.array([1.0, contrast]), 0.3)
+    w["phase"], w["lam"], w["mu"] = phase, lam, mu
+    w["lam0"], w["mu0"] = 5 * float(lam[0]), 5 * float(mu[0])
+    w["spheres"], w["d_over_R"] = spheres, dR
+    w["name"] = "indentation of a %dx%dx%d block with %d inclusions, R=%g, d/R=%.4f" % (nx, ny, nz, len(spheres), R, dR)
+    return w
+
+
 def normal_mixed_bc(normal):
     """bc[axis][face][component] from normal[axis][face] in (D, N): the normal component takes
     that condition and the tangential components the other one (sliding wall or its
