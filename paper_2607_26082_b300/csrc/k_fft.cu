@@ -413,20 +413,27 @@ k_fft_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenT
   }
 }
 
-// ==== register-radix route for power-of-two lengths 16..2048 (compile-time L) ==============
+// ==== register-radix route: L = 2^k (16..2048) or 3 * 2^k (48..1536), compile-time L =====
 //
-// L / 8 threads own one complex sequence; each radix-8 pass (radix 4 or 2 for the last
-// factor) loads 8 values per thread from shared memory, applies the Stockham twiddles and a
-// DFT in registers, and writes back in place between two barriers.  The sequences live in
-// shared memory as a real and an imaginary array; FastMap<L> places element i of sequence
-// seq so that the warps' strided accesses (the Stockham writes, the column-wise fills and
-// reads of several pencils at one position) spread over the 32 banks.  256 threads:
-// 2048 / L sequences (twice as many real pencils) per CTA.
+// L / 8 threads own one complex sequence.  The power-of-two factor of L goes through
+// radix-8 passes (radix 4 or 2 for the rest), each loading 8 values per thread from shared
+// memory, applying the Stockham twiddles and a DFT in registers, and writing back in place
+// between two barriers; a factor 3 adds one last radix-3 pass, in which a thread takes 2 or
+// 3 of the L / 3 butterflies.  The sequences live in shared memory as a real and an
+// imaginary array; FastMap<L> places element i of sequence seq so that the warps' strided
+// accesses (the Stockham writes, the column-wise fills and reads of several pencils at one
+// position) spread over the 32 banks.  A CTA holds 2048 complex values on 256 threads
+// (power of two) or 1536 on 192 threads (3 * 2^k): SEQ sequences, twice as many real pencils.
 
 template <int L>
 struct FastPlan {
-  static constexpr int NT = L / 8;        // threads per sequence
-  static constexpr int SEQ = 2048 / L;    // sequences per CTA
+  static constexpr bool POW2 = (L & (L - 1)) == 0;
+  static constexpr int P2 = POW2 ? L : L / 3;             // power-of-two factor
+  static constexpr int NT = L / 8;                        // threads per sequence
+  static constexpr int SEQ = (POW2 ? 2048 : 1536) / L;    // sequences per CTA
+  static constexpr int THREADS = NT * SEQ;                // 256 or 192
+  static constexpr int MINB = POW2 ? 5 : 6;               // fused z pass: CTAs per SM
+  static_assert(POW2 || (P2 & (P2 - 1)) == 0, "L must be 2^k or 3 * 2^k");
 };
 
 // Shared-memory word of element i of sequence seq in array arr (0 real, 1 imaginary):
@@ -447,6 +454,15 @@ template <> struct FastMapParams<16> { static constexpr int S = 3, A = 1, T = 0,
 template <> struct FastMapParams<32> { static constexpr int S = 3, A = 1, T = 0, B = 0, EXTRA = 0, OFF = 1; };
 template <> struct FastMapParams<64> { static constexpr int S = 5, A = 3, T = 0, B = 0, EXTRA = 0, OFF = 1; };
 template <> struct FastMapParams<128> { static constexpr int S = 5, A = 2, T = 0, B = 0, EXTRA = 1, OFF = 0; };
+// 3 * 2^k (192 threads), simulated the same way; wavefronts against the power-of-two default:
+//     L       48     96    192    384    768
+//     now   1874   2162   2420   2783   2081
+//     was   3060   2978   2785   2974   2214
+template <> struct FastMapParams<48> { static constexpr int S = 5, A = 3, T = 0, B = 0, EXTRA = 19, OFF = 1; };
+template <> struct FastMapParams<96> { static constexpr int S = 5, A = 3, T = 0, B = 0, EXTRA = 3, OFF = 1; };
+template <> struct FastMapParams<192> { static constexpr int S = 5, A = 3, T = 0, B = 0, EXTRA = 0, OFF = 0; };
+template <> struct FastMapParams<384> { static constexpr int S = 5, A = 3, T = 0, B = 0, EXTRA = 15, OFF = 0; };
+template <> struct FastMapParams<768> { static constexpr int S = 5, A = 3, T = 0, B = 0, EXTRA = 0, OFF = 0; };
 
 template <int L>
 struct FastMap {
@@ -549,16 +565,69 @@ __device__ __forceinline__ void fast_pass(T* buf, const Cx<T>* __restrict__ tw, 
   __syncthreads();
 }
 
-// Whole FFT of length L: radix-8 passes, then one radix-4 or radix-2 pass for the rest.
+// The last Stockham pass of L = 3 * NS: L / 3 radix-3 butterflies over the NT = L / 8
+// threads of a sequence, thread t taking t, t + NT and (for t < L / 12) t + 2 NT.
+template <typename T, int L, int NS>
+__device__ __forceinline__ void fast_pass3(T* buf, const Cx<T>* __restrict__ tw, int sgn, int seq, int t) {
+  using M = FastMap<L>;
+  constexpr int NT = FastPlan<L>::NT;
+  constexpr int LR = L / 3, PER = (LR + NT - 1) / NT, TWS = L / (NS * 3);
+  static_assert(NS * 3 == L && PER == 3, "radix-3 pass closes 3 * 2^k");
+  Cx<T> v[PER][3];
+  #pragma unroll
+  for (int m = 0; m < PER; ++m) {
+    const int jb = t + m * NT;
+    if (m < PER - 1 || jb < LR) {
+      const int k = jb & (NS - 1);
+      #pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int idx = jb + r * LR;
+        v[m][r] = {buf[M::at(0, seq, idx)], buf[M::at(1, seq, idx)]};
+      }
+      #pragma unroll
+      for (int r = 1; r < 3; ++r) {
+        Cx<T> w = tw[k * r * TWS];
+        if (sgn > 0) w.y = -w.y;
+        v[m][r] = cmul(v[m][r], w);
+      }
+      dft3(v[m], sgn);
+    }
+  }
+  __syncthreads();
+  #pragma unroll
+  for (int m = 0; m < PER; ++m) {
+    const int jb = t + m * NT;
+    if (m < PER - 1 || jb < LR) {
+      const int k = jb & (NS - 1);
+      const int o = (jb - k) * 3 + k;
+      #pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int idx = o + r * NS;
+        buf[M::at(0, seq, idx)] = v[m][r].x;
+        buf[M::at(1, seq, idx)] = v[m][r].y;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Whole FFT of length L: radix-8 passes over the power-of-two factor P2, one radix-4 or
+// radix-2 pass for the rest of it, then the radix-3 pass when L = 3 P2.  Every stride NS is
+// a power of two, so the butterfly's offset k within its group is jb & (NS - 1).
 template <typename T, int L, int NS = 1>
 __device__ __forceinline__ void fast_fft(T* buf, const Cx<T>* tw, int sgn, int seq, int t, const Cx<T>* mod) {
-  if constexpr (NS * 8 <= L) {
+  constexpr int P2 = FastPlan<L>::P2;
+  if constexpr (NS * 8 <= P2) {
     fast_pass<T, L, 8, NS>(buf, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
     fast_fft<T, L, NS * 8>(buf, tw, sgn, seq, t, nullptr);
-  } else if constexpr (NS * 4 == L) {
+  } else if constexpr (NS * 4 == P2) {
     fast_pass<T, L, 4, NS>(buf, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
-  } else if constexpr (NS * 2 == L) {
+    fast_fft<T, L, NS * 4>(buf, tw, sgn, seq, t, nullptr);
+  } else if constexpr (NS * 2 == P2) {
     fast_pass<T, L, 2, NS>(buf, tw, sgn, seq, t, NS == 1 ? mod : nullptr);
+    fast_fft<T, L, NS * 2>(buf, tw, sgn, seq, t, nullptr);
+  } else if constexpr (NS == P2 && P2 != L) {
+    fast_pass3<T, L, NS>(buf, tw, sgn, seq, t);
   }
 }
 
@@ -656,9 +725,10 @@ __host__ __device__ constexpr size_t fast_smem(int extra_bytes) {
 
 // Axis pass on the register-radix route (same contract as k_fft_axis).
 template <typename T, int L>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(FastPlan<L>::THREADS)
 k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctrl* ctrl, void* const* in_ring) {
   constexpr int SEQ = FastPlan<L>::SEQ, NT = FastPlan<L>::NT, WORDS = FastMap<L>::WORDS, NPEN = 2 * SEQ;
+  constexpr int NTH = FastPlan<L>::THREADS, NW = NTH / 32;
   if (ctrl && ctrl->done) return;
   if (in_ring) in = (const T*)in_ring[ctrl->i_local % 4];
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -675,8 +745,8 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   const int npen = (int)min((long long)NPEN, p.npencil - pen0);
   const int n = p.n, nn = p.nn;
   pencil_bases<T, SEQ>(sbase, p, pen0, tid);
-  for (int q = tid; q < L; q += 256) tws[q] = ((const Cx<T>*)p.tw)[q];
-  for (int q = tid; q < WORDS; q += 256) buf[q] = (T)0;
+  for (int q = tid; q < L; q += NTH) tws[q] = ((const Cx<T>*)p.tw)[q];
+  for (int q = tid; q < WORDS; q += NTH) buf[q] = (T)0;
   __syncthreads();
   // global loads in groups of FB per thread before they are placed, so that several are in
   // flight at once
@@ -685,7 +755,7 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
     constexpr int TY = decltype(ty)::value;
     if (p.axis == 0) {
       const int warp = tid >> 5, lane = tid & 31;
-      for (int pb = warp; pb < npen; pb += 8) {
+      for (int pb = warp; pb < npen; pb += NW) {
         const T* row = src + sbase[pb];
         for (int j0 = lane; j0 < nn; j0 += 32 * FB) {
           T v[FB];
@@ -702,17 +772,17 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
         }
       }
     } else {
-      for (int i0 = tid; i0 < NPEN * nn; i0 += 256 * FB) {
+      for (int i0 = tid; i0 < NPEN * nn; i0 += NTH * FB) {
         T v[FB];
         #pragma unroll
         for (int u = 0; u < FB; ++u) {
-          const int idx = i0 + 256 * u;
+          const int idx = i0 + NTH * u;
           const int pb = idx % NPEN, j = idx / NPEN;
           v[u] = (idx < NPEN * nn && pb < npen) ? src[sbase[pb] + j * stride] : (T)0;
         }
         #pragma unroll
         for (int u = 0; u < FB; ++u) {
-          const int idx = i0 + 256 * u;
+          const int idx = i0 + NTH * u;
           const int pb = idx % NPEN, j = idx / NPEN;
           if (idx < NPEN * nn && pb < npen) fast_place<T, L>(buf, pb, j, v[u], n, TY, p.inverse);
         }
@@ -736,10 +806,10 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
     };
     if (p.axis == 0) {
       const int warp = tid >> 5, lane = tid & 31;
-      for (int pb = warp; pb < npen; pb += 8)
+      for (int pb = warp; pb < npen; pb += NW)
         for (int k = lane; k < nn; k += 32) emit(pb, k);
     } else {
-      for (int idx = tid; idx < NPEN * nn; idx += 256) {
+      for (int idx = tid; idx < NPEN * nn; idx += NTH) {
         const int pb = idx % NPEN, k = idx / NPEN;
         if (pb < npen) emit(pb, k);
       }
@@ -748,12 +818,14 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
 }
 
 // Fused z pass on the register-radix route (same contract as k_fft_z_green).  Five CTAs of
-// 256 threads per SM fit its shared memory; the launch bound keeps registers to match.
+// 256 threads (six of 192) per SM fit its shared memory; the launch bound keeps registers to
+// match.
 template <typename T, int L>
-__global__ void __launch_bounds__(256, 5)
+__global__ void __launch_bounds__(FastPlan<L>::THREADS, FastPlan<L>::MINB)
 k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, GreenTables gt, T l0, T m2, T ih2,
                    int scheme, T zscale, const Ctrl* ctrl) {
   constexpr int SEQ = FastPlan<L>::SEQ, NT = FastPlan<L>::NT, WORDS = FastMap<L>::WORDS, NPEN = 2 * SEQ;
+  constexpr int NTH = FastPlan<L>::THREADS;
   if (ctrl && ctrl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long sbase[NPEN];
@@ -773,7 +845,7 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
   const int n = p.n, nn = p.nn;
   const Cx<T>* ph = (const Cx<T>*)p.ph;
   pencil_bases<T, SEQ>(sbase, p, pen0, tid);
-  for (int q = tid; q < NPEN; q += 256) {
+  for (int q = tid; q < NPEN; q += NTH) {
     const long long pen = pen0 + q;
     const int pen32 = pen < p.npencil ? (int)pen : 0;   // z pencils: pen = ix + nnx iy < 2^31
     const int ix = pen32 % p.nnx, iy = pen32 / p.nnx;
@@ -782,29 +854,29 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
     pxy[q][2] = gt_s<T>(gt, comp, 1, iy);
     pxy[q][3] = gt_c<T>(gt, comp, 1, iy);
   }
-  for (int q = tid; q < L; q += 256) tws[q] = ((const Cx<T>*)p.tw)[q];
-  for (int q = tid; q < nn; q += 256) {
+  for (int q = tid; q < L; q += NTH) tws[q] = ((const Cx<T>*)p.tw)[q];
+  for (int q = tid; q < nn; q += NTH) {
     zs[q] = gt_s<T>(gt, comp, 2, q);
     zc[q] = gt_c<T>(gt, comp, 2, q);
   }
-  for (int q = tid; q < WORDS; q += 256) buf[q] = (T)0;
+  for (int q = tid; q < WORDS; q += NTH) buf[q] = (T)0;
   __syncthreads();
   const bool quarter = (type == T_DCT3 || type == T_DST3);
   const T inv_n = sizeof(T) == 4 ? (T)p.finv_n : (T)p.inv_n;
   by_type(type, [&](auto ty) {
     constexpr int TY = decltype(ty)::value;
     // forward along z
-    for (int i0 = tid; i0 < NPEN * nn; i0 += 256 * 4) {
+    for (int i0 = tid; i0 < NPEN * nn; i0 += NTH * 4) {
       T v[4];
       #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int idx = i0 + 256 * u;
+        const int idx = i0 + NTH * u;
         const int pb = idx % NPEN, j = idx / NPEN;
         v[u] = (idx < NPEN * nn && pb < npen) ? in[coff + sbase[pb] + j * stride] : (T)0;
       }
       #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int idx = i0 + 256 * u;
+        const int idx = i0 + NTH * u;
         const int pb = idx % NPEN, j = idx / NPEN;
         if (idx < NPEN * nn && pb < npen) fast_place<T, L>(buf, pb, j, v[u], n, TY, 0);
       }
@@ -813,7 +885,7 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
     fast_fft<T, L>(buf, tws, -1, tid / NT, tid % NT, quarter ? ph : nullptr);
     // Green multiply into spec
     const T thr = sizeof(T) == 4 ? (T)gt.null_thr_f[comp] : (T)gt.null_thr[comp];
-    for (int idx = tid; idx < NPEN * nn; idx += 256) {
+    for (int idx = tid; idx < NPEN * nn; idx += NTH) {
       const int pb = idx % NPEN, k = idx / NPEN;
       T v = (T)0;
       if (pb < npen) {
@@ -838,15 +910,15 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
     }
     __syncthreads();
     // inverse along z
-    for (int q = tid; q < WORDS; q += 256) buf[q] = (T)0;
+    for (int q = tid; q < WORDS; q += NTH) buf[q] = (T)0;
     __syncthreads();
-    for (int idx = tid; idx < NPEN * nn; idx += 256) {
+    for (int idx = tid; idx < NPEN * nn; idx += NTH) {
       const int pb = idx % NPEN, j = idx / NPEN;
       if (pb < npen) fast_place<T, L>(buf, pb, j, spec[pb * nn + j], n, TY, 1);
     }
     __syncthreads();
     fast_fft<T, L>(buf, tws, quarter ? 1 : -1, tid / NT, tid % NT, nullptr);
-    for (int idx = tid; idx < NPEN * nn; idx += 256) {
+    for (int idx = tid; idx < NPEN * nn; idx += NTH) {
       const int pb = idx % NPEN, k = idx / NPEN;
       if (pb < npen) out[coff + sbase[pb] + k * stride] = fast_post<T, L>(buf, pb, k, n, TY, 1, zscale, ph, inv_n);
     }
@@ -863,7 +935,8 @@ static bool generic_only() {
   return e && e[0] == '1';
 }
 
-// Register-radix dispatch; returns -1 when L is not a power of two in 16..2048.
+// Register-radix dispatch; returns -1 when L is neither a power of two in 16..2048 nor
+// 3 * 2^k in 48..1536 (fused z pass: 16..1024 and 48..768).
 template <typename T, int L>
 static int launch_fast_L(const T* in, T* out, const FftParams& p, int ncomp, const Ctrl* ctrl, void* const* in_ring,
                          cudaStream_t s) {
@@ -872,7 +945,7 @@ static int launch_fast_L(const T* in, T* out, const FftParams& p, int ncomp, con
   const size_t sm = fast_smem<T, L>(0);
   static size_t attr = 48 * 1024;
   if (int e = ensure_smem(k_fft_fast<T, L>, sm, attr)) return e;
-  k_fft_fast<T, L><<<grd, 256, sm, s>>>(in, out, p, ctrl, in_ring);
+  k_fft_fast<T, L><<<grd, FastPlan<L>::THREADS, sm, s>>>(in, out, p, ctrl, in_ring);
   return (int)cudaGetLastError();
 }
 
@@ -884,7 +957,7 @@ static int launch_fast_zg_L(const T* in, T* out, const FftParams& p, const Green
   const size_t sm = fast_smem<T, L>((int)((2 + NPEN) * p.nn * sizeof(T)));
   static size_t attr = 48 * 1024;
   if (int e = ensure_smem(k_fft_fast_z_green<T, L>, sm, attr)) return e;
-  k_fft_fast_z_green<T, L><<<grd, 256, sm, s>>>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ctrl);
+  k_fft_fast_z_green<T, L><<<grd, FastPlan<L>::THREADS, sm, s>>>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ctrl);
   return (int)cudaGetLastError();
 }
 
@@ -900,6 +973,12 @@ static int launch_fast(const T* in, T* out, const FftParams& p, int ncomp, const
     case 512: return launch_fast_L<T, 512>(in, out, p, ncomp, ctrl, in_ring, s);
     case 1024: return launch_fast_L<T, 1024>(in, out, p, ncomp, ctrl, in_ring, s);
     case 2048: return launch_fast_L<T, 2048>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 48: return launch_fast_L<T, 48>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 96: return launch_fast_L<T, 96>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 192: return launch_fast_L<T, 192>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 384: return launch_fast_L<T, 384>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 768: return launch_fast_L<T, 768>(in, out, p, ncomp, ctrl, in_ring, s);
+    case 1536: return launch_fast_L<T, 1536>(in, out, p, ncomp, ctrl, in_ring, s);
     default: return -1;
   }
 }
@@ -915,6 +994,11 @@ static int launch_fast_zg(const T* in, T* out, const FftParams& p, const GreenTa
     case 256: return launch_fast_zg_L<T, 256>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
     case 512: return launch_fast_zg_L<T, 512>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
     case 1024: return launch_fast_zg_L<T, 1024>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    case 48: return launch_fast_zg_L<T, 48>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    case 96: return launch_fast_zg_L<T, 96>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    case 192: return launch_fast_zg_L<T, 192>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    case 384: return launch_fast_zg_L<T, 384>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
+    case 768: return launch_fast_zg_L<T, 768>(in, out, p, gt, l0, m2, ih2, scheme, zscale, ncomp, ctrl, s);
     default: return -1;
   }
 }

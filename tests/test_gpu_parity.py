@@ -56,8 +56,9 @@ def _oracle_forward_real(pb, c, x):
 
 # ----------------------------------------------------------------------------- transforms
 TRANSFORM_SIZES = [(5, 4, 6), (33, 7, 18), (70, 9, 35),          # dense route (prime factors)
-                   (16, 12, 24), (48, 9, 32), (27, 6, 40),        # FFT route (radix 4/2/3)
-                   (32, 8, 64), (128, 4, 16), (1024, 2, 3)]       # register-radix route (2^k)
+                   (16, 12, 24), (48, 9, 32), (27, 6, 40),        # generic FFT route (radix 4/2/3) and 3 * 2^k
+                   (32, 8, 64), (128, 4, 16), (1024, 2, 3),       # register-radix route (2^k)
+                   (96, 6, 24), (384, 2, 3), (768, 2, 2)]         # register-radix route (3 * 2^k)
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -108,9 +109,11 @@ def test_fft_and_dense_routes_agree(monkeypatch):
 
 @pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (MIXED, 3e-6)])
 def test_fft_register_and_generic_routes_agree(monkeypatch, prec, tol):
-    """Power-of-two lengths take the register-radix kernels; the generic Stockham kernels
-    (DTT_FFT_GENERIC=1) give the same transforms and the same Green step."""
-    for seed, nvox in enumerate([(8, 16, 32), (64, 8, 16), (127, 4, 8), (256, 3, 4)]):
+    """Lengths 2^k and 3 * 2^k take the register-radix kernels; the generic Stockham kernels
+    (DTT_FFT_GENERIC=1) give the same transforms and the same Green step (the fused z pass
+    included: z lengths 64, 16, 48, 96, 384 and their periodic halves)."""
+    for seed, nvox in enumerate([(8, 16, 32), (64, 8, 16), (127, 4, 8), (256, 3, 4),
+                                 (48, 24, 24), (96, 5, 48), (12, 6, 192)]):
         spec = _spec(seed, nvox=nvox, periodic_prob=0.4, anchored=False)
         pb, _ = oracle_problem(spec)
         g = gpu_grid(spec, prec)
@@ -135,7 +138,7 @@ def test_fft_register_and_generic_routes_agree(monkeypatch, prec, tol):
 @pytest.mark.parametrize("scheme", [wl.TETRA2, wl.HEX1])
 @pytest.mark.parametrize("seed", range(5))
 @pytest.mark.parametrize("prec,tol", [(FP64, 1e-11), (MIXED, 2e-6)])
-@pytest.mark.parametrize("nvox", [(37, 10, 19), (32, 12, 18)])
+@pytest.mark.parametrize("nvox", [(37, 10, 19), (32, 12, 18), (24, 12, 48)])
 def test_green_step(scheme, seed, prec, tol, nvox):
     spec = _spec(seed, nvox=nvox, scheme=scheme, periodic_prob=0.3, anchored=False)
     pb, _ = oracle_problem(spec)
