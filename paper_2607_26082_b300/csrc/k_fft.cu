@@ -717,6 +717,22 @@ __device__ __forceinline__ T fast_post(const T* buf, int pb, int k, int n, int t
   return (k >= 1) ? (imf ? -e.x : e.y) * inv_n : (T)0;
 }
 
+// Row pb and position j of element idx of a block of consecutive rows of nn values
+// (idx < 2^23): a float estimate of the quotient, off by at most one, then corrected.
+__device__ __forceinline__ void row_pos(int idx, int nn, float rnn, int& pb, int& j) {
+  int q = __float2int_rz((float)idx * rnn);
+  int r = idx - q * nn;
+  if (r < 0) {
+    --q;
+    r += nn;
+  } else if (r >= nn) {
+    ++q;
+    r -= nn;
+  }
+  pb = q;
+  j = r;
+}
+
 template <typename T, int L>
 __host__ __device__ constexpr size_t fast_smem(int extra_bytes) {
   return (size_t)FastMap<L>::WORDS * sizeof(T) + (size_t)L * sizeof(Cx<T>) +
@@ -751,9 +767,33 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   // global loads in groups of FB per thread before they are placed, so that several are in
   // flight at once
   constexpr int FB = 4;
+  // x axis: a warp per pencil row when the rows divide evenly among the warps, else the
+  // CTA's rows (consecutive in memory) as one block spread over all threads
+  constexpr bool WARP_ROWS = NPEN % NW == 0;
+  const float rnn = 1.0f / (float)nn;
   by_type(type, [&](auto ty) {
     constexpr int TY = decltype(ty)::value;
-    if (p.axis == 0) {
+    if (p.axis == 0 && !WARP_ROWS) {
+      const T* blk = src + sbase[0];
+      const int tot = npen * nn;
+      for (int i0 = tid; i0 < tot; i0 += NTH * FB) {
+        T v[FB];
+        #pragma unroll
+        for (int u = 0; u < FB; ++u) {
+          const int idx = i0 + NTH * u;
+          v[u] = idx < tot ? blk[idx] : (T)0;
+        }
+        #pragma unroll
+        for (int u = 0; u < FB; ++u) {
+          const int idx = i0 + NTH * u;
+          if (idx < tot) {
+            int pb, j;
+            row_pos(idx, nn, rnn, pb, j);
+            fast_place<T, L>(buf, pb, j, v[u], n, TY, p.inverse);
+          }
+        }
+      }
+    } else if (p.axis == 0) {
       const int warp = tid >> 5, lane = tid & 31;
       for (int pb = warp; pb < npen; pb += NW) {
         const T* row = src + sbase[pb];
@@ -804,7 +844,13 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
       if (p.incr) add_to_u<T>(e, v, p);
       else out[e] = v;
     };
-    if (p.axis == 0) {
+    if (p.axis == 0 && !WARP_ROWS) {
+      for (int idx = tid; idx < npen * nn; idx += NTH) {
+        int pb, k;
+        row_pos(idx, nn, rnn, pb, k);
+        emit(pb, k);
+      }
+    } else if (p.axis == 0) {
       const int warp = tid >> 5, lane = tid & 31;
       for (int pb = warp; pb < npen; pb += NW)
         for (int k = lane; k < nn; k += 32) emit(pb, k);
