@@ -10,6 +10,8 @@ so the checks use properties that hold at any size:
     value at an interior node depends only on the 27 nodes and 8 voxels around it, so the
     oracle evaluates it on a 2x2x2-voxel window cut from the full grid, at sampled nodes
     (half of them next to a phase interface), in small and in finite strain.
+  * Contact (Algorithm 2): the first increment's converged state satisfies Eq. 33 and the
+    force balance of Section 5.4.
 
 Tolerances as in test_gpu_parity.py: FP64 1e-11 relative; mixed 2e-6 of the field scale
 for the residual operator, 5e-6 for the Green step of a single mode on these long axes.
@@ -129,3 +131,32 @@ def test_residual_operator_full_size_sampled(case, kin, prec, tol):
     assert np.abs(got_pt - ref_pt).max() <= tol * scale_pt
     # the interface samples do see both phases
     assert len(nodes) > 100 or len(np.unique(spec["phase"])) == 1
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_contact_full_size_first_increment(case):
+    """Algorithm 2 on the full grid, mixed precision, first increment from u~ = 0 (d/R =
+    0.001), in the runner's configuration (tolerance 1e-6, Anderson every 3 iterations):
+    Eq. 33 complementarity at convergence (no penetration, no tensile reaction, zero gap on
+    the contact set).  On the 256x256x128 block, the contact force equals the volume average
+    of sigma_zz times the top face's area (Section 5.4)."""
+    spec = CASES[case]()
+    I = spec["indenter"]
+    g = gpu_grid(spec, MIXED)
+    g.dtt_set_indenter(I["axis"], I["face"], I["centers"][0], I["radius"])
+    g.dtt_move_indenter(I["centers"][0])
+    rep = g.dtt_solve_step(1e-6, 20000, acv_mod=spec["acv_mod"], init=dtt.INIT_ZERO, graph_iters=16)
+    assert rep.status == dtt.OK, rep.as_dict()
+    act, gap, fn, force = g.dtt_get_contact()
+    assert act.sum() >= 5
+    assert gap.min() >= -1e-6 * I["radius"]
+    assert np.abs(gap[act]).max() <= 1e-6 * I["radius"]
+    assert (fn[act] <= 1e-8 * np.abs(fn).max()).all()
+    assert force[2] < 0.0
+    if case == "indentation_256x256x128":
+        sig = g.dtt_get_stress_tensor()
+        w = 0.5 if sig.shape[3] == 2 else 1.0
+        mean_zz = w * sig[..., 2, 2].sum() / float(np.prod(spec["nvox"]))
+        area = spec["nvox"][0] * spec["nvox"][1] * spec["h"] ** 2
+        assert abs(mean_zz * area - force[2]) <= 1e-5 * abs(force[2])   # measured 2e-7
+    g.close()
