@@ -825,9 +825,12 @@ dtt_status dtt_set_material(dtt_grid* G, const uint8_t* phase, int32_t nphase, c
   }
   CK(cudaMemcpy(G->d_lam, lambda, nphase * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(G->d_mu, mu, nphase * sizeof(double), cudaMemcpyHostToDevice));
+  // The captured iteration reads the phase ids and the Lame tables through device
+  // pointers, with the phase count by value: new values for as many phases keep it valid.
+  const bool same_layout = G->mat_set && G->nphase == nphase;
   G->nphase = nphase;
   G->mat_set = true;
-  invalidate_graph(G);
+  if (!same_layout) invalidate_graph(G);
   return DTT_OK;
 }
 
@@ -971,7 +974,10 @@ dtt_status dtt_set_constraints(dtt_grid* G, int32_t n_rows, const int32_t* row_p
       vaa.push_back(saa);
     }
   }
-  free_rows(G);
+  // Rows of the same count and total length reuse the device buffers; the captured
+  // iteration, which holds their addresses and the row count, then stays valid.
+  const bool same_layout = n_rows == G->nrows && dof.size() == G->h_dof.size() && (n_rows == 0 || G->d_ptr);
+  if (!same_layout) free_rows(G);
   G->nrows = n_rows;
   G->h_ptr = ptr;
   G->h_dof = dof;
@@ -982,15 +988,18 @@ dtt_status dtt_set_constraints(dtt_grid* G, int32_t n_rows, const int32_t* row_p
   G->h_aa = vaa;
   if (n_rows > 0) {
     size_t ne = dof.size();
-    dtt_status s = dalloc(&G->d_ptr, (n_rows + 1) * sizeof(int));
-    if (s == DTT_OK) s = dalloc(&G->d_dof, ne * sizeof(long long));
-    if (s == DTT_OK) s = dalloc(&G->d_a, ne * sizeof(double));
-    if (s == DTT_OK) s = dalloc(&G->d_b, ne * sizeof(double));
-    if (s == DTT_OK) s = dalloc(&G->d_target, n_rows * sizeof(double));
-    if (s == DTT_OK) s = dalloc(&G->d_mult, n_rows * sizeof(double));
-    if (s == DTT_OK) s = dalloc(&G->d_ab, n_rows * sizeof(double));
-    if (s == DTT_OK) s = dalloc(&G->d_aa, n_rows * sizeof(double));
-    if (s != DTT_OK) { G->nrows = 0; return s; }
+    dtt_status s = DTT_OK;
+    if (!same_layout) {
+      s = dalloc(&G->d_ptr, (n_rows + 1) * sizeof(int));
+      if (s == DTT_OK) s = dalloc(&G->d_dof, ne * sizeof(long long));
+      if (s == DTT_OK) s = dalloc(&G->d_a, ne * sizeof(double));
+      if (s == DTT_OK) s = dalloc(&G->d_b, ne * sizeof(double));
+      if (s == DTT_OK) s = dalloc(&G->d_target, n_rows * sizeof(double));
+      if (s == DTT_OK) s = dalloc(&G->d_mult, n_rows * sizeof(double));
+      if (s == DTT_OK) s = dalloc(&G->d_ab, n_rows * sizeof(double));
+      if (s == DTT_OK) s = dalloc(&G->d_aa, n_rows * sizeof(double));
+    }
+    if (s != DTT_OK) { G->nrows = 0; invalidate_graph(G); return s; }
     CK(cudaMemcpy(G->d_ptr, ptr.data(), (n_rows + 1) * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(G->d_dof, dof.data(), ne * sizeof(long long), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(G->d_a, va.data(), ne * sizeof(double), cudaMemcpyHostToDevice));
@@ -999,9 +1008,10 @@ dtt_status dtt_set_constraints(dtt_grid* G, int32_t n_rows, const int32_t* row_p
     CK(cudaMemcpy(G->d_aa, vaa.data(), n_rows * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemset(G->d_mult, 0, n_rows * sizeof(double)));
   }
+  const double* part_before = G->d_part;
   dtt_status s = ensure_partials(G);
   if (s != DTT_OK) return s;
-  invalidate_graph(G);
+  if (!same_layout || G->d_part != part_before) invalidate_graph(G);
   return rebuild_cmask(G);
 }
 

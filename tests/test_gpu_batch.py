@@ -146,3 +146,34 @@ def test_batch_with_finite_strain_and_isotropic_cells(kind):
         assert rep.status == dtt.OK and rep.iterations == it
         assert np.array_equal(g.dtt_get_fields(), u)
         g.close()
+
+
+@pytest.mark.parametrize("prec", [dtt.PREC_FP64, dtt.PREC_MIXED])
+def test_new_values_in_same_layout_keep_graph_and_match_fresh_grid(prec):
+    """New Lame values for the same number of phases, and new constraint values for the same
+    rows, are taken in place: the captured iteration stays, and the next solve equals a
+    fresh grid's bit for bit (and differs from the solve with the old values)."""
+    from paper_2607_26082_b300 import rows as prow
+    spec = wl.random_problem(21, nvox=(12, 10, 9))
+    ptr, node, comp, a, b, val = prow.csr_from_intents(spec["nvox"], spec["bc"], spec["intents"])
+    g = gpu_grid(spec, prec)
+    g.dtt_solve_step(1e-6, 3000, acv_mod=2, init=dtt.INIT_ZERO)
+    u_old = g.dtt_get_fields()
+    lam2, mu2, val2 = 1.7 * spec["lam"], 0.6 * spec["mu"], 1.5 * val + 1e-3
+    g.dtt_set_material(spec["phase"], lam2, mu2)
+    g.dtt_set_constraints(ptr, node, comp, a, b, val2)
+    r1 = g.dtt_solve_step(1e-6, 3000, acv_mod=2, init=dtt.INIT_ZERO)
+    spec2 = dict(spec, lam=lam2, mu=mu2)
+    g2 = gpu_grid(spec2, prec)
+    g2.dtt_set_constraints(ptr, node, comp, a, b, val2)
+    r2 = g2.dtt_solve_step(1e-6, 3000, acv_mod=2, init=dtt.INIT_ZERO)
+    assert r1.status == r2.status == dtt.OK
+    assert r1.iterations == r2.iterations
+    u1, u2 = g.dtt_get_fields(), g2.dtt_get_fields()
+    assert np.array_equal(u1, u2)
+    assert rel_l2(u1, u_old) > 1e-3
+    per1, _ = g.dtt_get_reactions(len(val))
+    per2, _ = g2.dtt_get_reactions(len(val))
+    assert np.array_equal(per1, per2)
+    g.close()
+    g2.close()
