@@ -75,7 +75,9 @@ dtt_status dtt_grid_sizes(const dtt_grid* grid, int64_t* n_nodes, int64_t* n_vox
 
 /* Material (Eq. 1: sigma = C : eps, isotropic per phase, Section 5.4 convention
  * sigma = lambda tr(eps) 1 + 2 mu eps).  phase: n_voxels uint8 ids (< nphase <= 256).
- * lambda, mu: host arrays of nphase values (>= 0).  Errors: DTT_ERR_ARG. */
+ * lambda, mu: host arrays of nphase values (>= 0).  Errors: DTT_ERR_ARG.  New values for
+ * the same nphase are taken in place and keep the captured iteration graph; another
+ * nphase invalidates it. */
 dtt_status dtt_set_material(dtt_grid* grid, const uint8_t* phase, int32_t nphase,
                             const double* lambda, const double* mu, int32_t phase_is_device);
 
@@ -118,7 +120,9 @@ dtt_status dtt_set_kinematics(dtt_grid* grid, int32_t kinematics);
  * by a Dirichlet face (DTT_ERR_ARG), and must not use a component whose Green symbol has
  * null modes, i.e. whose transforms keep q = 0 (or the TETRA2 checkerboard / a HEX1
  * hourglass) on every axis -- such a component needs a Dirichlet face, e.g. behind a void
- * buffer layer as in Section 4.1.2 (DTT_ERR_NULLMODE).  n_rows = 0 clears the rows. */
+ * buffer layer as in Section 4.1.2 (DTT_ERR_NULLMODE).  n_rows = 0 clears the rows.
+ * Rows with the same count and total number of entries as the current ones reuse their
+ * device buffers and keep the captured iteration graph; other rows invalidate it. */
 dtt_status dtt_set_constraints(dtt_grid* grid, int32_t n_rows, const int32_t* row_ptr,
                                const int32_t* node, const int8_t* comp, const double* a,
                                const double* b, const double* value);
