@@ -29,7 +29,8 @@ the phases); --medium picks the reference medium
 exactly K iterations (tolerance 0) of the first load step, which is the
 short, fixed launch sequence a profiler wants; --tol runs to convergence.  For the
 indentation block every load step moves the sphere (Algorithm 2, one increment each),
-starting from the previous step's solution.  Prints one JSON report per step.
+starting from the previous step's solution.  --tune runs dtt_autotune on the grid first
+(outside the reported step times).  Prints one JSON report per step.
 """
 import argparse
 import json
@@ -124,7 +125,9 @@ def main(argv=None):
     ap.add_argument("--acv-mod", type=int, default=0, help="0: the workload's")
     ap.add_argument("--cells", type=int, default=256)
     ap.add_argument("--seed0", type=int, default=1000)
-    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="batch: keep the built-in tiling")
+    ap.add_argument("--tune", action="store_true",
+                    help="single grid: dtt_autotune before the first step (residual z chunk, FFT route)")
     ap.add_argument("--sequential", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--iters", type=int, default=0, help="fixed iteration count (tolerance 0)")
@@ -162,6 +165,11 @@ def main(argv=None):
     nsteps = min(a.steps, len(ind["centers"])) if ind else 1
     if ind:
         g.dtt_set_indenter(ind["axis"], ind["face"], ind["centers"][0], ind["radius"])
+    tuning = None
+    if a.tune:
+        t = g.dtt_autotune(iters=4, acv_mod=a.acv_mod or spec["acv_mod"])
+        tuning = {"residual_zchunk": t.residual_zchunk, "fft_generic": t.fft_generic,
+                  "ms_per_iteration": t.ms_per_iteration}
     for s in range(nsteps):
         if ind:
             g.dtt_move_indenter(ind["centers"][s])
@@ -171,6 +179,8 @@ def main(argv=None):
         out = {"workload": spec["name"], "precision": a.precision, "kinematics": a.kinematics, "step": s,
                "medium": spec.get("medium", "paux"), "scheme": "tetra2" if spec["scheme"] == wl.TETRA2 else "hex1",
                "acv_on": a.acv_on, "acv_mod": a.acv_mod or spec["acv_mod"]}
+        if tuning:
+            out["tuning"] = tuning
         out.update(rep.as_dict())
         if "ligament_rows" in spec and g.n_rows:
             per, _ = g.dtt_get_reactions(g.n_rows)
