@@ -676,6 +676,23 @@ __device__ __forceinline__ void fast_place(T* buf, int pb, int j, T v, int n, in
   }
 }
 
+// The positions of pencil pb's extended sequence that fast_place leaves unwritten, set to
+// zero (instead of clearing the whole buffer before the fill): 0 and n for DST1, n for the
+// forward DCT3 extension, 0 for the forward DST3 extension.  DCT1, the Hartley sequence and
+// the inverse quarter-wave extensions write every position.
+template <typename T, int L, int TY>
+__device__ __forceinline__ void fast_holes(T* buf, int pb, int n, int inverse) {
+  const int arr = pb & 1, seq = pb >> 1;
+  if (TY == T_DST1) {
+    buf[FastMap<L>::at(arr, seq, 0)] = (T)0;
+    buf[FastMap<L>::at(arr, seq, n)] = (T)0;
+  } else if (TY == T_DCT3 && !inverse) {
+    buf[FastMap<L>::at(arr, seq, n)] = (T)0;
+  } else if (TY == T_DST3 && !inverse) {
+    buf[FastMap<L>::at(arr, seq, 0)] = (T)0;
+  }
+}
+
 // Transform value of pencil pb at position k from the FFT result of its pair (post_value on
 // the padded arrays).
 template <typename T, int L>
@@ -762,7 +779,11 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   const int n = p.n, nn = p.nn;
   pencil_bases<T, SEQ>(sbase, p, pen0, tid);
   for (int q = tid; q < L; q += NTH) tws[q] = ((const Cx<T>*)p.tw)[q];
-  for (int q = tid; q < WORDS; q += NTH) buf[q] = (T)0;
+  // A full CTA writes every position of its sequences (the fill, then fast_holes); the last
+  // CTA of a launch may hold fewer pencils, whose partners must then read as zero.
+  const bool full = npen == NPEN;
+  if (!full)
+    for (int q = tid; q < WORDS; q += NTH) buf[q] = (T)0;
   __syncthreads();
   // global loads in groups of FB per thread before they are placed, so that several are in
   // flight at once
@@ -828,6 +849,8 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
         }
       }
     }
+    if (full)
+      for (int pb = tid; pb < NPEN; pb += NTH) fast_holes<T, L, TY>(buf, pb, n, p.inverse);
   });
   __syncthreads();
   const bool quarter = (type == T_DCT3 || type == T_DST3);
@@ -905,7 +928,10 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
     zs[q] = gt_s<T>(gt, comp, 2, q);
     zc[q] = gt_c<T>(gt, comp, 2, q);
   }
-  for (int q = tid; q < WORDS; q += NTH) buf[q] = (T)0;
+  // see k_fft_fast: only a partial CTA clears its buffer, a full one writes the holes
+  const bool full = npen == NPEN;
+  if (!full)
+    for (int q = tid; q < WORDS; q += NTH) buf[q] = (T)0;
   __syncthreads();
   const bool quarter = (type == T_DCT3 || type == T_DST3);
   const T inv_n = sizeof(T) == 4 ? (T)p.finv_n : (T)p.inv_n;
@@ -927,6 +953,8 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
         if (idx < NPEN * nn && pb < npen) fast_place<T, L>(buf, pb, j, v[u], n, TY, 0);
       }
     }
+    if (full)
+      for (int pb = tid; pb < NPEN; pb += NTH) fast_holes<T, L, TY>(buf, pb, n, 0);
     __syncthreads();
     fast_fft<T, L>(buf, tws, -1, tid / NT, tid % NT, quarter ? ph : nullptr);
     // Green multiply into spec
@@ -956,12 +984,16 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
     }
     __syncthreads();
     // inverse along z
-    for (int q = tid; q < WORDS; q += NTH) buf[q] = (T)0;
-    __syncthreads();
+    if (!full) {
+      for (int q = tid; q < WORDS; q += NTH) buf[q] = (T)0;
+      __syncthreads();
+    }
     for (int idx = tid; idx < NPEN * nn; idx += NTH) {
       const int pb = idx % NPEN, j = idx / NPEN;
       if (pb < npen) fast_place<T, L>(buf, pb, j, spec[pb * nn + j], n, TY, 1);
     }
+    if (full)
+      for (int pb = tid; pb < NPEN; pb += NTH) fast_holes<T, L, TY>(buf, pb, n, 1);
     __syncthreads();
     fast_fft<T, L>(buf, tws, quarter ? 1 : -1, tid / NT, tid % NT, nullptr);
     for (int idx = tid; idx < NPEN * nn; idx += NTH) {
