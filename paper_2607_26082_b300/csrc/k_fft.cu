@@ -23,7 +23,9 @@
 
 namespace dtt {
 
-template <typename T> struct Cx { T x, y; };
+// Aligned to its full size, so that a complex value is one 64-bit (FP32) or 128-bit (FP64)
+// access: every array of them starts at a cudaMalloc base or a 16-byte-aligned shared offset.
+template <typename T> struct __align__(2 * sizeof(T)) Cx { T x, y; };
 
 template <typename T>
 __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
