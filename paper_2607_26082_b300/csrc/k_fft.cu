@@ -519,15 +519,60 @@ __device__ __forceinline__ void dft8(Cx<T>* v, int s) {
   v[1] = a[4]; v[5] = a[5]; v[3] = a[6]; v[7] = a[7];
 }
 
+// Radix of the register-radix pass at stride NS (0: past the last pass).
+template <int L, int NS>
+__host__ __device__ constexpr int fast_radix() {
+  constexpr int P2 = FastPlan<L>::P2;
+  return (NS * 8 <= P2) ? 8 : (NS * 4 == P2) ? 4 : (NS * 2 == P2) ? 2 : (NS == P2 && P2 != L) ? 3 : 0;
+}
+
+// Pass twiddles in shared memory, pass after pass, each as [k][r - 1] (k < NS, 1 <= r < R):
+// entry w(k, r) = e^{-2 pi i k r / (NS R)} is copied from the length-L table at k r L / (NS R).
+// The threads of a warp take consecutive k, so one r reads NS-strided words in the
+// length-L table (bank conflicts) but a stride of R - 1 here.  The tables hold at most L
+// entries in all.  OFF is the start of the pass at stride NS.
+template <int L, int NS = 1>
+__host__ __device__ constexpr int fast_tw_off() {
+  if constexpr (NS == 1) {
+    return 0;
+  } else {
+    // sum over the passes before stride NS: strides NS' > 1 with radix R'
+    int off = 0;
+    int ns = 1;
+    while (ns < NS) {
+      const int r = (ns * 8 <= FastPlan<L>::P2) ? 8 : (ns * 4 == FastPlan<L>::P2) ? 4 : (ns * 2 == FastPlan<L>::P2) ? 2 : 3;
+      if (ns > 1) off += ns * (r - 1);
+      ns *= r;
+    }
+    return off;
+  }
+}
+
+template <typename T, int L, int NS = 1>
+__device__ __forceinline__ void fast_tw_fill(Cx<T>* twp, const Cx<T>* __restrict__ tw, int tid, int nthr) {
+  constexpr int R = fast_radix<L, NS>();
+  if constexpr (R != 0) {
+    if constexpr (NS > 1) {
+      constexpr int TWS = L / (NS * R), CNT = NS * (R - 1), OFF = fast_tw_off<L, NS>();
+      for (int q = tid; q < CNT; q += nthr) {
+        const int k = q / (R - 1), r = q - k * (R - 1) + 1;
+        twp[OFF + q] = tw[k * r * TWS];
+      }
+    }
+    fast_tw_fill<T, L, NS * R>(twp, tw, tid, nthr);
+  }
+}
+
 // One in-place Stockham pass of radix R (stride NS) over the CTA's sequences; thread t of
 // sequence `seq` takes butterflies t, t + NT, ... (8 / R of them).  With `mod`, the inputs
 // are first multiplied by mod[index] (quarter-wave modulation of the forward transforms).
+// tw: the pass twiddle tables of fast_tw_fill.
 template <typename T, int L, int R, int NS>
 __device__ __forceinline__ void fast_pass(T* buf, const Cx<T>* __restrict__ tw, int sgn, int seq, int t,
                                           const Cx<T>* __restrict__ mod) {
   using M = FastMap<L>;
   constexpr int NT = FastPlan<L>::NT;
-  constexpr int LR = L / R, PER = 8 / R, TWS = L / (NS * R);
+  constexpr int LR = L / R, PER = 8 / R, OFF = fast_tw_off<L, NS>();
   Cx<T> v[PER][R];
   #pragma unroll
   for (int m = 0; m < PER; ++m) {
@@ -542,7 +587,7 @@ __device__ __forceinline__ void fast_pass(T* buf, const Cx<T>* __restrict__ tw, 
     if (NS > 1) {
       #pragma unroll
       for (int r = 1; r < R; ++r) {
-        Cx<T> w = tw[k * r * TWS];
+        Cx<T> w = tw[OFF + k * (R - 1) + (r - 1)];
         if (sgn > 0) w.y = -w.y;
         v[m][r] = cmul(v[m][r], w);
       }
@@ -573,7 +618,7 @@ template <typename T, int L, int NS>
 __device__ __forceinline__ void fast_pass3(T* buf, const Cx<T>* __restrict__ tw, int sgn, int seq, int t) {
   using M = FastMap<L>;
   constexpr int NT = FastPlan<L>::NT;
-  constexpr int LR = L / 3, PER = (LR + NT - 1) / NT, TWS = L / (NS * 3);
+  constexpr int LR = L / 3, PER = (LR + NT - 1) / NT, OFF = fast_tw_off<L, NS>();
   static_assert(NS * 3 == L && PER == 3, "radix-3 pass closes 3 * 2^k");
   Cx<T> v[PER][3];
   #pragma unroll
@@ -588,7 +633,7 @@ __device__ __forceinline__ void fast_pass3(T* buf, const Cx<T>* __restrict__ tw,
       }
       #pragma unroll
       for (int r = 1; r < 3; ++r) {
-        Cx<T> w = tw[k * r * TWS];
+        Cx<T> w = tw[OFF + k * 2 + (r - 1)];
         if (sgn > 0) w.y = -w.y;
         v[m][r] = cmul(v[m][r], w);
       }
@@ -780,7 +825,7 @@ k_fft_fast(const T* __restrict__ in, T* __restrict__ out, FftParams p, const Ctr
   const int npen = (int)min((long long)NPEN, p.npencil - pen0);
   const int n = p.n, nn = p.nn;
   pencil_bases<T, SEQ>(sbase, p, pen0, tid);
-  for (int q = tid; q < L; q += NTH) tws[q] = ((const Cx<T>*)p.tw)[q];
+  fast_tw_fill<T, L>(tws, (const Cx<T>*)p.tw, tid, NTH);
   // A full CTA writes every position of its sequences (the fill, then fast_holes); the last
   // CTA of a launch may hold fewer pencils, whose partners must then read as zero.
   const bool full = npen == NPEN;
@@ -925,7 +970,7 @@ k_fft_fast_z_green(const T* __restrict__ in, T* __restrict__ out, FftParams p, G
     pxy[q][2] = gt_s<T>(gt, comp, 1, iy);
     pxy[q][3] = gt_c<T>(gt, comp, 1, iy);
   }
-  for (int q = tid; q < L; q += NTH) tws[q] = ((const Cx<T>*)p.tw)[q];
+  fast_tw_fill<T, L>(tws, (const Cx<T>*)p.tw, tid, NTH);
   for (int q = tid; q < nn; q += NTH) {
     zs[q] = gt_s<T>(gt, comp, 2, q);
     zc[q] = gt_c<T>(gt, comp, 2, q);
