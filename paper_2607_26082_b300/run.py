@@ -12,7 +12,8 @@
 The batch workload draws N uneven two-phase cells (edges 32, 48, 64, 96), tunes the kernel
 tiling once per cell size (dtt_autotune on one cell, dtt_set_tuning on the others) and
 solves all cells with one dtt_batch_solve; --sequential also solves them one after the
-other with dtt_solve_step for comparison.
+other with dtt_solve_step for comparison.  Under torchrun (one rank per GPU) each rank
+takes its share of the cells by voxel count and rank 0 prints the merged report.
 
 --kinematics fs solves with the finite-strain stress step (Section 5.2, Algorithm 3 for
 the indentation); --r0-scale multiplies the workload's reference medium (the paper takes a
@@ -76,7 +77,17 @@ def make_workload(name, nvox=None, load_steps=None, contrast=4.0):
 
 def run_batch(a, prec):
     import time
-    cells = wl.batch_cells(a.cells, seed0=a.seed0)
+    from . import shard
+    rank, world, local = shard.rank_world()
+    all_cells = wl.batch_cells(a.cells, seed0=a.seed0)
+    if world > 1:
+        # one GPU per rank; the cells are split by voxel count, the reports gathered at the end
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    mine = shard.lpt_partition([int(np.prod(c["nvox"])) for c in all_cells], world)[rank]
+    cells = [all_cells[i] for i in mine]
     grids = [rows.setup_grid(c, prec) for c in cells]
     nvox = sum(int(np.prod(c["nvox"])) for c in cells)
     tuned = {}
@@ -106,9 +117,21 @@ def run_batch(a, prec):
         for g in grids:
             g.dtt_solve_step(1e-6, 20000, acv_mod=2, graph_iters=16)
         out["sequential_s"] = time.perf_counter() - t0
-    print(json.dumps(out), flush=True)
     for g in grids:
         g.close()
+    if world == 1:
+        print(json.dumps(out), flush=True)
+        return 0
+    part = {"cells": mine, "voxels": nvox, "voxel_iters": vi, "batch_s": dt,
+            "cell_iterations": [r.iterations for r in reps], "failed": [mine[i] for i in out["failed"]]}
+    per_rank = shard.gather_to_root(part, rank, world)
+    if rank == 0:
+        merged = shard.merge_reports(per_rank)
+        merged.update({"workload": "batch of %d two-phase cells" % len(all_cells), "precision": a.precision,
+                       "split": "cells across ranks by voxel count, longest first"})
+        print(json.dumps(merged), flush=True)
+    import torch.distributed as dist
+    dist.destroy_process_group()
     return 0
 
 
