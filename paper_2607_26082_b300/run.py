@@ -103,14 +103,15 @@ def run_batch(a, prec):
     out = {"workload": "batch of %d two-phase cells" % len(cells), "precision": a.precision,
            "voxels": nvox, "tuning_s": t_tune,
            "tuning": {str(k): v.as_dict() for k, v in tuned.items()}}
-    for rep_i in range(2):   # the first call captures the batch graph
+    st, reps, dt = dtt.OK, [], 0.0   # a rank can be left without cells when ranks outnumber them
+    for rep_i in range(2 if grids else 0):   # the first call captures the batch graph
         t0 = time.perf_counter()
         st, reps = dtt.dtt_batch_solve(grids, 1e-6, 20000, acv_mod=2, graph_iters=16)
         dt = time.perf_counter() - t0
     vi = sum(int(np.prod(c["nvox"])) * r.iterations for c, r in zip(cells, reps))
-    out.update({"status": st, "batch_s": dt, "voxel_iters": vi, "voxel_iters_per_s": vi / dt,
-                "iterations": {"min": min(r.iterations for r in reps), "max": max(r.iterations for r in reps),
-                               "mean": float(np.mean([r.iterations for r in reps]))},
+    its = [r.iterations for r in reps]
+    out.update({"status": st, "batch_s": dt, "voxel_iters": vi, "voxel_iters_per_s": vi / dt if dt > 0 else 0.0,
+                "iterations": {"min": min(its), "max": max(its), "mean": float(np.mean(its))} if its else None,
                 "failed": [i for i, r in enumerate(reps) if r.status != dtt.OK]})
     if a.sequential:
         t0 = time.perf_counter()
