@@ -155,6 +155,9 @@ def main(argv=None):
     ap.add_argument("--sequential", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--iters", type=int, default=0, help="fixed iteration count (tolerance 0)")
+    ap.add_argument("--repeat", type=int, default=1,
+                    help="with --iters: solve the first step this many times in one process and "
+                         "report every repetition's time per iteration (the first includes one-time set-up)")
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--steps", type=int, default=1, help="load steps (indentation only)")
     ap.add_argument("--graph-iters", type=int, default=0)
@@ -197,14 +200,19 @@ def main(argv=None):
     for s in range(nsteps):
         if ind:
             g.dtt_move_indenter(ind["centers"][s])
-        rep = g.dtt_solve_step(tol, max_iter, acv_mod=a.acv_mod or spec["acv_mod"],
-                               acv_on=dtt.ACV_P if a.acv_on == "p" else dtt.ACV_U,
-                               init=dtt.INIT_PREVIOUS if s else dtt.INIT_ZERO, graph_iters=a.graph_iters)
+        reps_ms = []
+        for _ in range(max(1, a.repeat) if (a.iters > 0 and s == 0) else 1):
+            rep = g.dtt_solve_step(tol, max_iter, acv_mod=a.acv_mod or spec["acv_mod"],
+                                   acv_on=dtt.ACV_P if a.acv_on == "p" else dtt.ACV_U,
+                                   init=dtt.INIT_PREVIOUS if s else dtt.INIT_ZERO, graph_iters=a.graph_iters)
+            reps_ms.append(1e3 * rep.seconds / max(rep.iterations, 1))
         out = {"workload": spec["name"], "precision": a.precision, "kinematics": a.kinematics, "step": s,
                "medium": spec.get("medium", "paux"), "scheme": "tetra2" if spec["scheme"] == wl.TETRA2 else "hex1",
                "acv_on": a.acv_on, "acv_mod": a.acv_mod or spec["acv_mod"]}
         if tuning:
             out["tuning"] = tuning
+        if len(reps_ms) > 1:
+            out["repeat_ms_per_iteration"] = reps_ms
         out.update(rep.as_dict())
         if "ligament_rows" in spec and g.n_rows:
             per, _ = g.dtt_get_reactions(g.n_rows)
