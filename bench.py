@@ -182,7 +182,7 @@ def launches_per_iteration(has_rows, has_contact, acv):
     n += 5                     # x, y forward; z forward + Green + z inverse; y, x inverse + increment
     n += 1 if has_rows else 0  # proj_U
     n += 1 if has_contact else 0
-    n += 1                     # ctrl end
+    n += 0 if (has_rows and not has_contact) else 1   # ctrl end (else done by proj_U's last CTA)
     return n
 
 

@@ -504,9 +504,14 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
                        : enqueue_green<T>(G, (const T*)G->gbuf, nullptr, (T*)G->spec2, (T*)G->spec, true, ctrl, 0, 3);
   if (st != DTT_OK) return st;
   prof_mark(7, s);
-  if (G->nrows > 0) CKL(launch_proj_U_rows<T>(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, (T*)G->step, ctrl, s));
-  if (G->contact) CKL(launch_contact_proj_U<T>(ca, G->u64, G->uhi, G->ulo, (T*)G->step, s));
-  CKL(launch_ctrl_end(ctrl, s));
+  if (G->nrows > 0 && !G->contact) {
+    // the rows' projection is the last step: its last CTA ends the iteration
+    CKL(launch_proj_U_rows_end<T>(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, (T*)G->step, ctrl, s));
+  } else {
+    if (G->nrows > 0) CKL(launch_proj_U_rows<T>(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, (T*)G->step, ctrl, s));
+    if (G->contact) CKL(launch_contact_proj_U<T>(ca, G->u64, G->uhi, G->ulo, (T*)G->step, s));
+    CKL(launch_ctrl_end(ctrl, s));
+  }
   prof_mark(8, s);
   return DTT_OK;
 }

@@ -63,6 +63,7 @@ struct Ctrl {
   float alpha_f[4];   // the same coefficients in FP32 (set with alpha; read by FP32 kernels)
   double gram[4][4];
   double hist[HIST];
+  unsigned int blocks_done;   // CTAs of the current k_proj_U that have finished (end of iteration)
 };
 
 // Sparse constraint rows (CSR over entries), disjoint supports.
@@ -274,6 +275,11 @@ int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p_direct, void* co
 template <typename T>
 int launch_proj_U_rows(const GridDev& g, const RowsDev& r, double* u64, float* uhi, float* ulo,
                        T* step, const Ctrl* ctrl, cudaStream_t s);
+// The same projection, its last CTA also ending the iteration (the work of k_ctrl_end):
+// one launch fewer per iteration when the rows' projection is the iteration's last step.
+template <typename T>
+int launch_proj_U_rows_end(const GridDev& g, const RowsDev& r, double* u64, float* uhi, float* ulo,
+                           T* step, Ctrl* ctrl, cudaStream_t s);
 
 struct ContactArgs {
   GridDev g;

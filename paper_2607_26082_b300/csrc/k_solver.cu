@@ -136,20 +136,32 @@ int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p_direct, void* co
 // ------------------------------------------------------------------ proj_U (rows)
 // The correction applied to u~ is also added to the step field (the Anderson difference
 // form needs the full step u~_{i+1} - u~_i).
+// end: when set, the CTA that finishes last advances the iteration counters (k_ctrl_end).
 template <typename T>
-__global__ void k_proj_U(const RowsDev r, double* u64, float* uhi, float* ulo, T* step, const Ctrl* ctrl) {
+__global__ void k_proj_U(const RowsDev r, double* u64, float* uhi, float* ulo, T* step, const Ctrl* ctrl,
+                         Ctrl* end) {
   if (ctrl && ctrl->done) return;
   int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= r.nrows) return;
-  double sau = 0.0;
-  for (int e = r.ptr[row]; e < r.ptr[row + 1]; ++e) sau += r.a[e] * read_u(r.dof[e], u64, uhi, ulo);
-  double corr = (r.target[row] - sau) / r.aa[row];
-  for (int e = r.ptr[row]; e < r.ptr[row + 1]; ++e) {
-    if (r.a[e] == 0.0) continue;
-    long long d = r.dof[e];
-    double du = r.a[e] * corr;
-    write_u(d, read_u(d, u64, uhi, ulo) + du, u64, uhi, ulo);
-    if (step) step[d] = (T)((double)step[d] + du);
+  if (row < r.nrows) {
+    double sau = 0.0;
+    for (int e = r.ptr[row]; e < r.ptr[row + 1]; ++e) sau += r.a[e] * read_u(r.dof[e], u64, uhi, ulo);
+    double corr = (r.target[row] - sau) / r.aa[row];
+    for (int e = r.ptr[row]; e < r.ptr[row + 1]; ++e) {
+      if (r.a[e] == 0.0) continue;
+      long long d = r.dof[e];
+      double du = r.a[e] * corr;
+      write_u(d, read_u(d, u64, uhi, ulo) + du, u64, uhi, ulo);
+      if (step) step[d] = (T)((double)step[d] + du);
+    }
+  }
+  if (end && threadIdx.x == 0) {
+    // every CTA passed the done test above before its count; the last one to count ends
+    // the iteration and clears the count for the next
+    if (atomicAdd(&end->blocks_done, 1u) == gridDim.x - 1) {
+      end->iter += 1;
+      end->i_local += 1;
+      end->blocks_done = 0;
+    }
   }
 }
 
@@ -159,7 +171,17 @@ int launch_proj_U_rows(const GridDev& g, const RowsDev& r, double* u64, float* u
   (void)g;
   int blocks = (r.nrows + SB - 1) / SB;
   if (blocks == 0) return 0;
-  k_proj_U<T><<<blocks, SB, 0, s>>>(r, u64, uhi, ulo, step, ctrl);
+  k_proj_U<T><<<blocks, SB, 0, s>>>(r, u64, uhi, ulo, step, ctrl, nullptr);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_proj_U_rows_end(const GridDev& g, const RowsDev& r, double* u64, float* uhi, float* ulo, T* step,
+                           Ctrl* ctrl, cudaStream_t s) {
+  (void)g;
+  int blocks = (r.nrows + SB - 1) / SB;
+  if (blocks == 0) return launch_ctrl_end(ctrl, s);
+  k_proj_U<T><<<blocks, SB, 0, s>>>(r, u64, uhi, ulo, step, ctrl, ctrl);
   return (int)cudaGetLastError();
 }
 
@@ -847,6 +869,8 @@ template int launch_proj_P_rows<double>(const GridDev&, const RowsDev&, double*,
 template int launch_proj_P_rows<float>(const GridDev&, const RowsDev&, float*, void* const*, void* const*, int, int, double*, const Ctrl*, cudaStream_t);
 template int launch_proj_U_rows<double>(const GridDev&, const RowsDev&, double*, float*, float*, double*, const Ctrl*, cudaStream_t);
 template int launch_proj_U_rows<float>(const GridDev&, const RowsDev&, double*, float*, float*, float*, const Ctrl*, cudaStream_t);
+template int launch_proj_U_rows_end<double>(const GridDev&, const RowsDev&, double*, float*, float*, double*, Ctrl*, cudaStream_t);
+template int launch_proj_U_rows_end<float>(const GridDev&, const RowsDev&, double*, float*, float*, float*, Ctrl*, cudaStream_t);
 template int launch_contact_eval<double>(const ContactArgs&, double*, void* const*, void* const*, int, int, cudaStream_t);
 template int launch_contact_eval<float>(const ContactArgs&, float*, void* const*, void* const*, int, int, cudaStream_t);
 template int launch_contact_proj_U<double>(const ContactArgs&, double*, float*, float*, double*, cudaStream_t);
