@@ -18,9 +18,10 @@ Modules:
   kkt          -- element-by-element stiffness and dense multiplier solve (Section 4.3)
   hertz        -- Eq. 30
 
-Parity status: every function is pinned by a "not gpu" test except the Anderson
-combination rule (parity unpinned -- the paper cites the method without printing
-an accelerated iterate; it is checked only for self-consistency: the accelerated
-solve must reach the same solution as the dense multiplier system).
+Parity status: every function is pinned by a "not gpu" test.  The Anderson
+combination rule, which the paper cites without printing an accelerated iterate, is
+pinned by a closed form (the first accelerated iterate of an affine map whose start
+error lies in a four-dimensional invariant subspace) and by accelerated solves that
+reach the dense multiplier system's solution.
 """
 from . import transforms, discrete, constraints, solver, kkt, hertz  # noqa: F401

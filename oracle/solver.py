@@ -19,8 +19,11 @@ Readings where the paper is silent (the same readings are implemented by the CUD
     The constrained least squares is solved as G y = 1, alpha = y / sum(y), with
     G_kl = <R_k, R_l> (Euclidean, all nodal values) in float64 by Gaussian
     elimination with partial pivoting; if a pivot is <= 1e-14 * max_k G_kk or
-    sum(y) is 0 the acceleration is skipped for that iteration.  Parity unpinned:
-    the paper prints no accelerated iterate.
+    sum(y) is 0 the acceleration is skipped for that iteration.  The paper prints no
+    accelerated iterate; the rule is pinned by a closed form instead: for an affine map
+    whose start error lies in a four-dimensional invariant subspace, the first
+    accelerated iterate is fixed by a weighted least-norm problem over the cubic
+    residual polynomials (Lagrange form on the four eigenvalues, no Gram matrix).
   * Residual: Eq. 5 with RMS norms (discrete.residual_norm), evaluated on p after
     proj_P, as in Algorithm 1.  Algorithm 2 prints the test before
     proj_P; it is read in the same order, and the contact solve exits only when the

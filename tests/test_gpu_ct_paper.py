@@ -110,7 +110,8 @@ def test_ct_paper_weak_line_load():
 def test_ct_paper_acceleration_periods():
     """Table 1 at tolerance 1e-4, FP64: period 2 beats period 3 for Anderson on u~ and on
     p~, the paper's best choice being mod_ACV = 2.  The paper also finds p~ ahead of u~;
-    with this library's combination rule (the paper prints none, parity unpinned) the two
+    with this library's combination rule (the paper prints none; the oracle's is pinned by
+    a closed form) the two
     are close at period 2 and that ordering is not asserted.  All four runs reach the same
     reactions to the tolerance's accuracy."""
     spec = wl.ct_specimen("strong_line")
