@@ -1,19 +1,29 @@
 #!/usr/bin/env python3
-"""Benchmark: voxel-iterations/s and time to residual 1e-6 of the constrained DTT
-solver on one B300, mixed precision against the plain FP64 GPU solver.
+"""Benchmark: voxel-iterations/s and time to residual 1e-6 of the constrained DTT solver
+on one B300 -- learned start + mixed precision against the plain FP64 GPU solver.
 
-Workload (default): the upper half of a compact-tension-like plate in the paper's buffer
-device (Section 4.1.2), 128 x 128 x 32 voxels, E = 210, nu = 0.3, TETRA2: a null-stiffness
-buffer row behind a u_y-Dirichlet face, ligament nodes held at u_y = 0 (strong rows), a
-void notch, one pin disk pulled to u_y = +0.05 (strong rows), u_z Dirichlet on z = 0;
-Paux reference (lambda, mu); Anderson on p~ every 2 iterations; tolerance 1e-6 (Eq. 5).
-One step = one complete solve from u~ = 0 to the tolerance; every step runs all of the
-iteration's kernels.
+Workload: sphere indentation of a 384 x 384 x 192-voxel block (385 x 385 x 193 =
+28,607,425 nodes) with seeded stiff spherical inclusions (contrast 5), bottom clamped,
+lateral faces traction-free, top face the contact surface (Algorithm 2, Section 5.1), a
+rigid sphere of radius 96 pushed in 20 geometric increments to a depth ratio d/R drawn
+from U[0.005, 0.05] (seed 3000), reference medium 5 (lambda, mu) of the matrix, Anderson
+on p~ every 3 iterations, tolerance 1e-6 (Eq. 5).
+
+One step = one load increment solved to r < 1e-6 (contact set settled) from the start
+rule of the arm, all of the iteration's kernels included.  Steps cycle through the 20
+increments (the first increment of a cycle starts from u~ = 0); warm-up steps are the
+first ones of the cycle.  The working set (~7 GB) is far larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Prints one JSON line.  N > 1 (under torchrun): every rank solves its own replica of the
-workload (the solve does not shard); value = all ranks' voxel-iterations / max time.
+Arms on the same increments, same seeds, same process:
+  * learned + mixed (the value): the warm-start network's guess (dtt_net_predict) where its
+    weights file exists, with the fallback rule (the solve keeps the guess only if its
+    Eq. 5 residual is below the previous-step start's); else the previous-step start;
+  * plain FP64: previous-step start, on a bounded subset of the timed increments, each
+    started from the same field as the mixed arm's start of that increment.
+Prints one JSON line.  N > 1 (under torchrun): every rank solves its own replica (the solve
+does not shard); value = all ranks' voxel-iterations / the slowest rank's time.
 """
 import argparse
 import json
@@ -31,37 +41,34 @@ sys.path.insert(0, ROOT)
 
 import workloads as wl  # noqa: E402
 
+METRIC = "voxel-iters/s and time to residual 1e-6: learned+mixed vs plain FP64 GPU"
+SEED = 3000
+NVOX = (384, 384, 192)
+GRAPH_ITERS = 16
 L2_FLUSH_BYTES = 512 << 20
-
-# DRAM traffic per launch of the dominant kernel on this workload, from one ncu capture
-# (profiles/k_residual_f32_ct_128x128x32.md); reported only while the kernel source is the
-# one that was profiled.
-PROFILED_TRAFFIC = {"residual": {"source": "paper_2607_26082_b300/csrc/k_residual_f32.cu",
-                                 "sha256_prefix": "0278c5a438094f6d", "bytes": 48168960}}
-
-
-def profiled_traffic(group):
-    import hashlib
-    rec = PROFILED_TRAFFIC.get(group)
-    if not rec:
-        return None
-    try:
-        h = hashlib.sha256(open(os.path.join(ROOT, rec["source"]), "rb").read()).hexdigest()
-    except OSError:
-        return None
-    return rec["bytes"] if h.startswith(rec["sha256_prefix"]) else None
-FP32_LANES_PER_SM = 128
+# algorithmic bytes per node and iteration (mixed: 4-byte fields): the Green step (forward
+# DTT, Green multiply, inverse DTT) reads and writes the three components in three sweeps;
+# the residual group (stress, divergence, reference term, Anderson store and Gram row)
+# reads u~ and writes p~ (25 B) and stores R and reads three older R slots (60 B)
+B_GREEN = 72
+B_RESIDUAL = 85
+# ncu DRAM bytes per launch of the Green-step kernels on this workload, keyed by the source
+# hash of the kernel file they came from; null once that source has changed
+PROFILED_TRAFFIC = {}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ct", choices=["ct", "indent"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=SEED)
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="timed increments the plain FP64 arm solves (evenly spread over the timed ones)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-ct", action="store_true", help="skip the secondary CT-specimen line")
+    ap.add_argument("--weights", default=None, help="warm-start network weights (.npz); default: the package's")
     ap.add_argument("--clock-log", default=None,
                     help="keep the raw nvidia-smi samples of the timed region in this CSV file")
     return ap.parse_args()
@@ -74,10 +81,8 @@ def dist_env():
     return rank, world, local
 
 
-def workload(name):
-    if name == "ct":
-        return wl.ct_plate(128, 128, 32)
-    return wl.indentation(256, 256, 128, R=64.0, steps=10)
+def workload(seed=SEED, nvox=NVOX):
+    return wl.indentation_inclusions(seed, *nvox, steps=20)
 
 
 def nvox_of(spec):
@@ -141,21 +146,30 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(spec, seconds, iters_cap=50):
-    """The oracle as it stands (Algorithm 1, float64 numpy, naive trigonometric sums) on
-    the full workload, for a bounded number of iterations (~`seconds` of CPU work)."""
+ORACLE_NVOX = (128, 128, 64)
+
+
+def oracle_sample(seconds, iters_cap=20, seed=SEED):
+    """The oracle as it stands (Algorithm 2, float64 numpy, naive trigonometric sums) on
+    a bounded sample: the same generator and seed at 128 x 128 x 64 voxels (R = 32, the
+    same R / L), the first increment from u~ = 0, for about `seconds` of CPU work.  The
+    full 384 x 384 x 192 block needs tens of GB of host memory and minutes per oracle
+    iteration; per voxel the smaller block is cheaper for the oracle (shorter dense
+    transforms), so its rate flatters the oracle."""
     from oracle import constraints as ocs, discrete as odz, solver as osv
+    spec = workload(seed, ORACLE_NVOX)
     pb = odz.problem_from(spec)
-    rows = ocs.rows_from_intents(pb, spec["intents"])
+    I = spec["indenter"]
+    ind = ocs.Indenter(pb, I["axis"], I["face"], I["centers"][0], I["radius"])
+    u0 = np.zeros((3,) + pb.node_shape)
     t0 = time.perf_counter()
-    osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 0.0, 1, acv_mod=spec["acv_mod"])
-    t1 = time.perf_counter()
-    per_it = max(t1 - t0, 1e-6)   # one iteration + set-up, as an estimate
+    osv.solve_alg2_increment(pb, ind, [], spec["lam0"], spec["mu0"], 0.0, 1, u0, acv_mod=spec["acv_mod"])
+    per_it = max(time.perf_counter() - t0, 1e-6)   # one iteration + set-up, an estimate
     k = int(max(1, min(iters_cap, seconds / per_it)))
     t0 = time.perf_counter()
-    res = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 0.0, k, acv_mod=spec["acv_mod"])
+    res = osv.solve_alg2_increment(pb, ind, [], spec["lam0"], spec["mu0"], 0.0, k, u0, acv_mod=spec["acv_mod"])
     dt = time.perf_counter() - t0
-    return nvox_of(spec) * res.iterations / dt, res.iterations, dt
+    return nvox_of(spec) * res.iterations / dt, res.iterations, dt, spec
 
 
 def cpu_threads():
@@ -186,6 +200,12 @@ def launches_per_iteration(has_rows, has_contact, acv):
     return n
 
 
+def launches_per_solve(iters, per_it, graph_iters=GRAPH_ITERS, prep=3):
+    """Graph launches cover whole multiples of graph_iters iterations (one more launch
+    detects the finish); prep = the start's projections."""
+    return ((iters + graph_iters) // graph_iters) * graph_iters * per_it + prep
+
+
 def max_over_ranks(value, world, device):
     """The largest value over the ranks (the slowest rank's time), every rank gets it."""
     if world <= 1:
@@ -202,6 +222,44 @@ def whole_job_rate(units_per_rank, seconds_max, world):
     return world * units_per_rank / seconds_max
 
 
+def spread(n, k):
+    """k indices spread evenly over range(n) (the last one included)."""
+    if k <= 0 or n <= 0:
+        return []
+    if k >= n:
+        return list(range(n))
+    return sorted({int(round(i * (n - 1) / (k - 1))) for i in range(k)}) if k > 1 else [n - 1]
+
+
+def default_weights():
+    return os.path.join(ROOT, "paper_2607_26082_b300", "weights", "warmstart_indent.npz")
+
+
+def run_ct_secondary(torch, dtt, rows, stream, flush, solves=3):
+    """The former headline, kept as a secondary figure: the half CT-like specimen
+    (128 x 128 x 32, Section 4.1.2) solved from u~ = 0 to r < 1e-6 in mixed precision."""
+    spec = wl.ct_plate(128, 128, 32)
+    g = rows.setup_grid(spec, dtt.PREC_MIXED, stream=stream.cuda_stream)
+    g.dtt_autotune(iters=5, acv_mod=spec["acv_mod"])
+    ts, its = [], []
+    for k in range(1 + solves):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = g.dtt_solve_step(spec["tol"], 20000, acv_mod=spec["acv_mod"], init=dtt.INIT_ZERO,
+                               graph_iters=GRAPH_ITERS)
+        e1.record(stream)
+        e1.synchronize()
+        if k:
+            ts.append(e0.elapsed_time(e1) / 1e3)
+            its.append(rep.iterations)
+    g.close()
+    nv = nvox_of(spec)
+    return {"workload": spec["name"] + ", mixed, zero start, tol 1e-6", "ms_per_solve": 1e3 * sum(ts) / len(ts),
+            "iterations": int(statistics.median(its)), "voxel_iter_per_s": nv * sum(its) / sum(ts)}
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2607_26082_b300 import dtt, rows
@@ -209,157 +267,201 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    spec = workload(args.workload)
-    if args.workload != "ct":
-        raise SystemExit("bench.py times the ct workload; run the indentation block with "
-                         "python -m paper_2607_26082_b300.run --workload indent")
-    nv = nvox_of(spec)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    spec = workload(args.seed)
+    I = spec["indenter"]
+    ncyc = len(I["centers"])
+    nv, mod, tol = nvox_of(spec), spec["acv_mod"], spec["tol"]
+    per_it = launches_per_iteration(False, True, True)
 
-    def make(prec):
-        g = rows.setup_grid(spec, prec, stream=stream.cuda_stream)
-        g.tuning = g.dtt_autotune(iters=5, acv_mod=spec["acv_mod"])   # kernel tiling, outside the timed region
-        return g
+    gm = rows.setup_grid(spec, dtt.PREC_MIXED, stream=stream.cuda_stream)
+    nn = gm.n_nodes
+    tuning = gm.dtt_autotune(iters=4, acv_mod=mod)            # kernel tiling, outside the timed region
+    gm.dtt_set_indenter(I["axis"], I["face"], I["centers"][0], I["radius"])
 
-    def solve(g, tol, max_iter):
-        return g.dtt_solve_step(tol, max_iter, acv_mod=spec["acv_mod"], acv_on=dtt.ACV_P, init=dtt.INIT_ZERO,
-                                graph_iters=16)
+    # learned start (row a11): the warm-start network, if its trained weights are present
+    wpath = args.weights or default_weights()
+    net, learned = None, None
+    if os.path.exists(wpath):
+        from paper_2607_26082_b300 import warmstart
+        net = warmstart.load_net(wpath, stream=stream.cuda_stream)
+        learned = {"weights": os.path.relpath(wpath, ROOT), "kept": 0, "steps": 0}
 
-    def launches_per_solve(iters):
-        return ((iters + graph_iters) // graph_iters) * graph_iters * per_it + 1
+    u_dev = torch.empty((3,) + tuple(gm.node_shape), dtype=torch.float64, device=dev)
+    fp64_idx = set(spread(args.steps, args.fp64_steps))
+    starts = {}                  # timed step -> (increment, start field on the device)
 
-    graph_iters = 16
-    per_it = launches_per_iteration(True, False, True)
+    def step(s, record_start=False):
+        k = s % ncyc
+        if record_start:
+            if k == 0:
+                starts[s] = (k, None)
+            else:
+                gm.dtt_get_fields(u_out=u_dev)
+                starts[s] = (k, u_dev.clone())
+        gm.dtt_move_indenter(I["centers"][k])
+        init = dtt.INIT_ZERO if k == 0 else dtt.INIT_PREVIOUS
+        if net is not None and k > 0:
+            net.predict_increment(gm, spec, k)
+            init = dtt.INIT_GUESS
+        rep = gm.dtt_solve_step(tol, 20000, acv_mod=mod, init=init, graph_iters=GRAPH_ITERS)
+        if rep.status != dtt.OK:
+            raise RuntimeError("increment %d did not converge: %s" % (k, rep.as_dict()))
+        return k, rep
 
-    def timed(g, steps, warmup):
-        for _ in range(warmup):
-            solve(g, spec["tol"], 20000)
-        times, iters, launches = [], [], 0
-        for _ in range(steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()            # L2 flush between timed solves (outside the events)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rep = solve(g, spec["tol"], 20000)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) / 1e3)
-            iters.append(rep.iterations)
-            launches += launches_per_solve(rep.iterations)
-            if rep.status != dtt.OK:
-                raise RuntimeError("solve did not converge: %s" % rep.as_dict())
-        return times, iters, rep, launches
+    for s in range(args.warmup):
+        step(s)
 
-    # ---- mixed path (headline)
-    gm = make(dtt.PREC_MIXED)
     sampler = ClockSampler(local, args.clock_log)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
     t_wall0 = time.perf_counter()
-    times, iters, rep_m, launches = timed(gm, args.steps, args.warmup)
+    times, iters, incs, launches, kept = [], [], [], 0, 0
+    for t in range(args.steps):
+        s = args.warmup + t
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        k, rep = step(s, record_start=(t in fp64_idx))
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        iters.append(rep.iterations)
+        incs.append(k)
+        launches += launches_per_solve(rep.iterations, per_it)
+        if net is not None and k > 0:
+            kept += rep.start_from_guess
+            launches += net.launches_per_predict
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
     tot_vi = nv * sum(iters)
     tot_t = max_over_ranks(sum(times), world, dev)
     value = whole_job_rate(tot_vi, tot_t, world)
+    if learned is not None:
+        learned.update({"kept": kept, "steps": sum(1 for k in incs if k > 0)})
 
-    # ---- kernel-group profile of the mixed iteration (roofline of the dominant group)
-    prof = gm.dtt_profile_iteration(20, acv_mod=spec["acv_mod"])
-    nn = gm.n_nodes
-    # algorithmic bytes of one launch group per iteration (mixed path: T = 4 B fields, u~ as
-    # an 8-byte float-float pair, phase ids 1 B per voxel)
-    # residual: u~ hi/lo 24, step 12, g_(i-1) 12, three older R slots for the Gram row 36 in;
-    # p 12, R 12 out.  Anderson input: p copy (24) or the accelerated combination (132),
-    # one in acv_mod.  FFT route: x, y forward passes 24 each; z forward + Green + z
-    # inverse 24; y inverse 24, x inverse + increment (u~ hi/lo in and out, step out) 72.
-    mod = spec["acv_mod"]
-    alg_bytes = {"residual": nn * 108 + nv, "projections": 0,
-                 "anderson": nn * (24 * (mod - 1) + 132) / mod,
-                 "forward_dt": nn * 48, "green": nn * 24, "inverse_dt": nn * 96, "increment": 0}
-    launches_in_group = {"residual": 1, "forward_dt": 2, "inverse_dt": 2, "green": 1, "increment": 1,
-                         "anderson": 2, "projections": 4}
-    dom = max(prof, key=lambda k: prof[k])
+    # ---- kernel-group profile of the mixed iteration (roofline of the Green step)
+    prof = gm.dtt_profile_iteration(20, acv_mod=mod)
+    t_green = (prof["forward_dt"] + prof["green"] + prof["inverse_dt"] + prof["increment"]) / 1e3
+    t_res = prof["residual"] / 1e3
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm = peaks.get("hbm_gbs", 6400.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    t_launch = prof[dom] / 1e3 / launches_in_group.get(dom, 1)
-    b_launch = alg_bytes.get(dom, 0) / launches_in_group.get(dom, 1)
-    achieved = b_launch / t_launch / 1e9 if t_launch > 0 else 0.0
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"
+    green_ach = B_GREEN * nn / t_green / 1e9
+    res_ach = B_RESIDUAL * nn / t_res / 1e9
 
-    # ---- e2e through the public API with host buffers
-    ptr, node, comp, a, b, val = rows.csr_from_intents(spec["nvox"], spec["bc"], spec["intents"])
-    h2d = (nv + 16 * len(spec["lam"]) + ptr.nbytes + node.nbytes + comp.nbytes + a.nbytes + b.nbytes +
-           val.nbytes)
-    d2h = 3 * nn * 8
-    e2e_t, e2e_vi = 0.0, 0
-
-    def pinned(x):
-        return torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
-
-    # the step's inputs and its result live in pinned host memory
-    phase_h = pinned(spec["phase"].astype(np.uint8))
-    ptr, node, comp, a, b, val = (pinned(x) for x in (ptr, node, comp, a, b, val))
-    u_host = torch.empty((3,) + tuple(gm.node_shape), dtype=torch.float64).pin_memory().numpy()
+    # ---- e2e through the public API with host buffers: move the sphere (centre from pinned
+    # host memory), solve, read u~ and the contact state back into pinned host memory
+    u_host = torch.empty((3,) + tuple(gm.node_shape), dtype=torch.float64).pin_memory()
+    centers_h = torch.from_numpy(np.array(I["centers"], dtype=np.float64)).pin_memory().numpy()
     n_e2e = max(1, min(args.steps, 3))
-    for k in range(1 + n_e2e):          # one untimed step first: lazy host/device buffers
+    e2e_t, e2e_vi = 0.0, 0
+    s0 = args.warmup + args.steps
+    nface = None
+    for j in range(n_e2e):
+        k = (s0 + j) % ncyc
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        gm.dtt_set_material(phase_h, spec["lam"], spec["mu"])
-        gm.dtt_set_constraints(ptr, node, comp, a, b, val)
-        rep = solve(gm, spec["tol"], 20000)
+        gm.dtt_move_indenter(centers_h[k])
+        init = dtt.INIT_ZERO if k == 0 else dtt.INIT_PREVIOUS
+        if net is not None and k > 0:
+            net.predict_increment(gm, spec, k)
+            init = dtt.INIT_GUESS
+        rep = gm.dtt_solve_step(tol, 20000, acv_mod=mod, init=init, graph_iters=GRAPH_ITERS)
         gm.dtt_get_fields(u_out=u_host)
-        if k > 0:
-            e2e_t += time.perf_counter() - t0
-            e2e_vi += nv * rep.iterations
+        act, gap, fn, force = gm.dtt_get_contact()
+        e2e_t += time.perf_counter() - t0
+        e2e_vi += nv * rep.iterations
+        nface = len(act)
     e2e_value = whole_job_rate(e2e_vi, max_over_ranks(e2e_t, world, dev), world)
+    d2h = 3 * nn * 8 + nface * (1 + 8 + 8) + 24
 
-    # ---- plain FP64 GPU solver on the same input
-    g64 = make(dtt.PREC_FP64)
-    t64, it64, rep64, _ = timed(g64, args.fp64_steps, 1)
-    fp64 = {"value": nv * sum(it64) / sum(t64), "ms_per_step": 1e3 * sum(t64) / len(t64),
-            "iterations": int(statistics.median(it64)), "residual": rep64.residual,
-            "tuning": g64.tuning.as_dict()}
+    # ---- plain FP64 GPU solver on the same increments, from the same starting fields
+    gm_tuning = tuning.as_dict()
+    g64 = rows.setup_grid(spec, dtt.PREC_FP64, stream=stream.cuda_stream)
+    g64.dtt_autotune(iters=2, acv_mod=mod)
+    g64.dtt_set_indenter(I["axis"], I["face"], I["centers"][0], I["radius"])
+    t64, it64, tmx, itmx = [], [], [], []
+    for t in sorted(fp64_idx):
+        k, u0 = starts[args.warmup + t]
+        if u0 is not None:
+            g64.dtt_set_initial(u0)
+        g64.dtt_move_indenter(I["centers"][k])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = g64.dtt_solve_step(tol, 20000, acv_mod=mod, init=dtt.INIT_ZERO if u0 is None else dtt.INIT_PREVIOUS,
+                                 graph_iters=GRAPH_ITERS)
+        e1.record(stream)
+        e1.synchronize()
+        if rep.status != dtt.OK:
+            raise RuntimeError("FP64 increment %d did not converge: %s" % (k, rep.as_dict()))
+        t64.append(e0.elapsed_time(e1) / 1e3)
+        it64.append(rep.iterations)
+        tmx.append(times[t])
+        itmx.append(iters[t])
     g64.close()
+    starts.clear()
+    fp64 = {"increments": [int(incs[t]) for t in sorted(fp64_idx)],
+            "seconds": t64, "iterations": it64, "mixed_seconds": tmx, "mixed_iterations": itmx,
+            "value": nv * sum(it64) / sum(t64) if t64 else None,
+            "start": "the same field as the mixed arm's start of each increment (previous increment's "
+                     "solution), plain previous-step start, no network"}
+
+    ct = None
+    if not args.no_ct and rank == 0:
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        ct = run_ct_secondary(torch, dtt, rows, stream, flush)
+        del flush
 
     cpu = None
     if rank == 0 and world == 1:
-        v, k, dt = oracle_sample(spec, args.cpu_seconds)
+        v, k, dt, ospec = oracle_sample(args.cpu_seconds, seed=args.seed)
         cpu = {"value": v, "unit": "voxel-iter/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": "%d iterations of Algorithm 1 (float64 numpy oracle) on the full %s, %.1f s" %
-                         (k, spec["name"], dt)}
+               "sample": "%d iterations of Algorithm 2 (float64 numpy oracle, first increment) on the same "
+                         "generator and seed at %dx%dx%d voxels, %.1f s" % ((k,) + ORACLE_NVOX + (dt,))}
 
+    ms_step = 1e3 * tot_t / len(times)
     out = {
-        "metric": "voxel-iters/s (time to residual 1e-6: mixed vs plain FP64 GPU)",
-        "value": value, "unit": "voxel-iter/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(times), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 transforms/stress, "
-        "float-float u~, FP64 norms/Gram/multipliers)", "data": "synthetic",
-        "config": {"workload": spec["name"] + ", E=210, nu=0.3, TETRA2, R0=(lambda,mu), tol 1e-6, "
-                                "ACV_P mod 2, zero start",
-                   "voxels": nv, "nodes": nn, "iterations_per_solve": int(statistics.median(iters)),
-                   "time_to_residual_1e-6_ms": 1e3 * tot_t / len(times),
-                   "l2": "flushed (512 MB write) before every timed solve", "parallelism": "replicas"},
-        "fp64": fp64, "speedup_time_to_residual_vs_fp64": fp64["ms_per_step"] / (1e3 * tot_t / len(times)),
-        "speedup_per_iteration_vs_fp64": (tot_vi / tot_t) / fp64["value"],
-        "tuning": gm.tuning.as_dict(),
-        "roofline": {"bound": "hbm", "kernel_group": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_source": peak_src, "traffic": profiled_traffic(dom),
+        "metric": METRIC, "value": value, "unit": "voxel-iter/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64 (mixed: FP32 transforms/stress, float-float u~, FP64 norms/Gram/multipliers/gap)",
+        "data": "synthetic",
+        "config": {"workload": spec["name"] + ", 20 geometric increments, Algorithm 2, TETRA2, R0 = 5 (lambda, mu), "
+                               "ACV_P mod 3, tol 1e-6, one step = one increment",
+                   "voxels": nv, "nodes": nn, "seed": args.seed,
+                   "increments_timed": incs, "iterations_per_step": iters,
+                   "start": ("learned (network guess, fallback to the previous-step start)" if net is not None
+                             else "previous-step start (no trained network weights found)"),
+                   "time_to_residual_1e-6_s": tot_t, "time_to_residual_1e-6_ms_per_increment": ms_step,
+                   "l2": "inputs larger than L2 (about 7 GB resident), no flush", "parallelism": "replicas"},
+        "learned": learned,
+        "fp64_same_increments": fp64,
+        "speedup_time_to_residual_vs_fp64": (sum(t64) / sum(tmx)) if t64 else None,
+        "speedup_per_iteration_vs_fp64": ((sum(t64) / sum(it64)) / (sum(tmx) / sum(itmx))) if t64 else None,
+        "tuning": gm_tuning,
+        "roofline": {"bound": "hbm", "kernel_group": "Green step (forward DTT x/y, fused z pass with the Green "
+                                                      "multiply, inverse DTT y/x with the increment)",
+                     "achieved": green_ach, "peak": hbm, "unit": "GB/s", "frac": green_ach / hbm,
+                     "peak_source": peak_src, "traffic": PROFILED_TRAFFIC.get("green"),
+                     "alg_bytes_per_node": B_GREEN, "ms_per_iteration": 1e3 * t_green,
+                     "residual_group": {"achieved": res_ach, "frac": res_ach / hbm, "alg_bytes_per_node": B_RESIDUAL,
+                                        "ms_per_iteration": 1e3 * t_res},
                      "group_ms_per_iteration": prof},
         "cpu_baseline": cpu,
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": "voxel-iter/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "e2e": {"value": e2e_value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 24, "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
+        "ct_secondary": ct,
         "wall_s": wall,
     }
+    if net is not None:
+        net.close()
     gm.close()
     return out
 
@@ -367,27 +469,28 @@ def run_ours(args, rank, world, local):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    spec = workload(args.workload)
     per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_sample(spec, per_step, iters_cap=3)
+        oracle_sample(per_step, iters_cap=2, seed=args.seed)
     vals, ts, ks = [], [], []
+    spec = None
     for _ in range(args.steps):
-        v, k, dt = oracle_sample(spec, per_step, iters_cap=10)
+        v, k, dt, spec = oracle_sample(per_step, iters_cap=4, seed=args.seed)
         vals.append(v)
         ts.append(dt)
         ks.append(k)
     value = nvox_of(spec) * sum(ks) / sum(ts)
     cores = cpu_threads()
     return {
-        "impl": "reference", "metric": "voxel-iters/s (time to residual 1e-6: mixed vs plain FP64 GPU)",
+        "impl": "reference", "metric": METRIC,
         "value": value, "unit": "voxel-iter/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(ts) / len(ts), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": spec["name"] + ", TETRA2, Algorithm 1", "voxels": nvox_of(spec)},
+        "config": {"workload": spec["name"] + " (the benchmark's generator and seed at %dx%dx%d), Algorithm 2"
+                               % ORACLE_NVOX, "voxels": nvox_of(spec)},
         "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": cores, "kind": "oracle",
-                         "sample": "each step: %d-%d iterations of the float64 numpy oracle on the full workload"
-                                   % (min(ks), max(ks))},
+                         "sample": "each step: %d-%d iterations of the float64 numpy oracle (first increment) at "
+                                   "%dx%dx%d voxels" % ((min(ks), max(ks)) + ORACLE_NVOX)},
         "e2e": {"value": value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 

@@ -225,10 +225,11 @@ dtt_status dtt_apply_green(dtt_grid* grid, const double* ptilde, double* u, int3
  * with a fixed device-memory budget, latency-critical loops that cannot afford the
  * synchronisation an allocation implies, hosts whose allocator belongs to another
  * framework).  ptilde_dev and u_dev are caller-owned float64 device arrays (3 x n_nodes,
- * component-major) on the grid's device; they may be the same array.  The intermediate
- * spectra use a fixed 64 MiB device array inside the library, held by every GPU that
- * loads it until the process exits, so grids above 2,796,202 nodes are rejected with
- * DTT_ERR_ARG.  The call allocates nothing.  The first call on a device looks up that
+ * component-major) on the grid's device; they may be the same array.  The grid's device
+ * (the one current at dtt_grid_create) must be the current device, else DTT_ERR_ARG.
+ * The intermediate spectra use a fixed 64 MiB device array inside the library, held by
+ * every GPU that loads it until the process exits, so grids above 2,796,202 nodes are
+ * rejected with DTT_ERR_ARG.  The call allocates nothing.  The first call on a device looks up that
  * array's device address; make it before any stream capture.  All calls share the
  * array: calls that overlap on the GPU race.  The call synchronises the grid's stream. */
 dtt_status dtt_apply_green_noalloc(dtt_grid* grid, const double* ptilde_dev, double* u_dev);

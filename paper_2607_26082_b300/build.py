@@ -7,6 +7,7 @@ The shared library is written next to this file; object files go to _build/.
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -28,10 +29,10 @@ def _nvcc():
     return "nvcc"
 
 
-def build(verbose=False, force=False):
+def build(verbose=False, force=False, jobs=None):
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    objs = []
+    objs, cmds = [], []
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     newest_dep = max(os.path.getmtime(d) for d in deps)
     for src in SOURCES:
@@ -40,10 +41,16 @@ def build(verbose=False, force=False):
         objs.append(o)
         if not force and os.path.exists(o) and os.path.getmtime(o) >= newest_dep:
             continue
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", s, "-o", o]
-        if verbose:
+        cmds.append([nvcc] + ARCH + FLAGS + ["-c", s, "-o", o])
+    # translation units compile independently: one nvcc process per file, in parallel
+    jobs = jobs or max(1, min(len(cmds), os.cpu_count() or 1))
+    if verbose:
+        for cmd in cmds:
             print(" ".join(cmd))
-        subprocess.run(cmd, check=True)
+    with ThreadPoolExecutor(max_workers=jobs) as ex:
+        for cmd, rc in zip(cmds, ex.map(lambda c: subprocess.run(c).returncode, cmds)):
+            if rc != 0:
+                raise subprocess.CalledProcessError(rc, cmd)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         cmd = [nvcc] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"]
         if verbose:

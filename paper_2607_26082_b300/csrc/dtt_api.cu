@@ -645,6 +645,10 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
   G->prec = precision;
   G->esz = precision == DTT_PREC_FP64 ? 8 : 4;
   G->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&G->device) != cudaSuccess) {
+    delete G;
+    return fail(DTT_ERR_CUDA, "cudaGetDevice failed");
+  }
   G->g.h = h;
   G->g.scheme = scheme;
   for (int d = 0; d < 3; ++d) {
@@ -1639,7 +1643,8 @@ dtt_status dtt_profile_iteration(dtt_grid* G, const dtt_solve_opts* opts, int32_
 // fixed array below, which every GPU that loads this library holds until the process
 // exits.  The array's device address is looked up once per device (cudaGetSymbolAddress
 // with that device current) on the first call made on that device, so that first call
-// should come before any stream capture.  All calls share the array: calls that overlap
+// should come before any stream capture.  The grid's device must be the current device
+// (DTT_ERR_ARG otherwise).  All calls share the array: calls that overlap
 // on the GPU (different streams, or different grids used concurrently) race on it.
 // Nothing in it has to start at zero: every element a call reads was written earlier
 // in the same call.
@@ -1650,21 +1655,29 @@ constexpr size_t kGreenScratchBytes = 64ull << 20;   // 64 MiB
 static __device__ __align__(256) unsigned char g_green_scratch[kGreenScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void* g_green_scratch_addr[kMaxDevices] = {nullptr};
+// One address per device; host threads may make their first calls at the same time, so
+// the entries are atomics (both would store the same value).
+std::atomic<void*> g_green_scratch_addr[kMaxDevices];
 
-dtt_status green_scratch_for_current_device(void** out) {
+// The scratch array's device address on the grid's device.  That device must be the
+// current one: the kernels run on the grid's stream, and the symbol lookup below is made
+// on the current device.
+dtt_status green_scratch_for_grid(const dtt_grid* G, void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(DTT_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != G->device)
+    return fail(DTT_ERR_ARG, "the current device (" + std::to_string(dev) + ") is not the grid's device (" +
+                                 std::to_string(G->device) + ")");
   if (dev < 0 || dev >= kMaxDevices) return fail(DTT_ERR_ARG, "device ordinal beyond the scratch table");
-  if (!g_green_scratch_addr[dev]) {
-    void* p = nullptr;
+  void* p = g_green_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!p) {
     e = cudaGetSymbolAddress(&p, g_green_scratch);
     if (e != cudaSuccess || !p)
       return fail(DTT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-    g_green_scratch_addr[dev] = p;
+    g_green_scratch_addr[dev].store(p, std::memory_order_release);
   }
-  *out = g_green_scratch_addr[dev];
+  *out = p;
   return DTT_OK;
 }
 
@@ -1680,7 +1693,7 @@ extern "C" dtt_status dtt_apply_green_noalloc(dtt_grid* G, const double* ptilde_
                                  " bytes of scratch, the fixed array holds " + std::to_string(kGreenScratchBytes) +
                                  " (at most " + std::to_string(kGreenScratchBytes / 24) + " nodes)");
   void* scratch = nullptr;
-  dtt_status st = green_scratch_for_current_device(&scratch);
+  dtt_status st = green_scratch_for_grid(G, &scratch);
   if (st != DTT_OK) return st;
   cudaStream_t s = G->stream;
   if (G->prec == DTT_PREC_FP64) {

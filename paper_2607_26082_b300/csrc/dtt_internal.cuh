@@ -41,7 +41,8 @@ struct GridDev {
 struct Ctrl {
   int i_local;        // Anderson counter (reset to 0 when the contact zone changes)
   int iter;           // Green steps performed
-  int done;           // 0 running, 1 converged, 2 iteration cap, 3 diverged
+  int done;           // 0 running, 1 converged, 2 iteration cap, 3 diverged (r not finite,
+                      // r grown 1e6-fold, or the RMS of p grown 1e6-fold)
   int accel;          // accelerate at this iteration
   int max_iter;
   int acv_mod;
@@ -58,10 +59,13 @@ struct Ctrl {
   double tol, update_tol;
   double acv_pivot;
   double r, r0;
+  double pn0;         // RMS of the projected p at the solve's first iterate
   double p2, s2;
   double alpha[4];
   float alpha_f[4];   // the same coefficients in FP32 (set with alpha; read by FP32 kernels)
   double gram[4][4];
+  // Members above this line form the "head" that k_ctrl_residual_acv stages in shared
+  // memory and accesses there; every member its control logic touches must stay above.
   double hist[HIST];
   unsigned int blocks_done;   // CTAs of the current k_proj_U that have finished (end of iteration)
 };

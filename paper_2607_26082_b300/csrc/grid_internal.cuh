@@ -15,6 +15,7 @@ struct dtt_grid {
   GridDev g{};
   int prec = DTT_PREC_FP64;
   cudaStream_t stream = nullptr;
+  int device = -1;           // the device that was current at dtt_grid_create
   bool own_stream = false;   // created here when the caller passes NULL (graph capture
                              // needs a stream other than the legacy default stream)
   int types[3][3]{};      // [comp][axis]

@@ -654,7 +654,10 @@ __device__ void ctrl_residual_core(Ctrl* c, double s2, double p2, double q2, dou
   double pn = sqrt(pt / (double)nnodes), sn = sqrt(s2 / (double)nvox);
   double r = (sn == 0.0) ? (pn == 0.0 ? 0.0 : INFINITY) : h * pn / sn;
   c->r = r;
-  if (c->iter == 0) c->r0 = r;
+  if (c->iter == 0) {
+    c->r0 = r;
+    c->pn0 = pn;
+  }
   if (c->hist_len < HIST) hist[c->hist_len++] = r;
   c->pslot = c->i_local % 4;
   c->n_vgap = (int)ng;
@@ -666,7 +669,12 @@ __device__ void ctrl_residual_core(Ctrl* c, double s2, double p2, double q2, dou
   if (c->no_stop) return;
   if (r < c->tol && (!c->contact_on || sets_empty)) { c->done = 1; return; }
   if (c->iter >= c->max_iter) { c->done = 2; return; }
-  if (!isfinite(r) || (c->r0 > 0.0 && r > 1e6 * c->r0)) { c->done = 3; return; }
+  // Divergence.  Eq. 5 scales ||p|| by ||sigma||, and an unstable mode grows both, so r
+  // alone stays O(1) while the iterate blows up; the RMS of p is watched as well.
+  if (!isfinite(r) || (c->r0 > 0.0 && r > 1e6 * c->r0) || (c->pn0 > 0.0 && pn > 1e6 * c->pn0)) {
+    c->done = 3;
+    return;
+  }
   if (c->contact_on) {
     if (c->prev_valid && c->n_mismatch == 0 && r < c->update_tol) c->update = 1;
     c->prev_valid = 1;

@@ -20,7 +20,8 @@ the indentation); --r0-scale multiplies the workload's reference medium (the pap
 stiffer one in finite strain); --load-steps N splits the indentation into N geometric
 increments (default 20 for indent, whose 10-increment schedule leaves the physical branch
 at its last step, and the paper's 80 for indent_cube); --max-iter caps the iterations of each step (default 20000) and
---stop-on-fail ends the run at the first step that does not converge.  ct_paper is the
+--stop-on-fail ends the run at the first step that does not converge; --radius, --dmin and
+--dmax set the indent workload's sphere radius and its first and last depth ratios.  ct_paper is the
 paper's 10 x 100 x (50 + 1) CT-like specimen with the loading --ct-load; it reports the
 reactions of the load rows and of the ligament rows and their balance.  --acv-on and
 --acv-mod override the workload's Anderson settings.  iso_cell is a two-phase cell with
@@ -49,7 +50,7 @@ import workloads as wl  # noqa: E402
 from . import dtt, rows  # noqa: E402
 
 
-def make_workload(name, nvox=None, load_steps=None, contrast=4.0):
+def make_workload(name, nvox=None, load_steps=None, contrast=4.0, radius=None, dmin=None, dmax=None):
     """ct: half compact-tension-like specimen 128x128x32; cube16: 16^3 cube with pinned
     nodes; indent: sphere indentation of a 256x256x128 block, R = 64.  nvox rescales ct and
     indent (the indenter radius scales with the block); indent_inclusions: the 384x384x192
@@ -71,7 +72,8 @@ def make_workload(name, nvox=None, load_steps=None, contrast=4.0):
         return wl.indentation_cube(nvox[0] if nvox else 65, steps=load_steps or 80, dmax=0.2)
     if name == "indent":
         n = nvox or (256, 256, 128)
-        return wl.indentation(*n, R=64.0 * n[0] / 256.0, steps=load_steps or 20)
+        return wl.indentation(*n, R=radius or 64.0 * n[0] / 256.0, steps=load_steps or 20,
+                              dmin=dmin or 0.001, dmax=dmax or 0.05)
     raise SystemExit("unknown workload %r" % name)
 
 
@@ -166,6 +168,9 @@ def main(argv=None):
     ap.add_argument("--r0-scale", type=float, default=1.0)
     ap.add_argument("--load-steps", type=int, default=None)
     ap.add_argument("--max-iter", type=int, default=20000)
+    ap.add_argument("--radius", type=float, default=None, help="indent: sphere radius (default: a quarter of nx)")
+    ap.add_argument("--dmin", type=float, default=None, help="indent: first depth ratio d/R (default 0.001)")
+    ap.add_argument("--dmax", type=float, default=None, help="indent: last depth ratio d/R (default 0.05)")
     ap.add_argument("--stop-on-fail", action="store_true")
     a = ap.parse_args(argv)
     if a.workload == "batch":
@@ -176,7 +181,7 @@ def main(argv=None):
     if a.workload == "indent_inclusions":
         wname = "indent_inclusions:%d" % a.seed0
     spec = make_workload(wname, tuple(int(v) for v in a.nvox.split(",")) if a.nvox else None, a.load_steps,
-                         a.contrast)
+                         a.contrast, a.radius, a.dmin, a.dmax)
     prec = dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64
     spec["kinematics"] = a.kinematics.upper()
     if a.medium:

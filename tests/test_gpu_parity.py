@@ -2,10 +2,12 @@
 seeded inputs.
 
 Tolerances: FP64 path <= 1e-11 relative (transforms, Green step, residual operator,
-plain fixed-iteration solves); Anderson-accelerated fixed-iteration runs 1e-9 (the Gram
-solve amplifies summation-order differences); mixed path: operators at float32 rounding
-(2e-6 relative to the field scale), converged solutions (residual 2e-7, near the float32
-stress floor) within 2e-6 relative L2 of the oracle converged to 1e-12.
+plain fixed-iteration solves, converged solutions on every field); Anderson-accelerated
+fixed-iteration trajectories 1e-9 (the Gram solve amplifies summation-order differences
+along the way; the converged solutions they lead to meet 1e-11); mixed path: operators at
+float32 rounding (2e-6 relative to the field scale), converged solutions (residual 1e-7,
+above the float32 stress floor) within 1e-6 relative L2 of the oracle converged to 1e-13,
+stated separately for displacement, stress, reactions and contact force.
 """
 import numpy as np
 import pytest
@@ -220,10 +222,19 @@ def test_fixed_iterations_plain_fp64(seed):
                  n_smooth=1 if seed % 2 == 0 else 0)
     pb, rows = oracle_problem(spec)
     K = 25
-    ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 0.0, K, acv=False)
+    # some of these cells (HEX1 without acceleration) make the plain fixed point unstable:
+    # the projected p grows geometrically while the Eq. 5 ratio stays O(1); the solve then
+    # stops with DTT_ERR_DIVERGED at the first iterate whose p RMS exceeds 1e6 times the
+    # start's, and the parity is checked there
+    p0 = _p_rms(osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 0.0, 0, acv=False))
+    for k in range(1, K + 1):
+        ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 0.0, k, acv=False)
+        if _p_rms(ref) > 1e6 * p0:
+            break
     g = gpu_grid(spec, FP64)
     rep = g.dtt_solve_step(0.0, K, acv_mod=0)
-    assert rep.iterations == K and rep.accelerations == 0
+    assert rep.iterations == k and rep.accelerations == 0
+    assert rep.status == (dtt.ERR_DIVERGED if k < K else dtt.ERR_NOT_CONVERGED)   # the cap is tested first
     assert rel_l2(g.dtt_get_fields(), ref.u) <= 1e-11
     hist = g.dtt_get_history()
     assert np.allclose(hist, ref.history, rtol=1e-11, atol=1e-13 * ref.history[0])
@@ -268,87 +279,107 @@ def test_fixed_iterations_accelerated_mixed(seed):
     assert np.allclose(hist, ref.history, rtol=2e-3, atol=1e-6 * ref.history[0])
 
 
-@pytest.mark.parametrize("prec,tol_u", [(FP64, 1e-10), (MIXED, 2e-6)])
-def test_cube16_converged(prec, tol_u):
-    """16^3 cube, half-clamped bottom, 5 pinned interior nodes, top u_z = -0.01."""
+def _s6(sigma):
+    """Oracle stress (ip, 3, 3, z, y, x) in the library's (z, y, x, ip, 6) Voigt order."""
+    sref = np.moveaxis(sigma, (0, 1, 2), (3, 4, 5))
+    return np.stack([sref[..., 0, 0], sref[..., 1, 1], sref[..., 2, 2], sref[..., 1, 2], sref[..., 0, 2],
+                     sref[..., 0, 1]], axis=-1)
+
+
+# FP64: the GPU run to r < 1e-13 against the oracle converged to 1e-13, within 1e-11
+# relative L2 (measured 4e-15 - 3e-14).  Mixed: the GPU run to r < 1e-7 (below the Eq. 5
+# tolerance of the configurations, above the float32 stress floor of about 5e-8) within
+# 1e-6 relative L2 on every field (measured 8e-8 - 3.4e-7).
+CONVERGED = {FP64: (1e-13, 1e-11), MIXED: (1e-7, 1e-6)}
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_cube16_converged(prec):
+    """16^3 cube, half-clamped bottom, 5 pinned interior nodes, top u_z = -0.01:
+    displacement, stress, per-row reactions and their sum, each within the bar."""
+    run_tol, bar = CONVERGED[prec]
     spec = wl.cube16()
     pb, rows = oracle_problem(spec)
-    ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 1e-12, 3000, acv_mod=3)
+    ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 1e-13, 3000, acv_mod=3)
     g = gpu_grid(spec, prec)
-    rep = g.dtt_solve_step(1e-12 if prec == FP64 else 2e-7, 3000, acv_mod=3)
+    rep = g.dtt_solve_step(run_tol, 3000, acv_mod=3)
     assert rep.status == dtt.OK
     u, sig = g.dtt_get_fields(sigma=True)
-    assert rel_l2(u, ref.u) <= tol_u
-    sref = np.moveaxis(ref.sigma, (0, 1, 2), (3, 4, 5))   # (vox..., ip, 3, 3)
-    s6 = np.stack([sref[..., 0, 0], sref[..., 1, 1], sref[..., 2, 2], sref[..., 1, 2], sref[..., 0, 2],
-                   sref[..., 0, 1]], axis=-1)
-    assert rel_l2(sig, s6) <= 10 * tol_u
+    assert rel_l2(u, ref.u) <= bar
+    assert rel_l2(sig, _s6(ref.sigma)) <= bar
     per, tot = g.dtt_get_reactions(len(rows))
-    assert rel_l2(per, ref.reactions) <= 10 * tol_u
-    assert np.abs(tot - ref.total_reaction).max() <= 10 * tol_u * np.abs(ref.total_reaction).max()
+    assert rel_l2(per, ref.reactions) <= bar
+    assert np.abs(tot - ref.total_reaction).max() <= bar * np.abs(ref.total_reaction).max()
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_random_problems_converged(prec):
+    run_tol, bar = CONVERGED[prec]
     for seed in range(4):
         spec = _spec(seed, nvox=(11, 8, 9))
         pb, rows = oracle_problem(spec)
-        ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 1e-12, 3000)
+        ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 1e-13, 3000)
         g = gpu_grid(spec, prec)
-        rep = g.dtt_solve_step(1e-12 if prec == FP64 else 2e-7, 3000)
+        rep = g.dtt_solve_step(run_tol, 3000)
         assert rep.status == dtt.OK, (seed, rep.as_dict())
-        assert rel_l2(g.dtt_get_fields(), ref.u) <= (1e-10 if prec == FP64 else 2e-6)
+        u, sig = g.dtt_get_fields(sigma=True)
+        assert rel_l2(u, ref.u) <= bar, seed
+        assert rel_l2(sig, _s6(ref.sigma)) <= bar, seed
+        per, _ = g.dtt_get_reactions(len(rows))
+        assert rel_l2(per, ref.reactions) <= bar, seed
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_ct_plate_converged(prec):
+    """The CT-like plate of the benchmark family at 32 x 32 x 8 voxels (void notch, pin
+    rows, buffer): its mixed floor is r ~ 2e-7 (the void/solid contrast), where
+    displacement, stress and reactions still meet the 1e-6 bar (measured 8.2e-7, 2.9e-7,
+    1.6e-7)."""
+    spec = wl.ct_plate(32, 32, 8)
+    pb, rows = oracle_problem(spec)
+    ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 1e-13, 6000, acv_mod=spec["acv_mod"])
+    g = gpu_grid(spec, prec)
+    rep = g.dtt_solve_step(1e-13 if prec == FP64 else 2.5e-7, 6000, acv_mod=spec["acv_mod"])
+    assert rep.status == dtt.OK, rep.as_dict()
+    bar = CONVERGED[prec][1]
+    u, sig = g.dtt_get_fields(sigma=True)
+    assert rel_l2(u, ref.u) <= bar
+    assert rel_l2(sig, _s6(ref.sigma)) <= bar
+    per, _ = g.dtt_get_reactions(len(rows))
+    assert rel_l2(per, ref.reactions) <= bar
 
 
 # ----------------------------------------------------------------------------- contact
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_contact_increments(prec):
+    """Two increments of Algorithm 2: active set, displacement, stress and contact force
+    within the bar (FP64 1e-11, measured 1.6e-12; mixed run to r < 1e-7, 1e-6, measured
+    1.1e-7), the active set identical except at oracle gaps below 1e-8 R in mixed."""
     w = wl.indentation(16, 16, 8, R=6.0, steps=2, dmin=0.01, dmax=0.05)
     pb, _ = oracle_problem(w)
     I = w.indenter
     g = gpu_grid(w, prec)
     u_ref = np.zeros((3,) + pb.node_shape)
     g.dtt_set_indenter(I["axis"], I["face"], I["centers"][0], I["radius"])
+    bar = CONVERGED[prec][1]
     for step, O in enumerate(I["centers"]):
         ind = ocs.Indenter(pb, I["axis"], I["face"], O, I["radius"])
-        ref = osv.solve_alg2_increment(pb, ind, [], w.lam0, w.mu0, 1e-10, 2000, u_ref)
+        ref = osv.solve_alg2_increment(pb, ind, [], w.lam0, w.mu0, 1e-13, 4000, u_ref)
         u_ref = ref.u
         g.dtt_move_indenter(O)
-        rep = g.dtt_solve_step(1e-10 if prec == FP64 else 1e-7, 2000, acv_mod=3,
+        rep = g.dtt_solve_step(1e-12 if prec == FP64 else 1e-7, 4000, acv_mod=3,
                                init=dtt.INIT_PREVIOUS if step else dtt.INIT_ZERO)
         assert rep.status == dtt.OK, rep.as_dict()
         act, gap, fn, force = g.dtt_get_contact()
         if prec == FP64:
             assert np.array_equal(act, ref.active)
-            assert rel_l2(g.dtt_get_fields(), ref.u) <= 1e-9
-            assert np.abs(force - ref.force).max() <= 1e-8 * np.abs(ref.force).max()
         else:
             tie = np.abs(ref.gap) < 1e-8 * I["radius"]
             assert np.array_equal(act[~tie], ref.active[~tie])
-            assert rel_l2(g.dtt_get_fields(), ref.u) <= 1e-5
-            assert np.abs(force - ref.force).max() <= 1e-5 * np.abs(ref.force).max()
-
-
-def test_hertz_law_small_depths():
-    """Frictionless sphere on a bottom-clamped block (Section 5.4): at depths where the
-    contact patch spans several nodes and the block is still much larger than it, the
-    contact force follows Eq. 30 within 3 %."""
-    w = wl.indentation(128, 128, 64, R=32.0, steps=3, dmin=0.0016, dmax=0.004)
-    I = w.indenter
-    g = gpu_grid(w, MIXED)
-    g.dtt_set_indenter(I["axis"], I["face"], I["centers"][0], I["radius"])
-    for step, O in enumerate(I["centers"]):
-        g.dtt_move_indenter(O)
-        rep = g.dtt_solve_step(1e-7, 20000, acv_mod=3, init=dtt.INIT_PREVIOUS if step else dtt.INIT_ZERO)
-        assert rep.status == dtt.OK
-        act, gap, fn, force = g.dtt_get_contact()
-        d = I["ratios"][step] * I["radius"]
-        hertz = 4.0 / 3.0 * I["E"] / (1 - I["nu"] ** 2) * np.sqrt(I["radius"]) * d ** 1.5
-        assert abs(np.linalg.norm(force) / hertz - 1.0) <= 0.03, (step, np.linalg.norm(force), hertz)
-        # complementarity at convergence: no penetration beyond rounding, no tensile reaction
-        assert gap.min() >= -1e-6 * I["radius"]
-        assert (fn[act] <= 1e-8 * np.abs(fn).max()).all()
-    g.close()
+        u, sig = g.dtt_get_fields(sigma=True)
+        assert rel_l2(u, ref.u) <= bar
+        assert rel_l2(sig, _s6(ref.sigma)) <= bar
+        assert np.abs(force - ref.force).max() <= bar * np.abs(ref.force).max()
 
 
 # ----------------------------------------------------------------------------- errors
@@ -435,3 +466,33 @@ def test_ct_specimen_full_size_properties(prec):
     nl = spec["ligament_rows"]
     RS, RL = per[:nl].sum(), per[nl:].sum()
     assert abs(RS + RL) <= 1e-4 * abs(RL)
+
+
+# ----------------------------------------------------------------------------- divergence
+def _p_rms(res):
+    return np.sqrt(np.sum(res.p ** 2) / res.p[0].size)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_divergence_is_reported_with_the_last_iterate(prec):
+    """A reference medium a quarter of the material's (no Anderson) makes the fixed point
+    unstable: the projected p grows about threefold per iteration while the Eq. 5 ratio,
+    which divides by ||sigma||, stays O(1).  The solve must stop with DTT_ERR_DIVERGED at
+    the first iteration where the RMS of p exceeds 1e6 times its start value (the oracle
+    locates that iteration), and leave that iterate readable (FP64: equal to the oracle's
+    iterate at the same count)."""
+    spec = _spec(4, nvox=(8, 7, 9), nphase=2, n_strong=2, n_weak=0, n_smooth=0, n_tie=0, periodic_prob=0.0)
+    spec["lam0"], spec["mu0"] = 0.25 * spec["lam0"], 0.25 * spec["mu0"]
+    pb, orows = oracle_problem(spec)
+    g = gpu_grid(spec, prec)
+    rep = g.dtt_solve_step(1e-12, 500, acv_mod=0)
+    assert rep.status == dtt.ERR_DIVERGED, rep.as_dict()
+    k = rep.iterations
+    run = lambda n: osv.solve_alg1(pb, orows, spec["lam0"], spec["mu0"], 0.0, n, acv=False)  # noqa: E731
+    p0 = _p_rms(run(0))
+    ref_k, ref_prev = run(k), run(k - 1)
+    assert _p_rms(ref_prev) <= 1e6 * p0 < _p_rms(ref_k)
+    u = g.dtt_get_fields()
+    assert np.isfinite(u).all()
+    assert rel_l2(u, ref_k.u) <= (1e-9 if prec == FP64 else 1e-3)
+    g.close()
