@@ -141,6 +141,13 @@ dtt_status dtt_clear_indenter(dtt_grid* grid);
  * the solver. */
 dtt_status dtt_set_initial(dtt_grid* grid, const double* u, int32_t ptr_is_device);
 
+/* Initial contact zone of the next increment (Algorithm 2 starts from C = {g < 0} at the
+ * starting field, Section 5.1.3; this replaces that rule for one solve): active[q] != 0
+ * puts surface node q (the order of dtt_get_contact) in C.  Host or device array of
+ * n_surface bytes.  The zone update rule of Algorithm 2 then corrects it as usual.
+ * DTT_ERR_STATE without an indenter. */
+dtt_status dtt_set_initial_contact(dtt_grid* grid, const uint8_t* active, int32_t ptr_is_device);
+
 typedef struct {
   double tol;          /* Eq. 5 tolerance (RMS norms): h ||p|| / ||sigma|| < tol */
   int32_t max_iter;    /* cap on Green steps (the paper declares failure at 2000) */
@@ -259,22 +266,28 @@ dtt_status dtt_profile_iteration(dtt_grid* grid, const dtt_solve_opts* opts, int
  *                    choice; otherwise 2..64);
  *   fft_generic:     1 keeps every transform length on the generic Stockham kernels,
  *                    0 lets power-of-two lengths take the register-radix kernels;
+ *   z_route:         the fused z pass (forward DTT along z, Green multiply, inverse DTT):
+ *                    0 = FFT (or dense) pass, 1 = two split-TF32 tensor-core contractions
+ *                    against the z DTT matrices (mixed precision, z operand <= 256
+ *                    nodes; elsewhere ignored);
  *   ms_per_iteration: (dtt_autotune output) measured time of one iteration with them. */
 typedef struct {
   int32_t residual_zchunk;
   int32_t fft_generic;
+  int32_t z_route;
   double ms_per_iteration;
 } dtt_tuning;
 
 /* Times `iters` iterations of the current problem (launch by launch, CUDA events on the
- * grid's stream) for each candidate tiling -- the FFT route first, then the residual
+ * grid's stream) for each candidate tiling -- the FFT route and the z route first, then the residual
  * kernel's z chunk in {built-in, 2, 4, 8, 16, 32, 64} -- keeps the fastest on the grid
  * and returns it in *best (may be NULL).  u~ and the solver rings are reset to zero
  * afterwards; call it before a solve.  iters < 1 is DTT_ERR_ARG. */
 dtt_status dtt_autotune(dtt_grid* grid, const dtt_solve_opts* opts, int32_t iters, dtt_tuning* best);
 
 /* Applies a tiling (e.g. one tuned on another grid of the same size); a zchunk outside
- * {0, 2..64} or fft_generic outside {0, 1} is DTT_ERR_ARG. */
+ * {0, 2..64}, fft_generic or z_route outside {0, 1}, or z_route 1 on a grid that cannot
+ * take it (FP64, or more than 256 nodes along z) is DTT_ERR_ARG. */
 dtt_status dtt_set_tuning(dtt_grid* grid, const dtt_tuning* tuning);
 
 /* Solves ncell independent grids at once: every cell is prepared as dtt_solve_step

@@ -157,6 +157,65 @@ void build_axis(int type, int n, int nn, std::vector<double>& F, std::vector<dou
   }
 }
 
+// Tensor-core z pass: the active node rows and spectral positions of each component's z
+// transform (Table 3), one operand size for the three components, and the forward and
+// inverse matrices packed for the kernel.  Grids whose z operand exceeds 256 keep the
+// FFT (or dense) z pass.  DTT_Z_TENSOR=1 in the environment selects the route at creation.
+dtt_status build_tz(dtt_grid* G) {
+  const int n = G->g.nvox[2], nn = G->g.nn[2];
+  int P = 0;
+  for (int c = 0; c < 3; ++c) {
+    TzComp& t = G->tz[c];
+    switch (G->types[c][2]) {
+      case T_DCT1: t.j0 = 0; t.nj = n + 1; t.k0 = 0; t.nk = n + 1; break;
+      case T_DCT3: t.j0 = 0; t.nj = n; t.k0 = 0; t.nk = n; break;
+      case T_DST1: t.j0 = 1; t.nj = n - 1; t.k0 = 1; t.nk = n - 1; break;
+      case T_DST3: t.j0 = 1; t.nj = n; t.k0 = 0; t.nk = n; break;
+      default: t.j0 = 0; t.nj = n; t.k0 = 0; t.nk = n; break;   // Hartley (periodic)
+    }
+    P = std::max(P, std::max(t.nj, t.nk));
+  }
+  P = (P + 31) / 32 * 32;
+  G->tz_ok = false;
+  if (P > 256 || n < 2) return DTT_OK;
+  for (int c = 0; c < 3; ++c) {
+    TzComp& t = G->tz[c];
+    t.P = P;
+    std::vector<double> F, B, cq, cc;
+    build_axis(G->types[c][2], n, nn, F, B, cq, cc);
+    std::vector<float> pf, pi;
+    tz_pack_matrix(F.data(), nn, t.k0, t.nk, t.j0, t.nj, P, pf);   // rows: spectral, columns: nodes
+    tz_pack_matrix(B.data(), nn, t.j0, t.nj, t.k0, t.nk, P, pi);   // rows: nodes, columns: spectral
+    dtt_status s = dalloc(&G->tz_mat[c], (pf.size() + pi.size()) * sizeof(float));
+    if (s != DTT_OK) return s;
+    CK(cudaMemcpy(G->tz_mat[c], pf.data(), pf.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->tz_mat[c] + pf.size(), pi.data(), pi.size() * 4, cudaMemcpyHostToDevice));
+    t.fwd = G->tz_mat[c];
+    t.inv = G->tz_mat[c] + pf.size();
+  }
+  if (!G->tz_err) {
+    dtt_status s = dalloc(&G->tz_err, sizeof(unsigned int));
+    if (s != DTT_OK) return s;
+  }
+  CK(cudaMemset(G->tz_err, 0, sizeof(unsigned int)));
+  G->tz_ok = true;
+  const char* e = std::getenv("DTT_Z_TENSOR");
+  if (e && e[0] == '1') G->z_route = 1;
+  return DTT_OK;
+}
+
+// 0 when no tensor-core z pass has recorded a timed-out wait, else DTT_ERR_CUDA.
+dtt_status check_tz(dtt_grid* G) {
+  if (!G->tz_err) return DTT_OK;
+  unsigned int e = 0;
+  CK(cudaMemcpy(&e, G->tz_err, sizeof(e), cudaMemcpyDeviceToHost));
+  if (e) {
+    cudaMemset(G->tz_err, 0, sizeof(unsigned int));
+    return fail(DTT_ERR_CUDA, "tensor-core z pass: a bounded wait ran out (the CTA skipped its work)");
+  }
+  return DTT_OK;
+}
+
 // FFT plan of one axis: length L = 2n (n on a periodic axis) factored into radices 4, 2
 // and 3; axes whose length has another prime factor, or n < 4, keep the dense contraction.
 dtt_status build_fft_axis(dtt_grid* G, int d) {
@@ -338,6 +397,9 @@ ContactArgs contact_args(dtt_grid* G, double* cont_part) {
 TransformTables tables(dtt_grid* G) {
   TransformTables t;
   for (int d = 0; d < 3; ++d) t.fft[d] = G->fft[d];
+  t.tz_use = (G->z_route == 1 && G->tz_ok && G->prec == DTT_PREC_MIXED && !G->g.ref_iso) ? 1 : 0;
+  for (int c = 0; c < 3; ++c) t.tz[c] = G->tz[c];
+  t.tz_err = G->tz_err;
   for (int c = 0; c < 3; ++c)
     for (int d = 0; d < 3; ++d) t.types[c][d] = G->types[c][d];
   for (int c = 0; c < 3; ++c)
@@ -386,7 +448,7 @@ dtt_status enqueue_green(dtt_grid* G, const T* in, void* const* in_ring, T* out,
   cudaStream_t s = G->stream;
   // the isotropic medium couples the components: its Green step needs all three spectra,
   // so it takes the unfused route
-  if (tt.fft[2].use && !G->g.ref_iso) {
+  if ((tt.fft[2].use || tt.tz_use) && !G->g.ref_iso) {
     const bool alias = (in_ring == nullptr && (const void*)in == (const void*)out);
     T* b1 = alias ? tmp : out;
     T* b2 = alias ? out : tmp;
@@ -737,6 +799,7 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
       }
     }
   for (int d = 0; d < 3 && s == DTT_OK; ++d) s = build_fft_axis(G, d);
+  if (s == DTT_OK && precision == DTT_PREC_MIXED) s = build_tz(G);
   if (s == DTT_OK) {
     cudaError_t e = cudaMemcpy(G->d_Sring, G->S, 5 * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(G->d_Rring, G->R, 4 * sizeof(void*), cudaMemcpyHostToDevice);
@@ -759,6 +822,7 @@ void dtt_grid_destroy(dtt_grid* G) {
   dfree(G->u64);
   dfree(G->uhi);
   dfree(G->ulo);
+  dfree(G->tz_err);
   for (auto& p : G->S) dfree(p);
   for (auto& p : G->R) dfree(p);
   for (auto& p : G->Gr) dfree(p);
@@ -786,6 +850,7 @@ void dtt_grid_destroy(dtt_grid* G) {
       dfree(G->cos2q[c][d]);
       dfree(G->sin2q_f[c][d]);
       dfree(G->cos2q_f[c][d]);
+      if (d == 0) dfree(G->tz_mat[c]);
       if (c == 0) {
         dfree(G->iso_s[d]);
         dfree(G->iso_c[d]);
@@ -1087,6 +1152,16 @@ dtt_status dtt_clear_indenter(dtt_grid* G) {
   return rebuild_cmask(G);
 }
 
+dtt_status dtt_set_initial_contact(dtt_grid* G, const uint8_t* active, int32_t ptr_is_device) {
+  if (!G || !active) return fail(DTT_ERR_ARG, "null argument");
+  if (!G->contact) return fail(DTT_ERR_STATE, "no indenter set");
+  CK(cudaMemcpyAsync(G->d_active, active, (size_t)G->nface,
+                     ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, G->stream));
+  CK(cudaStreamSynchronize(G->stream));
+  G->contact_given = true;
+  return DTT_OK;
+}
+
 dtt_status dtt_set_initial(dtt_grid* G, const double* u, int32_t ptr_is_device) {
   if (!G || !u) return fail(DTT_ERR_ARG, "null argument");
   dtt_status s = to_grid_u(G, u, ptr_is_device);
@@ -1116,7 +1191,7 @@ dtt_status eval_start_residual(dtt_grid* G, double* r) {
   CK(cudaMemcpyAsync(ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
   ContactArgs ca = contact_args(G, pr.cont);
   if (G->contact) {
-    CKL(launch_contact_init(ca, s));
+    CKL(launch_contact_init(ca, s, G->contact_given ? 1 : 0));
     CKL(launch_contact_proj_U<T>(ca, G->u64, G->uhi, G->ulo, nullptr, s));
   }
   if (G->nrows > 0) CKL(launch_proj_U_rows<T>(G->g, rows_dev(G), G->u64, G->uhi, G->ulo, nullptr, ctrl, s));
@@ -1251,7 +1326,8 @@ dtt_status prepare_solve(dtt_grid* G, const dtt_solve_opts* opts) {
   PartRegions pr = regions(G);
   ContactArgs ca = contact_args(G, pr.cont);
   if (G->contact) {
-    CKL(launch_contact_init(ca, s));
+    CKL(launch_contact_init(ca, s, G->contact_given ? 1 : 0));
+    G->contact_given = false;   // one start only
     if (G->prec == DTT_PREC_FP64) CKL(launch_contact_proj_U<double>(ca, G->u64, G->uhi, G->ulo, nullptr, s));
     else CKL(launch_contact_proj_U<float>(ca, G->u64, G->uhi, G->ulo, nullptr, s));
   }
@@ -1269,6 +1345,10 @@ dtt_status finish_solve(dtt_grid* G, std::chrono::steady_clock::time_point t0, d
   cudaStream_t s = G->stream;
   CK(cudaMemcpyAsync(G->h_ctrl, G->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (G->tz_ok) {
+    dtt_status te = check_tz(G);
+    if (te != DTT_OK) return te;
+  }
   G->last = *G->h_ctrl;
   G->solved = true;
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1550,7 +1630,7 @@ dtt_status dtt_apply_green(dtt_grid* G, const double* ptilde, double* u, int32_t
   CKL(launch_to_double((long long)n3, G->op_t1, isf, G->op_d, s));
   CK(cudaMemcpyAsync(u, G->op_d, n3 * 8, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  return DTT_OK;
+  return check_tz(G);
 }
 
 dtt_status dtt_transform(dtt_grid* G, int32_t component, int32_t inverse, const double* in, double* out,
@@ -1709,7 +1789,7 @@ extern "C" dtt_status dtt_apply_green_noalloc(dtt_grid* G, const double* ptilde_
     CKL(launch_to_double((long long)n3, a, 1, u_dev, s));
   }
   CK(cudaStreamSynchronize(s));
-  return DTT_OK;
+  return check_tz(G);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1773,9 +1853,10 @@ dtt_status reset_state(dtt_grid* G) {
   return DTT_OK;
 }
 
-dtt_status apply_tiling(dtt_grid* G, int zc, int generic) {
+dtt_status apply_tiling(dtt_grid* G, int zc, int generic, int z_route) {
   G->g.zc_override = zc;
   G->g.fft_generic = generic;
+  G->z_route = (z_route == 1 && G->tz_ok) ? 1 : 0;
   invalidate_graph(G);
   return ensure_partials(G);
 }
@@ -1821,26 +1902,29 @@ dtt_status dtt_autotune(dtt_grid* G, const dtt_solve_opts* opts, int32_t iters, 
   if (st != DTT_OK) return st;
   if (iters < 1) return fail(DTT_ERR_ARG, "iters must be >= 1");
   double t_best = 1e300;
-  int zc_best = 0, gen_best = 0;
-  for (int gen = 0; gen < 2; ++gen) {
-    if ((st = apply_tiling(G, 0, gen)) != DTT_OK) return st;
-    double t = 0.0;
-    if ((st = time_iterations(G, opts, iters, &t)) != DTT_OK) return st;
-    if (t < t_best) { t_best = t; gen_best = gen; }
-  }
+  int zc_best = 0, gen_best = 0, zr_best = 0;
+  for (int zr = 0; zr < (G->tz_ok ? 2 : 1); ++zr)
+    for (int gen = 0; gen < 2; ++gen) {
+      if ((st = apply_tiling(G, 0, gen, zr)) != DTT_OK) return st;
+      double t = 0.0;
+      if ((st = time_iterations(G, opts, iters, &t)) != DTT_OK) return st;
+      if (t < t_best) { t_best = t; gen_best = gen; zr_best = zr; }
+    }
   const int zcs[6] = {2, 4, 8, 16, 32, 64};
   for (int q = 0; q < 6; ++q) {
     if (zcs[q] > 2 * G->g.nn[2]) break;
-    if ((st = apply_tiling(G, zcs[q], gen_best)) != DTT_OK) return st;
+    if ((st = apply_tiling(G, zcs[q], gen_best, zr_best)) != DTT_OK) return st;
     double t = 0.0;
     if ((st = time_iterations(G, opts, iters, &t)) != DTT_OK) return st;
     if (t < t_best) { t_best = t; zc_best = zcs[q]; }
   }
-  if ((st = apply_tiling(G, zc_best, gen_best)) != DTT_OK) return st;
+  if ((st = apply_tiling(G, zc_best, gen_best, zr_best)) != DTT_OK) return st;
   if ((st = reset_state(G)) != DTT_OK) return st;
+  if ((st = check_tz(G)) != DTT_OK) return st;
   if (best) {
     best->residual_zchunk = zc_best;
     best->fft_generic = gen_best;
+    best->z_route = zr_best;
     best->ms_per_iteration = t_best;
   }
   return DTT_OK;
@@ -1851,7 +1935,10 @@ dtt_status dtt_set_tuning(dtt_grid* G, const dtt_tuning* t) {
   if (t->residual_zchunk != 0 && (t->residual_zchunk < 2 || t->residual_zchunk > 64))
     return fail(DTT_ERR_ARG, "residual_zchunk must be 0 or in [2, 64]");
   if (t->fft_generic != 0 && t->fft_generic != 1) return fail(DTT_ERR_ARG, "fft_generic must be 0 or 1");
-  return apply_tiling(G, t->residual_zchunk, t->fft_generic);
+  if (t->z_route != 0 && t->z_route != 1) return fail(DTT_ERR_ARG, "z_route must be 0 or 1");
+  if (t->z_route == 1 && !G->tz_ok)
+    return fail(DTT_ERR_ARG, "z_route 1 needs a mixed-precision grid whose z operand has at most 256 nodes");
+  return apply_tiling(G, t->residual_zchunk, t->fft_generic, t->z_route);
 }
 
 dtt_status dtt_batch_solve(int32_t ncell, dtt_grid* const* cells, const dtt_solve_opts* opts, dtt_report* reports) {

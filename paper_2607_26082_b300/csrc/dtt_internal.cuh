@@ -11,6 +11,8 @@
 //   * voxel phase ids: uint8, x fastest.
 #pragma once
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace dtt {
@@ -210,8 +212,29 @@ struct IsoTables {
   int sign[3];
   double null_thr;
 };
+// Tensor-core z pass (k_tensor_z.cu): per component, the active node rows [j0, j0 + nj)
+// and spectral positions [k0, k0 + nk) of its z transform, the operand size P (a multiple
+// of 32, >= nj and nk, the same for the three components), and the forward (P x P, rows =
+// spectral positions) and inverse (rows = nodes) matrices packed chunk by chunk in the
+// kernel's shared-memory operand layout, each chunk a TF32 high part and an FP32 remainder.
+struct TzComp {
+  const float* fwd;
+  const float* inv;
+  int j0, nj, k0, nk, P;
+};
+struct TzParams {
+  TzComp c[3];
+  int comp0;
+  int nnx, nnz;
+  long long npencil, NN, stride;
+  unsigned int* err;       // set to 1 by a CTA whose bounded wait ran out
+};
+
 struct TransformTables {
   FftAxisInfo fft[3];
+  int tz_use;              // 1: fused z pass as tensor-core contractions (mixed path)
+  TzComp tz[3];
+  unsigned int* tz_err;
   int types[3][3];         // [comp][axis]
   const void* fwd[3][3];   // [comp][axis] nn x nn row-major (spectral k, node j)
   const void* inv[3][3];   // [comp][axis] nn x nn row-major (node j, spectral k)
@@ -256,6 +279,12 @@ int launch_transform_axis(const GridDev& g, const T* in, T* out, const Transform
 template <typename T>
 int launch_z_green(const GridDev& g, const T* in, T* out, const TransformTables& tt, int ncomp_first, int ncomp,
                    const Ctrl* ctrl, cudaStream_t s);
+// the same pass as two split-TF32 tensor-core contractions (mixed path, z operand <= 256)
+int launch_tz_green(const float* in, float* out, const TzParams& p, const GreenTables& gt, double lam0, double mu0,
+                    int scheme, double h, int ncomp, const Ctrl* ctrl, cudaStream_t s);
+// rows [r0, r0 + nr) and columns [c0, c0 + ncol) of the nn x nn matrix M, packed for the
+// tensor-core z pass with operand size P
+void tz_pack_matrix(const double* M, int nn, int r0, int nr, int c0, int ncol, int P, std::vector<float>& out);
 // Green step of the isotropic reference medium: a 3 x 3 solve per spectral position over
 // the three components' spectra (component-major, node-grid positions), in place.
 template <typename T>
@@ -302,7 +331,7 @@ int launch_contact_update(const ContactArgs& a, cudaStream_t s);
 template <typename T>
 int launch_contact_proj_U(const ContactArgs& a, double* u64, float* uhi, float* ulo, T* step,
                           cudaStream_t s);
-int launch_contact_init(const ContactArgs& a, cudaStream_t s);
+int launch_contact_init(const ContactArgs& a, cudaStream_t s, int keep_active = 0);
 int contact_blocks(int nface);
 
 // Anderson on p~ in difference form: Gram row of R_{i-1}, then the accelerated Green input

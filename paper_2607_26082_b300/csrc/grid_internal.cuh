@@ -10,6 +10,7 @@
 using dtt::Ctrl;
 using dtt::FftAxisInfo;
 using dtt::GridDev;
+using dtt::TzComp;
 
 struct dtt_grid {
   GridDev g{};
@@ -61,6 +62,13 @@ struct dtt_grid {
   double* cos2q[3][3]{};
   float* sin2q_f[3][3]{};   // FP32 copies (mixed-precision Green multiply)
   float* cos2q_f[3][3]{};
+  // tensor-core z pass (mixed path): per component the packed forward and inverse
+  // matrices (one allocation, forward first), their ranges, and the route choice
+  float* tz_mat[3]{};
+  TzComp tz[3]{};
+  bool tz_ok = false;          // every component's z operand fits (size <= 256)
+  int z_route = 0;             // 0: FFT (or dense) z pass, 1: tensor-core contractions
+  unsigned int* tz_err = nullptr;
   // isotropic reference medium (Section 3.2.3): per-axis tables of sin^2(q/2), cos^2(q/2)
   // shared by the components, and per position the components with a mode there (bit c)
   double* iso_s[3]{};
@@ -85,6 +93,7 @@ struct dtt_grid {
   int c_axis = 2, c_face = 1;
   double center[3]{}, radius = 0;
   int nface = 0;
+  bool contact_given = false;   // the next start keeps the zone set by dtt_set_initial_contact
   long long* d_face = nullptr;
   uint8_t *d_active = nullptr, *d_vgap = nullptr, *d_vreact = nullptr, *d_vgap_prev = nullptr,
           *d_vreact_prev = nullptr;

@@ -337,22 +337,24 @@ int launch_contact_proj_U(const ContactArgs& a, double* u64, float* uhi, float* 
   return (int)cudaGetLastError();
 }
 
-__global__ void k_contact_init(const ContactArgs a) {
+// Initial contact zone of an increment: C = {g < 0} at the starting field (Section 5.1.3),
+// or, with keep_active, the zone the caller set (dtt_set_initial_contact).
+__global__ void k_contact_init(const ContactArgs a, int keep_active) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.c.nnodes_face) return;
   long long n = a.c.node[q];
   double Mp[3], nv[3], X[3], gap;
   contact_geom(a, n, Mp, nv, gap, X);
-  a.c.active[q] = gap < 0.0 ? 1 : 0;
+  if (!keep_active) a.c.active[q] = gap < 0.0 ? 1 : 0;
   a.c.vgap_prev[q] = 0;
   a.c.vreact_prev[q] = 0;
   a.c.gap[q] = gap;
 }
 
-int launch_contact_init(const ContactArgs& a, cudaStream_t s) {
+int launch_contact_init(const ContactArgs& a, cudaStream_t s, int keep_active) {
   int blocks = contact_blocks(a.c.nnodes_face);
   if (blocks == 0) return 0;
-  k_contact_init<<<blocks, SB, 0, s>>>(a);
+  k_contact_init<<<blocks, SB, 0, s>>>(a, keep_active);
   return (int)cudaGetLastError();
 }
 

@@ -173,7 +173,7 @@ static FftParams fft_params(const GridDev& g, const TransformTables& tt, int axi
 template <typename T>
 int launch_z_green(const GridDev& g, const T* in, T* out, const TransformTables& tt, int ncomp_first, int ncomp,
                    const Ctrl* ctrl, cudaStream_t s) {
-  if (!tt.fft[2].use) return (int)cudaErrorInvalidValue;
+  if (!tt.fft[2].use && !(sizeof(T) == 4 && tt.tz_use)) return (int)cudaErrorInvalidValue;
   FftParams p = fft_params(g, tt, 2, 0, ncomp_first);
   GreenTables gt;
   for (int c = 0; c < 3; ++c) {
@@ -185,6 +185,20 @@ int launch_z_green(const GridDev& g, const T* in, T* out, const TransformTables&
     }
     gt.null_thr[c] = tt.null_thr[c];
     gt.null_thr_f[c] = (float)tt.null_thr[c];
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (tt.tz_use) {
+      TzParams tp{};
+      for (int c = 0; c < 3; ++c) tp.c[c] = tt.tz[c];
+      tp.comp0 = ncomp_first;
+      tp.nnx = g.nn[0];
+      tp.nnz = g.nn[2];
+      tp.NN = g.nnodes;
+      tp.stride = (long long)g.nn[0] * g.nn[1];
+      tp.npencil = tp.stride;
+      tp.err = tt.tz_err;
+      return launch_tz_green((const float*)in, (float*)out, tp, gt, tt.lam0, tt.mu0, g.scheme, g.h, ncomp, ctrl, s);
+    }
   }
   return launch_fft_z_green<T>(in, out, p, gt, tt.lam0, tt.mu0, g.scheme, g.h, ncomp, ctrl, s);
 }

@@ -45,7 +45,8 @@ class Report(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("residual_zchunk", C.c_int32), ("fft_generic", C.c_int32), ("ms_per_iteration", C.c_double)]
+    _fields_ = [("residual_zchunk", C.c_int32), ("fft_generic", C.c_int32), ("z_route", C.c_int32),
+                ("ms_per_iteration", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -58,7 +59,7 @@ EXPORTS = ["dtt_grid_create", "dtt_grid_destroy", "dtt_grid_sizes", "dtt_set_mat
            "dtt_move_indenter", "dtt_clear_indenter", "dtt_set_initial", "dtt_solve_step",
            "dtt_get_history", "dtt_get_fields", "dtt_get_reactions", "dtt_get_contact",
            "dtt_set_kinematics", "dtt_get_stress_tensor", "dtt_get_min_jacobian", "dtt_set_reference_medium",
-           "dtt_apply_residual", "dtt_apply_green", "dtt_apply_green_noalloc", "dtt_transform",
+           "dtt_apply_residual", "dtt_apply_green", "dtt_apply_green_noalloc", "dtt_transform", "dtt_set_initial_contact",
            "dtt_profile_iteration", "dtt_autotune", "dtt_set_tuning", "dtt_batch_solve",
            "dtt_last_error", "dtt_version"]
 NPROF = 7
@@ -87,6 +88,7 @@ def lib():
     L.dtt_move_indenter.argtypes = [P, P]
     L.dtt_clear_indenter.argtypes = [P]
     L.dtt_set_initial.argtypes = [P, P, i32]
+    L.dtt_set_initial_contact.argtypes = [P, P, i32]
     L.dtt_solve_step.argtypes = [P, C.POINTER(SolveOpts), C.POINTER(Report)]
     L.dtt_get_history.argtypes = [P, P, C.POINTER(i32)]
     L.dtt_get_fields.argtypes = [P, P, P, i32]
@@ -205,6 +207,11 @@ class Grid:
         p, dev = _ptr(arr)
         _check(lib().dtt_set_initial(self._h, p, dev))
 
+    def dtt_set_initial_contact(self, active):
+        arr = active if hasattr(active, "data_ptr") else np.ascontiguousarray(active, dtype=np.uint8)
+        p, dev = _ptr(arr)
+        _check(lib().dtt_set_initial_contact(self._h, p, dev))
+
     def dtt_solve_step(self, tol, max_iter, acv_mod=3, acv_on=ACV_P, init=INIT_ZERO, update_tol=1e-2,
                        graph_iters=0, acv_pivot=0.0, raise_on_error=False):
         o = SolveOpts(float(tol), int(max_iter), int(acv_mod), int(acv_on), int(init), float(update_tol),
@@ -310,7 +317,8 @@ class Grid:
 
     def dtt_set_tuning(self, tuning):
         t = tuning if isinstance(tuning, Tuning) else Tuning(int(tuning["residual_zchunk"]),
-                                                                 int(tuning["fft_generic"]), 0.0)
+                                                                 int(tuning["fft_generic"]),
+                                                                 int(tuning.get("z_route", 0)), 0.0)
         _check(lib().dtt_set_tuning(self._h, C.byref(t)))
 
     def dtt_profile_iteration(self, iters, acv_mod=3, acv_on=ACV_P):
