@@ -50,6 +50,10 @@ L2_FLUSH_BYTES = 512 << 20
 # DTT, Green multiply, inverse DTT) reads and writes the three components in three sweeps;
 # the residual group (stress, divergence, reference term, Anderson store and Gram row)
 # reads u~ and writes p~ (25 B) and stores R and reads three older R slots (60 B)
+# kernel launches of one warm-start prediction: the features (5), the network's forward
+# pass (11 convolutions, 2 poolings, 2 upsamplings), the guess and its contact zone (2),
+# writing the guess (2) and the fallback rule's two start evaluations (2 x 5)
+LAUNCHES_PER_PREDICT = 34
 B_GREEN = 72
 B_RESIDUAL = 85
 # ncu DRAM bytes per launch of the Green-step kernels on this workload, keyed by the source
@@ -285,12 +289,16 @@ def run_ours(args, rank, world, local):
         from paper_2607_26082_b300 import warmstart
         net = warmstart.load_net(wpath, stream=stream.cuda_stream)
         learned = {"weights": os.path.relpath(wpath, ROOT), "kept": 0, "steps": 0}
+    dk = [float(r) * float(I["radius"]) for r in I["ratios"]]
 
     u_dev = torch.empty((3,) + tuple(gm.node_shape), dtype=torch.float64, device=dev)
     fp64_idx = set(spread(args.steps, args.fp64_steps))
     starts = {}                  # timed step -> (increment, start field on the device)
+    hist = {"u2": None, "fn": None, "u1": torch.empty_like(u_dev) if net is not None else None}
 
-    def step(s, record_start=False):
+    def step(s, record_start=False, centers=None):
+        """One increment: the learned arm keeps u~ of the increment before the previous
+        one and the previous reactions for the network's features."""
         k = s % ncyc
         if record_start:
             if k == 0:
@@ -298,14 +306,26 @@ def run_ours(args, rank, world, local):
             else:
                 gm.dtt_get_fields(u_out=u_dev)
                 starts[s] = (k, u_dev.clone())
-        gm.dtt_move_indenter(I["centers"][k])
+                torch.cuda.current_stream().synchronize()
+        if k == 0:
+            hist["u2"], hist["fn"] = None, None
+        gm.dtt_move_indenter((centers if centers is not None else I["centers"])[k])
         init = dtt.INIT_ZERO if k == 0 else dtt.INIT_PREVIOUS
         if net is not None and k > 0:
-            net.predict_increment(gm, spec, k)
+            gm.dtt_get_fields(u_out=hist["u1"])          # u~ of increment k-1, before it is replaced
+            depth = (dk[k - 2] if k >= 2 else 0.0, dk[k - 1], dk[k])
+            net.predict_increment(gm, hist["u2"], hist["fn"], depth)
             init = dtt.INIT_GUESS
         rep = gm.dtt_solve_step(tol, 20000, acv_mod=mod, init=init, graph_iters=GRAPH_ITERS)
         if rep.status != dtt.OK:
             raise RuntimeError("increment %d did not converge: %s" % (k, rep.as_dict()))
+        if net is not None:
+            if k > 0:
+                if hist["u2"] is None:
+                    hist["u2"] = torch.empty_like(u_dev)
+                hist["u2"], hist["u1"] = hist["u1"], hist["u2"]
+            hist["fn"] = torch.from_numpy(gm.dtt_get_contact()[2].copy()).to(dev)
+            torch.cuda.current_stream().synchronize()   # the library reads it on its own stream
         return k, rep
 
     for s in range(args.warmup):
@@ -331,7 +351,7 @@ def run_ours(args, rank, world, local):
         launches += launches_per_solve(rep.iterations, per_it)
         if net is not None and k > 0:
             kept += rep.start_from_guess
-            launches += net.launches_per_predict
+            launches += LAUNCHES_PER_PREDICT
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
@@ -364,15 +384,9 @@ def run_ours(args, rank, world, local):
     s0 = args.warmup + args.steps
     nface = None
     for j in range(n_e2e):
-        k = (s0 + j) % ncyc
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        gm.dtt_move_indenter(centers_h[k])
-        init = dtt.INIT_ZERO if k == 0 else dtt.INIT_PREVIOUS
-        if net is not None and k > 0:
-            net.predict_increment(gm, spec, k)
-            init = dtt.INIT_GUESS
-        rep = gm.dtt_solve_step(tol, 20000, acv_mod=mod, init=init, graph_iters=GRAPH_ITERS)
+        k, rep = step(s0 + j, centers=centers_h)
         gm.dtt_get_fields(u_out=u_host)
         act, gap, fn, force = gm.dtt_get_contact()
         e2e_t += time.perf_counter() - t0

@@ -17,8 +17,8 @@
  *   d1 = relu(conv(relu(conv(up(d2))) + e1))   c2 -> c1, c1 -> c1
  *   y  = conv(d1)                               c1 -> 16, channels 0..2 used
  * Input features per node (16 channels, 13 used): mean normalised stiffness E/E_max of the
- * adjacent voxels; for each component, 1 where the DOF is fixed (Dirichlet face or a
- * constraint row); eps* (6 entries) times 1000; the node coordinates divided by the cell
+ * adjacent voxels; for each component, 1 where the DOF is fixed (Dirichlet face, a
+ * constraint row, or the contact surface of an indenter); eps* (6 entries) times 1000; the node coordinates divided by the cell
  * edge.  Output: u~ / (n_max * 1e-3), n_max the largest voxel count of the cell's axes.
  * Parameters are packed layer by layer as W[27][cout][cin] (tap = 9 (dz+1) + 3 (dy+1) +
  * (dx+1)) followed by b[cout], in the layer order above; c1, c2, c3 are multiples of 16
@@ -75,6 +75,69 @@ dtt_status dtt_net_train_step(dtt_net* net, dtt_grid* grid, const double* u_targ
 /* Writes the network's guess of u~ into the grid (as dtt_set_initial), for a solve with
  * init = DTT_INIT_GUESS. */
 dtt_status dtt_net_predict(dtt_net* net, dtt_grid* grid);
+
+/* ---- Increment mode: the warm start of one load increment of a sphere indentation ----
+ *
+ * Algorithm 2 solves the contact problem increment by increment, each from the previous
+ * increment's field; its start sets the contact zone C = {g < 0} at the starting field
+ * (Section 5.1.3).  The paper names a better initialisation as a prospect (Section 5.4,
+ * conclusion).  In this mode the network maps the cell (stiffness, fixed-DOF masks, node
+ * coordinates: channels 0-3 and 10-12 as above) and the load of the increment to a guess
+ * of its displacement and of its contact pressure:
+ *   channels 4-6: the secant prediction of the increment divided by dd = d_k - d_(k-1):
+ *                 (u~_(k-1) - u~_(k-2)) s / dd with s = (d_k^1.5 - d_(k-1)^1.5) /
+ *                 (d_(k-1)^1.5 - d_(k-2)^1.5) (the Hertz force grows like d^1.5);
+ *   channel 7:    1 on the contact-surface nodes;
+ *   channel 8:    on those nodes, the gap of the secant-predicted position to the moved
+ *                 sphere (Section 5.1.1) divided by dd, clipped to [-8, 8];
+ *   channel 9:    on those nodes, the previous increment's contact pressure -f_n divided
+ *                 by its largest value f_max;
+ *   channels 13-15: 0.
+ * Outputs: channels 0-2 the correction c to the secant prediction, the guess being
+ * u~_k = u~_(k-1) + dd (secant / dd + c); channel 3 the contact pressure over f_max, the
+ * guess's initial contact zone being {pressure > threshold} (default 0.05).
+ * Training loss: mean over nodes and channels 0-2 of (y - t)^2 plus w times the mean over
+ * the surface nodes of (y_3 - t_3)^2 (w default 1), t the solver's converged increment
+ * (correction form) and pressure.
+ *
+ * Arguments common to the calls below: grid = a configured grid with an indenter, its u~
+ * the converged field of increment k-1 and its sphere moved to increment k's centre;
+ * u_prev2 = u~ of increment k-2 (device, 3 x n_nodes float64; NULL = zero); fn_prev = the
+ * normal reactions of increment k-1 at the surface nodes (device, n_surface float64, the
+ * order of dtt_get_contact); depth = {d_(k-2), d_(k-1), d_k} with 0 <= d_(k-2) < d_(k-1) <
+ * d_k (d_(k-2) = 0 with u_prev2 = NULL for the second increment).  DTT_ERR_STATE without
+ * an indenter, DTT_ERR_ARG on bad depths. */
+
+/* Loss weight w of the pressure term (>= 0), the pressure threshold of the initial contact
+ * zone, and the network's window: window_depth node layers from the contact face inward
+ * and window_lateral nodes across it, centred under the sphere (0: the whole grid).  The
+ * network sees, and corrects, only the window; outside it the guess is the secant
+ * prediction and no surface node starts in contact.  Defaults: 1, 0.05, 0, 0. */
+dtt_status dtt_net_set_increment(dtt_net* net, float pressure_weight, float active_threshold, int32_t window_lateral,
+                                 int32_t window_depth);
+
+/* Input features of increment k inside the window into host x [wz][wy][wx][16] (window
+ * extents; may be NULL: computed only). */
+dtt_status dtt_net_increment_features(dtt_net* net, dtt_grid* grid, const double* u_prev2, const double* fn_prev,
+                                      const double depth[3], float* x);
+
+/* One Adam step on increment k: u_target = its converged u~ (device, 3 x n_nodes float64),
+ * fn_target = its normal reactions (device, n_surface float64).  *loss before the update. */
+dtt_status dtt_net_train_increment(dtt_net* net, dtt_grid* grid, const double* u_prev2, const double* fn_prev,
+                                   const double depth[3], const double* u_target, const double* fn_target, float lr,
+                                   double* loss);
+
+/* Writes the guess of increment k into the grid: u~ and the initial contact zone, the
+ * current u~ (increment k-1's) kept as the fallback start.  The next solve with init =
+ * DTT_INIT_GUESS evaluates the Eq. 5 residual at the guess (its zone) and at the previous
+ * increment's field (zone {g < 0}) and starts from the lower. */
+dtt_status dtt_net_predict_increment(dtt_net* net, dtt_grid* grid, const double* u_prev2, const double* fn_prev,
+                                     const double depth[3]);
+
+/* Loss and gradients of the increment loss for host inputs (parity aid): x [nz][ny][nx][16],
+ * target [nz][ny][nx][4], pmask [nz][ny][nx] (1 on surface nodes), grad (host, num_params). */
+dtt_status dtt_net_loss_grad_increment(dtt_net* net, int32_t nx, int32_t ny, int32_t nz, const float* x,
+                                       const float* target, const float* pmask, double* loss, float* grad);
 
 #ifdef __cplusplus
 }

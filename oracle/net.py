@@ -180,8 +180,59 @@ def loss_and_output_grad(y, target, w=0.0):
 
 def loss_grad(layers, x, target, w=0.0):
     """Loss of loss_and_output_grad and its gradients per layer."""
+    return loss_grad_with(layers, x, lambda y: loss_and_output_grad(y, target, w))
+
+
+def increment_loss_and_output_grad(y, target, pmask, wp=1.0):
+    """Increment mode (include/dtt_net.h): mean over nodes and channels 0..2 of
+    (y - t)^2 plus wp times the mean over the surface nodes (pmask = 1) of (y_3 - t_3)^2;
+    returns (loss, dloss/dy)."""
+    V = np.prod(y.shape[:3])
+    ns = float((pmask != 0).sum())
+    d = y[..., :3] - target[..., :3]
+    dp = (y[..., 3] - target[..., 3]) * (pmask != 0)
+    loss = (d * d).sum() / (3 * V) + (wp * (dp * dp).sum() / ns if ns > 0 else 0.0)
+    gy = np.zeros_like(y)
+    gy[..., :3] = 2.0 * d / (3 * V)
+    if ns > 0:
+        gy[..., 3] = 2.0 * wp * dp / ns
+    return float(loss), gy
+
+
+def increment_loss_grad(layers, x, target, pmask, wp=1.0):
+    return loss_grad_with(layers, x, lambda y: increment_loss_and_output_grad(y, target, pmask, wp))
+
+
+def increment_features(x, u1, u2, fn_prev, depth, surface_ijk, center, radius, eps=None):
+    """Channels 4..9 of the increment mode over base features x [nz, ny, nx, 16] (a copy is
+    returned): u1, u2 the fields of increments k-1 and k-2 ([3, nz, ny, nx]; u2 None =
+    zero), fn_prev the normal reactions of increment k-1 at surface_ijk (a list of node
+    (i, j, k)), depth = (d_(k-2), d_(k-1), d_k), the sphere of increment k (centre, radius),
+    eps the macroscopic strain of the affine lift (h = 1)."""
+    x = np.array(x, dtype=np.float64)
+    d0, d1, d2 = depth
+    s = (d2 ** 1.5 - d1 ** 1.5) / (d1 ** 1.5 - d0 ** 1.5)
+    dd = d2 - d1
+    du = u1 - (0.0 if u2 is None else u2)
+    w = du * s / dd                              # secant prediction over dd
+    x[..., 4:7] = np.moveaxis(w, 0, -1)
+    x[..., 7:10] = 0.0
+    e = np.zeros((3, 3)) if eps is None else np.asarray(eps, float)
+    fmax = max(0.0, float(np.max(-np.asarray(fn_prev)))) if len(fn_prev) else 0.0
+    for q, (i, j, k) in enumerate(surface_ijk):
+        X = np.array([i, j, k], float)
+        M = X + e @ X + u1[:, k, j, i] + dd * w[:, k, j, i]
+        gap = np.linalg.norm(M - np.asarray(center, float)) - radius
+        x[k, j, i, 7] = 1.0
+        x[k, j, i, 8] = min(8.0, max(-8.0, gap / dd))
+        x[k, j, i, 9] = -fn_prev[q] / fmax if fmax > 0 else 0.0
+    return x
+
+
+def loss_grad_with(layers, x, loss_fn):
+    """Loss of loss_fn(y) -> (loss, dloss/dy) and its gradients per layer."""
     y, c = forward(layers, x)
-    loss, gy = loss_and_output_grad(y, target, w)
+    loss, gy = loss_fn(y)
     grads = [None] * 11
     L = layers
 
@@ -257,6 +308,11 @@ def features(spec):
             for node, comp in zip(row.nodes, row.comps):
                 i, j, k = node % nn[0], (node // nn[0]) % nn[1], node // (nn[0] * nn[1])
                 fixed[k, j, i, comp] = True
+    ind = spec.get("indenter")
+    if ind:   # the contact surface's DOFs count as constrained
+        sl = [slice(None)] * 3
+        sl[2 - ind["axis"]] = 0 if ind["face"] == 0 else nn[ind["axis"]] - 1
+        fixed[tuple(sl)] = True
     for c in range(3):
         for d in range(3):
             if per[d]:

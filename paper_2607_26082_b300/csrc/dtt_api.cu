@@ -622,31 +622,9 @@ dtt_status to_grid_u(dtt_grid* G, const double* u, int is_dev) {
 }
 
 dtt_status zero_dirichlet(dtt_grid* G) {
-  // enforce u~ = 0 on Dirichlet-face DOFs via a host mask pass (set-up only)
-  const size_t n3 = (size_t)(3 * G->NN);
-  std::vector<double> hu(n3);
-  if (G->prec == DTT_PREC_FP64) {
-    CK(cudaMemcpy(hu.data(), G->u64, n3 * sizeof(double), cudaMemcpyDeviceToHost));
-  } else {
-    CKL(launch_join((long long)n3, G->uhi, G->ulo, G->op_d, G->stream));
-    CK(cudaStreamSynchronize(G->stream));
-    CK(cudaMemcpy(hu.data(), G->op_d, n3 * sizeof(double), cudaMemcpyDeviceToHost));
-  }
-  bool changed = false;
-  for (int c = 0; c < 3; ++c)
-    for (long long n = 0; n < G->NN; ++n) {
-      bool dof;
-      double W;
-      host_node_W(G, c, n, dof, W);
-      if (!dof && hu[(size_t)(c * G->NN + n)] != 0.0) {
-        hu[(size_t)(c * G->NN + n)] = 0.0;
-        changed = true;
-      }
-    }
-  if (changed) {
-    CK(cudaMemcpy(G->op_d, hu.data(), n3 * sizeof(double), cudaMemcpyHostToDevice));
-    return to_grid_u(G, G->op_d, 1);
-  }
+  // enforce u~ = 0 on Dirichlet-face DOFs
+  CKL(launch_zero_dirichlet(G->g, G->u64, G->uhi, G->ulo, G->stream));
+  CK(cudaStreamSynchronize(G->stream));
   return DTT_OK;
 }
 
@@ -679,8 +657,10 @@ void free_contact(dtt_grid* G) {
   dfree(G->d_gap);
   dfree(G->d_fn);
   dfree(G->d_nvec);
+  dfree(G->d_active_saved);
   G->nface = 0;
   G->contact = false;
+  G->contact_given = false;
 }
 
 }  // namespace
@@ -1152,6 +1132,29 @@ dtt_status dtt_clear_indenter(dtt_grid* G) {
   return rebuild_cmask(G);
 }
 
+}  // extern "C"
+
+dtt_status dtt::set_guess_with_fallback(dtt_grid* G, const double* u_dev, const uint8_t* active_dev) {
+  cudaStream_t s = G->stream;
+  const size_t n3 = (size_t)(3 * G->NN);
+  if (G->prec == DTT_PREC_FP64) {
+    CK(cudaMemcpyAsync(G->R[0], G->u64, n3 * 8, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(cudaMemcpyAsync(G->R[0], G->uhi, n3 * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(G->R[1], G->ulo, n3 * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  dtt_status st = dtt_set_initial(G, u_dev, 1);
+  if (st != DTT_OK) return st;
+  if (active_dev && G->contact) {
+    st = dtt_set_initial_contact(G, active_dev, 1);
+    if (st != DTT_OK) return st;
+  }
+  G->fallback_saved = true;
+  return DTT_OK;
+}
+
+extern "C" {
+
 dtt_status dtt_set_initial_contact(dtt_grid* G, const uint8_t* active, int32_t ptr_is_device) {
   if (!G || !active) return fail(DTT_ERR_ARG, "null argument");
   if (!G->contact) return fail(DTT_ERR_STATE, "no indenter set");
@@ -1224,27 +1227,59 @@ dtt_status eval_start_residual(dtt_grid* G, double* r) {
   return DTT_OK;
 }
 
-// DTT_INIT_GUESS: keep the supplied u~ only if its starting residual is below u~ = 0's.
+// DTT_INIT_GUESS: keep the supplied u~ only if its starting residual is below the plain
+// start's: u~ = 0, or the previous increment's u~ when the guess was set over it
+// (set_guess_with_fallback).  A contact zone set with the guess is the guess's; the plain
+// start takes the zone {g < 0} of its own field.
 dtt_status choose_start(dtt_grid* G) {
   cudaStream_t s = G->stream;
   const size_t n3 = (size_t)(3 * G->NN);
   const bool f64 = G->prec == DTT_PREC_FP64;
+  const bool zone = G->contact && G->contact_given;
   double rg = 0.0, r0 = 0.0;
   dtt_status st = f64 ? eval_start_residual<double>(G, &rg) : eval_start_residual<float>(G, &rg);
   if (st != DTT_OK) return st;
+  if (zone) {
+    if (!G->d_active_saved && (st = dalloc(&G->d_active_saved, (size_t)G->nface)) != DTT_OK) return st;
+    CK(cudaMemcpyAsync(G->d_active_saved, G->d_active, (size_t)G->nface, cudaMemcpyDeviceToDevice, s));
+  }
+  // the guess to S[3] / S[4]; the plain start into u~
   if (f64) {
     CK(cudaMemcpyAsync(G->S[4], G->u64, n3 * 8, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(G->u64, 0, n3 * 8, s));
+    if (G->fallback_saved) CK(cudaMemcpyAsync(G->u64, G->R[0], n3 * 8, cudaMemcpyDeviceToDevice, s));
+    else CK(cudaMemsetAsync(G->u64, 0, n3 * 8, s));
   } else {
     CK(cudaMemcpyAsync(G->S[3], G->uhi, n3 * 4, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(G->S[4], G->ulo, n3 * 4, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(G->uhi, 0, n3 * 4, s));
-    CK(cudaMemsetAsync(G->ulo, 0, n3 * 4, s));
+    if (G->fallback_saved) {
+      CK(cudaMemcpyAsync(G->uhi, G->R[0], n3 * 4, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(G->ulo, G->R[1], n3 * 4, cudaMemcpyDeviceToDevice, s));
+    } else {
+      CK(cudaMemsetAsync(G->uhi, 0, n3 * 4, s));
+      CK(cudaMemsetAsync(G->ulo, 0, n3 * 4, s));
+    }
   }
+  const bool had_fallback = G->fallback_saved;
+  G->contact_given = false;
+  G->fallback_saved = false;
   st = f64 ? eval_start_residual<double>(G, &r0) : eval_start_residual<float>(G, &r0);
   if (st != DTT_OK) return st;
   G->start_guess = (std::isfinite(rg) && rg < r0) ? 1 : 0;
   G->start_r = G->start_guess ? rg : r0;
+  if (!G->start_guess) {
+    // the plain start as it was before its evaluation projected it: the solve's own start
+    // then matches a plain solve exactly
+    if (f64) {
+      if (had_fallback) CK(cudaMemcpyAsync(G->u64, G->R[0], n3 * 8, cudaMemcpyDeviceToDevice, s));
+      else CK(cudaMemsetAsync(G->u64, 0, n3 * 8, s));
+    } else if (had_fallback) {
+      CK(cudaMemcpyAsync(G->uhi, G->R[0], n3 * 4, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(G->ulo, G->R[1], n3 * 4, cudaMemcpyDeviceToDevice, s));
+    } else {
+      CK(cudaMemsetAsync(G->uhi, 0, n3 * 4, s));
+      CK(cudaMemsetAsync(G->ulo, 0, n3 * 4, s));
+    }
+  }
   if (G->start_guess) {
     if (f64) {
       CK(cudaMemcpyAsync(G->u64, G->S[4], n3 * 8, cudaMemcpyDeviceToDevice, s));
@@ -1252,10 +1287,10 @@ dtt_status choose_start(dtt_grid* G) {
       CK(cudaMemcpyAsync(G->uhi, G->S[3], n3 * 4, cudaMemcpyDeviceToDevice, s));
       CK(cudaMemcpyAsync(G->ulo, G->S[4], n3 * 4, cudaMemcpyDeviceToDevice, s));
     }
-  } else if (G->contact) {
-    // the contact zone was initialised for the guess; zero u~ takes the plain start's
-    dtt_status st2 = f64 ? eval_start_residual<double>(G, &r0) : eval_start_residual<float>(G, &r0);
-    if (st2 != DTT_OK) return st2;
+    if (zone) {
+      CK(cudaMemcpyAsync(G->d_active, G->d_active_saved, (size_t)G->nface, cudaMemcpyDeviceToDevice, s));
+      G->contact_given = true;
+    }
   }
   CK(cudaStreamSynchronize(s));
   return DTT_OK;

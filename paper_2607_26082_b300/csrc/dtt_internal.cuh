@@ -369,6 +369,7 @@ int launch_ctrl_end(Ctrl* c, cudaStream_t s);
 int launch_to_double(long long n, const void* in, int in_is_float, double* out, cudaStream_t s);
 int launch_from_double(long long n, const double* in, void* out, int out_is_float, cudaStream_t s);
 int launch_split(long long n, const double* in, float* hi, float* lo, cudaStream_t s);
+int launch_zero_dirichlet(const GridDev& g, double* u64, float* uhi, float* ulo, cudaStream_t s);
 int launch_join(long long n, const float* hi, const float* lo, double* out, cudaStream_t s);
 int min_jacobian_blocks(const GridDev& g);
 int launch_min_jacobian(const GridDev& g, const double* u, const double eps[3][3], double* block_min,

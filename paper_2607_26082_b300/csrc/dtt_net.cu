@@ -71,6 +71,18 @@ struct dtt_net {
   double* d_loss = nullptr;
   double* d_u = nullptr;   // [3][V0] guess of u~ (float64)
   float* d_en = nullptr;   // per-phase normalised stiffness
+  // increment mode
+  float* inc_t = nullptr;  // [V0][4] targets
+  float* inc_m = nullptr;  // [V0] surface mask of the pressure term
+  float* d_fmax = nullptr; // largest contact pressure of the previous increment
+  uint8_t* d_act = nullptr;
+  int act_cap = 0;
+  float inc_wp = 1.f;      // weight of the pressure term of the loss
+  float inc_thr = 0.05f;   // predicted pressure above which a surface node starts in contact
+  int win_lat = 0;         // window: nodes across the contact face (0: whole grid)
+  int win_dep = 0;         // window: node layers below the contact face (0: whole grid)
+  double* d_ug = nullptr;  // [3][NN] guess of u~ on the whole grid (increment mode)
+  long long ug_cap = 0;
 };
 
 namespace {
@@ -98,7 +110,7 @@ void free_workspace(dtt_net* N) {
   nfree(N->xf); nfree(N->x); nfree(N->a0); nfree(N->e1); nfree(N->p1); nfree(N->a2); nfree(N->e2); nfree(N->p2);
   nfree(N->a4); nfree(N->e3); nfree(N->u2); nfree(N->r6); nfree(N->d2a); nfree(N->d2b); nfree(N->u1); nfree(N->r8);
   nfree(N->d1a); nfree(N->d1b); nfree(N->y); nfree(N->tgt); nfree(N->gP); nfree(N->gQ); nfree(N->ge1); nfree(N->ge2);
-  nfree(N->dz); nfree(N->d_u);
+  nfree(N->dz); nfree(N->d_u); nfree(N->inc_t); nfree(N->inc_m);
   N->cap0 = N->cap1 = N->cap2 = 0;
 }
 
@@ -124,6 +136,7 @@ dtt_status ensure_workspace(dtt_net* N, int nx, int ny, int nz) {
   F(&N->y, c0 * NET_COUT); F(&N->tgt, c0 * 3);
   F(&N->gP, c0 * cmax); F(&N->gQ, c0 * cmax); F(&N->ge1, c0 * c1); F(&N->ge2, cc1 * c2);
   B(&N->dz, c0 * cmax);
+  F(&N->inc_t, c0 * 4); F(&N->inc_m, c0);
   if (s == DTT_OK) s = nalloc(&N->d_u, (size_t)c0 * 3 * sizeof(double));
   if (s != DTT_OK) {
     free_workspace(N);
@@ -208,15 +221,32 @@ dtt_status forward(dtt_net* N) {
   return DTT_OK;
 }
 
+dtt_status bwd_chain(dtt_net* N);
+
 // loss against N->tgt and the gradients of every parameter into N->g
 dtt_status backward(dtt_net* N, double* loss) {
-  const Dims &d0 = N->d0, &d1 = N->d1, &d2 = N->d2;
+  const Dims& d0 = N->d0;
   cudaStream_t s = N->stream;
-  const int c1 = N->c1, c2 = N->c2, c3 = N->c3;
   NCK(cudaMemsetAsync(N->g, 0, (size_t)N->np * sizeof(float), s));
   NCK(cudaMemsetAsync(N->d_loss, 0, sizeof(double), s));
   const float sc = (float)std::max(d0.n[0], std::max(d0.n[1], d0.n[2]));
   NCKL(launch_loss(N->y, N->tgt, d0.n[0], d0.n[1], d0.n[2], NET_COUT, N->grad_weight * sc * sc, N->gP, N->d_loss, s));
+  dtt_status st = bwd_chain(N);
+  if (st != DTT_OK) return st;
+  if (loss) {
+    NCK(cudaMemcpyAsync(loss, N->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NCK(cudaStreamSynchronize(s));
+  }
+  return DTT_OK;
+}
+
+// the layers' backward passes from the output gradient in N->gP (parameter gradients
+// accumulate into N->g, which the caller has cleared)
+dtt_status bwd_chain(dtt_net* N) {
+  const Dims &d0 = N->d0, &d1 = N->d1, &d2 = N->d2;
+  cudaStream_t s = N->stream;
+  const int c1 = N->c1, c2 = N->c2, c3 = N->c3;
+  (void)c3;
   dtt_status st;
   if ((st = bwd_layer(N, 10, d0, N->d1b, N->gP, nullptr, N->gQ)) != DTT_OK) return st;
   if ((st = bwd_layer(N, 9, d0, N->d1a, N->gQ, N->d1b, N->gP)) != DTT_OK) return st;
@@ -235,10 +265,6 @@ dtt_status backward(dtt_net* N, double* loss) {
   NCKL(launch_pool_bwd_add(N->gQ, d0.n[0], d0.n[1], d0.n[2], c1, N->ge1, s));
   if ((st = bwd_layer(N, 1, d0, N->a0, N->ge1, N->e1, N->gP)) != DTT_OK) return st;
   if ((st = bwd_layer(N, 0, d0, N->x, N->gP, N->a0, nullptr)) != DTT_OK) return st;
-  if (loss) {
-    NCK(cudaMemcpyAsync(loss, N->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
-    NCK(cudaStreamSynchronize(s));
-  }
   return DTT_OK;
 }
 
@@ -249,10 +275,19 @@ dtt_status upload_input(dtt_net* N, const float* x_host) {
   return DTT_OK;
 }
 
-// features of a grid into N->xf / N->x (workspace sized for the grid's nodes)
-dtt_status grid_features(dtt_net* N, dtt_grid* G) {
+Window whole_grid(const dtt_grid* G) {
+  Window w{};
+  for (int d = 0; d < 3; ++d) {
+    w.o[d] = 0;
+    w.n[d] = G->g.nn[d];
+  }
+  return w;
+}
+
+// features of a grid's nodes inside window w into N->xf / N->x (workspace sized for w)
+dtt_status grid_features(dtt_net* N, dtt_grid* G, const Window& w) {
   if (!G->mat_set) return set_error(DTT_ERR_STATE, "dtt_set_material not called");
-  dtt_status st = ensure_workspace(N, G->g.nn[0], G->g.nn[1], G->g.nn[2]);
+  dtt_status st = ensure_workspace(N, w.n[0], w.n[1], w.n[2]);
   if (st != DTT_OK) return st;
   std::vector<double> lam(G->nphase), mu(G->nphase);
   NCK(cudaMemcpy(lam.data(), G->d_lam, G->nphase * sizeof(double), cudaMemcpyDeviceToHost));
@@ -272,6 +307,7 @@ dtt_status grid_features(dtt_net* N, dtt_grid* G) {
   NCK(cudaMemcpyAsync(N->d_en, en.data(), MAX_PHASE * sizeof(float), cudaMemcpyHostToDevice, N->stream));
   FeatArgs fa{};
   fa.g = G->g;
+  fa.w = w;
   fa.phase = G->phase;
   fa.enorm = N->d_en;
   fa.cmask = G->cmask;
@@ -279,6 +315,59 @@ dtt_status grid_features(dtt_net* N, dtt_grid* G) {
   for (int q = 0; q < 6; ++q) fa.eps6[q] = (float)(1000.0 * e6[q]);
   fa.x = N->xf;
   NCKL(launch_features(fa, N->stream));
+  NCKL(launch_f2bf(N->xf, N->d0.V() * 16, N->x, N->stream));
+  return DTT_OK;
+}
+
+// Increment mode: base features of the grid, then the increment channels (secant
+// prediction, surface gap at the moved sphere, previous pressure) from u~ of increment
+// k-1 (the grid's current u~), u~ of increment k-2 (u2, device, null = zero), the previous
+// normal reactions fn_prev (device, per surface node) and the depths d_(k-2), d_(k-1), d_k.
+dtt_status inc_setup(dtt_net* N, dtt_grid* G, const double* u2, const double* fn_prev, const double depth[3],
+                     IncArgs& a) {
+  if (!G->contact) return set_error(DTT_ERR_STATE, "no indenter set");
+  if (!fn_prev || !depth) return set_error(DTT_ERR_ARG, "null argument");
+  if (!(depth[0] >= 0.0) || !(depth[1] > depth[0]) || !(depth[2] > depth[1]))
+    return set_error(DTT_ERR_ARG, "depths must satisfy 0 <= d_(k-2) < d_(k-1) < d_k");
+  // the window: win_dep layers from the contact face inward, win_lat nodes across it
+  // centred under the sphere
+  Window w = whole_grid(G);
+  for (int d = 0; d < 3; ++d) {
+    const int nn = G->g.nn[d];
+    if (d == G->c_axis) {
+      if (N->win_dep > 0 && N->win_dep < nn) {
+        w.n[d] = N->win_dep;
+        w.o[d] = G->c_face == 1 ? nn - N->win_dep : 0;
+      }
+    } else if (N->win_lat > 0 && N->win_lat < nn) {
+      w.n[d] = N->win_lat;
+      const int c = (int)std::lround(G->center[d] / G->g.h) - N->win_lat / 2;
+      w.o[d] = std::min(std::max(c, 0), nn - N->win_lat);
+    }
+  }
+  dtt_status st = grid_features(N, G, w);
+  if (st != DTT_OK) return st;
+  if (!N->d_fmax && (st = nalloc(&N->d_fmax, sizeof(float))) != DTT_OK) return st;
+  const double p0 = std::pow(depth[0], 1.5), p1 = std::pow(depth[1], 1.5), p2 = std::pow(depth[2], 1.5);
+  a = IncArgs{};
+  a.g = G->g;
+  a.w = w;
+  a.u64 = G->u64;
+  a.uhi = G->uhi;
+  a.ulo = G->ulo;
+  a.u2 = u2;
+  a.s_sec = (p2 - p1) / (p1 - p0);
+  a.dd = depth[2] - depth[1];
+  a.nface = G->nface;
+  a.node = G->d_face;
+  a.fn_prev = fn_prev;
+  for (int c = 0; c < 3; ++c) a.center[c] = G->center[c];
+  a.radius = G->radius;
+  std::memcpy(a.eps, G->eps, sizeof(a.eps));
+  a.fmax = N->d_fmax;
+  a.x = N->xf;
+  NCKL(launch_inc_fmax(a, N->stream));
+  NCKL(launch_inc_features(a, N->stream));
   NCKL(launch_f2bf(N->xf, N->d0.V() * 16, N->x, N->stream));
   return DTT_OK;
 }
@@ -369,6 +458,9 @@ void dtt_net_destroy(dtt_net* N) {
   nfree(N->wbuf);
   nfree(N->d_loss);
   nfree(N->d_en);
+  nfree(N->d_fmax);
+  nfree(N->d_act);
+  nfree(N->d_ug);
   if (N->own_stream && N->stream) cudaStreamDestroy(N->stream);
   delete N;
 }
@@ -435,7 +527,7 @@ dtt_status dtt_net_forward(dtt_net* N, int32_t nx, int32_t ny, int32_t nz, const
 
 dtt_status dtt_net_features(dtt_net* N, dtt_grid* G, float* x) {
   if (!N || !G || !x) return set_error(DTT_ERR_ARG, "null argument");
-  dtt_status s = grid_features(N, G);
+  dtt_status s = grid_features(N, G, whole_grid(G));
   if (s != DTT_OK) return s;
   NCK(cudaMemcpyAsync(x, N->xf, (size_t)N->d0.V() * 16 * sizeof(float), cudaMemcpyDeviceToHost, N->stream));
   NCK(cudaStreamSynchronize(N->stream));
@@ -444,7 +536,7 @@ dtt_status dtt_net_features(dtt_net* N, dtt_grid* G, float* x) {
 
 dtt_status dtt_net_train_step(dtt_net* N, dtt_grid* G, const double* u_target, float lr, double* loss) {
   if (!N || !G || !u_target || !(lr > 0.f)) return set_error(DTT_ERR_ARG, "bad argument");
-  dtt_status s = grid_features(N, G);
+  dtt_status s = grid_features(N, G, whole_grid(G));
   if (s != DTT_OK) return s;
   const long long V = N->d0.V();
   const double inv = 1.0 / u_scale(G);
@@ -463,9 +555,120 @@ dtt_status dtt_net_train_step(dtt_net* N, dtt_grid* G, const double* u_target, f
   return DTT_OK;
 }
 
+dtt_status dtt_net_set_increment(dtt_net* N, float pressure_weight, float active_threshold, int32_t window_lateral,
+                                 int32_t window_depth) {
+  if (!N || !(pressure_weight >= 0.f) || !std::isfinite(active_threshold) || window_lateral < 0 || window_depth < 0)
+    return set_error(DTT_ERR_ARG, "pressure_weight >= 0, a finite threshold and window sizes >= 0 required");
+  N->inc_wp = pressure_weight;
+  N->inc_thr = active_threshold;
+  N->win_lat = window_lateral;
+  N->win_dep = window_depth;
+  return DTT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// surface nodes inside the window (the pressure term's count)
+long long window_surface(const dtt_grid* G, const IncArgs& a) {
+  long long n = 1;
+  for (int d = 0; d < 3; ++d)
+    if (d != G->c_axis) n *= a.w.n[d];
+  return n;
+}
+}  // namespace
+
+extern "C" {
+
+dtt_status dtt_net_increment_features(dtt_net* N, dtt_grid* G, const double* u_prev2, const double* fn_prev,
+                                      const double depth[3], float* x) {
+  if (!N || !G) return set_error(DTT_ERR_ARG, "null argument");
+  IncArgs a;
+  dtt_status s = inc_setup(N, G, u_prev2, fn_prev, depth, a);
+  if (s != DTT_OK) return s;
+  if (x) NCK(cudaMemcpyAsync(x, N->xf, (size_t)N->d0.V() * 16 * sizeof(float), cudaMemcpyDeviceToHost, N->stream));
+  NCK(cudaStreamSynchronize(N->stream));
+  return DTT_OK;
+}
+
+dtt_status dtt_net_train_increment(dtt_net* N, dtt_grid* G, const double* u_prev2, const double* fn_prev,
+                                   const double depth[3], const double* u_target, const double* fn_target, float lr,
+                                   double* loss) {
+  if (!N || !G || !u_target || !fn_target || !(lr > 0.f)) return set_error(DTT_ERR_ARG, "bad argument");
+  IncArgs a;
+  dtt_status s = inc_setup(N, G, u_prev2, fn_prev, depth, a);
+  if (s != DTT_OK) return s;
+  cudaStream_t st = N->stream;
+  NCKL(launch_inc_targets(a, u_target, fn_target, N->inc_t, N->inc_m, st));
+  if ((s = forward(N)) != DTT_OK) return s;
+  NCK(cudaMemsetAsync(N->g, 0, (size_t)N->np * sizeof(float), st));
+  NCK(cudaMemsetAsync(N->d_loss, 0, sizeof(double), st));
+  const float wp = N->inc_wp / (float)window_surface(G, a);
+  NCKL(launch_inc_loss(N->y, N->inc_t, N->inc_m, N->d0.V(), NET_COUT, wp, N->gP, N->d_loss, st));
+  if ((s = bwd_chain(N)) != DTT_OK) return s;
+  double l = 0.0;
+  NCK(cudaMemcpyAsync(&l, N->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+  N->step += 1;
+  NCKL(launch_adam(N->p, N->g, N->m, N->v, N->np, lr, N->step, st));
+  if ((s = refresh_bf16(N)) != DTT_OK) return s;
+  NCK(cudaStreamSynchronize(st));
+  if (loss) *loss = l;
+  return DTT_OK;
+}
+
+dtt_status dtt_net_predict_increment(dtt_net* N, dtt_grid* G, const double* u_prev2, const double* fn_prev,
+                                     const double depth[3]) {
+  if (!N || !G) return set_error(DTT_ERR_ARG, "null argument");
+  IncArgs a;
+  dtt_status s = inc_setup(N, G, u_prev2, fn_prev, depth, a);
+  if (s != DTT_OK) return s;
+  if (N->act_cap < G->nface) {
+    nfree(N->d_act);
+    N->act_cap = 0;
+    if ((s = nalloc(&N->d_act, (size_t)G->nface)) != DTT_OK) return s;
+    N->act_cap = G->nface;
+  }
+  if (N->ug_cap < 3 * G->NN) {
+    nfree(N->d_ug);
+    N->ug_cap = 0;
+    if ((s = nalloc(&N->d_ug, (size_t)(3 * G->NN) * sizeof(double))) != DTT_OK) return s;
+    N->ug_cap = 3 * G->NN;
+  }
+  if ((s = forward(N)) != DTT_OK) return s;
+  NCKL(launch_inc_guess(a, N->y, NET_COUT, N->inc_thr, N->d_ug, N->d_act, N->stream));
+  NCK(cudaStreamSynchronize(N->stream));
+  return set_guess_with_fallback(G, N->d_ug, N->d_act);
+}
+
+dtt_status dtt_net_loss_grad_increment(dtt_net* N, int32_t nx, int32_t ny, int32_t nz, const float* x,
+                                       const float* target, const float* pmask, double* loss, float* grad) {
+  if (!N || !x || !target || !pmask || nx < 1 || ny < 1 || nz < 1) return set_error(DTT_ERR_ARG, "bad argument");
+  dtt_status s = ensure_workspace(N, nx, ny, nz);
+  if (s != DTT_OK) return s;
+  if ((s = upload_input(N, x)) != DTT_OK) return s;
+  const long long V = N->d0.V();
+  cudaStream_t st = N->stream;
+  NCK(cudaMemcpyAsync(N->inc_t, target, (size_t)V * 4 * sizeof(float), cudaMemcpyHostToDevice, st));
+  NCK(cudaMemcpyAsync(N->inc_m, pmask, (size_t)V * sizeof(float), cudaMemcpyHostToDevice, st));
+  double ns = 0.0;
+  for (long long v = 0; v < V; ++v) ns += pmask[v] != 0.f ? 1.0 : 0.0;
+  if ((s = forward(N)) != DTT_OK) return s;
+  NCK(cudaMemsetAsync(N->g, 0, (size_t)N->np * sizeof(float), st));
+  NCK(cudaMemsetAsync(N->d_loss, 0, sizeof(double), st));
+  const float wp = ns > 0.0 ? N->inc_wp / (float)ns : 0.f;
+  NCKL(launch_inc_loss(N->y, N->inc_t, N->inc_m, V, NET_COUT, wp, N->gP, N->d_loss, st));
+  if ((s = bwd_chain(N)) != DTT_OK) return s;
+  double l = 0.0;
+  NCK(cudaMemcpyAsync(&l, N->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (grad) NCK(cudaMemcpyAsync(grad, N->g, N->np * sizeof(float), cudaMemcpyDeviceToHost, st));
+  NCK(cudaStreamSynchronize(st));
+  if (loss) *loss = l;
+  return DTT_OK;
+}
+
 dtt_status dtt_net_predict(dtt_net* N, dtt_grid* G) {
   if (!N || !G) return set_error(DTT_ERR_ARG, "null argument");
-  dtt_status s = grid_features(N, G);
+  dtt_status s = grid_features(N, G, whole_grid(G));
   if (s != DTT_OK) return s;
   if ((s = forward(N)) != DTT_OK) return s;
   NCKL(launch_out_to_u(N->y, N->d0.V(), NET_COUT, u_scale(G), N->d_u, N->stream));

@@ -94,6 +94,9 @@ struct dtt_grid {
   double center[3]{}, radius = 0;
   int nface = 0;
   bool contact_given = false;   // the next start keeps the zone set by dtt_set_initial_contact
+  bool fallback_saved = false;  // a guess was set over u~ of the previous increment, kept in
+                                // the R ring as the fallback start of DTT_INIT_GUESS
+  uint8_t* d_active_saved = nullptr;
   long long* d_face = nullptr;
   uint8_t *d_active = nullptr, *d_vgap = nullptr, *d_vreact = nullptr, *d_vgap_prev = nullptr,
           *d_vreact_prev = nullptr;
@@ -125,4 +128,11 @@ struct dtt_grid {
 namespace dtt {
 // sets the thread's last-error message and returns s (dtt_last_error reads it)
 dtt_status set_error(dtt_status s, const std::string& msg);
+}  // namespace dtt
+
+namespace dtt {
+// Writes a guess of u~ (device, 3 x n_nodes float64) over the current u~, keeping the
+// current u~ as the fallback start of the next DTT_INIT_GUESS solve; with `active`
+// (device, n_surface bytes) the guess's initial contact zone as well.
+dtt_status set_guess_with_fallback(dtt_grid* G, const double* u_dev, const uint8_t* active_dev);
 }  // namespace dtt

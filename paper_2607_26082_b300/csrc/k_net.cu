@@ -547,9 +547,11 @@ int launch_relayout(const float* W, int cin, int cout, __nv_bfloat16* Wt, __nv_b
 // ---- input features of a grid's nodes (layout in include/dtt_net.h)
 __global__ void k_features(FeatArgs a) {
   const GridDev& g = a.g;
-  const long long n = g.nnodes;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-    const int idx[3] = {(int)(v % g.nn[0]), (int)((v / g.nn[0]) % g.nn[1]), (int)(v / ((long long)g.nn[0] * g.nn[1]))};
+  const long long n = win_volume(a.w);
+  for (long long vw = blockIdx.x * (long long)blockDim.x + threadIdx.x; vw < n; vw += (long long)gridDim.x * blockDim.x) {
+    const int idx[3] = {a.w.o[0] + (int)(vw % a.w.n[0]), a.w.o[1] + (int)((vw / a.w.n[0]) % a.w.n[1]),
+                        a.w.o[2] + (int)(vw / ((long long)a.w.n[0] * a.w.n[1]))};
+    const long long v = idx[0] + (long long)g.nn[0] * (idx[1] + (long long)g.nn[1] * idx[2]);
     float es = 0.f;
     int cnt = 0;
     for (int oz = -1; oz <= 0; ++oz)
@@ -568,7 +570,7 @@ __global__ void k_features(FeatArgs a) {
           es += a.enorm[a.phase[w[0] + (long long)g.nvox[0] * (w[1] + (long long)g.nvox[1] * w[2])]];
           ++cnt;
         }
-    float* x = a.x + v * 16;
+    float* x = a.x + vw * 16;
     x[0] = cnt ? es / (float)cnt : 0.f;
     const uint8_t cm = a.cmask ? a.cmask[v] : 0;
     for (int c = 0; c < 3; ++c) {
@@ -587,7 +589,183 @@ __global__ void k_features(FeatArgs a) {
 }
 
 int launch_features(const FeatArgs& a, cudaStream_t s) {
-  k_features<<<grid_1d(a.g.nnodes), 256, 0, s>>>(a);
+  k_features<<<grid_1d(win_volume(a.w)), 256, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+// ---- increment mode ---------------------------------------------------------------------
+__device__ __forceinline__ double inc_u1(const IncArgs& a, long long i) {
+  return a.u64 ? a.u64[i] : (double)a.uhi[i] + (double)a.ulo[i];
+}
+
+// fmax = max over the surface of -fn_prev (the previous increment's largest contact
+// pressure): non-negative floats order like their bit patterns
+__global__ void k_inc_fmax(IncArgs a) {
+  float m = 0.f;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < a.nface; q += gridDim.x * blockDim.x)
+    m = fmaxf(m, (float)(-a.fn_prev[q]));
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax((int*)a.fmax, __float_as_int(m));
+}
+
+__device__ __forceinline__ long long win_to_grid(const IncArgs& a, long long vw) {
+  const int i = a.w.o[0] + (int)(vw % a.w.n[0]), j = a.w.o[1] + (int)((vw / a.w.n[0]) % a.w.n[1]),
+            k = a.w.o[2] + (int)(vw / ((long long)a.w.n[0] * a.w.n[1]));
+  return i + (long long)a.g.nn[0] * (j + (long long)a.g.nn[1] * k);
+}
+// window index of grid node n, or -1 outside the window
+__device__ __forceinline__ long long grid_to_win(const IncArgs& a, long long n) {
+  int idx[3] = {(int)(n % a.g.nn[0]), (int)((n / a.g.nn[0]) % a.g.nn[1]), (int)(n / ((long long)a.g.nn[0] * a.g.nn[1]))};
+  for (int d = 0; d < 3; ++d) {
+    idx[d] -= a.w.o[d];
+    if (idx[d] < 0 || idx[d] >= a.w.n[d]) return -1;
+  }
+  return idx[0] + (long long)a.w.n[0] * (idx[1] + (long long)a.w.n[1] * idx[2]);
+}
+// the secant prediction of u~ at DOF i, divided by dd
+__device__ __forceinline__ double inc_secant(const IncArgs& a, long long i) {
+  return (inc_u1(a, i) - (a.u2 ? a.u2[i] : 0.0)) * a.s_sec / a.dd;
+}
+
+// channels 4-6: the secant prediction of the increment divided by dd; 7-9 cleared
+__global__ void k_inc_nodes(IncArgs a) {
+  const long long V = a.g.nnodes, Vw = win_volume(a.w);
+  for (long long vw = blockIdx.x * (long long)blockDim.x + threadIdx.x; vw < Vw; vw += (long long)gridDim.x * blockDim.x) {
+    const long long v = win_to_grid(a, vw);
+    float* x = a.x + vw * 16;
+    for (int c = 0; c < 3; ++c) x[4 + c] = (float)inc_secant(a, c * V + v);
+    x[7] = x[8] = x[9] = 0.f;
+  }
+}
+
+// surface nodes in the window: channel 7 = 1, 8 = gap of the secant-predicted position to
+// the moved sphere over dd (clipped to +-8), 9 = previous pressure over its maximum
+__global__ void k_inc_surface(IncArgs a) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.nface) return;
+  const long long V = a.g.nnodes;
+  const long long n = a.node[q];
+  const long long vw = grid_to_win(a, n);
+  if (vw < 0) return;
+  const int idx[3] = {(int)(n % a.g.nn[0]), (int)((n / a.g.nn[0]) % a.g.nn[1]), (int)(n / ((long long)a.g.nn[0] * a.g.nn[1]))};
+  float* x = a.x + vw * 16;
+  double X[3], r2 = 0.0;
+  for (int c = 0; c < 3; ++c) X[c] = a.g.h * idx[c];
+  for (int c = 0; c < 3; ++c) {
+    const double us = a.eps[c][0] * X[0] + a.eps[c][1] * X[1] + a.eps[c][2] * X[2];
+    const double m = X[c] + us + inc_u1(a, c * V + n) + a.dd * inc_secant(a, c * V + n);
+    r2 += (m - a.center[c]) * (m - a.center[c]);
+  }
+  const double gap = sqrt(r2) - a.radius;
+  const float fm = *a.fmax;
+  x[7] = 1.f;
+  x[8] = fminf(8.f, fmaxf(-8.f, (float)(gap / a.dd)));
+  x[9] = fm > 0.f ? (float)(-a.fn_prev[q]) / fm : 0.f;
+}
+
+__global__ void k_inc_targets(IncArgs a, const double* __restrict__ ut, float* __restrict__ t,
+                              float* __restrict__ m) {
+  const long long V = a.g.nnodes, Vw = win_volume(a.w);
+  for (long long vw = blockIdx.x * (long long)blockDim.x + threadIdx.x; vw < Vw; vw += (long long)gridDim.x * blockDim.x) {
+    const long long v = win_to_grid(a, vw);
+    for (int c = 0; c < 3; ++c) {
+      const long long i = c * V + v;
+      t[vw * 4 + c] = (float)((ut[i] - inc_u1(a, i)) / a.dd - inc_secant(a, i));
+    }
+    t[vw * 4 + 3] = 0.f;
+    m[vw] = 0.f;
+  }
+}
+__global__ void k_inc_targets_surface(IncArgs a, const double* __restrict__ fnt, float* __restrict__ t,
+                                      float* __restrict__ m) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.nface) return;
+  const long long vw = grid_to_win(a, a.node[q]);
+  if (vw < 0) return;
+  const float fm = *a.fmax;
+  t[vw * 4 + 3] = fm > 0.f ? (float)(-fnt[q]) / fm : 0.f;
+  m[vw] = 1.f;
+}
+
+// loss = mean over window nodes and the three displacement channels of (y - t)^2 + wp *
+// mean over the window's surface nodes of (y3 - t3)^2; gy = dloss/dy
+__global__ void k_inc_loss(const float* __restrict__ y, const float* __restrict__ t, const float* __restrict__ m,
+                           long long V, int CY, float inv3v, float wp_ns, float* __restrict__ gy,
+                           double* __restrict__ loss) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V * CY; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % CY);
+    const long long v = i / CY;
+    float g = 0.f;
+    if (c < 3) {
+      const float d = y[i] - t[v * 4 + c];
+      acc += (double)(d * d) * inv3v;
+      g = 2.f * d * inv3v;
+    } else if (c == 3 && m[v] != 0.f) {
+      const float d = y[i] - t[v * 4 + 3];
+      acc += (double)(d * d) * wp_ns;
+      g = 2.f * d * wp_ns;
+    }
+    gy[i] = g;
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    atomicAdd(loss, s);
+  }
+}
+
+// every node: u = u~_(k-1) + dd (secant + correction), the correction 0 outside the window
+__global__ void k_inc_guess(IncArgs a, const float* __restrict__ y, int CY, double* __restrict__ u) {
+  const long long V = a.g.nnodes;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * V; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / V);
+    const long long v = i - c * V;
+    const long long vw = grid_to_win(a, v);
+    const double corr = vw >= 0 ? (double)y[vw * CY + c] : 0.0;
+    u[i] = inc_u1(a, i) + a.dd * (inc_secant(a, i) + corr);
+  }
+}
+// surface nodes: in the initial zone where the predicted pressure exceeds thr (none
+// outside the window)
+__global__ void k_inc_active(IncArgs a, const float* __restrict__ y, int CY, float thr, uint8_t* __restrict__ act) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.nface) return;
+  const long long vw = grid_to_win(a, a.node[q]);
+  act[q] = (vw >= 0 && y[vw * CY + 3] > thr) ? 1 : 0;
+}
+
+int launch_inc_fmax(const IncArgs& a, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(a.fmax, 0, sizeof(float), s);
+  if (e != cudaSuccess) return (int)e;
+  if (a.nface > 0) k_inc_fmax<<<(a.nface + 255) / 256, 256, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+int launch_inc_features(const IncArgs& a, cudaStream_t s) {
+  k_inc_nodes<<<grid_1d(win_volume(a.w)), 256, 0, s>>>(a);
+  if (a.nface > 0) k_inc_surface<<<(a.nface + 255) / 256, 256, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+int launch_inc_targets(const IncArgs& a, const double* u_target, const double* fn_target, float* t, float* m,
+                       cudaStream_t s) {
+  k_inc_targets<<<grid_1d(win_volume(a.w)), 256, 0, s>>>(a, u_target, t, m);
+  if (a.nface > 0) k_inc_targets_surface<<<(a.nface + 255) / 256, 256, 0, s>>>(a, fn_target, t, m);
+  return (int)cudaGetLastError();
+}
+int launch_inc_loss(const float* y, const float* t, const float* m, long long V, int CY, float wp, float* gy,
+                    double* loss, cudaStream_t s) {
+  // the number of surface nodes enters through wp (wp / Ns computed by the caller)
+  k_inc_loss<<<grid_1d(V * CY), 256, 0, s>>>(y, t, m, V, CY, 1.f / (3.f * (float)V), wp, gy, loss);
+  return (int)cudaGetLastError();
+}
+int launch_inc_guess(const IncArgs& a, const float* y, int CY, float thr, double* u, uint8_t* active,
+                     cudaStream_t s) {
+  k_inc_guess<<<grid_1d(3 * a.g.nnodes), 256, 0, s>>>(a, y, CY, u);
+  if (a.nface > 0 && active) k_inc_active<<<(a.nface + 255) / 256, 256, 0, s>>>(a, y, CY, thr, active);
   return (int)cudaGetLastError();
 }
 

@@ -154,6 +154,10 @@ __device__ __forceinline__ void tz_put16(unsigned char* hi, unsigned char* lo, i
   }
 }
 
+// NC = P / 32 operand chunks (compile time: the pencil values of GEMM 1 are gathered into
+// registers in one batch of 16 NC loads per thread before the first chunk is written, so
+// that the whole tile's loads are in flight together)
+template <int NC>
 __global__ void __launch_bounds__(TZ_THREADS, 1)
 k_tz_green(const float* __restrict__ in, float* __restrict__ out, TzParams p, GreenTables gt, float l0, float m2,
            float ih2, int scheme, const Ctrl* ctrl) {
@@ -164,7 +168,7 @@ k_tz_green(const float* __restrict__ in, float* __restrict__ out, TzParams p, Gr
   __shared__ int s_err;
   const int comp = p.comp0 + blockIdx.y;
   const TzComp& cp = p.c[comp];
-  const int P = cp.P, NC = P / TZ_KC;
+  constexpr int P = NC * TZ_KC;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int m = tid & (TZ_M - 1);        // pencil row = tensor-memory lane
   const int half = tid >> 7;             // which 16 of a 32-wide chunk this thread handles
@@ -223,6 +227,7 @@ k_tz_green(const float* __restrict__ in, float* __restrict__ out, TzParams p, Gr
   // One pipelined contraction: chunk g (global count over both GEMMs) uses stage g & 1.
   // produce(cidx, hi, lo) writes A chunk cidx; the matrix chunk comes by bulk copy.
   auto run_gemm = [&](int g0, const unsigned char* mat, uint32_t dcol, auto produce) {
+#pragma unroll
     for (int c = 0; c < NC; ++c) {
       const int g = g0 + c, s = g & 1;
       if (g >= 2 && !s_err) {
@@ -269,15 +274,16 @@ k_tz_green(const float* __restrict__ in, float* __restrict__ out, TzParams p, Gr
   };
 
   // ---- GEMM 1: D1 = X F^T
-  run_gemm(0, (const unsigned char*)cp.fwd, d1, [&](int c, unsigned char* hi, unsigned char* lo) {
-    float v[16];
-    const int kb = c * TZ_KC + half * 16;
+  float xv[NC][16];
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int k = kb + q;
-      v[q] = (valid && k < cp.nj) ? in[base + (long long)(cp.j0 + k) * stride] : 0.f;
+      const int k = c * TZ_KC + half * 16 + q;
+      xv[c][q] = (valid && k < cp.nj) ? __ldg(in + base + (long long)(cp.j0 + k) * stride) : 0.f;
     }
-    tz_put16(hi, lo, m, half * 16, v);
+  run_gemm(0, (const unsigned char*)cp.fwd, d1, [&](int c, unsigned char* hi, unsigned char* lo) {
+    tz_put16(hi, lo, m, half * 16, xv[c]);
   });
   wait_last(NC - 1);
 
@@ -310,6 +316,7 @@ k_tz_green(const float* __restrict__ in, float* __restrict__ out, TzParams p, Gr
 
   // ---- epilogue 2: node values of the active rows, zeros on the others
   if (!s_err) {
+#pragma unroll
     for (int c = 0; c < NC; ++c) {
       float v[16];
       const int nb = c * TZ_KC + half * 16;
@@ -343,6 +350,19 @@ k_tz_green(const float* __restrict__ in, float* __restrict__ out, TzParams p, Gr
   }
 }
 
+template <int NC>
+static int tz_launch(dim3 grid, size_t sm, const float* in, float* out, const TzParams& p, const GreenTables& gt,
+                     float l0, float m2, float ih2, int scheme, const Ctrl* ctrl, cudaStream_t s) {
+  static size_t done = 0;   // per instance: the largest dynamic shared memory granted so far
+  if (sm > done) {
+    cudaError_t e = cudaFuncSetAttribute(k_tz_green<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    done = sm;
+  }
+  k_tz_green<NC><<<grid, TZ_THREADS, sm, s>>>(in, out, p, gt, l0, m2, ih2, scheme, ctrl);
+  return (int)cudaGetLastError();
+}
+
 size_t tz_smem_bytes(int P) {
   return (size_t)2 * 2 * TZ_M * TZ_KC * 4 + (size_t)2 * 2 * P * TZ_KC * 4 + (size_t)2 * P * 4;
 }
@@ -355,16 +375,19 @@ int launch_tz_green(const float* in, float* out, const TzParams& p, const GreenT
     if (p.c[c].P != P) return (int)cudaErrorInvalidValue;   // one shared-memory plan per launch
   if (P < TZ_KC || P > 256 || P % TZ_KC) return (int)cudaErrorInvalidValue;
   const size_t sm = tz_smem_bytes(P);
-  static size_t done = 0;
-  if (sm > done) {
-    cudaError_t e = cudaFuncSetAttribute(k_tz_green, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return (int)e;
-    done = sm;
-  }
   const float l0 = (float)lam0, m2 = (float)(2.0 * mu0), ih2 = (float)(4.0 / (h * h));
   dim3 grid((unsigned)((p.npencil + TZ_M - 1) / TZ_M), (unsigned)ncomp);
-  k_tz_green<<<grid, TZ_THREADS, sm, s>>>(in, out, p, gt, l0, m2, ih2, scheme, ctrl);
-  return (int)cudaGetLastError();
+  switch (P / TZ_KC) {
+    case 1: return tz_launch<1>(grid, sm, in, out, p, gt, l0, m2, ih2, scheme, ctrl, s);
+    case 2: return tz_launch<2>(grid, sm, in, out, p, gt, l0, m2, ih2, scheme, ctrl, s);
+    case 3: return tz_launch<3>(grid, sm, in, out, p, gt, l0, m2, ih2, scheme, ctrl, s);
+    case 4: return tz_launch<4>(grid, sm, in, out, p, gt, l0, m2, ih2, scheme, ctrl, s);
+    case 5: return tz_launch<5>(grid, sm, in, out, p, gt, l0, m2, ih2, scheme, ctrl, s);
+    case 6: return tz_launch<6>(grid, sm, in, out, p, gt, l0, m2, ih2, scheme, ctrl, s);
+    case 7: return tz_launch<7>(grid, sm, in, out, p, gt, l0, m2, ih2, scheme, ctrl, s);
+    case 8: return tz_launch<8>(grid, sm, in, out, p, gt, l0, m2, ih2, scheme, ctrl, s);
+    default: return (int)cudaErrorInvalidValue;
+  }
 }
 
 // Host side: the operand chunks of one component's matrices in the layout above.  For

@@ -3,6 +3,8 @@
 // or the finite-strain stresses of Section 5.2) used by dtt_get_fields and
 // dtt_get_stress_tensor, and the smallest det F over the integration points.  Not on the
 // iteration path.
+#include <algorithm>
+
 #include "dtt_internal.cuh"
 
 namespace dtt {
@@ -39,6 +41,34 @@ int launch_from_double(long long n, const double* in, void* out, int out_is_floa
   else k_convert<double, double><<<nblk(n), 256, 0, s>>>(n, in, (double*)out);
   return (int)cudaGetLastError();
 }
+// u~ = 0 on every Dirichlet-face DOF (a node on a face whose condition for the component
+// is Dirichlet, periodic axes excepted): the DOFs the discrete problem removes
+__global__ void k_zero_dirichlet(GridDev g, double* u64, float* uhi, float* ulo) {
+  const long long n3 = 3 * g.nnodes;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / g.nnodes);
+    const long long n = i - (long long)c * g.nnodes;
+    const int idx[3] = {(int)(n % g.nn[0]), (int)((n / g.nn[0]) % g.nn[1]), (int)(n / ((long long)g.nn[0] * g.nn[1]))};
+    bool dir = false;
+    for (int d = 0; d < 3; ++d) {
+      if (g.periodic[d]) continue;
+      if (idx[d] == 0 && g.bc[d][0][c] == BC_D) dir = true;
+      else if (idx[d] == g.nn[d] - 1 && g.bc[d][1][c] == BC_D) dir = true;
+    }
+    if (!dir) continue;
+    if (u64) u64[i] = 0.0;
+    if (uhi) uhi[i] = 0.f;
+    if (ulo) ulo[i] = 0.f;
+  }
+}
+
+int launch_zero_dirichlet(const GridDev& g, double* u64, float* uhi, float* ulo, cudaStream_t s) {
+  const long long n3 = 3 * g.nnodes;
+  const int blocks = (int)std::min<long long>((n3 + 255) / 256, 148LL * 16);
+  k_zero_dirichlet<<<blocks, 256, 0, s>>>(g, u64, uhi, ulo);
+  return (int)cudaGetLastError();
+}
+
 int launch_split(long long n, const double* in, float* hi, float* lo, cudaStream_t s) {
   k_split<<<nblk(n), 256, 0, s>>>(n, in, hi, lo);
   return (int)cudaGetLastError();

@@ -32,14 +32,54 @@ struct ConvArgs {
   float* db;                  // [cout] accumulated
 };
 
+// A box of the node grid: origin o and extent n (the whole grid: o = 0, n = nn).
+struct Window {
+  int o[3];
+  int n[3];
+};
+
 struct FeatArgs {
   GridDev g;
+  Window w;             // nodes whose features are written, x indexed inside the window
   const uint8_t* phase;
   const float* enorm;   // E / E_max per phase
   const uint8_t* cmask;
   float eps6[6];        // eps* xx yy zz yz xz xy, times 1000
-  float* x;             // [V][16]
+  float* x;             // [Vw][16]
 };
+
+// Increment mode (one load increment of a sphere indentation, Algorithm 2): features
+// built from the previous increments' fields, targets of the displacement correction and
+// of the contact pressure, and the guess written back (layout in include/dtt_net.h).
+struct IncArgs {
+  GridDev g;
+  Window w;              // the network's window (features, targets and outputs inside it)
+  const double* u64;     // u~ of increment k-1 (FP64 grid) ...
+  const float* uhi;      // ... or its float-float pair (mixed grid)
+  const float* ulo;
+  const double* u2;      // u~ of increment k-2 (device, [3][V]; null: zero)
+  double s_sec;          // secant factor of the increment (d^(3/2) steps)
+  double dd;             // depth increment d_k - d_(k-1) (> 0)
+  int nface;
+  const long long* node; // surface nodes
+  const double* fn_prev; // normal reactions of increment k-1 at the surface nodes
+  double center[3];      // sphere centre of increment k
+  double radius;
+  double eps[3][3];
+  float* fmax;           // device scalar: max over the surface of -fn_prev (set by launch_inc_fmax)
+  float* x;              // [Vw][16] features (base channels already written)
+};
+__host__ __device__ inline long long win_volume(const Window& w) { return (long long)w.n[0] * w.n[1] * w.n[2]; }
+int launch_inc_fmax(const IncArgs& a, cudaStream_t s);
+int launch_inc_features(const IncArgs& a, cudaStream_t s);
+// targets t[V][4] (displacement correction, pressure) and the pressure mask m[V]
+int launch_inc_targets(const IncArgs& a, const double* u_target, const double* fn_target, float* t, float* m,
+                       cudaStream_t s);
+int launch_inc_loss(const float* y, const float* t, const float* m, long long V, int CY, float wp, float* gy,
+                    double* loss, cudaStream_t s);
+// guess u = u~_(k-1) + dd (x[4..6] + y[0..2]) into u[3][V]; active[q] = y[node q][3] > thr
+int launch_inc_guess(const IncArgs& a, const float* y, int CY, float thr, double* u, uint8_t* active,
+                     cudaStream_t s);
 
 int launch_conv_fwd(const ConvArgs& a, cudaStream_t s);
 int launch_conv_bwd(const ConvArgs& a, cudaStream_t s);

@@ -12,7 +12,8 @@ from . import dtt
 NET_CIN = 16
 EXPORTS = ["dtt_net_create", "dtt_net_destroy", "dtt_net_num_params", "dtt_net_get_params", "dtt_net_set_params",
            "dtt_net_loss_grad", "dtt_net_forward", "dtt_net_features", "dtt_net_train_step", "dtt_net_predict",
-           "dtt_net_set_loss"]
+           "dtt_net_set_loss", "dtt_net_set_increment", "dtt_net_increment_features", "dtt_net_train_increment",
+           "dtt_net_predict_increment", "dtt_net_loss_grad_increment"]
 _bound = False
 
 
@@ -34,9 +35,15 @@ def _lib():
         L.dtt_net_train_step.argtypes = [P, P, P, f32, C.POINTER(C.c_double)]
         L.dtt_net_predict.argtypes = [P, P]
         L.dtt_net_set_loss.argtypes = [P, f32]
+        L.dtt_net_set_increment.argtypes = [P, f32, f32, i32, i32]
+        L.dtt_net_increment_features.argtypes = [P, P, P, P, P, P]
+        L.dtt_net_train_increment.argtypes = [P, P, P, P, P, P, P, f32, C.POINTER(C.c_double)]
+        L.dtt_net_predict_increment.argtypes = [P, P, P, P, P]
+        L.dtt_net_loss_grad_increment.argtypes = [P, i32, i32, i32, P, P, P, C.POINTER(C.c_double), P]
         for name in ("dtt_net_create", "dtt_net_get_params", "dtt_net_set_params", "dtt_net_loss_grad",
                      "dtt_net_forward", "dtt_net_features", "dtt_net_train_step", "dtt_net_predict",
-                     "dtt_net_set_loss"):
+                     "dtt_net_set_loss", "dtt_net_set_increment", "dtt_net_increment_features",
+                     "dtt_net_train_increment", "dtt_net_predict_increment", "dtt_net_loss_grad_increment"):
             getattr(L, name).restype = i32
         _bound = True
     return L
@@ -120,3 +127,54 @@ class Net:
     def predict(self, grid):
         """Writes the network's guess of u~ into the grid (solve with init=INIT_GUESS)."""
         dtt._check(_lib().dtt_net_predict(self._h, grid._h))
+
+    # ---- increment mode (include/dtt_net.h): device arrays are torch CUDA tensors, complete
+    # before the call (the library reads them on its own stream)
+    def set_increment(self, pressure_weight=1.0, active_threshold=0.05, window_lateral=0, window_depth=0):
+        dtt._check(_lib().dtt_net_set_increment(self._h, float(pressure_weight), float(active_threshold),
+                                                int(window_lateral), int(window_depth)))
+        self.window = (int(window_lateral), int(window_depth))
+
+    @staticmethod
+    def _dev(t):
+        if t is None:
+            return None
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+            raise ValueError("increment-mode arrays are contiguous CUDA tensors")
+        return C.c_void_p(t.data_ptr())
+
+    def increment_features(self, grid, u_prev2, fn_prev, depth):
+        """Features of the window (the whole grid unless set_increment gave one, the
+        contact face being the top z face)."""
+        lat, dep = getattr(self, "window", (0, 0))
+        nz, ny, nx = grid.node_shape
+        shape = (dep if 0 < dep < nz else nz, lat if 0 < lat < ny else ny, lat if 0 < lat < nx else nx)
+        x = np.zeros(shape + (NET_CIN,), np.float32)
+        d = np.ascontiguousarray(depth, dtype=np.float64)
+        dtt._check(_lib().dtt_net_increment_features(self._h, grid._h, self._dev(u_prev2), self._dev(fn_prev),
+                                                     d.ctypes.data_as(C.c_void_p), x.ctypes.data_as(C.c_void_p)))
+        return x
+
+    def train_increment(self, grid, u_prev2, fn_prev, depth, u_target, fn_target, lr):
+        d = np.ascontiguousarray(depth, dtype=np.float64)
+        loss = C.c_double()
+        dtt._check(_lib().dtt_net_train_increment(self._h, grid._h, self._dev(u_prev2), self._dev(fn_prev),
+                                                  d.ctypes.data_as(C.c_void_p), self._dev(u_target),
+                                                  self._dev(fn_target), float(lr), C.byref(loss)))
+        return loss.value
+
+    def predict_increment(self, grid, u_prev2, fn_prev, depth):
+        d = np.ascontiguousarray(depth, dtype=np.float64)
+        dtt._check(_lib().dtt_net_predict_increment(self._h, grid._h, self._dev(u_prev2), self._dev(fn_prev),
+                                                    d.ctypes.data_as(C.c_void_p)))
+
+    def loss_grad_increment(self, x, target, pmask):
+        """x: [nz, ny, nx, 16], target: [nz, ny, nx, 4], pmask: [nz, ny, nx] -> (loss, grad)."""
+        x, t, m = _f32(x), _f32(target), _f32(pmask)
+        nz, ny, nx = x.shape[:3]
+        loss = C.c_double()
+        g = np.zeros(self.num_params, np.float32)
+        dtt._check(_lib().dtt_net_loss_grad_increment(self._h, nx, ny, nz, x.ctypes.data_as(C.c_void_p),
+                                                      t.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
+                                                      C.byref(loss), g.ctypes.data_as(C.c_void_p)))
+        return loss.value, g

@@ -7,6 +7,7 @@ kernels).  Evaluation solves each held-out cell twice, from u~ = 0 and from the 
 guess with init = INIT_GUESS (which keeps the guess only if its first Eq. 5 residual is
 below the plain start's), and reports iterations, starting residuals and times.
 """
+import json
 import time
 
 import numpy as np
@@ -61,3 +62,179 @@ def evaluate(net, specs, precision=dtt.PREC_MIXED, tol=1e-6, graph_iters=16):
 
 def make_net(seed=0, channels=(16, 32, 64)):
     return Net(*channels, seed=seed)
+
+
+# ---------------------------------------------------------------------------------------
+# Increment mode: the warm start of the load increments of a sphere indentation
+# (include/dtt_net.h).  Training data are the solver's own converged increments of
+# training seeds; the network learns the correction to the secant prediction of each
+# increment and the increment's contact pressure, whose sign sets the initial contact zone.
+# ---------------------------------------------------------------------------------------
+def depths(spec):
+    """Indentation depth d_k of every increment (voxels)."""
+    I = spec["indenter"]
+    return [float(r) * float(I["radius"]) for r in I["ratios"]]
+
+
+def depth_triple(dk, k):
+    """(d_(k-2), d_(k-1), d_k), with d_(-1) = 0 (the unloaded state)."""
+    return (dk[k - 2] if k >= 2 else 0.0, dk[k - 1], dk[k])
+
+
+def solve_increments(spec, precision=dtt.PREC_MIXED, tol=1e-6, graph_iters=16, keep=True, store_dtype=None):
+    """Solves every increment of an indentation from the previous one; returns the grid,
+    the converged fields (CUDA tensors, float32 unless store_dtype says otherwise) and the
+    normal reactions of each increment (CUDA float64), and the reports."""
+    import torch
+    I = spec["indenter"]
+    g = rows.setup_grid(spec, precision)
+    g.dtt_set_indenter(I["axis"], I["face"], I["centers"][0], I["radius"])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    U, FN, reps = [], [], []
+    u = torch.empty((3,) + tuple(g.node_shape), dtype=torch.float64, device=dev)
+    for k, O in enumerate(I["centers"]):
+        g.dtt_move_indenter(O)
+        r = g.dtt_solve_step(tol, 20000, acv_mod=spec["acv_mod"], init=dtt.INIT_ZERO if k == 0 else dtt.INIT_PREVIOUS,
+                             graph_iters=graph_iters)
+        reps.append(r)
+        if keep:
+            g.dtt_get_fields(u_out=u)
+            U.append(u.to(store_dtype or torch.float32).clone())
+            FN.append(torch.from_numpy(g.dtt_get_contact()[2].copy()).to(dev))
+    torch.cuda.current_stream().synchronize()
+    return g, U, FN, reps
+
+
+def train_increments(net, data, epochs=8, lr=1e-3, seed=0, log=None):
+    """Adam over the increments k >= 1 of the training seeds, in a fresh random order each
+    epoch.  data: list of (grid, spec, U, FN) from solve_increments."""
+    import torch
+    rng = np.random.default_rng(seed)
+    items = [(i, k) for i, (_, spec, U, _) in enumerate(data) for k in range(1, len(U))]
+    hist = []
+    for ep in range(epochs):
+        rng.shuffle(items)
+        losses = []
+        for i, k in items:
+            g, spec, U, FN = data[i]
+            dk = depths(spec)
+            g.dtt_move_indenter(spec["indenter"]["centers"][k])
+            u1 = U[k - 1].double().contiguous()
+            u2 = U[k - 2].double().contiguous() if k >= 2 else None
+            ut = U[k].double().contiguous()
+            # the library works on its own streams: the conversions above (torch's stream)
+            # must be complete before it reads them
+            torch.cuda.current_stream().synchronize()
+            g.dtt_set_initial(u1)
+            losses.append(net.train_increment(g, u2, FN[k - 1], depth_triple(dk, k), ut, FN[k], lr))
+            del u1, u2, ut
+        hist.append(float(np.mean(losses)))
+        if log:
+            log(ep, hist[-1])
+        torch.cuda.empty_cache()
+    return hist
+
+
+def evaluate_increments(net, spec, tol=1e-6, graph_iters=16, ks=None):
+    """Per increment k >= 1 of a held-out seed: the plain previous-step start against the
+    network's guess (INIT_GUESS, fallback to the previous-step field), both from the same
+    field of increment k-1 (the plain run's).  Returns one dict per increment."""
+    import torch
+    g, U, FN, reps = solve_increments(spec, tol=tol, graph_iters=graph_iters, store_dtype=torch.float64)
+    I = spec["indenter"]
+    dk = depths(spec)
+    out = []
+    for k in (ks or range(1, len(U))):
+        g.dtt_move_indenter(I["centers"][k])
+        g.dtt_set_initial(U[k - 1])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net.predict_increment(g, U[k - 2] if k >= 2 else None, FN[k - 1], depth_triple(dk, k))
+        r = g.dtt_solve_step(tol, 20000, acv_mod=spec["acv_mod"], init=dtt.INIT_GUESS, graph_iters=graph_iters)
+        t_guess = time.perf_counter() - t0
+        out.append({"k": k, "plain_iters": reps[k].iterations, "plain_s": reps[k].seconds,
+                    "plain_updates": reps[k].active_set_updates, "guess_iters": r.iterations, "guess_s": t_guess,
+                    "guess_updates": r.active_set_updates, "guess_used": r.start_from_guess,
+                    "guess_r0": r.start_residual, "status": r.status})
+    g.close()
+    return out
+
+
+def save_net(net, path, meta=None):
+    import os
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    np.savez_compressed(path, params=net.get_params(), channels=np.array(net.channels),
+                        meta=np.array(json.dumps(meta or {})))
+
+
+def load_net(path, stream=None):
+    z = np.load(path)
+    c = [int(v) for v in z["channels"]]
+    net = Net(*c, seed=0, stream=stream)
+    net.set_params(z["params"])
+    meta = json.loads(str(z["meta"])) if "meta" in z else {}
+    net.set_increment(float(meta.get("pressure_weight", 1.0)), float(meta.get("active_threshold", 0.05)),
+                      int(meta.get("window_lateral", 0)), int(meta.get("window_depth", 0)))
+    net.meta = meta
+    return net
+
+
+def main(argv=None):
+    """python -m paper_2607_26082_b300.warmstart train-indent --seeds 2000:2006 [--nvox 384,384,192]
+    [--epochs 8] [--lr 1e-3] [--out paper_2607_26082_b300/weights/warmstart_indent.npz]
+    [--eval-seed 3000]"""
+    import argparse
+    import os
+    import sys
+    import torch
+    import workloads as wl
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=["train-indent"])
+    ap.add_argument("--seeds", default="2000:2006")
+    ap.add_argument("--nvox", default="384,384,192")
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--pressure-weight", type=float, default=1.0)
+    ap.add_argument("--threshold", type=float, default=0.05)
+    ap.add_argument("--window", default="128,48", help="lateral,depth node extents of the network's window "
+                                                       "(0,0: the whole grid)")
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                                                  "warmstart_indent.npz"))
+    ap.add_argument("--eval-seed", type=int, default=3000)
+    ap.add_argument("--seed", type=int, default=1, help="initial weights")
+    a = ap.parse_args(argv)
+    nv = tuple(int(v) for v in a.nvox.split(","))
+    s0, s1 = (int(v) for v in a.seeds.split(":"))
+    t0 = time.perf_counter()
+    data = []
+    for sd in range(s0, s1):
+        spec = wl.indentation_inclusions(sd, *nv, steps=20)
+        g, U, FN, reps = solve_increments(spec)
+        data.append((g, spec, U, FN))
+        print(json.dumps({"seed": sd, "iterations": sum(r.iterations for r in reps),
+                          "s": round(time.perf_counter() - t0, 1)}), flush=True)
+    net = make_net(seed=a.seed)
+    wl_, wd_ = (int(v) for v in a.window.split(","))
+    net.set_increment(a.pressure_weight, a.threshold, wl_, wd_)
+    hist = train_increments(net, data, epochs=a.epochs, lr=a.lr,
+                            log=lambda ep, l: print(json.dumps({"epoch": ep, "loss": l,
+                                                                "s": round(time.perf_counter() - t0, 1)}), flush=True))
+    for g, _, _, _ in data:
+        g.close()
+    del data
+    torch.cuda.empty_cache()
+    meta = {"seeds": a.seeds, "nvox": nv, "epochs": a.epochs, "lr": a.lr, "pressure_weight": a.pressure_weight,
+            "active_threshold": a.threshold, "window_lateral": wl_, "window_depth": wd_, "loss": hist}
+    save_net(net, a.out, meta)
+    ev = evaluate_increments(net, wl.indentation_inclusions(a.eval_seed, *nv, steps=20))
+    for e in ev:
+        print(json.dumps(e), flush=True)
+    print(json.dumps({"eval_seed": a.eval_seed, "plain_iters": sum(e["plain_iters"] for e in ev),
+                      "guess_iters": sum(e["guess_iters"] for e in ev), "plain_s": sum(e["plain_s"] for e in ev),
+                      "guess_s": sum(e["guess_s"] for e in ev), "kept": sum(e["guess_used"] for e in ev)}), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    import sys
+    sys.exit(main())

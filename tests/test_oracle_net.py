@@ -85,3 +85,51 @@ def test_features_of_a_small_cell():
     e = c["eps_star"]
     assert np.allclose(x[..., 4], 1000 * e[0, 0]) and np.allclose(x[..., 9], 1000 * e[0, 1])
     assert x[..., 10].max() == (nn[0] - 1) / c["nvox"][0] and (x[..., 13:] == 0).all()
+
+
+def test_increment_loss_backward_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    layers = _rand_layers(rng)
+    x = rng.standard_normal((3, 4, 5, 16))
+    t = rng.standard_normal((3, 4, 5, 4))
+    m = np.zeros((3, 4, 5))
+    m[-1] = 1.0                                   # the top layer is the surface
+    wp = 0.7
+    loss, grads, _ = onet.increment_loss_grad(layers, x, t, m, wp)
+    p0 = onet.pack(layers)
+    g = onet.pack(grads)
+    h = 1e-6
+    for q in np.concatenate([rng.choice(p0.size, 30, replace=False), [onet.pack(layers[:10]).size + 3]]):
+        pp, pm = p0.copy(), p0.copy()
+        pp[q] += h
+        pm[q] -= h
+        fd = (onet.increment_loss_grad(onet.unpack(pp, 16, 16, 16), x, t, m, wp)[0] -
+              onet.increment_loss_grad(onet.unpack(pm, 16, 16, 16), x, t, m, wp)[0]) / (2 * h)
+        assert abs(fd - g[q]) <= 1e-5 * max(1e-3, abs(fd)) + 1e-9, (q, fd, g[q])
+    # the pressure term sees only surface nodes: changing the target elsewhere changes nothing
+    t2 = t.copy()
+    t2[0, ..., 3] += 5.0
+    assert onet.increment_loss_grad(layers, x, t2, m, wp)[0] == loss
+
+
+def test_increment_features_closed_forms():
+    """Channels of the increment mode on a hand-made state: the secant factor of d^1.5,
+    the gap of a surface node right below the sphere, the pressure normalisation."""
+    nz, ny, nx = 3, 4, 5
+    x = np.zeros((nz, ny, nx, 16))
+    u1 = np.zeros((3, nz, ny, nx))
+    u2 = np.zeros((3, nz, ny, nx))
+    u1[2] = -0.3
+    u2[2] = -0.1
+    depth = (1.0, 2.0, 3.0)
+    s = (3.0 ** 1.5 - 2.0 ** 1.5) / (2.0 ** 1.5 - 1.0)
+    surf = [(2, 1, 2), (0, 0, 2)]
+    R = 10.0
+    center = (2.0, 1.0, 2.0 + R + 0.5)      # 0.5 above the top node (2, 1, 2) before it moves
+    f = onet.increment_features(x, u1, u2, [-2.0, -0.5], depth, surf, center, R)
+    assert np.allclose(f[..., 6], -0.2 * s)   # secant over dd = 1
+    assert np.allclose(f[..., 4:6], 0.0)
+    # node (2, 1, 2) moves by -0.3 + (-0.2 s): its gap is 0.5 + 0.3 + 0.2 s
+    assert np.isclose(f[2, 1, 2, 8], 0.5 + 0.3 + 0.2 * s)
+    assert f[2, 1, 2, 7] == 1.0 and f[2, 0, 0, 7] == 1.0 and f[1, 1, 2, 7] == 0.0
+    assert np.isclose(f[2, 1, 2, 9], 1.0) and np.isclose(f[2, 0, 0, 9], 0.25)
