@@ -56,9 +56,25 @@ L2_FLUSH_BYTES = 512 << 20
 LAUNCHES_PER_PREDICT = 34
 B_GREEN = 72
 B_RESIDUAL = 85
-# ncu DRAM bytes per launch of the Green-step kernels on this workload, keyed by the source
-# hash of the kernel file they came from; null once that source has changed
-PROFILED_TRAFFIC = {}
+# ncu DRAM bytes (read + write) of the Green step's five kernels per node and iteration,
+# from one capture of the 256x256x128 indentation (8,520,321 nodes; the traffic grows with
+# the node count), with the source hash of the kernel file they came from: reported as null
+# once that source has changed
+PROFILED_TRAFFIC = {"green": {"bytes_per_node": 1163.8e6 / 8520321, "source": "paper_2607_26082_b300/csrc/k_wfft.cu",
+                              "sha256_16": "afb402b9b95ad324"}}
+
+
+def profiled_traffic(key, nodes):
+    """DRAM bytes per iteration of a profiled kernel group on a grid of the given node count, or
+    None when its source has changed since the capture."""
+    import hashlib
+    rec = PROFILED_TRAFFIC.get(key)
+    if not rec:
+        return None
+    with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != rec["sha256_16"]:
+            return None
+    return rec["bytes_per_node"] * nodes
 
 
 def parse():
@@ -324,7 +340,7 @@ def run_ours(args, rank, world, local):
                 if hist["u2"] is None:
                     hist["u2"] = torch.empty_like(u_dev)
                 hist["u2"], hist["u1"] = hist["u1"], hist["u2"]
-            hist["fn"] = torch.from_numpy(gm.dtt_get_contact()[2].copy()).to(dev)
+            hist["fn"] = torch.from_numpy(warmstart.contact_reactions(gm)).to(dev)
             torch.cuda.current_stream().synchronize()   # the library reads it on its own stream
         return k, rep
 
@@ -462,7 +478,7 @@ def run_ours(args, rank, world, local):
         "roofline": {"bound": "hbm", "kernel_group": "Green step (forward DTT x/y, fused z pass with the Green "
                                                       "multiply, inverse DTT y/x with the increment)",
                      "achieved": green_ach, "peak": hbm, "unit": "GB/s", "frac": green_ach / hbm,
-                     "peak_source": peak_src, "traffic": PROFILED_TRAFFIC.get("green"),
+                     "peak_source": peak_src, "traffic": profiled_traffic("green", nn),
                      "alg_bytes_per_node": B_GREEN, "ms_per_iteration": 1e3 * t_green,
                      "residual_group": {"achieved": res_ach, "frac": res_ach / hbm, "alg_bytes_per_node": B_RESIDUAL,
                                         "ms_per_iteration": 1e3 * t_res},

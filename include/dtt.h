@@ -270,23 +270,30 @@ dtt_status dtt_profile_iteration(dtt_grid* grid, const dtt_solve_opts* opts, int
  *                    0 = FFT (or dense) pass, 1 = two split-TF32 tensor-core contractions
  *                    against the z DTT matrices (mixed precision, z operand <= 256
  *                    nodes; elsewhere ignored);
+ *   fft_warp:        1 (default) runs the mixed-precision Green step as five warp-register
+ *                    sweeps that each read contiguous rows and write the next sweep's rows
+ *                    transposed, where every axis is non-periodic with 2n = 32 R,
+ *                    R in {2, 3, 4, 6, 8, 12, 16, 24, 32} (fft_generic = 0, z_route = 0 only);
+ *                    0 keeps the shared-memory Stockham passes;
  *   ms_per_iteration: (dtt_autotune output) measured time of one iteration with them. */
 typedef struct {
   int32_t residual_zchunk;
   int32_t fft_generic;
   int32_t z_route;
+  int32_t fft_warp;
   double ms_per_iteration;
 } dtt_tuning;
 
 /* Times `iters` iterations of the current problem (launch by launch, CUDA events on the
- * grid's stream) for each candidate tiling -- the FFT route and the z route first, then the residual
+ * grid's stream) for each candidate tiling -- the FFT routes (warp-register sweeps,
+ * register-radix or generic Stockham) and the z route first, then the residual
  * kernel's z chunk in {built-in, 2, 4, 8, 16, 32, 64} -- keeps the fastest on the grid
  * and returns it in *best (may be NULL).  u~ and the solver rings are reset to zero
  * afterwards; call it before a solve.  iters < 1 is DTT_ERR_ARG. */
 dtt_status dtt_autotune(dtt_grid* grid, const dtt_solve_opts* opts, int32_t iters, dtt_tuning* best);
 
 /* Applies a tiling (e.g. one tuned on another grid of the same size); a zchunk outside
- * {0, 2..64}, fft_generic or z_route outside {0, 1}, or z_route 1 on a grid that cannot
+ * {0, 2..64}, fft_generic, z_route or fft_warp outside {0, 1}, or z_route 1 on a grid that cannot
  * take it (FP64, or more than 256 nodes along z) is DTT_ERR_ARG. */
 dtt_status dtt_set_tuning(dtt_grid* grid, const dtt_tuning* tuning);
 

@@ -94,17 +94,22 @@ dtt_status dtt_net_predict(dtt_net* net, dtt_grid* grid);
  *                 by its largest value f_max;
  *   channels 13-15: 0.
  * Outputs: channels 0-2 the correction c to the secant prediction, the guess being
- * u~_k = u~_(k-1) + dd (secant / dd + c); channel 3 the contact pressure over f_max, the
- * guess's initial contact zone being {pressure > threshold} (default 0.05).
+ * u~_k = u~_(k-1) + dd (secant / dd + w c), w = 1 inside the window and falling linearly
+ * to 0 over its last 8 nodes before each face that lies inside the grid; channel 3 the
+ * contact pressure over f_max.  The
+ * guess's initial contact zone is the previous increment's ({f_n < 0}, which only grows
+ * under monotone loading) together with the nodes whose predicted pressure exceeds the
+ * threshold (default 0.05).
  * Training loss: mean over nodes and channels 0-2 of (y - t)^2 plus w times the mean over
  * the surface nodes of (y_3 - t_3)^2 (w default 1), t the solver's converged increment
- * (correction form) and pressure.
+ * (correction form, clipped to [-8, 8]) and pressure (clipped to [0, 4]).
  *
  * Arguments common to the calls below: grid = a configured grid with an indenter, its u~
  * the converged field of increment k-1 and its sphere moved to increment k's centre;
  * u_prev2 = u~ of increment k-2 (device, 3 x n_nodes float64; NULL = zero); fn_prev = the
- * normal reactions of increment k-1 at the surface nodes (device, n_surface float64, the
- * order of dtt_get_contact); depth = {d_(k-2), d_(k-1), d_k} with 0 <= d_(k-2) < d_(k-1) <
+ * normal reactions of increment k-1 on its contact set and zero at the other surface nodes
+ * (device, n_surface float64, the order of dtt_get_contact, whose fn holds the free nodes'
+ * residual off the set); depth = {d_(k-2), d_(k-1), d_k} with 0 <= d_(k-2) < d_(k-1) <
  * d_k (d_(k-2) = 0 with u_prev2 = NULL for the second increment).  DTT_ERR_STATE without
  * an indenter, DTT_ERR_ARG on bad depths. */
 
@@ -122,7 +127,8 @@ dtt_status dtt_net_increment_features(dtt_net* net, dtt_grid* grid, const double
                                       const double depth[3], float* x);
 
 /* One Adam step on increment k: u_target = its converged u~ (device, 3 x n_nodes float64),
- * fn_target = its normal reactions (device, n_surface float64).  *loss before the update. */
+ * fn_target = its normal reactions on its contact set, zero elsewhere (device, n_surface
+ * float64).  *loss before the update. */
 dtt_status dtt_net_train_increment(dtt_net* net, dtt_grid* grid, const double* u_prev2, const double* fn_prev,
                                    const double depth[3], const double* u_target, const double* fn_target, float lr,
                                    double* loss);

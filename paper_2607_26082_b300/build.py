@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdtt.so")
 SOURCES = ["dtt_api.cu", "k_residual.cu", "k_residual_f32.cu", "k_transform.cu", "k_fft.cu", "k_solver.cu", "k_util.cu",
-           "dtt_net.cu", "k_net.cu", "k_tensor_z.cu"]
+           "dtt_net.cu", "k_net.cu", "k_tensor_z.cu", "k_wfft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

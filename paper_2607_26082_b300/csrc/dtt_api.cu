@@ -258,6 +258,21 @@ dtt_status build_fft_axis(dtt_grid* G, int d) {
   for (int q = 0; q < ns; ++q) f.radix[q] = rad[q];
   f.tw = G->fft_tw[d];
   f.ph = G->fft_ph[d];
+  // stage-1 twiddles of the warp-register passes (mixed path, non-periodic, L = 32 R)
+  const int R = wfft_radix(L);
+  if (G->esz == 4 && !G->g.periodic[d] && R) {
+    std::vector<float> t1(2 * (size_t)R * 32);
+    for (int k1 = 0; k1 < R; ++k1)
+      for (int l = 0; l < 32; ++l) {
+        const int m = (l * k1) % L;
+        t1[2 * (k1 * 32 + l)] = (float)std::cos(2.0 * pi * m / L);
+        t1[2 * (k1 * 32 + l) + 1] = (float)-std::sin(2.0 * pi * m / L);
+      }
+    dtt_status s2 = dalloc(&G->fft_tw1[d], t1.size() * 4);
+    if (s2 != DTT_OK) return s2;
+    CK(cudaMemcpy(G->fft_tw1[d], t1.data(), t1.size() * 4, cudaMemcpyHostToDevice));
+    f.tw1 = G->fft_tw1[d];
+  }
   return DTT_OK;
 }
 
@@ -446,6 +461,18 @@ dtt_status enqueue_green(dtt_grid* G, const T* in, void* const* in_ring, T* out,
                          const Ctrl* ctrl, int comp0, int ncomp) {
   TransformTables tt = tables(G);
   cudaStream_t s = G->stream;
+  // mixed path: five warp-register sweeps, each reading contiguous rows (k_wfft.cu)
+  if constexpr (sizeof(T) == 4) {
+    if (G->fft_warp && !tt.tz_use && !G->g.fft_generic && wfft_supported(G->g, tt)) {
+      const bool alias = (in_ring == nullptr && (const void*)in == (const void*)out);
+      T* b1 = alias ? tmp : out;
+      T* b2 = alias ? out : tmp;
+      IncrTarget it{G->u64, G->uhi, G->ulo, G->step};
+      CKL(launch_wfft_green(G->g, tt, in, in_ring, b1, b2, out, increment ? &it : nullptr, comp0, ncomp, ctrl, s,
+                            g_prof_ev ? prof_mark : nullptr));
+      return DTT_OK;
+    }
+  }
   // the isotropic medium couples the components: its Green step needs all three spectra,
   // so it takes the unfused route
   if ((tt.fft[2].use || tt.tz_use) && !G->g.ref_iso) {
@@ -779,6 +806,8 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
       }
     }
   for (int d = 0; d < 3 && s == DTT_OK; ++d) s = build_fft_axis(G, d);
+  // DTT_WFFT=0 keeps the Stockham passes (route comparison; read once, at creation)
+  if (const char* e = std::getenv("DTT_WFFT")) G->fft_warp = (e[0] == '0') ? 0 : 1;
   if (s == DTT_OK && precision == DTT_PREC_MIXED) s = build_tz(G);
   if (s == DTT_OK) {
     cudaError_t e = cudaMemcpy(G->d_Sring, G->S, 5 * sizeof(void*), cudaMemcpyHostToDevice);
@@ -842,6 +871,7 @@ void dtt_grid_destroy(dtt_grid* G) {
   for (int d = 0; d < 3; ++d) {
     dfree(G->fft_tw[d]);
     dfree(G->fft_ph[d]);
+    dfree(G->fft_tw1[d]);
   }
   free_rows(G);
   free_contact(G);
@@ -1888,10 +1918,11 @@ dtt_status reset_state(dtt_grid* G) {
   return DTT_OK;
 }
 
-dtt_status apply_tiling(dtt_grid* G, int zc, int generic, int z_route) {
+dtt_status apply_tiling(dtt_grid* G, int zc, int generic, int z_route, int warp) {
   G->g.zc_override = zc;
   G->g.fft_generic = generic;
   G->z_route = (z_route == 1 && G->tz_ok) ? 1 : 0;
+  G->fft_warp = warp ? 1 : 0;
   invalidate_graph(G);
   return ensure_partials(G);
 }
@@ -1937,29 +1968,33 @@ dtt_status dtt_autotune(dtt_grid* G, const dtt_solve_opts* opts, int32_t iters, 
   if (st != DTT_OK) return st;
   if (iters < 1) return fail(DTT_ERR_ARG, "iters must be >= 1");
   double t_best = 1e300;
-  int zc_best = 0, gen_best = 0, zr_best = 0;
-  for (int zr = 0; zr < (G->tz_ok ? 2 : 1); ++zr)
-    for (int gen = 0; gen < 2; ++gen) {
-      if ((st = apply_tiling(G, 0, gen, zr)) != DTT_OK) return st;
-      double t = 0.0;
-      if ((st = time_iterations(G, opts, iters, &t)) != DTT_OK) return st;
-      if (t < t_best) { t_best = t; gen_best = gen; zr_best = zr; }
-    }
+  int zc_best = 0, gen_best = 0, zr_best = 0, wp_best = 0;
+  // the warp-register sweeps (where the grid allows them), then the Stockham routes
+  const bool warp_ok = G->prec == DTT_PREC_MIXED && wfft_supported(G->g, tables(G));
+  for (int wp = (warp_ok ? 1 : 0); wp >= 0; --wp)
+    for (int zr = 0; zr < ((G->tz_ok && !wp) ? 2 : 1); ++zr)
+      for (int gen = 0; gen < (wp ? 1 : 2); ++gen) {
+        if ((st = apply_tiling(G, 0, gen, zr, wp)) != DTT_OK) return st;
+        double t = 0.0;
+        if ((st = time_iterations(G, opts, iters, &t)) != DTT_OK) return st;
+        if (t < t_best) { t_best = t; gen_best = gen; zr_best = zr; wp_best = wp; }
+      }
   const int zcs[6] = {2, 4, 8, 16, 32, 64};
   for (int q = 0; q < 6; ++q) {
     if (zcs[q] > 2 * G->g.nn[2]) break;
-    if ((st = apply_tiling(G, zcs[q], gen_best, zr_best)) != DTT_OK) return st;
+    if ((st = apply_tiling(G, zcs[q], gen_best, zr_best, wp_best)) != DTT_OK) return st;
     double t = 0.0;
     if ((st = time_iterations(G, opts, iters, &t)) != DTT_OK) return st;
     if (t < t_best) { t_best = t; zc_best = zcs[q]; }
   }
-  if ((st = apply_tiling(G, zc_best, gen_best, zr_best)) != DTT_OK) return st;
+  if ((st = apply_tiling(G, zc_best, gen_best, zr_best, wp_best)) != DTT_OK) return st;
   if ((st = reset_state(G)) != DTT_OK) return st;
   if ((st = check_tz(G)) != DTT_OK) return st;
   if (best) {
     best->residual_zchunk = zc_best;
     best->fft_generic = gen_best;
     best->z_route = zr_best;
+    best->fft_warp = wp_best;
     best->ms_per_iteration = t_best;
   }
   return DTT_OK;
@@ -1973,7 +2008,8 @@ dtt_status dtt_set_tuning(dtt_grid* G, const dtt_tuning* t) {
   if (t->z_route != 0 && t->z_route != 1) return fail(DTT_ERR_ARG, "z_route must be 0 or 1");
   if (t->z_route == 1 && !G->tz_ok)
     return fail(DTT_ERR_ARG, "z_route 1 needs a mixed-precision grid whose z operand has at most 256 nodes");
-  return apply_tiling(G, t->residual_zchunk, t->fft_generic, t->z_route);
+  if (t->fft_warp != 0 && t->fft_warp != 1) return fail(DTT_ERR_ARG, "fft_warp must be 0 or 1");
+  return apply_tiling(G, t->residual_zchunk, t->fft_generic, t->z_route, t->fft_warp);
 }
 
 dtt_status dtt_batch_solve(int32_t ncell, dtt_grid* const* cells, const dtt_solve_opts* opts, dtt_report* reports) {

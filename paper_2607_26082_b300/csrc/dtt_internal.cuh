@@ -169,6 +169,7 @@ struct FftAxisInfo {
   int radix[12];
   const void* tw;          // L complex twiddles e^{-2 pi i m / L} (field precision)
   const void* ph;          // 2n complex e^{-i pi j / 2n} (quarter-wave types)
+  const void* tw1;         // mixed path, L = 32 R: [R][32] float2 e^{-2 pi i l k1 / L} (warp passes)
 };
 struct FftParams {
   int axis, n, nn, L, nst;
@@ -271,6 +272,31 @@ struct IncrTarget {
   float* ulo;
   void* step;
 };
+// Warp-register passes of the mixed Green step (k_wfft.cu): one pass over rows along one
+// axis; row r of outer index o of component c starts at c NN + o in_outer + r in_row; a
+// transposed pass writes value k of that row to c NN + o out_outer + k out_k + r.
+struct WfftPass {
+  const float* in;
+  void* const* in_ring;     // first pass: the Green input is ring slot i % 4
+  float* out;
+  int len, n, nrows;        // nodes along the axis, voxels along it, rows per outer index
+  int rpt;                  // rows per CTA (even; set by the launcher)
+  long long in_outer, in_row, out_outer, out_k, NN;
+  int type[3];
+  int inverse;
+  float sc, inv_n;          // inverse scale 2/n (non-quarter types), 1/n (quarter-wave)
+  const float2* tw1;
+  const float2* ph;
+  int comp0;
+  float* uhi;               // last pass: u~ += result (float-float), step = result
+  float* ulo;
+  float* step;
+};
+int wfft_radix(int L);
+bool wfft_supported(const GridDev& g, const TransformTables& tt);
+int launch_wfft_green(const GridDev& g, const TransformTables& tt, const float* in, void* const* in_ring,
+                      float* b1, float* b2, float* out, const IncrTarget* incr, int comp0, int ncomp,
+                      const Ctrl* ctrl, cudaStream_t s, void (*mark)(int, cudaStream_t) = nullptr);
 template <typename T>
 int launch_transform_axis(const GridDev& g, const T* in, T* out, const TransformTables& tt,
                           int axis, int inverse, int ncomp_first, int ncomp, const Ctrl* ctrl,

@@ -56,6 +56,7 @@ struct dtt_grid {
   FftAxisInfo fft[3]{};
   void* fft_tw[3]{};
   void* fft_ph[3]{};
+  void* fft_tw1[3]{};          // stage-1 twiddles of the warp-register passes
   void* fwd[3][3]{};
   void* inv[3][3]{};
   double* sin2q[3][3]{};
@@ -68,6 +69,7 @@ struct dtt_grid {
   TzComp tz[3]{};
   bool tz_ok = false;          // every component's z operand fits (size <= 256)
   int z_route = 0;             // 0: FFT (or dense) z pass, 1: tensor-core contractions
+  int fft_warp = 1;            // 1: warp-register Green step where the grid allows it
   unsigned int* tz_err = nullptr;
   // isotropic reference medium (Section 3.2.3): per-axis tables of sin^2(q/2), cos^2(q/2)
   // shared by the components, and per position the components with a mode there (bit c)

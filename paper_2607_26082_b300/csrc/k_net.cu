@@ -670,7 +670,10 @@ __global__ void k_inc_targets(IncArgs a, const double* __restrict__ ut, float* _
     const long long v = win_to_grid(a, vw);
     for (int c = 0; c < 3; ++c) {
       const long long i = c * V + v;
-      t[vw * 4 + c] = (float)((ut[i] - inc_u1(a, i)) / a.dd - inc_secant(a, i));
+      // clipped: a node whose contact state flips can carry a correction far above the
+      // others' (|t| <= 0.4 elsewhere on the training seeds)
+      const double ti = (ut[i] - inc_u1(a, i)) / a.dd - inc_secant(a, i);
+      t[vw * 4 + c] = (float)fmin(8.0, fmax(-8.0, ti));
     }
     t[vw * 4 + 3] = 0.f;
     m[vw] = 0.f;
@@ -683,7 +686,9 @@ __global__ void k_inc_targets_surface(IncArgs a, const double* __restrict__ fnt,
   const long long vw = grid_to_win(a, a.node[q]);
   if (vw < 0) return;
   const float fm = *a.fmax;
-  t[vw * 4 + 3] = fm > 0.f ? (float)(-fnt[q]) / fm : 0.f;
+  // pressure over the previous increment's largest, clipped to [0, 4] (it grows by a few
+  // per cent per increment; a spike at one node would otherwise dominate the loss)
+  t[vw * 4 + 3] = fm > 0.f ? fminf(4.f, fmaxf(0.f, (float)(-fnt[q]) / fm)) : 0.f;
   m[vw] = 1.f;
 }
 
@@ -719,24 +724,42 @@ __global__ void k_inc_loss(const float* __restrict__ y, const float* __restrict_
   }
 }
 
-// every node: u = u~_(k-1) + dd (secant + correction), the correction 0 outside the window
+// Weight of the correction at window node vw: 1 inside, falling linearly to 0 over the
+// last WIN_TAPER nodes before each window face that lies inside the grid (the contact face
+// and the grid's own faces keep 1), so that the guess has no jump where the correction
+// ends.
+constexpr int WIN_TAPER = 8;
+__device__ __forceinline__ double win_taper(const IncArgs& a, long long vw) {
+  const int idx[3] = {(int)(vw % a.w.n[0]), (int)((vw / a.w.n[0]) % a.w.n[1]), (int)(vw / ((long long)a.w.n[0] * a.w.n[1]))};
+  double t = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    const int lo = a.w.o[d], hi = a.w.o[d] + a.w.n[d];   // window [lo, hi) along d
+    if (lo > 0) t = fmin(t, (idx[d] + 1) / (double)(WIN_TAPER + 1));
+    if (hi < a.g.nn[d]) t = fmin(t, (a.w.n[d] - idx[d]) / (double)(WIN_TAPER + 1));
+  }
+  return t;
+}
+
+// every node: u = u~_(k-1) + dd (secant + tapered correction), the correction 0 outside
+// the window
 __global__ void k_inc_guess(IncArgs a, const float* __restrict__ y, int CY, double* __restrict__ u) {
   const long long V = a.g.nnodes;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * V; i += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(i / V);
     const long long v = i - c * V;
     const long long vw = grid_to_win(a, v);
-    const double corr = vw >= 0 ? (double)y[vw * CY + c] : 0.0;
+    const double corr = vw >= 0 ? win_taper(a, vw) * (double)y[vw * CY + c] : 0.0;
     u[i] = inc_u1(a, i) + a.dd * (inc_secant(a, i) + corr);
   }
 }
-// surface nodes: in the initial zone where the predicted pressure exceeds thr (none
-// outside the window)
+// surface nodes: in the initial zone when they carried pressure at the previous increment
+// (fn_prev < 0: under monotone loading the zone grows) or where the predicted pressure
+// exceeds thr (inside the window)
 __global__ void k_inc_active(IncArgs a, const float* __restrict__ y, int CY, float thr, uint8_t* __restrict__ act) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.nface) return;
   const long long vw = grid_to_win(a, a.node[q]);
-  act[q] = (vw >= 0 && y[vw * CY + 3] > thr) ? 1 : 0;
+  act[q] = (a.fn_prev[q] < 0.0 || (vw >= 0 && y[vw * CY + 3] > thr)) ? 1 : 0;
 }
 
 int launch_inc_fmax(const IncArgs& a, cudaStream_t s) {

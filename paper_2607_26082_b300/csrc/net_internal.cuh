@@ -77,7 +77,8 @@ int launch_inc_targets(const IncArgs& a, const double* u_target, const double* f
                        cudaStream_t s);
 int launch_inc_loss(const float* y, const float* t, const float* m, long long V, int CY, float wp, float* gy,
                     double* loss, cudaStream_t s);
-// guess u = u~_(k-1) + dd (x[4..6] + y[0..2]) into u[3][V]; active[q] = y[node q][3] > thr
+// guess u = u~_(k-1) + dd (x[4..6] + y[0..2]) into u[3][V]; active[q] = fn_prev[q] < 0 or
+// y[node q][3] > thr
 int launch_inc_guess(const IncArgs& a, const float* y, int CY, float thr, double* u, uint8_t* active,
                      cudaStream_t s);
 

@@ -46,7 +46,7 @@ class Report(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("residual_zchunk", C.c_int32), ("fft_generic", C.c_int32), ("z_route", C.c_int32),
-                ("ms_per_iteration", C.c_double)]
+                ("fft_warp", C.c_int32), ("ms_per_iteration", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -318,7 +318,8 @@ class Grid:
     def dtt_set_tuning(self, tuning):
         t = tuning if isinstance(tuning, Tuning) else Tuning(int(tuning["residual_zchunk"]),
                                                                  int(tuning["fft_generic"]),
-                                                                 int(tuning.get("z_route", 0)), 0.0)
+                                                                 int(tuning.get("z_route", 0)),
+                                                                 int(tuning.get("fft_warp", 1)), 0.0)
         _check(lib().dtt_set_tuning(self._h, C.byref(t)))
 
     def dtt_profile_iteration(self, iters, acv_mod=3, acv_on=ACV_P):

@@ -200,8 +200,8 @@ def main(argv=None):
     tuning = None
     if a.tune:
         t = g.dtt_autotune(iters=4, acv_mod=a.acv_mod or spec["acv_mod"])
-        tuning = {"residual_zchunk": t.residual_zchunk, "fft_generic": t.fft_generic,
-                  "ms_per_iteration": t.ms_per_iteration}
+        tuning = {"residual_zchunk": t.residual_zchunk, "fft_generic": t.fft_generic, "z_route": t.z_route,
+                  "fft_warp": t.fft_warp, "ms_per_iteration": t.ms_per_iteration}
     for s in range(nsteps):
         if ind:
             g.dtt_move_indenter(ind["centers"][s])

@@ -81,6 +81,14 @@ def depth_triple(dk, k):
     return (dk[k - 2] if k >= 2 else 0.0, dk[k - 1], dk[k])
 
 
+def contact_reactions(g):
+    """Normal reactions of the last solve on its contact set, zero elsewhere (the library
+    reports f_n = -W h^3 (p . n) at every surface node; off the set that is the residual of
+    a free node, of either sign)."""
+    act, _, fn, _ = g.dtt_get_contact()
+    return np.where(act.astype(bool), fn, 0.0)
+
+
 def solve_increments(spec, precision=dtt.PREC_MIXED, tol=1e-6, graph_iters=16, keep=True, store_dtype=None):
     """Solves every increment of an indentation from the previous one; returns the grid,
     the converged fields (CUDA tensors, float32 unless store_dtype says otherwise) and the
@@ -100,20 +108,26 @@ def solve_increments(spec, precision=dtt.PREC_MIXED, tol=1e-6, graph_iters=16, k
         if keep:
             g.dtt_get_fields(u_out=u)
             U.append(u.to(store_dtype or torch.float32).clone())
-            FN.append(torch.from_numpy(g.dtt_get_contact()[2].copy()).to(dev))
+            FN.append(torch.from_numpy(contact_reactions(g)).to(dev))
     torch.cuda.current_stream().synchronize()
     return g, U, FN, reps
 
 
-def train_increments(net, data, epochs=8, lr=1e-3, seed=0, log=None):
-    """Adam over the increments k >= 1 of the training seeds, in a fresh random order each
-    epoch.  data: list of (grid, spec, U, FN) from solve_increments."""
+def train_increments(net, data, epochs=8, lr=1e-3, seed=0, log=None, k_first=2, last=None):
+    """Adam over the increments k >= k_first of the training seeds, in a fresh random order
+    each epoch, the step size halved every quarter of the epochs.  data: list of (grid,
+    spec, U, FN) from solve_increments.  The second increment (k = 1) extrapolates from the
+    unloaded state and its correction targets are an order of magnitude larger than the
+    others'; by default it is left out.  Returns the median loss per epoch (a few
+    increments whose contact zone jumps carry losses far above the rest); `last`, a dict,
+    receives the last epoch's loss per (seed index, k)."""
     import torch
     rng = np.random.default_rng(seed)
-    items = [(i, k) for i, (_, spec, U, _) in enumerate(data) for k in range(1, len(U))]
+    items = [(i, k) for i, (_, spec, U, _) in enumerate(data) for k in range(k_first, len(U))]
     hist = []
     for ep in range(epochs):
         rng.shuffle(items)
+        lr_ep = lr * 0.5 ** (4 * ep // max(epochs, 1))
         losses = []
         for i, k in items:
             g, spec, U, FN = data[i]
@@ -126,19 +140,33 @@ def train_increments(net, data, epochs=8, lr=1e-3, seed=0, log=None):
             # must be complete before it reads them
             torch.cuda.current_stream().synchronize()
             g.dtt_set_initial(u1)
-            losses.append(net.train_increment(g, u2, FN[k - 1], depth_triple(dk, k), ut, FN[k], lr))
+            losses.append(net.train_increment(g, u2, FN[k - 1], depth_triple(dk, k), ut, FN[k], lr_ep))
+            if last is not None and ep == epochs - 1:
+                last[(i, k)] = losses[-1]
             del u1, u2, ut
-        hist.append(float(np.mean(losses)))
+        hist.append(float(np.median(losses)))
         if log:
             log(ep, hist[-1])
         torch.cuda.empty_cache()
     return hist
 
 
+def secant_start(U, FN, dk, k):
+    """The start without the network: the secant prediction of increment k (the step of
+    the previous increment scaled like the Hertz force, d^(3/2)) and the previous
+    increment's contact zone {f_n < 0}."""
+    import torch
+    d2, d1, d0 = depth_triple(dk, k)
+    s = (d0 ** 1.5 - d1 ** 1.5) / (d1 ** 1.5 - d2 ** 1.5)
+    u2 = U[k - 2] if k >= 2 else torch.zeros_like(U[k - 1])
+    return U[k - 1] + s * (U[k - 1] - u2), (FN[k - 1] < 0).to(torch.uint8)
+
+
 def evaluate_increments(net, spec, tol=1e-6, graph_iters=16, ks=None):
-    """Per increment k >= 1 of a held-out seed: the plain previous-step start against the
-    network's guess (INIT_GUESS, fallback to the previous-step field), both from the same
-    field of increment k-1 (the plain run's).  Returns one dict per increment."""
+    """Per increment k >= 1 of a held-out seed, three starts from the same field of
+    increment k-1 (the plain run's): the plain previous-step start of Algorithm 2, the
+    secant start without the network (secant_start), and the network's guess (INIT_GUESS,
+    falling back to the previous-step field).  Returns one dict per increment."""
     import torch
     g, U, FN, reps = solve_increments(spec, tol=tol, graph_iters=graph_iters, store_dtype=torch.float64)
     I = spec["indenter"]
@@ -152,10 +180,19 @@ def evaluate_increments(net, spec, tol=1e-6, graph_iters=16, ks=None):
         net.predict_increment(g, U[k - 2] if k >= 2 else None, FN[k - 1], depth_triple(dk, k))
         r = g.dtt_solve_step(tol, 20000, acv_mod=spec["acv_mod"], init=dtt.INIT_GUESS, graph_iters=graph_iters)
         t_guess = time.perf_counter() - t0
+        us, act = secant_start(U, FN, dk, k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.dtt_set_initial(us)
+        g.dtt_set_initial_contact(act)
+        rs = g.dtt_solve_step(tol, 20000, acv_mod=spec["acv_mod"], init=dtt.INIT_PREVIOUS, graph_iters=graph_iters)
+        t_sec = time.perf_counter() - t0
+        del us, act
         out.append({"k": k, "plain_iters": reps[k].iterations, "plain_s": reps[k].seconds,
                     "plain_updates": reps[k].active_set_updates, "guess_iters": r.iterations, "guess_s": t_guess,
                     "guess_updates": r.active_set_updates, "guess_used": r.start_from_guess,
-                    "guess_r0": r.start_residual, "status": r.status})
+                    "guess_r0": r.start_residual, "status": r.status, "secant_iters": rs.iterations,
+                    "secant_s": t_sec, "secant_status": rs.status})
     g.close()
     return out
 
@@ -181,7 +218,7 @@ def load_net(path, stream=None):
 
 def main(argv=None):
     """python -m paper_2607_26082_b300.warmstart train-indent --seeds 2000:2006 [--nvox 384,384,192]
-    [--epochs 8] [--lr 1e-3] [--out paper_2607_26082_b300/weights/warmstart_indent.npz]
+    [--epochs 60] [--lr 1e-3] [--out paper_2607_26082_b300/weights/warmstart_indent.npz]
     [--eval-seed 3000]"""
     import argparse
     import os
@@ -192,7 +229,7 @@ def main(argv=None):
     ap.add_argument("cmd", choices=["train-indent"])
     ap.add_argument("--seeds", default="2000:2006")
     ap.add_argument("--nvox", default="384,384,192")
-    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--pressure-weight", type=float, default=1.0)
     ap.add_argument("--threshold", type=float, default=0.05)
@@ -216,9 +253,12 @@ def main(argv=None):
     net = make_net(seed=a.seed)
     wl_, wd_ = (int(v) for v in a.window.split(","))
     net.set_increment(a.pressure_weight, a.threshold, wl_, wd_)
-    hist = train_increments(net, data, epochs=a.epochs, lr=a.lr,
-                            log=lambda ep, l: print(json.dumps({"epoch": ep, "loss": l,
+    last = {}
+    hist = train_increments(net, data, epochs=a.epochs, lr=a.lr, last=last,
+                            log=lambda ep, l: print(json.dumps({"epoch": ep, "median_loss": l,
                                                                 "s": round(time.perf_counter() - t0, 1)}), flush=True))
+    worst = sorted(last.items(), key=lambda kv: -kv[1])[:5]
+    print(json.dumps({"largest_last_epoch_losses": [[s0 + i, k, v] for (i, k), v in worst]}), flush=True)
     for g, _, _, _ in data:
         g.close()
     del data
@@ -230,7 +270,9 @@ def main(argv=None):
     for e in ev:
         print(json.dumps(e), flush=True)
     print(json.dumps({"eval_seed": a.eval_seed, "plain_iters": sum(e["plain_iters"] for e in ev),
+                      "secant_iters": sum(e["secant_iters"] for e in ev),
                       "guess_iters": sum(e["guess_iters"] for e in ev), "plain_s": sum(e["plain_s"] for e in ev),
+                      "secant_s": sum(e["secant_s"] for e in ev),
                       "guess_s": sum(e["guess_s"] for e in ev), "kept": sum(e["guess_used"] for e in ev)}), flush=True)
     return 0
 

@@ -138,16 +138,21 @@ def test_rejected_guess_reproduces_the_previous_increment_start():
 
 
 def test_trained_network_gains_on_a_held_out_seed():
-    """The committed network (trained on seeds 2000.. of the 384 x 384 x 192 indentation
-    with inclusions) on the held-out seed 3000: starting every increment k >= 1 from its
-    guess (with the fallback rule) takes strictly fewer iterations in total than the
-    previous-increment start from the same fields."""
+    """The committed network (trained on seeds 2000-2005 of the 384 x 384 x 192 indentation
+    with inclusions; its contact-zone threshold chosen on seed 3000) on the held-out seed
+    3001, every increment k >= 1 started three ways from the same field of increment k-1:
+    the plain previous-increment start of Algorithm 2, the secant start without the
+    network (Hertz-scaled secant, previous contact zone), and the network's guess with the
+    fallback rule.  The learned start takes at most 80 % of the plain start's iterations and
+    fewer than the secant start's."""
     assert os.path.exists(WEIGHTS), "trained warm-start weights missing"
     net = warmstart.load_net(WEIGHTS)
-    spec = wl.indentation_inclusions(3000, 384, 384, 192, steps=20)
+    spec = wl.indentation_inclusions(3001, 384, 384, 192, steps=20)
     ev = warmstart.evaluate_increments(net, spec)
     plain = sum(e["plain_iters"] for e in ev)
+    secant = sum(e["secant_iters"] for e in ev)
     guess = sum(e["guess_iters"] for e in ev)
-    assert all(e["status"] == dtt.OK for e in ev)
-    assert guess < plain, (guess, plain)
+    assert all(e["status"] == dtt.OK and e["secant_status"] == dtt.OK for e in ev)
+    assert guess <= 0.8 * plain, (guess, secant, plain)
+    assert guess < secant, (guess, secant, plain)
     net.close()
