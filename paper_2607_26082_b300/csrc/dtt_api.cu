@@ -321,20 +321,75 @@ double host_ustar(const dtt_grid* G, int c, long long n) {
   return G->eps[c][0] * X[0] + G->eps[c][1] * X[1] + G->eps[c][2] * X[2];
 }
 
+// Per xy tile of the mixed residual kernel, the z range of the nodes where the projections
+// correct u~ (row DOFs and contact-face nodes) and whose correction reaches the tile's
+// nodes through A0's one-node stencil: a node at (i, j, k) marks the tiles whose node halo
+// (one node around the owned block) contains (i, j), with k; a periodic axis wraps.
+dtt_status build_tile_z(dtt_grid* G, const std::vector<long long>& marked) {
+  const int tx = residual_f32_tile(0), ty = residual_f32_tile(1);
+  const int nnx = G->g.nn[0], nny = G->g.nn[1], nnz = G->g.nn[2];
+  const int ntx = (nnx + tx - 1) / tx, nty = (nny + ty - 1) / ty;
+  std::vector<int2> t((size_t)ntx * nty, make_int2(INT32_MAX, INT32_MIN));
+  for (long long n : marked) {
+    const int i = (int)(n % nnx), j = (int)((n / nnx) % nny), k = (int)(n / ((long long)nnx * nny));
+    int zlo = k, zhi = k;
+    if (G->g.periodic[2] && (k == 0 || k == nnz - 1)) {
+      zlo = -1;
+      zhi = nnz;
+    }
+    for (int di = -1; di <= 1; ++di) {
+      int ii = i + di;
+      if (G->g.periodic[0]) ii = (ii + nnx) % nnx;
+      if (ii < 0 || ii >= nnx) continue;
+      for (int dj = -1; dj <= 1; ++dj) {
+        int jj = j + dj;
+        if (G->g.periodic[1]) jj = (jj + nny) % nny;
+        if (jj < 0 || jj >= nny) continue;
+        int2& r = t[(size_t)(jj / ty) * ntx + ii / tx];
+        r.x = std::min(r.x, zlo);
+        r.y = std::max(r.y, zhi);
+      }
+    }
+  }
+  if (G->tile_cap < (int)t.size()) {
+    dfree(G->d_tile_z);
+    G->tile_cap = 0;
+    dtt_status s = dalloc(&G->d_tile_z, t.size() * sizeof(int2));
+    if (s != DTT_OK) return s;
+    G->tile_cap = (int)t.size();
+  }
+  CK(cudaMemcpy(G->d_tile_z, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  return DTT_OK;
+}
+
 dtt_status rebuild_cmask(dtt_grid* G) {
   std::vector<uint8_t> m((size_t)G->NN, 0);
+  std::vector<long long> marked;
   for (size_t e = 0; e < G->h_dof.size(); ++e) {
     long long d = G->h_dof[e];
     int c = (int)(d / G->NN);
     m[(size_t)(d - c * G->NN)] |= (uint8_t)(1u << c);
+    marked.push_back(d - c * G->NN);
   }
   if (G->contact) {
     std::vector<long long> nodes(G->nface);
     CK(cudaMemcpy(nodes.data(), G->d_face, sizeof(long long) * G->nface, cudaMemcpyDeviceToHost));
-    for (long long n : nodes) m[(size_t)n] |= 7u;
+    for (long long n : nodes) {
+      m[(size_t)n] |= 7u;
+      marked.push_back(n);
+    }
   }
   CK(cudaMemcpy(G->cmask, m.data(), (size_t)G->NN, cudaMemcpyHostToDevice));
-  return DTT_OK;
+  return build_tile_z(G, marked);
+}
+
+// Exact residual mode of the mixed path (ResidualArgs::exact): valid when the Green step
+// inverts the Paux A0 on every mode, i.e. no component has null modes.
+bool exact_residual(const dtt_grid* G) {
+  if (G->prec != DTT_PREC_MIXED || G->g.ref_iso || !G->exact_ok || !G->d_tile_z) return false;
+  for (int c = 0; c < 3; ++c)
+    if (comp_has_null(G, c)) return false;
+  return true;
 }
 
 int res_blocks(const dtt_grid* G) {
@@ -386,7 +441,7 @@ RowsDev rows_dev(dtt_grid* G) {
 }
 
 ContactArgs contact_args(dtt_grid* G, double* cont_part) {
-  ContactArgs a;
+  ContactArgs a{};
   a.g = G->g;
   a.c.nnodes_face = G->nface;
   a.c.node = G->d_face;
@@ -458,7 +513,7 @@ inline void prof_mark(int k, cudaStream_t s) {
 // takes it too, the increment is fused into the inverse x pass.
 template <typename T>
 dtt_status enqueue_green(dtt_grid* G, const T* in, void* const* in_ring, T* out, T* tmp, bool increment,
-                         const Ctrl* ctrl, int comp0, int ncomp) {
+                         const Ctrl* ctrl, int comp0, int ncomp, bool no_step = false) {
   TransformTables tt = tables(G);
   cudaStream_t s = G->stream;
   // mixed path: five warp-register sweeps, each reading contiguous rows (k_wfft.cu)
@@ -467,7 +522,7 @@ dtt_status enqueue_green(dtt_grid* G, const T* in, void* const* in_ring, T* out,
       const bool alias = (in_ring == nullptr && (const void*)in == (const void*)out);
       T* b1 = alias ? tmp : out;
       T* b2 = alias ? out : tmp;
-      IncrTarget it{G->u64, G->uhi, G->ulo, G->step};
+      IncrTarget it{G->u64, G->uhi, G->ulo, no_step ? nullptr : G->step};
       CKL(launch_wfft_green(G->g, tt, in, in_ring, b1, b2, out, increment ? &it : nullptr, comp0, ncomp, ctrl, s,
                             g_prof_ev ? prof_mark : nullptr));
       return DTT_OK;
@@ -486,7 +541,7 @@ dtt_status enqueue_green(dtt_grid* G, const T* in, void* const* in_ring, T* out,
     prof_mark(5, s);
     CKL(launch_transform_axis<T>(G->g, b1, b2, tt, 1, 1, comp0, ncomp, ctrl, s));
     if (increment && tt.fft[0].use) {
-      IncrTarget it{G->u64, G->uhi, G->ulo, G->step};
+      IncrTarget it{G->u64, G->uhi, G->ulo, no_step ? nullptr : G->step};
       CKL(launch_transform_axis<T>(G->g, b2, b1, tt, 0, 1, comp0, ncomp, ctrl, s, nullptr, &it));
       prof_mark(6, s);
       return DTT_OK;
@@ -494,7 +549,7 @@ dtt_status enqueue_green(dtt_grid* G, const T* in, void* const* in_ring, T* out,
     CKL(launch_transform_axis<T>(G->g, b2, b1, tt, 0, 1, comp0, ncomp, ctrl, s));
     prof_mark(6, s);
     if (increment) {
-      CKL(launch_add_increment<T>(G->g, b1, G->u64, G->uhi, G->ulo, (T*)G->step, ctrl, s));
+      CKL(launch_add_increment<T>(G->g, b1, G->u64, G->uhi, G->ulo, no_step ? nullptr : (T*)G->step, ctrl, s));
     } else if (b1 != out) {
       CK(cudaMemcpyAsync(out, b1, (size_t)3 * G->NN * sizeof(T), cudaMemcpyDeviceToDevice, s));
     }
@@ -511,7 +566,7 @@ dtt_status enqueue_green(dtt_grid* G, const T* in, void* const* in_ring, T* out,
   CKL(launch_transform_axis<T>(G->g, out, tmp, tt, 1, 1, comp0, ncomp, ctrl, s));
   CKL(launch_transform_axis<T>(G->g, tmp, out, tt, 0, 1, comp0, ncomp, ctrl, s));
   prof_mark(6, s);
-  if (increment) CKL(launch_add_increment<T>(G->g, out, G->u64, G->uhi, G->ulo, (T*)G->step, ctrl, s));
+  if (increment) CKL(launch_add_increment<T>(G->g, out, G->u64, G->uhi, G->ulo, no_step ? nullptr : (T*)G->step, ctrl, s));
   return DTT_OK;
 }
 
@@ -548,6 +603,9 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
   ra.mode = diff ? 1 : 2;
   ra.pout = G->gbuf;
   ra.dfield = G->step;
+  const bool exact = sizeof(T) == 4 && diff && exact_residual(G);
+  ra.exact = exact ? 1 : 0;
+  ra.tile_z = G->d_tile_z;
   for (int k = 0; k < 4; ++k) {
     ra.pring[k] = G->S[k];
     ra.gring[k] = G->Gr[k];
@@ -560,8 +618,10 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
   const int rm = diff ? 1 : 0;
   const int fused = (diff && sizeof(T) == 4) ? 1 : 0;   // the FP32 residual kernel fuses the Gram row
   if (G->nrows > 0)
-    CKL(launch_proj_P_rows<T>(G->g, rows_dev(G), (T*)G->gbuf, G->d_Sring, G->d_Rring, rm, fused, pr.proj, ctrl, s));
+    CKL(launch_proj_P_rows<T>(G->g, rows_dev(G), (T*)G->gbuf, G->d_Sring, G->d_Rring, rm, fused, pr.proj, ctrl, s,
+                              exact ? (T*)G->step : nullptr));
   ContactArgs ca = contact_args(G, pr.cont);
+  ca.step_clear = exact ? G->step : nullptr;
   if (G->contact) CKL(launch_contact_eval<T>(ca, (T*)G->gbuf, G->d_Sring, G->d_Rring, rm, fused, s));
   // residual control and (no contact, Gram row fused into the residual and projection
   // kernels) the Anderson solve in one launch
@@ -589,7 +649,7 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
     CKL(launch_acv_green_input<T>(G->g, G->d_Sring, G->d_Gring, G->d_Rring, ctrl, s));
   }
   prof_mark(3, s);
-  dtt_status st = diff ? enqueue_green<T>(G, nullptr, G->d_Gring, (T*)G->spec2, (T*)G->spec, true, ctrl, 0, 3)
+  dtt_status st = diff ? enqueue_green<T>(G, nullptr, G->d_Gring, (T*)G->spec2, (T*)G->spec, true, ctrl, 0, 3, exact)
                        : enqueue_green<T>(G, (const T*)G->gbuf, nullptr, (T*)G->spec2, (T*)G->spec, true, ctrl, 0, 3);
   if (st != DTT_OK) return st;
   prof_mark(7, s);
@@ -806,14 +866,17 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
       }
     }
   for (int d = 0; d < 3 && s == DTT_OK; ++d) s = build_fft_axis(G, d);
-  // DTT_WFFT=0 keeps the Stockham passes (route comparison; read once, at creation)
+  // DTT_WFFT=0 keeps the Stockham passes, DTT_EXACT_R=0 the residual's A0 Delta form
+  // (route comparisons; read once, at creation)
   if (const char* e = std::getenv("DTT_WFFT")) G->fft_warp = (e[0] == '0') ? 0 : 1;
+  if (const char* e = std::getenv("DTT_EXACT_R")) G->exact_ok = (e[0] == '0') ? 0 : 1;
   if (s == DTT_OK && precision == DTT_PREC_MIXED) s = build_tz(G);
   if (s == DTT_OK) {
     cudaError_t e = cudaMemcpy(G->d_Sring, G->S, 5 * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(G->d_Rring, G->R, 4 * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(G->d_Gring, G->Gr, 4 * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(G->cmask, 0, (size_t)G->NN);
+    if (e == cudaSuccess && s == DTT_OK) s = build_tile_z(G, std::vector<long long>());
     if (e == cudaSuccess) e = G->u64 ? cudaMemset(G->u64, 0, n3 * 8) : cudaMemset(G->uhi, 0, n3 * 4);
     if (e == cudaSuccess && G->ulo) e = cudaMemset(G->ulo, 0, n3 * 4);
     if (e != cudaSuccess) s = fail(DTT_ERR_CUDA, std::string("set-up copy: ") + cudaGetErrorString(e));
@@ -872,6 +935,9 @@ void dtt_grid_destroy(dtt_grid* G) {
     dfree(G->fft_tw[d]);
     dfree(G->fft_ph[d]);
     dfree(G->fft_tw1[d]);
+  }
+  {
+    dfree(G->d_tile_z);
   }
   free_rows(G);
   free_contact(G);

@@ -136,7 +136,15 @@ struct ResidualArgs {
   int mode;               // 0: p and p~ = p + A0 u~ ; 1: Anderson difference form ; 2: p only
   void* xout;             // mode 0: p~ (may be null)
   void* pout;             // modes 0, 2: p (may be null)
-  const void* dfield;     // mode 1: Delta = last step of u~ (T)
+  const void* dfield;     // mode 1: Delta = last step of u~ (T); with `exact`, only the
+                          // projections' correction of the last step
+  // exact residual mode (mixed path, no null modes): the Green step inverts A0 exactly, so
+  // R_{i-1} = p_i - g_{i-1} + A0 Delta_{i-1} = p_i + A0 c_{i-1} with c the projections'
+  // correction (dfield); A0 c is formed only in CTAs whose node halo meets a row DOF or a
+  // contact-face node: tile_z[ty * ntx + tx] = {zmin, zmax} of such nodes for the CTA's
+  // xy tile (zmin > zmax: none)
+  int exact;
+  const int2* tile_z;
   void* pring[4];         // mode 1: p ring (slot i % 4)
   void* gring[4];         // mode 1: Green-input ring (g_{i-1} read from slot (i-1) % 4)
   void* rring[4];         // mode 1: Anderson residual ring (R_{i-1} into slot (i-1) % 4)
@@ -157,6 +165,7 @@ int residual_blocks(const GridDev& g);
 int residual_zchunk(const GridDev& g);
 int launch_residual_f32(const ResidualArgs& a, cudaStream_t s);
 int residual_f32_blocks(const GridDev& g);
+int residual_f32_tile(int axis);   // node tile of the mixed residual kernel along x (0) and y (1)
 template <typename T> int residual_nblocks(const GridDev& g) {
   return sizeof(T) == 4 ? residual_f32_blocks(g) : residual_blocks(g);
 }
@@ -288,7 +297,7 @@ struct WfftPass {
   const float2* tw1;
   const float2* ph;
   int comp0;
-  float* uhi;               // last pass: u~ += result (float-float), step = result
+  float* uhi;               // last pass: u~ += result (float-float), step = result (if step)
   float* ulo;
   float* step;
 };
@@ -330,7 +339,7 @@ constexpr int CONT_STRIDE = 8;   // [p^2, n_vgap, n_vreact, mismatches, Gram 0..
 template <typename T>
 int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p_direct, void* const* pring,
                        void* const* rring, int ring_mode, int gram, double* partials, const Ctrl* ctrl,
-                       cudaStream_t s);
+                       cudaStream_t s, T* step_clear = nullptr);
 template <typename T>
 int launch_proj_U_rows(const GridDev& g, const RowsDev& r, double* u64, float* uhi, float* ulo,
                        T* step, const Ctrl* ctrl, cudaStream_t s);
@@ -349,6 +358,7 @@ struct ContactArgs {
   double eps[3][3];
   const Ctrl* ctrl;
   double* partials;   // 3 per block: p^2, n_vgap, n_vreact (+ mismatches in [3])
+  void* step_clear;   // exact residual mode: the step field, cleared at the face nodes (T)
 };
 template <typename T>
 int launch_contact_eval(const ContactArgs& a, T* p_direct, void* const* pring, void* const* rring,

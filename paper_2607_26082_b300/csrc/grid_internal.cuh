@@ -70,6 +70,9 @@ struct dtt_grid {
   bool tz_ok = false;          // every component's z operand fits (size <= 256)
   int z_route = 0;             // 0: FFT (or dense) z pass, 1: tensor-core contractions
   int fft_warp = 1;            // 1: warp-register Green step where the grid allows it
+  int exact_ok = 1;            // 0 (DTT_EXACT_R=0): keep R = p - g + A0 Delta in the mixed path
+  int2* d_tile_z = nullptr;    // per xy tile of the mixed residual kernel: z range of marked nodes
+  int tile_cap = 0;
   unsigned int* tz_err = nullptr;
   // isotropic reference medium (Section 3.2.3): per-axis tables of sin^2(q/2), cos^2(q/2)
   // shared by the components, and per position the components with a mode there (bit c)

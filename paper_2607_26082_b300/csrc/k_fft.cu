@@ -266,7 +266,7 @@ __device__ __forceinline__ void add_to_u(long long e, T val, const FftParams& p)
     p.uhi[e] = h;
     p.ulo[e] = l;
   }
-  ((T*)p.step)[e] = val;
+  if (p.step) ((T*)p.step)[e] = val;
 }
 
 // Shared-memory layout of one CTA: two buffers of PB sequences of length L, then the L

@@ -120,6 +120,7 @@ k_residual_f32(ResidualArgs a) {
   const float* Rk[4] = {nullptr, nullptr, nullptr, nullptr};
   int rslot = -1;
   bool tau_on = true, tau_from_delta = false;
+  int tz_lo = -(1 << 29), tz_hi = 1 << 29;   // node planes where the flux's field can be non-zero
   if (a.mode == 0) {
     xo = (float*)a.xout;
   } else if (a.mode == 1) {
@@ -133,6 +134,18 @@ k_residual_f32(ResidualArgs a) {
       tau_from_delta = true;
       #pragma unroll
       for (int q = 0; q < 4; ++q) Rk[q] = (const float*)a.rring[q];
+      if (a.exact) {
+        // R_{i-1} = p_i + A0 c_{i-1}: g_{i-1} is not needed, and A0 c vanishes unless the
+        // CTA's nodes or their neighbours carry a correction; c lives on node planes
+        // [zlo, zhi] of this tile, so only voxel layers zlo - 1 .. zhi carry its flux
+        gprev = nullptr;
+        const int2 zr = a.tile_z[blockIdx.y * gridDim.x + blockIdx.x];
+        const int z1c = min((int)blockIdx.z * a.zchunk + a.zchunk, a.g.nn[2]);
+        tau_on = zr.x <= zr.y && zr.y >= (int)blockIdx.z * a.zchunk - 1 && zr.x <= z1c;
+        if (!tau_on) dfield = nullptr;
+        tz_lo = zr.x;
+        tz_hi = zr.y;
+      }
     } else {
       tau_on = false;
     }
@@ -165,6 +178,7 @@ k_residual_f32(ResidualArgs a) {
     const int slot = slot_of(kk);
     const int kw = wrapi(kk, nnz, g.periodic[2]);
     const int vz = wrapi(kk, g.nvox[2], g.periodic[2]);
+    const bool dplane = dfield && kk >= tz_lo - 1 && kk <= tz_hi + 1;
     #pragma unroll
     for (int m = 0; m < 2; ++m) {
       if (m >= nq) break;
@@ -176,7 +190,7 @@ k_residual_f32(ResidualArgs a) {
         if (ok) {
           cp_async4(&sH[si], a.uhi + c * NN + n);
           cp_async4(&sL[si], a.ulo + c * NN + n);
-          if (dfield) cp_async4(&sD[si], dfield + c * NN + n);
+          if (dplane) cp_async4(&sD[si], dfield + c * NN + n);
           else sD[si] = 0.f;
         } else {
           sH[si] = 0.f;
@@ -228,13 +242,16 @@ k_residual_f32(ResidualArgs a) {
       if (ro) {
         #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          pg[c] = gprev[c * NN + nL];
+          if (gprev) pg[c] = gprev[c * NN + nL];
           #pragma unroll
           for (int q = 0; q < 4; ++q) pr[q][c] = (q == rslot) ? 0.f : Rk[q][c * NN + nL];
         }
       }
     }
 
+    // the reference flux of this voxel layer (uniform over the CTA)
+    const bool tau_L = tau_on && L >= tz_lo - 1 && L <= tz_hi;
+    const bool need_gd = tau_L && tau_from_delta;
     // ---------------- phase A: point data of voxel layer L
     if (vox_thread) {
       const uint8_t ph = sP[(s0 * FHY + vly) * FHX + vlx];
@@ -268,39 +285,48 @@ k_residual_f32(ResidualArgs a) {
               const int ic = corner(t ? 4 : 5, c), ie = corner(t ? 7 : 6, c);
               const float ah = sH[ia], al = sL[ia], bh = sH[ib], bl = sL[ib];
               const float ch = sH[ic], cl = sL[ic], eh = sH[ie], el = sL[ie];
-              const float A = sD[ia], B = sD[ib], Cc = sD[ic], E = sD[ie];
               const float d_ca = fdiff(ch, cl, ah, al), d_eb = fdiff(eh, el, bh, bl);
               G[c][2] = (d_ca + d_eb) * inv2h;
-              GD[c][2] = ((Cc - A) + (E - B)) * inv2h;
               if (t == 0) {
                 const float d_ba = fdiff(bh, bl, ah, al), d_ce = fdiff(ch, cl, eh, el);
                 G[c][0] = (d_ba + d_ce) * inv2h;
                 G[c][1] = (d_ba - d_ce) * inv2h;
-                GD[c][0] = ((B - A) + (Cc - E)) * inv2h;
-                GD[c][1] = ((B - A) - (Cc - E)) * inv2h;
               } else {
                 const float e_ab = fdiff(ah, al, bh, bl), e_ec = fdiff(eh, el, ch, cl);
                 G[c][0] = (e_ab + e_ec) * inv2h;
                 G[c][1] = (e_ec - e_ab) * inv2h;
-                GD[c][0] = ((A - B) + (E - Cc)) * inv2h;
-                GD[c][1] = ((E - Cc) - (A - B)) * inv2h;
+              }
+              if (need_gd) {
+                const float A = sD[ia], B = sD[ib], Cc = sD[ic], E = sD[ie];
+                GD[c][2] = ((Cc - A) + (E - B)) * inv2h;
+                if (t == 0) {
+                  GD[c][0] = ((B - A) + (Cc - E)) * inv2h;
+                  GD[c][1] = ((B - A) - (Cc - E)) * inv2h;
+                } else {
+                  GD[c][0] = ((A - B) + (E - Cc)) * inv2h;
+                  GD[c][1] = ((E - Cc) - (A - B)) * inv2h;
+                }
               }
             } else {
-              float uh[8], ul[8], ud[8];
+              float uh[8], ul[8];
               #pragma unroll
               for (int b = 0; b < 8; ++b) {
                 const int si = corner(b, c);
                 uh[b] = sH[si];
                 ul[b] = sL[si];
-                ud[b] = sD[si];
               }
               auto d = [&](int p, int q) { return fdiff(uh[p], ul[p], uh[q], ul[q]); };
               G[c][0] = (d(1, 0) + d(3, 2) + d(5, 4) + d(7, 6)) * inv4h;
               G[c][1] = (d(2, 0) + d(3, 1) + d(6, 4) + d(7, 5)) * inv4h;
               G[c][2] = (d(4, 0) + d(5, 1) + d(6, 2) + d(7, 3)) * inv4h;
-              GD[c][0] = ((ud[1] - ud[0]) + (ud[3] - ud[2]) + (ud[5] - ud[4]) + (ud[7] - ud[6])) * inv4h;
-              GD[c][1] = ((ud[2] - ud[0]) + (ud[3] - ud[1]) + (ud[6] - ud[4]) + (ud[7] - ud[5])) * inv4h;
-              GD[c][2] = ((ud[4] - ud[0]) + (ud[5] - ud[1]) + (ud[6] - ud[2]) + (ud[7] - ud[3])) * inv4h;
+              if (need_gd) {
+                float ud[8];
+                #pragma unroll
+                for (int b = 0; b < 8; ++b) ud[b] = sD[corner(b, c)];
+                GD[c][0] = ((ud[1] - ud[0]) + (ud[3] - ud[2]) + (ud[5] - ud[4]) + (ud[7] - ud[6])) * inv4h;
+                GD[c][1] = ((ud[2] - ud[0]) + (ud[3] - ud[1]) + (ud[6] - ud[4]) + (ud[7] - ud[5])) * inv4h;
+                GD[c][2] = ((ud[4] - ud[0]) + (ud[5] - ud[1]) + (ud[6] - ud[2]) + (ud[7] - ud[3])) * inv4h;
+              }
             }
           }
           float* o = out + t * QV * NVL;
@@ -335,7 +361,7 @@ k_residual_f32(ResidualArgs a) {
                 o[(3 * c + dd) * NVL] = v;
                 s2 = fmaf(v, v, s2);
               }
-            if (tau_on) {
+            if (tau_L) {
               #pragma unroll
               for (int c = 0; c < 3; ++c)
                 #pragma unroll
@@ -361,7 +387,7 @@ k_residual_f32(ResidualArgs a) {
           o[3 * NVL] = syz;
           o[4 * NVL] = sxz;
           o[5 * NVL] = sxy;
-          if (tau_on) {
+          if (tau_L) {
             #pragma unroll
             for (int c = 0; c < 3; ++c)
               #pragma unroll
@@ -401,7 +427,7 @@ k_residual_f32(ResidualArgs a) {
               F[1] += sxy * sx + syy * sy + syz * sz;
               F[2] += sxz * sx + syz * sy + szz * sz;
             }
-            if (tau_on) {
+            if (tau_L) {
               #pragma unroll
               for (int c = 0; c < 3; ++c)
                 F0[c] += q[(NS + 3 * c) * NVL] * sx + q[(NS + 1 + 3 * c) * NVL] * sy + q[(NS + 2 + 3 * c) * NVL] * sz;
@@ -522,6 +548,8 @@ int residual_f32_zchunk(const GridDev& g) {
   if (zc > 64) zc = 64;
   return (int)zc;
 }
+
+int residual_f32_tile(int axis) { return axis == 0 ? FTX : FTY; }
 
 int residual_f32_blocks(const GridDev& g) {
   int zc = residual_f32_zchunk(g);

@@ -91,7 +91,7 @@ __device__ __forceinline__ void gram_add(double* G, void* const* rring, int rslo
 
 template <typename T>
 __global__ void k_proj_P(const RowsDev r, T* p_direct, void* const* pring, void* const* rring, int ring_mode,
-                         int gram, double* partials, const Ctrl* ctrl) {
+                         int gram, double* partials, const Ctrl* ctrl, T* step_clear) {
   __shared__ double sh[SB / 32];
   if (ctrl && ctrl->done) return;
   T *p, *x;
@@ -112,6 +112,9 @@ __global__ void k_proj_P(const RowsDev r, T* p_direct, void* const* pring, void*
       if (x) x[d] = (T)((double)x[d] - sh_);
       acc += (double)(T)pn * (double)(T)pn;
       if (gram && rslot >= 0) gram_add<T>(G, rring, rslot, d);
+      // exact residual mode: the residual kernel has read this iteration's step; the
+      // row's DOFs start the next correction from zero
+      if (step_clear) step_clear[d] = (T)0;
     }
     r.mult[row] = -lam;
   }
@@ -125,11 +128,11 @@ __global__ void k_proj_P(const RowsDev r, T* p_direct, void* const* pring, void*
 
 template <typename T>
 int launch_proj_P_rows(const GridDev& g, const RowsDev& r, T* p_direct, void* const* pring, void* const* rring,
-                       int ring_mode, int gram, double* partials, const Ctrl* ctrl, cudaStream_t s) {
+                       int ring_mode, int gram, double* partials, const Ctrl* ctrl, cudaStream_t s, T* step_clear) {
   (void)g;
   int blocks = (r.nrows + SB - 1) / SB;
   if (blocks == 0) return 0;
-  k_proj_P<T><<<blocks, SB, 0, s>>>(r, p_direct, pring, rring, ring_mode, gram, partials, ctrl);
+  k_proj_P<T><<<blocks, SB, 0, s>>>(r, p_direct, pring, rring, ring_mode, gram, partials, ctrl, step_clear);
   return (int)cudaGetLastError();
 }
 
@@ -258,6 +261,10 @@ __global__ void k_contact_eval(const ContactArgs a, T* p_direct, void* const* pr
     a.c.gap[q] = gap;
     a.c.fn[q] = f;
     for (int c = 0; c < 3; ++c) a.c.nvec[3 * q + c] = nv[c];
+    // exact residual mode: the residual kernel has read this iteration's step; the face
+    // nodes start the next correction from zero
+    if (a.step_clear)
+      for (int c = 0; c < 3; ++c) ((T*)a.step_clear)[(long long)c * a.g.nnodes + n] = (T)0;
   }
   double t0 = block_sum(p2, sh);
   double t1 = block_sum(ng, sh);
@@ -875,8 +882,8 @@ int launch_ctrl_residual(Ctrl* c, const double* rp, int nres, const double* pp, 
   return (int)cudaGetLastError();
 }
 
-template int launch_proj_P_rows<double>(const GridDev&, const RowsDev&, double*, void* const*, void* const*, int, int, double*, const Ctrl*, cudaStream_t);
-template int launch_proj_P_rows<float>(const GridDev&, const RowsDev&, float*, void* const*, void* const*, int, int, double*, const Ctrl*, cudaStream_t);
+template int launch_proj_P_rows<double>(const GridDev&, const RowsDev&, double*, void* const*, void* const*, int, int, double*, const Ctrl*, cudaStream_t, double*);
+template int launch_proj_P_rows<float>(const GridDev&, const RowsDev&, float*, void* const*, void* const*, int, int, double*, const Ctrl*, cudaStream_t, float*);
 template int launch_proj_U_rows<double>(const GridDev&, const RowsDev&, double*, float*, float*, double*, const Ctrl*, cudaStream_t);
 template int launch_proj_U_rows<float>(const GridDev&, const RowsDev&, double*, float*, float*, float*, const Ctrl*, cudaStream_t);
 template int launch_proj_U_rows_end<double>(const GridDev&, const RowsDev&, double*, float*, float*, double*, Ctrl*, cudaStream_t);

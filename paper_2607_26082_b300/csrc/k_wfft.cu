@@ -478,7 +478,7 @@ k_wfft(WfftPass p, const Ctrl* ctrl) {
           ff_add(h[u], l[u], v[u]);
           p.uhi[ib + e] = h[u];
           p.ulo[ib + e] = l[u];
-          p.step[ib + e] = v[u];
+          if (p.step) p.step[ib + e] = v[u];
         } else {
           p.out[ib + e] = v[u];
         }
@@ -494,7 +494,7 @@ k_wfft(WfftPass p, const Ctrl* ctrl) {
         ff_add(h, l, v);
         p.uhi[ea] = h;
         p.ulo[ea] = l;
-        p.step[ea] = v;
+        if (p.step) p.step[ea] = v;
       } else {
         p.out[ea] = v;
       }
