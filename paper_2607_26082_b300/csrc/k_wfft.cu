@@ -393,7 +393,7 @@ __device__ __forceinline__ void wfill(float* sr, float* si, const float* __restr
 
 // MODE 0: transposed output through the tile; MODE 2: row output (or increment into u~).
 template <int R, int NW, int MODE>
-__global__ void __launch_bounds__(NW * 32, 2)
+__global__ void __launch_bounds__(NW * 32, 16 / NW)
 k_wfft(WfftPass p, const Ctrl* ctrl) {
   using PL = WPlan<R>;
   constexpr int P = PL::P, Q = PL::Q, RPC = 2 * P * NW, RPCP = RPC + 1, NK = 17;
@@ -505,7 +505,7 @@ k_wfft(WfftPass p, const Ctrl* ctrl) {
 // Fused z pass: forward z DTT of the rows (c, kx, ky), Green multiply (the Paux symbol
 // of Section 3.2.3 with the TETRA2 / HEX1 S_j), inverse z DTT, written transposed.
 template <int R, int NW>
-__global__ void __launch_bounds__(NW * 32, 2)
+__global__ void __launch_bounds__(NW * 32, 16 / NW)
 k_wfft_zg(WfftPass p, GreenTables gt, float l0, float m2, float ih2, int scheme, const Ctrl* ctrl) {
   using PL = WPlan<R>;
   constexpr int P = PL::P, Q = PL::Q, RPC = 2 * P * NW, RPCP = RPC + 1, NK = 17;
@@ -606,7 +606,7 @@ k_wfft_zg(WfftPass p, GreenTables gt, float l0, float m2, float ih2, int scheme,
 
 namespace {
 
-constexpr int WNW = 8;   // warps per CTA
+constexpr int WNW = 4;   // warps per CTA
 
 // per-warp scratch, then the CTA's tile: len x (RPC + 1) (transposed output) or
 // RPC x (len | 1) (row output)
