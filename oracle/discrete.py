@@ -259,16 +259,14 @@ def apply_A0(pb, u, lam0, mu0):
 
 
 def is_normal_mixed(pb):
-    """True when every face has "normal mixed" conditions: on each face the normal
-    component's condition differs from both tangential components' (normal Dirichlet with
-    tangential Neumann, or the reverse), and no axis is periodic.  Section 3.2.3: the
-    isotropic reference medium is usable with the per-component DTTs only for periodic and
-    normal mixed conditions; this library takes the non-periodic ones (its periodic axes
-    use a separable Hartley transform, which the medium's cross terms do not keep
-    diagonal)."""
+    """True when every axis is periodic for all components or has "normal mixed"
+    conditions on both faces: the normal component's condition differs from both tangential
+    components' (normal Dirichlet with tangential Neumann, or the reverse).  Section 3.2.3:
+    the isotropic reference medium is usable with the per-component transforms for
+    periodic and normal mixed conditions."""
     for d in range(3):
         if pb.periodic[d]:
-            return False
+            continue
         for f in range(2):
             normal = pb.bc[d, f, d]
             for c in range(3):

@@ -997,9 +997,16 @@ dtt_status dtt_set_reference(dtt_grid* G, double lambda0, double mu0) {
 
 // Normal mixed conditions on every face (no periodic axis): the normal component's
 // condition differs from both tangential components'.
+// The isotropic medium's conditions (Section 3.2.3): every axis periodic for all
+// components, or normal mixed on both of its faces.
 static bool normal_mixed(const dtt_grid* G) {
   for (int d = 0; d < 3; ++d) {
-    if (G->g.periodic[d]) return false;
+    if (G->g.periodic[d]) {
+      for (int f = 0; f < 2; ++f)
+        for (int c = 0; c < 3; ++c)
+          if (G->g.bc[d][f][c] != BC_P) return false;
+      continue;
+    }
     for (int f = 0; f < 2; ++f) {
       const int nrm = G->g.bc[d][f][d];
       for (int c = 0; c < 3; ++c)
@@ -1055,8 +1062,9 @@ dtt_status dtt_set_reference_medium(dtt_grid* G, int32_t medium) {
     return fail(DTT_ERR_ARG, "medium must be DTT_MEDIUM_PAUX or DTT_MEDIUM_ISOTROPIC");
   const int iso = medium == DTT_MEDIUM_ISOTROPIC;
   if (iso && !normal_mixed(G))
-    return fail(DTT_ERR_BC, "the isotropic reference medium needs normal mixed conditions on every face "
-                            "(normal component Dirichlet with tangential Neumann, or the reverse; no periodic axis)");
+    return fail(DTT_ERR_BC, "the isotropic reference medium needs, on every axis, periodic conditions for all "
+                            "components or normal mixed conditions (normal component Dirichlet with tangential "
+                            "Neumann, or the reverse) on both faces");
   if (iso && !G->iso_s[0]) {
     dtt_status st = build_iso_tables(G);
     if (st != DTT_OK) return st;

@@ -307,18 +307,30 @@ int launch_green_multiply(const GridDev& g, T* spec, const TransformTables& tt, 
 
 // Green step of the isotropic reference medium R0 : grad u = lambda0 tr(grad u) 1 +
 // mu0 (grad u + grad u^T) (Section 3.2.3; Eq. 4 for HEX1 in the periodic case).  With
-// normal mixed conditions every component's DTT basis function of wave vector q is mapped
-// by A0 onto the same q of every component, so A0 is a symmetric 3 x 3 matrix per
-// position:
+// normal mixed conditions on the non-periodic axes, every component's DTT basis function
+// of wave vector q is mapped by A0 onto the same q of every component along those axes.
+// Along a periodic axis the basis is the Hartley cas(q x), and a first difference maps
+// cas(q x) onto cas(-q x): the cross term of components c and d flips the wave numbers of
+// the periodic axes among {c, d}.  Those flips compose, so u_x at position q, u_y at q
+// flipped on the periodic axes of {x, y} and u_z at q flipped on those of {x, z} form a
+// closed symmetric 3 x 3 system:
 //     M_cc = (lambda0 + mu0) S_c + mu0 (S_x + S_y + S_z),
-//     M_cd = sign_c sign_d (lambda0 + mu0) T_cd            (c != d),
-// with the scheme's S_j (as in k_green) and the cross symbols
+//     M_cd = sign_c sign_d tau_cd (lambda0 + mu0) T_cd        (c != d),
+// with the scheme's S_j (as in k_green; even in every q, so the same at the three
+// positions), the cross symbols
 //     TETRA2: T_cd = sin q_c sin q_d / h^2,  HEX1: T_cd = sin q_c sin q_d cos^2(q_e / 2) / h^2
 // (e the third axis; both from the schemes' gradients, and real because both stencils are
-// centrosymmetric).  In the quarter units of the tables (4 / h^2 factored out):
-// sin q_c sin q_d / 4 = sqrt(s_c c'_c s_d c'_d).  A component without a mode at the position,
-// or whose diagonal vanishes (a null mode, where all its cross terms vanish too), keeps
-// a zero coefficient; the rest is solved by LDL^T (symmetric positive definite).
+// centrosymmetric) taken at the x component's position q with signed sines on the
+// periodic axes, sign_d = +1 when the normal component's transform along d is a sine
+// transform and -1 otherwise (a periodic axis counts as -1), and tau_cd = -1 for the pairs
+// (x, y), (x, z) when the x axis is periodic, +1 otherwise.  (Rule checked against the
+// operator's spectral matrix, entry by entry, for every periodic pattern and both
+// schemes.)  In the quarter units of the tables (4 / h^2 factored out):
+// |sin q_c sin q_d| / 4 = sqrt(s_c c'_c s_d c'_d).  A component without a mode at its
+// position, or whose diagonal vanishes (a null mode, where all its cross terms vanish too),
+// keeps a zero coefficient; the rest is solved by LDL^T (symmetric positive definite).
+// Each thread takes the triple of one x position; the flips are bijections, so every
+// position of every component belongs to exactly one triple.
 // The scalar constants come from the host (ih2 = 4 / h^2, ih2r = its inverse, lm = lambda0 +
 // mu0, m0 = mu0, thr the null threshold): no per-thread FP64 arithmetic.
 template <typename T>
@@ -342,6 +354,18 @@ __global__ void k_green_iso(const GridDev g, T* __restrict__ spec, IsoTables it,
       k = (int)(r / g.nn[1]);
     }
     const int valid = it.valid[0][i] & it.valid[1][j] & it.valid[2][k];
+    // positions of the triple: flips on the periodic axes of {x, y} (y) and {x, z} (z)
+    const int fi = g.periodic[0] ? (i == 0 ? 0 : g.nn[0] - i) : i;
+    const int fj = g.periodic[1] ? (j == 0 ? 0 : g.nn[1] - j) : j;
+    const int fk = g.periodic[2] ? (k == 0 ? 0 : g.nn[2] - k) : k;
+    const long long np[3] = {n, fi + (long long)g.nn[0] * (fj + (long long)g.nn[1] * k),
+                             fi + (long long)g.nn[0] * (j + (long long)g.nn[1] * fk)};
+    // sign of sin q at the x position: + on a non-periodic axis (q in [0, pi]); on a
+    // periodic axis + for 0 < p < n/2, - for p > n/2 (0 where sin q = 0)
+    const int pidx[3] = {i, j, k};
+    T ssg[3];
+    #pragma unroll
+    for (int d = 0; d < 3; ++d) ssg[d] = (g.periodic[d] && 2 * pidx[d] > g.nn[d]) ? (T)-1 : (T)1;
     T sv[3], cv[3];
     const int pos[3] = {i, j, k};
     #pragma unroll
@@ -372,16 +396,17 @@ __global__ void k_green_iso(const GridDev g, T* __restrict__ spec, IsoTables it,
     for (int c = 0; c < 3; ++c) {
       M[c][c] = lm * S[c] + m0 * Ssum;
       on[c] = ((valid >> c) & 1) && M[c][c] * ih2 > thr;
-      b[c] = on[c] ? spec[(long long)c * NN + n] : (T)0;
+      b[c] = on[c] ? spec[(long long)c * NN + np[c]] : (T)0;
     }
     #pragma unroll
     for (int c = 0; c < 3; ++c)
       #pragma unroll
       for (int d = c + 1; d < 3; ++d) {
         const int e = 3 - c - d;
-        T t = rt[c] * rt[d];
+        T t = (rt[c] * ssg[c]) * (rt[d] * ssg[d]);
         if (g.scheme != SCHEME_TETRA2) t *= cv[e];
-        t *= (T)(it.sign[c] * it.sign[d]) * lm;
+        const int tau = (g.periodic[0] && c == 0) ? -1 : 1;   // pairs (x, y), (x, z) when x is periodic
+        t *= (T)(it.sign[c] * it.sign[d] * tau) * lm;
         if (!on[c] || !on[d]) t = (T)0;
         M[c][d] = t;
         M[d][c] = t;
@@ -403,7 +428,7 @@ __global__ void k_green_iso(const GridDev g, T* __restrict__ spec, IsoTables it,
     const T x0 = y0 * r0 - L10 * x1 - L20 * x2;
     const T x[3] = {x0, x1, x2};
     #pragma unroll
-    for (int c = 0; c < 3; ++c) spec[(long long)c * NN + n] = on[c] ? x[c] * ih2r : (T)0;
+    for (int c = 0; c < 3; ++c) spec[(long long)c * NN + np[c]] = on[c] ? x[c] * ih2r : (T)0;
   }
 }
 

@@ -145,3 +145,43 @@ def test_iso_argument_checks():
     # two reference media, one discrete problem: the same solution
     assert rel_l2(g.dtt_get_fields(), u1) <= 1e-5
     g.close()
+
+
+# Periodic axes (Section 3.2.3: the isotropic medium with periodic and normal mixed
+# conditions): the Hartley basis of a periodic axis couples u_x at q, u_y and u_z at
+# partner positions; every periodic pattern, odd and even periods, both schemes.
+PERIODIC = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
+
+
+@pytest.mark.parametrize("scheme", [wl.TETRA2, wl.HEX1])
+@pytest.mark.parametrize("periodic", PERIODIC)
+@pytest.mark.parametrize("nvox", [(6, 5, 4), (4, 8, 6)])
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-11), (MIXED, 2e-6)])
+def test_iso_green_step_periodic(scheme, periodic, nvox, prec, tol):
+    seed = 20 + 4 * sum(periodic) + nvox[0]
+    spec = wl.iso_cell(seed, nvox=nvox, scheme=scheme, n_strong=0, periodic=periodic)
+    pb, _ = oracle_problem(spec)
+    g = gpu_grid(spec, prec)
+    g.dtt_set_reference_medium(dtt.MEDIUM_ISOTROPIC)
+    p = _p(pb, seed)
+    green = odz.make_dense_green(pb, lambda u: odz.apply_A0_iso(pb, u, spec["lam0"], spec["mu0"]))
+    ref = green(p)
+    got = g.dtt_apply_green(p)
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    g.close()
+
+
+@pytest.mark.parametrize("periodic", [(1, 0, 0), (0, 1, 1), (1, 1, 1)])
+def test_iso_fixed_iterations_periodic_fp64(periodic):
+    """Algorithm 1 with the isotropic medium on a cell with periodic axes: iterate for
+    iterate against the oracle (dense Green step)."""
+    spec = wl.iso_cell(31 + sum(periodic), nvox=(6, 5, 7), scheme=wl.TETRA2, n_strong=2, periodic=periodic)
+    pb, rows = oracle_problem(spec)
+    K = 15
+    ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 0.0, K, acv_on="P", acv_mod=2, medium="iso")
+    g = gpu_grid(spec, FP64)
+    g.dtt_set_reference_medium(dtt.MEDIUM_ISOTROPIC)
+    rep = g.dtt_solve_step(0.0, K, acv_mod=2)
+    assert rep.iterations == K and rep.accelerations == ref.accelerations
+    assert rel_l2(g.dtt_get_fields(), ref.u) <= 1e-9
+    g.close()

@@ -174,3 +174,115 @@ def test_iso_solver_laminate_closed_form(scheme):
     uz = np.where(z <= 2, e[0] * z, e[0] * 2 + e[1] * (z - 2))
     assert np.abs(res.u[2] - uz[:, None, None]).max() <= 1e-10
     assert np.abs(res.u[0]).max() <= 1e-10 and np.abs(res.u[1]).max() <= 1e-10
+
+
+def _axis_forward(ttype, n):
+    """Forward transform of one axis with the spectral index k of the library (DST1: k = 1
+    .. n-1 at index k); a periodic axis takes the Hartley transform sum_j x_j cas(2 pi j k / n)."""
+    if ttype == otr.DFT:
+        a = 2 * np.pi * np.outer(np.arange(n), np.arange(n)) / n
+        return np.cos(a) + np.sin(a)
+    F = otr.forward_matrix(ttype, n)
+    _, kidx, _ = otr.selection(ttype, n)
+    full = np.zeros((n + 1, n + 1))
+    for a, k in enumerate(kidx):
+        full[k] = F[a]
+    return full
+
+
+def _axis_inverse(ttype, n):
+    if ttype == otr.DFT:
+        a = 2 * np.pi * np.outer(np.arange(n), np.arange(n)) / n
+        return (np.cos(a) + np.sin(a)) / n
+    B = otr.inverse_matrix(ttype, n)
+    _, kidx, _ = otr.selection(ttype, n)
+    full = np.zeros((n + 1, n + 1))
+    for a, k in enumerate(kidx):
+        full[:, k] = B[:, a]
+    return full
+
+
+@pytest.mark.parametrize("scheme", [dz.TETRA2, dz.HEX1])
+@pytest.mark.parametrize("periodic", [(1, 0, 0), (0, 1, 1), (1, 1, 1)])
+def test_iso_operator_couples_partner_positions(scheme, periodic):
+    """The isotropic A0 (Section 3.2.3) in the per-axis bases: along a periodic axis the
+    Hartley cas(q x) is mapped by a first difference onto cas(-q x), so the operator couples
+    u_x at q with u_y at q flipped on the periodic axes of {x, y} and u_z at q flipped on
+    those of {x, z}, and nothing else; the 3 x 3 blocks are M_cc = 4 ((lambda0 + mu0) S_c +
+    mu0 sum S) and M_cd = (lambda0 + mu0) sign_c sign_d tau_cd sin q_c sin q_d (times
+    cos^2(q_e / 2) for HEX1), sines signed at the x position on periodic axes, sign_d = +1
+    for a sine-type normal transform along d (-1 otherwise, a periodic axis -1), tau = -1 for
+    the pairs with x when x is periodic.  Checked entry by entry on the operator's spectral
+    matrix (h = 1)."""
+    rng = np.random.default_rng(7)
+    normal = rng.choice([D, N], size=(3, 2))
+    bc = _normal_mixed_bc(normal)
+    for d in range(3):
+        if periodic[d]:
+            bc[d] = P
+    nvox = (4, 5, 3)
+    pb = dz.Problem(nvox, 1.0, bc, scheme, np.zeros(tuple(reversed(nvox)), np.uint8), np.array([1.0]),
+                    np.array([1.0]))
+    lam0, mu0 = 0.7, 0.4
+    nx, ny, nz = pb.nn
+    n_all = nx * ny * nz
+    F = np.zeros((3 * n_all, 3 * n_all))
+    B = np.zeros_like(F)
+    for c in range(3):
+        fx, fy, fz = (_axis_forward(pb.types[c][d], nvox[d]) for d in range(3))
+        bx, by, bz = (_axis_inverse(pb.types[c][d], nvox[d]) for d in range(3))
+        F[c * n_all:(c + 1) * n_all, c * n_all:(c + 1) * n_all] = np.kron(fz, np.kron(fy, fx))
+        B[c * n_all:(c + 1) * n_all, c * n_all:(c + 1) * n_all] = np.kron(bz, np.kron(by, bx))
+    A = np.zeros_like(F)
+    for e in range(3 * n_all):
+        u = np.zeros(3 * n_all)
+        u[e] = 1.0
+        A[:, e] = dz.apply_A0_iso(pb, u.reshape((3, nz, ny, nx)), lam0, mu0).reshape(-1)
+    S = F @ A @ B
+    qv = [[dict(zip(otr.selection(pb.types[c][d], nvox[d])[1], otr.selection(pb.types[c][d], nvox[d])[2]))
+           for d in range(3)] for c in range(3)]
+    sgn = [1.0 if pb.types[d][d] in (otr.DST1, otr.DST3) else -1.0 for d in range(3)]
+    lm = lam0 + mu0
+
+    def flip(pos, axes):
+        return tuple(((-p) % pb.nn[a]) if (a in axes and periodic[a]) else p for a, p in enumerate(pos))
+
+    def idx(c, pos):
+        return c * n_all + (pos[2] * ny + pos[1]) * nx + pos[0]
+
+    for k, j, i in itertools.product(range(nz), range(ny), range(nx)):
+        q = (i, j, k)
+        pos = [q, flip(q, (0, 1)), flip(q, (0, 2))]
+        on = [all(pos[c][d] in qv[c][d] for d in range(3)) for c in range(3)]
+        rows = [idx(c, pos[c]) for c in range(3)]
+        for c in range(3):
+            if not on[c]:
+                continue
+            # nothing outside the triple
+            others = np.delete(S[rows[c]], [rows[d] for d in range(3) if on[d]])
+            assert np.abs(others).max() <= 1e-12
+            qq = [qv[c][d][pos[c][d]] for d in range(3)]
+            s = [np.sin(x / 2) ** 2 for x in qq]
+            cp = [np.cos(x / 2) ** 2 for x in qq]
+            if scheme == dz.TETRA2:
+                Sx = s[0] * cp[1] + s[2] * (s[1] - s[0])
+                Sy = s[1] * cp[2] + s[0] * (s[2] - s[1])
+                Sz = s[2] * cp[0] + s[1] * (s[0] - s[2])
+            else:
+                Sx, Sy, Sz = s[0] * cp[1] * cp[2], s[1] * cp[0] * cp[2], s[2] * cp[0] * cp[1]
+            assert abs(S[rows[c], rows[c]] - 4 * (lm * (Sx, Sy, Sz)[c] + mu0 * (Sx + Sy + Sz))) <= 1e-12
+            for d in range(3):
+                if d == c or not on[d]:
+                    continue
+                e = 3 - c - d
+
+                def sine(a):
+                    if periodic[a]:
+                        return np.sin(2 * np.pi * q[a] / nvox[a])
+                    return np.sin(qv[c][a][pos[c][a]] if a == c else qv[d][a][pos[d][a]])
+
+                tau = -1.0 if (periodic[0] and 0 in (c, d)) else 1.0
+                want = lm * sgn[c] * sgn[d] * tau * sine(c) * sine(d)
+                if scheme == dz.HEX1:
+                    want *= np.cos(qv[c][e][pos[c][e]] / 2) ** 2
+                assert abs(S[rows[c], rows[d]] - want) <= 1e-12

@@ -172,14 +172,18 @@ def normal_mixed_bc(normal):
     return bc
 
 
-def iso_cell(seed, nvox=(12, 10, 8), scheme=TETRA2, n_strong=3, eps_scale=1e-3, contrast=4.0):
+def iso_cell(seed, nvox=(12, 10, 8), scheme=TETRA2, n_strong=3, eps_scale=1e-3, contrast=4.0, periodic=(0, 0, 0)):
     """Two-phase cell for the isotropic reference medium: every face normal mixed (drawn at
-    random), a random two-phase map of stiffness ratio `contrast` (nu = 0.3), random eps*,
+    random) except on the axes flagged in `periodic`, which are periodic for every
+    component; a random two-phase map of stiffness ratio `contrast` (nu = 0.3), random eps*,
     and up to n_strong interior strong rows on components that have a Dirichlet face.
     Reference media: (lambda0, mu0) = the mean of the phases' Lame coefficients."""
     rng = np.random.default_rng(seed)
     normal = rng.choice([D, N], size=(3, 2))
     bc = normal_mixed_bc(normal)
+    for d in range(3):
+        if periodic[d]:
+            bc[d] = P
     phase = (rng.random((nvox[2], nvox[1], nvox[0])) < 0.35).astype(np.uint8)
     lam, mu = lame(np.array([1.0, contrast]), 0.3)
     e = rng.uniform(-eps_scale, eps_scale, size=(3, 3))
