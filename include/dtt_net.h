@@ -140,6 +140,19 @@ dtt_status dtt_net_train_increment(dtt_net* net, dtt_grid* grid, const double* u
 dtt_status dtt_net_predict_increment(dtt_net* net, dtt_grid* grid, const double* u_prev2, const double* fn_prev,
                                      const double depth[3]);
 
+/* Tracing aid for per-layer parity: runs dtt_net_loss_grad's forward and backward passes on
+ * host x [nz][ny][nx][16] and target [nz][ny][nx][3] and returns, for `layer` (0 .. 10 in the
+ * order of the network listing above), its input activation act_in (host float [V][cin], the
+ * BF16 values the layer read), the gradient of the loss with respect to its output taken
+ * through its ReLU, as the weight-gradient kernel consumed it (host float [V][cout], BF16
+ * values; the last layer has no ReLU), its parameter gradients grad_w ([27][cout][cin]) and
+ * grad_b ([cout]), and the gradient with respect to its input grad_in ([V][cin], FP32; zero
+ * for layer 0, whose input gradient is not formed); V = the node count of the layer's level
+ * (full, half or quarter resolution, halves rounded up).  Any output pointer may be NULL.
+ * DTT_ERR_ARG for a layer outside 0 .. 10. */
+dtt_status dtt_net_layer_trace(dtt_net* net, int32_t nx, int32_t ny, int32_t nz, const float* x, const float* target,
+                               int32_t layer, float* act_in, float* dz, float* grad_w, float* grad_b, float* grad_in);
+
 /* Loss and gradients of the increment loss for host inputs (parity aid): x [nz][ny][nx][16],
  * target [nz][ny][nx][4], pmask [nz][ny][nx] (1 on surface nodes), grad (host, num_params). */
 dtt_status dtt_net_loss_grad_increment(dtt_net* net, int32_t nx, int32_t ny, int32_t nz, const float* x,

@@ -83,6 +83,12 @@ struct dtt_net {
   int win_dep = 0;         // window: node layers below the contact face (0: whole grid)
   double* d_ug = nullptr;  // [3][NN] guess of u~ on the whole grid (increment mode)
   long long ug_cap = 0;
+  // tracing (dtt_net_layer_trace): the input activation and the output gradient through the
+  // ReLU of one layer, copied by its backward pass
+  int trace_layer = -1;
+  bf16* tr_in = nullptr;
+  bf16* tr_dz = nullptr;
+  float* tr_dx = nullptr;
 };
 
 namespace {
@@ -191,10 +197,16 @@ dtt_status fwd_layer(dtt_net* N, int l, const Dims& d, const bf16* in, bf16* out
 dtt_status bwd_layer(dtt_net* N, int l, const Dims& d, const bf16* in, const float* G, const bf16* R, float* dX) {
   ConvArgs a = conv_args(N, l, d);
   NCKL(launch_relu_bwd(G, R, d.V() * a.cout, N->dz, N->stream));
+  if (l == N->trace_layer && N->tr_in && N->tr_dz) {
+    NCK(cudaMemcpyAsync(N->tr_in, in, (size_t)d.V() * a.cin * sizeof(bf16), cudaMemcpyDeviceToDevice, N->stream));
+    NCK(cudaMemcpyAsync(N->tr_dz, N->dz, (size_t)d.V() * a.cout * sizeof(bf16), cudaMemcpyDeviceToDevice, N->stream));
+  }
   a.x = in;
   a.dz = N->dz;
   a.dx = dX;
   NCKL(launch_conv_bwd(a, N->stream));
+  if (l == N->trace_layer && N->tr_dx && dX)
+    NCK(cudaMemcpyAsync(N->tr_dx, dX, (size_t)d.V() * a.cin * sizeof(float), cudaMemcpyDeviceToDevice, N->stream));
   return DTT_OK;
 }
 
@@ -507,6 +519,66 @@ dtt_status dtt_net_loss_grad(dtt_net* N, int32_t nx, int32_t ny, int32_t nz, con
     NCK(cudaMemcpyAsync(grad, N->g, N->np * sizeof(float), cudaMemcpyDeviceToHost, N->stream));
     NCK(cudaStreamSynchronize(N->stream));
   }
+  return DTT_OK;
+}
+
+dtt_status dtt_net_layer_trace(dtt_net* N, int32_t nx, int32_t ny, int32_t nz, const float* x, const float* target,
+                               int32_t layer, float* act_in, float* dz, float* grad_w, float* grad_b,
+                               float* grad_in) {
+  if (!N || !x || !target || nx < 1 || ny < 1 || nz < 1 || layer < 0 || layer >= NLAYER)
+    return set_error(DTT_ERR_ARG, "bad argument");
+  dtt_status s = ensure_workspace(N, nx, ny, nz);
+  if (s != DTT_OK) return s;
+  // the layer's level: full resolution (0, 1, 8, 9, 10), half (2, 3, 6, 7), quarter (4, 5)
+  const Dims& d = (layer == 4 || layer == 5) ? N->d2 : ((layer >= 2 && layer <= 7) ? N->d1 : N->d0);
+  const Layer& L = N->L[layer];
+  const size_t nin = (size_t)d.V() * L.cin, nout = (size_t)d.V() * L.cout;
+  if ((s = nalloc(&N->tr_in, nin * sizeof(bf16))) != DTT_OK) return s;
+  if ((s = nalloc(&N->tr_dz, nout * sizeof(bf16))) != DTT_OK || (s = nalloc(&N->tr_dx, nin * sizeof(float))) != DTT_OK) {
+    nfree(N->tr_in);
+    nfree(N->tr_dz);
+    return s;
+  }
+  cudaMemsetAsync(N->tr_dx, 0, nin * sizeof(float), N->stream);
+  N->trace_layer = layer;
+  s = upload_input(N, x);
+  if (s == DTT_OK) {
+    cudaError_t e = cudaMemcpyAsync(N->tgt, target, (size_t)N->d0.V() * 3 * sizeof(float), cudaMemcpyHostToDevice,
+                                    N->stream);
+    if (e != cudaSuccess) s = set_error(DTT_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (s == DTT_OK) s = forward(N);
+  if (s == DTT_OK) s = backward(N, nullptr);
+  N->trace_layer = -1;
+  std::vector<uint16_t> hin(nin), hdz(nout);
+  if (s == DTT_OK) {
+    cudaError_t e = cudaMemcpyAsync(hin.data(), N->tr_in, nin * sizeof(bf16), cudaMemcpyDeviceToHost, N->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hdz.data(), N->tr_dz, nout * sizeof(bf16), cudaMemcpyDeviceToHost, N->stream);
+    if (e == cudaSuccess && grad_w)
+      e = cudaMemcpyAsync(grad_w, N->g + L.woff, (size_t)27 * L.cin * L.cout * sizeof(float), cudaMemcpyDeviceToHost,
+                          N->stream);
+    if (e == cudaSuccess && grad_b)
+      e = cudaMemcpyAsync(grad_b, N->g + L.boff, (size_t)L.cout * sizeof(float), cudaMemcpyDeviceToHost, N->stream);
+    if (e == cudaSuccess && grad_in)
+      e = cudaMemcpyAsync(grad_in, N->tr_dx, nin * sizeof(float), cudaMemcpyDeviceToHost, N->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(N->stream);
+    if (e != cudaSuccess) s = set_error(DTT_ERR_CUDA, cudaGetErrorString(e));
+  }
+  nfree(N->tr_in);
+  nfree(N->tr_dz);
+  nfree(N->tr_dx);
+  if (s != DTT_OK) return s;
+  // BF16 is the upper half of an FP32 word
+  auto widen = [](uint16_t h) {
+    const uint32_t w = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &w, sizeof(f));
+    return f;
+  };
+  if (act_in)
+    for (size_t q = 0; q < nin; ++q) act_in[q] = widen(hin[q]);
+  if (dz)
+    for (size_t q = 0; q < nout; ++q) dz[q] = widen(hdz[q]);
   return DTT_OK;
 }
 

@@ -13,7 +13,7 @@ NET_CIN = 16
 EXPORTS = ["dtt_net_create", "dtt_net_destroy", "dtt_net_num_params", "dtt_net_get_params", "dtt_net_set_params",
            "dtt_net_loss_grad", "dtt_net_forward", "dtt_net_features", "dtt_net_train_step", "dtt_net_predict",
            "dtt_net_set_loss", "dtt_net_set_increment", "dtt_net_increment_features", "dtt_net_train_increment",
-           "dtt_net_predict_increment", "dtt_net_loss_grad_increment"]
+           "dtt_net_predict_increment", "dtt_net_loss_grad_increment", "dtt_net_layer_trace"]
 _bound = False
 
 
@@ -40,13 +40,21 @@ def _lib():
         L.dtt_net_train_increment.argtypes = [P, P, P, P, P, P, P, f32, C.POINTER(C.c_double)]
         L.dtt_net_predict_increment.argtypes = [P, P, P, P, P]
         L.dtt_net_loss_grad_increment.argtypes = [P, i32, i32, i32, P, P, P, C.POINTER(C.c_double), P]
+        L.dtt_net_layer_trace.argtypes = [P, i32, i32, i32, P, P, i32, P, P, P, P, P]
         for name in ("dtt_net_create", "dtt_net_get_params", "dtt_net_set_params", "dtt_net_loss_grad",
                      "dtt_net_forward", "dtt_net_features", "dtt_net_train_step", "dtt_net_predict",
                      "dtt_net_set_loss", "dtt_net_set_increment", "dtt_net_increment_features",
-                     "dtt_net_train_increment", "dtt_net_predict_increment", "dtt_net_loss_grad_increment"):
+                     "dtt_net_train_increment", "dtt_net_predict_increment", "dtt_net_loss_grad_increment",
+                     "dtt_net_layer_trace"):
             getattr(L, name).restype = i32
         _bound = True
     return L
+
+
+def layer_shapes(c1=16, c2=32, c3=64):
+    """(cin, cout) of the eleven convolutions in the order of include/dtt_net.h."""
+    return [(16, c1), (c1, c1), (c1, c2), (c2, c2), (c2, c3), (c3, c3), (c3, c2), (c2, c2), (c2, c1), (c1, c1),
+            (c1, 16)]
 
 
 def _f32(a):
@@ -101,6 +109,30 @@ class Net:
                                             t.ctypes.data_as(C.c_void_p), C.byref(loss),
                                             g.ctypes.data_as(C.c_void_p)))
         return loss.value, g
+
+    def layer_trace(self, x, target, layer):
+        """For layer `layer` of the loss_grad pass on (x, target): its input activation
+        [nz', ny', nx', cin], the output gradient through its ReLU [nz', ny', nx', cout] (both
+        the BF16 values the kernels used), its gradients (W [27, cout, cin], b [cout]) and the
+        gradient with respect to its input [nz', ny', nx', cin], at the layer's level."""
+        x, t = _f32(x), _f32(target)
+        nz, ny, nx = x.shape[:3]
+        lvl = 2 if layer in (4, 5) else (1 if 2 <= layer <= 7 else 0)
+        dims = (nz, ny, nx)
+        for _ in range(lvl):
+            dims = tuple((v + 1) // 2 for v in dims)
+        cin, cout = layer_shapes(*self.channels)[layer]
+        a = np.zeros(dims + (cin,), np.float32)
+        dz = np.zeros(dims + (cout,), np.float32)
+        gw = np.zeros((27, cout, cin), np.float32)
+        gb = np.zeros(cout, np.float32)
+        gx = np.zeros(dims + (cin,), np.float32)
+        dtt._check(_lib().dtt_net_layer_trace(self._h, nx, ny, nz, x.ctypes.data_as(C.c_void_p),
+                                              t.ctypes.data_as(C.c_void_p), int(layer),
+                                              a.ctypes.data_as(C.c_void_p), dz.ctypes.data_as(C.c_void_p),
+                                              gw.ctypes.data_as(C.c_void_p), gb.ctypes.data_as(C.c_void_p),
+                                              gx.ctypes.data_as(C.c_void_p)))
+        return a, dz, gw, gb, gx
 
     def forward(self, x):
         x = _f32(x)

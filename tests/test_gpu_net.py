@@ -119,3 +119,34 @@ def test_trained_warm_start_on_held_out_cells():
     for q in grids:
         q.close()
     net.close()
+
+
+def bf16_weights(p, ch):
+    return [(bf16_round(W), b) for W, b in onet.unpack(p, *ch)]
+
+
+@pytest.mark.parametrize("ch", [(16, 32, 64), (32, 16, 32)])
+def test_net_layers_match_reference_one_by_one(ch):
+    """Every layer on its own: given the layer's input activation and its output gradient
+    as the GPU kernels used them (BF16 values), the float64 reference's weight, bias and
+    input gradients (with the BF16-rounded weights) agree to 1e-4: the products of BF16
+    operands are exact in FP32, so only the order of the FP32 sums remains.  A wrong tap, a
+    transposed weight or a shifted index in any layer is an O(1) error here."""
+    net = Net(*ch, seed=3)
+    rng = np.random.default_rng(5)
+    shape = (11, 7, 9)
+    x = rng.standard_normal(shape + (16,)).astype(np.float32)
+    t = rng.standard_normal(shape + (3,)).astype(np.float32)
+    layers = bf16_weights(net.get_params(), ch)
+    for l in range(11):
+        a, dz, gw, gb, gx = net.layer_trace(x, t, l)
+        assert np.abs(dz).max() > 0, l
+        rgx, rgW, rgb = onet.conv_backward(a.astype(np.float64), layers[l][0], dz.astype(np.float64))
+        assert _rel(gw, rgW) <= 1e-4, l
+        assert _rel(gb, rgb) <= 1e-4, l
+        if l > 0:
+            assert _rel(gx, rgx) <= 1e-4, l
+    # the first layer's input is the BF16-rounded features
+    a0 = net.layer_trace(x, t, 0)[0]
+    assert np.array_equal(a0, bf16_round(x).astype(np.float32))
+    net.close()
