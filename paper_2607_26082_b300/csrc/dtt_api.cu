@@ -670,23 +670,102 @@ dtt_status enqueue_iter_any(dtt_grid* G, int acv_on, bool acv) {
                                   : enqueue_iteration<float>(G, acv_on, acv);
 }
 
-dtt_status build_graph(dtt_grid* G, int acv_on, bool acv, int iters) {
-  invalidate_graph(G);
+// The whole solve as one CUDA graph: a conditional WHILE node whose body is one round
+// (`round` enqueues it on stream s, which may fork to other streams and join back) followed
+// by the loop condition (k_loop_continue: another round while a grid runs, at most
+// rounds[1] rounds; rounds[0] counts them).  *looped = false, with no graph, when the
+// driver does not take conditional nodes (or DTT_GRAPH_LOOP=0 asks for the host loop); the
+// caller then captures one round and loops on the host.
+template <typename F>
+dtt_status build_loop_graph(cudaStream_t s, F&& round, Ctrl* const* ctrls, const Ctrl* one, int n, int* rounds,
+                            cudaGraphExec_t* exec, bool* looped) {
+  *looped = false;
+  *exec = nullptr;
+  if (const char* v = std::getenv("DTT_GRAPH_LOOP"))
+    if (v[0] == '0') return DTT_OK;
   cudaGraph_t graph = nullptr;
-  CK(cudaStreamBeginCapture(G->stream, cudaStreamCaptureModeThreadLocal));
-  dtt_status st = DTT_OK;
-  for (int k = 0; k < iters && st == DTT_OK; ++k) st = enqueue_iter_any(G, acv_on, acv);
-  cudaError_t e = cudaStreamEndCapture(G->stream, &graph);
-  if (st != DTT_OK) {
-    if (graph) cudaGraphDestroy(graph);
-    return st;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h{};
+  cudaGraphNodeParams cp{};
+  cudaGraphNode_t node{};
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
   }
-  if (e != cudaSuccess) return fail(DTT_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&G->gexec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return DTT_OK;
+  }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return DTT_OK;
+  }
+  dtt_status st = round();
+  if (st == DTT_OK && launch_loop_continue(ctrls, one, n, h, rounds, 0, s) != 0)
+    st = fail(DTT_ERR_CUDA, "loop condition launch");
+  cudaGraph_t got = nullptr;
+  e = cudaStreamEndCapture(s, &got);
+  if (st != DTT_OK || e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    if (st != DTT_OK) return st;
+    return fail(DTT_ERR_CUDA, std::string("loop capture: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
-    G->gexec = nullptr;
-    return fail(DTT_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    *exec = nullptr;
+    return fail(DTT_ERR_CUDA, std::string("cudaGraphInstantiate (loop): ") + cudaGetErrorString(e));
+  }
+  *looped = true;
+  return DTT_OK;
+}
+
+// Resets the loop's round counter and sets its cap (before each launch of a loop graph).
+dtt_status arm_loop(int* rounds, int max_rounds, cudaStream_t s) {
+  const int v[2] = {0, max_rounds};
+  CK(cudaMemcpyAsync(rounds, v, sizeof(v), cudaMemcpyHostToDevice, s));
+  return DTT_OK;
+}
+
+dtt_status build_graph(dtt_grid* G, int acv_on, bool acv, int iters) {
+  invalidate_graph(G);
+  if (!G->d_rounds) {
+    dtt_status st = dalloc(&G->d_rounds, 2 * sizeof(int));
+    if (st != DTT_OK) return st;
+  }
+  auto round = [&]() {
+    dtt_status st = DTT_OK;
+    for (int k = 0; k < iters && st == DTT_OK; ++k) st = enqueue_iter_any(G, acv_on, acv);
+    return st;
+  };
+  bool looped = false;
+  dtt_status st = build_loop_graph(G->stream, round, nullptr, G->d_ctrl, 1, G->d_rounds, &G->gexec, &looped);
+  if (st != DTT_OK) return st;
+  G->g_loop = looped;
+  if (!looped) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(G->stream, cudaStreamCaptureModeThreadLocal));
+    st = round();
+    cudaError_t e = cudaStreamEndCapture(G->stream, &graph);
+    if (st != DTT_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(DTT_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&G->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      G->gexec = nullptr;
+      return fail(DTT_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
   }
   G->g_key = acv_on * 1000000 + (acv ? 100000 : 0) + iters;
   return DTT_OK;
@@ -938,6 +1017,7 @@ void dtt_grid_destroy(dtt_grid* G) {
   }
   {
     dfree(G->d_tile_z);
+    dfree(G->d_rounds);
   }
   free_rows(G);
   free_contact(G);
@@ -1534,6 +1614,14 @@ dtt_status dtt_solve_step(dtt_grid* G, const dtt_solve_opts* opts, dtt_report* r
   }
   long long launched = 0;
   const long long cap = (long long)opts->max_iter + 2LL * iters + 8;
+  if (G->g_loop) {
+    // one launch runs the solve to its end (the device loop stops at max_iter; the round
+    // cap only guards it)
+    dtt_status st = arm_loop(G->d_rounds, (int)std::min<long long>(cap / iters + 2, 1 << 30), s);
+    if (st != DTT_OK) return st;
+    CK(cudaGraphLaunch(G->gexec, s));
+    return finish_solve(G, t0, rep);
+  }
   while (true) {
     CK(cudaGraphLaunch(G->gexec, s));
     launched += iters;
@@ -2004,6 +2092,8 @@ dtt_status apply_tiling(dtt_grid* G, int zc, int generic, int z_route, int warp)
 struct BatchCache {
   std::vector<unsigned long long> key;   // device, opts key, then (id, version) per cell
   cudaGraphExec_t exec = nullptr;
+  bool looped = false;                   // exec runs the whole batch (conditional WHILE node)
+  int* d_rounds = nullptr;
   cudaStream_t bs = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   Ctrl** d_ctrls = nullptr;
@@ -2015,6 +2105,7 @@ BatchCache g_batch;
 
 dtt_status batch_buffers(int n) {
   if (!g_batch.bs) CK(cudaStreamCreateWithFlags(&g_batch.bs, cudaStreamNonBlocking));
+  if (!g_batch.d_rounds) CK(cudaMalloc(&g_batch.d_rounds, 2 * sizeof(int)));
   if (!g_batch.fork) CK(cudaEventCreateWithFlags(&g_batch.fork, cudaEventDisableTiming));
   if (!g_batch.join) CK(cudaEventCreateWithFlags(&g_batch.join, cudaEventDisableTiming));
   if (n > g_batch.cap) {
@@ -2121,34 +2212,51 @@ dtt_status dtt_batch_solve(int32_t ncell, dtt_grid* const* cells, const dtt_solv
     std::vector<Ctrl*> ctrls(ncell);
     for (int i = 0; i < ncell; ++i) ctrls[i] = cells[i]->d_ctrl;
     CK(cudaMemcpy(g_batch.d_ctrls, ctrls.data(), ncell * sizeof(Ctrl*), cudaMemcpyHostToDevice));
-    // fork-join capture: every cell's iterations on its own stream, joined back to bs
-    CK(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
-    cudaEventRecord(g_batch.fork, bs);
-    for (int i = 0; i < ncell; ++i) {
-      cudaStreamWaitEvent(cells[i]->stream, g_batch.fork, 0);
-      for (int k = 0; k < iters && st == DTT_OK; ++k) st = enqueue_iter_any(cells[i], opts->acv_on, acv);
-      cudaEventRecord(g_batch.join, cells[i]->stream);
-      cudaStreamWaitEvent(bs, g_batch.join, 0);
-      if (st != DTT_OK) break;
-    }
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(bs, &graph);
-    if (st != DTT_OK || e != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      if (st != DTT_OK) return st;
-      return fail(DTT_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
-    }
-    e = cudaGraphInstantiate(&g_batch.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      g_batch.exec = nullptr;
-      return fail(DTT_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    // fork-join round: every cell's iterations on its own stream, joined back to bs
+    auto round = [&]() {
+      dtt_status rs = DTT_OK;
+      cudaEventRecord(g_batch.fork, bs);
+      for (int i = 0; i < ncell; ++i) {
+        cudaStreamWaitEvent(cells[i]->stream, g_batch.fork, 0);
+        for (int k = 0; k < iters && rs == DTT_OK; ++k) rs = enqueue_iter_any(cells[i], opts->acv_on, acv);
+        cudaEventRecord(g_batch.join, cells[i]->stream);
+        cudaStreamWaitEvent(bs, g_batch.join, 0);
+        if (rs != DTT_OK) break;
+      }
+      return rs;
+    };
+    // the whole batch as one launch (conditional WHILE node), else one round per launch
+    bool looped = false;
+    st = build_loop_graph(bs, round, g_batch.d_ctrls, nullptr, ncell, g_batch.d_rounds, &g_batch.exec, &looped);
+    if (st != DTT_OK) return st;
+    g_batch.looped = looped;
+    if (!looped) {
+      CK(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+      st = round();
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(bs, &graph);
+      if (st != DTT_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (st != DTT_OK) return st;
+        return fail(DTT_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+      }
+      e = cudaGraphInstantiate(&g_batch.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        g_batch.exec = nullptr;
+        return fail(DTT_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+      }
     }
     g_batch.key = key;
   }
   long long launched = 0;
   const long long cap = (long long)opts->max_iter + 2LL * iters + 8;
-  while (true) {
+  if (g_batch.looped) {
+    if ((st = arm_loop(g_batch.d_rounds, (int)std::min<long long>(cap / iters + 2, 1 << 30), bs)) != DTT_OK) return st;
+    CK(cudaGraphLaunch(g_batch.exec, bs));
+    CK(cudaStreamSynchronize(bs));
+  }
+  while (!g_batch.looped) {
     CK(cudaGraphLaunch(g_batch.exec, bs));
     launched += iters;
     CKL(launch_batch_done(g_batch.d_ctrls, ncell, g_batch.d_done, bs));

@@ -160,6 +160,9 @@ struct ResidualArgs {
 constexpr int RES_STRIDE = 6;
 // done flags of many grids' control blocks gathered into one array (batched solves)
 int launch_batch_done(Ctrl* const* ctrls, int n, int* done, cudaStream_t s);
+// condition kernel of the device-side solve loop (conditional WHILE node)
+int launch_loop_continue(Ctrl* const* ctrls, const Ctrl* one, int n, cudaGraphConditionalHandle h, int* rounds,
+                         int max_rounds, cudaStream_t s);
 template <typename T> int launch_residual(const ResidualArgs& a, cudaStream_t s);
 int residual_blocks(const GridDev& g);
 int residual_zchunk(const GridDev& g);

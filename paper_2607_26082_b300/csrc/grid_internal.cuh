@@ -121,6 +121,8 @@ struct dtt_grid {
   // graph
   cudaGraphExec_t gexec = nullptr;
   int g_key = -1;
+  bool g_loop = false;         // gexec runs the whole solve (conditional WHILE node around the iterations)
+  int* d_rounds = nullptr;     // rounds of the device-side loop (reset before each launch)
   unsigned long long id = 0;        // unique per grid of the process
   unsigned long long version = 0;   // bumped whenever captured launch arguments go stale
 

@@ -906,6 +906,34 @@ __global__ void k_batch_done(Ctrl* const* ctrls, int n, int* done) {
   if (i < n) done[i] = ctrls[i]->done;
 }
 
+// Condition of the device-side solve loop (a conditional WHILE node of the solve's CUDA
+// graph around `iters` captured iterations): run another round while any of the grids
+// (ctrls[0..n), or the single control block `one`) is still iterating and fewer than
+// rounds[1] rounds have run (rounds[0] counts them; the cap only guards the loop, each grid
+// stops at its max_iter).  max_rounds > 0 overrides rounds[1].
+__global__ void k_loop_continue(Ctrl* const* ctrls, const Ctrl* one, int n, cudaGraphConditionalHandle h,
+                                int* rounds, int max_rounds) {
+  __shared__ int running;
+  if (threadIdx.x == 0) running = one ? !one->done : 0;
+  __syncthreads();
+  if (!one)
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (!ctrls[i]->done) atomicOr(&running, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int r = rounds[0] + 1;
+    rounds[0] = r;
+    const int cap = max_rounds > 0 ? max_rounds : rounds[1];
+    cudaGraphSetConditional(h, (running && r < cap) ? 1u : 0u);
+  }
+}
+
+int launch_loop_continue(Ctrl* const* ctrls, const Ctrl* one, int n, cudaGraphConditionalHandle h, int* rounds,
+                         int max_rounds, cudaStream_t s) {
+  k_loop_continue<<<1, 256, 0, s>>>(ctrls, one, n, h, rounds, max_rounds);
+  return (int)cudaGetLastError();
+}
+
 int launch_batch_done(Ctrl* const* ctrls, int n, int* done, cudaStream_t s) {
   if (n <= 0) return 0;
   k_batch_done<<<(n + 255) / 256, 256, 0, s>>>(ctrls, n, done);

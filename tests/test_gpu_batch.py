@@ -177,3 +177,46 @@ def test_new_values_in_same_layout_keep_graph_and_match_fresh_grid(prec):
     assert np.array_equal(per1, per2)
     g.close()
     g2.close()
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_device_loop_matches_host_loop(prec, monkeypatch):
+    """A solve (and a batch) runs as one graph launch: a conditional WHILE node repeats a
+    round of graph_iters iterations while a grid is running.  With DTT_GRAPH_LOOP=0 the
+    host launches one round at a time and polls the done flags instead.  Both loops stop at
+    the same iterate: fields bit-identical, same iteration counts, the max_iter cap
+    honoured mid-round."""
+    cells = _cells(4, seed0=4200)
+
+    def run(loop):
+        if loop:
+            monkeypatch.delenv("DTT_GRAPH_LOOP", raising=False)
+        else:
+            monkeypatch.setenv("DTT_GRAPH_LOOP", "0")
+        one = []
+        for c in cells:
+            g = gpu_grid(c, prec)
+            rep = g.dtt_solve_step(_tol(prec), 4000, acv_mod=c["acv_mod"], graph_iters=8)
+            capped = gpu_grid(c, prec)
+            rc = capped.dtt_solve_step(_tol(prec), 5, acv_mod=c["acv_mod"], graph_iters=8)
+            one.append((rep.status, rep.iterations, g.dtt_get_fields(), rc.status, rc.iterations,
+                        capped.dtt_get_fields()))
+            g.close()
+            capped.close()
+        grids = [gpu_grid(c, prec) for c in cells]
+        st, reps = dtt.dtt_batch_solve(grids, _tol(prec), 4000, acv_mod=2, graph_iters=8)
+        assert st == dtt.OK
+        batch = [(r.status, r.iterations, g.dtt_get_fields()) for g, r in zip(grids, reps)]
+        for g in grids:
+            g.close()
+        return one, batch
+
+    dev, host = run(True), run(False)
+    for a, b in zip(dev[0], host[0]):
+        assert a[0] == b[0] == dtt.OK and a[1] == b[1]
+        assert np.array_equal(a[2], b[2])
+        assert a[3] == b[3] == dtt.ERR_NOT_CONVERGED and a[4] == b[4] == 5
+        assert np.array_equal(a[5], b[5])
+    for a, b in zip(dev[1], host[1]):
+        assert a[0] == b[0] == dtt.OK and a[1] == b[1]
+        assert np.array_equal(a[2], b[2])
