@@ -1,19 +1,26 @@
 // Stress / divergence / reference-operator kernel of the mixed path (same operator as
 // k_residual.cu: Eq. 3 with the HEX1 / TETRA2 gradients of Section 3.1.1, the Paux
 // reference medium of Section 3.2.3 and the symmetry weights W of Table 1), organised for
-// FP32 throughput on B300:
+// instruction throughput on B300:
 //
 //  * a CTA owns a 32 x 8 tile of node columns and marches along z one voxel layer at a
 //    time; the layer between node planes L and L+1 is processed in two phases:
-//      A. one thread per voxel of the 33 x 9 halo layer forms, once, the gradients of both
-//         tetrahedra (TETRA2) or of the single point (HEX1), the stress sigma = C:(eps* +
-//         sym grad u~) and the reference-medium flux tau_cd = (2 mu0 + lambda0 delta_cd)
-//         d(.)_c/dx_d, and stores them in shared memory (structure of arrays);
+//      A. one thread per voxel of the 33 x 9 halo layer forms, once, the gradients of its
+//         points, the stress sigma = C:(eps* + sym grad u~) and, on the layers that need
+//         it, the reference-medium flux tau_cd = (2 mu0 + lambda0 delta_cd) d(.)_c/dx_d,
+//         and stores them in shared memory (structure of arrays);
 //      B. one thread per node gathers, from the 4 voxels of the layer around its column,
 //         the divergence contributions to node L (as their lower corner) and to node L+1
 //         (as their upper corner); node L is then complete and its outputs are written;
-//  * u~ (float-float hi / lo), the step Delta and the voxel phases of node planes L..L+2
-//    sit in a 3-slot shared-memory ring filled with cp.async one plane ahead;
+//  * u~ sits in shared memory as interleaved (hi, lo) pairs, so that one 64-bit load
+//    fetches a corner and one packed subtraction forms both halves of a difference;
+//  * TETRA2: the two tetrahedra of a voxel are the two lanes of packed FP32x2 arithmetic
+//    (gradients, stress, flux, the stored point data); in phase B a voxel's lane pair
+//    feeds node L from one tetrahedron and node L+1 from the other, so each gather is
+//    one packed FMA per stress value;
+//  * u~, the step Delta and the voxel phases of node planes sit in a 4-slot ring filled
+//    with cp.async two planes ahead (layer L reads planes L and L+1 while L+2 and L+3
+//    are in flight); the phases travel as aligned 4-byte words where the grid allows;
 //  * in the Anderson difference form the kernel also forms the Gram row <R_{i-1}, R_k>
 //    (k = 0..3) over the unconstrained DOFs; the projection kernels add the constrained
 //    ones after they have shifted R_{i-1};
@@ -26,20 +33,26 @@
 // Partial sums per CTA (FP64): [sum w sigma:sigma, sum p^2, Gram 0..3].
 #include "dtt_internal.cuh"
 
+#include <map>
+#include <mutex>
+#include <queue>
+#include <tuple>
+#include <vector>
+
 namespace dtt {
 
 namespace {
 
-constexpr int FTX = 32, FTY = 8;                 // node tile
-constexpr int FVX = FTX + 1, FVY = FTY + 1;      // voxel layer with its low-side halo
+constexpr int FTX = 32, FTY = 8;
+constexpr int FVX = FTX + 1, FVY = FTY + 1;
 constexpr int NVL = FVX * FVY;                   // 297 voxels per layer
-constexpr int FTHREADS = 320;                    // >= NVL, multiple of 32
-constexpr int FNP = 3;                           // node-plane ring slots
-constexpr int FHX = FTX + 2, FHY = FTY + 2;      // node plane with halo (x0-1 .. x0+32)
-constexpr int FPLANE = 3 * FHY * FHX;            // floats per plane (3 components)
+constexpr int FTHREADS = 320;
+constexpr int FHX = FTX + 2, FHY = FTY + 2;
+constexpr int FPL = FHY * FHX;                   // 340 positions per node plane
+constexpr int RING = 4;                         // node-plane ring slots
+constexpr int PWX = 40;                         // phase bytes per voxel row in word mode
 template <bool FS> struct PointLayout {
-  static constexpr int NS = FS ? 9 : 6;          // stress values per point (Pi or sigma)
-  static constexpr int QV = NS + 9;              // plus tau 9
+  static constexpr int NS = FS ? 9 : 6;          // stress values per point (Pi or sigma); the flux adds 9
 };
 
 __device__ __forceinline__ void cp_async4(void* smem_ptr, const void* gptr) {
@@ -48,52 +61,73 @@ __device__ __forceinline__ void cp_async4(void* smem_ptr, const void* gptr) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 __device__ __forceinline__ int wrapi(int i, int n, int per) {
   if (per) { i %= n; if (i < 0) i += n; return i; }
   return (i < 0 || i >= n) ? -1 : i;
 }
-__device__ __forceinline__ int slot_of(int plane) { return ((plane % FNP) + FNP) % FNP; }
 
-// compensated FP32 accumulator (TwoSum: s + c carries the sum to about FP32^2)
-struct Acc2 {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = s + x;
-    const float z = t - s;
-    c += (s - (t - z)) + (x - z);
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-
-__device__ __forceinline__ int sidx(int slot, int c, int ly, int lx) { return ((slot * 3 + c) * FHY + ly) * FHX + lx; }
-
-// (ph + pl) - (qh + ql) from the pairs' differences, so that increments far below the
-// FP32 resolution of u~ survive
-__device__ __forceinline__ float fdiff(float ph, float pl, float qh, float ql) {
-  return __fadd_rn(__fsub_rn(ph, qh), __fsub_rn(pl, ql));
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 r;
+  asm("{ .reg .b64 ra, rb, rr; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; sub.rn.f32x2 rr, ra, rb; mov.b64 {%0, %1}, rr; }"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+// (ph + pl) - (qh + ql) of float-float pairs, formed from their differences
+__device__ __forceinline__ float fd(float2 p, float2 q) {
+  const float2 d = sub2(p, q);
+  return __fadd_rn(d.x, d.y);
 }
 
-// Reference flux tau = R0 : grad u, Paux or isotropic medium (Section 3.2.3).
-__device__ __forceinline__ float ref_flux(const float (&Gm)[3][3], int c, int d, float lam0, float mu0, bool iso) {
+// compensated FP32 accumulators, two lanes at once (TwoSum per lane)
+struct Acc2x2 {
+  float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+  __device__ __forceinline__ void add(float2 x) {
+    const float2 t = add2(s, x);
+    const float2 z = sub2(t, s);
+    c = add2(c, add2(sub2(s, sub2(t, z)), sub2(x, z)));
+    s = t;
+  }
+  __device__ __forceinline__ double value(int lane) const {
+    return lane ? (double)s.y + (double)c.y : (double)s.x + (double)c.x;
+  }
+};
+
+// reference flux tau = R0 : grad u of both points at once (Paux or isotropic medium)
+__device__ __forceinline__ float2 ref_flux2(const float2 (&Gm)[3][3], int c, int d, float lam0, float mu0, bool iso) {
+  if (iso) {
+    float2 v = mul2(bc2(mu0), add2(Gm[c][d], Gm[d][c]));
+    if (c == d) v = fma2(bc2(lam0), add2(add2(Gm[0][0], Gm[1][1]), Gm[2][2]), v);
+    return v;
+  }
+  return mul2(bc2(2.f * mu0 + (c == d ? lam0 : 0.f)), Gm[c][d]);
+}
+__device__ __forceinline__ float ref_flux1(const float (&Gm)[3][3], int c, int d, float lam0, float mu0, bool iso) {
   if (iso) return (c == d ? lam0 * (Gm[0][0] + Gm[1][1] + Gm[2][2]) : 0.f) + mu0 * (Gm[c][d] + Gm[d][c]);
   return (2.f * mu0 + (c == d ? lam0 : 0.f)) * Gm[c][d];
 }
 
 }  // namespace
 
-template <int SCHEME, bool FS>
+// PHW: voxel phases loaded as aligned 4-byte words (x extent a multiple of 4, x not
+// periodic, phase array 4-byte aligned); otherwise one byte per halo position
+template <int SCHEME, bool FS, bool PHW>
 __global__ void __launch_bounds__(FTHREADS, 2)
 k_residual_f32(ResidualArgs a) {
-  constexpr int NPT = (SCHEME == SCHEME_TETRA2) ? 2 : 1;
-  constexpr int NS = PointLayout<FS>::NS, QV = PointLayout<FS>::QV;
+  constexpr bool TET = SCHEME == SCHEME_TETRA2;
+  constexpr int NS = PointLayout<FS>::NS;
+  constexpr int NPT = TET ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sH = (float*)smem_raw;                 // [FNP][3][FHY][FHX] u~ hi
-  float* sL = sH + FNP * FPLANE;                // u~ lo
-  float* sD = sL + FNP * FPLANE;                // Delta
-  float* sV = sD + FNP * FPLANE;                // [NPT * QV][NVL] point data of the current layer
-  uint8_t* sP = (uint8_t*)(sV + NPT * QV * NVL);   // [FNP][FHY][FHX] voxel phases (layer of plane)
+  float2* sU = (float2*)smem_raw;                       // [RING][3][FPL] u~ (hi, lo)
+  float* sD = (float*)(sU + RING * 3 * FPL);            // [RING][3][FPL] Delta
+  float* sSf = sD + RING * 3 * FPL;                     // stress point data [NS][NVL] (x NPT floats)
+  float* sTf = sSf + NS * NVL * NPT;                    // flux point data [9][NVL] (x NPT floats)
+  uint8_t* sP = (uint8_t*)(sTf + 9 * NVL * NPT);        // phases: [RING][FPL] bytes, or [RING][FVY][PWX] words
   __shared__ float sLam[MAX_PHASE], sMu[MAX_PHASE];
   __shared__ double sRed[6][FTHREADS / 32];
 
@@ -111,16 +145,15 @@ k_residual_f32(ResidualArgs a) {
   const long long NN = g.nnodes;
   const int nnx = g.nn[0], nny = g.nn[1], nnz = g.nn[2];
 
-  // outputs by mode
   float* po = (float*)a.pout;
   float* xo = nullptr;
   float* ro = nullptr;
   const float* gprev = nullptr;
   const float* dfield = nullptr;
-  const float* Rk[4] = {nullptr, nullptr, nullptr, nullptr};
+  const float* Rq[3] = {nullptr, nullptr, nullptr};   // the other three R slots, (rslot + 1 + k) % 4
   int rslot = -1;
   bool tau_on = true, tau_from_delta = false;
-  int tz_lo = -(1 << 29), tz_hi = 1 << 29;   // node planes where the flux's field can be non-zero
+  int tz_lo = -(1 << 29), tz_hi = 1 << 29;
   if (a.mode == 0) {
     xo = (float*)a.xout;
   } else if (a.mode == 1) {
@@ -133,15 +166,11 @@ k_residual_f32(ResidualArgs a) {
       dfield = (const float*)a.dfield;
       tau_from_delta = true;
       #pragma unroll
-      for (int q = 0; q < 4; ++q) Rk[q] = (const float*)a.rring[q];
+      for (int k = 0; k < 3; ++k) Rq[k] = (const float*)a.rring[(rslot + 1 + k) % 4];
       if (a.exact) {
-        // R_{i-1} = p_i + A0 c_{i-1}: g_{i-1} is not needed, and A0 c vanishes unless the
-        // CTA's nodes or their neighbours carry a correction; c lives on node planes
-        // [zlo, zhi] of this tile, so only voxel layers zlo - 1 .. zhi carry its flux
         gprev = nullptr;
         const int2 zr = a.tile_z[blockIdx.y * gridDim.x + blockIdx.x];
-        const int z1c = min((int)blockIdx.z * a.zchunk + a.zchunk, a.g.nn[2]);
-        tau_on = zr.x <= zr.y && zr.y >= (int)blockIdx.z * a.zchunk - 1 && zr.x <= z1c;
+        tau_on = zr.x <= zr.y && zr.y >= z0 - 1 && zr.x <= z1;
         if (!tau_on) dfield = nullptr;
         tz_lo = zr.x;
         tz_hi = zr.y;
@@ -158,26 +187,33 @@ k_residual_f32(ResidualArgs a) {
   const float c4h = inv4h;
   const float (&eps)[3][3] = a.f_eps;
 
-  // ---- plane loader: node plane kk and the voxel phases of layer kk into ring slot.  Each
-  // thread owns at most two positions of the 34 x 10 plane; their xy offsets are fixed for
-  // the whole march.
-  int nq = 0, q_off[2] = {0, 0};
-  long long q_node[2] = {-1, -1}, q_vox[2] = {-1, -1};
-  for (int q = tid; q < FHX * FHY; q += FTHREADS, ++nq) {
+  // ---- phase words: 10 aligned words per voxel row cover voxels x0 - 4 .. x0 + 35
+  int w_off = -1;                  // byte offset of this thread's word in a voxel plane, -1: none
+  if (PHW && tid < FVY * (PWX / 4)) {
+    const int ly = tid / (PWX / 4), xs = x0 - 4 + 4 * (tid % (PWX / 4));
+    const int vy = wrapi(y0 - 1 + ly, g.nvox[1], g.periodic[1]);
+    if (vy >= 0 && xs >= 0 && xs + 4 <= g.nvox[0]) w_off = xs + g.nvox[0] * vy;
+  }
+  // ---- plane loader (each thread owns at most two of the 34 x 10 positions)
+  // position m of this thread: q = tid + m * FTHREADS (m = 1 only for the first FPL - FTHREADS threads)
+  const int nq = tid + FTHREADS < FPL ? 2 : 1;
+  int q_node[2] = {-1, -1}, q_vox[2] = {-1, -1};     // in-plane indices (a plane holds < 2^31 nodes)
+  for (int m = 0; m < nq; ++m) {
+    const int q = tid + m * FTHREADS;
     const int lx = q % FHX, ly = q / FHX;
-    q_off[nq] = ly * FHX + lx;
     const int gi = wrapi(x0 - 1 + lx, nnx, g.periodic[0]);
     const int gj = wrapi(y0 - 1 + ly, nny, g.periodic[1]);
-    q_node[nq] = (gi >= 0 && gj >= 0) ? gi + (long long)nnx * gj : -1;
+    q_node[m] = (gi >= 0 && gj >= 0) ? gi + nnx * gj : -1;
     const int vx = wrapi(x0 - 1 + lx, g.nvox[0], g.periodic[0]);
     const int vy = wrapi(y0 - 1 + ly, g.nvox[1], g.periodic[1]);
-    q_vox[nq] = (vx >= 0 && vy >= 0) ? vx + (long long)g.nvox[0] * vy : -1;
+    q_vox[m] = (vx >= 0 && vy >= 0) ? vx + g.nvox[0] * vy : -1;
   }
   const long long plane_n = (long long)nnx * nny, plane_v = (long long)g.nvox[0] * g.nvox[1];
   auto load_plane = [&](int kk) {
-    const int slot = slot_of(kk);
+    const int slot = kk & (RING - 1);
     const int kw = wrapi(kk, nnz, g.periodic[2]);
     const int vz = wrapi(kk, g.nvox[2], g.periodic[2]);
+    // Delta is read only on planes next to the layers that carry the flux
     const bool dplane = dfield && kk >= tz_lo - 1 && kk <= tz_hi + 1;
     #pragma unroll
     for (int m = 0; m < 2; ++m) {
@@ -186,57 +222,84 @@ k_residual_f32(ResidualArgs a) {
       const long long n = ok ? q_node[m] + plane_n * kw : 0;
       #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const int si = (slot * 3 + c) * FHY * FHX + q_off[m];
+        const int si = (slot * 3 + c) * FPL + (tid + m * FTHREADS);
         if (ok) {
-          cp_async4(&sH[si], a.uhi + c * NN + n);
-          cp_async4(&sL[si], a.ulo + c * NN + n);
+          cp_async4(&sU[si].x, a.uhi + c * NN + n);
+          cp_async4(&sU[si].y, a.ulo + c * NN + n);
           if (dplane) cp_async4(&sD[si], dfield + c * NN + n);
-          else sD[si] = 0.f;
         } else {
-          sH[si] = 0.f;
-          sL[si] = 0.f;
-          sD[si] = 0.f;
+          sU[si] = make_float2(0.f, 0.f);
+          if (dplane) sD[si] = 0.f;
         }
       }
-      uint8_t ph = 255;   // 255 = no voxel
-      if (vz >= 0 && q_vox[m] >= 0) ph = a.phase[q_vox[m] + plane_v * vz];
-      sP[slot * FHY * FHX + q_off[m]] = ph;
+      if (!PHW) {
+        uint8_t ph = 255;   // 255 = no voxel
+        if (vz >= 0 && q_vox[m] >= 0) ph = a.phase[q_vox[m] + plane_v * vz];
+        sP[slot * FPL + (tid + m * FTHREADS)] = ph;
+      }
+    }
+    if (PHW && tid < FVY * (PWX / 4)) {
+      uint32_t* dst = (uint32_t*)(sP + slot * FVY * PWX) + tid;
+      if (vz >= 0 && w_off >= 0) cp_async4(dst, a.phase + w_off + plane_v * vz);
+      else *dst = 0xffffffffu;
     }
   };
 
-  Acc2 acc_s2, acc_p2, acc_g[4];
+  Acc2x2 acc_sp;            // lanes: sum w sigma:sigma, sum p^2
+  Acc2x2 acc_g01, acc_g23;  // Gram row: lanes (R slot rslot, slot rslot + 1), (rslot + 2, rslot + 3)
 
-  // node thread (i, j)
   const bool node_thread = tid < FTX * FTY;
   const int tx = tid % FTX, ty = tid / FTX;
   const int i = x0 + tx, j = y0 + ty;
   const bool active = node_thread && (i < nnx && j < nny);
-  // voxel thread: local voxel (vlx, vly) = global voxel (x0 - 1 + vlx, y0 - 1 + vly); warps
-  // 0..8 take the voxel rows' first 32 columns (one row per warp: bank-conflict free), the
-  // first 9 lanes of warp 9 take column 32
   const bool vox_thread = tid < NVL;
   const int vlx = tid < FTX * FVY ? (tid % FTX) : FTX;
   const int vly = tid < FTX * FVY ? (tid / FTX) : (tid - FTX * FVY);
   const int vslot = vly * FVX + vlx;
+  const bool own_xy = vlx >= 1 && vly >= 1 && (x0 - 1 + vlx) < g.nvox[0] && (y0 - 1 + vly) < g.nvox[1];
 
-  float Fc[3] = {0.f, 0.f, 0.f}, F0c[3] = {0.f, 0.f, 0.f};   // node plane L (complete after layer L)
-  float Fn[3] = {0.f, 0.f, 0.f}, F0n[3] = {0.f, 0.f, 0.f};   // node plane L+1 (partial)
+  // x / y faces of this thread's node column: DOF flags and Neumann weights per component
+  // bits 3c: (node, c) is not a DOF; bits 3c+1..3c+2: number of Neumann faces through it
+  int fxy = 0;
+  {
+    const int idx[2] = {i, j};
+    #pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      if (g.periodic[d]) continue;
+      int f = -1;
+      if (idx[d] == 0) f = 0;
+      else if (idx[d] == g.nn[d] - 1) f = 1;
+      if (f < 0) continue;
+      #pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int t = g.bc[d][f][c];
+        if (t == BC_D) fxy |= 1 << (3 * c);
+        else if (t == BC_N) fxy += 2 << (3 * c);
+      }
+    }
+  }
 
+  float Fc[3] = {0.f, 0.f, 0.f}, F0c[3] = {0.f, 0.f, 0.f};
+
+  // ring of RING node planes (slot = plane & 3), filled two planes ahead: layer L reads
+  // planes L and L+1 while L+2 and L+3 are in flight
   load_plane(z0 - 1);
   load_plane(z0);
   cp_async_commit();
-  cp_async_wait_all();
+  if (z0 + 1 <= z1) load_plane(z0 + 1);
+  cp_async_commit();
+  cp_async_wait_1();
   __syncthreads();
 
-  for (int L = z0 - 1; L < z1; ++L) {
-    if (L + 2 <= z1) load_plane(L + 2);
+  long long nL = (long long)i + (long long)nnx * (j + (long long)nny * (z0 - 1));
+  for (int L = z0 - 1; L < z1; ++L, nL += plane_n) {
+    if (L + 3 <= z1) load_plane(L + 3);
     cp_async_commit();
-    const int s0 = slot_of(L), s1 = slot_of(L + 1);
-    // operands of node L's outputs, loaded now so that their latency overlaps phase A
+    const int s0 = L & (RING - 1), s1 = (L + 1) & (RING - 1);
+
     uint8_t cm = 0;
-    float pg[3] = {0.f, 0.f, 0.f}, pr[4][3];
+    float pg[3] = {0.f, 0.f, 0.f}, pr[3][3];
     const bool fin = active && L >= z0;
-    const long long nL = (long long)i + (long long)nnx * (j + (long long)nny * L);
     if (fin) {
       cm = a.cmask ? a.cmask[nL] : 0;
       if (ro) {
@@ -244,92 +307,171 @@ k_residual_f32(ResidualArgs a) {
         for (int c = 0; c < 3; ++c) {
           if (gprev) pg[c] = gprev[c * NN + nL];
           #pragma unroll
-          for (int q = 0; q < 4; ++q) pr[q][c] = (q == rslot) ? 0.f : Rk[q][c * NN + nL];
+          for (int k = 0; k < 3; ++k) pr[k][c] = Rq[k][c * NN + nL];
         }
       }
     }
 
-    // the reference flux of this voxel layer (uniform over the CTA)
     const bool tau_L = tau_on && L >= tz_lo - 1 && L <= tz_hi;
     const bool need_gd = tau_L && tau_from_delta;
     // ---------------- phase A: point data of voxel layer L
     if (vox_thread) {
-      const uint8_t ph = sP[(s0 * FHY + vly) * FHX + vlx];
-      float* out = sV + vslot;
+      const uint8_t ph = PHW ? sP[s0 * FVY * PWX + vly * PWX + vlx + 3] : sP[s0 * FPL + vly * FHX + vlx];
       if (ph == 255) {
-        #pragma unroll
-        for (int q = 0; q < NPT * QV; ++q) out[q * NVL] = 0.f;
+        if constexpr (TET) {
+          #pragma unroll
+          for (int q = 0; q < NS; ++q) ((float2*)sSf)[q * NVL + vslot] = make_float2(0.f, 0.f);
+          if (tau_L) {
+            #pragma unroll
+            for (int q = 0; q < 9; ++q) ((float2*)sTf)[q * NVL + vslot] = make_float2(0.f, 0.f);
+          }
+        } else {
+          #pragma unroll
+          for (int q = 0; q < NS; ++q) sSf[q * NVL + vslot] = 0.f;
+          if (tau_L) {
+            #pragma unroll
+            for (int q = 0; q < 9; ++q) sTf[q * NVL + vslot] = 0.f;
+          }
+        }
       } else {
         const float lam = sLam[ph], mu = sMu[ph];
-        // each voxel's sigma:sigma counted by the tile that holds its lower corner node
-        const bool own = vlx >= 1 && vly >= 1 && L >= z0 && (x0 - 1 + vlx) < g.nvox[0] &&
-                         (y0 - 1 + vly) < g.nvox[1] && L < g.nvox[2];
-        const float w = (SCHEME == SCHEME_TETRA2) ? 0.5f : 1.f;
+        const bool own = own_xy && L >= z0 && L < g.nvox[2];
+        const float2* U0 = sU + s0 * 3 * FPL + vly * FHX + vlx;
+        const float2* U1 = sU + s1 * 3 * FPL + vly * FHX + vlx;
+        const float* D0 = sD + s0 * 3 * FPL + vly * FHX + vlx;
+        const float* D1 = sD + s1 * 3 * FPL + vly * FHX + vlx;
         // corner b = cx + 2 cy + 4 cz of the voxel, component c
-        // corner b = cx + 2 cy + 4 cz, component c: the plane's base index plus a constant
-        const int base0 = sidx(s0, 0, vly, vlx), base1 = sidx(s1, 0, vly, vlx);
-        auto corner = [&](int b, int c) {
-          return ((b >> 2) ? base1 : base0) + c * (FHY * FHX) + ((b >> 1) & 1) * FHX + (b & 1);
-        };
-        #pragma unroll
-        for (int t = 0; t < NPT; ++t) {
+        auto cu = [&](int b, int c) { return ((b >> 2) ? U1 : U0)[c * FPL + ((b >> 1) & 1) * FHX + (b & 1)]; };
+        auto cd = [&](int b, int c) { return ((b >> 2) ? D1 : D0)[c * FPL + ((b >> 1) & 1) * FHX + (b & 1)]; };
+        if constexpr (TET) {
+          // lanes (T1, T2): T1 = corners {0, 3, 5, 6}, T2 = {1, 2, 4, 7} as (a, b, c, e);
+          // with X = (b-a | a-b) and Y = (c-e | e-c):
+          //   d/dx = X + Y,  d/dy = (X - Y) * (1 | -1),  d/dz = (c-a) + (e-b)   (all / 2h)
+          const float2 i2 = bc2(inv2h), i2m = make_float2(inv2h, -inv2h);
+          auto grad_u = [&](float2 (&G)[3][3]) {
+            #pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float2 u0 = cu(0, c), u1 = cu(1, c), u2 = cu(2, c), u3 = cu(3, c);
+              const float2 u4 = cu(4, c), u5 = cu(5, c), u6 = cu(6, c), u7 = cu(7, c);
+              const float2 dca = make_float2(fd(u5, u0), fd(u4, u1));
+              const float2 deb = make_float2(fd(u6, u3), fd(u7, u2));
+              const float2 X = make_float2(fd(u3, u0), fd(u1, u2));
+              const float2 Y = make_float2(fd(u5, u6), fd(u7, u4));
+              G[c][2] = mul2(add2(dca, deb), i2);
+              G[c][0] = mul2(add2(X, Y), i2);
+              G[c][1] = mul2(sub2(X, Y), i2m);
+            }
+          };
+          auto grad_d = [&](float2 (&G)[3][3]) {
+            #pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float v0 = cd(0, c), v1 = cd(1, c), v2 = cd(2, c), v3 = cd(3, c);
+              const float v4 = cd(4, c), v5 = cd(5, c), v6 = cd(6, c), v7 = cd(7, c);
+              const float2 gca = sub2(make_float2(v5, v4), make_float2(v0, v1));
+              const float2 geb = sub2(make_float2(v6, v7), make_float2(v3, v2));
+              const float2 gX = sub2(make_float2(v3, v1), make_float2(v0, v2));
+              const float2 gY = sub2(make_float2(v5, v7), make_float2(v6, v4));
+              G[c][2] = mul2(add2(gca, geb), i2);
+              G[c][0] = mul2(add2(gX, gY), i2);
+              G[c][1] = mul2(sub2(gX, gY), i2m);
+            }
+          };
+          float2 G[3][3];
+          grad_u(G);
+          float2* o = (float2*)sSf + vslot;
+          float2* ot = (float2*)sTf + vslot;
+          if constexpr (FS) {
+            float2 H[3][3], S[3][3];
+            #pragma unroll
+            for (int c = 0; c < 3; ++c)
+              #pragma unroll
+              for (int d = 0; d < 3; ++d) H[c][d] = add2(bc2(eps[c][d]), G[c][d]);
+            #pragma unroll
+            for (int p = 0; p < 3; ++p)
+              #pragma unroll
+              for (int q = p; q < 3; ++q) {
+                float2 v = add2(H[p][q], H[q][p]);
+                #pragma unroll
+                for (int k = 0; k < 3; ++k) v = fma2(H[k][p], H[k][q], v);
+                S[p][q] = S[q][p] = mul2(bc2(0.5f), v);
+              }
+            const float2 tr = add2(add2(S[0][0], S[1][1]), S[2][2]);
+            const float2 ltr = mul2(bc2(lam), tr);
+            #pragma unroll
+            for (int p = 0; p < 3; ++p)
+              #pragma unroll
+              for (int q = p; q < 3; ++q) {
+                const float2 v = mul2(bc2(2.f * mu), S[p][q]);
+                S[p][q] = S[q][p] = (p == q) ? add2(v, ltr) : v;
+              }
+            float2 s2v = make_float2(0.f, 0.f);
+            #pragma unroll
+            for (int c = 0; c < 3; ++c)
+              #pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                float2 v = S[c][d];
+                #pragma unroll
+                for (int k = 0; k < 3; ++k) v = fma2(H[c][k], S[k][d], v);
+                o[(3 * c + d) * NVL] = v;
+                s2v = fma2(v, v, s2v);
+              }
+            if (own) acc_sp.add(make_float2(0.5f * (s2v.x + s2v.y), 0.f));
+          } else {
+            const float2 exx = add2(bc2(eps[0][0]), G[0][0]), eyy = add2(bc2(eps[1][1]), G[1][1]);
+            const float2 ezz = add2(bc2(eps[2][2]), G[2][2]);
+            const float2 eyz = fma2(bc2(0.5f), add2(G[1][2], G[2][1]), bc2(eps[1][2]));
+            const float2 exz = fma2(bc2(0.5f), add2(G[0][2], G[2][0]), bc2(eps[0][2]));
+            const float2 exy = fma2(bc2(0.5f), add2(G[0][1], G[1][0]), bc2(eps[0][1]));
+            const float2 ltr = mul2(bc2(lam), add2(add2(exx, eyy), ezz));
+            const float2 m2 = bc2(2.f * mu);
+            const float2 sxx = fma2(m2, exx, ltr), syy = fma2(m2, eyy, ltr), szz = fma2(m2, ezz, ltr);
+            const float2 syz = mul2(m2, eyz), sxz = mul2(m2, exz), sxy = mul2(m2, exy);
+            o[0 * NVL] = sxx;
+            o[1 * NVL] = syy;
+            o[2 * NVL] = szz;
+            o[3 * NVL] = syz;
+            o[4 * NVL] = sxz;
+            o[5 * NVL] = sxy;
+            if (own) {
+              const float2 dg = fma2(szz, szz, fma2(syy, syy, mul2(sxx, sxx)));
+              const float2 od = fma2(sxy, sxy, fma2(sxz, sxz, mul2(syz, syz)));
+              const float2 s2v = fma2(bc2(2.f), od, dg);
+              acc_sp.add(make_float2(0.5f * (s2v.x + s2v.y), 0.f));
+            }
+          }
+          if (tau_L) {
+            // reference flux (few layers): the gradient of Delta, or of u~ again
+            float2 T[3][3];
+            if (tau_from_delta) grad_d(T);
+            else grad_u(T);
+            #pragma unroll
+            for (int c = 0; c < 3; ++c)
+              #pragma unroll
+              for (int d = 0; d < 3; ++d) ot[(3 * c + d) * NVL] = ref_flux2(T, c, d, lam0, mu0, iso);
+          }
+        } else {
+          // HEX1: one point at the voxel centre
           float G[3][3], GD[3][3];
           #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            if constexpr (SCHEME == SCHEME_TETRA2) {
-              // T1 = {000, 110, 101, 011} = corners {0, 3, 5, 6}; T2 = {100, 010, 001, 111} =
-              // corners {1, 2, 4, 7}; with (a, b, c, e) in that order the two gradients are
-              //   T1: ((b-a) + (c-e), (b-a) - (c-e), (c-a) + (e-b)) / 2h
-              //   T2: ((a-b) + (e-c), (e-c) - (a-b), (c-a) + (e-b)) / 2h
-              const int ia = corner(t ? 1 : 0, c), ib = corner(t ? 2 : 3, c);
-              const int ic = corner(t ? 4 : 5, c), ie = corner(t ? 7 : 6, c);
-              const float ah = sH[ia], al = sL[ia], bh = sH[ib], bl = sL[ib];
-              const float ch = sH[ic], cl = sL[ic], eh = sH[ie], el = sL[ie];
-              const float d_ca = fdiff(ch, cl, ah, al), d_eb = fdiff(eh, el, bh, bl);
-              G[c][2] = (d_ca + d_eb) * inv2h;
-              if (t == 0) {
-                const float d_ba = fdiff(bh, bl, ah, al), d_ce = fdiff(ch, cl, eh, el);
-                G[c][0] = (d_ba + d_ce) * inv2h;
-                G[c][1] = (d_ba - d_ce) * inv2h;
-              } else {
-                const float e_ab = fdiff(ah, al, bh, bl), e_ec = fdiff(eh, el, ch, cl);
-                G[c][0] = (e_ab + e_ec) * inv2h;
-                G[c][1] = (e_ec - e_ab) * inv2h;
-              }
-              if (need_gd) {
-                const float A = sD[ia], B = sD[ib], Cc = sD[ic], E = sD[ie];
-                GD[c][2] = ((Cc - A) + (E - B)) * inv2h;
-                if (t == 0) {
-                  GD[c][0] = ((B - A) + (Cc - E)) * inv2h;
-                  GD[c][1] = ((B - A) - (Cc - E)) * inv2h;
-                } else {
-                  GD[c][0] = ((A - B) + (E - Cc)) * inv2h;
-                  GD[c][1] = ((E - Cc) - (A - B)) * inv2h;
-                }
-              }
-            } else {
-              float uh[8], ul[8];
+            float2 u[8];
+            #pragma unroll
+            for (int b = 0; b < 8; ++b) u[b] = cu(b, c);
+            auto d = [&](int p, int q) { return fd(u[p], u[q]); };
+            G[c][0] = (d(1, 0) + d(3, 2) + d(5, 4) + d(7, 6)) * inv4h;
+            G[c][1] = (d(2, 0) + d(3, 1) + d(6, 4) + d(7, 5)) * inv4h;
+            G[c][2] = (d(4, 0) + d(5, 1) + d(6, 2) + d(7, 3)) * inv4h;
+            if (need_gd) {
+              float ud[8];
               #pragma unroll
-              for (int b = 0; b < 8; ++b) {
-                const int si = corner(b, c);
-                uh[b] = sH[si];
-                ul[b] = sL[si];
-              }
-              auto d = [&](int p, int q) { return fdiff(uh[p], ul[p], uh[q], ul[q]); };
-              G[c][0] = (d(1, 0) + d(3, 2) + d(5, 4) + d(7, 6)) * inv4h;
-              G[c][1] = (d(2, 0) + d(3, 1) + d(6, 4) + d(7, 5)) * inv4h;
-              G[c][2] = (d(4, 0) + d(5, 1) + d(6, 2) + d(7, 3)) * inv4h;
-              if (need_gd) {
-                float ud[8];
-                #pragma unroll
-                for (int b = 0; b < 8; ++b) ud[b] = sD[corner(b, c)];
-                GD[c][0] = ((ud[1] - ud[0]) + (ud[3] - ud[2]) + (ud[5] - ud[4]) + (ud[7] - ud[6])) * inv4h;
-                GD[c][1] = ((ud[2] - ud[0]) + (ud[3] - ud[1]) + (ud[6] - ud[4]) + (ud[7] - ud[5])) * inv4h;
-                GD[c][2] = ((ud[4] - ud[0]) + (ud[5] - ud[1]) + (ud[6] - ud[2]) + (ud[7] - ud[3])) * inv4h;
-              }
+              for (int b = 0; b < 8; ++b) ud[b] = cd(b, c);
+              GD[c][0] = ((ud[1] - ud[0]) + (ud[3] - ud[2]) + (ud[5] - ud[4]) + (ud[7] - ud[6])) * inv4h;
+              GD[c][1] = ((ud[2] - ud[0]) + (ud[3] - ud[1]) + (ud[6] - ud[4]) + (ud[7] - ud[5])) * inv4h;
+              GD[c][2] = ((ud[4] - ud[0]) + (ud[5] - ud[1]) + (ud[6] - ud[2]) + (ud[7] - ud[3])) * inv4h;
             }
           }
-          float* o = out + t * QV * NVL;
+          float* o = sSf + vslot;
+          float* ot = sTf + vslot;
           if constexpr (FS) {
             float H[3][3], S[3][3];
             #pragma unroll
@@ -343,7 +485,7 @@ k_residual_f32(ResidualArgs a) {
                 float v = H[p][q] + H[q][p];
                 #pragma unroll
                 for (int k = 0; k < 3; ++k) v = fmaf(H[k][p], H[k][q], v);
-                S[p][q] = S[q][p] = 0.5f * v;   // E for now
+                S[p][q] = S[q][p] = 0.5f * v;
               }
             const float tr = S[0][0] + S[1][1] + S[2][2];
             #pragma unroll
@@ -361,115 +503,151 @@ k_residual_f32(ResidualArgs a) {
                 o[(3 * c + dd) * NVL] = v;
                 s2 = fmaf(v, v, s2);
               }
-            if (tau_L) {
-              #pragma unroll
-              for (int c = 0; c < 3; ++c)
-                #pragma unroll
-                for (int dd = 0; dd < 3; ++dd)
-                  o[(NS + 3 * c + dd) * NVL] =
-                      (tau_from_delta ? ref_flux(GD, c, dd, lam0, mu0, iso) : ref_flux(G, c, dd, lam0, mu0, iso));
-            }
-            if (own) acc_s2.add(w * s2);
-            continue;
+            if (own) acc_sp.add(make_float2(s2, 0.f));
+          } else {
+            const float exx = eps[0][0] + G[0][0], eyy = eps[1][1] + G[1][1];
+            const float ezz = eps[2][2] + G[2][2];
+            const float eyz = eps[1][2] + 0.5f * (G[1][2] + G[2][1]);
+            const float exz = eps[0][2] + 0.5f * (G[0][2] + G[2][0]);
+            const float exy = eps[0][1] + 0.5f * (G[0][1] + G[1][0]);
+            const float tr = exx + eyy + ezz;
+            const float sxx = lam * tr + 2.f * mu * exx, syy = lam * tr + 2.f * mu * eyy;
+            const float szz = lam * tr + 2.f * mu * ezz;
+            const float syz = 2.f * mu * eyz, sxz = 2.f * mu * exz, sxy = 2.f * mu * exy;
+            o[0 * NVL] = sxx;
+            o[1 * NVL] = syy;
+            o[2 * NVL] = szz;
+            o[3 * NVL] = syz;
+            o[4 * NVL] = sxz;
+            o[5 * NVL] = sxy;
+            if (own) acc_sp.add(make_float2(sxx * sxx + syy * syy + szz * szz + 2.f * (syz * syz + sxz * sxz + sxy * sxy), 0.f));
           }
-          const float exx = eps[0][0] + G[0][0], eyy = eps[1][1] + G[1][1];
-          const float ezz = eps[2][2] + G[2][2];
-          const float eyz = eps[1][2] + 0.5f * (G[1][2] + G[2][1]);
-          const float exz = eps[0][2] + 0.5f * (G[0][2] + G[2][0]);
-          const float exy = eps[0][1] + 0.5f * (G[0][1] + G[1][0]);
-          const float tr = exx + eyy + ezz;
-          const float sxx = lam * tr + 2.f * mu * exx, syy = lam * tr + 2.f * mu * eyy;
-          const float szz = lam * tr + 2.f * mu * ezz;
-          const float syz = 2.f * mu * eyz, sxz = 2.f * mu * exz, sxy = 2.f * mu * exy;
-          o[0 * NVL] = sxx;
-          o[1 * NVL] = syy;
-          o[2 * NVL] = szz;
-          o[3 * NVL] = syz;
-          o[4 * NVL] = sxz;
-          o[5 * NVL] = sxy;
           if (tau_L) {
             #pragma unroll
             for (int c = 0; c < 3; ++c)
               #pragma unroll
               for (int dd = 0; dd < 3; ++dd)
-                o[(NS + 3 * c + dd) * NVL] =
-                    (tau_from_delta ? ref_flux(GD, c, dd, lam0, mu0, iso) : ref_flux(G, c, dd, lam0, mu0, iso));
+                ot[(3 * c + dd) * NVL] =
+                    tau_from_delta ? ref_flux1(GD, c, dd, lam0, mu0, iso) : ref_flux1(G, c, dd, lam0, mu0, iso);
           }
-          if (own) acc_s2.add(w * (sxx * sxx + syy * syy + szz * szz + 2.f * (syz * syz + sxz * sxz + sxy * sxy)));
         }
       }
     }
+    cp_async_wait_1();   // plane L+2 has landed (L+3 may still be in flight)
     __syncthreads();
 
     // ---------------- phase B: gather into node L (lower corner) and node L+1 (upper corner)
+    float Fn[3] = {0.f, 0.f, 0.f}, F0n[3] = {0.f, 0.f, 0.f};
     if (active) {
-      #pragma unroll
-      for (int ey = 0; ey < 2; ++ey) {
+      if constexpr (TET) {
+        // voxels whose lower-corner point is T1 accumulate into A = (node L | node L+1),
+        // the others into B = (node L+1 | node L)
+        float2 A[3], B[3], A0[3], B0[3];
         #pragma unroll
-        for (int ex = 0; ex < 2; ++ex) {
-          const int v = (ty + ey) * FVX + (tx + ex);
-          const int dx = 1 - ex, dy = 1 - ey;
-          const float sx = dx ? 1.f : -1.f, sy = dy ? 1.f : -1.f;
-          // node L is corner (dx, dy, 0) of the voxel, node L+1 its corner (dx, dy, 1);
-          // TETRA2: the point whose tetrahedron holds the corner (T1 = even parity)
-          const int tlo = (SCHEME == SCHEME_TETRA2) ? ((dx + dy) & 1) : 0;
-          const int thi = (SCHEME == SCHEME_TETRA2) ? (1 - tlo) : 0;
-          auto gather = [&](float (&F)[3], float (&F0)[3], int t, float sz) {
-            const float* q = sV + t * QV * NVL + v;
+        for (int c = 0; c < 3; ++c) A[c] = B[c] = A0[c] = B0[c] = make_float2(0.f, 0.f);
+        #pragma unroll
+        for (int ey = 0; ey < 2; ++ey) {
+          #pragma unroll
+          for (int ex = 0; ex < 2; ++ex) {
+            const int v = (ty + ey) * FVX + (tx + ex);
+            const int dx = 1 - ex, dy = 1 - ey;
+            const bool tlo = (dx + dy) & 1;
+            const float2 SX = bc2(dx ? 1.f : -1.f), SY = bc2(dy ? 1.f : -1.f);
+            const float2 SZ = tlo ? make_float2(1.f, -1.f) : make_float2(-1.f, 1.f);
+            const float2* q = (const float2*)sSf + v;
+            const float2* qt = (const float2*)sTf + v;
+            auto gather = [&](float2 (&F)[3], float2 (&F0)[3]) {
+              if constexpr (FS) {
+                #pragma unroll
+                for (int c = 0; c < 3; ++c)
+                  F[c] = fma2(q[(3 * c + 2) * NVL], SZ, fma2(q[(3 * c + 1) * NVL], SY, fma2(q[(3 * c) * NVL], SX, F[c])));
+              } else {
+                const float2 sxx = q[0], syy = q[NVL], szz = q[2 * NVL];
+                const float2 syz = q[3 * NVL], sxz = q[4 * NVL], sxy = q[5 * NVL];
+                F[0] = fma2(sxz, SZ, fma2(sxy, SY, fma2(sxx, SX, F[0])));
+                F[1] = fma2(syz, SZ, fma2(syy, SY, fma2(sxy, SX, F[1])));
+                F[2] = fma2(szz, SZ, fma2(syz, SY, fma2(sxz, SX, F[2])));
+              }
+              if (tau_L) {
+                #pragma unroll
+                for (int c = 0; c < 3; ++c)
+                  F0[c] = fma2(qt[(2 + 3 * c) * NVL], SZ,
+                               fma2(qt[(1 + 3 * c) * NVL], SY, fma2(qt[(3 * c) * NVL], SX, F0[c])));
+              }
+            };
+            if (tlo) gather(B, B0);
+            else gather(A, A0);
+          }
+        }
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Fc[c] += A[c].x + B[c].y;
+          Fn[c] = A[c].y + B[c].x;
+          F0c[c] += A0[c].x + B0[c].y;
+          F0n[c] = A0[c].y + B0[c].x;
+        }
+      } else {
+        #pragma unroll
+        for (int ey = 0; ey < 2; ++ey) {
+          #pragma unroll
+          for (int ex = 0; ex < 2; ++ex) {
+            const int v = (ty + ey) * FVX + (tx + ex);
+            const int dx = 1 - ex, dy = 1 - ey;
+            const float sx = dx ? 1.f : -1.f, sy = dy ? 1.f : -1.f;
+            const float* q = sSf + v;
+            const float* qt = sTf + v;
+            float t[3];
             if constexpr (FS) {
               #pragma unroll
-              for (int c = 0; c < 3; ++c)
-                F[c] += q[(3 * c) * NVL] * sx + q[(3 * c + 1) * NVL] * sy + q[(3 * c + 2) * NVL] * sz;
+              for (int c = 0; c < 3; ++c) t[c] = q[(3 * c) * NVL] * sx + q[(3 * c + 1) * NVL] * sy;
+              #pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                Fc[c] += t[c] - q[(3 * c + 2) * NVL];
+                Fn[c] += t[c] + q[(3 * c + 2) * NVL];
+              }
             } else {
               const float sxx = q[0], syy = q[NVL], szz = q[2 * NVL];
               const float syz = q[3 * NVL], sxz = q[4 * NVL], sxy = q[5 * NVL];
-              F[0] += sxx * sx + sxy * sy + sxz * sz;
-              F[1] += sxy * sx + syy * sy + syz * sz;
-              F[2] += sxz * sx + syz * sy + szz * sz;
+              t[0] = sxx * sx + sxy * sy;
+              t[1] = sxy * sx + syy * sy;
+              t[2] = sxz * sx + syz * sy;
+              Fc[0] += t[0] - sxz; Fn[0] += t[0] + sxz;
+              Fc[1] += t[1] - syz; Fn[1] += t[1] + syz;
+              Fc[2] += t[2] - szz; Fn[2] += t[2] + szz;
             }
             if (tau_L) {
               #pragma unroll
-              for (int c = 0; c < 3; ++c)
-                F0[c] += q[(NS + 3 * c) * NVL] * sx + q[(NS + 1 + 3 * c) * NVL] * sy + q[(NS + 2 + 3 * c) * NVL] * sz;
+              for (int c = 0; c < 3; ++c) {
+                const float tt = qt[(3 * c) * NVL] * sx + qt[(1 + 3 * c) * NVL] * sy;
+                F0c[c] += tt - qt[(2 + 3 * c) * NVL];
+                F0n[c] += tt + qt[(2 + 3 * c) * NVL];
+              }
             }
-          };
-          gather(Fc, F0c, tlo, -1.f);
-          gather(Fn, F0n, thi, 1.f);
+          }
         }
       }
       // node plane L is complete
       if (fin) {
-        const int k = L;
-        const long long n = nL;
-        const int idx[3] = {i, j, k};
-        // nodes on no non-periodic face (most of them) skip the per-component face checks
-        bool face = false;
-        #pragma unroll
-        for (int d = 0; d < 3; ++d) face |= !g.periodic[d] && (idx[d] == 0 || idx[d] == g.nn[d] - 1);
-        float p2loc = 0.f, gloc[4] = {0.f, 0.f, 0.f, 0.f};
+        // z faces (uniform over the layer)
+        int zf = -1;
+        if (!g.periodic[2]) zf = (L == 0) ? 0 : (L == nnz - 1) ? 1 : -1;
+        float p2loc = 0.f;
+        float2 g01 = make_float2(0.f, 0.f), g23 = make_float2(0.f, 0.f);
         #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          float invW = 1.f;
-          bool dof = true;
-          if (face) {
-            #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              if (g.periodic[d]) continue;
-              int f = -1;
-              if (idx[d] == 0) f = 0;
-              else if (idx[d] == g.nn[d] - 1) f = 1;
-              if (f < 0) continue;
-              const int t = g.bc[d][f][c];
-              if (t == BC_D) dof = false;
-              else if (t == BC_N) invW *= 2.f;
-            }
+          bool dof = !((fxy >> (3 * c)) & 1);
+          float invW = (float)(1 << ((fxy >> (3 * c + 1)) & 3));
+          if (zf >= 0) {
+            const int t = g.bc[2][zf][c];
+            if (t == BC_D) dof = false;
+            else if (t == BC_N) invW *= 2.f;
           }
           float pv = 0.f, a0v = 0.f;
           if (dof) {
             pv = -Fc[c] * c4h * invW;
             if (tau_on) a0v = F0c[c] * c4h * invW;
           }
-          const long long e = c * NN + n;
+          const long long e = c * NN + nL;
           const bool free_dof = dof && !((cm >> c) & 1);
           if (free_dof) p2loc = fmaf(pv, pv, p2loc);
           if (po) po[e] = pv;
@@ -478,43 +656,53 @@ k_residual_f32(ResidualArgs a) {
             const float rv = dof ? (pv - pg[c] + a0v) : 0.f;
             ro[e] = rv;
             if (free_dof) {
-              #pragma unroll
-              for (int q = 0; q < 4; ++q) gloc[q] = fmaf(rv, (q == rslot ? rv : pr[q][c]), gloc[q]);
+              const float2 r2 = bc2(rv);
+              g01 = fma2(r2, make_float2(rv, pr[0][c]), g01);
+              g23 = fma2(r2, make_float2(pr[1][c], pr[2][c]), g23);
             }
           }
         }
-        acc_p2.add(p2loc);
+        acc_sp.add(make_float2(0.f, p2loc));
         if (ro) {
-          #pragma unroll
-          for (int q = 0; q < 4; ++q) acc_g[q].add(gloc[q]);
+          acc_g01.add(g01);
+          acc_g23.add(g23);
         }
       }
-      #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        Fc[c] = Fn[c];
-        F0c[c] = F0n[c];
-        Fn[c] = 0.f;
-        F0n[c] = 0.f;
-      }
     }
-    cp_async_wait_all();
+    #pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Fc[c] = Fn[c];
+      F0c[c] = F0n[c];
+    }
+    // the gather must finish before the next layer's phase A rewrites the point data
     __syncthreads();
   }
+  cp_async_wait_all();
 
   // block reduction: compensated FP32 pairs across the warp, FP64 across warps
-  Acc2 v[6] = {acc_s2, acc_p2, acc_g[0], acc_g[1], acc_g[2], acc_g[3]};
+  Acc2x2 v3[3] = {acc_sp, acc_g01, acc_g23};
   const int warp = tid >> 5, lane = tid & 31;
   #pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    Acc2 t = v[q];
+  for (int q = 0; q < 3; ++q) {
+    Acc2x2 t = v3[q];
     #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      const float os = __shfl_down_sync(0xffffffffu, t.s, off);
-      const float oc = __shfl_down_sync(0xffffffffu, t.c, off);
+      float2 os, oc;
+      os.x = __shfl_down_sync(0xffffffffu, t.s.x, off);
+      os.y = __shfl_down_sync(0xffffffffu, t.s.y, off);
+      oc.x = __shfl_down_sync(0xffffffffu, t.c.x, off);
+      oc.y = __shfl_down_sync(0xffffffffu, t.c.y, off);
       t.add(os);
-      t.c += oc;
+      t.c = add2(t.c, oc);
     }
-    if (lane == 0) sRed[q][warp] = t.value();
+    if (lane == 0) {
+      // partial index: 0 sigma:sigma, 1 p^2, 2 + Gram slot
+      const int rs = rslot < 0 ? 0 : rslot;
+      const int i0 = q == 0 ? 0 : 2 + (rs + 2 * (q - 1)) % 4;
+      const int i1 = q == 0 ? 1 : 2 + (rs + 2 * (q - 1) + 1) % 4;
+      sRed[i0][warp] = t.value(0);
+      sRed[i1][warp] = t.value(1);
+    }
   }
   __syncthreads();
   if (tid < 6) {
@@ -524,6 +712,7 @@ k_residual_f32(ResidualArgs a) {
     a.partials[6 * b + tid] = t;
   }
 }
+
 
 namespace {
 int resident_ctas() {
@@ -537,16 +726,64 @@ int resident_ctas() {
 }
 }  // namespace
 
-// z planes per CTA: about two waves of resident CTAs, at least 4 planes per CTA (each CTA
-// also processes the voxel layer below its first plane).
+// Modelled duration of the grid for a z chunk of zc planes: a CTA takes its chunk's voxel
+// layers (planes + 1) plus a start-up cost of about 4 layers (ring fill, constants, block
+// reduction); CTAs start in launch order (xy tiles, then z chunks) on the first free one of
+// S resident slots.  (Fits the measured chunk sweeps on 256 x 256 x 128 and 384 x 384 x 192
+// blocks to a few per cent.)
+static double zchunk_makespan(int nnz, long long bxy, int zc, int S) {
+  constexpr double C0 = 4.0;
+  const long long full = bxy * (nnz / zc);
+  const int rem = nnz % zc;
+  const double d = zc + 1 + C0;
+  // equal CTAs fill the slots round-robin: r slots end at (q + 1) d, the others at q d
+  const long long q = full / S, r = full % S;
+  std::priority_queue<double, std::vector<double>, std::greater<double>> slots;
+  double end = 0.0;
+  for (int k = 0; k < S; ++k) {
+    const double t = (k < r ? q + 1 : q) * d;
+    slots.push(t);
+    end = std::max(end, t);
+  }
+  if (rem) {
+    const double ds = rem + 1 + C0;
+    for (long long k = 0; k < bxy; ++k) {
+      const double t = slots.top() + ds;
+      slots.pop();
+      slots.push(t);
+      end = std::max(end, t);
+    }
+  }
+  return end;
+}
+
+// z planes per CTA: the chunk in [4, 64] with the shortest modelled duration (ties to the
+// larger chunk), cached per grid shape.
 int residual_f32_zchunk(const GridDev& g) {
   if (g.zc_override > 0) return g.zc_override;
-  long long bxy = (long long)((g.nn[0] + FTX - 1) / FTX) * ((g.nn[1] + FTY - 1) / FTY);
-  long long want = 2LL * resident_ctas();
-  long long zc = (g.nn[2] * bxy + want - 1) / want;
-  if (zc < 4) zc = 4;
-  if (zc > 64) zc = 64;
-  return (int)zc;
+  const long long bxy = (long long)((g.nn[0] + FTX - 1) / FTX) * ((g.nn[1] + FTY - 1) / FTY);
+  const int S = resident_ctas();
+  const int nnz = g.nn[2];
+  static std::mutex mu;
+  static std::map<std::tuple<int, long long, int>, int> cache;
+  const auto key = std::make_tuple(nnz, bxy, S);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  int best = 64;
+  double t_best = 1e300;
+  for (int zc = 64; zc >= 4; --zc) {
+    const double t = zchunk_makespan(nnz, bxy, zc, S);
+    if (t < t_best * (1.0 - 1e-9)) {
+      t_best = t;
+      best = zc;
+    }
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = best;
+  return best;
 }
 
 int residual_f32_tile(int axis) { return axis == 0 ? FTX : FTY; }
@@ -569,16 +806,21 @@ static int launch_f32_impl(const ResidualArgs& a, cudaStream_t s) {
   aa.f_inv2h = (float)(1.0 / (2.0 * a.g.h));
   aa.f_inv4h = (float)(1.0 / (4.0 * a.g.h));
   constexpr int NPT = (SCHEME == SCHEME_TETRA2) ? 2 : 1;
-  constexpr int QV = PointLayout<FS>::QV;
-  const size_t sm = (size_t)3 * FNP * FPLANE * sizeof(float) + (size_t)NPT * QV * NVL * sizeof(float) +
-                    (size_t)FNP * FHY * FHX;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_residual_f32<SCHEME, FS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  constexpr int NS = PointLayout<FS>::NS;
+  // ring: u~ pairs (8 B) and Delta (4 B) per position; stress and flux point data; phases
+  const size_t sm = (size_t)RING * 3 * FPL * (sizeof(float2) + sizeof(float)) +
+                    (size_t)(NS + 9) * NVL * NPT * sizeof(float) + (size_t)RING * FVY * PWX;
+  static_assert(RING * FVY * PWX >= RING * FPL, "phase ring holds either layout");
+  // word loads of the phases: every voxel row then starts on a 4-byte boundary
+  const bool phw = a.g.nvox[0] % 4 == 0 && !a.g.periodic[0] && ((uintptr_t)a.phase & 3) == 0;
+  auto k = phw ? k_residual_f32<SCHEME, FS, true> : k_residual_f32<SCHEME, FS, false>;
+  static bool attr[2] = {false, false};
+  if (!attr[phw]) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    attr = true;
+    attr[phw] = true;
   }
-  k_residual_f32<SCHEME, FS><<<grd, FTHREADS, sm, s>>>(aa);
+  k<<<grd, FTHREADS, sm, s>>>(aa);
   return (int)cudaGetLastError();
 }
 
