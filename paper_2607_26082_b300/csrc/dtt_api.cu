@@ -646,7 +646,7 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
       CKL(launch_acv_gram<T>(G->g, G->d_Rring, pr.acv, ctrl, s));
       CKL(launch_ctrl_acv(ctrl, pr.acv, pr.nacv, s));
     }
-    CKL(launch_acv_green_input<T>(G->g, G->d_Sring, G->d_Gring, G->d_Rring, ctrl, s));
+    CKL(launch_acv_green_input<T>(G->g, G->d_Sring, G->d_Gring, G->d_Gown, G->d_Rring, ctrl, exact ? 1 : 0, s));
   }
   prof_mark(3, s);
   dtt_status st = diff ? enqueue_green<T>(G, nullptr, G->d_Gring, (T*)G->spec2, (T*)G->spec, true, ctrl, 0, 3, exact)
@@ -903,6 +903,7 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
   if (s == DTT_OK) s = dalloc(&G->d_Sring, 5 * sizeof(void*));
   if (s == DTT_OK) s = dalloc(&G->d_Rring, 4 * sizeof(void*));
   if (s == DTT_OK) s = dalloc(&G->d_Gring, 4 * sizeof(void*));
+  if (s == DTT_OK) s = dalloc(&G->d_Gown, 4 * sizeof(void*));
   if (s == DTT_OK) s = dalloc(&G->phase, (size_t)G->NV);
   if (s == DTT_OK) s = dalloc(&G->d_lam, MAX_PHASE * sizeof(double));
   if (s == DTT_OK) s = dalloc(&G->d_mu, MAX_PHASE * sizeof(double));
@@ -954,6 +955,7 @@ dtt_status dtt_grid_create(dtt_grid** out, const int32_t nvox[3], double h, cons
     cudaError_t e = cudaMemcpy(G->d_Sring, G->S, 5 * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(G->d_Rring, G->R, 4 * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(G->d_Gring, G->Gr, 4 * sizeof(void*), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(G->d_Gown, G->Gr, 4 * sizeof(void*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(G->cmask, 0, (size_t)G->NN);
     if (e == cudaSuccess && s == DTT_OK) s = build_tile_z(G, std::vector<long long>());
     if (e == cudaSuccess) e = G->u64 ? cudaMemset(G->u64, 0, n3 * 8) : cudaMemset(G->uhi, 0, n3 * 4);
@@ -984,6 +986,7 @@ void dtt_grid_destroy(dtt_grid* G) {
   dfree(G->d_Sring);
   dfree(G->d_Rring);
   dfree(G->d_Gring);
+  dfree(G->d_Gown);
   dfree(G->phase);
   dfree(G->d_lam);
   dfree(G->d_mu);
@@ -1541,6 +1544,8 @@ dtt_status prepare_solve(dtt_grid* G, const dtt_solve_opts* opts) {
   for (int k = 0; k < 5; ++k) CK(cudaMemsetAsync(G->S[k], 0, n3 * G->esz, s));
   for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(G->R[k], 0, n3 * G->esz, s));
   for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(G->Gr[k], 0, n3 * G->esz, s));
+  // the Green-input ring points at the own buffers again (a solve may leave aliases of p)
+  CK(cudaMemcpyAsync(G->d_Gring, G->d_Gown, 4 * sizeof(void*), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(G->step, 0, n3 * G->esz, s));
   PartRegions pr = regions(G);
   ContactArgs ca = contact_args(G, pr.cont);
@@ -2075,6 +2080,8 @@ dtt_status reset_state(dtt_grid* G) {
   for (int k = 0; k < 5; ++k) CK(cudaMemsetAsync(G->S[k], 0, n3 * G->esz, s));
   for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(G->R[k], 0, n3 * G->esz, s));
   for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(G->Gr[k], 0, n3 * G->esz, s));
+  // the Green-input ring points at the own buffers again (a solve may leave aliases of p)
+  CK(cudaMemcpyAsync(G->d_Gring, G->d_Gown, 4 * sizeof(void*), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(G->step, 0, n3 * G->esz, s));
   CK(cudaStreamSynchronize(s));
   return DTT_OK;

@@ -41,6 +41,7 @@ struct dtt_grid {
   void** d_Sring = nullptr;
   void** d_Rring = nullptr;
   void** d_Gring = nullptr;
+  void** d_Gown = nullptr;    // the own Green-input buffers (d_Gring entries may alias the p ring)
 
   // material
   uint8_t* phase = nullptr;

@@ -510,20 +510,31 @@ __device__ __forceinline__ float acv_combine(float q0, float q1, float q2, float
   return v;
 }
 
-__global__ void k_acv_green_input_v4(long long total, void* const* P, void* const* Gr, void* const* R,
-                                     const Ctrl* ctrl) {
+__global__ void k_acv_green_input_v4(long long total, void* const* P, void** Gr, void* const* Gown, void* const* R,
+                                     const Ctrl* ctrl, int alias) {
   if (ctrl->done) return;
   const int i = ctrl->i_local;
-  float* gi = (float*)Gr[i % 4];
+  float* gi = (float*)Gown[i % 4];
   const long long n4 = total / 4;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // one thread sets this iteration's ring entry; the blocks read only the other entries
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   if (!ctrl->accel) {
-    const float* pi = (const float*)P[i == 0 ? ctrl->pslot : i % 4];
+    const int src = i == 0 ? ctrl->pslot : i % 4;
+    const float* pi = (const float*)P[src];
+    // g_i = p_i: the ring entry can point at p_i itself when its slot is i % 4, since the
+    // residual kernel rewrites that slot only at iteration i + 4, after g_i's last reader
+    if (alias && src == i % 4) {
+      if (lead) Gr[i % 4] = (void*)pi;
+      return;
+    }
+    if (lead) Gr[i % 4] = gi;
     for (long long e = t0; e < n4; e += stride) ((float4*)gi)[e] = ((const float4*)pi)[e];
     for (long long e = 4 * n4 + t0; e < total; e += stride) gi[e] = pi[e];
     return;
   }
+  if (lead) Gr[i % 4] = gi;
   // FP32 copies made by the control kernel: no per-thread FP64 conversion
   const float a0 = ctrl->alpha_f[0], a1 = ctrl->alpha_f[1], a2 = ctrl->alpha_f[2], a3 = ctrl->alpha_f[3];
   const float b0 = a0, b1 = a0 + a1, b2 = a0 + a1 + a2;
@@ -555,11 +566,11 @@ __global__ void k_acv_green_input_v4(long long total, void* const* P, void* cons
 }
 
 template <typename T>
-int launch_acv_green_input(const GridDev& g, void* const* pring, void* const* gring, void* const* rring,
-                           const Ctrl* ctrl, cudaStream_t s) {
+int launch_acv_green_input(const GridDev& g, void* const* pring, void** gring, void* const* gown, void* const* rring,
+                           const Ctrl* ctrl, int alias, cudaStream_t s) {
   long long total = 3 * g.nnodes;
   if constexpr (sizeof(T) == 4)
-    k_acv_green_input_v4<<<acv_blocks(g), SB, 0, s>>>(total, pring, gring, rring, ctrl);
+    k_acv_green_input_v4<<<acv_blocks(g), SB, 0, s>>>(total, pring, gring, gown, rring, ctrl, alias);
   else
     k_acv_green_input<T><<<acv_blocks(g), SB, 0, s>>>(total, pring, gring, rring, ctrl);
   return (int)cudaGetLastError();
@@ -894,8 +905,10 @@ template int launch_contact_proj_U<double>(const ContactArgs&, double*, float*, 
 template int launch_contact_proj_U<float>(const ContactArgs&, double*, float*, float*, float*, cudaStream_t);
 template int launch_acv_gram<double>(const GridDev&, void* const*, double*, const Ctrl*, cudaStream_t);
 template int launch_acv_gram<float>(const GridDev&, void* const*, double*, const Ctrl*, cudaStream_t);
-template int launch_acv_green_input<double>(const GridDev&, void* const*, void* const*, void* const*, const Ctrl*, cudaStream_t);
-template int launch_acv_green_input<float>(const GridDev&, void* const*, void* const*, void* const*, const Ctrl*, cudaStream_t);
+template int launch_acv_green_input<double>(const GridDev&, void* const*, void**, void* const*, void* const*, const Ctrl*,
+                                            int, cudaStream_t);
+template int launch_acv_green_input<float>(const GridDev&, void* const*, void**, void* const*, void* const*, const Ctrl*,
+                                           int, cudaStream_t);
 template int launch_acv_store<double>(const GridDev&, int, void* const*, void* const*, const double*, double*, const Ctrl*, cudaStream_t);
 template int launch_acv_store<float>(const GridDev&, int, void* const*, void* const*, const double*, double*, const Ctrl*, cudaStream_t);
 template int launch_acv_accel<double>(const GridDev&, int, void* const*, void* const*, double*, double*, const Ctrl*, cudaStream_t);

@@ -184,6 +184,143 @@ struct Dft<4, S> {
   }
 };
 
+// ---- two DFTs at once in the lanes of packed FP32x2 registers ----------------------------
+// P2 holds the same position of two independent sequences: re = (a.re, b.re), im =
+// (a.im, b.im); every butterfly and twiddle below is one packed instruction per part.
+struct P2 {
+  float2 re, im;
+};
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+  float2 r;
+  asm("{ .reg .b64 ra, rb, rr; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; sub.rn.f32x2 rr, ra, rb; mov.b64 {%0, %1}, rr; }"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2c(float v) { return make_float2(v, v); }
+__device__ __forceinline__ P2 padd(P2 a, P2 b) { return P2{f2add(a.re, b.re), f2add(a.im, b.im)}; }
+__device__ __forceinline__ P2 psub(P2 a, P2 b) { return P2{f2sub(a.re, b.re), f2sub(a.im, b.im)}; }
+// a + i T b (T = +1 or -1)
+template <int T>
+__device__ __forceinline__ P2 padd_i(P2 a, P2 b) {
+  return T > 0 ? P2{f2sub(a.re, b.im), f2add(a.im, b.re)} : P2{f2add(a.re, b.im), f2sub(a.im, b.re)};
+}
+
+// v * e^(S 2 pi i M / N) in both lanes
+template <int N, int M, int S>
+__device__ __forceinline__ P2 ptwmul(P2 v) {
+  constexpr int mm = ((M % N) + N) % N;
+  if constexpr (mm == 0) {
+    return v;
+  } else if constexpr (2 * mm == N) {
+    return P2{f2mul(v.re, f2c(-1.f)), f2mul(v.im, f2c(-1.f))};
+  } else if constexpr (4 * mm == N) {   // i S v
+    return S > 0 ? P2{f2mul(v.im, f2c(-1.f)), v.re} : P2{v.im, f2mul(v.re, f2c(-1.f))};
+  } else if constexpr (4 * mm == 3 * N) {   // -i S v
+    return S > 0 ? P2{v.im, f2mul(v.re, f2c(-1.f))} : P2{f2mul(v.im, f2c(-1.f)), v.re};
+  } else {
+    constexpr float c = (float)cos2pi(mm, N);
+    constexpr float s = (float)((double)S * sin2pi(mm, N));
+    return P2{f2fma(v.im, f2c(-s), f2mul(v.re, f2c(c))), f2fma(v.im, f2c(c), f2mul(v.re, f2c(s)))};
+  }
+}
+
+// Two in-place DFTs of N values (same plan as Dft, on packed pairs).
+template <int N, int S>
+struct Dft2 {
+  static constexpr int N1 = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 3);
+  static constexpr int N2 = N / N1;
+  __device__ __forceinline__ static void run(P2* v) {
+    P2 w[N];
+    sfor<0, N2>([&](auto j2c) {
+      constexpr int j2 = decltype(j2c)::value;
+      P2 t[N1];
+      sfor<0, N1>([&](auto j1c) {
+        constexpr int j1 = decltype(j1c)::value;
+        t[j1] = v[N2 * j1 + j2];
+      });
+      Dft2<N1, S>::run(t);
+      sfor<0, N1>([&](auto k1c) {
+        constexpr int k1 = decltype(k1c)::value;
+        w[j2 * N1 + k1] = ptwmul<N, j2 * k1, S>(t[k1]);
+      });
+    });
+    sfor<0, N1>([&](auto k1c) {
+      constexpr int k1 = decltype(k1c)::value;
+      P2 t[N2];
+      sfor<0, N2>([&](auto j2c) {
+        constexpr int j2 = decltype(j2c)::value;
+        t[j2] = w[j2 * N1 + k1];
+      });
+      Dft2<N2, S>::run(t);
+      sfor<0, N2>([&](auto k2c) {
+        constexpr int k2 = decltype(k2c)::value;
+        v[k1 + N1 * k2] = t[k2];
+      });
+    });
+  }
+};
+template <int S>
+struct Dft2<1, S> {
+  __device__ __forceinline__ static void run(P2*) {}
+};
+template <int S>
+struct Dft2<2, S> {
+  __device__ __forceinline__ static void run(P2* v) {
+    const P2 a = v[0], b = v[1];
+    v[0] = padd(a, b);
+    v[1] = psub(a, b);
+  }
+};
+template <int S>
+struct Dft2<3, S> {
+  __device__ __forceinline__ static void run(P2* v) {
+    constexpr float h = 0.8660254037844386f;
+    const P2 s = padd(v[1], v[2]), d = psub(v[1], v[2]);
+    const P2 m = P2{f2fma(s.re, f2c(-0.5f), v[0].re), f2fma(s.im, f2c(-0.5f), v[0].im)};
+    // m +- i S h d
+    v[0] = padd(v[0], s);
+    v[1] = P2{f2fma(d.im, f2c(-S * h), m.re), f2fma(d.re, f2c(S * h), m.im)};
+    v[2] = P2{f2fma(d.im, f2c(S * h), m.re), f2fma(d.re, f2c(-S * h), m.im)};
+  }
+};
+template <int S>
+struct Dft2<4, S> {
+  __device__ __forceinline__ static void run(P2* v) {
+    const P2 a = padd(v[0], v[2]), b = psub(v[0], v[2]);
+    const P2 c = padd(v[1], v[3]), d = psub(v[1], v[3]);
+    v[0] = padd(a, c);
+    v[2] = psub(a, c);
+    v[1] = padd_i<S>(b, d);
+    v[3] = padd_i<-S>(b, d);
+  }
+};
+
+// One DFT of N values (N even), natural order, of which the first NK outputs are formed:
+// the even- and odd-indexed halves run as the two lanes of one packed DFT of N / 2, then
+// X_k = E_k + w^k O_k and X_(k + N/2) = E_k - w^k O_k with w = e^(S 2 pi i / N).
+template <int N, int S, int NK = N>
+__device__ __forceinline__ void dft_split(C2* v) {
+  if constexpr (N % 2 != 0) {
+    Dft<N, S>::run(v);
+  } else {
+    constexpr int H = N / 2;
+    P2 t[H];
+#pragma unroll
+    for (int m = 0; m < H; ++m) t[m] = P2{make_float2(v[2 * m].x, v[2 * m + 1].x), make_float2(v[2 * m].y, v[2 * m + 1].y)};
+    Dft2<H, S>::run(t);
+    sfor<0, H>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      const C2 e = C2{t[k].re.x, t[k].im.x};
+      const C2 o = twmul<N, k, S>(C2{t[k].re.y, t[k].im.y});
+      if constexpr (k < NK) v[k] = cadd(e, o);
+      if constexpr (k + H < NK) v[k + H] = csub(e, o);
+    });
+  }
+}
+
 // ---- plan of one pass --------------------------------------------------------------
 template <int R>
 struct WPlan {
@@ -315,7 +452,7 @@ __device__ __forceinline__ void wfft(float* sr, float* si, const float2* tw1, co
   }
   __syncwarp();
 #pragma unroll
-  for (int q = 0; q < P; ++q) Dft<R, S>::run(z[q]);
+  for (int q = 0; q < P; ++q) dft_split<R, S>(z[q]);
 #pragma unroll
   for (int k1 = 1; k1 < R; ++k1) {
     float2 w = __ldg(tw1 + k1 * 32 + lane);   // e^(-2 pi i lane k1 / L)
@@ -340,7 +477,7 @@ __device__ __forceinline__ void wfft(float* sr, float* si, const float2* tw1, co
 #pragma unroll
   for (int l = 0; l < 32; ++l) x[l] = C2{sr[t * 33 + l], si[t * 33 + l]};
   __syncwarp();
-  Dft<32, S>::run(x);
+  dft_split<32, S, NK>(x);
 #pragma unroll
   for (int k2 = 0; k2 < NK; ++k2) X[k2] = x[k2];
 }
