@@ -221,9 +221,11 @@ def launches_per_iteration(has_rows, has_contact, acv):
 
 
 def launches_per_solve(iters, per_it, graph_iters=GRAPH_ITERS, prep=3):
-    """Graph launches cover whole multiples of graph_iters iterations (one more launch
-    detects the finish); prep = the start's projections."""
-    return ((iters + graph_iters) // graph_iters) * graph_iters * per_it + prep
+    """The solve's graph runs whole rounds of graph_iters iterations (the round after the
+    last Green step detects the finish), each round followed by the loop's condition kernel;
+    prep = the start's projections."""
+    rounds = (iters + graph_iters) // graph_iters
+    return rounds * (graph_iters * per_it + 1) + prep
 
 
 def max_over_ranks(value, world, device):
