@@ -312,11 +312,12 @@ def run_ours(args, rank, world, local):
     u_dev = torch.empty((3,) + tuple(gm.node_shape), dtype=torch.float64, device=dev)
     fp64_idx = set(spread(args.steps, args.fp64_steps))
     starts = {}                  # timed step -> (increment, start field on the device)
-    hist = {"u2": None, "fn": None, "u1": torch.empty_like(u_dev) if net is not None else None}
+    hist = {"u2": None, "u1": torch.empty_like(u_dev) if net is not None else None}
 
     def step(s, record_start=False, centers=None):
         """One increment: the learned arm keeps u~ of the increment before the previous
-        one and the previous reactions for the network's features."""
+        one for the network's features; the previous reactions are the grid's own (its last
+        solve), read on the device."""
         k = s % ncyc
         if record_start:
             if k == 0:
@@ -326,24 +327,21 @@ def run_ours(args, rank, world, local):
                 starts[s] = (k, u_dev.clone())
                 torch.cuda.current_stream().synchronize()
         if k == 0:
-            hist["u2"], hist["fn"] = None, None
+            hist["u2"] = None
         gm.dtt_move_indenter((centers if centers is not None else I["centers"])[k])
         init = dtt.INIT_ZERO if k == 0 else dtt.INIT_PREVIOUS
         if net is not None and k > 0:
             gm.dtt_get_fields(u_out=hist["u1"])          # u~ of increment k-1, before it is replaced
             depth = (dk[k - 2] if k >= 2 else 0.0, dk[k - 1], dk[k])
-            net.predict_increment(gm, hist["u2"], hist["fn"], depth)
+            net.predict_increment(gm, hist["u2"], None, depth)
             init = dtt.INIT_GUESS
         rep = gm.dtt_solve_step(tol, 20000, acv_mod=mod, init=init, graph_iters=GRAPH_ITERS)
         if rep.status != dtt.OK:
             raise RuntimeError("increment %d did not converge: %s" % (k, rep.as_dict()))
-        if net is not None:
-            if k > 0:
-                if hist["u2"] is None:
-                    hist["u2"] = torch.empty_like(u_dev)
-                hist["u2"], hist["u1"] = hist["u1"], hist["u2"]
-            hist["fn"] = torch.from_numpy(warmstart.contact_reactions(gm)).to(dev)
-            torch.cuda.current_stream().synchronize()   # the library reads it on its own stream
+        if net is not None and k > 0:
+            if hist["u2"] is None:
+                hist["u2"] = torch.empty_like(u_dev)
+            hist["u2"], hist["u1"] = hist["u1"], hist["u2"]
         return k, rep
 
     for s in range(args.warmup):

@@ -109,7 +109,8 @@ dtt_status dtt_net_predict(dtt_net* net, dtt_grid* grid);
  * u_prev2 = u~ of increment k-2 (device, 3 x n_nodes float64; NULL = zero); fn_prev = the
  * normal reactions of increment k-1 on its contact set and zero at the other surface nodes
  * (device, n_surface float64, the order of dtt_get_contact, whose fn holds the free nodes'
- * residual off the set); depth = {d_(k-2), d_(k-1), d_k} with 0 <= d_(k-2) < d_(k-1) <
+ * residual off the set; NULL: the grid's own reactions and contact set of its last solve,
+ * read on the device); depth = {d_(k-2), d_(k-1), d_k} with 0 <= d_(k-2) < d_(k-1) <
  * d_k (d_(k-2) = 0 with u_prev2 = NULL for the second increment).  DTT_ERR_STATE without
  * an indenter, DTT_ERR_ARG on bad depths. */
 

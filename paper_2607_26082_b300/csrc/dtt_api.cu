@@ -646,7 +646,8 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
       CKL(launch_acv_gram<T>(G->g, G->d_Rring, pr.acv, ctrl, s));
       CKL(launch_ctrl_acv(ctrl, pr.acv, pr.nacv, s));
     }
-    CKL(launch_acv_green_input<T>(G->g, G->d_Sring, G->d_Gring, G->d_Gown, G->d_Rring, ctrl, exact ? 1 : 0, s));
+    CKL(launch_acv_green_input<T>(G->g, G->d_Sring, G->d_Gring, G->d_Gown, G->d_Rring, ctrl, exact ? 1 : 0,
+                                  G->d_tile_z, s));
   }
   prof_mark(3, s);
   dtt_status st = diff ? enqueue_green<T>(G, nullptr, G->d_Gring, (T*)G->spec2, (T*)G->spec, true, ctrl, 0, 3, exact)

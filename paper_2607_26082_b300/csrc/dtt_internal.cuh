@@ -381,10 +381,12 @@ int launch_acv_gram(const GridDev& g, void* const* rring, double* partials, cons
                     cudaStream_t s);
 // gring: the ring of Green-input pointers read by the Green step (slot i % 4); gown: the
 // grid's own Green-input buffers.  alias (FP32, exact residual mode only): an iteration
-// without acceleration points gring[i % 4] at p_i's buffer instead of copying p_i.
+// without acceleration points gring[i % 4] at p_i's buffer instead of copying p_i, and an
+// accelerated one reads the R ring only in the tiles of tile_z (the residual kernel's
+// per-tile z ranges of constrained DOFs), where R_k and p_(k+1) can differ.
 template <typename T>
 int launch_acv_green_input(const GridDev& g, void* const* pring, void** gring, void* const* gown,
-                           void* const* rring, const Ctrl* ctrl, int alias, cudaStream_t s);
+                           void* const* rring, const Ctrl* ctrl, int alias, const int2* tile_z, cudaStream_t s);
 // Anderson on u~ (FP64 path): S ring of u~ copies, R = u~_i - S_{i-1}.
 template <typename T>
 int launch_acv_store(const GridDev& g, int acv_on, void* const* Sring, void* const* Rring,

@@ -338,7 +338,7 @@ dtt_status grid_features(dtt_net* N, dtt_grid* G, const Window& w) {
 dtt_status inc_setup(dtt_net* N, dtt_grid* G, const double* u2, const double* fn_prev, const double depth[3],
                      IncArgs& a) {
   if (!G->contact) return set_error(DTT_ERR_STATE, "no indenter set");
-  if (!fn_prev || !depth) return set_error(DTT_ERR_ARG, "null argument");
+  if (!depth) return set_error(DTT_ERR_ARG, "null argument");
   if (!(depth[0] >= 0.0) || !(depth[1] > depth[0]) || !(depth[2] > depth[1]))
     return set_error(DTT_ERR_ARG, "depths must satisfy 0 <= d_(k-2) < d_(k-1) < d_k");
   // the window: win_dep layers from the contact face inward, win_lat nodes across it
@@ -372,7 +372,9 @@ dtt_status inc_setup(dtt_net* N, dtt_grid* G, const double* u2, const double* fn
   a.dd = depth[2] - depth[1];
   a.nface = G->nface;
   a.node = G->d_face;
-  a.fn_prev = fn_prev;
+  // fn_prev = NULL: the grid's reactions of its last solve on that solve's contact set
+  a.fn_prev = fn_prev ? fn_prev : G->d_fn;
+  a.fn_act = fn_prev ? nullptr : G->d_active;
   for (int c = 0; c < 3; ++c) a.center[c] = G->center[c];
   a.radius = G->radius;
   std::memcpy(a.eps, G->eps, sizeof(a.eps));

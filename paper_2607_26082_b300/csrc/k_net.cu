@@ -603,7 +603,7 @@ __device__ __forceinline__ double inc_u1(const IncArgs& a, long long i) {
 __global__ void k_inc_fmax(IncArgs a) {
   float m = 0.f;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < a.nface; q += gridDim.x * blockDim.x)
-    m = fmaxf(m, (float)(-a.fn_prev[q]));
+    m = fmaxf(m, (float)(-inc_fn(a, q)));
   for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, off));
   if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax((int*)a.fmax, __float_as_int(m));
 }
@@ -660,7 +660,7 @@ __global__ void k_inc_surface(IncArgs a) {
   const float fm = *a.fmax;
   x[7] = 1.f;
   x[8] = fminf(8.f, fmaxf(-8.f, (float)(gap / a.dd)));
-  x[9] = fm > 0.f ? (float)(-a.fn_prev[q]) / fm : 0.f;
+  x[9] = fm > 0.f ? (float)(-inc_fn(a, q)) / fm : 0.f;
 }
 
 __global__ void k_inc_targets(IncArgs a, const double* __restrict__ ut, float* __restrict__ t,
@@ -759,7 +759,7 @@ __global__ void k_inc_active(IncArgs a, const float* __restrict__ y, int CY, flo
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.nface) return;
   const long long vw = grid_to_win(a, a.node[q]);
-  act[q] = (a.fn_prev[q] < 0.0 || (vw >= 0 && y[vw * CY + 3] > thr)) ? 1 : 0;
+  act[q] = (inc_fn(a, q) < 0.0 || (vw >= 0 && y[vw * CY + 3] > thr)) ? 1 : 0;
 }
 
 int launch_inc_fmax(const IncArgs& a, cudaStream_t s) {

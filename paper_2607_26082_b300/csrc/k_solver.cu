@@ -509,6 +509,16 @@ __device__ __forceinline__ float acv_combine(float q0, float q1, float q2, float
   v -= b2 * (r2 - q3 + g2);
   return v;
 }
+// the same combination where R_k = p_(k+1) (exact residual mode away from constrained DOFs):
+// R_k - p_(k+1) + g_k is then g_k exactly, so the result is the same bit for bit
+__device__ __forceinline__ float acv_combine_free(float q0, float q1, float q2, float q3, float g0, float g1, float g2,
+                                                  float a0, float a1, float a2, float a3, float b0, float b1, float b2) {
+  float v = a0 * q0 + a1 * q1 + a2 * q2 + a3 * q3;
+  v -= b0 * g0;
+  v -= b1 * g1;
+  v -= b2 * g2;
+  return v;
+}
 
 __global__ void k_acv_green_input_v4(long long total, void* const* P, void** Gr, void* const* Gown, void* const* R,
                                      const Ctrl* ctrl, int alias) {
@@ -548,6 +558,25 @@ __global__ void k_acv_green_input_v4(long long total, void* const* P, void** Gr,
   const float* g0 = (const float*)Gr[(i - 3) % 4];
   const float* g1 = (const float*)Gr[(i - 2) % 4];
   const float* g2 = (const float*)Gr[(i - 1) % 4];
+  if (alias) {
+    // exact residual mode: R_k = p_(k+1) bit for bit outside the tiles that hold constrained
+    // DOFs (their flux and projections), so the R ring is not read here; k_acv_green_fix
+    // recomputes those tiles' nodes from the full formula
+    for (long long e = t0; e < n4; e += stride) {
+      const float4 q0 = ((const float4*)p0)[e], q1 = ((const float4*)p1)[e], q2 = ((const float4*)p2)[e],
+                   q3 = ((const float4*)p3)[e];
+      const float4 h0 = ((const float4*)g0)[e], h1 = ((const float4*)g1)[e], h2 = ((const float4*)g2)[e];
+      float4 v;
+      v.x = acv_combine_free(q0.x, q1.x, q2.x, q3.x, h0.x, h1.x, h2.x, a0, a1, a2, a3, b0, b1, b2);
+      v.y = acv_combine_free(q0.y, q1.y, q2.y, q3.y, h0.y, h1.y, h2.y, a0, a1, a2, a3, b0, b1, b2);
+      v.z = acv_combine_free(q0.z, q1.z, q2.z, q3.z, h0.z, h1.z, h2.z, a0, a1, a2, a3, b0, b1, b2);
+      v.w = acv_combine_free(q0.w, q1.w, q2.w, q3.w, h0.w, h1.w, h2.w, a0, a1, a2, a3, b0, b1, b2);
+      ((float4*)gi)[e] = v;
+    }
+    for (long long e = 4 * n4 + t0; e < total; e += stride)
+      gi[e] = acv_combine_free(p0[e], p1[e], p2[e], p3[e], g0[e], g1[e], g2[e], a0, a1, a2, a3, b0, b1, b2);
+    return;
+  }
   for (long long e = t0; e < n4; e += stride) {
     const float4 q0 = ((const float4*)p0)[e], q1 = ((const float4*)p1)[e], q2 = ((const float4*)p2)[e],
                  q3 = ((const float4*)p3)[e];
@@ -565,14 +594,56 @@ __global__ void k_acv_green_input_v4(long long total, void* const* P, void** Gr,
                         b2);
 }
 
+// The accelerated Green input at the nodes of the tiles that hold constrained DOFs (one CTA
+// per tile of tx x ty node columns, its z range tile_z +- 1 layer): the full formula, after
+// k_acv_green_input_v4 has written the R-free form everywhere.
+__global__ void k_acv_green_fix(const GridDev g, void* const* P, void* const* Gr, void* const* Gown, void* const* R,
+                                const Ctrl* ctrl, const int2* __restrict__ tile_z, int tx, int ty) {
+  if (ctrl->done || !ctrl->accel) return;
+  const int2 zr = tile_z[blockIdx.x];
+  if (zr.x > zr.y) return;
+  const int ntx = (g.nn[0] + tx - 1) / tx;
+  const int x = (blockIdx.x % ntx) * tx + (int)threadIdx.x % tx;
+  const int y = (blockIdx.x / ntx) * ty + (int)threadIdx.x / tx;
+  if ((int)threadIdx.x >= tx * ty || x >= g.nn[0] || y >= g.nn[1]) return;
+  const int i = ctrl->i_local;
+  float* gi = (float*)Gown[i % 4];
+  const float a0 = ctrl->alpha_f[0], a1 = ctrl->alpha_f[1], a2 = ctrl->alpha_f[2], a3 = ctrl->alpha_f[3];
+  const float b0 = a0, b1 = a0 + a1, b2 = a0 + a1 + a2;
+  const float* p0 = (const float*)P[(i - 3) % 4];
+  const float* p1 = (const float*)P[(i - 2) % 4];
+  const float* p2 = (const float*)P[(i - 1) % 4];
+  const float* p3 = (const float*)P[i % 4];
+  const float* r0 = (const float*)R[(i - 3) % 4];
+  const float* r1 = (const float*)R[(i - 2) % 4];
+  const float* r2 = (const float*)R[(i - 1) % 4];
+  const float* g0 = (const float*)Gr[(i - 3) % 4];
+  const float* g1 = (const float*)Gr[(i - 2) % 4];
+  const float* g2 = (const float*)Gr[(i - 1) % 4];
+  const int z0 = max(zr.x - 1, 0), z1 = min(zr.y + 1, g.nn[2] - 1);
+  const long long plane = (long long)g.nn[0] * g.nn[1];
+  for (int z = z0; z <= z1; ++z)
+    for (int c = 0; c < 3; ++c) {
+      const long long e = c * g.nnodes + plane * z + (long long)g.nn[0] * y + x;
+      gi[e] = acv_combine(p0[e], p1[e], p2[e], p3[e], r0[e], r1[e], r2[e], g0[e], g1[e], g2[e], a0, a1, a2, a3, b0,
+                          b1, b2);
+    }
+}
+
 template <typename T>
 int launch_acv_green_input(const GridDev& g, void* const* pring, void** gring, void* const* gown, void* const* rring,
-                           const Ctrl* ctrl, int alias, cudaStream_t s) {
+                           const Ctrl* ctrl, int alias, const int2* tile_z, cudaStream_t s) {
   long long total = 3 * g.nnodes;
-  if constexpr (sizeof(T) == 4)
+  if constexpr (sizeof(T) == 4) {
     k_acv_green_input_v4<<<acv_blocks(g), SB, 0, s>>>(total, pring, gring, gown, rring, ctrl, alias);
-  else
+    if (alias) {
+      const int tx = residual_f32_tile(0), ty = residual_f32_tile(1);
+      const int ntiles = ((g.nn[0] + tx - 1) / tx) * ((g.nn[1] + ty - 1) / ty);
+      k_acv_green_fix<<<ntiles, tx * ty, 0, s>>>(g, pring, gring, gown, rring, ctrl, tile_z, tx, ty);
+    }
+  } else {
     k_acv_green_input<T><<<acv_blocks(g), SB, 0, s>>>(total, pring, gring, rring, ctrl);
+  }
   return (int)cudaGetLastError();
 }
 
@@ -906,9 +977,9 @@ template int launch_contact_proj_U<float>(const ContactArgs&, double*, float*, f
 template int launch_acv_gram<double>(const GridDev&, void* const*, double*, const Ctrl*, cudaStream_t);
 template int launch_acv_gram<float>(const GridDev&, void* const*, double*, const Ctrl*, cudaStream_t);
 template int launch_acv_green_input<double>(const GridDev&, void* const*, void**, void* const*, void* const*, const Ctrl*,
-                                            int, cudaStream_t);
+                                            int, const int2*, cudaStream_t);
 template int launch_acv_green_input<float>(const GridDev&, void* const*, void**, void* const*, void* const*, const Ctrl*,
-                                           int, cudaStream_t);
+                                           int, const int2*, cudaStream_t);
 template int launch_acv_store<double>(const GridDev&, int, void* const*, void* const*, const double*, double*, const Ctrl*, cudaStream_t);
 template int launch_acv_store<float>(const GridDev&, int, void* const*, void* const*, const double*, double*, const Ctrl*, cudaStream_t);
 template int launch_acv_accel<double>(const GridDev&, int, void* const*, void* const*, double*, double*, const Ctrl*, cudaStream_t);

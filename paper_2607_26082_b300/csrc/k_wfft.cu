@@ -529,7 +529,8 @@ __device__ __forceinline__ void wfill(float* sr, float* si, const float* __restr
 }  // namespace
 
 // MODE 0: transposed output through the tile; MODE 2: row output (or increment into u~).
-template <int R, int NW, int MODE>
+// TY, INV: transform type of the covered components and direction (one FFT body per kernel)
+template <int R, int NW, int MODE, int TY, bool INV>
 __global__ void __launch_bounds__(NW * 32, 16 / NW)
 k_wfft(WfftPass p, const Ctrl* ctrl) {
   using PL = WPlan<R>;
@@ -549,12 +550,11 @@ k_wfft(WfftPass p, const Ctrl* ctrl) {
   const int LENP = len | 1;   // row stride of the MODE 2 tile (odd: lanes of two rows spread)
   const int p0 = warp * P;
   const bool busy = 2 * p0 < nvalid;
-  wby_type(p.type[comp], [&](auto ty) {
-    constexpr int TY = decltype(ty)::value;
+  {
     constexpr bool quarter = (TY == T_DCT3 || TY == T_DST3);
     if (busy) {
       C2 X[NK];
-      if (p.inverse) {
+      if constexpr (INV) {
         wfill<R, TY, true>(sr, si, in + ib, p.in_row, p0, nvalid, len, n, lane);
         wfft<R, quarter ? 1 : -1, false, NK>(sr, si, p.tw1, p.ph, lane, X);
       } else {
@@ -569,8 +569,7 @@ k_wfft(WfftPass p, const Ctrl* ctrl) {
           const int k = k1 + R * k2;
           if (k < len) {
             float va, vb;
-            if (p.inverse) wpost<TY, true>(X[k2], k, n, p.sc, p.inv_n, p.ph, va, vb);
-            else wpost<TY, false>(X[k2], k, n, p.sc, p.inv_n, p.ph, va, vb);
+            wpost<TY, INV>(X[k2], k, n, p.sc, p.inv_n, p.ph, va, vb);
             if constexpr (MODE == 0) {
               tile[k * RPCP + ra] = va;
               tile[k * RPCP + ra + 1] = vb;
@@ -582,7 +581,7 @@ k_wfft(WfftPass p, const Ctrl* ctrl) {
         }
       }
     }
-  });
+  }
   __syncthreads();
   if constexpr (MODE == 0) {
     const long long ob = (long long)comp * p.NN + (long long)blockIdx.y * p.out_outer + row0;
@@ -641,7 +640,9 @@ k_wfft(WfftPass p, const Ctrl* ctrl) {
 
 // Fused z pass: forward z DTT of the rows (c, kx, ky), Green multiply (the Paux symbol
 // of Section 3.2.3 with the TETRA2 / HEX1 S_j), inverse z DTT, written transposed.
-template <int R, int NW>
+// TY: the transform type of every component the launch covers (one body per type keeps
+// the unrolled forward and inverse FFTs within the instruction cache)
+template <int R, int NW, int TY>
 __global__ void __launch_bounds__(NW * 32, 16 / NW)
 k_wfft_zg(WfftPass p, GreenTables gt, float l0, float m2, float ih2, int scheme, const Ctrl* ctrl) {
   using PL = WPlan<R>;
@@ -662,8 +663,7 @@ k_wfft_zg(WfftPass p, GreenTables gt, float l0, float m2, float ih2, int scheme,
   const bool busy = 2 * p0 < nvalid;
   const float sx = gt.sf[comp][0][kx], cx = gt.cpf[comp][0][kx];
   const float thr = gt.null_thr_f[comp];
-  wby_type(p.type[comp], [&](auto ty) {
-    constexpr int TY = decltype(ty)::value;
+  {
     constexpr bool quarter = (TY == T_DCT3 || TY == T_DST3);
     if (busy) {
       C2 X[NK];
@@ -732,7 +732,7 @@ k_wfft_zg(WfftPass p, GreenTables gt, float l0, float m2, float ih2, int scheme,
         }
       }
     }
-  });
+  }
   __syncthreads();
   const long long ob = (long long)comp * p.NN + (long long)kx * p.out_outer + row0;
   for (int e = threadIdx.x; e < len * RPC; e += NW * 32) {
@@ -775,23 +775,43 @@ int balanced_rows(int nrows) {
   return rpt < RPC ? rpt : RPC;
 }
 
+template <int R, int MODE, int TY, bool INV>
+int launch_pass_k(const WfftPass& q, dim3 grd, cudaStream_t s, const Ctrl* ctrl) {
+  const size_t sm = wfft_smem<R>(q.len, MODE == 0);
+  static size_t attr = 48 * 1024;
+  if (int e = wfft_attr(k_wfft<R, WNW, MODE, TY, INV>, sm, attr)) return e;
+  k_wfft<R, WNW, MODE, TY, INV><<<grd, WNW * 32, sm, s>>>(q, ctrl);
+  return (int)cudaGetLastError();
+}
+template <int R, int MODE, bool INV>
+int launch_pass_ty(int ty, const WfftPass& q, dim3 grd, cudaStream_t s, const Ctrl* ctrl) {
+  switch (ty) {
+    case T_DCT1: return launch_pass_k<R, MODE, T_DCT1, INV>(q, grd, s, ctrl);
+    case T_DCT3: return launch_pass_k<R, MODE, T_DCT3, INV>(q, grd, s, ctrl);
+    case T_DST1: return launch_pass_k<R, MODE, T_DST1, INV>(q, grd, s, ctrl);
+    default: return launch_pass_k<R, MODE, T_DST3, INV>(q, grd, s, ctrl);
+  }
+}
 template <int R>
 int launch_pass_R(const WfftPass& p0, int mode, int nouter, int ncomp, const Ctrl* ctrl, cudaStream_t s) {
   WfftPass p = p0;
   p.rpt = balanced_rows<R>(p.nrows);
-  dim3 grd((unsigned)((p.nrows + p.rpt - 1) / p.rpt), (unsigned)nouter, (unsigned)ncomp);
-  if (mode == 0) {
-    const size_t sm = wfft_smem<R>(p.len, true);
-    static size_t attr = 48 * 1024;
-    if (int e = wfft_attr(k_wfft<R, WNW, 0>, sm, attr)) return e;
-    k_wfft<R, WNW, 0><<<grd, WNW * 32, sm, s>>>(p, ctrl);
-  } else {
-    const size_t sm = wfft_smem<R>(p.len, false);
-    static size_t attr = 48 * 1024;
-    if (int e = wfft_attr(k_wfft<R, WNW, 2>, sm, attr)) return e;
-    k_wfft<R, WNW, 2><<<grd, WNW * 32, sm, s>>>(p, ctrl);
+  dim3 grd((unsigned)((p.nrows + p.rpt - 1) / p.rpt), (unsigned)nouter, 1u);
+  // one launch per run of consecutive components of equal type
+  for (int c = 0; c < ncomp;) {
+    const int ty = p0.type[p0.comp0 + c];
+    int m = 1;
+    while (c + m < ncomp && p0.type[p0.comp0 + c + m] == ty) ++m;
+    WfftPass q = p;
+    q.comp0 = p0.comp0 + c;
+    grd.z = (unsigned)m;
+    int e;
+    if (mode == 0) e = p.inverse ? launch_pass_ty<R, 0, true>(ty, q, grd, s, ctrl) : launch_pass_ty<R, 0, false>(ty, q, grd, s, ctrl);
+    else e = p.inverse ? launch_pass_ty<R, 2, true>(ty, q, grd, s, ctrl) : launch_pass_ty<R, 2, false>(ty, q, grd, s, ctrl);
+    if (e) return e;
+    c += m;
   }
-  return (int)cudaGetLastError();
+  return 0;
 }
 
 template <int R>
@@ -801,10 +821,31 @@ int launch_zg_R(const WfftPass& p0, const GreenTables& gt, float l0, float m2, f
   p.rpt = balanced_rows<R>(p.nrows);
   dim3 grd((unsigned)((p.nrows + p.rpt - 1) / p.rpt), (unsigned)nouter, (unsigned)ncomp);
   const size_t sm = wfft_smem<R>(p.len, true);
-  static size_t attr = 48 * 1024;
-  if (int e = wfft_attr(k_wfft_zg<R, WNW>, sm, attr)) return e;
-  k_wfft_zg<R, WNW><<<grd, WNW * 32, sm, s>>>(p, gt, l0, m2, ih2, scheme, ctrl);
-  return (int)cudaGetLastError();
+  // one launch per run of consecutive components of equal type
+  for (int c = 0; c < ncomp;) {
+    const int ty = p0.type[p0.comp0 + c];
+    int m = 1;
+    while (c + m < ncomp && p0.type[p0.comp0 + c + m] == ty) ++m;
+    WfftPass q = p;
+    q.comp0 = p0.comp0 + c;
+    grd.z = (unsigned)m;
+    int e = 0;
+    auto go = [&](auto kern, size_t& attr) {
+      if ((e = wfft_attr(kern, sm, attr))) return;
+      kern<<<grd, WNW * 32, sm, s>>>(q, gt, l0, m2, ih2, scheme, ctrl);
+      e = (int)cudaGetLastError();
+    };
+    static size_t attr[4] = {48 * 1024, 48 * 1024, 48 * 1024, 48 * 1024};
+    switch (ty) {
+      case T_DCT1: go(k_wfft_zg<R, WNW, T_DCT1>, attr[0]); break;
+      case T_DCT3: go(k_wfft_zg<R, WNW, T_DCT3>, attr[1]); break;
+      case T_DST1: go(k_wfft_zg<R, WNW, T_DST1>, attr[2]); break;
+      default: go(k_wfft_zg<R, WNW, T_DST3>, attr[3]); break;
+    }
+    if (e) return e;
+    c += m;
+  }
+  return 0;
 }
 
 int launch_pass(int R, const WfftPass& p, int mode, int nouter, int ncomp, const Ctrl* ctrl, cudaStream_t s) {

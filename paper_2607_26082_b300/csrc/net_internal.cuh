@@ -63,12 +63,17 @@ struct IncArgs {
   int nface;
   const long long* node; // surface nodes
   const double* fn_prev; // normal reactions of increment k-1 at the surface nodes
+  const uint8_t* fn_act; // if set: fn_prev counts only where fn_act[q] != 0 (the grid's own contact set)
   double center[3];      // sphere centre of increment k
   double radius;
   double eps[3][3];
   float* fmax;           // device scalar: max over the surface of -fn_prev (set by launch_inc_fmax)
   float* x;              // [Vw][16] features (base channels already written)
 };
+// normal reaction of increment k-1 at surface node q (zero off its contact set)
+__device__ inline double inc_fn(const IncArgs& a, int q) {
+  return (a.fn_act && !a.fn_act[q]) ? 0.0 : a.fn_prev[q];
+}
 __host__ __device__ inline long long win_volume(const Window& w) { return (long long)w.n[0] * w.n[1] * w.n[2]; }
 int launch_inc_fmax(const IncArgs& a, cudaStream_t s);
 int launch_inc_features(const IncArgs& a, cudaStream_t s);

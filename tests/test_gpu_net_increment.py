@@ -137,6 +137,34 @@ def test_rejected_guess_reproduces_the_previous_increment_start():
     g.close()
 
 
+def test_prediction_reads_the_grids_own_reactions():
+    """fn_prev = NULL: the prediction takes the grid's reactions of its last solve on that
+    solve's contact set, on the device; the guess (field and initial zone) equals the one
+    from the same reactions passed explicitly."""
+    spec = _small_indent()
+    g, U, FN, reps = warmstart.solve_increments(spec, store_dtype=torch.float64)
+    I = spec["indenter"]
+    dk = warmstart.depths(spec)
+    k = 3
+    net = Net(16, 32, 64, seed=7)
+    # the grid's contact state becomes increment k-1's again (same start, same solve)
+    g.dtt_move_indenter(I["centers"][k - 1])
+    g.dtt_set_initial(U[k - 2])
+    r = g.dtt_solve_step(1e-6, 20000, acv_mod=spec["acv_mod"], init=dtt.INIT_PREVIOUS, graph_iters=16)
+    assert r.status == dtt.OK
+    fn = torch.from_numpy(warmstart.contact_reactions(g)).cuda()
+    u_prev = torch.from_numpy(g.dtt_get_fields()).cuda()
+    g.dtt_move_indenter(I["centers"][k])
+    net.predict_increment(g, U[k - 2], None, warmstart.depth_triple(dk, k))
+    u_own, act_own = g.dtt_get_fields(), g.dtt_get_contact()[0].copy()
+    g.dtt_set_initial(u_prev)
+    net.predict_increment(g, U[k - 2], fn, warmstart.depth_triple(dk, k))
+    assert np.array_equal(u_own, g.dtt_get_fields())
+    assert np.array_equal(act_own, g.dtt_get_contact()[0])
+    net.close()
+    g.close()
+
+
 def test_trained_network_gains_on_a_held_out_seed():
     """The committed network (trained on seeds 2000-2005 of the 384 x 384 x 192 indentation
     with inclusions; its contact-zone threshold chosen on seed 3000) on the held-out seed
