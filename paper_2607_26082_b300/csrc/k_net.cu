@@ -724,32 +724,46 @@ __global__ void k_inc_loss(const float* __restrict__ y, const float* __restrict_
   }
 }
 
-// Weight of the correction at window node vw: 1 inside, falling linearly to 0 over the
-// last WIN_TAPER nodes before each window face that lies inside the grid (the contact face
-// and the grid's own faces keep 1), so that the guess has no jump where the correction
-// ends.
+// Weight of the correction at a window node: 1 inside, falling linearly to 0 over the last
+// WIN_TAPER nodes before each window face that lies inside the grid (the contact face and
+// the grid's own faces keep 1), so that the guess has no jump where the correction ends.
 constexpr int WIN_TAPER = 8;
-__device__ __forceinline__ double win_taper(const IncArgs& a, long long vw) {
-  const int idx[3] = {(int)(vw % a.w.n[0]), (int)((vw / a.w.n[0]) % a.w.n[1]), (int)(vw / ((long long)a.w.n[0] * a.w.n[1]))};
-  double t = 1.0;
-  for (int d = 0; d < 3; ++d) {
-    const int lo = a.w.o[d], hi = a.w.o[d] + a.w.n[d];   // window [lo, hi) along d
-    if (lo > 0) t = fmin(t, (idx[d] + 1) / (double)(WIN_TAPER + 1));
-    if (hi < a.g.nn[d]) t = fmin(t, (a.w.n[d] - idx[d]) / (double)(WIN_TAPER + 1));
-  }
-  return t;
-}
 
 // every node: u = u~_(k-1) + dd (secant + tapered correction), the correction 0 outside
 // the window
-__global__ void k_inc_guess(IncArgs a, const float* __restrict__ y, int CY, double* __restrict__ u) {
-  const long long V = a.g.nnodes;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * V; i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i / V);
-    const long long v = i - c * V;
-    const long long vw = grid_to_win(a, v);
-    const double corr = vw >= 0 ? win_taper(a, vw) * (double)y[vw * CY + c] : 0.0;
-    u[i] = inc_u1(a, i) + a.dd * (inc_secant(a, i) + corr);
+// One CTA per node row (c, z, y), threads along x: the window test and the taper of the row
+// are fixed once, the secant factor s / dd comes from the host (no FP64 division and no
+// 64-bit index division per value).
+__global__ void k_inc_guess(IncArgs a, const float* __restrict__ y, int CY, double sec, double* __restrict__ u) {
+  const int nx = a.g.nn[0], ny = a.g.nn[1], nz = a.g.nn[2];
+  const int rows = 3 * ny * nz;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int c = r / (ny * nz), rz = r - c * ny * nz, zz = rz / ny, yy = rz - zz * ny;
+    const long long base = (long long)c * a.g.nnodes + ((long long)zz * ny + yy) * nx;
+    const int wy = yy - a.w.o[1], wz = zz - a.w.o[2];
+    const bool rin = wy >= 0 && wy < a.w.n[1] && wz >= 0 && wz < a.w.n[2];
+    double trow = 1.0;   // taper along y and z
+    if (rin) {
+      const int idx[3] = {0, wy, wz};
+      for (int d = 1; d < 3; ++d) {
+        if (a.w.o[d] > 0) trow = fmin(trow, (idx[d] + 1) / (double)(WIN_TAPER + 1));
+        if (a.w.o[d] + a.w.n[d] < a.g.nn[d]) trow = fmin(trow, (a.w.n[d] - idx[d]) / (double)(WIN_TAPER + 1));
+      }
+    }
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      const long long i = base + x;
+      const int wx = x - a.w.o[0];
+      double corr = 0.0;
+      if (rin && wx >= 0 && wx < a.w.n[0]) {
+        double t = trow;
+        if (a.w.o[0] > 0) t = fmin(t, (wx + 1) / (double)(WIN_TAPER + 1));
+        if (a.w.o[0] + a.w.n[0] < nx) t = fmin(t, (a.w.n[0] - wx) / (double)(WIN_TAPER + 1));
+        const long long vw = wx + (long long)a.w.n[0] * (wy + (long long)a.w.n[1] * wz);
+        corr = t * (double)y[vw * CY + c];
+      }
+      const double u1 = inc_u1(a, i);
+      u[i] = u1 + a.dd * ((u1 - (a.u2 ? a.u2[i] : 0.0)) * sec + corr);
+    }
   }
 }
 // surface nodes: in the initial zone when they carried pressure at the previous increment
@@ -787,7 +801,8 @@ int launch_inc_loss(const float* y, const float* t, const float* m, long long V,
 }
 int launch_inc_guess(const IncArgs& a, const float* y, int CY, float thr, double* u, uint8_t* active,
                      cudaStream_t s) {
-  k_inc_guess<<<grid_1d(3 * a.g.nnodes), 256, 0, s>>>(a, y, CY, u);
+  const int rows = 3 * a.g.nn[1] * a.g.nn[2];
+  k_inc_guess<<<rows < 148 * 32 ? rows : 148 * 32, 128, 0, s>>>(a, y, CY, a.s_sec / a.dd, u);
   if (a.nface > 0 && active) k_inc_active<<<(a.nface + 255) / 256, 256, 0, s>>>(a, y, CY, thr, active);
   return (int)cudaGetLastError();
 }

@@ -43,29 +43,30 @@ int launch_from_double(long long n, const double* in, void* out, int out_is_floa
 }
 // u~ = 0 on every Dirichlet-face DOF (a node on a face whose condition for the component
 // is Dirichlet, periodic axes excepted): the DOFs the discrete problem removes
+// Zeroes the Dirichlet DOFs: blockIdx.y = axis d and face f (2 d + f), blockIdx.z = component;
+// the CTAs of a face sweep its node plane.
 __global__ void k_zero_dirichlet(GridDev g, double* u64, float* uhi, float* ulo) {
-  const long long n3 = 3 * g.nnodes;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i / g.nnodes);
-    const long long n = i - (long long)c * g.nnodes;
-    const int idx[3] = {(int)(n % g.nn[0]), (int)((n / g.nn[0]) % g.nn[1]), (int)(n / ((long long)g.nn[0] * g.nn[1]))};
-    bool dir = false;
-    for (int d = 0; d < 3; ++d) {
-      if (g.periodic[d]) continue;
-      if (idx[d] == 0 && g.bc[d][0][c] == BC_D) dir = true;
-      else if (idx[d] == g.nn[d] - 1 && g.bc[d][1][c] == BC_D) dir = true;
-    }
-    if (!dir) continue;
-    if (u64) u64[i] = 0.0;
-    if (uhi) uhi[i] = 0.f;
-    if (ulo) ulo[i] = 0.f;
+  const int d = blockIdx.y >> 1, f = blockIdx.y & 1, c = blockIdx.z;
+  if (g.periodic[d] || g.bc[d][f][c] != BC_D) return;
+  const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;   // the plane's two axes
+  const int n1 = g.nn[a1], n2 = g.nn[a2];
+  const long long st[3] = {1, g.nn[0], (long long)g.nn[0] * g.nn[1]};
+  const long long off = (long long)c * g.nnodes + (f ? (long long)(g.nn[d] - 1) * st[d] : 0);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n1 * n2; q += gridDim.x * blockDim.x) {
+    const int i2 = q / n1, i1 = q - i2 * n1;
+    const long long e = off + i1 * st[a1] + i2 * st[a2];
+    if (u64) u64[e] = 0.0;
+    if (uhi) uhi[e] = 0.f;
+    if (ulo) ulo[e] = 0.f;
   }
 }
 
 int launch_zero_dirichlet(const GridDev& g, double* u64, float* uhi, float* ulo, cudaStream_t s) {
-  const long long n3 = 3 * g.nnodes;
-  const int blocks = (int)std::min<long long>((n3 + 255) / 256, 148LL * 16);
-  k_zero_dirichlet<<<blocks, 256, 0, s>>>(g, u64, uhi, ulo);
+  int plane = 1;
+  for (int d = 0; d < 3; ++d)
+    for (int e = d + 1; e < 3; ++e) plane = std::max(plane, g.nn[d] * g.nn[e]);
+  const int blocks = std::min((plane + 255) / 256, 148 * 4);
+  k_zero_dirichlet<<<dim3(blocks, 6, 3), 256, 0, s>>>(g, u64, uhi, ulo);
   return (int)cudaGetLastError();
 }
 
