@@ -482,17 +482,6 @@ __device__ __forceinline__ void wfft(float* sr, float* si, const float2* tw1, co
   for (int k2 = 0; k2 < NK; ++k2) X[k2] = x[k2];
 }
 
-// Runs f with the transform type as a compile-time constant (uniform per CTA).
-template <typename F>
-__device__ __forceinline__ void wby_type(int type, F&& f) {
-  switch (type) {
-    case T_DCT1: f(std::integral_constant<int, T_DCT1>()); break;
-    case T_DCT3: f(std::integral_constant<int, T_DCT3>()); break;
-    case T_DST1: f(std::integral_constant<int, T_DST1>()); break;
-    default: f(std::integral_constant<int, T_DST3>()); break;
-  }
-}
-
 // Loads the P row pairs of this warp (rows 2 (p0 + q), + 1 of the CTA, zero beyond
 // nvalid) and writes their extended sequences into the fill layout.
 template <int R, int TY, bool INV>
