@@ -3,7 +3,7 @@
   python -m paper_2607_26082_b300.run --workload ct|ct_paper|cube16|indent|indent_cube|indent_inclusions|iso_cell
          [--precision mixed|fp64]
          [--iters K | --tol T] [--steps S] [--graph-iters G] [--nvox nx,ny,nz]
-         [--kinematics ss|fs] [--r0-scale K] [--load-steps N] [--max-iter M] [--stop-on-fail]
+         [--kinematics ss|fs] [--r0-scale K] [--load-steps N] [--max-iter M] [--stop-on-fail] [--learned]
          [--ct-load strong_line|weak_line|strong_node|weak_node|smooth_node] [--acv-on u|p] [--acv-mod M]
          [--medium paux|iso] [--scheme tetra2|hex1] [--contrast K]
   python -m paper_2607_26082_b300.run --workload batch [--cells N] [--seed0 S] [--no-tune]
@@ -21,7 +21,10 @@ stiffer one in finite strain); --load-steps N splits the indentation into N geom
 increments (default 20 for indent, whose 10-increment schedule leaves the physical branch
 at its last step, and the paper's 80 for indent_cube); --max-iter caps the iterations of each step (default 20000) and
 --stop-on-fail ends the run at the first step that does not converge; --radius, --dmin and
---dmax set the indent workload's sphere radius and its first and last depth ratios.  ct_paper is the
+--dmax set the indent workload's sphere radius and its first and last depth ratios;
+--learned starts every increment of an indentation after the first from the warm-start
+network's guess (the package's trained weights; the solve keeps the fallback rule and
+reports start_from_guess).  ct_paper is the
 paper's 10 x 100 x (50 + 1) CT-like specimen with the loading --ct-load; it reports the
 reactions of the load rows and of the ligament rows and their balance.  --acv-on and
 --acv-mod override the workload's Anderson settings.  iso_cell is a two-phase cell with
@@ -172,6 +175,8 @@ def main(argv=None):
     ap.add_argument("--dmin", type=float, default=None, help="indent: first depth ratio d/R (default 0.001)")
     ap.add_argument("--dmax", type=float, default=None, help="indent: last depth ratio d/R (default 0.05)")
     ap.add_argument("--stop-on-fail", action="store_true")
+    ap.add_argument("--learned", action="store_true",
+                    help="indentation: increments after the first start from the warm-start network's guess")
     a = ap.parse_args(argv)
     if a.workload == "batch":
         return run_batch(a, dtt.PREC_MIXED if a.precision == "mixed" else dtt.PREC_FP64)
@@ -202,15 +207,33 @@ def main(argv=None):
         t = g.dtt_autotune(iters=4, acv_mod=a.acv_mod or spec["acv_mod"])
         tuning = {"residual_zchunk": t.residual_zchunk, "fft_generic": t.fft_generic, "z_route": t.z_route,
                   "fft_warp": t.fft_warp, "ms_per_iteration": t.ms_per_iteration}
+    net, hist = None, {}
+    if a.learned and ind:
+        import torch
+        from paper_2607_26082_b300 import warmstart
+        net = warmstart.load_net(os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                                              "warmstart_indent.npz"))
+        dk = [float(r) * float(ind["radius"]) for r in ind["ratios"]]
+        hist = {"u1": torch.empty((3,) + tuple(g.node_shape), dtype=torch.float64, device="cuda"), "u2": None}
     for s in range(nsteps):
         if ind:
             g.dtt_move_indenter(ind["centers"][s])
+        init = dtt.INIT_PREVIOUS if s else dtt.INIT_ZERO
+        if net is not None and s > 0:
+            # the guess from u~ of the last two increments and the grid's own reactions
+            g.dtt_get_fields(u_out=hist["u1"])
+            net.predict_increment(g, hist["u2"], None, (dk[s - 2] if s >= 2 else 0.0, dk[s - 1], dk[s]))
+            init = dtt.INIT_GUESS
         reps_ms = []
         for _ in range(max(1, a.repeat) if (a.iters > 0 and s == 0) else 1):
             rep = g.dtt_solve_step(tol, max_iter, acv_mod=a.acv_mod or spec["acv_mod"],
                                    acv_on=dtt.ACV_P if a.acv_on == "p" else dtt.ACV_U,
-                                   init=dtt.INIT_PREVIOUS if s else dtt.INIT_ZERO, graph_iters=a.graph_iters)
+                                   init=init, graph_iters=a.graph_iters)
             reps_ms.append(1e3 * rep.seconds / max(rep.iterations, 1))
+        if net is not None and s > 0:
+            if hist["u2"] is None:
+                hist["u2"] = torch.empty_like(hist["u1"])
+            hist["u2"], hist["u1"] = hist["u1"], hist["u2"]
         out = {"workload": spec["name"], "precision": a.precision, "kinematics": a.kinematics, "step": s,
                "medium": spec.get("medium", "paux"), "scheme": "tetra2" if spec["scheme"] == wl.TETRA2 else "hex1",
                "acv_on": a.acv_on, "acv_mod": a.acv_mod or spec["acv_mod"]}
