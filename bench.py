@@ -204,15 +204,17 @@ def cpu_threads():
 
 
 # ------------------------------------------------------------------ GPU arm
-def launches_per_iteration(has_rows, has_contact, acv):
+def launches_per_iteration(has_rows, has_contact, acv, exact=True):
     """Kernel launches of one captured iteration (every launch runs; after convergence they
-    return at once)."""
+    return at once); exact: the exact residual mode's Green-input fix-up over the tiles of
+    constrained DOFs."""
     n = 1                      # residual
     n += 1 if has_rows else 0  # proj_P
     n += 1 if has_contact else 0
     n += 1                     # ctrl residual
     n += 2 if has_contact else 0
     n += 2 if acv else 0       # ctrl (Gram row, alpha), Green input
+    n += 1 if (acv and exact) else 0
     n += 5                     # x, y forward; z forward + Green + z inverse; y, x inverse + increment
     n += 1 if has_rows else 0  # proj_U
     n += 1 if has_contact else 0
