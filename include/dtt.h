@@ -236,9 +236,11 @@ dtt_status dtt_apply_green(dtt_grid* grid, const double* ptilde, double* u, int3
  * (the one current at dtt_grid_create) must be the current device, else DTT_ERR_ARG.
  * The intermediate spectra use a fixed 64 MiB device array inside the library, held by
  * every GPU that loads it until the process exits, so grids above 2,796,202 nodes are
- * rejected with DTT_ERR_ARG.  The call allocates nothing.  The first call on a device looks up that
- * array's device address; make it before any stream capture.  All calls share the
- * array: calls that overlap on the GPU race.  The call synchronises the grid's stream. */
+ * rejected with DTT_ERR_ARG.  The call allocates nothing.  It synchronises the grid's
+ * stream before it returns, so it cannot itself be recorded into a CUDA graph.  The first
+ * call on a device looks up that array's device address, which a capture in global mode
+ * on another stream would not allow: make that first call before such a capture.  All
+ * calls share the array: calls that overlap on the GPU race. */
 dtt_status dtt_apply_green_noalloc(dtt_grid* grid, const double* ptilde_dev, double* u_dev);
 
 /* Forward (inverse = 0) or inverse (inverse = 1) transform of one nodal component array
