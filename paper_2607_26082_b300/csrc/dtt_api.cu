@@ -328,7 +328,7 @@ double host_ustar(const dtt_grid* G, int c, long long n) {
 dtt_status build_tile_z(dtt_grid* G, const std::vector<long long>& marked) {
   const int tx = residual_f32_tile(0), ty = residual_f32_tile(1);
   const int nnx = G->g.nn[0], nny = G->g.nn[1], nnz = G->g.nn[2];
-  const int ntx = (nnx + tx - 1) / tx, nty = (nny + ty - 1) / ty;
+  const int ntx = res_ntx(G->g, tx), nty = (nny + ty - 1) / ty;
   std::vector<int2> t((size_t)ntx * nty, make_int2(INT32_MAX, INT32_MIN));
   for (long long n : marked) {
     const int i = (int)(n % nnx), j = (int)((n / nnx) % nny), k = (int)(n / ((long long)nnx * nny));
@@ -345,11 +345,21 @@ dtt_status build_tile_z(dtt_grid* G, const std::vector<long long>& marked) {
         int jj = j + dj;
         if (G->g.periodic[1]) jj = (jj + nny) % nny;
         if (jj < 0 || jj >= nny) continue;
-        int2& r = t[(size_t)(jj / ty) * ntx + ii / tx];
+        int2& r = t[(size_t)(jj / ty) * ntx + res_tile_of_x(G->g, ii, tx)];
         r.x = std::min(r.x, zlo);
         r.y = std::max(r.y, zhi);
       }
     }
+  }
+  // the exact mode's residual runs as a flux-free pass plus one CTA per marked tile over
+  // its marked planes +- 1 when those ranges are short (else one pass does everything)
+  int span = 0;
+  for (const int2& r : t)
+    if (r.x <= r.y) span = std::max(span, r.y - r.x + 3);
+  const int split = span == 0 ? 2 : (span <= 16 ? 1 : 0);
+  if (split != G->res_split) {
+    G->res_split = split;
+    invalidate_graph(G);
   }
   if (G->tile_cap < (int)t.size()) {
     dfree(G->d_tile_z);
@@ -606,6 +616,7 @@ dtt_status enqueue_iteration(dtt_grid* G, int acv_on, bool acv) {
   const bool exact = sizeof(T) == 4 && diff && exact_residual(G);
   ra.exact = exact ? 1 : 0;
   ra.tile_z = G->d_tile_z;
+  ra.split = exact ? G->res_split : 0;
   for (int k = 0; k < 4; ++k) {
     ra.pring[k] = G->S[k];
     ra.gring[k] = G->Gr[k];

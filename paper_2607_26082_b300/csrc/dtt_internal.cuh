@@ -145,6 +145,10 @@ struct ResidualArgs {
   // xy tile (zmin > zmax: none)
   int exact;
   const int2* tile_z;
+  // mixed kernel in the exact mode: 0 = one pass; 1 = a pass without the flux, then one CTA
+  // per marked xy tile over the node planes tile_z +- 1 (short marked z ranges); 2 = the
+  // pass without the flux alone (no marked tile)
+  int split;
   void* pring[4];         // mode 1: p ring (slot i % 4)
   void* gring[4];         // mode 1: Green-input ring (g_{i-1} read from slot (i-1) % 4)
   void* rring[4];         // mode 1: Anderson residual ring (R_{i-1} into slot (i-1) % 4)
@@ -169,6 +173,19 @@ int residual_zchunk(const GridDev& g);
 int launch_residual_f32(const ResidualArgs& a, cudaStream_t s);
 int residual_f32_blocks(const GridDev& g);
 int residual_f32_tile(int axis);   // node tile of the mixed residual kernel along x (0) and y (1)
+// xy tiles of the mixed residual kernel (tx x ty node columns).  When x is not periodic and
+// holds tx k + 1 nodes, the last x tile also owns the final node column (tx + 1 wide), whose
+// voxels to the right lie outside the grid, instead of a tile of one column.
+__host__ __device__ inline bool res_wide_last_x(const GridDev& g, int tx) {
+  return !g.periodic[0] && g.nn[0] > tx && g.nn[0] % tx == 1;
+}
+__host__ __device__ inline int res_ntx(const GridDev& g, int tx) {
+  return res_wide_last_x(g, tx) ? g.nn[0] / tx : (g.nn[0] + tx - 1) / tx;
+}
+__host__ __device__ inline int res_tile_of_x(const GridDev& g, int i, int tx) {
+  const int t = i / tx, n = res_ntx(g, tx);
+  return t < n ? t : n - 1;
+}
 template <typename T> int residual_nblocks(const GridDev& g) {
   return sizeof(T) == 4 ? residual_f32_blocks(g) : residual_blocks(g);
 }

@@ -74,6 +74,7 @@ struct dtt_grid {
   int exact_ok = 1;            // 0 (DTT_EXACT_R=0): keep R = p - g + A0 Delta in the mixed path
   int2* d_tile_z = nullptr;    // per xy tile of the mixed residual kernel: z range of marked nodes
   int tile_cap = 0;
+  int res_split = 0;           // ResidualArgs::split of the exact mode, from the marked z ranges
   unsigned int* tz_err = nullptr;
   // isotropic reference medium (Section 3.2.3): per-axis tables of sin^2(q/2), cos^2(q/2)
   // shared by the components, and per position the components with a mode there (bit c)

@@ -3,8 +3,10 @@
 // reference medium of Section 3.2.3 and the symmetry weights W of Table 1), organised for
 // instruction throughput on B300:
 //
-//  * a CTA owns a 32 x 8 tile of node columns and marches along z one voxel layer at a
-//    time; the layer between node planes L and L+1 is processed in two phases:
+//  * a CTA owns a 32 x 8 tile of node columns (the last x tile 33 x 8 when x is not
+//    periodic and has 32 k + 1 nodes, rather than a tile of one column) and marches along
+//    z one voxel layer at a time; the layer between node planes L and L+1 is processed in
+//    two phases:
 //      A. one thread per voxel of the 33 x 9 halo layer forms, once, the gradients of its
 //         points, the stress sigma = C:(eps* + sym grad u~) and, on the layers that need
 //         it, the reference-medium flux tau_cd = (2 mu0 + lambda0 delta_cd) d(.)_c/dx_d,
@@ -115,8 +117,13 @@ __device__ __forceinline__ float ref_flux1(const float (&Gm)[3][3], int c, int d
 }  // namespace
 
 // PHW: voxel phases loaded as aligned 4-byte words (x extent a multiple of 4, x not
-// periodic, phase array 4-byte aligned); otherwise one byte per halo position
-template <int SCHEME, bool FS, bool PHW>
+// periodic, phase array 4-byte aligned); otherwise one byte per halo position.
+// PART (exact Anderson mode, whose R_{i-1} = p_i + A0 c needs the reference flux only next
+// to the constrained nodes): 0 = one pass doing everything; 1 = the pass without the flux
+// (no Delta ring, no flux point data: less shared memory and fewer registers), which leaves
+// R and the Gram row of the node planes tile_z +- 1 to PART 2; 2 = one CTA per marked xy
+// tile over those planes only, writing their R and Gram row (partials after the chunks').
+template <int SCHEME, bool FS, bool PHW, int PART>
 __global__ void __launch_bounds__(FTHREADS, 2)
 k_residual_f32(ResidualArgs a) {
   constexpr bool TET = SCHEME == SCHEME_TETRA2;
@@ -124,10 +131,10 @@ k_residual_f32(ResidualArgs a) {
   constexpr int NPT = TET ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* sU = (float2*)smem_raw;                       // [RING][3][FPL] u~ (hi, lo)
-  float* sD = (float*)(sU + RING * 3 * FPL);            // [RING][3][FPL] Delta
-  float* sSf = sD + RING * 3 * FPL;                     // stress point data [NS][NVL] (x NPT floats)
-  float* sTf = sSf + NS * NVL * NPT;                    // flux point data [9][NVL] (x NPT floats)
-  uint8_t* sP = (uint8_t*)(sTf + 9 * NVL * NPT);        // phases: [RING][FPL] bytes, or [RING][FVY][PWX] words
+  float* sD = (float*)(sU + RING * 3 * FPL);            // [RING][3][FPL] Delta (not in PART 1)
+  float* sSf = PART == 1 ? sD : sD + RING * 3 * FPL;    // stress point data [NS][NVL] (x NPT floats)
+  float* sTf = sSf + NS * NVL * NPT;                    // flux point data [9][NVL] (x NPT floats; not in PART 1)
+  uint8_t* sP = PART == 1 ? (uint8_t*)sTf : (uint8_t*)(sTf + 9 * NVL * NPT);   // phases: [RING][FPL] bytes, or [RING][FVY][PWX] words
   __shared__ float sLam[MAX_PHASE], sMu[MAX_PHASE];
   __shared__ double sRed[6][FTHREADS / 32];
 
@@ -140,10 +147,15 @@ k_residual_f32(ResidualArgs a) {
   }
   const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
   const int zc = a.zchunk;
-  const int z0 = blockIdx.z * zc;
-  const int z1 = min(z0 + zc, g.nn[2]);
   const long long NN = g.nnodes;
   const int nnx = g.nn[0], nny = g.nn[1], nnz = g.nn[2];
+  int z0 = blockIdx.z * zc;
+  int z1 = min(z0 + zc, nnz);
+  const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+  // without a PART 2 launch, the chunk CTAs of the lowest chunk zero its partials slots
+  if (PART != 2 && a.split != 1 && blockIdx.z == 0 && tid < RES_STRIDE)
+    a.partials[(long long)RES_STRIDE * ((long long)gridDim.x * gridDim.y * gridDim.z + blockIdx.x +
+                                        (long long)gridDim.x * blockIdx.y) + tid] = 0.0;
 
   float* po = (float*)a.pout;
   float* xo = nullptr;
@@ -154,6 +166,7 @@ k_residual_f32(ResidualArgs a) {
   int rslot = -1;
   bool tau_on = true, tau_from_delta = false;
   int tz_lo = -(1 << 29), tz_hi = 1 << 29;
+  int fl_lo = 1 << 30, fl_hi = -(1 << 30);   // PART 1: node planes whose R and Gram row PART 2 forms
   if (a.mode == 0) {
     xo = (float*)a.xout;
   } else if (a.mode == 1) {
@@ -170,16 +183,32 @@ k_residual_f32(ResidualArgs a) {
       if (a.exact) {
         gprev = nullptr;
         const int2 zr = a.tile_z[blockIdx.y * gridDim.x + blockIdx.x];
+        if (PART == 2 && zr.x <= zr.y) {
+          z0 = max(zr.x - 1, 0);
+          z1 = min(zr.y + 2, nnz);
+        }
         tau_on = zr.x <= zr.y && zr.y >= z0 - 1 && zr.x <= z1;
         if (!tau_on) dfield = nullptr;
         tz_lo = zr.x;
         tz_hi = zr.y;
+        if (PART == 1 && zr.x <= zr.y) {
+          fl_lo = zr.x - 1;
+          fl_hi = zr.y + 1;
+        }
       }
     } else {
       tau_on = false;
     }
   } else {
     tau_on = false;
+  }
+  if (PART == 2 && !(ro && tau_on)) {   // no flux node planes in this tile (or no R yet)
+    if (tid < RES_STRIDE) a.partials[RES_STRIDE * blk + tid] = 0.0;
+    return;
+  }
+  if (PART == 1) {
+    tau_on = false;
+    dfield = nullptr;
   }
   const float lam0 = a.f_lam0, mu0 = a.f_mu0;
   const bool iso = g.ref_iso != 0;
@@ -248,8 +277,11 @@ k_residual_f32(ResidualArgs a) {
   Acc2x2 acc_sp;            // lanes: sum w sigma:sigma, sum p^2
   Acc2x2 acc_g01, acc_g23;  // Gram row: lanes (R slot rslot, slot rslot + 1), (rslot + 2, rslot + 3)
 
-  const bool node_thread = tid < FTX * FTY;
-  const int tx = tid % FTX, ty = tid / FTX;
+  // the wide last x tile: threads FTX FTY .. + FTY - 1 (idle in phase B otherwise) own the
+  // final node column, tx = FTX
+  const bool xtra = tid >= FTX * FTY && tid < FTX * FTY + FTY && blockIdx.x == gridDim.x - 1 && res_wide_last_x(g, FTX);
+  const bool node_thread = tid < FTX * FTY || xtra;
+  const int tx = xtra ? FTX : tid % FTX, ty = xtra ? tid - FTX * FTY : tid / FTX;
   const int i = x0 + tx, j = y0 + ty;
   const bool active = node_thread && (i < nnx && j < nny);
   const bool vox_thread = tid < NVL;
@@ -335,7 +367,7 @@ k_residual_f32(ResidualArgs a) {
         }
       } else {
         const float lam = sLam[ph], mu = sMu[ph];
-        const bool own = own_xy && L >= z0 && L < g.nvox[2];
+        const bool own = PART != 2 && own_xy && L >= z0 && L < g.nvox[2];
         const float2* U0 = sU + s0 * 3 * FPL + vly * FHX + vlx;
         const float2* U1 = sU + s1 * 3 * FPL + vly * FHX + vlx;
         const float* D0 = sD + s0 * 3 * FPL + vly * FHX + vlx;
@@ -549,6 +581,7 @@ k_residual_f32(ResidualArgs a) {
         for (int ey = 0; ey < 2; ++ey) {
           #pragma unroll
           for (int ex = 0; ex < 2; ++ex) {
+            if (ex == 1 && tx == FTX) continue;   // right of the final column: no voxel
             const int v = (ty + ey) * FVX + (tx + ex);
             const int dx = 1 - ex, dy = 1 - ey;
             const bool tlo = (dx + dy) & 1;
@@ -591,6 +624,7 @@ k_residual_f32(ResidualArgs a) {
         for (int ey = 0; ey < 2; ++ey) {
           #pragma unroll
           for (int ex = 0; ex < 2; ++ex) {
+            if (ex == 1 && tx == FTX) continue;   // right of the final column: no voxel
             const int v = (ty + ey) * FVX + (tx + ex);
             const int dx = 1 - ex, dy = 1 - ey;
             const float sx = dx ? 1.f : -1.f, sy = dy ? 1.f : -1.f;
@@ -633,6 +667,7 @@ k_residual_f32(ResidualArgs a) {
         if (!g.periodic[2]) zf = (L == 0) ? 0 : (L == nnz - 1) ? 1 : -1;
         float p2loc = 0.f;
         float2 g01 = make_float2(0.f, 0.f), g23 = make_float2(0.f, 0.f);
+        const bool fix_owned = PART == 1 && L >= fl_lo && L <= fl_hi;
         #pragma unroll
         for (int c = 0; c < 3; ++c) {
           bool dof = !((fxy >> (3 * c)) & 1);
@@ -650,9 +685,9 @@ k_residual_f32(ResidualArgs a) {
           const long long e = c * NN + nL;
           const bool free_dof = dof && !((cm >> c) & 1);
           if (free_dof) p2loc = fmaf(pv, pv, p2loc);
-          if (po) po[e] = pv;
+          if (PART != 2 && po) po[e] = pv;
           if (xo) xo[e] = pv + a0v;
-          if (ro) {
+          if (ro && !fix_owned) {
             const float rv = dof ? (pv - pg[c] + a0v) : 0.f;
             ro[e] = rv;
             if (free_dof) {
@@ -662,8 +697,8 @@ k_residual_f32(ResidualArgs a) {
             }
           }
         }
-        acc_sp.add(make_float2(0.f, p2loc));
-        if (ro) {
+        if (PART != 2) acc_sp.add(make_float2(0.f, p2loc));
+        if (ro && !fix_owned) {
           acc_g01.add(g01);
           acc_g23.add(g23);
         }
@@ -705,11 +740,10 @@ k_residual_f32(ResidualArgs a) {
     }
   }
   __syncthreads();
-  if (tid < 6) {
+  if (tid < RES_STRIDE) {
     double t = 0.0;
     for (int w = 0; w < FTHREADS / 32; ++w) t += sRed[tid][w];
-    const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-    a.partials[6 * b + tid] = t;
+    a.partials[RES_STRIDE * blk + tid] = t;
   }
 }
 
@@ -761,7 +795,7 @@ static double zchunk_makespan(int nnz, long long bxy, int zc, int S) {
 // larger chunk), cached per grid shape.
 int residual_f32_zchunk(const GridDev& g) {
   if (g.zc_override > 0) return g.zc_override;
-  const long long bxy = (long long)((g.nn[0] + FTX - 1) / FTX) * ((g.nn[1] + FTY - 1) / FTY);
+  const long long bxy = (long long)res_ntx(g, FTX) * ((g.nn[1] + FTY - 1) / FTY);
   const int S = resident_ctas();
   const int nnz = g.nn[2];
   static std::mutex mu;
@@ -788,15 +822,31 @@ int residual_f32_zchunk(const GridDev& g) {
 
 int residual_f32_tile(int axis) { return axis == 0 ? FTX : FTY; }
 
+// partials slots: one per chunk CTA, then one per xy tile (the flux-column pass)
 int residual_f32_blocks(const GridDev& g) {
   int zc = residual_f32_zchunk(g);
-  return ((g.nn[0] + FTX - 1) / FTX) * ((g.nn[1] + FTY - 1) / FTY) * ((g.nn[2] + zc - 1) / zc);
+  const int ntiles = res_ntx(g, FTX) * ((g.nn[1] + FTY - 1) / FTY);
+  return ntiles * ((g.nn[2] + zc - 1) / zc) + ntiles;
+}
+
+template <int SCHEME, bool FS, int PART>
+static int launch_part(const ResidualArgs& a, dim3 grd, size_t sm, bool phw, cudaStream_t s) {
+  auto k = phw ? k_residual_f32<SCHEME, FS, true, PART> : k_residual_f32<SCHEME, FS, false, PART>;
+  static bool attr[2] = {false, false};
+  if (!attr[phw]) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    attr[phw] = true;
+  }
+  k<<<grd, FTHREADS, sm, s>>>(a);
+  return (int)cudaGetLastError();
 }
 
 template <int SCHEME, bool FS>
 static int launch_f32_impl(const ResidualArgs& a, cudaStream_t s) {
   const int zc = residual_f32_zchunk(a.g);
-  dim3 grd((a.g.nn[0] + FTX - 1) / FTX, (a.g.nn[1] + FTY - 1) / FTY, (a.g.nn[2] + zc - 1) / zc);
+  dim3 grd(res_ntx(a.g, FTX), (a.g.nn[1] + FTY - 1) / FTY, (a.g.nn[2] + zc - 1) / zc);
+  const long long nchunk = (long long)grd.x * grd.y * grd.z;
   ResidualArgs aa = a;
   aa.zchunk = zc;
   for (int p = 0; p < 3; ++p)
@@ -810,18 +860,22 @@ static int launch_f32_impl(const ResidualArgs& a, cudaStream_t s) {
   // ring: u~ pairs (8 B) and Delta (4 B) per position; stress and flux point data; phases
   const size_t sm = (size_t)RING * 3 * FPL * (sizeof(float2) + sizeof(float)) +
                     (size_t)(NS + 9) * NVL * NPT * sizeof(float) + (size_t)RING * FVY * PWX;
+  // the flux-free pass: no Delta ring and no flux point data
+  const size_t sm_nf = (size_t)RING * 3 * FPL * sizeof(float2) + (size_t)NS * NVL * NPT * sizeof(float) +
+                       (size_t)RING * FVY * PWX;
   static_assert(RING * FVY * PWX >= RING * FPL, "phase ring holds either layout");
   // word loads of the phases: every voxel row then starts on a 4-byte boundary
   const bool phw = a.g.nvox[0] % 4 == 0 && !a.g.periodic[0] && ((uintptr_t)a.phase & 3) == 0;
-  auto k = phw ? k_residual_f32<SCHEME, FS, true> : k_residual_f32<SCHEME, FS, false>;
-  static bool attr[2] = {false, false};
-  if (!attr[phw]) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return (int)e;
-    attr[phw] = true;
+  const bool split = a.mode == 1 && a.exact && a.split != 0;
+  if (!split) {
+    aa.split = 0;
+    return launch_part<SCHEME, FS, 0>(aa, grd, sm, phw, s);
   }
-  k<<<grd, FTHREADS, sm, s>>>(aa);
-  return (int)cudaGetLastError();
+  int e = launch_part<SCHEME, FS, 1>(aa, grd, sm_nf, phw, s);
+  if (e != 0 || a.split != 1) return e;
+  ResidualArgs af = aa;
+  af.partials = a.partials + RES_STRIDE * nchunk;
+  return launch_part<SCHEME, FS, 2>(af, dim3(grd.x, grd.y, 1), sm, phw, s);
 }
 
 int launch_residual_f32(const ResidualArgs& a, cudaStream_t s) {

@@ -595,17 +595,22 @@ __global__ void k_acv_green_input_v4(long long total, void* const* P, void** Gr,
 }
 
 // The accelerated Green input at the nodes of the tiles that hold constrained DOFs (one CTA
-// per tile of tx x ty node columns, its z range tile_z +- 1 layer): the full formula, after
+// per xy tile of the mixed residual kernel, tx x ty node columns, plus the final column in a
+// wide last x tile, threads tx ty ..; its z range tile_z +- 1 layer): the full formula, after
 // k_acv_green_input_v4 has written the R-free form everywhere.
 __global__ void k_acv_green_fix(const GridDev g, void* const* P, void* const* Gr, void* const* Gown, void* const* R,
                                 const Ctrl* ctrl, const int2* __restrict__ tile_z, int tx, int ty) {
   if (ctrl->done || !ctrl->accel) return;
   const int2 zr = tile_z[blockIdx.x];
   if (zr.x > zr.y) return;
-  const int ntx = (g.nn[0] + tx - 1) / tx;
-  const int x = (blockIdx.x % ntx) * tx + (int)threadIdx.x % tx;
-  const int y = (blockIdx.x / ntx) * ty + (int)threadIdx.x / tx;
-  if ((int)threadIdx.x >= tx * ty || x >= g.nn[0] || y >= g.nn[1]) return;
+  const int ntx = res_ntx(g, tx);
+  const int bx = blockIdx.x % ntx, by = blockIdx.x / ntx;
+  const int t = threadIdx.x;
+  const bool xtra = t >= tx * ty;
+  if (xtra && !(bx == ntx - 1 && res_wide_last_x(g, tx))) return;
+  const int x = bx * tx + (xtra ? tx : t % tx);
+  const int y = by * ty + (xtra ? t - tx * ty : t / tx);
+  if (x >= g.nn[0] || y >= g.nn[1]) return;
   const int i = ctrl->i_local;
   float* gi = (float*)Gown[i % 4];
   const float a0 = ctrl->alpha_f[0], a1 = ctrl->alpha_f[1], a2 = ctrl->alpha_f[2], a3 = ctrl->alpha_f[3];
@@ -638,8 +643,8 @@ int launch_acv_green_input(const GridDev& g, void* const* pring, void** gring, v
     k_acv_green_input_v4<<<acv_blocks(g), SB, 0, s>>>(total, pring, gring, gown, rring, ctrl, alias);
     if (alias) {
       const int tx = residual_f32_tile(0), ty = residual_f32_tile(1);
-      const int ntiles = ((g.nn[0] + tx - 1) / tx) * ((g.nn[1] + ty - 1) / ty);
-      k_acv_green_fix<<<ntiles, tx * ty, 0, s>>>(g, pring, gring, gown, rring, ctrl, tile_z, tx, ty);
+      const int ntiles = res_ntx(g, tx) * ((g.nn[1] + ty - 1) / ty);
+      k_acv_green_fix<<<ntiles, tx * ty + ty, 0, s>>>(g, pring, gring, gown, rring, ctrl, tile_z, tx, ty);
     }
   } else {
     k_acv_green_input<T><<<acv_blocks(g), SB, 0, s>>>(total, pring, gring, rring, ctrl);
