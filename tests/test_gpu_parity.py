@@ -279,6 +279,24 @@ def test_fixed_iterations_accelerated_mixed(seed):
     assert np.allclose(hist, ref.history, rtol=2e-3, atol=1e-6 * ref.history[0])
 
 
+@pytest.mark.parametrize("seed", [8, 9])
+def test_fixed_iterations_accelerated_mixed_wide_tile(seed):
+    """The same history check on 64 x 12 x 9 voxels with no periodic axis: x holds 65 = 2 x 32
+    + 1 nodes, so the mixed residual kernel's last x tile owns 33 node columns, and the
+    exact Anderson mode's residual runs as the flux-free pass followed by the pass over the
+    node planes next to the rows' DOFs."""
+    spec = wl.random_problem(seed, nvox=(64, 12, 9), periodic_prob=0.0)
+    pb, rows = oracle_problem(spec)
+    K = 14
+    ref = osv.solve_alg1(pb, rows, spec["lam0"], spec["mu0"], 0.0, K, acv_on="P", acv_mod=spec["acv_mod"])
+    g = gpu_grid(spec, MIXED)
+    rep = g.dtt_solve_step(0.0, K, acv_mod=spec["acv_mod"], graph_iters=1)
+    assert rep.iterations == K
+    assert rep.accelerations == ref.accelerations
+    hist = g.dtt_get_history()
+    assert np.allclose(hist, ref.history, rtol=2e-3, atol=1e-6 * ref.history[0])
+
+
 def _s6(sigma):
     """Oracle stress (ip, 3, 3, z, y, x) in the library's (z, y, x, ip, 6) Voigt order."""
     sref = np.moveaxis(sigma, (0, 1, 2), (3, 4, 5))
@@ -376,6 +394,35 @@ def test_contact_increments(prec):
         else:
             tie = np.abs(ref.gap) < 1e-8 * I["radius"]
             assert np.array_equal(act[~tie], ref.active[~tie])
+        u, sig = g.dtt_get_fields(sigma=True)
+        assert rel_l2(u, ref.u) <= bar
+        assert rel_l2(sig, _s6(ref.sigma)) <= bar
+        assert np.abs(force - ref.force).max() <= bar * np.abs(ref.force).max()
+
+
+def test_contact_increments_wide_tile():
+    """Two mixed increments of Algorithm 2 on 64 x 16 x 8 voxels (65 nodes along x: a last
+    residual tile of 33 columns; the contact face marks every tile's top planes, so the
+    exact mode's residual runs as two passes): active set, displacement, stress and force
+    against the oracle within the mixed bar."""
+    w = wl.indentation(64, 16, 8, R=6.0, steps=2, dmin=0.01, dmax=0.05)
+    pb, _ = oracle_problem(w)
+    I = w.indenter
+    g = gpu_grid(w, MIXED)
+    u_ref = np.zeros((3,) + pb.node_shape)
+    g.dtt_set_indenter(I["axis"], I["face"], I["centers"][0], I["radius"])
+    bar = CONVERGED[MIXED][1]
+    for step, O in enumerate(I["centers"]):
+        ind = ocs.Indenter(pb, I["axis"], I["face"], O, I["radius"])
+        # the float64 oracle's residual settles near 1.3e-13 on this grid: stop it at 1e-12
+        ref = osv.solve_alg2_increment(pb, ind, [], w.lam0, w.mu0, 1e-12, 4000, u_ref)
+        u_ref = ref.u
+        g.dtt_move_indenter(O)
+        rep = g.dtt_solve_step(1e-7, 4000, acv_mod=3, init=dtt.INIT_PREVIOUS if step else dtt.INIT_ZERO)
+        assert rep.status == dtt.OK, rep.as_dict()
+        act, gap, fn, force = g.dtt_get_contact()
+        tie = np.abs(ref.gap) < 1e-8 * I["radius"]
+        assert np.array_equal(act[~tie], ref.active[~tie])
         u, sig = g.dtt_get_fields(sigma=True)
         assert rel_l2(u, ref.u) <= bar
         assert rel_l2(sig, _s6(ref.sigma)) <= bar
