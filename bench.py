@@ -204,11 +204,12 @@ def cpu_threads():
 
 
 # ------------------------------------------------------------------ GPU arm
-def launches_per_iteration(has_rows, has_contact, acv, exact=True):
+def launches_per_iteration(has_rows, has_contact, acv, exact=True, split=True):
     """Kernel launches of one captured iteration (every launch runs; after convergence they
     return at once); exact: the exact residual mode's Green-input fix-up over the tiles of
-    constrained DOFs."""
-    n = 1                      # residual
+    constrained DOFs; split: its residual as two passes (without the reference flux, then
+    the marked tiles' node planes), as short marked z ranges (a contact face) give."""
+    n = 2 if (exact and split) else 1   # residual
     n += 1 if has_rows else 0  # proj_P
     n += 1 if has_contact else 0
     n += 1                     # ctrl residual
