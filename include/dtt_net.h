@@ -134,6 +134,26 @@ dtt_status dtt_net_train_increment(dtt_net* net, dtt_grid* grid, const double* u
                                    const double depth[3], const double* u_target, const double* fn_target, float lr,
                                    double* loss);
 
+/* Data-parallel training: dtt_net_train_increment split at the optimiser, so that ranks
+ * that each hold their own increments can sum their gradients (one all-reduce of
+ * dtt_net_num_params floats per step) before every rank takes the same Adam step.
+ *
+ * dtt_net_grad_increment: the features, forward pass, loss and backward pass of increment k
+ * (arguments as dtt_net_train_increment); grad (device, num_params floats, caller-owned)
+ * receives dloss/dparam, *loss the loss; the parameters and the Adam state are unchanged.
+ *
+ * dtt_net_apply_grad: one Adam step (as dtt_net_train_step's) with the gradient scale x grad
+ * (grad: device, num_params floats, complete when the call is made: the library reads it on
+ * the net's stream; scale: finite, > 0, e.g. 1 / the number of gradients summed into grad).
+ * grad_increment followed by apply_grad(scale 1) on its output is train_increment (the
+ * weight gradients are summed with float atomics, so any two evaluations of one gradient
+ * agree to the order of those sums, about 1e-7 relative).  Both calls synchronise the net's
+ * stream before returning; DTT_ERR_ARG for a host pointer, lr <= 0 or a bad scale. */
+dtt_status dtt_net_grad_increment(dtt_net* net, dtt_grid* grid, const double* u_prev2, const double* fn_prev,
+                                  const double depth[3], const double* u_target, const double* fn_target, float* grad,
+                                  double* loss);
+dtt_status dtt_net_apply_grad(dtt_net* net, const float* grad, float scale, float lr);
+
 /* Writes the guess of increment k into the grid: u~ and the initial contact zone, the
  * current u~ (increment k-1's) kept as the fallback start.  The next solve with init =
  * DTT_INIT_GUESS evaluates the Eq. 5 residual at the guess (its zone) and at the previous

@@ -650,6 +650,37 @@ long long window_surface(const dtt_grid* G, const IncArgs& a) {
     if (d != G->c_axis) n *= a.w.n[d];
   return n;
 }
+
+// Features, targets, forward pass, loss and backward pass of increment k: the gradient in
+// N->g and the loss in N->d_loss (on the net's stream, not synchronised).
+dtt_status inc_loss_grad(dtt_net* N, dtt_grid* G, const double* u_prev2, const double* fn_prev,
+                         const double depth[3], const double* u_target, const double* fn_target) {
+  IncArgs a;
+  dtt_status s = inc_setup(N, G, u_prev2, fn_prev, depth, a);
+  if (s != DTT_OK) return s;
+  cudaStream_t st = N->stream;
+  NCKL(launch_inc_targets(a, u_target, fn_target, N->inc_t, N->inc_m, st));
+  if ((s = forward(N)) != DTT_OK) return s;
+  NCK(cudaMemsetAsync(N->g, 0, (size_t)N->np * sizeof(float), st));
+  NCK(cudaMemsetAsync(N->d_loss, 0, sizeof(double), st));
+  const float wp = N->inc_wp / (float)window_surface(G, a);
+  NCKL(launch_inc_loss(N->y, N->inc_t, N->inc_m, N->d0.V(), NET_COUT, wp, N->gP, N->d_loss, st));
+  return bwd_chain(N);
+}
+
+// DTT_ERR_ARG unless p points into device (or managed) memory: a kernel given a plain host
+// pointer would fault
+dtt_status check_device_floats(const float* p, long long n, const char* what) {
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(DTT_ERR_ARG, std::string(what) + ": not a CUDA pointer");
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return set_error(DTT_ERR_ARG, std::string(what) + ": device memory of " + std::to_string(n) + " floats required");
+  return DTT_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -669,17 +700,9 @@ dtt_status dtt_net_train_increment(dtt_net* N, dtt_grid* G, const double* u_prev
                                    const double depth[3], const double* u_target, const double* fn_target, float lr,
                                    double* loss) {
   if (!N || !G || !u_target || !fn_target || !(lr > 0.f)) return set_error(DTT_ERR_ARG, "bad argument");
-  IncArgs a;
-  dtt_status s = inc_setup(N, G, u_prev2, fn_prev, depth, a);
+  dtt_status s = inc_loss_grad(N, G, u_prev2, fn_prev, depth, u_target, fn_target);
   if (s != DTT_OK) return s;
   cudaStream_t st = N->stream;
-  NCKL(launch_inc_targets(a, u_target, fn_target, N->inc_t, N->inc_m, st));
-  if ((s = forward(N)) != DTT_OK) return s;
-  NCK(cudaMemsetAsync(N->g, 0, (size_t)N->np * sizeof(float), st));
-  NCK(cudaMemsetAsync(N->d_loss, 0, sizeof(double), st));
-  const float wp = N->inc_wp / (float)window_surface(G, a);
-  NCKL(launch_inc_loss(N->y, N->inc_t, N->inc_m, N->d0.V(), NET_COUT, wp, N->gP, N->d_loss, st));
-  if ((s = bwd_chain(N)) != DTT_OK) return s;
   double l = 0.0;
   NCK(cudaMemcpyAsync(&l, N->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
   N->step += 1;
@@ -687,6 +710,35 @@ dtt_status dtt_net_train_increment(dtt_net* N, dtt_grid* G, const double* u_prev
   if ((s = refresh_bf16(N)) != DTT_OK) return s;
   NCK(cudaStreamSynchronize(st));
   if (loss) *loss = l;
+  return DTT_OK;
+}
+
+dtt_status dtt_net_grad_increment(dtt_net* N, dtt_grid* G, const double* u_prev2, const double* fn_prev,
+                                  const double depth[3], const double* u_target, const double* fn_target, float* grad,
+                                  double* loss) {
+  if (!N || !G || !u_target || !fn_target || !grad) return set_error(DTT_ERR_ARG, "bad argument");
+  dtt_status s = check_device_floats(grad, N->np, "grad");
+  if (s != DTT_OK) return s;
+  if ((s = inc_loss_grad(N, G, u_prev2, fn_prev, depth, u_target, fn_target)) != DTT_OK) return s;
+  cudaStream_t st = N->stream;
+  double l = 0.0;
+  NCK(cudaMemcpyAsync(&l, N->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+  NCK(cudaMemcpyAsync(grad, N->g, (size_t)N->np * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  NCK(cudaStreamSynchronize(st));
+  if (loss) *loss = l;
+  return DTT_OK;
+}
+
+dtt_status dtt_net_apply_grad(dtt_net* N, const float* grad, float scale, float lr) {
+  if (!N || !grad || !(lr > 0.f) || !(scale > 0.f) || !std::isfinite(scale))
+    return set_error(DTT_ERR_ARG, "a gradient, lr > 0 and a finite scale > 0 required");
+  dtt_status s = check_device_floats(grad, N->np, "grad");
+  if (s != DTT_OK) return s;
+  cudaStream_t st = N->stream;
+  N->step += 1;
+  NCKL(launch_adam(N->p, grad, N->m, N->v, N->np, lr, N->step, st, scale));
+  if ((s = refresh_bf16(N)) != DTT_OK) return s;
+  NCK(cudaStreamSynchronize(st));
   return DTT_OK;
 }
 

@@ -390,11 +390,12 @@ __global__ void k_loss(const float* __restrict__ y, const float* __restrict__ t,
   }
 }
 
-// Adam on the FP32 master parameters; b1t, b2t = 1 - beta^t
+// Adam on the FP32 master parameters; b1t, b2t = 1 - beta^t; the gradient is gscale * g
+// (gscale = 1: the gradient as stored; 1/W: the mean of W ranks' summed gradients)
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                       long long n, float lr, float b1, float b2, float b1t, float b2t, float eps) {
+                       long long n, float lr, float b1, float b2, float b1t, float b2t, float eps, float gscale) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float gi = g[i];
+    const float gi = g[i] * gscale;
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
@@ -533,10 +534,11 @@ int launch_loss(const float* y, const float* t, int nx, int ny, int nz, int CY, 
   k_loss<<<grid_1d((long long)nx * ny * nz * CY), 256, 0, s>>>(y, t, nx, ny, nz, CY, s2, gy, loss);
   return (int)cudaGetLastError();
 }
-int launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, int step, cudaStream_t s) {
+int launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, int step, cudaStream_t s,
+                float gscale) {
   const float b1 = 0.9f, b2 = 0.999f;
   const float b1t = 1.f - powf(b1, (float)step), b2t = 1.f - powf(b2, (float)step);
-  k_adam<<<grid_1d(n), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, b1t, b2t, 1e-8f);
+  k_adam<<<grid_1d(n), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, b1t, b2t, 1e-8f, gscale);
   return (int)cudaGetLastError();
 }
 int launch_relayout(const float* W, int cin, int cout, __nv_bfloat16* Wt, __nv_bfloat16* Wd, cudaStream_t s) {

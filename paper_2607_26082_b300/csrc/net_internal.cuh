@@ -98,7 +98,8 @@ int launch_add(float* a, const float* b, long long n, cudaStream_t s);
 int launch_f2bf(const float* a, long long n, __nv_bfloat16* b, cudaStream_t s);
 int launch_loss(const float* y, const float* t, int nx, int ny, int nz, int CY, float s2, float* gy, double* loss,
                 cudaStream_t s);
-int launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, int step, cudaStream_t s);
+int launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, int step, cudaStream_t s,
+                float gscale = 1.f);
 int launch_relayout(const float* W, int cin, int cout, __nv_bfloat16* Wt, __nv_bfloat16* Wd, cudaStream_t s);
 int launch_features(const FeatArgs& a, cudaStream_t s);
 int launch_out_to_u(const float* y, long long V, int CY, double scale, double* u, cudaStream_t s);

@@ -13,7 +13,8 @@ NET_CIN = 16
 EXPORTS = ["dtt_net_create", "dtt_net_destroy", "dtt_net_num_params", "dtt_net_get_params", "dtt_net_set_params",
            "dtt_net_loss_grad", "dtt_net_forward", "dtt_net_features", "dtt_net_train_step", "dtt_net_predict",
            "dtt_net_set_loss", "dtt_net_set_increment", "dtt_net_increment_features", "dtt_net_train_increment",
-           "dtt_net_predict_increment", "dtt_net_loss_grad_increment", "dtt_net_layer_trace"]
+           "dtt_net_predict_increment", "dtt_net_loss_grad_increment", "dtt_net_layer_trace", "dtt_net_grad_increment",
+           "dtt_net_apply_grad"]
 _bound = False
 
 
@@ -38,6 +39,8 @@ def _lib():
         L.dtt_net_set_increment.argtypes = [P, f32, f32, i32, i32]
         L.dtt_net_increment_features.argtypes = [P, P, P, P, P, P]
         L.dtt_net_train_increment.argtypes = [P, P, P, P, P, P, P, f32, C.POINTER(C.c_double)]
+        L.dtt_net_grad_increment.argtypes = [P, P, P, P, P, P, P, P, C.POINTER(C.c_double)]
+        L.dtt_net_apply_grad.argtypes = [P, P, f32, f32]
         L.dtt_net_predict_increment.argtypes = [P, P, P, P, P]
         L.dtt_net_loss_grad_increment.argtypes = [P, i32, i32, i32, P, P, P, C.POINTER(C.c_double), P]
         L.dtt_net_layer_trace.argtypes = [P, i32, i32, i32, P, P, i32, P, P, P, P, P]
@@ -55,6 +58,11 @@ def layer_shapes(c1=16, c2=32, c3=64):
     """(cin, cout) of the eleven convolutions in the order of include/dtt_net.h."""
     return [(16, c1), (c1, c1), (c1, c2), (c2, c2), (c2, c3), (c3, c3), (c3, c2), (c2, c2), (c2, c1), (c1, c1),
             (c1, 16)]
+
+
+def _torch():
+    import torch
+    return torch
 
 
 def _f32(a):
@@ -194,6 +202,28 @@ class Net:
                                                   d.ctypes.data_as(C.c_void_p), self._dev(u_target),
                                                   self._dev(fn_target), float(lr), C.byref(loss)))
         return loss.value
+
+    def grad_increment(self, grid, u_prev2, fn_prev, depth, u_target, fn_target, grad):
+        """Loss of increment k; its gradient goes into grad (a float32 CUDA tensor of
+        num_params values), the parameters stay as they are."""
+        if grad.dtype != _torch().float32 or grad.numel() != self.num_params:
+            raise ValueError("grad: float32 CUDA tensor of num_params values")
+        d = np.ascontiguousarray(depth, dtype=np.float64)
+        loss = C.c_double()
+        dtt._check(_lib().dtt_net_grad_increment(self._h, grid._h, self._dev(u_prev2), self._dev(fn_prev),
+                                                 d.ctypes.data_as(C.c_void_p), self._dev(u_target),
+                                                 self._dev(fn_target), self._dev(grad), C.byref(loss)))
+        return loss.value
+
+    def apply_grad(self, grad, scale, lr):
+        """One Adam step with the gradient scale * grad (a float32 CUDA tensor of num_params
+        values, e.g. the sum of the ranks' gradients with scale 1 / their number).  Torch's
+        current stream is synchronised first, since the library reads grad on its own."""
+        if grad.dtype != _torch().float32 or grad.numel() != self.num_params:
+            raise ValueError("grad: float32 CUDA tensor of num_params values")
+        p = self._dev(grad)
+        _torch().cuda.current_stream().synchronize()
+        dtt._check(_lib().dtt_net_apply_grad(self._h, p, float(scale), float(lr)))
 
     def predict_increment(self, grid, u_prev2, fn_prev, depth):
         d = np.ascontiguousarray(depth, dtype=np.float64)

@@ -1,6 +1,12 @@
-"""Batched cells across ranks: each rank solves a share of the cells with its own GPU and
-its own dtt_batch_solve, and only the per-cell reports are gathered on rank 0 at the end
-(no collective on the data path; one solve never spans GPUs).
+"""Work across ranks, one GPU per rank.
+
+Batched cells: each rank solves a share of the cells with its own GPU and its own
+dtt_batch_solve, and only the per-cell reports are gathered on rank 0 at the end (no
+collective on the data path; one solve never spans GPUs).
+
+Warm-start training (train_data_parallel): each rank holds its own training items, and
+every step sums the ranks' gradients with one all-reduce before all ranks take the same
+optimiser step.
 
 lpt_partition assigns cells to ranks by the longest-processing-time-first rule, with the
 voxel count as a cell's cost: cells in decreasing order of cost, each to the rank with the
@@ -52,3 +58,62 @@ def merge_reports(per_rank):
             "rank_voxels": [r["voxels"] for r in per_rank],
             "iterations": {"min": min(its), "max": max(its), "mean": sum(its) / len(its)} if its else None,
             "failed": [c for r in per_rank for c in r["failed"]]}
+
+
+def local_order(seed, epoch, rank, n):
+    """The order in which a rank visits its n items in an epoch (a permutation of its own)."""
+    import numpy as np
+    return [int(j) for j in np.random.default_rng((int(seed), int(epoch), int(rank))).permutation(n)]
+
+
+def step_contributors(counts):
+    """Per step of an epoch, how many ranks hold an item for it: every rank runs
+    max(counts) steps, and a rank past its own items adds a zero gradient."""
+    return [sum(1 for c in counts if c > t) for t in range(max(counts, default=0))]
+
+
+def train_data_parallel(n_local, grad_fn, apply_fn, grad, epochs, lr_at, seed=0, group=None, log=None):
+    """Data-parallel training with one gradient all-reduce per step.
+
+    n_local: this rank's item count; grad_fn(j, grad) writes the gradient of the rank's item
+    j into grad (a float32 tensor on the rank's device) and returns its loss; apply_fn(grad,
+    scale, lr) takes the optimiser step with the gradient scale * grad; lr_at(epoch) the step
+    size.  Per epoch every rank visits its items in local_order; at step t a rank with a
+    t-th item computes its gradient (otherwise zeroes grad), the ranks sum grad with one
+    all-reduce, and every rank applies the sum with scale 1 / (ranks that contributed), the
+    mean gradient of the step.  All ranks apply the same values, so their parameters stay
+    the same.  Without an initialised process group this is the single-rank loop.  Returns
+    the mean loss over all ranks' items per epoch (one small all-reduce per epoch).
+    """
+    import torch
+    import torch.distributed as dist
+    on = dist.is_available() and dist.is_initialized()
+    world = dist.get_world_size(group) if on else 1
+    rank = dist.get_rank(group) if on else 0
+    counts = [int(n_local)]
+    if world > 1:
+        cnt = torch.zeros(world, dtype=torch.int64, device=grad.device)
+        cnt[rank] = int(n_local)
+        dist.all_reduce(cnt, group=group)
+        counts = [int(c) for c in cnt.tolist()]
+    contrib = step_contributors(counts)
+    hist = []
+    for ep in range(epochs):
+        order = local_order(seed, ep, rank, n_local)
+        lr = lr_at(ep)
+        loss_sum = 0.0
+        for t, m in enumerate(contrib):
+            if t < n_local:
+                loss_sum += float(grad_fn(order[t], grad))
+            else:
+                grad.zero_()
+            if world > 1:
+                dist.all_reduce(grad, group=group)
+            apply_fn(grad, 1.0 / m, lr)
+        tot = torch.tensor([loss_sum, float(n_local)], dtype=torch.float64, device=grad.device)
+        if world > 1:
+            dist.all_reduce(tot, group=group)
+        hist.append(float(tot[0] / tot[1]) if float(tot[1]) > 0 else 0.0)
+        if log:
+            log(ep, hist[-1])
+    return hist

@@ -12,7 +12,7 @@ import time
 
 import numpy as np
 
-from . import dtt, rows
+from . import dtt, rows, shard
 from .net import Net
 
 
@@ -151,6 +151,38 @@ def train_increments(net, data, epochs=8, lr=1e-3, seed=0, log=None, k_first=2, 
     return hist
 
 
+def lr_schedule(lr, epochs):
+    """Step size of an epoch: lr, halved every quarter of the epochs (train_increments')."""
+    return lambda ep: lr * 0.5 ** (4 * ep // max(epochs, 1))
+
+
+def train_increments_data_parallel(net, data, epochs=8, lr=1e-3, seed=0, k_first=2, group=None, log=None):
+    """train_increments across ranks (one GPU each): data holds this rank's own seeds (from
+    solve_increments), and every step sums the ranks' gradients of one increment each with
+    one all-reduce of the network's num_params float32 gradient (NCCL between GPUs) before
+    the same Adam step on every rank (shard.train_data_parallel).  On one rank it visits the
+    increments in shard.local_order and is train_increment called in that order.  Returns the mean loss over all ranks' increments per epoch."""
+    import torch
+    items = [(i, k) for i, (_, spec, U, _) in enumerate(data) for k in range(k_first, len(U))]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    grad = torch.zeros(net.num_params, dtype=torch.float32, device=dev)
+
+    def grad_fn(j, gbuf):
+        i, k = items[j]
+        g, spec, U, FN = data[i]
+        g.dtt_move_indenter(spec["indenter"]["centers"][k])
+        u1 = U[k - 1].double().contiguous()
+        u2 = U[k - 2].double().contiguous() if k >= 2 else None
+        ut = U[k].double().contiguous()
+        torch.cuda.current_stream().synchronize()
+        g.dtt_set_initial(u1)
+        return net.grad_increment(g, u2, FN[k - 1], depth_triple(depths(spec), k), ut, FN[k], gbuf)
+
+    hist = shard.train_data_parallel(len(items), grad_fn, net.apply_grad, grad, epochs, lr_schedule(lr, epochs),
+                                     seed=seed, group=group, log=log)
+    return hist, items
+
+
 def secant_start(U, FN, dk, k):
     """The start without the network: the secant prediction of increment k (the step of
     the previous increment scaled like the Hertz force, d^(3/2)) and the previous
@@ -219,7 +251,11 @@ def load_net(path, stream=None):
 def main(argv=None):
     """python -m paper_2607_26082_b300.warmstart train-indent --seeds 2000:2006 [--nvox 384,384,192]
     [--epochs 60] [--lr 1e-3] [--out paper_2607_26082_b300/weights/warmstart_indent.npz]
-    [--eval-seed 3000]"""
+    [--eval-seed 3000]
+
+    Under torchrun (WORLD_SIZE > 1, one GPU per rank) the seeds are dealt round-robin to the
+    ranks, each rank solves its own, and training is data-parallel (one NCCL all-reduce of
+    the gradient per step, train_increments_data_parallel); rank 0 saves and evaluates."""
     import argparse
     import os
     import sys
@@ -242,9 +278,14 @@ def main(argv=None):
     a = ap.parse_args(argv)
     nv = tuple(int(v) for v in a.nvox.split(","))
     s0, s1 = (int(v) for v in a.seeds.split(":"))
+    rank, world, local = shard.rank_world()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     t0 = time.perf_counter()
-    data = []
-    for sd in range(s0, s1):
+    data, mine = [], list(range(s0, s1))[rank::world]
+    for sd in mine:
         spec = wl.indentation_inclusions(sd, *nv, steps=20)
         g, U, FN, reps = solve_increments(spec)
         data.append((g, spec, U, FN))
@@ -253,16 +294,28 @@ def main(argv=None):
     net = make_net(seed=a.seed)
     wl_, wd_ = (int(v) for v in a.window.split(","))
     net.set_increment(a.pressure_weight, a.threshold, wl_, wd_)
-    last = {}
-    hist = train_increments(net, data, epochs=a.epochs, lr=a.lr, last=last,
-                            log=lambda ep, l: print(json.dumps({"epoch": ep, "median_loss": l,
-                                                                "s": round(time.perf_counter() - t0, 1)}), flush=True))
-    worst = sorted(last.items(), key=lambda kv: -kv[1])[:5]
-    print(json.dumps({"largest_last_epoch_losses": [[s0 + i, k, v] for (i, k), v in worst]}), flush=True)
+    if world > 1:
+        hist, _ = train_increments_data_parallel(
+            net, data, epochs=a.epochs, lr=a.lr,
+            log=lambda ep, l: rank == 0 and print(json.dumps({"epoch": ep, "mean_loss": l, "ranks": world,
+                                                              "s": round(time.perf_counter() - t0, 1)}), flush=True))
+    else:
+        last = {}
+        hist = train_increments(net, data, epochs=a.epochs, lr=a.lr, last=last,
+                                log=lambda ep, l: print(json.dumps({"epoch": ep, "median_loss": l,
+                                                                    "s": round(time.perf_counter() - t0, 1)}),
+                                                        flush=True))
+        worst = sorted(last.items(), key=lambda kv: -kv[1])[:5]
+        print(json.dumps({"largest_last_epoch_losses": [[s0 + i, k, v] for (i, k), v in worst]}), flush=True)
     for g, _, _, _ in data:
         g.close()
     del data
     torch.cuda.empty_cache()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+        if rank != 0:
+            return 0
     meta = {"seeds": a.seeds, "nvox": nv, "epochs": a.epochs, "lr": a.lr, "pressure_weight": a.pressure_weight,
             "active_threshold": a.threshold, "window_lateral": wl_, "window_depth": wd_, "loss": hist}
     save_net(net, a.out, meta)

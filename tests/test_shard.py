@@ -94,3 +94,126 @@ def test_two_gloo_ranks_gather_on_root():
     assert merged["voxel_iters"] == sum(c * c for c in [9, 7, 5, 4, 3, 2, 1])
     assert merged["batch_s"] == 2.0
     assert sorted(merged["rank_voxels"]) == [15, 16]
+
+
+# ---- data-parallel training: one gradient all-reduce per step ------------------------------
+# A stand-in model (least squares, float32, plain gradient steps) exercises the host loop of
+# shard.train_data_parallel; the network's own gradient and Adam entry points are checked on
+# the GPU (tests/test_gpu_net_dp.py).
+def _ls_items(rank, n, dim=6, seed=40):
+    rng = np.random.default_rng((seed, rank))
+    return [(rng.standard_normal((4, dim)).astype(np.float32), rng.standard_normal(4).astype(np.float32))
+            for _ in range(n)]
+
+
+def _ls_grad(item, w):
+    A, b = item
+    r = A @ w - b
+    return (2.0 * (A.T @ r)).astype(np.float32), float(r @ r)
+
+
+def _ls_expected(counts, epochs, lr, seed, dim=6):
+    """The same training written out on one process: at step t the gradients of the ranks
+    that hold a t-th item, summed in rank order, times 1 / their number."""
+    items = [_ls_items(r, n, dim) for r, n in enumerate(counts)]
+    w = np.zeros(dim, np.float32)
+    hist = []
+    for ep in range(epochs):
+        orders = [shard.local_order(seed, ep, r, n) for r, n in enumerate(counts)]
+        losses = []
+        for t in range(max(counts)):
+            tot, m = np.zeros(dim, np.float32), 0
+            for r, n in enumerate(counts):
+                if t < n:
+                    g, loss = _ls_grad(items[r][orders[r][t]], w)
+                    tot = tot + g
+                    losses.append(loss)
+                    m += 1
+            w = w - np.float32(lr) * (np.float32(1.0 / m) * tot)
+        hist.append(float(np.mean(losses)))
+    return w, hist
+
+
+def _ls_train(rank, n, epochs, lr, seed):
+    import torch
+    items = _ls_items(rank, n)
+    w = torch.zeros(6, dtype=torch.float32)
+    grad = torch.zeros(6, dtype=torch.float32)
+
+    def grad_fn(j, g):
+        gv, loss = _ls_grad(items[j], w.numpy())
+        g.copy_(torch.from_numpy(gv))
+        return loss
+
+    def apply_fn(g, scale, lr_):
+        w.copy_(w - np.float32(lr_) * (np.float32(scale) * g))
+
+    hist = shard.train_data_parallel(n, grad_fn, apply_fn, grad, epochs, lambda ep: lr, seed=seed)
+    return w.numpy().copy(), hist
+
+
+def test_step_contributors_and_local_order():
+    assert shard.step_contributors([3, 5]) == [2, 2, 2, 1, 1]
+    assert shard.step_contributors([2, 0, 2]) == [2, 2]
+    assert shard.step_contributors([]) == []
+    o = shard.local_order(7, 2, 1, 9)
+    assert sorted(o) == list(range(9)) and o == shard.local_order(7, 2, 1, 9)
+    assert o != shard.local_order(7, 3, 1, 9) or o != shard.local_order(7, 2, 0, 9)
+
+
+def test_data_parallel_single_rank_is_the_plain_loop():
+    pytest.importorskip("torch")
+    w, hist = _ls_train(0, 5, 3, 0.05, 11)
+    w_ref, h_ref = _ls_expected([5], 3, 0.05, 11)
+    np.testing.assert_array_equal(w, w_ref)
+    np.testing.assert_allclose(hist, h_ref, rtol=1e-12)
+
+
+def _dp_rank(rank, world, port, counts, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    calls = []
+    real = dist.all_reduce
+
+    def counted(t, *a, **k):
+        calls.append(t.numel())
+        return real(t, *a, **k)
+
+    dist.all_reduce = counted
+    try:
+        w, hist = _ls_train(rank, counts[rank], 3, 0.05, 11)
+        out[rank] = (w.tolist(), hist, calls)
+    finally:
+        dist.all_reduce = real
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("counts", [(4, 4), (3, 5)])
+def test_data_parallel_two_gloo_ranks(counts):
+    """Two gloo ranks with their own items (equal and unequal counts): the parameters agree
+    on both ranks bit for bit, equal the single-process computation of the mean gradient
+    per step, and each step makes exactly one all-reduce of the gradient (besides one of
+    the item counts at the start and one of the loss per epoch)."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_dp_rank, args=(r, 2, port, list(counts), out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+        res = dict(out)
+    w0, h0, c0 = res[0]
+    w1, h1, c1 = res[1]
+    assert w0 == w1 and h0 == h1
+    w_ref, h_ref = _ls_expected(list(counts), 3, 0.05, 11)
+    np.testing.assert_allclose(np.array(w0, np.float32), w_ref, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(h0, h_ref, rtol=1e-6)
+    steps = max(counts)
+    assert c0 == c1 == [2] + ([6] * steps + [2]) * 3
