@@ -72,6 +72,12 @@ dtt_status dtt_net_features(dtt_net* net, dtt_grid* grid, float* x);
  * converged u~), backward, update.  *loss receives the loss before the update. */
 dtt_status dtt_net_train_step(dtt_net* net, dtt_grid* grid, const double* u_target, float lr, double* loss);
 
+/* The first half of dtt_net_train_step for data-parallel training: features, forward, loss
+ * and backward of one grid, dloss/dparam into grad (device, num_params floats,
+ * caller-owned), the loss into *loss; the parameters and the Adam state are unchanged.
+ * dtt_net_apply_grad (below) takes the step.  DTT_ERR_ARG for a host grad pointer. */
+dtt_status dtt_net_grad_step(dtt_net* net, dtt_grid* grid, const double* u_target, float* grad, double* loss);
+
 /* Writes the network's guess of u~ into the grid (as dtt_set_initial), for a solve with
  * init = DTT_INIT_GUESS. */
 dtt_status dtt_net_predict(dtt_net* net, dtt_grid* grid);

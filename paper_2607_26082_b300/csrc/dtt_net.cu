@@ -393,6 +393,25 @@ double u_scale(const dtt_grid* G) {
 
 }  // namespace
 
+namespace {
+// Features, target, forward pass, loss and backward pass of one cell (the gradient in N->g,
+// the loss on the host).
+dtt_status cell_loss_grad(dtt_net* N, dtt_grid* G, const double* u_target, double* loss) {
+  dtt_status s = grid_features(N, G, whole_grid(G));
+  if (s != DTT_OK) return s;
+  const long long V = N->d0.V();
+  const double inv = 1.0 / u_scale(G);
+  std::vector<float> t((size_t)V * 3);
+  for (int c = 0; c < 3; ++c)
+    for (long long v = 0; v < V; ++v) t[v * 3 + c] = (float)(u_target[c * V + v] * inv);
+  NCK(cudaMemcpyAsync(N->tgt, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice, N->stream));
+  if ((s = forward(N)) != DTT_OK) return s;
+  return backward(N, loss);
+}
+
+dtt_status check_device_floats(const float* p, long long n, const char* what);
+}  // namespace
+
 extern "C" {
 
 dtt_status dtt_net_create(dtt_net** out, int32_t c1, int32_t c2, int32_t c3, uint64_t seed, void* stream) {
@@ -610,20 +629,24 @@ dtt_status dtt_net_features(dtt_net* N, dtt_grid* G, float* x) {
 
 dtt_status dtt_net_train_step(dtt_net* N, dtt_grid* G, const double* u_target, float lr, double* loss) {
   if (!N || !G || !u_target || !(lr > 0.f)) return set_error(DTT_ERR_ARG, "bad argument");
-  dtt_status s = grid_features(N, G, whole_grid(G));
-  if (s != DTT_OK) return s;
-  const long long V = N->d0.V();
-  const double inv = 1.0 / u_scale(G);
-  std::vector<float> t((size_t)V * 3);
-  for (int c = 0; c < 3; ++c)
-    for (long long v = 0; v < V; ++v) t[v * 3 + c] = (float)(u_target[c * V + v] * inv);
-  NCK(cudaMemcpyAsync(N->tgt, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice, N->stream));
-  if ((s = forward(N)) != DTT_OK) return s;
   double l = 0.0;
-  if ((s = backward(N, &l)) != DTT_OK) return s;
+  dtt_status s = cell_loss_grad(N, G, u_target, &l);
+  if (s != DTT_OK) return s;
   N->step += 1;
   NCKL(launch_adam(N->p, N->g, N->m, N->v, N->np, lr, N->step, N->stream));
   if ((s = refresh_bf16(N)) != DTT_OK) return s;
+  NCK(cudaStreamSynchronize(N->stream));
+  if (loss) *loss = l;
+  return DTT_OK;
+}
+
+dtt_status dtt_net_grad_step(dtt_net* N, dtt_grid* G, const double* u_target, float* grad, double* loss) {
+  if (!N || !G || !u_target || !grad) return set_error(DTT_ERR_ARG, "bad argument");
+  dtt_status s = check_device_floats(grad, N->np, "grad");
+  if (s != DTT_OK) return s;
+  double l = 0.0;
+  if ((s = cell_loss_grad(N, G, u_target, &l)) != DTT_OK) return s;
+  NCK(cudaMemcpyAsync(grad, N->g, (size_t)N->np * sizeof(float), cudaMemcpyDeviceToDevice, N->stream));
   NCK(cudaStreamSynchronize(N->stream));
   if (loss) *loss = l;
   return DTT_OK;

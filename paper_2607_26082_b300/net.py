@@ -14,7 +14,7 @@ EXPORTS = ["dtt_net_create", "dtt_net_destroy", "dtt_net_num_params", "dtt_net_g
            "dtt_net_loss_grad", "dtt_net_forward", "dtt_net_features", "dtt_net_train_step", "dtt_net_predict",
            "dtt_net_set_loss", "dtt_net_set_increment", "dtt_net_increment_features", "dtt_net_train_increment",
            "dtt_net_predict_increment", "dtt_net_loss_grad_increment", "dtt_net_layer_trace", "dtt_net_grad_increment",
-           "dtt_net_apply_grad"]
+           "dtt_net_apply_grad", "dtt_net_grad_step"]
 _bound = False
 
 
@@ -41,6 +41,7 @@ def _lib():
         L.dtt_net_train_increment.argtypes = [P, P, P, P, P, P, P, f32, C.POINTER(C.c_double)]
         L.dtt_net_grad_increment.argtypes = [P, P, P, P, P, P, P, P, C.POINTER(C.c_double)]
         L.dtt_net_apply_grad.argtypes = [P, P, f32, f32]
+        L.dtt_net_grad_step.argtypes = [P, P, P, P, C.POINTER(C.c_double)]
         L.dtt_net_predict_increment.argtypes = [P, P, P, P, P]
         L.dtt_net_loss_grad_increment.argtypes = [P, i32, i32, i32, P, P, P, C.POINTER(C.c_double), P]
         L.dtt_net_layer_trace.argtypes = [P, i32, i32, i32, P, P, i32, P, P, P, P, P]
@@ -162,6 +163,17 @@ class Net:
         loss = C.c_double()
         dtt._check(_lib().dtt_net_train_step(self._h, grid._h, u.ctypes.data_as(C.c_void_p), float(lr),
                                              C.byref(loss)))
+        return loss.value
+
+    def grad_step(self, grid, u_target, grad):
+        """Loss of one grid; its gradient goes into grad (a float32 CUDA tensor of num_params
+        values), the parameters stay as they are."""
+        if grad.dtype != _torch().float32 or grad.numel() != self.num_params:
+            raise ValueError("grad: float32 CUDA tensor of num_params values")
+        u = np.ascontiguousarray(u_target, dtype=np.float64)
+        loss = C.c_double()
+        dtt._check(_lib().dtt_net_grad_step(self._h, grid._h, u.ctypes.data_as(C.c_void_p), self._dev(grad),
+                                            C.byref(loss)))
         return loss.value
 
     def predict(self, grid):

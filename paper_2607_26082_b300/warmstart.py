@@ -39,6 +39,18 @@ def train(net, grids, targets, epochs=30, lr=2e-3, seed=0, log=None):
     return hist
 
 
+def train_data_parallel(net, grids, targets, epochs=30, lr=2e-3, seed=0, group=None, log=None):
+    """train across ranks (one GPU each): grids and targets are this rank's own cells (from
+    solve_targets), and every step sums the ranks' gradients of one cell each with one
+    all-reduce before the same Adam step on every rank (shard.train_data_parallel).  Returns
+    the mean loss over all ranks' cells per epoch."""
+    import torch
+    idx = [i for i, t in enumerate(targets) if t is not None]
+    grad = torch.zeros(net.num_params, dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
+    return shard.train_data_parallel(len(idx), lambda j, gbuf: net.grad_step(grids[idx[j]], targets[idx[j]], gbuf),
+                                     net.apply_grad, grad, epochs, lambda ep: lr, seed=seed, group=group, log=log)
+
+
 def evaluate(net, specs, precision=dtt.PREC_MIXED, tol=1e-6, graph_iters=16):
     """Per cell: plain start vs network guess (INIT_GUESS)."""
     out = []

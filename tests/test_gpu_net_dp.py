@@ -1,5 +1,6 @@
-"""Data-parallel training of the increment warm start on the GPU: the two halves of
-dtt_net_train_increment (dtt_net_grad_increment, dtt_net_apply_grad) give its parameters,
+"""Data-parallel training of the warm start on the GPU: the two halves of
+dtt_net_train_increment (dtt_net_grad_increment, dtt_net_apply_grad) and of
+dtt_net_train_step (dtt_net_grad_step, dtt_net_apply_grad) give their parameters,
 the gradient scale of apply_grad is exact for powers of two, the single-rank data-parallel
 loop equals train_increment calls in the same order, and the entry points reject host
 pointers and bad scales without launching anything.  The all-reduce between ranks is
@@ -130,3 +131,34 @@ def test_grad_entry_points_reject_host_memory_and_bad_scales(increments):
             net.apply_grad(dev, scale, 1e-3)
     np.testing.assert_array_equal(net.get_params(), p0)
     net.close()
+
+
+def test_cell_mode_grad_then_apply_is_train_step():
+    """The cell mode's split (dtt_net_grad_step, dtt_net_apply_grad) against
+    dtt_net_train_step, and its single-rank data-parallel loop against train_step calls in
+    the same order, on solver-produced cells."""
+    specs = [wl.batch_cell(5000 + i, sizes=(12, 16)) for i in range(3)]
+    grids, targets, reps = warmstart.solve_targets(specs, tol=1e-6)
+    assert all(t is not None for t in targets)
+    a, b = Net(16, 32, 64, seed=9), Net(16, 32, 64, seed=9)
+    p0 = a.get_params()
+    grad = torch.zeros(a.num_params, dtype=torch.float32, device="cuda")
+    for i, lr in ((0, 2e-3), (1, 1e-3), (2, 2e-3)):
+        la = a.train_step(grids[i], targets[i], lr)
+        lb = b.grad_step(grids[i], targets[i], grad)
+        assert abs(la - lb) <= 1e-5 * abs(la)
+        if i == 0:
+            np.testing.assert_array_equal(b.get_params(), p0)
+        b.apply_grad(grad, 1.0, lr)
+        _same_steps(a.get_params(), b.get_params(), p0)
+    c, d = Net(16, 32, 64, seed=9), Net(16, 32, 64, seed=9)
+    hist = warmstart.train_data_parallel(c, grids, targets, epochs=2, lr=1e-3, seed=2)
+    ref = []
+    for ep in range(2):
+        ref.append(float(np.mean([d.train_step(grids[j], targets[j], 1e-3) for j in shard.local_order(2, ep, 0, 3)])))
+    _same_steps(c.get_params(), d.get_params(), p0)
+    np.testing.assert_allclose(hist, ref, rtol=1e-3)
+    for n in (a, b, c, d):
+        n.close()
+    for g in grids:
+        g.close()
