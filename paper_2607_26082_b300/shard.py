@@ -60,6 +60,23 @@ def merge_reports(per_rank):
             "failed": [c for r in per_rank for c in r["failed"]]}
 
 
+class RankFailure(RuntimeError):
+    """A collective of the training loop failed: another rank left (crashed, raised, or
+    stopped answering until the process group's timeout).  Carries where it happened."""
+
+    def __init__(self, epoch, step, cause):
+        super().__init__("data-parallel training: collective failed at epoch %d, step %d (another rank left?): %s"
+                         % (epoch, step, cause))
+        self.epoch, self.step = epoch, step
+
+
+def _all_reduce(dist, t, group, epoch, step):
+    try:
+        dist.all_reduce(t, group=group)
+    except RuntimeError as e:    # gloo and NCCL report a lost peer or a timeout this way
+        raise RankFailure(epoch, step, e) from e
+
+
 def local_order(seed, epoch, rank, n):
     """The order in which a rank visits its n items in an epoch (a permutation of its own)."""
     import numpy as np
@@ -84,6 +101,12 @@ def train_data_parallel(n_local, grad_fn, apply_fn, grad, epochs, lr_at, seed=0,
     mean gradient of the step.  All ranks apply the same values, so their parameters stay
     the same.  Without an initialised process group this is the single-rank loop.  Returns
     the mean loss over all ranks' items per epoch (one small all-reduce per epoch).
+
+    A rank that fails leaves the others blocked in their next all-reduce until the backend
+    reports the lost peer or the process group's timeout ends it; they then raise
+    RankFailure with the epoch and step (step -1: the start; step = the epoch's step count:
+    its loss reduction).  Ranks enter each all-reduce only between optimiser steps, with no
+    kernel of theirs in flight.
     """
     import torch
     import torch.distributed as dist
@@ -94,7 +117,7 @@ def train_data_parallel(n_local, grad_fn, apply_fn, grad, epochs, lr_at, seed=0,
     if world > 1:
         cnt = torch.zeros(world, dtype=torch.int64, device=grad.device)
         cnt[rank] = int(n_local)
-        dist.all_reduce(cnt, group=group)
+        _all_reduce(dist, cnt, group, -1, -1)
         counts = [int(c) for c in cnt.tolist()]
     contrib = step_contributors(counts)
     hist = []
@@ -108,11 +131,11 @@ def train_data_parallel(n_local, grad_fn, apply_fn, grad, epochs, lr_at, seed=0,
             else:
                 grad.zero_()
             if world > 1:
-                dist.all_reduce(grad, group=group)
+                _all_reduce(dist, grad, group, ep, t)
             apply_fn(grad, 1.0 / m, lr)
         tot = torch.tensor([loss_sum, float(n_local)], dtype=torch.float64, device=grad.device)
         if world > 1:
-            dist.all_reduce(tot, group=group)
+            _all_reduce(dist, tot, group, ep, len(contrib))
         hist.append(float(tot[0] / tot[1]) if float(tot[1]) > 0 else 0.0)
         if log:
             log(ep, hist[-1])

@@ -217,3 +217,59 @@ def test_data_parallel_two_gloo_ranks(counts):
     np.testing.assert_allclose(h0, h_ref, rtol=1e-6)
     steps = max(counts)
     assert c0 == c1 == [2] + ([6] * steps + [2]) * 3
+
+
+def _dp_failing_rank(rank, world, port, out):
+    import datetime
+    import time as _time
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    from paper_2607_26082_b300 import shard as sh
+    items = _ls_items(rank, 4)
+    w = torch.zeros(6, dtype=torch.float32)
+    grad = torch.zeros(6, dtype=torch.float32)
+    seen = []
+
+    def grad_fn(j, g):
+        if rank == 1 and len(seen) == 2:
+            os._exit(3)                    # rank 1 dies before its third gradient
+        seen.append(j)
+        gv, loss = _ls_grad(items[j], w.numpy())
+        g.copy_(torch.from_numpy(gv))
+        return loss
+
+    def apply_fn(g, scale, lr_):
+        w.copy_(w - np.float32(lr_) * (np.float32(scale) * g))
+
+    t0 = _time.monotonic()
+    try:
+        sh.train_data_parallel(4, grad_fn, apply_fn, grad, 2, lambda ep: 0.05, seed=11)
+        out[rank] = ("finished",)
+    except sh.RankFailure as e:
+        out[rank] = ("RankFailure", e.epoch, e.step, _time.monotonic() - t0)
+
+
+def test_data_parallel_rank_failure_is_reported_not_hung():
+    """Failure detection without a GPU: rank 1 exits in the middle of epoch 0 (before its
+    third gradient); rank 0 does not hang in the all-reduce of that step but raises
+    RankFailure naming epoch 0, step 2, well within the process group's timeout."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_dp_failing_rank, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+        codes = [p.exitcode for p in procs]
+        res = dict(out)
+    assert codes == [0, 3]
+    kind, epoch, step, secs = res[0]
+    assert kind == "RankFailure" and (epoch, step) == (0, 2)
+    assert secs < 20.0
