@@ -75,7 +75,8 @@ dtt_status dtt_net_train_step(dtt_net* net, dtt_grid* grid, const double* u_targ
 /* The first half of dtt_net_train_step for data-parallel training: features, forward, loss
  * and backward of one grid, dloss/dparam into grad (device, num_params floats,
  * caller-owned), the loss into *loss; the parameters and the Adam state are unchanged.
- * dtt_net_apply_grad (below) takes the step.  DTT_ERR_ARG for a host grad pointer. */
+ * dtt_net_apply_grad (below) takes the step.  DTT_ERR_ARG for a grad pointer that is not
+ * device memory of the current device. */
 dtt_status dtt_net_grad_step(dtt_net* net, dtt_grid* grid, const double* u_target, float* grad, double* loss);
 
 /* Writes the network's guess of u~ into the grid (as dtt_set_initial), for a solve with
@@ -154,7 +155,8 @@ dtt_status dtt_net_train_increment(dtt_net* net, dtt_grid* grid, const double* u
  * grad_increment followed by apply_grad(scale 1) on its output is train_increment (the
  * weight gradients are summed with float atomics, so any two evaluations of one gradient
  * agree to the order of those sums, about 1e-7 relative).  Both calls synchronise the net's
- * stream before returning; DTT_ERR_ARG for a host pointer, lr <= 0 or a bad scale. */
+ * stream before returning; DTT_ERR_ARG for a host pointer, memory of another device than
+ * the current one, lr <= 0 or a bad scale. */
 dtt_status dtt_net_grad_increment(dtt_net* net, dtt_grid* grid, const double* u_prev2, const double* fn_prev,
                                   const double depth[3], const double* u_target, const double* fn_target, float* grad,
                                   double* loss);

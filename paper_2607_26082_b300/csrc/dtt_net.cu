@@ -691,8 +691,9 @@ dtt_status inc_loss_grad(dtt_net* N, dtt_grid* G, const double* u_prev2, const d
   return bwd_chain(N);
 }
 
-// DTT_ERR_ARG unless p points into device (or managed) memory: a kernel given a plain host
-// pointer would fault
+// DTT_ERR_ARG unless p points into managed memory or device memory of the current device
+// (the net's): a kernel given a plain host pointer, or another GPU's memory without peer
+// access, would fault
 dtt_status check_device_floats(const float* p, long long n, const char* what) {
   cudaPointerAttributes at{};
   cudaError_t e = cudaPointerGetAttributes(&at, p);
@@ -702,6 +703,11 @@ dtt_status check_device_floats(const float* p, long long n, const char* what) {
   }
   if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
     return set_error(DTT_ERR_ARG, std::string(what) + ": device memory of " + std::to_string(n) + " floats required");
+  int cur = -1;
+  NCK(cudaGetDevice(&cur));
+  if (at.type == cudaMemoryTypeDevice && at.device != cur)
+    return set_error(DTT_ERR_ARG, std::string(what) + ": memory of device " + std::to_string(at.device) +
+                                      ", not of the current device " + std::to_string(cur));
   return DTT_OK;
 }
 }  // namespace
