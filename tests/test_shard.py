@@ -190,19 +190,21 @@ def _dp_rank(rank, world, port, counts, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("counts", [(4, 4), (3, 5)])
-def test_data_parallel_two_gloo_ranks(counts):
-    """Two gloo ranks with their own items (equal and unequal counts): the parameters agree
-    on both ranks bit for bit, equal the single-process computation of the mean gradient
-    per step, and each step makes exactly one all-reduce of the gradient (besides one of
-    the item counts at the start and one of the loss per epoch)."""
+@pytest.mark.parametrize("counts", [(4, 4), (3, 5), (2, 5, 0)])
+def test_data_parallel_gloo_ranks(counts):
+    """Two or three gloo ranks with their own items (equal and unequal counts, one rank
+    without any): the parameters agree on every rank bit for bit, equal the single-process
+    computation of the mean gradient per step, and each step makes exactly one all-reduce
+    of the gradient (besides one of the item counts at the start and one of the loss per
+    epoch)."""
     pytest.importorskip("torch")
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
     with ctx.Manager() as m:
         out = m.dict()
         port = _free_port()
-        procs = [ctx.Process(target=_dp_rank, args=(r, 2, port, list(counts), out)) for r in range(2)]
+        world = len(counts)
+        procs = [ctx.Process(target=_dp_rank, args=(r, world, port, list(counts), out)) for r in range(world)]
         for p in procs:
             p.start()
         for p in procs:
@@ -210,13 +212,13 @@ def test_data_parallel_two_gloo_ranks(counts):
             assert p.exitcode == 0
         res = dict(out)
     w0, h0, c0 = res[0]
-    w1, h1, c1 = res[1]
-    assert w0 == w1 and h0 == h1
+    for r in range(1, len(counts)):
+        assert res[r] == res[0]
     w_ref, h_ref = _ls_expected(list(counts), 3, 0.05, 11)
     np.testing.assert_allclose(np.array(w0, np.float32), w_ref, rtol=1e-6, atol=1e-7)
     np.testing.assert_allclose(h0, h_ref, rtol=1e-6)
     steps = max(counts)
-    assert c0 == c1 == [2] + ([6] * steps + [2]) * 3
+    assert c0 == [len(counts)] + ([6] * steps + [2]) * 3
 
 
 def _dp_failing_rank(rank, world, port, out):
