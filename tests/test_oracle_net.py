@@ -3,7 +3,6 @@ convolution against scipy.ndimage.correlate, the backward pass against central f
 differences of the loss, the pooling / upsampling adjoint identities, and the input
 features of a small cell checked channel by channel."""
 import numpy as np
-import pytest
 from scipy import ndimage
 
 import workloads as wl

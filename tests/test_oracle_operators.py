@@ -1,6 +1,5 @@
 """Pins of the oracle operators: gradients, divergence, the Paux symbol (P2 eigenmodes),
 the Green step and the Eq. 5 residual (Sections 3.1-3.2)."""
-import itertools
 
 import numpy as np
 import pytest
