@@ -226,3 +226,44 @@ def test_constraint_validation():
         cs.check_rows(pb, [cs.strong_row(pb, (0, 1, 1), 0, 0.0)])
     with pytest.raises(ValueError):
         cs.check_rows(pb, [cs.strong_row(pb, (1, 1, 1), 1, 0.0), cs.weak_voxel_row(pb, (1, 1, 1), 1, 0.0)])
+
+
+def test_contact_solution_is_a_kkt_point_of_the_assembled_energy():
+    """Pin of Algorithm 2 against the plain definition of the contact problem (Section 5.1,
+    Eq. 33): the converged increments minimise the discrete energy over the points outside
+    the sphere.  With K and the prescribed-strain force assembled element by element in
+    kkt.py (independently of the solver's operators), the energy gradient r = K u~ + F* at
+    the oracle's solution vanishes at every free DOF off the contact zone, is normal to the
+    sphere at every contact node (no tangential part: frictionless), points into the body
+    (a non-negative multiplier of the constraint g >= 0, whose gradient is -n_c), and its
+    normal part is the reported reaction f_n, whose sum is the reported force."""
+    w = wl.indentation(10, 10, 6, R=4.0, steps=2, dmin=0.05, dmax=0.15)
+    pb = dz.problem_from(w)
+    I = w.indenter
+    K, Fs = kkt.assemble(pb)
+    nn = int(np.prod(pb.node_shape))
+    free = np.concatenate([pb.dof_mask(c).ravel() for c in range(3)])
+    u = np.zeros((3,) + pb.node_shape)
+    for O in I["centers"]:
+        ind = cs.Indenter(pb, I["axis"], I["face"], O, I["radius"])
+        res = sv.solve_alg2_increment(pb, ind, [], w.lam0, w.mu0, 1e-11, 5000, u)
+        assert res.converged
+        u = res.u
+        r = K @ u.ravel() + Fs
+        act = res.active
+        an = ind.nodes[act]
+        assert act.sum() >= 5
+        cdofs = np.concatenate([an + c * nn for c in range(3)])
+        assert free[cdofs].all()
+        off = free.copy()
+        off[cdofs] = False
+        R3 = np.stack([r[an + c * nn] for c in range(3)])
+        scale = np.abs(R3).max()
+        assert np.abs(r[off]).max() <= 1e-11 * scale
+        _, n = cs.contact_geometry(pb, ind, u)
+        N3 = n[:, act]
+        rn = (R3 * N3).sum(axis=0)
+        assert np.abs(R3 - rn * N3).max() <= 1e-11 * scale
+        assert (rn < 0).all()
+        assert np.allclose(rn, res.fn[act], rtol=1e-10, atol=1e-12 * scale)
+        assert abs(R3[2].sum() - res.force[2]) <= 1e-10 * abs(res.force[2])
