@@ -182,3 +182,47 @@ def test_fs_contact_tends_to_small_strain():
     d1 = F["FS", 0.0005][0] / F["SS", 0.0005][0] - 1.0
     d2 = F["FS", 0.005][0] / F["SS", 0.005][0] - 1.0
     assert abs(d2) > 1e-3 and abs(d2 / d1 - 10.0) < 0.5
+
+
+def test_fs_contact_solution_is_stationary_for_the_svk_energy():
+    """Pin of Algorithm 3's converged increments against the energy they minimise over the
+    points outside the sphere (Section 5.2 with Eq. 33): central differences of the discrete
+    St Venant-Kirchhoff energy (_energy, written from its definition, not from the solver's
+    Pi) vanish along a random direction of the free DOFs off the contact zone and along the
+    sphere's tangent at every contact node, and along the normal n_c of a contact node they
+    equal the reported reaction f_n (negative: the multiplier of g >= 0 is non-negative)."""
+    from oracle import constraints as cs
+    w = __import__("workloads").indentation(10, 10, 6, R=4.0, steps=2, dmin=0.05, dmax=0.15)
+    pb = dz.problem_from(w)
+    I = w.indenter
+    free = np.stack([pb.dof_mask(c) for c in range(3)])
+    rng = np.random.default_rng(1)
+    u = np.zeros((3,) + pb.node_shape)
+    step = 1e-6
+
+    def slope(v):
+        return (_energy(pb, u + step * v) - _energy(pb, u - step * v)) / (2 * step)
+
+    for O in I["centers"]:
+        ind = cs.Indenter(pb, I["axis"], I["face"], O, I["radius"])
+        res = osv.solve_alg2_increment(pb, ind, [], w.lam0, w.mu0, 1e-11, 5000, u, kinematics="FS")
+        assert res.converged
+        u = res.u
+        act = res.active
+        an = ind.nodes[act]
+        assert act.sum() >= 5
+        fn = res.fn[act]
+        tol = 1e-8 * np.abs(fn).max()
+        _, n = cs.contact_geometry(pb, ind, u)
+        v = rng.standard_normal(u.shape) * free
+        v.reshape(3, -1)[:, an] = 0.0
+        assert abs(slope(v / np.linalg.norm(v))) <= tol
+        for j, M in enumerate(an):
+            nv = n[:, act][:, j]
+            t = np.cross(nv, [1.0, 0.3, 0.0])
+            t /= np.linalg.norm(t)
+            for d, want in ((nv, fn[j]), (t, 0.0)):
+                e = np.zeros_like(u)
+                e.reshape(3, -1)[:, M] = d
+                assert abs(slope(e) - want) <= tol, (M, slope(e), want)
+        assert (fn < 0).all()
